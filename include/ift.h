@@ -1,0 +1,170 @@
+/*
+ * ift.h -- C ABI of the GB300 implementation of the EQP-IFT online hot path
+ * (implicit feature tracking with empirical quadrature, arXiv 2305.15661).
+ *
+ * The library evaluates, on one GPU, the weighted reduced residuals and
+ * Gauss-Newton system of the hyperreduced implicit-feature-tracking model and
+ * solves it with Levenberg-Marquardt:
+ *   state U = Phi w, mesh x = X + Psi tau                      (Sec. 3.1)
+ *   S~ = sum_e rho_e (Phi_e^T dR_e/dU_e^T + Phi_e'^T dR_e/dU_e'^T) R_e
+ *   T~ = sum_e rho_e Psi_e^T (dR_e/dx_e^T R_e + dN_e/dx_e^T N_e)  (Eqs. ift-eqp-res0, ift-res-elem2)
+ *   H  = sum_e rho_e [A_w A_t]^T [A_w A_t] (+ distortion block)  (Eq. levmarq-elem)
+ *   J~ = sum_e rho_e (|R_e|^2 + N_e^2) / 2                         (Eq. ift-opt-eqp2)
+ * with A_w = dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e', A_t = dR_e/dx_e Psi_e.
+ * The paper's notation w, tau is written y, z in the argument names.
+ *
+ * Conventions for every call:
+ *  - All pointers are HOST pointers unless the function name ends in "_dev";
+ *    host inputs are copied in and the caller keeps ownership. "_dev" calls take
+ *    device pointers and run on the stream given at ift_create (or the stream
+ *    argument), asynchronously, and write their outputs to caller buffers.
+ *  - Floating-point inputs and outputs are IEEE double, integers int32/int64,
+ *    all arrays dense and row-major (C order).
+ *  - Degrees of freedom are element-major: DOF index = e*n_u + node*m + var, with
+ *    n_u = n_b*m (m = 1 Burgers, m = 4 Euler); nodal order per element as
+ *    ift_reference_nodes() reports. Mesh coordinates are vertex-major:
+ *    x[v*dim + c].
+ *  - Call order: ift_create -> ift_set_mesh -> ift_set_bases -> (ift_set_eq_weights)
+ *    -> evaluate / solve. Out-of-order calls return IFT_ERR_STATE. Without
+ *    ift_set_eq_weights every element has weight 1 (the unweighted ROM,
+ *    Remark rom-eqp-ones).
+ *  - Errors are returned as status codes; ift_last_error() gives the message.
+ *    No call aborts, traps or prints. A failed call leaves the context usable.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef IFT_H
+#define IFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ift_ctx ift_ctx;
+
+typedef enum {
+  IFT_OK = 0,
+  IFT_NOT_CONVERGED = 1,     /* solver hit max_iters; outputs are the last iterate */
+  IFT_LINESEARCH_FAILED = 2, /* no step length in 1, 1/2, ..., 2^-30 gave sufficient decrease */
+  IFT_ERR_ARG = -1,          /* bad argument (size, pointer, degree, mesh orientation) */
+  IFT_ERR_STATE = -2,        /* call out of order */
+  IFT_ERR_CUDA = -3,         /* CUDA runtime error (message in ift_last_error) */
+  IFT_ERR_OOM = -4,          /* device allocation failed */
+  IFT_ERR_NONPHYSICAL = -5,  /* evaluation point has g <= 0, rho <= 0 or P <= 0, or non-finite R */
+  IFT_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
+  IFT_ERR_NOTIMPL = -7       /* combination of options not built */
+} ift_status;
+
+enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
+/* Arithmetic of the element evaluation and contraction. IFT_FP64: all FP64.
+   IFT_FP32: FP32 element kernels and contraction with FP32 accumulation of each
+   element's products, FP64 accumulation across elements. The LM normal
+   equations, line search and stopping test are FP64 in every mode. */
+enum { IFT_FP64 = 0, IFT_FP32 = 1 };
+/* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
+   LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */
+enum { IFT_INIT_PAPER = 0, IFT_INIT_GIVEN = 1 };
+
+typedef struct {
+  int problem;        /* IFT_BURGERS1D or IFT_EULER2D */
+  int p;              /* DG degree: Burgers 1..3, Euler 1..3 */
+  int precision;      /* IFT_FP64 or IFT_FP32 */
+  double gamma;       /* ratio of specific heats (Euler) */
+  double kappa;       /* distortion weight kappa of Eq. dist_elem0 (>= 0) */
+  double eps_g;       /* epsilon of Eq. dist_elem1 (the paper uses 1e-8) */
+  double tol;         /* stop when |[S~;T~]| <= tol * max(1, |[S~;T~]| at phase start) */
+  int max_iters;      /* per LM phase */
+  int lm_init;        /* IFT_INIT_PAPER or IFT_INIT_GIVEN */
+} ift_config;
+
+/* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,
+   max_iters 200, FP64, IFT_INIT_PAPER. */
+void ift_config_default(ift_config* cfg);
+
+/* Creates a context on the current CUDA device. stream: a cudaStream_t to run on
+   (NULL = a stream owned by the context). Returns IFT_ERR_ARG for a bad problem
+   or degree, IFT_ERR_CUDA if no device is usable. */
+ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out);
+ift_status ift_destroy(ift_ctx* ctx);
+const char* ift_last_error(const ift_ctx* ctx);
+/* Message for a failed ift_create (thread-local). */
+const char* ift_create_error(void);
+
+/* Reference element of the context: nodes (n_b x dim master coordinates:
+   [0,1] for Burgers, triangle (0,0),(1,0),(0,1) for Euler) and, per face, its
+   p+1 trace nodes in the face's direction (n_face x n_trace). Sizes come from
+   ift_sizes. */
+ift_status ift_reference_nodes(const ift_ctx* ctx, double* nodes, int32_t* face_nodes);
+
+/* sizes[0..7] = n_b, n_u, n_u' (neighbour trace DOFs per element), n_x per element,
+   n_face, n_trace, n_q (volume points), n_fq (points per face). */
+ift_status ift_sizes(const ift_ctx* ctx, int64_t* sizes);
+
+/* Mesh (Sec. 2.3, Eq. hdm_elem): reference nodes X (n_verts x dim) and simplices
+   elem_verts (n_elems x (dim+1)), counter-clockwise (Burgers: left to right).
+   Faces are matched by shared vertices; unmatched faces are boundary faces:
+   Euler far field U_inf(mu); Burgers inflow u = 1 on the face with outward
+   normal -x, outflow (exterior = interior state) on the other.
+   Returns IFT_ERR_ARG for an inverted element or a face shared three times. */
+ift_status ift_set_mesh(ift_ctx* ctx, int64_t n_verts, const double* X, int64_t n_elems,
+                        const int32_t* elem_verts);
+
+/* Bases of the implicit-feature-tracking manifold (Sec. 3.1): Phi (N_u x k_u),
+   Psi (N_x x k_x), N_u = n_elems*n_u, N_x = n_verts*dim. k_u >= 1, k_x >= 0,
+   k_u + k_x <= 64. */
+ift_status ift_set_bases(ift_ctx* ctx, int64_t N_u, int k_u, const double* Phi, int64_t N_x, int k_x,
+                         const double* Psi);
+
+/* Empirical-quadrature weights (Eq. ift-eqp-res0): nnz pairs (elem[i], rho[i]),
+   elements distinct, rho > 0. nnz = -1 restores rho = 1 on every element.
+   Only the listed elements (and their neighbours' trace rows of Phi) are read by
+   the evaluation (the hyperreduced gather, Sec. 3.2.1). */
+ift_status ift_set_eq_weights(ift_ctx* ctx, int64_t nnz, const int32_t* elem, const double* rho);
+
+/* Weighted reduced residuals, Gauss-Newton matrix and objective at (y, z) = (w, tau):
+   S (k_u), T (k_x), H ((k_u+k_x)^2, full symmetric), J (1). mu: problem
+   parameters (Burgers: mu[0]; Euler: mu = (Mach, angle in radians)).
+   Any output pointer may be NULL. Returns IFT_ERR_NONPHYSICAL (outputs written,
+   J = +inf) when an element with non-zero weight is non-physical at (y, z). */
+ift_status ift_reduced_residual_jacobian(ift_ctx* ctx, const double* mu, const double* y, const double* z,
+                                         double* S, double* T, double* H, double* J);
+ift_status ift_reduced_residual_jacobian_dev(ift_ctx* ctx, const double* mu, const double* y, const double* z,
+                                             double* S, double* T, double* H, double* J, void* stream);
+
+/* Per-element residuals and Jacobians at a full state (inspection of the
+   element kernel): for each of the n listed elements, R_e (n_u), dR_e/dU_e
+   (n_u x n_u), dR_e/dU_e' (n_u x n_u'), dR_e/dx_e (n_u x n_x), N_e and dN_e/dx_e
+   (n_x), at global state U (N_u) and mesh x (N_x). U_e' is the neighbours'
+   trace nodes, face by face, ordered along this element's face direction,
+   m variables each (zero on boundary faces). Output pointers may be NULL. */
+ift_status ift_element_eval(ift_ctx* ctx, const double* mu, const double* U, const double* x, int64_t n,
+                            const int32_t* elems, double* R, double* JU, double* JUp, double* Jx, double* N,
+                            double* dN);
+
+typedef struct {
+  int status;          /* ift_status of the solve */
+  int init_iters;      /* accepted LM steps of the w-only initialisation */
+  int iters;           /* accepted LM steps of the joint iteration */
+  int trials;          /* objective evaluations in line searches */
+  int shifts;          /* Cholesky diagonal shifts */
+  double J;            /* final objective */
+  double normS, normT; /* final |S~|, |T~| */
+  double g0;           /* |[S~;T~]| at the start of the joint iteration */
+} ift_solve_info;
+
+/* Levenberg-Marquardt solve of the hyperreduced problem (Sec. 3.2.3):
+   (H + diag(0, lambda I)) dz = -[S~; T~], Armijo backtracking on J~,
+   lambda_0 = 1e-4, lambda/10 after a full step, 10 lambda after a shortened one.
+   With IFT_INIT_PAPER y and z are outputs only; with IFT_INIT_GIVEN they are
+   also the start. Returns the final status (also in info->status). */
+ift_status ift_solve_rom(ift_ctx* ctx, const double* mu, double* y, double* z, ift_solve_info* info);
+ift_status ift_solve_rom_dev(ift_ctx* ctx, const double* mu, double* y, double* z, ift_solve_info* info_host,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFT_H */

@@ -1,0 +1,838 @@
+// C ABI of the EQP-IFT GB300 library (declared in include/ift.h).
+//
+// The context owns every device buffer: mesh and connectivity, bases, weights,
+// reference tables, per-CTA partial sums, the reduced result and the solver
+// state. The solve is a CUDA graph whose while-loop body is
+// [assemble at the trial point -> reduce the CTA partials -> LM step]; the LM
+// step kernel sets the loop condition, so a whole solve is one graph launch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ift.h"
+#include "elem.cuh"
+#include "kernels.h"
+#include "lm.cuh"
+#include "refelem.h"
+
+namespace ift {
+__global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
+                               int use_cond);
+__global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0, int ku, int kx, int phase);
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);
+__global__ void phit_u_partial_kernel(const double* Phi, long Nu, int ku, int m, int problem, double gamma,
+                                      const double* mu, long chunk, double* part);
+__global__ void sum_columns_kernel(const double* part, int nparts, int ku, double* w);
+}  // namespace ift
+
+using namespace ift;
+
+namespace {
+
+constexpr int kWarpsPerCta = 2;
+constexpr int kPhitBlocks = 256;
+thread_local std::string g_create_error;
+
+// Unpack [H | g | J | count] into separate outputs; J = +inf if any element was non-physical.
+__global__ void unpack_kernel(const double* res, int ku, int kx, double* S, double* T, double* H, double* J) {
+  const int k = ku + kx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k * k + k + 1; i += gridDim.x * blockDim.x) {
+    if (i < k * k) {
+      if (H) H[i] = res[i];
+    } else if (i < k * k + ku) {
+      if (S) S[i - k * k] = res[i];
+    } else if (i < k * k + k) {
+      if (T) T[i - k * k - ku] = res[i];
+    } else if (J) {
+      J[0] = res[k * k + k + 1] > 0.0 ? INFINITY : res[k * k + k];
+    }
+  }
+}
+
+}  // namespace
+
+struct ift_ctx {
+  ift_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  RefTables T;
+  int dim = 1, m = 1, nv = 2, nb = 0, nu = 0, nup = 0, nxe = 0, nface = 0, ntrace = 0, nq = 0, nfq = 0;
+  KernelSet ks64, ksP;
+  int sm_count = 0;
+  double* d_tables = nullptr;
+  // mesh
+  bool have_mesh = false;
+  int64_t n_verts = 0, n_elems = 0;
+  double* d_X = nullptr;
+  int* d_ev = nullptr;
+  int* d_nbr = nullptr;
+  int* d_nbrf = nullptr;
+  signed char* d_bc = nullptr;
+  // bases
+  bool have_bases = false;
+  int ku = 0, kx = 0;
+  double* d_Phi = nullptr;
+  float* d_Phi32 = nullptr;
+  double* d_Psi = nullptr;
+  // weights
+  int64_t nnz = -1;
+  int* d_elems = nullptr;
+  double* d_rho = nullptr;
+  // work buffers
+  double* d_mu = nullptr;       // 4
+  double* d_w = nullptr;        // LM_KMAX
+  double* d_tau = nullptr;      // LM_KMAX
+  double* d_res = nullptr;      // nacc
+  double* d_partial = nullptr;  // max_parts * nacc
+  int max_parts = 0;
+  double* d_phit = nullptr;     // kPhitBlocks * LM_KMAX
+  LMState* d_lm = nullptr;
+  // launch plan of the element kernels, index 0: objective only, 1: fused assembly
+  int plan_grid[2] = {0, 0};
+  size_t plan_smem[2] = {0, 0};
+  int plan_epoch = -1;
+  // solve graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_epoch = -1;
+  int epoch = 0;
+  bool graph_failed = false;
+
+  ift_status fail(ift_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+  }
+  ift_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? IFT_ERR_OOM : IFT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+  int nacc() const { return (ku + kx) * (ku + kx) + ku + kx + 2; }
+};
+
+#define CK(call, what)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return c->cuda_fail(e_, what); \
+  } while (0)
+
+namespace {
+
+template <class P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <class P>
+cudaError_t dalloc(P*& p, size_t n) {
+  dfree(p);
+  return cudaMalloc((void**)&p, n * sizeof(P));
+}
+
+void drop_graph(ift_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_epoch = -1;
+}
+
+// Fill the kernel arguments for the configured precision (or FP64 if force64).
+template <class TT>
+AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* tau, const double* mu, bool dense,
+                      const int* skip) {
+  AsmArgs<TT> a;
+  a.X = c->d_X;
+  a.ev = c->d_ev;
+  a.nbr = c->d_nbr;
+  a.nbr_face = c->d_nbrf;
+  a.bc = c->d_bc;
+  a.Phi = Phi;
+  a.Psi = c->d_Psi;
+  a.ku = c->ku;
+  a.kx = c->kx;
+  if (dense || c->nnz < 0) {
+    a.elems = nullptr;
+    a.rho = nullptr;
+    a.n_items = c->n_elems;
+  } else {
+    a.elems = c->d_elems;
+    a.rho = c->d_rho;
+    a.n_items = c->nnz;
+  }
+  a.w = w;
+  a.tau = tau;
+  a.mu = mu;
+  a.tables = c->d_tables;
+  a.gamma = c->cfg.gamma;
+  a.kappa = c->cfg.kappa;
+  a.eps = c->cfg.eps_g;
+  a.partial = c->d_partial;
+  a.skip = skip;
+  return a;
+}
+
+// Grid and shared memory of the element kernels for the current bases and
+// weights: as many CTAs as fit on the GPU at once, but no more than the items
+// need; the shape is fixed per configuration, so sums are reproducible.
+ift_status plan_launch(ift_ctx* c) {
+  const KernelSet& ks = c->ksP;
+  const int block = 32 * kWarpsPerCta;
+  const long items = (c->nnz < 0) ? c->n_elems : c->nnz;
+  for (int j = 0; j < 2; ++j) {
+    const bool jac = j == 1;
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, kWarpsPerCta);
+    cudaError_t e = ks.prepare(jac, smem);
+    if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
+    const int bps = ks.blocks_per_sm(jac, block, smem);
+    if (bps < 1) return c->fail(IFT_ERR_CUDA, "element kernel does not fit on an SM (%zu bytes shared)", smem);
+    long grid = (long)c->sm_count * bps;
+    const long need = (items + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (grid > need) grid = need;
+    if (grid > c->max_parts) grid = c->max_parts;
+    if (grid < 1) grid = 1;
+    c->plan_grid[j] = (int)grid;
+    c->plan_smem[j] = smem;
+  }
+  // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
+  const size_t ismem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
+  if (ismem > c->plan_smem[1]) {
+    cudaError_t e = ks.prepare(true, ismem);
+    if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
+  }
+  c->plan_epoch = c->epoch;
+  return IFT_OK;
+}
+
+// Launch the element pass (jac: fused assembly, else objective only) and the
+// partial reduction into out. Uses the configured precision.
+ift_status launch_assemble(ift_ctx* c, bool jac, const double* w, const double* tau, const double* mu, double* out,
+                           const int* skip, cudaStream_t s) {
+  if (c->plan_epoch != c->epoch) {
+    ift_status st = plan_launch(c);
+    if (st != IFT_OK) return st;
+  }
+  const KernelSet& ks = c->ksP;
+  const int block = 32 * kWarpsPerCta;
+  const int grid = c->plan_grid[jac ? 1 : 0];
+  const size_t smem = c->plan_smem[jac ? 1 : 0];
+  cudaError_t e;
+  if (c->cfg.precision == IFT_FP32) {
+    AsmArgs<float> a = make_args<float>(c, c->d_Phi32, w, tau, mu, false, skip);
+    e = ks.assemble(&a, jac, grid, block, smem, s);
+  } else {
+    AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
+    e = ks.assemble(&a, jac, grid, block, smem, s);
+  }
+  if (e != cudaSuccess) return c->cuda_fail(e, "element kernel launch");
+  const int nacc = c->nacc();
+  reduce_partials_kernel<<<(nacc + 127) / 128, 128, 0, s>>>(c->d_partial, grid, nacc, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return c->cuda_fail(e, "reduce launch");
+  return IFT_OK;
+}
+
+ift_status check_ready(ift_ctx* c) {
+  if (!c) return IFT_ERR_ARG;
+  if (!c->have_mesh || !c->have_bases) return c->fail(IFT_ERR_STATE, "set_mesh and set_bases must come first");
+  return IFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ift_config_default(ift_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->problem = IFT_EULER2D;
+  cfg->p = 2;
+  cfg->precision = IFT_FP64;
+  cfg->gamma = 1.4;
+  cfg->kappa = 0.0;
+  cfg->eps_g = 1e-8;
+  cfg->tol = 1e-8;
+  cfg->max_iters = 200;
+  cfg->lm_init = IFT_INIT_PAPER;
+}
+
+const char* ift_create_error(void) { return g_create_error.c_str(); }
+
+ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
+  g_create_error.clear();
+  if (!cfg || !out) {
+    g_create_error = "null argument";
+    return IFT_ERR_ARG;
+  }
+  *out = nullptr;
+  if (cfg->problem != IFT_BURGERS1D && cfg->problem != IFT_EULER2D) {
+    g_create_error = "unknown problem";
+    return IFT_ERR_ARG;
+  }
+  if (cfg->p < 1 || cfg->p > 3) {
+    g_create_error = "degree p must be 1, 2 or 3";
+    return IFT_ERR_ARG;
+  }
+  if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32) {
+    g_create_error = "precision must be IFT_FP64 or IFT_FP32";
+    return IFT_ERR_ARG;
+  }
+  if (!(cfg->gamma > 1.0) || !(cfg->kappa >= 0.0) || !(cfg->eps_g > 0.0) || !(cfg->tol >= 0.0) ||
+      cfg->max_iters < 0 || (cfg->lm_init != IFT_INIT_PAPER && cfg->lm_init != IFT_INIT_GIVEN)) {
+    g_create_error = "bad configuration value";
+    return IFT_ERR_ARG;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return IFT_ERR_CUDA;
+  }
+  ift_ctx* c = new ift_ctx();
+  c->cfg = *cfg;
+  const int dim = (cfg->problem == IFT_BURGERS1D) ? 1 : 2;
+  if (!build_tables(dim, cfg->p, c->T)) {
+    delete c;
+    g_create_error = "reference element construction failed";
+    return IFT_ERR_ARG;
+  }
+  c->dim = dim;
+  c->m = (dim == 1) ? 1 : 4;
+  c->nv = dim + 1;
+  c->nb = c->T.nb;
+  c->nu = c->nb * c->m;
+  c->nface = c->T.nface;
+  c->ntrace = c->T.ntrace;
+  c->nup = c->nface * c->ntrace * c->m;
+  c->nxe = c->nv * dim;
+  c->nq = c->T.nq;
+  c->nfq = c->T.nfq;
+  c->ks64 = (dim == 1) ? burgers_kernels(cfg->p, 0) : euler_kernels(cfg->p, 0);
+  c->ksP = (dim == 1) ? burgers_kernels(cfg->p, cfg->precision) : euler_kernels(cfg->p, cfg->precision);
+  if (!c->ks64.valid || !c->ksP.valid) {
+    delete c;
+    g_create_error = "kernels for this problem/degree/precision are not built";
+    return IFT_ERR_NOTIMPL;
+  }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      g_create_error = std::string("stream: ") + cudaGetErrorString(e);
+      return IFT_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  // reference tables, packed D | B | Lt | fw | qw | qxi (see elem.cuh Tabs)
+  std::vector<double> tab;
+  tab.insert(tab.end(), c->T.D.begin(), c->T.D.end());
+  tab.insert(tab.end(), c->T.B.begin(), c->T.B.end());
+  tab.insert(tab.end(), c->T.Lt.begin(), c->T.Lt.end());
+  tab.insert(tab.end(), c->T.fw.begin(), c->T.fw.end());
+  tab.insert(tab.end(), c->T.qw.begin(), c->T.qw.end());
+  if (dim == 1) {
+    tab.insert(tab.end(), c->T.qxi.begin(), c->T.qxi.end());
+  } else {
+    tab.insert(tab.end(), (size_t)c->nq, 0.0);  // 2-D kernels do not read the 1-D point table
+  }
+  c->max_parts = c->sm_count * 32;
+  bool ok = dalloc(c->d_tables, tab.size()) == cudaSuccess &&
+            cudaMemcpy(c->d_tables, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            dalloc(c->d_mu, 4) == cudaSuccess && dalloc(c->d_w, LM_KMAX) == cudaSuccess &&
+            dalloc(c->d_tau, LM_KMAX) == cudaSuccess && dalloc(c->d_phit, (size_t)kPhitBlocks * LM_KMAX) == cudaSuccess &&
+            dalloc(c->d_lm, 1) == cudaSuccess;
+  if (ok) {
+    cudaMemset(c->d_w, 0, LM_KMAX * 8);
+    cudaMemset(c->d_tau, 0, LM_KMAX * 8);
+    cudaMemset(c->d_mu, 0, 4 * 8);
+    cudaMemset(c->d_lm, 0, sizeof(LMState));
+  }
+  if (!ok) {
+    g_create_error = "device allocation failed";
+    ift_destroy(c);
+    return IFT_ERR_OOM;
+  }
+  *out = c;
+  return IFT_OK;
+}
+
+ift_status ift_destroy(ift_ctx* c) {
+  if (!c) return IFT_ERR_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  dfree(c->d_tables);
+  dfree(c->d_X);
+  dfree(c->d_ev);
+  dfree(c->d_nbr);
+  dfree(c->d_nbrf);
+  dfree(c->d_bc);
+  dfree(c->d_Phi);
+  dfree(c->d_Phi32);
+  dfree(c->d_Psi);
+  dfree(c->d_elems);
+  dfree(c->d_rho);
+  dfree(c->d_mu);
+  dfree(c->d_w);
+  dfree(c->d_tau);
+  dfree(c->d_res);
+  dfree(c->d_partial);
+  dfree(c->d_phit);
+  dfree(c->d_lm);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return IFT_OK;
+}
+
+const char* ift_last_error(const ift_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ift_status ift_sizes(const ift_ctx* c, int64_t* s) {
+  if (!c || !s) return IFT_ERR_ARG;
+  s[0] = c->nb;
+  s[1] = c->nu;
+  s[2] = c->nup;
+  s[3] = c->nxe;
+  s[4] = c->nface;
+  s[5] = c->ntrace;
+  s[6] = c->nq;
+  s[7] = c->nfq;
+  return IFT_OK;
+}
+
+ift_status ift_reference_nodes(const ift_ctx* c, double* nodes, int32_t* face_nodes) {
+  if (!c) return IFT_ERR_ARG;
+  if (nodes) std::memcpy(nodes, c->T.nodes.data(), c->T.nodes.size() * sizeof(double));
+  if (face_nodes)
+    for (size_t i = 0; i < c->T.face_nodes.size(); ++i) face_nodes[i] = c->T.face_nodes[i];
+  return IFT_OK;
+}
+
+ift_status ift_set_mesh(ift_ctx* c, int64_t n_verts, const double* X, int64_t n_elems, const int32_t* ev) {
+  if (!c) return IFT_ERR_ARG;
+  if (n_verts < c->nv || n_elems < 1 || !X || !ev) return c->fail(IFT_ERR_ARG, "empty mesh or null pointer");
+  if (n_elems > (int64_t)1 << 30 || n_verts > (int64_t)1 << 30) return c->fail(IFT_ERR_ARG, "mesh too large");
+  const int dim = c->dim, nv = c->nv, nf = c->nface;
+  for (int64_t i = 0; i < n_elems * nv; ++i)
+    if (ev[i] < 0 || ev[i] >= n_verts) return c->fail(IFT_ERR_ARG, "vertex index out of range in element %lld",
+                                                      (long long)(i / nv));
+  for (int64_t e = 0; e < n_elems; ++e) {
+    const int32_t* v = &ev[e * nv];
+    double det;
+    if (dim == 1) {
+      det = X[v[1]] - X[v[0]];
+    } else {
+      det = (X[2 * v[1]] - X[2 * v[0]]) * (X[2 * v[2] + 1] - X[2 * v[0] + 1]) -
+            (X[2 * v[2]] - X[2 * v[0]]) * (X[2 * v[1] + 1] - X[2 * v[0] + 1]);
+    }
+    if (!(det > 0.0)) return c->fail(IFT_ERR_ARG, "element %lld is inverted or degenerate", (long long)e);
+  }
+  // faces matched by their vertex set
+  std::vector<int> nbr(n_elems * nf, -1), nbrf(n_elems * nf, -1);
+  std::vector<signed char> bc(n_elems * nf, 0);
+  std::unordered_map<uint64_t, int64_t> open_faces;
+  open_faces.reserve((size_t)n_elems * nf);
+  for (int64_t e = 0; e < n_elems; ++e)
+    for (int k = 0; k < nf; ++k) {
+      uint64_t key;
+      if (dim == 1) {
+        key = (uint64_t)(uint32_t)ev[e * 2 + k];
+      } else {
+        uint32_t a = (uint32_t)ev[e * 3 + k], b = (uint32_t)ev[e * 3 + (k + 1) % 3];
+        key = ((uint64_t)(a < b ? a : b) << 32) | (uint64_t)(a < b ? b : a);
+      }
+      auto it = open_faces.find(key);
+      if (it == open_faces.end()) {
+        open_faces.emplace(key, e * nf + k);
+      } else {
+        const int64_t other = it->second;
+        if (other < 0) return c->fail(IFT_ERR_ARG, "a face is shared by more than two elements");
+        const int64_t e2 = other / nf;
+        const int k2 = (int)(other % nf);
+        if (dim == 1 && k2 == k) return c->fail(IFT_ERR_ARG, "1-D elements must run left to right");
+        nbr[e * nf + k] = (int)e2;
+        nbrf[e * nf + k] = k2;
+        nbr[e2 * nf + k2] = (int)e;
+        nbrf[e2 * nf + k2] = k;
+        it->second = -1;
+      }
+    }
+  for (int64_t i = 0; i < n_elems * nf; ++i)
+    if (nbr[i] < 0) bc[i] = (dim == 1) ? ((i % nf == 0) ? 1 : 2) : 1;
+  drop_graph(c);
+  c->have_mesh = false;
+  c->have_bases = false;
+  c->nnz = -1;
+  CK(dalloc(c->d_X, (size_t)n_verts * dim), "alloc X");
+  CK(dalloc(c->d_ev, (size_t)n_elems * nv), "alloc elements");
+  CK(dalloc(c->d_nbr, (size_t)n_elems * nf), "alloc neighbours");
+  CK(dalloc(c->d_nbrf, (size_t)n_elems * nf), "alloc neighbours");
+  CK(dalloc(c->d_bc, (size_t)n_elems * nf), "alloc boundary types");
+  CK(cudaMemcpy(c->d_X, X, (size_t)n_verts * dim * 8, cudaMemcpyHostToDevice), "copy X");
+  CK(cudaMemcpy(c->d_ev, ev, (size_t)n_elems * nv * 4, cudaMemcpyHostToDevice), "copy elements");
+  CK(cudaMemcpy(c->d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "copy neighbours");
+  CK(cudaMemcpy(c->d_nbrf, nbrf.data(), nbrf.size() * 4, cudaMemcpyHostToDevice), "copy neighbours");
+  CK(cudaMemcpy(c->d_bc, bc.data(), bc.size(), cudaMemcpyHostToDevice), "copy boundary types");
+  c->n_verts = n_verts;
+  c->n_elems = n_elems;
+  c->have_mesh = true;
+  c->epoch++;
+  return IFT_OK;
+}
+
+ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, int64_t N_x, int k_x,
+                         const double* Psi) {
+  if (!c) return IFT_ERR_ARG;
+  if (!c->have_mesh) return c->fail(IFT_ERR_STATE, "set_mesh must come first");
+  if (N_u != c->n_elems * c->nu) return c->fail(IFT_ERR_ARG, "N_u must be n_elems * n_u = %lld",
+                                                (long long)(c->n_elems * c->nu));
+  if (N_x != c->n_verts * c->dim) return c->fail(IFT_ERR_ARG, "N_x must be n_verts * dim = %lld",
+                                                 (long long)(c->n_verts * c->dim));
+  if (k_u < 1 || k_x < 0 || k_u + k_x > LM_KMAX) return c->fail(IFT_ERR_ARG, "need k_u >= 1, k_x >= 0, k_u + k_x <= %d",
+                                                              LM_KMAX);
+  if (!Phi || (k_x > 0 && !Psi)) return c->fail(IFT_ERR_ARG, "null basis pointer");
+  drop_graph(c);
+  c->have_bases = false;
+  CK(dalloc(c->d_Phi, (size_t)N_u * k_u), "alloc Phi");
+  CK(cudaMemcpy(c->d_Phi, Phi, (size_t)N_u * k_u * 8, cudaMemcpyHostToDevice), "copy Phi");
+  if (c->cfg.precision == IFT_FP32) {
+    std::vector<float> p32((size_t)N_u * k_u);
+    for (size_t i = 0; i < p32.size(); ++i) p32[i] = (float)Phi[i];
+    CK(dalloc(c->d_Phi32, p32.size()), "alloc Phi (FP32)");
+    CK(cudaMemcpy(c->d_Phi32, p32.data(), p32.size() * 4, cudaMemcpyHostToDevice), "copy Phi (FP32)");
+  }
+  CK(dalloc(c->d_Psi, (size_t)N_x * (k_x > 0 ? k_x : 1)), "alloc Psi");
+  if (k_x > 0) CK(cudaMemcpy(c->d_Psi, Psi, (size_t)N_x * k_x * 8, cudaMemcpyHostToDevice), "copy Psi");
+  c->ku = k_u;
+  c->kx = k_x;
+  const int nacc = c->nacc();
+  CK(dalloc(c->d_res, nacc), "alloc result");
+  CK(dalloc(c->d_partial, (size_t)c->max_parts * nacc), "alloc partials");
+  c->have_bases = true;
+  c->epoch++;
+  return IFT_OK;
+}
+
+ift_status ift_set_eq_weights(ift_ctx* c, int64_t nnz, const int32_t* elem, const double* rho) {
+  if (!c) return IFT_ERR_ARG;
+  if (!c->have_mesh) return c->fail(IFT_ERR_STATE, "set_mesh must come first");
+  drop_graph(c);
+  c->epoch++;
+  if (nnz < 0) {
+    c->nnz = -1;
+    return IFT_OK;
+  }
+  if (nnz == 0) return c->fail(IFT_ERR_ARG, "an empty weight set has no objective");
+  if (!elem || !rho) return c->fail(IFT_ERR_ARG, "null weight pointer");
+  std::vector<char> seen(c->n_elems, 0);
+  for (int64_t i = 0; i < nnz; ++i) {
+    if (elem[i] < 0 || elem[i] >= c->n_elems) return c->fail(IFT_ERR_ARG, "weight element out of range");
+    if (seen[elem[i]]) return c->fail(IFT_ERR_ARG, "element %d listed twice", elem[i]);
+    seen[elem[i]] = 1;
+    if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return c->fail(IFT_ERR_ARG, "weights must be positive and finite");
+  }
+  CK(dalloc(c->d_elems, (size_t)nnz), "alloc weights");
+  CK(dalloc(c->d_rho, (size_t)nnz), "alloc weights");
+  CK(cudaMemcpy(c->d_elems, elem, (size_t)nnz * 4, cudaMemcpyHostToDevice), "copy weights");
+  CK(cudaMemcpy(c->d_rho, rho, (size_t)nnz * 8, cudaMemcpyHostToDevice), "copy weights");
+  c->nnz = nnz;
+  return IFT_OK;
+}
+
+ift_status ift_reduced_residual_jacobian_dev(ift_ctx* c, const double* mu, const double* y, const double* z,
+                                             double* S, double* T, double* H, double* J, void* stream) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  st = launch_assemble(c, true, y, c->kx > 0 ? z : c->d_tau, mu, c->d_res, nullptr, s);
+  if (st != IFT_OK) return st;
+  const int nacc = c->nacc();
+  unpack_kernel<<<(nacc + 255) / 256, 256, 0, s>>>(c->d_res, c->ku, c->kx, S, T, H, J);
+  CK(cudaGetLastError(), "unpack launch");
+  return IFT_OK;
+}
+
+ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const double* y, const double* z, double* S,
+                                         double* T, double* H, double* J) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s), "copy mu");
+  CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice, s), "copy y");
+  if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice, s), "copy z");
+  st = launch_assemble(c, true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
+  if (st != IFT_OK) return st;
+  const int nacc = c->nacc(), k = c->ku + c->kx;
+  std::vector<double> res(nacc);
+  CK(cudaMemcpyAsync(res.data(), c->d_res, nacc * 8, cudaMemcpyDeviceToHost, s), "copy result");
+  CK(cudaStreamSynchronize(s), "assembly");
+  if (H) std::memcpy(H, res.data(), (size_t)k * k * 8);
+  if (S) std::memcpy(S, res.data() + k * k, c->ku * 8);
+  if (T && c->kx > 0) std::memcpy(T, res.data() + k * k + c->ku, c->kx * 8);
+  const bool bad = res[k * k + k + 1] > 0.0;
+  if (J) J[0] = bad ? INFINITY : res[k * k + k];
+  if (bad) return c->fail(IFT_ERR_NONPHYSICAL, "%d elements are non-physical at this point", (int)res[k * k + k + 1]);
+  return IFT_OK;
+}
+
+ift_status ift_element_eval(ift_ctx* c, const double* mu, const double* U, const double* x, int64_t n,
+                            const int32_t* elems, double* R, double* JU, double* JUp, double* Jx, double* N,
+                            double* dN) {
+  if (!c) return IFT_ERR_ARG;
+  if (!c->have_mesh) return c->fail(IFT_ERR_STATE, "set_mesh must come first");
+  if (!mu || !U || !x || !elems || n < 1) return c->fail(IFT_ERR_ARG, "bad inspection arguments");
+  for (int64_t i = 0; i < n; ++i)
+    if (elems[i] < 0 || elems[i] >= c->n_elems) return c->fail(IFT_ERR_ARG, "element out of range");
+  const int nu = c->nu, nup = c->nup, nxe = c->nxe, nd = nu + nup + nxe;
+  const size_t Nu = (size_t)c->n_elems * nu, Nx = (size_t)c->n_verts * c->dim;
+  double *dU = nullptr, *dx = nullptr, *dR = nullptr, *dJ = nullptr, *dNn = nullptr, *ddN = nullptr;
+  int* dl = nullptr;
+  auto cleanup = [&]() {
+    dfree(dU);
+    dfree(dx);
+    dfree(dR);
+    dfree(dJ);
+    dfree(dNn);
+    dfree(ddN);
+    dfree(dl);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(dU, Nu)) != cudaSuccess || (e = dalloc(dx, Nx)) != cudaSuccess ||
+      (e = dalloc(dR, (size_t)n * nu)) != cudaSuccess || (e = dalloc(dJ, (size_t)n * nu * nd)) != cudaSuccess ||
+      (e = dalloc(dNn, (size_t)n)) != cudaSuccess || (e = dalloc(ddN, (size_t)n * nxe)) != cudaSuccess ||
+      (e = dalloc(dl, (size_t)n)) != cudaSuccess) {
+    cleanup();
+    return c->cuda_fail(e, "inspection buffers");
+  }
+  cudaStream_t s = c->stream;
+  cudaMemcpyAsync(dU, U, Nu * 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dx, x, Nx * 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dl, elems, (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s);
+  const KernelSet& ks = c->ksP;
+  const int block = 32 * kWarpsPerCta;
+  const size_t smem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
+  e = ks.prepare(true, c->have_bases && c->plan_smem[1] > smem ? c->plan_smem[1] : smem);
+  if (e == cudaSuccess) {
+    const int grid = (int)((n + kWarpsPerCta - 1) / kWarpsPerCta);
+    if (c->cfg.precision == IFT_FP32) {
+      AsmArgs<float> a = make_args<float>(c, c->d_Phi32, c->d_w, c->d_tau, c->d_mu, true, nullptr);
+      a.ku = 1;
+      a.kx = 0;
+      a.elems = dl;
+      a.n_items = n;
+      e = ks.inspect(&a, dU, dx, dR, dJ, dNn, ddN, grid, block, smem, s);
+    } else {
+      AsmArgs<double> a = make_args<double>(c, c->d_Phi, c->d_w, c->d_tau, c->d_mu, true, nullptr);
+      a.ku = 1;
+      a.kx = 0;
+      a.elems = dl;
+      a.n_items = n;
+      e = ks.inspect(&a, dU, dx, dR, dJ, dNn, ddN, grid, block, smem, s);
+    }
+  }
+  std::vector<double> hR((size_t)n * nu), hJ((size_t)n * nu * nd), hN(n), hdN((size_t)n * nxe);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hR.data(), dR, hR.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hJ.data(), dJ, hJ.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hN.data(), dNn, hN.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hdN.data(), ddN, hdN.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return c->cuda_fail(e, "element inspection");
+  for (int64_t i = 0; i < n; ++i) {
+    for (int r = 0; r < nu; ++r) {
+      const double* row = &hJ[((size_t)i * nu + r) * nd];
+      if (JU) std::memcpy(&JU[((size_t)i * nu + r) * nu], row, nu * 8);
+      if (JUp) std::memcpy(&JUp[((size_t)i * nu + r) * nup], row + nu, nup * 8);
+      if (Jx) std::memcpy(&Jx[((size_t)i * nu + r) * nxe], row + nu + nup, nxe * 8);
+    }
+  }
+  if (R) std::memcpy(R, hR.data(), hR.size() * 8);
+  if (N) std::memcpy(N, hN.data(), hN.size() * 8);
+  if (dN) std::memcpy(dN, hdN.data(), hdN.size() * 8);
+  return IFT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Starting point of a solve: paper initialisation (w0 = Phi^T U_guess(mu), tau = 0,
+// w-only phase first) or the caller's (y, z) (joint phase only).
+ift_status solve_prologue(ift_ctx* c, const double* d_mu, const double* d_y0, const double* d_z0, cudaStream_t s) {
+  const int ku = c->ku, kx = c->kx;
+  if (c->cfg.lm_init == IFT_INIT_PAPER) {
+    const long Nu = (long)c->n_elems * c->nu;
+    const long chunk = (Nu + kPhitBlocks - 1) / kPhitBlocks;
+    int block = 256;
+    if (block < ku) block = ku;
+    phit_u_partial_kernel<<<kPhitBlocks, block, block * sizeof(double), s>>>(
+        c->d_Phi, Nu, ku, c->m, c->cfg.problem, c->cfg.gamma, d_mu, chunk, c->d_phit);
+    sum_columns_kernel<<<1, 64, 0, s>>>(c->d_phit, kPhitBlocks, ku, c->d_w);
+    CK(cudaMemsetAsync(c->d_tau, 0, LM_KMAX * 8, s), "zero tau");
+    lm_init_kernel<<<1, 64, 0, s>>>(c->d_lm, c->d_w, c->d_tau, ku, kx, 0);
+  } else {
+    lm_init_kernel<<<1, 64, 0, s>>>(c->d_lm, d_y0, kx > 0 ? d_z0 : nullptr, ku, kx, 1);
+  }
+  CK(cudaGetLastError(), "solve prologue");
+  return IFT_OK;
+}
+
+LMConsts lm_consts(ift_ctx* c) {
+  LMConsts k;
+  k.tol = c->cfg.tol;
+  k.max_iters = c->cfg.max_iters;
+  k.ku = c->ku;
+  k.kx = c->kx;
+  k.body_limit = (2 * c->cfg.max_iters + 4) * 34;
+  return k;
+}
+
+// The loop body: assemble at the trial point, reduce, LM step.
+ift_status enqueue_body(ift_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+  double* trial = (double*)((char*)c->d_lm + offsetof(LMState, trial));
+  const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
+  ift_status st = launch_assemble(c, true, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
+  if (st != IFT_OK) return st;
+  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, lm_consts(c), handle, use_cond);
+  CK(cudaGetLastError(), "LM step launch");
+  return IFT_OK;
+}
+
+// Build (once per configuration) the solve graph: one while node whose body is
+// the loop body above, with the LM step kernel setting the loop condition.
+ift_status build_graph(ift_ctx* c) {
+  drop_graph(c);
+  if (c->plan_epoch != c->epoch) {
+    ift_status st = plan_launch(c);
+    if (st != IFT_OK) return st;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0), "graph create");
+  c->graph = g;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+  // the parameter struct holds a union without a default constructor: build it in zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(pbuf, 0, sizeof(pbuf));
+  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = h;
+  p->conditional.type = cudaGraphCondTypeWhile;
+  p->conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, p), "while node");
+  cudaGraph_t body = p->conditional.phGraph_out[0];
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return c->cuda_fail(e, "begin capture");
+  }
+  ift_status st = enqueue_body(c, cs, (unsigned long long)h, 1);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (st != IFT_OK) return st;
+  if (e != cudaSuccess) return c->cuda_fail(e, "end capture");
+  CK(cudaGraphInstantiate(&c->graph_exec, g, 0), "graph instantiate");
+  c->graph_epoch = c->epoch;
+  return IFT_OK;
+}
+
+ift_status run_solve(ift_ctx* c, cudaStream_t s) {
+  if (c->graph_epoch != c->epoch || !c->graph_exec) {
+    ift_status st = build_graph(c);
+    if (st != IFT_OK) return st;
+  }
+  CK(cudaGraphLaunch(c->graph_exec, s), "graph launch");
+  return IFT_OK;
+}
+
+void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
+  if (!info) return;
+  info->status = st.status;
+  info->init_iters = st.iters[0];
+  info->iters = st.iters[1];
+  info->trials = st.trials;
+  info->shifts = st.shifts;
+  info->J = st.J;
+  double ns = 0.0, nt = 0.0;
+  for (int i = 0; i < ku; ++i) ns += st.g[i] * st.g[i];
+  for (int i = 0; i < kx; ++i) nt += st.g[ku + i] * st.g[ku + i];
+  info->normS = std::sqrt(ns);
+  info->normT = std::sqrt(nt);
+  info->g0 = st.g0;
+}
+
+}  // namespace
+
+extern "C" {
+
+ift_status ift_solve_rom(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s), "copy mu");
+  if (c->cfg.lm_init == IFT_INIT_GIVEN) {
+    CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice, s), "copy y");
+    if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice, s), "copy z");
+  }
+  st = solve_prologue(c, c->d_mu, c->d_w, c->d_tau, s);
+  if (st != IFT_OK) return st;
+  st = run_solve(c, s);
+  if (st != IFT_OK) return st;
+  LMState hs;
+  CK(cudaMemcpyAsync(&hs, c->d_lm, sizeof(LMState), cudaMemcpyDeviceToHost, s), "copy state");
+  CK(cudaStreamSynchronize(s), "solve");
+  for (int i = 0; i < c->ku; ++i) y[i] = hs.z[i];
+  for (int i = 0; i < c->kx; ++i) z[i] = hs.z[c->ku + i];
+  fill_info(hs, info, c->ku, c->kx);
+  return (ift_status)hs.status;
+}
+
+ift_status ift_solve_rom_dev(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info_host,
+                             void* stream) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  CK(cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyDeviceToDevice, s), "copy mu");
+  if (c->cfg.lm_init == IFT_INIT_GIVEN) {
+    CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyDeviceToDevice, s), "copy y");
+    if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyDeviceToDevice, s), "copy z");
+  }
+  st = solve_prologue(c, c->d_mu, c->d_w, c->d_tau, s);
+  if (st != IFT_OK) return st;
+  st = run_solve(c, s);
+  if (st != IFT_OK) return st;
+  const double* zsrc = (const double*)((char*)c->d_lm + offsetof(LMState, z));
+  CK(cudaMemcpyAsync(y, zsrc, c->ku * 8, cudaMemcpyDeviceToDevice, s), "copy y");
+  if (c->kx > 0) CK(cudaMemcpyAsync(z, zsrc + c->ku, c->kx * 8, cudaMemcpyDeviceToDevice, s), "copy z");
+  if (info_host) {
+    LMState hs;
+    CK(cudaMemcpyAsync(&hs, c->d_lm, sizeof(LMState), cudaMemcpyDeviceToHost, s), "copy state");
+    CK(cudaStreamSynchronize(s), "solve");
+    fill_info(hs, info_host, c->ku, c->kx);
+    return (ift_status)hs.status;
+  }
+  return IFT_OK;
+}
+
+}  // extern "C"

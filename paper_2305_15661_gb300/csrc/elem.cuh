@@ -1,0 +1,761 @@
+// Element kernels of the EQP-IFT hot path (device code).
+//
+// One warp evaluates one element at a time (a grid-stride loop over a list of
+// (element, weight) items, so the same kernel serves the full assembly with
+// rho = 1 and the hyperreduced gather over the sampled elements):
+//   1. gather Phi_e, the neighbours' trace rows Phi_e', Psi_e and X_e into the
+//      warp's shared memory (coalesced row blocks);
+//   2. U_e = Phi_e w, U_e' = Phi_e' w, x_e = X_e + Psi_e tau        (Sec. 3.1)
+//   3. straight-sided geometry: cofactor matrix g J^{-T} of the element map
+//      and scaled face normals (Eq. p2r-flux; Nanson's formula);
+//   4. lanes split the quadrature points: contravariant volume fluxes and flux
+//      Jacobians, Roe fluxes and their derivatives (dual numbers) at face points;
+//   5. lanes split the residual entries: R_e (Eq. hdm_elem, DG weak form);
+//   6. lane c forms column c of A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' |
+//      dR_e/dx_e Psi_e] as a Jacobian-vector product (Eq. levmarq-elem);
+//   7. lanes split the rows of the weighted contraction
+//      H += rho A^T A, g += rho A^T R, J += rho |R|^2/2 (+ distortion terms)
+//      into the warp's accumulators (Eqs. ift-eqp-res0, levmarq-elem, ift-opt-eqp2).
+// At the end each CTA sums its warps' accumulators in warp order and writes one
+// FP64 partial; a second kernel sums the partials in CTA order. The result is
+// deterministic for a fixed launch shape.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "physics.cuh"
+
+namespace ift {
+
+// Element-list items, state and problem data shared by the element kernels.
+template <class T>
+struct AsmArgs {
+  // mesh
+  const double* X;          // n_verts x DIM
+  const int* ev;            // n_elems x NV
+  const int* nbr;           // n_elems x NFACE: neighbour element or -1
+  const int* nbr_face;      // n_elems x NFACE: neighbour's local face
+  const signed char* bc;    // n_elems x NFACE: 0 interior, 1 far field / inflow, 2 outflow
+  // bases
+  const T* Phi;             // N_u x ku
+  const double* Psi;        // N_x x kx
+  int ku, kx;
+  // items: element ids and weights (elems == nullptr: item i is element i, weight 1)
+  const int* elems;
+  const double* rho;
+  long n_items;
+  // evaluation point (FP64) and parameters
+  const double* w;
+  const double* tau;
+  const double* mu;
+  // reference tables (FP64, packed: D | B | Lt | fw | qw | qxi)
+  const double* tables;
+  double gamma, kappa, eps;
+  // output: per-CTA partial sums [H (k*k) | g (k) | J | nonphysical count]
+  double* partial;
+  // optional: a device flag; when non-zero the kernel returns at once (a finished solve)
+  const int* skip;
+};
+
+template <class T, int PROB, int P>
+struct Tabs {
+  using Dd = Disc<PROB, P>;
+  static constexpr int nD = Dd::DIM * Dd::NQ * Dd::NB, nB = Dd::NQ * Dd::NB, nL = Dd::NFQ * Dd::NTRACE,
+                       nfw = Dd::NFQ, nqw = Dd::NQ, nqx = Dd::NQ;
+  static constexpr int total = nD + nB + nL + nfw + nqw + nqx;
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Per-warp shared-memory layout.
+template <class T, int PROB, int P, bool JAC>
+struct WarpLayout {
+  using Dd = Disc<PROB, P>;
+  static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
+                       NF = Dd::NFACE, NFQ = Dd::NFQ;
+  size_t oxe, oPsie, odN, oPhie, oPhp, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oR, oA, odNt, oacc,
+      bytes;
+  __host__ __device__ WarpLayout(int ku, int kx) {
+    const int k = ku + kx;
+    size_t b = 0;
+    auto put = [&](size_t n, size_t es) {
+      size_t o = b;
+      b = align16(b + n * es);
+      return o;
+    };
+    oxe = put(NXE, 8);
+    oPsie = put((size_t)NXE * (kx > 0 ? kx : 1), 8);
+    odN = put(NXE + 2, 8);
+    oPhie = put((size_t)NU * ku, sizeof(T));
+    oPhp = put((size_t)NUP * ku, sizeof(T));
+    oUe = put(NU, sizeof(T));
+    oUp = put(NUP, sizeof(T));
+    oFh = put(NQ * DIM * M, sizeof(T));
+    ofph = put(NQ * DIM * M, sizeof(T));
+    oAh = put(JAC ? NQ * DIM * M * M : 1, sizeof(T));
+    osq = put(NQ, sizeof(T));
+    oHf = put(NF * NFQ * M, sizeof(T));
+    oHp = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
+    oHm = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
+    oHn = put(JAC ? NF * NFQ * M * 2 : 1, sizeof(T));
+    oR = put(NU, sizeof(T));
+    oA = put(JAC ? (size_t)NU * k : 1, sizeof(T));
+    odNt = put(kx + 1, sizeof(T));
+    oacc = put((size_t)k * k + k + 2, sizeof(T));
+    bytes = b;
+  }
+};
+
+template <class T, int PROB, int P>
+__host__ __device__ inline size_t cta_bytes(int ku, int kx) {
+  return align16(Tabs<T, PROB, P>::total * sizeof(T)) + align16((size_t)(ku > 0 ? ku : 1) * sizeof(T)) +
+         align16((size_t)(kx > 0 ? kx : 1) * 8);
+}
+
+template <class T, int PROB, int P, bool JAC>
+__host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps) {
+  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+}
+
+// Pointwise stage and residual for one element whose U_e, U_e', x_e are staged.
+// Leaves Fh/fph/Ah (volume), Hf/Hp/Hm/Hn (faces), R (residual), and returns the
+// non-physical flag (warp-uniform).
+template <class T, int PROB, int P, bool JAC>
+struct ElemCore {
+  using Dd = Disc<PROB, P>;
+  static constexpr int M = Dd::M, DIM = Dd::DIM, NB = Dd::NB, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP,
+                       NXE = Dd::NXE, NF = Dd::NFACE, NFQ = Dd::NFQ, NT = Dd::NTRACE;
+  // shared tables
+  const T *D, *B, *Lt, *fw, *qw, *qxi;
+  // warp buffers
+  double *xe, *Psie, *dN;
+  T *Phie, *Php, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *R, *A, *dNt, *acc;
+  // geometry (registers, identical on all lanes)
+  T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
+  T detJ;
+  T nt[3][2];    // scaled face normals (2-D)
+  double x0d, x1d;  // 1-D end points
+
+  __device__ void carve(unsigned char* base, int ku, int kx) {
+    WarpLayout<T, PROB, P, JAC> L(ku, kx);
+    xe = (double*)(base + L.oxe);
+    Psie = (double*)(base + L.oPsie);
+    dN = (double*)(base + L.odN);
+    Phie = (T*)(base + L.oPhie);
+    Php = (T*)(base + L.oPhp);
+    Ue = (T*)(base + L.oUe);
+    Up = (T*)(base + L.oUp);
+    Fh = (T*)(base + L.oFh);
+    fph = (T*)(base + L.ofph);
+    Ah = (T*)(base + L.oAh);
+    sq = (T*)(base + L.osq);
+    Hf = (T*)(base + L.oHf);
+    Hp = (T*)(base + L.oHp);
+    Hm = (T*)(base + L.oHm);
+    Hn = (T*)(base + L.oHn);
+    R = (T*)(base + L.oR);
+    A = (T*)(base + L.oA);
+    dNt = (T*)(base + L.odNt);
+    acc = (T*)(base + L.oacc);
+  }
+
+  // Geometry from xe (FP64). Returns false if the element is inverted.
+  __device__ bool geometry() {
+    if (DIM == 1) {
+      x0d = xe[0];
+      x1d = xe[1];
+      double det = x1d - x0d;
+      detJ = (T)det;
+      cof[0] = T(1);
+      return det > 0.0;
+    } else {
+      double j00 = xe[2] - xe[0], j01 = xe[4] - xe[0];
+      double j10 = xe[3] - xe[1], j11 = xe[5] - xe[1];
+      double det = j00 * j11 - j01 * j10;
+      detJ = (T)det;
+      cof[0] = (T)j11;
+      cof[1] = (T)(-j10);
+      cof[2] = (T)(-j01);
+      cof[3] = (T)j00;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int k1 = (k + 1) % 3;
+        nt[k][0] = (T)(xe[2 * k1 + 1] - xe[2 * k + 1]);
+        nt[k][1] = (T)(-(xe[2 * k1] - xe[2 * k]));
+      }
+      return det > 0.0;
+    }
+  }
+
+  // Step 4: pointwise quantities. bcs: per-face boundary type.
+  __device__ bool pointwise(int lane, const signed char* bcs, const double* mu, double gamma, bool need_hn) {
+    bool bad = false;
+    const T g1 = (T)(gamma - 1.0);
+    // volume points
+    for (int q = lane; q < NQ; q += 32) {
+      T U[4];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) s += B[q * NB + j] * Ue[j * M + a];
+        U[a] = s;
+      }
+      if (PROB == PROB_EULER) {
+        T fx[4], fy[4], Pq;
+        euler_flux(U, g1, fx, fy, Pq);
+        if (!(U[0] > T(0)) || !(Pq > T(0))) bad = true;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          fph[(q * 2 + 0) * 4 + a] = fx[a];
+          fph[(q * 2 + 1) * 4 + a] = fy[a];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) Fh[(q * 2 + r) * 4 + a] = fx[a] * cof[0 * 2 + r] + fy[a] * cof[1 * 2 + r];
+        }
+        if (JAC) {
+          T Ax[16], Ay[16];
+          euler_flux_jac(U, g1, Ax, Ay);
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int ab = 0; ab < 16; ++ab) Ah[(q * 2 + r) * 16 + ab] = Ax[ab] * cof[r] + Ay[ab] * cof[2 + r];
+        }
+      } else {
+        T f = T(0.5) * U[0] * U[0];
+        Fh[q] = f;
+        fph[q] = f;
+        if (JAC) Ah[q] = U[0];
+        // source s(x) = 0.5 exp(mu x) at the mapped point
+        double xq = x0d + (double)qxi[q] * (x1d - x0d);
+        sq[q] = (T)(0.5 * exp(mu[0] * xq));
+      }
+    }
+    // face points: task t -> (group, face point); groups 0: d/dU+, 1: d/dU-, 2: d/dn
+    const int npts = NF * NFQ;
+    const int ngroups = (PROB == PROB_EULER) ? (JAC ? (need_hn ? 3 : 2) : 1) : 1;
+    for (int t = lane; t < npts * ngroups; t += 32) {
+      const int grp = t / npts, pt = t % npts;
+      const int k = pt / NFQ, f = pt % NFQ;
+      T Ui[4], Uo[4];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        T s = T(0), so = T(0);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          // face_node depends on the runtime face k: read Ue through the small switch
+          int node = (k == 0) ? Dd::face_node(0, j) : ((k == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+          s += Lt[f * NT + j] * Ue[node * M + a];
+          so += Lt[f * NT + j] * Up[(k * NT + j) * M + a];
+        }
+        Ui[a] = s;
+        Uo[a] = so;
+      }
+      const signed char bt = bcs[k];
+      if (PROB == PROB_EULER) {
+        if (bt == 1) {
+          double Uf[4];
+          euler_farfield(gamma, mu[0], mu[1], Uf);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) Uo[a] = (T)Uf[a];
+        }
+        if (grp == 0) {
+          T Pi = g1 * (Ui[3] - T(0.5) * (Ui[1] * Ui[1] + Ui[2] * Ui[2]) / Ui[0]);
+          T Po = g1 * (Uo[3] - T(0.5) * (Uo[1] * Uo[1] + Uo[2] * Uo[2]) / Uo[0]);
+          if (!(Ui[0] > T(0)) || !(Pi > T(0)) || !(Uo[0] > T(0)) || !(Po > T(0))) bad = true;
+        }
+        T* hf = &Hf[pt * 4];
+        if (!JAC) {
+          T n2[2] = {nt[k][0], nt[k][1]};
+          T H[4];
+          euler_roe<T, T>(Ui, Uo, n2, g1, H);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) hf[a] = H[a];
+        } else if (grp < 2) {
+          Dual<T, 4> di[4], dd[4], dn[2], H[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            di[a] = dconst<T, 4>(Ui[a]);
+            dd[a] = dconst<T, 4>(Uo[a]);
+          }
+          dn[0] = dconst<T, 4>(nt[k][0]);
+          dn[1] = dconst<T, 4>(nt[k][1]);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (grp == 0) di[a].d[a] = T(1);
+            else dd[a].d[a] = T(1);
+          }
+          euler_roe<Dual<T, 4>, T>(di, dd, dn, g1, H);
+          T* dst = (grp == 0) ? &Hp[pt * 16] : &Hm[pt * 16];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (grp == 0) hf[a] = H[a].v;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) dst[a * 4 + b] = H[a].d[b];
+          }
+        } else {
+          Dual<T, 2> di[4], dd[4], dn[2], H[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            di[a] = dconst<T, 2>(Ui[a]);
+            dd[a] = dconst<T, 2>(Uo[a]);
+          }
+          dn[0] = dconst<T, 2>(nt[k][0]);
+          dn[1] = dconst<T, 2>(nt[k][1]);
+          dn[0].d[0] = T(1);
+          dn[1].d[1] = T(1);
+          euler_roe<Dual<T, 2>, T>(di, dd, dn, g1, H);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            Hn[pt * 8 + a * 2 + 0] = H[a].d[0];
+            Hn[pt * 8 + a * 2 + 1] = H[a].d[1];
+          }
+        }
+      } else {
+        // Burgers: inflow u- = 1 on the face with normal -x, outflow u- = u+
+        T n = (k == 0) ? T(-1) : T(1);
+        if (bt == 1) Uo[0] = T(1);
+        if (bt == 2) Uo[0] = Ui[0];
+        T H, Hi, Ho;
+        burgers_roe(Ui[0], Uo[0], n, H, Hi, Ho);
+        Hf[pt] = H;
+        if (JAC) {
+          Hp[pt] = Hi;
+          Hm[pt] = Ho;
+        }
+      }
+    }
+    return __any_sync(0xffffffffu, bad);
+  }
+
+  // Step 5: residual entries.
+  __device__ bool residual(int lane) {
+    bool bad = false;
+    for (int ia = lane; ia < NU; ia += 32) {
+      const int i = ia / M, a = ia % M;
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) s -= D[(r * NQ + q) * NB + i] * Fh[(q * DIM + r) * M + a];
+      if (PROB == PROB_BURGERS) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s -= qw[q] * B[q * NB + i] * sq[q] * detJ;
+      }
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          if (Dd::face_node(k, j) != i) continue;
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) s += fw[f] * Lt[f * NT + j] * Hf[(k * NFQ + f) * M + a];
+        }
+      R[ia] = s;
+      if (!isfinite((double)s)) bad = true;
+    }
+    return __any_sync(0xffffffffu, bad);
+  }
+
+  // Step 6a: derivative of R_e along a state direction (dUe: n_u values, dUp: n_u'
+  // values, read through accessors), accumulated into dR.
+  template <class FE, class FP>
+  __device__ void jvp_state(FE dUe, FP dUp, const signed char* bcs, T dR[NU]) {
+#pragma unroll
+    for (int i = 0; i < NU; ++i) dR[i] = T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T du[M];
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) s += B[q * NB + j] * dUe(j * M + b);
+        du[b] = s;
+      }
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          T dF = T(0);
+#pragma unroll
+          for (int b = 0; b < M; ++b) dF += Ah[((q * DIM + r) * M + a) * M + b] * du[b];
+#pragma unroll
+          for (int i = 0; i < NB; ++i) dR[i * M + a] -= D[(r * NQ + q) * NB + i] * dF;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const signed char bt = bcs[k];
+#pragma unroll
+      for (int f = 0; f < NFQ; ++f) {
+        T dui[M], duo[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          T s = T(0), so = T(0);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            s += Lt[f * NT + j] * dUe(Dd::face_node(k, j) * M + b);
+            so += Lt[f * NT + j] * dUp((k * NT + j) * M + b);
+          }
+          dui[b] = s;
+          duo[b] = (bt == 0) ? so : ((bt == 2) ? s : T(0));
+        }
+        const int pt = k * NFQ + f;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          T dH = T(0);
+#pragma unroll
+          for (int b = 0; b < M; ++b) dH += Hp[(pt * M + a) * M + b] * dui[b] + Hm[(pt * M + a) * M + b] * duo[b];
+#pragma unroll
+          for (int j = 0; j < NT; ++j) dR[Dd::face_node(k, j) * M + a] += fw[f] * Lt[f * NT + j] * dH;
+        }
+      }
+    }
+  }
+
+  // Step 6b: derivative of R_e along a mesh direction dx (n_x values, FP64).
+  __device__ void jvp_geom(const double* dx, const double* mu, T dR[NU]) {
+#pragma unroll
+    for (int i = 0; i < NU; ++i) dR[i] = T(0);
+    if (DIM == 2) {
+      T dj00 = (T)(dx[2] - dx[0]), dj01 = (T)(dx[4] - dx[0]);
+      T dj10 = (T)(dx[3] - dx[1]), dj11 = (T)(dx[5] - dx[1]);
+      T dcof[4] = {dj11, -dj10, -dj01, dj00};
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T dF = fph[(q * 2 + 0) * M + a] * dcof[0 * 2 + r] + fph[(q * 2 + 1) * M + a] * dcof[1 * 2 + r];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) dR[i * M + a] -= D[(r * NQ + q) * NB + i] * dF;
+          }
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        const int k1 = (k + 1) % 3;
+        T dnx = (T)(dx[2 * k1 + 1] - dx[2 * k + 1]);
+        T dny = (T)(-(dx[2 * k1] - dx[2 * k]));
+#pragma unroll
+        for (int f = 0; f < NFQ; ++f) {
+          const int pt = k * NFQ + f;
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T dH = Hn[(pt * M + a) * 2 + 0] * dnx + Hn[(pt * M + a) * 2 + 1] * dny;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) dR[Dd::face_node(k, j) * M + a] += fw[f] * Lt[f * NT + j] * dH;
+          }
+        }
+      }
+    } else {
+      // Burgers: only the source term -int v s(x) dX depends on the mesh
+      T dx0 = (T)dx[0], ddet = (T)(dx[1] - dx[0]);
+      T mu0 = (T)mu[0];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        T dxq = dx0 + qxi[q] * ddet;
+        T ds = qw[q] * (mu0 * sq[q] * dxq * detJ + sq[q] * ddet);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) dR[i] -= B[q * NB + i] * ds;
+      }
+    }
+  }
+
+  // Distortion N_e (Eq. dist_elem0-1) for straight-sided simplices and dN/dx_e,
+  // written by lane 0 into dN[0..NXE-1], dN[NXE] = N_e. Xe: reference vertices.
+  __device__ void distortion(const double* Xe, double kappa, double eps) {
+    if (DIM == 1) {
+      // eta = |Omega_0e| (G^2 / max(g, eps)^2)^2 with G = g = (x1 - x0)/(X1 - X0)
+      double h0 = Xe[1] - Xe[0];
+      double G = (xe[1] - xe[0]) / h0;
+      double den = G >= eps ? G : eps;
+      double r = G * G / (den * den);
+      double eta = h0 * r * r;
+      double dr_dG = (G >= eps) ? 0.0 : 2.0 * G / (den * den);
+      double deta = h0 * 2.0 * r * dr_dG / h0;  // d/dx1 (and minus for x0)
+      dN[0] = -kappa * deta;
+      dN[1] = kappa * deta;
+      dN[NXE] = kappa * (eta - h0);
+      return;
+    }
+    // G = Jx JX^{-1}; eta = |Omega_0e| (|G|_F^2 / max(g, eps))^2
+    double a00 = Xe[2] - Xe[0], a01 = Xe[4] - Xe[0], a10 = Xe[3] - Xe[1], a11 = Xe[5] - Xe[1];
+    double dA = a00 * a11 - a01 * a10;
+    double i00 = a11 / dA, i01 = -a01 / dA, i10 = -a10 / dA, i11 = a00 / dA;
+    double j00 = xe[2] - xe[0], j01 = xe[4] - xe[0], j10 = xe[3] - xe[1], j11 = xe[5] - xe[1];
+    double G00 = j00 * i00 + j01 * i10, G01 = j00 * i01 + j01 * i11;
+    double G10 = j10 * i00 + j11 * i10, G11 = j10 * i01 + j11 * i11;
+    double nrm = G00 * G00 + G01 * G01 + G10 * G10 + G11 * G11;
+    double g = G00 * G11 - G01 * G10;
+    double area = 0.5 * dA;
+    double den = g >= eps ? g : eps;
+    double ratio = nrm / den;
+    double eta = area * ratio * ratio;
+    double eta0 = area * 4.0;  // G = I: |I|_F^2 / 1 = 2
+    // d eta / d G = 2 area ratio (2 G / den - [g >= eps] nrm / den^2 cof(G))
+    double c = 2.0 * area * ratio;
+    double gb = (g >= eps) ? nrm / (den * den) : 0.0;
+    double dG00 = c * (2.0 * G00 / den - gb * G11), dG01 = c * (2.0 * G01 / den + gb * G10);
+    double dG10 = c * (2.0 * G10 / den + gb * G01), dG11 = c * (2.0 * G11 / den - gb * G00);
+    // dG = dJx JX^{-1}: d eta / d Jx = (d eta / d G) JX^{-T}
+    double dJ00 = dG00 * i00 + dG01 * i01, dJ01 = dG00 * i10 + dG01 * i11;
+    double dJ10 = dG10 * i00 + dG11 * i01, dJ11 = dG10 * i10 + dG11 * i11;
+    // Jx columns: vertex 1 - vertex 0, vertex 2 - vertex 0
+    dN[0] = -kappa * (dJ00 + dJ01);
+    dN[1] = -kappa * (dJ10 + dJ11);
+    dN[2] = kappa * dJ00;
+    dN[3] = kappa * dJ10;
+    dN[4] = kappa * dJ01;
+    dN[5] = kappa * dJ11;
+    dN[NXE] = kappa * (eta - eta0);
+  }
+};
+
+// Stage the shared reference tables (converted to T) and the evaluation point.
+template <class T, int PROB, int P>
+__device__ inline void stage_cta(const AsmArgs<T>& a, unsigned char* smem, const double* w, const double* tau,
+                                 T*& tab, T*& wT, double*& tauD) {
+  using TB = Tabs<T, PROB, P>;
+  tab = (T*)smem;
+  wT = (T*)(smem + align16(TB::total * sizeof(T)));
+  tauD = (double*)(smem + align16(TB::total * sizeof(T)) + align16((size_t)(a.ku > 0 ? a.ku : 1) * sizeof(T)));
+  for (int i = threadIdx.x; i < TB::total; i += blockDim.x) tab[i] = (T)a.tables[i];
+  for (int i = threadIdx.x; i < a.ku; i += blockDim.x) wT[i] = (T)w[i];
+  for (int i = threadIdx.x; i < a.kx; i += blockDim.x) tauD[i] = tau[i];
+}
+
+template <class T, int PROB, int P, bool JAC>
+__device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
+  using TB = Tabs<T, PROB, P>;
+  C.D = tab;
+  C.B = C.D + TB::nD;
+  C.Lt = C.B + TB::nB;
+  C.fw = C.Lt + TB::nL;
+  C.qw = C.fw + TB::nfw;
+  C.qxi = C.qw + TB::nqw;
+}
+
+// The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false).
+template <class T, int PROB, int P, bool JAC>
+__global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, JAC>;
+  constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
+                NT = Dd::NTRACE, NV = Dd::NV;
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (a.skip != nullptr && *(volatile const int*)a.skip) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  T *tab, *wT;
+  double* tauD;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
+  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, ku, kx);
+  bind_tables(C, tab);
+  const int nacc = k * k + k + 2;
+  for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+  __syncthreads();
+  const bool need_hn = JAC && kx > 0;
+  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
+    const int e = a.elems ? a.elems[it] : (int)it;
+    const double rho = a.rho ? a.rho[it] : 1.0;
+    const int* vv = &a.ev[(long)e * NV];
+    // 1. gather
+    const T* phe = a.Phi + (size_t)e * NU * ku;
+    for (int i = lane; i < NU * ku; i += 32) C.Phie[i] = phe[i];
+    for (int kf = 0; kf < NF; ++kf) {
+      const int e2 = a.nbr[(long)e * NF + kf];
+      const int k2 = a.nbr_face[(long)e * NF + kf];
+      const int rowlen = M * ku;
+      for (int i = lane; i < NT * rowlen; i += 32) {
+        const int j = i / rowlen, rem = i - j * rowlen;
+        T v = T(0);
+        if (e2 >= 0) {
+          // neighbour trace node at position j along this face = its node NT-1-j on face k2
+          const int jj = NT - 1 - j;
+          const int node = (k2 == 0) ? Dd::face_node(0, jj) : ((k2 == 1) ? Dd::face_node(1, jj) : Dd::face_node(2, jj));
+          v = a.Phi[((size_t)e2 * NU + node * M) * ku + rem];
+        }
+        C.Php[(kf * NT + j) * rowlen + rem] = v;
+      }
+    }
+    for (int i = lane; i < NXE * kx; i += 32) {
+      const int r = i / kx, c = i - r * kx;
+      const int v = r / DIM, d = r - v * DIM;
+      C.Psie[i] = a.Psi[((size_t)vv[v] * DIM + d) * kx + c];
+    }
+    __syncwarp();
+    // 2. reconstruction
+    for (int i = lane; i < NU + NUP; i += 32) {
+      const T* row = (i < NU) ? &C.Phie[i * ku] : &C.Php[(i - NU) * ku];
+      T s = T(0);
+      for (int c = 0; c < ku; ++c) s += row[c] * wT[c];
+      if (i < NU) C.Ue[i] = s;
+      else C.Up[i - NU] = s;
+    }
+    if (lane < NXE) {
+      const int v = lane / DIM, d = lane - v * DIM;
+      double s = a.X[(size_t)vv[v] * DIM + d];
+      for (int c = 0; c < kx; ++c) s += C.Psie[lane * kx + c] * tauD[c];
+      C.xe[lane] = s;
+    }
+    __syncwarp();
+    // 3. geometry
+    bool bad = !C.geometry();
+    signed char bcs[NF];
+#pragma unroll
+    for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
+    // 4. pointwise, 5. residual
+    bad |= C.pointwise(lane, bcs, a.mu, a.gamma, need_hn);
+    __syncwarp();
+    bad |= C.residual(lane);
+    // distortion
+    const bool dist = a.kappa != 0.0;
+    if (dist && lane == 0) {
+      double Xe[6];
+      for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+      C.distortion(Xe, a.kappa, a.eps);
+    }
+    __syncwarp();
+    const T Ne = dist ? (T)C.dN[NXE] : T(0);
+    if (JAC) {
+      // 6. columns of A_e
+      for (int c = lane; c < k; c += 32) {
+        T dR[NU];
+        if (c < ku) {
+          auto fe = [&](int i) { return C.Phie[i * ku + c]; };
+          auto fp = [&](int i) { return C.Php[i * ku + c]; };
+          C.jvp_state(fe, fp, bcs, dR);
+        } else {
+          double dx[NXE];
+#pragma unroll
+          for (int r = 0; r < NXE; ++r) dx[r] = C.Psie[r * kx + (c - ku)];
+          C.jvp_geom(dx, a.mu, dR);
+          if (dist) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < NXE; ++r) s += C.dN[r] * dx[r];
+            C.dNt[c - ku] = (T)s;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NU; ++i) C.A[i * k + c] = dR[i];
+      }
+      __syncwarp();
+      // 7. weighted contraction
+      const T rT = (T)rho;
+      for (int r = lane; r < k; r += 32) {
+        T* hrow = &C.acc[r * k];
+        for (int b = 0; b < k; ++b) {
+          T s = T(0);
+#pragma unroll
+          for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.A[i * k + b];
+          if (dist && r >= ku && b >= ku) s += C.dNt[r - ku] * C.dNt[b - ku];
+          hrow[b] += rT * s;
+        }
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
+        if (dist && r >= ku) s += C.dNt[r - ku] * Ne;
+        C.acc[k * k + r] += rT * s;
+      }
+    }
+    if (lane == 0) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) s += C.R[i] * C.R[i];
+      C.acc[k * k + k] += T(0.5) * (T)rho * (s + Ne * Ne);
+      if (bad) C.acc[k * k + k + 1] += T(1);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // CTA partial: sum the warps' accumulators in warp order, in FP64
+  WarpLayout<T, PROB, P, JAC> L(ku, kx);
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[i];
+    a.partial[(size_t)blockIdx.x * nacc + i] = s;
+  }
+}
+
+// Sum of the per-CTA partials in CTA order: out[i] = sum_c partial[c][i].
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);
+
+// Per-element inspection: R_e and [dR_e/dU_e | dR_e/dU_e' | dR_e/dx_e], N_e, dN_e
+// at a full state (U, x). One warp per listed element; the Jacobian columns are
+// the same Jacobian-vector products as in the fused kernel, taken along unit vectors.
+template <class T, int PROB, int P>
+__global__ void __launch_bounds__(128) inspect_kernel(AsmArgs<T> a, const double* U, const double* x, double* Rout,
+                                                      double* Jout, double* Nout, double* dNout) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, true>;
+  constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
+                NT = Dd::NTRACE, NV = Dd::NV;
+  constexpr int ND = NU + NUP + NXE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T *tab, *wT;
+  double* tauD;
+  // ku = ND (state columns), kx = 0: only the layout of the warp buffers is used
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(a.ku, a.kx);
+  const size_t wb = WarpLayout<T, PROB, P, true>(a.ku, a.kx).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, a.ku, a.kx);
+  bind_tables(C, tab);
+  __syncthreads();
+  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
+    const int e = a.elems[it];
+    const int* vv = &a.ev[(long)e * NV];
+    for (int i = lane; i < NU; i += 32) C.Ue[i] = (T)U[(size_t)e * NU + i];
+    for (int i = lane; i < NUP; i += 32) {
+      const int kf = i / (NT * M), rem = i - kf * NT * M, j = rem / M, b = rem - j * M;
+      const int e2 = a.nbr[(long)e * NF + kf], k2 = a.nbr_face[(long)e * NF + kf];
+      T v = T(0);
+      if (e2 >= 0) {
+        const int jj = NT - 1 - j;
+        const int node = (k2 == 0) ? Dd::face_node(0, jj) : ((k2 == 1) ? Dd::face_node(1, jj) : Dd::face_node(2, jj));
+        v = (T)U[(size_t)e2 * NU + node * M + b];
+      }
+      C.Up[i] = v;
+    }
+    if (lane < NXE) C.xe[lane] = x[(size_t)vv[lane / DIM] * DIM + (lane % DIM)];
+    __syncwarp();
+    C.geometry();
+    signed char bcs[NF];
+#pragma unroll
+    for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
+    C.pointwise(lane, bcs, a.mu, a.gamma, true);
+    __syncwarp();
+    C.residual(lane);
+    if (lane == 0) {
+      double Xe[6];
+      for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+      C.distortion(Xe, a.kappa, a.eps);
+    }
+    __syncwarp();
+    for (int c = lane; c < ND; c += 32) {
+      T dR[NU];
+      if (c < NU + NUP) {
+        auto fe = [&](int i) { return (c < NU && i == c) ? T(1) : T(0); };
+        auto fp = [&](int i) { return (c >= NU && i == c - NU) ? T(1) : T(0); };
+        C.jvp_state(fe, fp, bcs, dR);
+      } else {
+        double dx[NXE];
+#pragma unroll
+        for (int r = 0; r < NXE; ++r) dx[r] = (r == c - NU - NUP) ? 1.0 : 0.0;
+        C.jvp_geom(dx, a.mu, dR);
+      }
+#pragma unroll
+      for (int i = 0; i < NU; ++i) Jout[((size_t)it * NU + i) * ND + c] = (double)dR[i];
+    }
+    for (int i = lane; i < NU; i += 32) Rout[(size_t)it * NU + i] = (double)C.R[i];
+    if (lane < NXE) dNout[(size_t)it * NXE + lane] = C.dN[lane];
+    if (lane == 0) Nout[it] = C.dN[NXE];
+    __syncwarp();
+  }
+}
+
+}  // namespace ift

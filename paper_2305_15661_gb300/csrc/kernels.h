@@ -1,0 +1,25 @@
+// Host-side table of the element kernels instantiated for each
+// (problem, degree, precision), so the C-ABI code can dispatch at run time.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace ift {
+
+struct KernelSet {
+  bool valid = false;
+  // launch the fused assembly (jac = true) or the objective-only pass (jac = false);
+  // args points to an AsmArgs<T> of the set's precision
+  cudaError_t (*assemble)(const void* args, bool jac, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
+  size_t (*smem_bytes)(bool jac, int ku, int kx, int warps) = nullptr;
+  cudaError_t (*prepare)(bool jac, size_t smem) = nullptr;
+  int (*blocks_per_sm)(bool jac, int block, size_t smem) = nullptr;
+  cudaError_t (*inspect)(const void* args, const double* U, const double* x, double* R, double* J, double* N,
+                         double* dN, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
+};
+
+// precision: 0 = FP64, 1 = FP32
+KernelSet euler_kernels(int p, int precision);
+KernelSet burgers_kernels(int p, int precision);
+
+}  // namespace ift

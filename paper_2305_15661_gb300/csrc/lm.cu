@@ -1,0 +1,304 @@
+// Levenberg-Marquardt step kernel and small helper kernels of the solve.
+#include <cuda_runtime.h>
+
+#include "../../include/ift.h"
+#include "elem.cuh"
+#include "lm.cuh"
+
+namespace ift {
+
+namespace {
+
+// Constants of the line search and damping rule (readings of Sec. 3.2.3):
+// lambda_0 = 1e-4, lambda/10 (>= 1e-12) after a full step, 10 lambda (<= 1e8)
+// after a shortened step; Armijo constant 1e-4 with an allowance of 16 machine
+// epsilons of |J| for rounding in J; at most 30 halvings; on a failed Cholesky
+// the diagonal is shifted by 1e-14 trace/k, times 10 per retry, at most 10 times.
+constexpr double kLam0 = 1e-4, kLamMin = 1e-12, kLamMax = 1e8, kC1 = 1e-4;
+constexpr double kRound = 16.0 * 2.220446049250313e-16;
+constexpr int kMaxHalvings = 30, kMaxShifts = 10;
+
+__device__ double active_norm(const LMState& s, int ku, int kx, bool full) {
+  double t = 0.0;
+  for (int c = 0; c < ku; ++c) t += s.g[c] * s.g[c];
+  if (full)
+    for (int c = 0; c < kx; ++c) t += s.g[ku + c] * s.g[ku + c];
+  return sqrt(t);
+}
+
+// Cholesky of the n x n matrix in shared memory A (row-major, lower triangle used),
+// done by one warp: for each column, lane-parallel updates of the rows below.
+__device__ bool warp_cholesky(double* A, int n, int lane) {
+  for (int j = 0; j < n; ++j) {
+    double d = 0.0;
+    if (lane == 0) {
+      double s = A[j * n + j];
+      for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+      d = s;
+    }
+    d = __shfl_sync(0xffffffffu, d, 0);
+    if (!(d > 0.0)) return false;
+    const double r = sqrt(d);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = t / r;
+    }
+    if (lane == 0) A[j * n + j] = r;
+    __syncwarp();
+  }
+  return true;
+}
+
+}  // namespace
+
+// Lane-0 logic of the iteration, in the order of the oracle's loop:
+//   at the current iterate: stop if |g| <= thresh (converged), else stop if the
+//   phase has taken max_iters steps, else solve for a step.
+// end_phase(): phase 0 hands over to phase 1 at the same point (the joint
+// iteration restarts there with lambda_0 and its own reference norm);
+// phase 1 finishes the solve.
+__device__ void begin_phase(LMState& s, const LMConsts& c) {
+  s.g0 = active_norm(s, c.ku, c.kx, s.phase == 1);
+  s.thresh = c.tol * fmax(1.0, s.g0);
+  s.lam = kLam0;
+}
+
+// Returns true if a step must be solved for, false if the solve finished.
+__device__ bool decide(LMState& s, const LMConsts& c) {
+  for (;;) {
+    const bool full = s.phase == 1;
+    int st = -100;
+    if (active_norm(s, c.ku, c.kx, full) <= s.thresh) st = IFT_OK;
+    else if (s.iters[s.phase] >= c.max_iters) st = IFT_NOT_CONVERGED;
+    if (st == -100) return true;
+    if (!full) {
+      s.init_status = st;
+      s.phase = 1;
+      begin_phase(s, c);
+      continue;
+    }
+    s.status = st;
+    s.done = 1;
+    return false;
+  }
+}
+
+// One LM step, single warp. res = [H (k*k) | g (k) | J | nonphysical count] at s.trial.
+__global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
+                               int use_cond) {
+  __shared__ double Ms[LM_KMAX * LM_KMAX];
+  __shared__ double rhs[LM_KMAX];
+  const int lane = threadIdx.x;
+  LMState& s = *sp;
+  const int ku = c.ku, kx = c.kx, k = ku + kx;
+  const double* Hr = res;
+  const double* gr = res + k * k;
+  const double Jr = res[k * k + k];
+  const double npr = res[k * k + k + 1];
+  int need_solve = 0;
+  if (lane == 0 && !s.done) {
+    s.bodies += 1;
+    if (s.bodies > c.body_limit) {
+      s.status = IFT_ERR_TIMEOUT;
+      s.done = 1;
+    } else if (s.state == 0) {
+      // result at the starting point of the solve
+      if (npr > 0.0 || !isfinite(Jr)) {
+        s.status = IFT_ERR_NONPHYSICAL;
+        s.done = 1;
+      } else {
+        for (int i = 0; i < k; ++i) {
+          s.z[i] = s.trial[i];
+          s.g[i] = gr[i];
+        }
+        s.J = Jr;
+        s.state = 1;
+        begin_phase(s, c);
+        need_solve = decide(s, c);
+      }
+    } else {
+      const bool ok = npr == 0.0 && isfinite(Jr) && Jr <= s.J + kC1 * s.alpha * s.slope + kRound * fabs(s.J);
+      if (ok) {
+        s.lam = (s.h == 0) ? fmax(s.lam / 10.0, kLamMin) : fmin(s.lam * 10.0, kLamMax);
+        for (int i = 0; i < k; ++i) {
+          s.z[i] = s.trial[i];
+          s.g[i] = gr[i];
+        }
+        s.J = Jr;
+        s.iters[s.phase] += 1;
+        need_solve = decide(s, c);
+      } else if (s.h + 1 > kMaxHalvings) {
+        // line search failed: this phase ends at the current iterate
+        if (s.phase == 0) {
+          s.init_status = IFT_LINESEARCH_FAILED;
+          s.phase = 1;
+          begin_phase(s, c);
+          need_solve = decide(s, c);
+        } else {
+          s.status = IFT_LINESEARCH_FAILED;
+          s.done = 1;
+        }
+      } else {
+        s.h += 1;
+        s.alpha *= 0.5;
+        const int ka = (s.phase == 1) ? k : ku;
+        for (int i = 0; i < ka; ++i) s.trial[i] = s.z[i] + s.alpha * s.dz[i];
+        s.trials += 1;
+      }
+    }
+  }
+  need_solve = __shfl_sync(0xffffffffu, need_solve, 0);
+  while (need_solve) {
+    __syncwarp();
+    // (H + diag(0, lambda I)) dz = -g on the active block
+    const int ka = (s.phase == 1) ? k : ku;
+    const double lam = s.lam;
+    const bool damp = s.phase == 1;
+    for (int i = lane; i < ka * ka; i += 32) {
+      const int r = i / ka, cc = i % ka;
+      double v = Hr[r * k + cc];
+      if (damp && r == cc && r >= ku) v += lam;
+      Ms[i] = v;
+    }
+    __syncwarp();
+    double tr = 0.0;
+    for (int i = 0; i < ka; ++i) tr += Ms[i * ka + i];
+    __syncwarp();
+    bool ok = warp_cholesky(Ms, ka, lane);
+    double sh = 1e-14 * tr / ka;
+    int nsh = 0;
+    while (!ok && nsh < kMaxShifts) {
+      __syncwarp();
+      for (int i = lane; i < ka * ka; i += 32) {
+        const int r = i / ka, cc = i % ka;
+        double v = Hr[r * k + cc];
+        if (damp && r == cc && r >= ku) v += lam;
+        if (r == cc) v += sh;
+        Ms[i] = v;
+      }
+      __syncwarp();
+      ok = warp_cholesky(Ms, ka, lane);
+      sh *= 10.0;
+      ++nsh;
+    }
+    __syncwarp();
+    int again = 0;
+    if (lane == 0) {
+      s.shifts += nsh;
+      if (ok) {
+        for (int i = 0; i < ka; ++i) rhs[i] = -s.g[i];
+        for (int i = 0; i < ka; ++i) {  // L y = -g
+          double t = rhs[i];
+          for (int j = 0; j < i; ++j) t -= Ms[i * ka + j] * rhs[j];
+          rhs[i] = t / Ms[i * ka + i];
+        }
+        for (int i = ka - 1; i >= 0; --i) {  // L^T dz = y
+          double t = rhs[i];
+          for (int j = i + 1; j < ka; ++j) t -= Ms[j * ka + i] * rhs[j];
+          rhs[i] = t / Ms[i * ka + i];
+        }
+        double slope = 0.0;
+        for (int i = 0; i < ka; ++i) {
+          s.dz[i] = rhs[i];
+          slope += s.g[i] * rhs[i];
+        }
+        for (int i = ka; i < k; ++i) s.dz[i] = 0.0;
+        s.slope = slope;
+        s.alpha = 1.0;
+        s.h = 0;
+        for (int i = 0; i < k; ++i) s.trial[i] = s.z[i] + s.dz[i];
+        s.trials += 1;
+      } else if (s.phase == 0) {
+        s.init_status = IFT_LINESEARCH_FAILED;
+        s.phase = 1;
+        begin_phase(s, c);
+        again = decide(s, c);
+      } else {
+        s.status = IFT_LINESEARCH_FAILED;
+        s.done = 1;
+      }
+    }
+    need_solve = __shfl_sync(0xffffffffu, again, 0);
+  }
+  __syncwarp();
+  // inside the solve graph: keep looping while the solve is not finished
+  if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, s.done ? 0u : 1u);
+}
+
+// Starting state: z = trial = (w0, tau0), phase 0 (paper initialisation) or 1 (given start).
+__global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0, int ku, int kx, int phase) {
+  LMState& s = *sp;
+  const int k = ku + kx;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double v = (i < ku) ? w0[i] : (tau0 ? tau0[i - ku] : 0.0);
+    s.z[i] = v;
+    s.trial[i] = v;
+    s.dz[i] = 0.0;
+    s.g[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    s.phase = phase;
+    s.state = 0;
+    s.status = IFT_NOT_CONVERGED;
+    s.init_status = IFT_OK;
+    s.iters[0] = s.iters[1] = 0;
+    s.trials = 0;
+    s.shifts = 0;
+    s.h = 0;
+    s.bodies = 0;
+    s.done = 0;
+    s.lam = kLam0;
+    s.alpha = 1.0;
+    s.J = 0.0;
+    s.slope = 0.0;
+    s.g0 = 0.0;
+    s.thresh = 0.0;
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nacc) return;
+  double s = 0.0;
+  for (int c = 0; c < nparts; ++c) s += partial[(size_t)c * nacc + i];
+  out[i] = s;
+}
+
+// w_guess = Phi^T U_guess, U_guess the constant state (Burgers u = 1, Euler U_inf(mu))
+// at every node. Block b sums rows [b*chunk, (b+1)*chunk) into part[b][c].
+__global__ void phit_u_partial_kernel(const double* Phi, long Nu, int ku, int m, int problem, double gamma,
+                                      const double* mu, long chunk, double* part) {
+  extern __shared__ double sh[];
+  double Ug[4];
+  if (problem == 2) {
+    euler_farfield(gamma, mu[0], mu[1], Ug);
+  } else {
+    Ug[0] = 1.0;
+  }
+  const long r0 = (long)blockIdx.x * chunk;
+  const long r1 = (r0 + chunk < Nu) ? r0 + chunk : Nu;
+  const int lanes_per_col = blockDim.x / ku;  // >= 1 (blockDim >= ku)
+  const int c = threadIdx.x % ku, sub = threadIdx.x / ku;
+  double s = 0.0;
+  if (sub < lanes_per_col)
+    for (long r = r0 + sub; r < r1; r += lanes_per_col) s += Phi[r * ku + c] * Ug[r % m];
+  sh[threadIdx.x] = (sub < lanes_per_col) ? s : 0.0;
+  __syncthreads();
+  if (threadIdx.x < ku) {
+    double t = 0.0;
+    for (int j = 0; j < lanes_per_col; ++j) t += sh[j * ku + threadIdx.x];
+    part[(size_t)blockIdx.x * ku + threadIdx.x] = t;
+  }
+}
+
+__global__ void sum_columns_kernel(const double* part, int nparts, int ku, double* w) {
+  const int c = threadIdx.x;
+  if (c >= ku) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += part[(size_t)b * ku + c];
+  w[c] = s;
+}
+
+}  // namespace ift

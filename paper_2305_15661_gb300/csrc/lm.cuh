@@ -1,0 +1,40 @@
+// Levenberg-Marquardt driver of the hyperreduced problem on the device (Sec. 3.2.3).
+//
+// The solve is a loop of identical bodies [assemble at the trial point ->
+// reduce -> lm_step]; lm_step reads the assembled (H, g, J) at the trial point,
+// accepts or rejects it by the sufficient-decrease test, updates lambda, checks
+// the stopping test, and on acceptance solves (H + diag(0, lambda I)) dz = -g by
+// Cholesky and writes the next trial point z + dz. A rejected trial halves the
+// step. Because the assembly at an accepted trial point is the assembly at the
+// new iterate, every LM iteration costs one fused assembly pass in the common
+// case (full step accepted).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ift {
+
+constexpr int LM_KMAX = 64;
+
+struct LMConsts {
+  double tol;
+  int max_iters;
+  int ku, kx;
+  int body_limit;   // hard bound on loop bodies (then IFT_ERR_TIMEOUT)
+};
+
+// Device-resident solver state (one per query).
+struct LMState {
+  int phase;        // 0: w only (tau frozen), 1: joint (w, tau), 2: finished
+  int state;        // 0: the pending assembly is at the starting point, 1: at a trial point
+  int status;       // ift_status
+  int init_status;  // status at the end of phase 0
+  int iters[2];     // accepted steps per phase
+  int trials, shifts, h, bodies, done;
+  double lam, alpha, J, slope, g0, thresh;
+  double z[LM_KMAX];      // current iterate (w | tau)
+  double dz[LM_KMAX];     // step
+  double g[LM_KMAX];      // gradient [S; T] at the current iterate
+  double trial[LM_KMAX];  // point of the next assembly (w | tau)
+};
+
+}  // namespace ift

@@ -1,0 +1,179 @@
+// Pointwise physics of the two conservation laws (device code):
+//  * compressible Euler (Eq. euler, Sec. 4.2): flux, analytic flux Jacobians,
+//    Roe numerical flux with an unnormalised face normal;
+//  * steady 1-D Burgers with source 0.5 exp(mu x): flux and Roe flux.
+// Discretisation sizes per (problem, degree) are compile-time constants.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dual.cuh"
+
+namespace ift {
+
+constexpr int PROB_BURGERS = 1;
+constexpr int PROB_EULER = 2;
+
+template <int PROB, int P>
+struct Disc;
+
+template <int P>
+struct Disc<PROB_BURGERS, P> {
+  static constexpr int M = 1, DIM = 1, NB = P + 1, NQ = P + 2, NFACE = 2, NTRACE = 1, NFQ = 1, NV = 2;
+  static constexpr int NU = NB * M, NUP = NFACE * NTRACE * M, NXE = NV * DIM;
+  // trace node j of face k (faces are the left and right end points)
+  __host__ __device__ static constexpr int face_node(int k, int j) { return (k == 0 || P == 0) ? 0 : P; }
+};
+
+template <int P>
+struct Disc<PROB_EULER, P> {
+  static constexpr int M = 4, DIM = 2, NB = (P + 1) * (P + 2) / 2, NQ = (P + 2) * (P + 2), NFACE = 3,
+                       NTRACE = P + 1, NFQ = P + 2, NV = 3;
+  static constexpr int NU = NB * M, NUP = NFACE * NTRACE * M, NXE = NV * DIM;
+  // face k runs from vertex k to vertex k+1 through edge k's interior nodes
+  __host__ __device__ static constexpr int face_node(int k, int j) {
+    return j == 0 ? k : (j == P ? (k + 1) % 3 : 3 + k * (P - 1) + (j - 1));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Euler
+// ---------------------------------------------------------------------------
+
+// Physical flux columns fx, fy and pressure of the conserved state U.
+template <class T>
+__device__ __forceinline__ void euler_flux(const T U[4], T g1, T fx[4], T fy[4], T& P) {
+  T ir = T(1) / U[0];
+  T u = U[1] * ir, v = U[2] * ir;
+  P = g1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+  T eh = U[3] + P;
+  fx[0] = U[1];
+  fx[1] = U[1] * u + P;
+  fx[2] = U[1] * v;
+  fx[3] = u * eh;
+  fy[0] = U[2];
+  fy[1] = U[2] * u;
+  fy[2] = U[2] * v + P;
+  fy[3] = v * eh;
+}
+
+// Flux Jacobians Ax = dfx/dU, Ay = dfy/dU (row-major 4x4) in closed form.
+template <class T>
+__device__ __forceinline__ void euler_flux_jac(const T U[4], T g1, T Ax[16], T Ay[16]) {
+  T ir = T(1) / U[0];
+  T u = U[1] * ir, v = U[2] * ir;
+  T k = T(0.5) * (u * u + v * v);  // kinetic energy per unit mass
+  T P = g1 * (U[3] - U[0] * k);
+  T Hs = (U[3] + P) * ir;          // total enthalpy
+  T gam = g1 + T(1);
+  Ax[0] = T(0); Ax[1] = T(1); Ax[2] = T(0); Ax[3] = T(0);
+  Ax[4] = g1 * k - u * u; Ax[5] = (T(3) - gam) * u; Ax[6] = -g1 * v; Ax[7] = g1;
+  Ax[8] = -u * v; Ax[9] = v; Ax[10] = u; Ax[11] = T(0);
+  Ax[12] = u * (g1 * k - Hs); Ax[13] = Hs - g1 * u * u; Ax[14] = -g1 * u * v; Ax[15] = gam * u;
+  Ay[0] = T(0); Ay[1] = T(0); Ay[2] = T(1); Ay[3] = T(0);
+  Ay[4] = -u * v; Ay[5] = v; Ay[6] = u; Ay[7] = T(0);
+  Ay[8] = g1 * k - v * v; Ay[9] = -g1 * u; Ay[10] = (T(3) - gam) * v; Ay[11] = g1;
+  Ay[12] = v * (g1 * k - Hs); Ay[13] = -g1 * u * v; Ay[14] = Hs - g1 * v * v; Ay[15] = gam * v;
+}
+
+// Plain-value overloads so euler_roe<T, T> compiles with the same helpers.
+template <class T>
+__device__ __forceinline__ T recip(T a) { return T(1) / a; }
+__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double dabs(double a) { return fabs(a); }
+__device__ __forceinline__ float dabs(float a) { return fabsf(a); }
+
+// Roe flux H(U+, U-; nt) for the scaled normal nt (|nt| = face measure factor):
+// the average of the two normal fluxes minus half the Roe-matrix upwinding,
+// |A_roe| dU = sum over the acoustic, entropy and shear waves of
+// |eigenvalue| x strength x eigenvector, with Roe averages weighted by sqrt(rho).
+// No entropy fix. S is T or a Dual over T.
+template <class S, class T>
+__device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const S nt[2], T g1, S H[4]) {
+  const T half = T(0.5);
+  S len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
+  S il = recip(len);
+  S nx = nt[0] * il, ny = nt[1] * il;
+  // interior side
+  S ri = recip(Ui[0]);
+  S ui = Ui[1] * ri, vi = Ui[2] * ri;
+  S pi = g1 * (Ui[3] - half * (Ui[1] * ui + Ui[2] * vi));
+  S hi = (Ui[3] + pi) * ri;
+  S vni = ui * nx + vi * ny;
+  // exterior side
+  S ro = recip(Uo[0]);
+  S uo = Uo[1] * ro, vo = Uo[2] * ro;
+  S po = g1 * (Uo[3] - half * (Uo[1] * uo + Uo[2] * vo));
+  S ho = (Uo[3] + po) * ro;
+  S vno = uo * nx + vo * ny;
+  // Roe averages
+  S si = dsqrt(Ui[0]), so = dsqrt(Uo[0]);
+  S iw = recip(si + so);
+  S ua = (si * ui + so * uo) * iw;
+  S va = (si * vi + so * vo) * iw;
+  S ha = (si * hi + so * ho) * iw;
+  S rhoa = si * so;
+  S qa = half * (ua * ua + va * va);
+  S c2 = g1 * (ha - qa);
+  S ca = dsqrt(c2);
+  S ic2 = recip(c2);
+  S vna = ua * nx + va * ny;
+  // jumps (exterior minus interior)
+  S drho = Uo[0] - Ui[0];
+  S dp = po - pi;
+  S du = uo - ui, dv = vo - vi;
+  S dvn = du * nx + dv * ny;
+  S dtx = du - dvn * nx, dty = dv - dvn * ny;  // tangential velocity jump
+  // wave strengths
+  S rcd = rhoa * ca * dvn;
+  S am = half * (dp - rcd) * ic2;  // eigenvalue vn - c
+  S ap = half * (dp + rcd) * ic2;  // eigenvalue vn + c
+  S ae = drho - dp * ic2;          // entropy wave, eigenvalue vn
+  S lm = dabs(vna - ca), lp = dabs(vna + ca), l0 = dabs(vna);
+  S wm = lm * am, wp = lp * ap, we = l0 * ae, ws = l0 * rhoa;
+  S cnx = ca * nx, cny = ca * ny, cvn = ca * vna;
+  S d0 = wm + wp + we;
+  S d1 = wm * (ua - cnx) + wp * (ua + cnx) + we * ua + ws * dtx;
+  S d2 = wm * (va - cny) + wp * (va + cny) + we * va + ws * dty;
+  S d3 = wm * (ha - cvn) + wp * (ha + cvn) + we * qa + ws * (ua * dtx + va * dty);
+  // normal fluxes
+  S ehi = Ui[3] + pi, eho = Uo[3] + po;
+  S f0 = Ui[0] * vni + Uo[0] * vno;
+  S f1 = Ui[1] * vni + pi * nx + Uo[1] * vno + po * nx;
+  S f2 = Ui[2] * vni + pi * ny + Uo[2] * vno + po * ny;
+  S f3 = ehi * vni + eho * vno;
+  S hl = half * len;
+  H[0] = hl * (f0 - d0);
+  H[1] = hl * (f1 - d1);
+  H[2] = hl * (f2 - d2);
+  H[3] = hl * (f3 - d3);
+}
+
+// Far-field state U_inf(mu): rho = 1, P = 1, c = sqrt(gamma), velocity M c (cos a, sin a).
+__device__ __forceinline__ void euler_farfield(double gamma, double mach, double ang, double U[4]) {
+  double c = sqrt(gamma);
+  double vx = mach * c * cos(ang), vy = mach * c * sin(ang);
+  U[0] = 1.0;
+  U[1] = vx;
+  U[2] = vy;
+  U[3] = 1.0 / (gamma - 1.0) + 0.5 * (vx * vx + vy * vy);
+}
+
+// ---------------------------------------------------------------------------
+// Burgers: f(u) = u^2/2, Roe speed a = (u+ + u-)/2, flux
+// H = (f(u+) + f(u-)) n / 2 - |a n| (u- - u+) / 2, and its two partial derivatives.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void burgers_roe(T ui, T uo, T n, T& H, T& Hi, T& Ho) {
+  T an = T(0.5) * (ui + uo) * n;
+  T s = (an > T(0)) ? T(1) : ((an < T(0)) ? T(-1) : T(0));
+  T aa = fabs(an);
+  T jump = uo - ui;
+  H = T(0.25) * (ui * ui + uo * uo) * n - T(0.5) * aa * jump;
+  // d|a n|/du = sign(a n) n / 2 for either side
+  T dabs_du = T(0.5) * s * n;
+  Hi = T(0.5) * ui * n - T(0.5) * dabs_du * jump + T(0.5) * aa;
+  Ho = T(0.5) * uo * n - T(0.5) * dabs_du * jump - T(0.5) * aa;
+}
+
+}  // namespace ift

@@ -1,0 +1,244 @@
+"""Python binding of the C-ABI library libift.so (include/ift.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels. There is no CPU fallback; if the library cannot be loaded the
+calls raise. PyTorch is used only for device memory and streams in the
+``*_dev`` variants (tensors' data pointers and the current stream).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libift.so")
+
+IFT_OK = 0
+IFT_NOT_CONVERGED = 1
+IFT_LINESEARCH_FAILED = 2
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "LINESEARCH_FAILED", -1: "ERR_ARG", -2: "ERR_STATE",
+                -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_NONPHYSICAL", -6: "ERR_TIMEOUT", -7: "ERR_NOTIMPL"}
+BURGERS1D = 1
+EULER2D = 2
+FP64 = 0
+FP32 = 1
+INIT_PAPER = 0
+INIT_GIVEN = 1
+
+
+class IFTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_int), ("p", ctypes.c_int), ("precision", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("eps_g", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("lm_init", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("init_iters", ctypes.c_int), ("iters", ctypes.c_int),
+                ("trials", ctypes.c_int), ("shifts", ctypes.c_int), ("J", ctypes.c_double),
+                ("normS", ctypes.c_double), ("normT", ctypes.c_double), ("g0", ctypes.c_double)]
+
+
+_lib = None
+
+EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", "ift_create_error",
+           "ift_reference_nodes", "ift_sizes", "ift_set_mesh", "ift_set_bases", "ift_set_eq_weights",
+           "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
+           "ift_solve_rom", "ift_solve_rom_dev"]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libift.so; raises OSError if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libift.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pd = ctypes.POINTER(ctypes.c_double)
+    pi = ctypes.POINTER(ctypes.c_int32)
+    pl = ctypes.POINTER(ctypes.c_int64)
+    P = ctypes.POINTER
+    sigs = {
+        "ift_config_default": (None, [P(Config)]),
+        "ift_create": (i32, [P(Config), vp, P(vp)]),
+        "ift_destroy": (i32, [vp]),
+        "ift_last_error": (ctypes.c_char_p, [vp]),
+        "ift_create_error": (ctypes.c_char_p, []),
+        "ift_reference_nodes": (i32, [vp, pd, pi]),
+        "ift_sizes": (i32, [vp, pl]),
+        "ift_set_mesh": (i32, [vp, i64, pd, i64, pi]),
+        "ift_set_bases": (i32, [vp, i64, i32, pd, i64, i32, pd]),
+        "ift_set_eq_weights": (i32, [vp, i64, pi, pd]),
+        "ift_reduced_residual_jacobian": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
+        "ift_reduced_residual_jacobian_dev": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ift_element_eval": (i32, [vp, pd, pd, pd, i64, pi, pd, pd, pd, pd, pd, pd]),
+        "ift_solve_rom": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
+        "ift_solve_rom_dev": (i32, [vp, vp, vp, vp, P(SolveInfo), vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _pd(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _tptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One problem instance on the current CUDA device."""
+
+    def __init__(self, problem: int, p: int, precision: int = FP64, gamma: float = 1.4, kappa: float = 0.0,
+                 eps_g: float = 1e-8, tol: float = 1e-8, max_iters: int = 200, lm_init: int = INIT_PAPER,
+                 stream=None):
+        lib = load()
+        cfg = Config()
+        lib.ift_config_default(ctypes.byref(cfg))
+        cfg.problem, cfg.p, cfg.precision = problem, p, precision
+        cfg.gamma, cfg.kappa, cfg.eps_g, cfg.tol = gamma, kappa, eps_g, tol
+        cfg.max_iters, cfg.lm_init = max_iters, lm_init
+        h = ctypes.c_void_p()
+        st = lib.ift_create(ctypes.byref(cfg), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if st != IFT_OK:
+            raise IFTError(st, lib.ift_create_error().decode())
+        self._h = h
+        self.cfg = cfg
+        s = np.zeros(8, dtype=np.int64)
+        lib.ift_sizes(h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        self.nb, self.nu, self.nup, self.nxe, self.nface, self.ntrace, self.nq, self.nfq = (int(v) for v in s)
+        self.dim = 1 if problem == BURGERS1D else 2
+        self.n_mu = 1 if problem == BURGERS1D else 2
+        self.ku = self.kx = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ift_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow_positive=False):
+        if st < 0 or (st > 0 and not allow_positive):
+            raise IFTError(st, load().ift_last_error(self._h).decode())
+        return st
+
+    # -- set-up ------------------------------------------------------------
+    def reference_nodes(self):
+        nodes = np.zeros(self.nb * self.dim)
+        fn = np.zeros(self.nface * self.ntrace, dtype=np.int32)
+        self._check(load().ift_reference_nodes(self._h, _pd(nodes), _pi(fn)))
+        return nodes.reshape(self.nb, self.dim), fn.reshape(self.nface, self.ntrace)
+
+    def set_mesh(self, X, ev):
+        X = _f64(X)
+        ev = np.ascontiguousarray(ev, dtype=np.int32)
+        self.n_verts = X.shape[0]
+        self.n_elems = ev.shape[0]
+        self._check(load().ift_set_mesh(self._h, self.n_verts, _pd(X), self.n_elems, _pi(ev)))
+
+    def set_bases(self, Phi, Psi):
+        Phi = _f64(Phi)
+        Psi = _f64(Psi)
+        self.ku, self.kx = Phi.shape[1], Psi.shape[1]
+        self._check(load().ift_set_bases(self._h, Phi.shape[0], self.ku, _pd(Phi), Psi.shape[0], self.kx,
+                                         _pd(Psi) if self.kx else None))
+
+    def set_eq_weights(self, rho_set):
+        """rho_set = (elems, rho) or None for rho = 1 on every element."""
+        if rho_set is None:
+            self._check(load().ift_set_eq_weights(self._h, -1, None, None))
+            return
+        elems = np.ascontiguousarray(rho_set[0], dtype=np.int32)
+        rho = _f64(rho_set[1])
+        self._check(load().ift_set_eq_weights(self._h, len(elems), _pi(elems), _pd(rho)))
+
+    @classmethod
+    def from_workload(cls, wl, precision=FP64, **kw):
+        ctx = cls(wl.problem, wl.p, precision=precision, gamma=wl.gamma, kappa=kw.pop("kappa", wl.kappa), **kw)
+        ctx.set_mesh(wl.X, wl.ev)
+        ctx.set_bases(wl.Phi, wl.Psi)
+        return ctx
+
+    # -- evaluation --------------------------------------------------------
+    def reduced_residual_jacobian(self, mu, y, z):
+        k = self.ku + self.kx
+        S = np.zeros(self.ku)
+        T = np.zeros(max(self.kx, 1))
+        H = np.zeros(k * k)
+        J = np.zeros(1)
+        zz = _f64(z) if self.kx else np.zeros(1)
+        st = load().ift_reduced_residual_jacobian(self._h, _pd(_f64(mu)), _pd(_f64(y)), _pd(zz), _pd(S), _pd(T),
+                                                  _pd(H), _pd(J))
+        if st not in (IFT_OK, -5):
+            self._check(st)
+        return {"S": S, "T": T[:self.kx], "H": H.reshape(k, k), "J": float(J[0]), "status": int(st)}
+
+    def reduced_residual_jacobian_dev(self, mu, y, z, S, T, H, J, stream=None):
+        """Device-pointer variant; all arguments are CUDA tensors (float64)."""
+        self._check(load().ift_reduced_residual_jacobian_dev(self._h, _tptr(mu), _tptr(y), _tptr(z), _tptr(S),
+                                                             _tptr(T), _tptr(H), _tptr(J),
+                                                             ctypes.c_void_p(stream) if stream else None))
+
+    def element_eval(self, mu, U, x, elems):
+        elems = np.ascontiguousarray(elems, dtype=np.int32)
+        n = len(elems)
+        R = np.zeros(n * self.nu)
+        JU = np.zeros(n * self.nu * self.nu)
+        JUp = np.zeros(n * self.nu * self.nup)
+        Jx = np.zeros(n * self.nu * self.nxe)
+        N = np.zeros(n)
+        dN = np.zeros(n * self.nxe)
+        self._check(load().ift_element_eval(self._h, _pd(_f64(mu)), _pd(_f64(U)), _pd(_f64(x)), n, _pi(elems),
+                                            _pd(R), _pd(JU), _pd(JUp), _pd(Jx), _pd(N), _pd(dN)))
+        return {"R": R.reshape(n, self.nu), "JU": JU.reshape(n, self.nu, self.nu),
+                "JUp": JUp.reshape(n, self.nu, self.nup), "Jx": Jx.reshape(n, self.nu, self.nxe), "N": N,
+                "dN": dN.reshape(n, self.nxe)}
+
+    def solve_rom(self, mu, y0=None, z0=None):
+        y = np.zeros(self.ku) if y0 is None else _f64(y0).copy()
+        z = np.zeros(max(self.kx, 1)) if z0 is None else np.concatenate([_f64(z0), np.zeros(1)])
+        info = SolveInfo()
+        st = load().ift_solve_rom(self._h, _pd(_f64(mu)), _pd(y), _pd(z), ctypes.byref(info))
+        self._check(st, allow_positive=True)
+        return {"status": int(st), "w": y, "tau": z[:self.kx], "init_iters": info.init_iters, "iters": info.iters,
+                "trials": info.trials, "shifts": info.shifts, "J": info.J, "normS": info.normS,
+                "normT": info.normT, "g0": info.g0}
+
+    def solve_rom_dev(self, mu, y, z, stream=None, want_info=True):
+        info = SolveInfo()
+        st = load().ift_solve_rom_dev(self._h, _tptr(mu), _tptr(y), _tptr(z),
+                                      ctypes.byref(info) if want_info else None,
+                                      ctypes.c_void_p(stream) if stream else None)
+        self._check(st, allow_positive=True)
+        if not want_info:
+            return None
+        return {"status": int(st), "init_iters": info.init_iters, "iters": info.iters, "trials": info.trials,
+                "J": info.J, "normS": info.normS, "normT": info.normT, "g0": info.g0}

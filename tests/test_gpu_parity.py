@@ -1,0 +1,302 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Tolerances (FP64): element residuals and Jacobians rel 1e-12, reduced H, g, J
+rel 1e-10 (Frobenius / max-norm), LM iterates rel 1e-10 at the same iteration
+count. FP32 element kernels: the tolerances below follow from FP32 rounding
+(unit roundoff 6e-8) amplified by sums of a few hundred terms and by the
+cancellation in g = sum_e A_e^T R_e.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2305_15661_gb300 import ift
+from paper_2305_15661_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def deformed(X, ev, n, seed, amp=0.3):
+    rng = np.random.default_rng(seed)
+    interior = np.all((X > 1e-12) & (X < 1 - 1e-12), axis=1)
+    d = rng.uniform(-1, 1, size=X.shape) * amp / n
+    d[~interior] = 0.0
+    return X + d
+
+
+# ---------------------------------------------------------------------------
+# element level
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("kappa", [0.0, 0.1])
+def test_euler_element_parity(p, kappa):
+    n = 4
+    X, ev = W.square_tri_mesh(n)
+    O = orc.Oracle(orc.PROB_EULER2D, p, X, ev, gamma=GAMMA, kappa=kappa)
+    ctx = ift.Context(ift.EULER2D, p, kappa=kappa)
+    ctx.set_mesh(X, ev)
+    mu = np.array([2.0, 0.03])
+    rng = np.random.default_rng(p)
+    U = np.tile(orc.freestream(GAMMA, mu), O.Nu // 4) * (1 + 0.05 * rng.normal(size=O.Nu))
+    x = deformed(X, ev, n, seed=p).ravel()
+    elems = np.arange(O.n_elems, dtype=np.int32)
+    g = ctx.element_eval(mu, U, x, elems)
+    for e in elems:
+        Ue, Up, xe = O.gather(U, x, e)
+        r = O.element(e, Ue, Up, xe, mu)
+        assert rel(g["R"][e], r["R"]) < 1e-12
+        assert rel(g["JU"][e], r["JU"]) < 1e-12
+        assert rel(g["JUp"][e], r["JUp"]) < 1e-12
+        assert rel(g["Jx"][e], r["Jx"]) < 1e-12
+        assert abs(g["N"][e] - r["N"]) <= 1e-12 * max(abs(r["N"]), 1e-12)
+        if kappa:
+            assert rel(g["dN"][e], r["dN"]) < 1e-10
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_burgers_element_parity(p):
+    X, ev = W.interval_mesh(7)
+    O = orc.Oracle(orc.PROB_BURGERS1D, p, X, ev)
+    ctx = ift.Context(ift.BURGERS1D, p)
+    ctx.set_mesh(X, ev)
+    rng = np.random.default_rng(p)
+    U = 1.0 + 0.3 * rng.normal(size=O.Nu)
+    x = X + np.concatenate([[0], 0.03 * rng.uniform(-1, 1, 6), [0]])
+    mu = np.array([1.3])
+    g = ctx.element_eval(mu, U, x, np.arange(7, dtype=np.int32))
+    for e in range(7):
+        Ue, Up, xe = O.gather(U, x, e)
+        r = O.element(e, Ue, Up, xe, mu)
+        for key in ("R", "JU", "JUp", "Jx"):
+            assert rel(g[key][e], r[key]) < 1e-12, key
+
+
+def test_fp32_element_accuracy():
+    n, p = 4, 2
+    X, ev = W.square_tri_mesh(n)
+    O = orc.Oracle(orc.PROB_EULER2D, p, X, ev, gamma=GAMMA)
+    ctx = ift.Context(ift.EULER2D, p, precision=ift.FP32)
+    ctx.set_mesh(X, ev)
+    mu = np.array([2.0, 0.0])
+    rng = np.random.default_rng(3)
+    U = np.tile(orc.freestream(GAMMA, mu), O.Nu // 4) * (1 + 0.05 * rng.normal(size=O.Nu))
+    x = deformed(X, ev, n, seed=3).ravel()
+    g = ctx.element_eval(mu, U, x, np.arange(O.n_elems, dtype=np.int32))
+    worst = {"R": 0.0, "JU": 0.0, "JUp": 0.0, "Jx": 0.0}
+    for e in range(O.n_elems):
+        Ue, Up, xe = O.gather(U, x, e)
+        r = O.element(e, Ue, Up, xe, mu)
+        for key in worst:
+            # residuals are differences of O(1) fluxes: measure against the flux scale
+            scale = np.abs(r["JU"]).max() * np.abs(Ue).max() if key == "R" else np.abs(r[key]).max()
+            worst[key] = max(worst[key], np.abs(g[key][e] - r[key]).max() / scale)
+    assert all(v < 1e-5 for v in worst.values()), worst
+
+
+# ---------------------------------------------------------------------------
+# reduced assembly
+# ---------------------------------------------------------------------------
+
+def _assembly_pair(wl, rho_set=None, precision=ift.FP64, kappa=None):
+    O = orc.Oracle.from_workload(wl, kappa=kappa)
+    ctx = ift.Context.from_workload(wl, precision=precision, **({"kappa": kappa} if kappa is not None else {}))
+    ctx.set_eq_weights(rho_set)
+    mu = wl.mus[0]
+    g = ctx.reduced_residual_jacobian(mu, wl.w_eval, wl.tau_eval)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, mu, rho_set=rho_set)
+    return g, r, ctx
+
+
+def _fro(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.1])
+def test_euler_reduced_fp64_dense(kappa):
+    wl = W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=5)
+    g, r, _ = _assembly_pair(wl, kappa=kappa)
+    assert g["status"] == 0
+    for key in ("S", "T", "H"):
+        assert _fro(g[key], r[key]) < 1e-10, key
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_euler_reduced_fp64_sparse_rho(p):
+    wl = W.euler_workload(n=10, p=p, k_u=7, k_x=3, seed=6)
+    sets = W.eq_weight_sets(wl, 2, seed=7, lo=20, hi=60)
+    for rs in sets:
+        g, r, _ = _assembly_pair(wl, rho_set=rs)
+        for key in ("S", "T", "H"):
+            assert _fro(g[key], r[key]) < 1e-10, key
+        assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+
+
+def test_burgers_reduced_fp64_full_size():
+    wl = W.burgers_workload()
+    wl.w_eval = wl.Phi.T @ W.replicate_guess(wl, wl.U_guess) + 0.05 * wl.w_eval
+    g, r, _ = _assembly_pair(wl)
+    for key in ("S", "T", "H"):
+        assert _fro(g[key], r[key]) < 1e-10, key
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+
+
+def test_euler_config2_full_size_fp64_and_fp32():
+    # 100 x 100 x 2 triangles, p = 2, k_u = 20, k_x = 4: the full assembly of the benchmark
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+    g, r, _ = _assembly_pair(wl)
+    for key in ("S", "T", "H"):
+        assert _fro(g[key], r[key]) < 1e-10, key
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+    ctx32 = ift.Context.from_workload(wl, precision=ift.FP32)
+    g32 = ctx32.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert _fro(g32["H"], r["H"]) < 1e-5
+    assert _fro(np.concatenate([g32["S"], g32["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-3
+    assert abs(g32["J"] - r["J"]) <= 1e-5 * r["J"]
+
+
+def test_fp32_small_assembly_tolerances():
+    wl = W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=5)
+    g, r, _ = _assembly_pair(wl, precision=ift.FP32)
+    assert _fro(g["H"], r["H"]) < 1e-5
+    assert _fro(np.concatenate([g["S"], g["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-3
+    assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
+
+
+def test_assembly_is_deterministic():
+    wl = W.euler_workload(n=20, p=2, k_u=10, k_x=4, seed=8)
+    ctx = ift.Context.from_workload(wl)
+    a = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    b = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    for key in ("S", "T", "H"):
+        np.testing.assert_array_equal(a[key], b[key])
+    assert a["J"] == b["J"]
+
+
+def test_device_pointer_variant_matches_host():
+    import torch
+
+    wl = W.euler_workload(n=10, p=2, k_u=8, k_x=4, seed=9)
+    ctx = ift.Context.from_workload(wl)
+    h = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
+    k = wl.ku + wl.kx
+    S, T, H, J = (torch.zeros(n, dtype=torch.float64, device=dev) for n in (wl.ku, wl.kx, k * k, 1))
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx.reduced_residual_jacobian_dev(t(wl.mus[0]), t(wl.w_eval), t(wl.tau_eval), S, T, H, J, stream=stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(S.cpu().numpy(), h["S"])
+    np.testing.assert_array_equal(T.cpu().numpy(), h["T"])
+    np.testing.assert_array_equal(H.cpu().numpy().reshape(k, k), h["H"])
+    assert J.item() == h["J"]
+
+
+# ---------------------------------------------------------------------------
+# LM solve
+# ---------------------------------------------------------------------------
+
+def _solve_pair(wl, tol, rho_set=None):
+    O = orc.Oracle.from_workload(wl)
+    ctx = ift.Context.from_workload(wl, tol=tol)
+    ctx.set_eq_weights(rho_set)
+    mu = wl.mus[0]
+    g = ctx.solve_rom(mu)
+    wg = wl.Phi.T @ W.replicate_guess(wl, wl.U_guess)
+    r = O.solve(wl.Phi, wl.Psi, mu, wg, rho_set=rho_set, tol=tol)
+    return g, r
+
+
+def _check_solve(g, r):
+    assert g["status"] == 0 and r["status"] == 0, (g, r["status"])
+    assert g["init_iters"] == r["init_iters"] and g["iters"] == r["iters"], (g, r)
+    assert g["trials"] == r["trials"]
+    z = np.concatenate([g["w"], g["tau"]])
+    zr = np.concatenate([r["w"], r["tau"]])
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr), np.linalg.norm(z - zr) / np.linalg.norm(zr)
+    assert abs(g["J"] - r["J"]) <= 1e-12 * r["J"]
+
+
+def test_burgers_config1_solve():
+    _check_solve(*_solve_pair(W.burgers_workload(), tol=1e-10))
+
+
+def test_euler_small_solve_dense():
+    _check_solve(*_solve_pair(W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6), tol=1e-8))
+
+
+def test_euler_small_solve_sparse_rho():
+    wl = W.euler_workload(n=12, p=2, k_u=8, k_x=4, seed=6)
+    rs = W.eq_weight_sets(wl, 1, seed=7, lo=40, hi=80)[0]
+    _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs))
+
+
+def test_given_start_and_repeat_solves():
+    wl = W.burgers_workload(n_elems=60)
+    ctx = ift.Context.from_workload(wl, tol=1e-10)
+    mu = wl.mus[0]
+    a = ctx.solve_rom(mu)
+    b = ctx.solve_rom(mu)
+    np.testing.assert_array_equal(a["w"], b["w"])
+    warm = ift.Context.from_workload(wl, tol=1e-10, lm_init=ift.INIT_GIVEN)
+    c = warm.solve_rom(mu, a["w"], a["tau"])
+    assert c["status"] == 0 and c["init_iters"] == 0 and c["iters"] <= 1
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+
+def test_errors_and_call_order():
+    ctx = ift.Context(ift.EULER2D, 2)
+    with pytest.raises(ift.IFTError) as ei:
+        ctx.reduced_residual_jacobian(np.array([2.0, 0.0]), np.zeros(3), np.zeros(1))
+    assert ei.value.status == -2
+    X, ev = W.square_tri_mesh(2)
+    with pytest.raises(ift.IFTError) as ei:
+        ctx.set_mesh(X, ev[:, [0, 2, 1]])  # clockwise: inverted
+    assert ei.value.status == -1
+    ctx.set_mesh(X, ev)
+    with pytest.raises(ift.IFTError):
+        ctx.set_bases(np.zeros((10, 2)), np.zeros((18, 1)))  # wrong N_u
+    with pytest.raises(ift.IFTError):
+        ctx.set_eq_weights((np.array([0, 0]), np.array([1.0, 1.0])))  # duplicate element
+    with pytest.raises(ift.IFTError):
+        ctx.set_eq_weights((np.array([0, 1]), np.array([1.0, -1.0])))  # negative weight
+    with pytest.raises(ift.IFTError):
+        ift.Context(ift.EULER2D, 7)
+
+
+def test_nonphysical_point_reported():
+    wl = W.euler_workload(n=6, p=1, k_u=4, k_x=2, seed=3)
+    ctx = ift.Context.from_workload(wl)
+    w = -wl.w_eval  # negative density everywhere
+    g = ctx.reduced_residual_jacobian(wl.mus[0], w, wl.tau_eval)
+    assert g["status"] == -5 and np.isinf(g["J"])
+
+
+def test_no_mesh_motion_basis():
+    wl = W.euler_workload(n=6, p=2, k_u=5, k_x=2, seed=3)
+    wl.Psi = np.zeros((wl.Psi.shape[0], 0))
+    wl.tau_eval = np.zeros(0)
+    g, r, _ = _assembly_pair(wl)
+    for key in ("S", "H"):
+        assert _fro(g[key], r[key]) < 1e-10, key
+    assert g["T"].shape == (0,)
+
+
+def test_single_element_and_ragged_weight_list():
+    wl = W.euler_workload(n=5, p=2, k_u=6, k_x=2, seed=2)
+    for elems in ([7], [0, 1, 2], list(range(0, 50, 3))):
+        rs = (np.array(elems), np.linspace(0.5, 3.0, len(elems)))
+        g, r, _ = _assembly_pair(wl, rho_set=rs)
+        for key in ("S", "T", "H"):
+            assert _fro(g[key], r[key]) < 1e-10, key
