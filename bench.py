@@ -1,0 +1,373 @@
+"""Benchmark of the EQP-IFT hot path on GB300.
+
+Workload (the configuration the headline metric is quoted on): steady 2-D
+Euler, DG p = 2 on 100 x 100 x 2 triangles (20,000 elements), Mach 2, k_u = 20
+state modes and k_x = 4 mesh modes, rho = 1 (full assembly), FP64. One step is
+one complete ROM solve: the paper's initialisation (LM on w with tau = 0) and
+the joint Levenberg-Marquardt iteration to a relative optimality of 1e-8, every
+assembly and line-search evaluation running in the library's kernels inside one
+CUDA graph.
+
+Timed region: K solves, each bracketed by CUDA events on the library's stream;
+L2 is flushed (a 512 MB write) between steps, outside the events. value =
+solves/s over all ranks (replicas: each rank solves its own queries).
+e2e: the same solves through the host API (host mu in, y, z and solve info
+back), wall clock with the copies inside.
+roofline: the fused assembly kernel, FP64 ALU bound; achieved = algorithmic
+FLOPs of the assemblies executed in the timed region / timed duration.
+cpu_baseline: the FP64 oracle's solve of the same workload on the host cores.
+
+--impl reference runs the oracle itself (the paper provides no code; the oracle
+is the reference implementation here), one solve per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ROM solves/sec at rel. resid 1e-8 vs FP64 oracle; element R+J evals/sec"
+WORKLOAD = "euler2d_p2_20000el_ku20_kx4_rho1_fp64"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload():
+    from paper_2305_15661_gb300 import workloads as W
+
+    return W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def fp64_alu_peak():
+    """Measured FP64 FMA throughput of this GPU (TFLOP/s) from the FMA probe."""
+    import ctypes
+
+    from paper_2305_15661_gb300 import build as B
+
+    lib = ctypes.CDLL(B.build_probe())
+    lib.fma_probe.restype = ctypes.c_int
+    lib.fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_double)]
+    best = 0.0
+    for _ in range(3):
+        v = ctypes.c_double()
+        if lib.fma_probe(0, 152 * 8, 256, 4096, ctypes.byref(v)) == 0:
+            best = max(best, v.value / 1e12)
+    return best
+
+
+def cpu_baseline_solve(wl, reps=1):
+    import oracle as orc
+    from paper_2305_15661_gb300 import workloads as W
+
+    O = orc.Oracle.from_workload(wl)
+    mu = wl.mus[0]
+    wg = wl.Phi.T @ W.replicate_guess(wl, wl.U_guess)
+    times = []
+    res = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        res = O.solve(wl.Phi, wl.Psi, mu, wg, tol=1e-8)
+        times.append(time.perf_counter() - t0)
+    return min(times), res, orc.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = make_workload()
+    for _ in range(args.warmup):
+        cpu_baseline_solve(wl)
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        _, res, threads = cpu_baseline_solve(wl)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": 20000, "p": 2, "k_u": 20, "k_x": 4, "tol": 1e-8},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} full FP64 oracle solves of the workload "
+                                       f"({res['init_iters']}+{res['iters']} LM steps each)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ift.load()
+    wl = make_workload()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ift.Context.from_workload(wl, tol=1e-8, stream=stream.cuda_stream)
+    mu_d = torch.as_tensor(wl.mus[0], dtype=torch.float64, device=dev)
+    y_d = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
+    z_d = torch.zeros(wl.kx, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (also builds the solve graph)
+    info = None
+    for _ in range(args.warmup):
+        info = ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=True)
+    assert info is not None and info["status"] == 0, info
+    assemblies = 1 + info["trials"]
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=False)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # end to end through the host API: host mu in, y, z and info out
+    e2e_steps = max(3, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = ctx.solve_rom(wl.mus[0])
+    e2e_s = time.perf_counter() - t0
+    assert out["status"] == 0
+    e2e_value = world * e2e_steps / e2e_s
+    h2d = 8 * len(wl.mus[0])
+    d2h = 2144  # solver state read back for y, z and the solve info (sizeof of the device state)
+
+    # isolated assembly timing (device pointers), for the per-launch duration
+    S = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
+    T = torch.zeros(wl.kx, dtype=torch.float64, device=dev)
+    k = wl.ku + wl.kx
+    H = torch.zeros(k * k, dtype=torch.float64, device=dev)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    yv = torch.as_tensor(wl.w_eval, dtype=torch.float64, device=dev)
+    zv = torch.as_tensor(wl.tau_eval, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ctx.reduced_residual_jacobian_dev(mu_d, yv, zv, S, T, H, J, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    n_iso = 20
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(n_iso):
+        ctx.reduced_residual_jacobian_dev(mu_d, yv, zv, S, T, H, J, stream=stream.cuda_stream)
+    a1.record(stream)
+    a1.synchronize()
+    iso_ms = a0.elapsed_time(a1) / n_iso
+
+    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    n_el = wl.n_elems
+    # achieved over the timed region: all assemblies of the K solves / timed duration
+    achieved_tf = assemblies * args.steps * fl * n_el / (sum(step_ms) / 1e3) / 1e12
+    iso_tf = fl * n_el / (iso_ms / 1e3) / 1e12
+    peak_tf = fp64_alu_peak()
+    evals_per_s = world * assemblies * args.steps * n_el / total_s
+
+    line = None
+    if rank == 0:
+        launches_per_solve = 4 + 3 * assemblies
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            cpu_s, res, threads = cpu_baseline_solve(wl)
+            cpu = {"value": 1.0 / cpu_s, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                   "sample": f"one full FP64 oracle solve of the workload ({res['init_iters']}+{res['iters']} "
+                             f"LM steps, {cpu_s:.1f} s)"}
+        clk = clocks.summary()
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "elements": n_el, "p": 2, "k_u": wl.ku, "k_x": wl.kx,
+                           "tol": 1e-8, "l2": "flushed between steps (512 MB write)",
+                           "assemblies_per_solve": assemblies, "parallelism": f"replicas{world}"},
+                "element_rj_evals_per_s": evals_per_s,
+                "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "roofline": {"bound": "alu", "kernel": "assemble_kernel<double,Euler,p=2,JAC>",
+                             "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                             "frac": achieved_tf / peak_tf if peak_tf else None, "traffic": None,
+                             "peak_source": "FP64 FMA probe on this GPU (measured)",
+                             "flops_per_element": fl, "isolated_assembly_ms": iso_ms,
+                             "isolated_achieved": iso_tf},
+                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_solve * args.steps}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_assembly(args):
+    """Isolated fused assemblies of the workload at its evaluation point."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+
+    dev = torch.device("cuda", 0)
+    ift.load()
+    wl = make_workload()
+    stream = torch.cuda.Stream(device=dev)
+    prec = ift.FP64 if args.precision == "fp64" else ift.FP32
+    ctx = ift.Context.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    k = wl.ku + wl.kx
+    t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
+    mu, y, z = t(wl.mus[0]), t(wl.w_eval), t(wl.tau_eval)
+    S, T, H, J = (torch.zeros(n, dtype=torch.float64, device=dev) for n in (wl.ku, wl.kx, k * k, 1))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.reduced_residual_jacobian_dev(mu, y, z, S, T, H, J, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.reduced_residual_jacobian_dev(mu, y, z, S, T, H, J, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    med = statistics.median(ms)
+    print(json.dumps({"mode": "assembly", "precision": args.precision, "elements": wl.n_elems,
+                      "median_ms": med, "min_ms": min(ms), "element_rj_evals_per_s": wl.n_elems / (med / 1e3),
+                      "achieved_tflops": fl * wl.n_elems / (med / 1e3) / 1e12, "flops_per_element": fl}))
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", choices=["solve", "assembly"], default="solve",
+                    help="assembly: only time isolated fused assemblies (for profiler captures)")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="element/contraction arithmetic for --mode assembly")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.mode == "assembly":
+        return run_assembly(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -23,6 +23,10 @@ def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
 
 
+def jac_scale(r):
+    return max(np.abs(r["JU"]).max(), np.abs(r["JUp"]).max(), np.abs(r["Jx"]).max())
+
+
 def deformed(X, ev, n, seed, amp=0.3):
     rng = np.random.default_rng(seed)
     interior = np.all((X > 1e-12) & (X < 1 - 1e-12), axis=1)
@@ -53,9 +57,11 @@ def test_euler_element_parity(p, kappa):
         Ue, Up, xe = O.gather(U, x, e)
         r = O.element(e, Ue, Up, xe, mu)
         assert rel(g["R"][e], r["R"]) < 1e-12
-        assert rel(g["JU"][e], r["JU"]) < 1e-12
-        assert rel(g["JUp"][e], r["JUp"]) < 1e-12
-        assert rel(g["Jx"][e], r["Jx"]) < 1e-12
+        # Jacobian blocks against the element's Jacobian scale: a block can be pure
+        # rounding noise (a supersonic outflow face does not depend on the exterior state)
+        scale = jac_scale(r)
+        for key in ("JU", "JUp", "Jx"):
+            assert np.abs(g[key][e] - r[key]).max() <= 1e-12 * scale, key
         assert abs(g["N"][e] - r["N"]) <= 1e-12 * max(abs(r["N"]), 1e-12)
         if kappa:
             assert rel(g["dN"][e], r["dN"]) < 1e-10
@@ -75,8 +81,9 @@ def test_burgers_element_parity(p):
     for e in range(7):
         Ue, Up, xe = O.gather(U, x, e)
         r = O.element(e, Ue, Up, xe, mu)
-        for key in ("R", "JU", "JUp", "Jx"):
-            assert rel(g[key][e], r[key]) < 1e-12, key
+        assert rel(g["R"][e], r["R"]) < 1e-12
+        for key in ("JU", "JUp", "Jx"):
+            assert np.abs(g[key][e] - r[key]).max() <= 1e-12 * jac_scale(r), key
 
 
 def test_fp32_element_accuracy():
@@ -95,8 +102,9 @@ def test_fp32_element_accuracy():
         Ue, Up, xe = O.gather(U, x, e)
         r = O.element(e, Ue, Up, xe, mu)
         for key in worst:
-            # residuals are differences of O(1) fluxes: measure against the flux scale
-            scale = np.abs(r["JU"]).max() * np.abs(Ue).max() if key == "R" else np.abs(r[key]).max()
+            # residuals are differences of O(1) fluxes: measure against the flux scale;
+            # Jacobian blocks against the element's Jacobian scale
+            scale = np.abs(r["JU"]).max() * np.abs(Ue).max() if key == "R" else jac_scale(r)
             worst[key] = max(worst[key], np.abs(g[key][e] - r[key]).max() / scale)
     assert all(v < 1e-5 for v in worst.values()), worst
 
@@ -234,16 +242,17 @@ def test_euler_small_solve_dense():
 
 
 def test_euler_small_solve_sparse_rho():
-    wl = W.euler_workload(n=12, p=2, k_u=8, k_x=4, seed=6)
-    rs = W.eq_weight_sets(wl, 1, seed=7, lo=40, hi=80)[0]
+    wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=6)
+    rs = W.eq_weight_sets(wl, 1, seed=7, lo=96, hi=150)[0]
     _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs))
 
 
 def test_given_start_and_repeat_solves():
-    wl = W.burgers_workload(n_elems=60)
+    wl = W.burgers_workload()
     ctx = ift.Context.from_workload(wl, tol=1e-10)
     mu = wl.mus[0]
     a = ctx.solve_rom(mu)
+    assert a["status"] == 0
     b = ctx.solve_rom(mu)
     np.testing.assert_array_equal(a["w"], b["w"])
     warm = ift.Context.from_workload(wl, tol=1e-10, lm_init=ift.INIT_GIVEN)
