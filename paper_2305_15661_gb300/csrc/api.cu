@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -755,7 +756,28 @@ ift_status build_graph(ift_ctx* c) {
   return IFT_OK;
 }
 
+// Host-driven loop over the same body (no graph): used when IFT_SOLVE_NO_GRAPH is set,
+// e.g. so that a profiler that does not enter conditional graph nodes sees every launch.
+// Bodies are enqueued in groups of 8; after a group the done flag is read back.
+ift_status run_solve_loop(ift_ctx* c, cudaStream_t s) {
+  const LMConsts k = lm_consts(c);
+  const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
+  for (int b = 0; b <= k.body_limit; b += 8) {
+    for (int j = 0; j < 8; ++j) {
+      ift_status st = enqueue_body(c, s, 0ull, 0);
+      if (st != IFT_OK) return st;
+    }
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, done, sizeof(int), cudaMemcpyDeviceToHost, s), "read done flag");
+    CK(cudaStreamSynchronize(s), "solve loop");
+    if (h) return IFT_OK;
+  }
+  return IFT_OK;
+}
+
 ift_status run_solve(ift_ctx* c, cudaStream_t s) {
+  static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
+  if (no_graph) return run_solve_loop(c, s);
   if (c->graph_epoch != c->epoch || !c->graph_exec) {
     ift_status st = build_graph(c);
     if (st != IFT_OK) return st;
