@@ -163,6 +163,40 @@ ift_status ift_solve_rom(ift_ctx* ctx, const double* mu, double* y, double* z, i
 ift_status ift_solve_rom_dev(ift_ctx* ctx, const double* mu, double* y, double* z, ift_solve_info* info_host,
                              void* stream);
 
+/* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
+   cannot call cudaMalloc when they need the reduced system: code that is
+   capturing a stream into a CUDA graph, code that owns all device memory
+   through its own pool or arena, and latency-critical loops where an allocation
+   would synchronise the device. It has no counterpart in the paper: it computes
+   the same S~, T~, H, J~ (FP64) as the context-based call, without a context.
+
+   Every pointer is a caller-owned DEVICE pointer: X (n_verts x dim),
+   elem_verts (n_elems x (dim+1)), the face connectivity nbr / nbr_face
+   (n_elems x n_face: neighbour element and its local face, -1 on boundary
+   faces) and bc (n_elems x n_face: 0 interior, 1 far field (Euler) or inflow
+   u = 1 (Burgers, the face with outward normal -x), 2 outflow (Burgers)),
+   Phi (N_u x k_u), Psi (N_x x k_x), the weights (nnz pairs elem/rho, or
+   nnz = -1 for rho = 1 on every element), mu, y, z, and the outputs S, T, H, J
+   as in ift_reduced_residual_jacobian (any output may be NULL). stream: a
+   cudaStream_t or NULL for the default stream; the call is asynchronous.
+
+   The call allocates nothing: its scratch (reference tables, per-CTA partial
+   sums, the reduced result) lives in a 2 MiB array in the library's device
+   memory, held on every GPU that loads the library until the process exits.
+   Limits: k_u + k_x <= 64, p in 1..3. Larger sizes return IFT_ERR_ARG; bad
+   pointers or sizes return IFT_ERR_ARG, CUDA failures IFT_ERR_CUDA (no message
+   is stored: there is no context). The array is shared by all calls and keeps
+   the last call's contents; calls whose GPU work overlaps on one device (other
+   streams or host threads) race on it and must be serialised by the caller.
+   The first call on each device looks up the array's device address; make that
+   first call before any stream capture on that device. */
+ift_status ift_reduced_residual_jacobian_static(
+    int problem, int p, int64_t n_verts, const double* X, int64_t n_elems, const int32_t* elem_verts,
+    const int32_t* nbr, const int32_t* nbr_face, const int8_t* bc, const double* Phi, int k_u,
+    const double* Psi, int k_x, int64_t nnz, const int32_t* elems, const double* rho, const double* mu,
+    const double* y, const double* z, double gamma, double kappa, double eps_g, double* S, double* T,
+    double* H, double* J, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,7 +52,7 @@ _lib = None
 EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", "ift_create_error",
            "ift_reference_nodes", "ift_sizes", "ift_set_mesh", "ift_set_bases", "ift_set_eq_weights",
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
-           "ift_solve_rom", "ift_solve_rom_dev"]
+           "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -84,6 +84,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_element_eval": (i32, [vp, pd, pd, pd, i64, pi, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_dev": (i32, [vp, vp, vp, vp, P(SolveInfo), vp]),
+        "ift_reduced_residual_jacobian_static": (i32, [i32, i32, i64, vp, i64, vp, vp, vp, vp, vp, i32, vp, i32,
+                                                       i64, vp, vp, vp, vp, vp, dbl, dbl, dbl, vp, vp, vp, vp,
+                                                       vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -107,6 +110,22 @@ def _f64(a):
 
 def _tptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def reduced_residual_jacobian_static(problem, p, X, ev, nbr, nbr_face, bc, Phi, Psi, elems, rho, mu, y, z, S, T,
+                                     H, J, gamma=1.4, kappa=0.0, eps_g=1e-8, stream=None):
+    """The allocation-free assembly: every array argument is a caller-owned CUDA tensor
+    (X, Phi, Psi, rho, mu, y, z, S, T, H, J float64; ev, nbr, nbr_face, elems int32; bc int8).
+    elems = rho = None means rho = 1 on every element."""
+    lib = load()
+    nnz = -1 if elems is None else int(elems.numel())
+    st = lib.ift_reduced_residual_jacobian_static(
+        problem, p, int(X.shape[0]), _tptr(X), int(ev.shape[0]), _tptr(ev), _tptr(nbr), _tptr(nbr_face), _tptr(bc),
+        _tptr(Phi), int(Phi.shape[1]), _tptr(Psi) if Psi.shape[1] else None, int(Psi.shape[1]), nnz, _tptr(elems),
+        _tptr(rho), _tptr(mu), _tptr(y), _tptr(z) if Psi.shape[1] else None, gamma, kappa, eps_g, _tptr(S),
+        _tptr(T), _tptr(H), _tptr(J), ctypes.c_void_p(stream) if stream else None)
+    if st != IFT_OK:
+        raise IFTError(st, "ift_reduced_residual_jacobian_static failed")
 
 
 class Context:
