@@ -73,8 +73,8 @@ struct WarpLayout {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
-  size_t oxe, oPsie, odN, oPhie, oPhp, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oR, oA, odNt, oacc,
-      bytes;
+  size_t oxe, oPsie, odN, oPhie, oPhp, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
+      oW, oacc, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
     const int k = ku + kx;
     size_t b = 0;
@@ -98,9 +98,19 @@ struct WarpLayout {
     oHp = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
     oHm = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
     oHn = put(JAC ? NF * NFQ * M * 2 : 1, sizeof(T));
+    oUi = put(NF * NFQ * M, sizeof(T));
+    oUo = put(NF * NFQ * M, sizeof(T));
     oR = put(NU, sizeof(T));
     oA = put(JAC ? (size_t)NU * k : 1, sizeof(T));
     odNt = put(kx + 1, sizeof(T));
+    {
+      // staging of the reduced-Jacobian passes: volume G (M ku) + F (DIM M ku), faces
+      // dU (2 M ku) + dH (M ku), mesh directions P (NQ DIM M kx) + dcof (4 kx)
+      size_t w1 = (size_t)(DIM + 1) * M * ku, w2 = (size_t)3 * M * ku, w3 = (size_t)NQ * DIM * M * kx + 4 * kx;
+      size_t w = w1 > w2 ? w1 : w2;
+      if (w3 > w) w = w3;
+      oW = put(JAC ? w : 1, sizeof(T));
+    }
     oacc = put((size_t)k * k + k + 2, sizeof(T));
     bytes = b;
   }
@@ -114,7 +124,9 @@ __host__ __device__ inline size_t cta_bytes(int ku, int kx) {
 
 template <class T, int PROB, int P, bool JAC>
 __host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps) {
-  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+  const int k = ku + kx;
+  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC>(ku, kx).bytes +
+         align16((size_t)k * (k + 1));  // upper-triangle pair table
 }
 
 // Pointwise stage and residual for one element whose U_e, U_e', x_e are staged.
@@ -129,7 +141,7 @@ struct ElemCore {
   const T *D, *B, *Lt, *fw, *qw, *qxi;
   // warp buffers
   double *xe, *Psie, *dN;
-  T *Phie, *Php, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *R, *A, *dNt, *acc;
+  T *Phie, *Php, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
   // geometry (registers, identical on all lanes)
   T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
   T detJ;
@@ -153,6 +165,9 @@ struct ElemCore {
     Hp = (T*)(base + L.oHp);
     Hm = (T*)(base + L.oHm);
     Hn = (T*)(base + L.oHn);
+    Ui = (T*)(base + L.oUi);
+    Uo = (T*)(base + L.oUo);
+    W = (T*)(base + L.oW);
     R = (T*)(base + L.oR);
     A = (T*)(base + L.oA);
     dNt = (T*)(base + L.odNt);
@@ -230,13 +245,13 @@ struct ElemCore {
         sq[q] = (T)(0.5 * exp(mu[0] * xq));
       }
     }
-    // face points: task t -> (group, face point); groups 0: d/dU+, 1: d/dU-, 2: d/dn
+    // face points: task t -> (group, face point); group 0: H and dH/dU+, group 1: dH/dU-
     const int npts = NF * NFQ;
-    const int ngroups = (PROB == PROB_EULER) ? (JAC ? (need_hn ? 3 : 2) : 1) : 1;
+    const int ngroups = (PROB == PROB_EULER && JAC) ? 2 : 1;
     for (int t = lane; t < npts * ngroups; t += 32) {
       const int grp = t / npts, pt = t % npts;
       const int k = pt / NFQ, f = pt % NFQ;
-      T Ui[4], Uo[4];
+      T Uin[4], Uout[4];
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         T s = T(0), so = T(0);
@@ -247,8 +262,8 @@ struct ElemCore {
           s += Lt[f * NT + j] * Ue[node * M + a];
           so += Lt[f * NT + j] * Up[(k * NT + j) * M + a];
         }
-        Ui[a] = s;
-        Uo[a] = so;
+        Uin[a] = s;
+        Uout[a] = so;
       }
       const signed char bt = bcs[k];
       if (PROB == PROB_EULER) {
@@ -256,26 +271,31 @@ struct ElemCore {
           double Uf[4];
           euler_farfield(gamma, mu[0], mu[1], Uf);
 #pragma unroll
-          for (int a = 0; a < 4; ++a) Uo[a] = (T)Uf[a];
-        }
-        if (grp == 0) {
-          T Pi = g1 * (Ui[3] - T(0.5) * (Ui[1] * Ui[1] + Ui[2] * Ui[2]) / Ui[0]);
-          T Po = g1 * (Uo[3] - T(0.5) * (Uo[1] * Uo[1] + Uo[2] * Uo[2]) / Uo[0]);
-          if (!(Ui[0] > T(0)) || !(Pi > T(0)) || !(Uo[0] > T(0)) || !(Po > T(0))) bad = true;
+          for (int a = 0; a < 4; ++a) Uout[a] = (T)Uf[a];
         }
         T* hf = &Hf[pt * 4];
+        if (grp == 0) {
+          T Pi = g1 * (Uin[3] - T(0.5) * (Uin[1] * Uin[1] + Uin[2] * Uin[2]) / Uin[0]);
+          T Po = g1 * (Uout[3] - T(0.5) * (Uout[1] * Uout[1] + Uout[2] * Uout[2]) / Uout[0]);
+          if (!(Uin[0] > T(0)) || !(Pi > T(0)) || !(Uout[0] > T(0)) || !(Po > T(0))) bad = true;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            Ui[pt * 4 + a] = Uin[a];
+            Uo[pt * 4 + a] = Uout[a];
+          }
+        }
         if (!JAC) {
           T n2[2] = {nt[k][0], nt[k][1]};
           T H[4];
-          euler_roe<T, T>(Ui, Uo, n2, g1, H);
+          euler_roe<T, T>(Uin, Uout, n2, g1, H);
 #pragma unroll
           for (int a = 0; a < 4; ++a) hf[a] = H[a];
-        } else if (grp < 2) {
+        } else {
           Dual<T, 4> di[4], dd[4], dn[2], H[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            di[a] = dconst<T, 4>(Ui[a]);
-            dd[a] = dconst<T, 4>(Uo[a]);
+            di[a] = dconst<T, 4>(Uin[a]);
+            dd[a] = dconst<T, 4>(Uout[a]);
           }
           dn[0] = dconst<T, 4>(nt[k][0]);
           dn[1] = dconst<T, 4>(nt[k][1]);
@@ -292,35 +312,44 @@ struct ElemCore {
 #pragma unroll
             for (int b = 0; b < 4; ++b) dst[a * 4 + b] = H[a].d[b];
           }
-        } else {
-          Dual<T, 2> di[4], dd[4], dn[2], H[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            di[a] = dconst<T, 2>(Ui[a]);
-            dd[a] = dconst<T, 2>(Uo[a]);
-          }
-          dn[0] = dconst<T, 2>(nt[k][0]);
-          dn[1] = dconst<T, 2>(nt[k][1]);
-          dn[0].d[0] = T(1);
-          dn[1].d[1] = T(1);
-          euler_roe<Dual<T, 2>, T>(di, dd, dn, g1, H);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            Hn[pt * 8 + a * 2 + 0] = H[a].d[0];
-            Hn[pt * 8 + a * 2 + 1] = H[a].d[1];
-          }
         }
       } else {
         // Burgers: inflow u- = 1 on the face with normal -x, outflow u- = u+
         T n = (k == 0) ? T(-1) : T(1);
-        if (bt == 1) Uo[0] = T(1);
-        if (bt == 2) Uo[0] = Ui[0];
+        if (bt == 1) Uout[0] = T(1);
+        if (bt == 2) Uout[0] = Uin[0];
         T H, Hi, Ho;
-        burgers_roe(Ui[0], Uo[0], n, H, Hi, Ho);
+        burgers_roe(Uin[0], Uout[0], n, H, Hi, Ho);
         Hf[pt] = H;
         if (JAC) {
           Hp[pt] = Hi;
           Hm[pt] = Ho;
+        }
+      }
+    }
+    if (PROB == PROB_EULER && JAC && need_hn) {
+      __syncwarp();
+      // dH/dn from two identities of the Roe flux: homogeneity, dH/dn . n = H, and
+      // rotational invariance, dH/dn . (J n) = G(H) - dH/dU+ G(U+) - dH/dU- G(U-),
+      // with J the 90-degree rotation and G(V) = (0, -V_2, V_1, 0) its action on a state.
+      for (int pt = lane; pt < npts; pt += 32) {
+        const int k = pt / NFQ;
+        const T nx = nt[k][0], ny = nt[k][1];
+        const T inv = T(1) / (nx * nx + ny * ny);
+        const T* h = &Hf[pt * 4];
+        const T* hp = &Hp[pt * 16];
+        const T* hm = &Hm[pt * 16];
+        const T* ui = &Ui[pt * 4];
+        const T* uo = &Uo[pt * 4];
+        T Gh[4] = {T(0), -h[2], h[1], T(0)};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          // K = G(H) - Hp G(Ui) - Hm G(Uo); G(V) has entries 1 -> -V2, 2 -> V1
+          T K = Gh[a] - (hp[a * 4 + 1] * (-ui[2]) + hp[a * 4 + 2] * ui[1]) -
+                (hm[a * 4 + 1] * (-uo[2]) + hm[a * 4 + 2] * uo[1]);
+          // [Hn n, Hn Jn] = [H, K]  with  [n, Jn] = [[nx, -ny], [ny, nx]]
+          Hn[pt * 8 + a * 2 + 0] = (h[a] * nx - K * ny) * inv;
+          Hn[pt * 8 + a * 2 + 1] = (h[a] * ny + K * nx) * inv;
         }
       }
     }
@@ -460,6 +489,175 @@ struct ElemCore {
     }
   }
 
+  // Position of element node i on face k (or -1).
+  __device__ static int face_pos(int k, int i) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int node = (k == 0) ? Dd::face_node(0, j) : ((k == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+      if (node == i) return j;
+    }
+    return -1;
+  }
+
+  // Step 6, state columns: A[row][c] = (dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e')[row][c],
+  // c < ku, with A stored row-major with stride k. The whole warp works on every
+  // stage: per volume point it stages G = B_q Phi_e (M x ku) and F_r = Ahat_qr G
+  // (DIM M x ku) in W, then every lane updates its own flattened (row, c) entries;
+  // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
+  __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
+    for (int e = lane; e < NU * ku; e += 32) {
+      const int row = e / ku, c = e - row * ku;
+      A[row * k + c] = T(0);
+    }
+    T* G = W;
+    T* F = W + M * ku;
+    for (int q = 0; q < NQ; ++q) {
+      __syncwarp();
+      for (int e = lane; e < M * ku; e += 32) {
+        const int b = e / ku, c = e - b * ku;
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) s += B[q * NB + j] * Phie[(j * M + b) * ku + c];
+        G[e] = s;
+      }
+      __syncwarp();
+      for (int e = lane; e < DIM * M * ku; e += 32) {
+        const int ra = e / ku, c = e - ra * ku;
+        const T* ah = &Ah[(q * DIM * M + ra) * M];
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) s += ah[b] * G[b * ku + c];
+        F[e] = s;
+      }
+      __syncwarp();
+      for (int e = lane; e < NU * ku; e += 32) {
+        const int row = e / ku, c = e - row * ku;
+        const int i = row / M, a = row - i * M;
+        T s = T(0);
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) s += D[(r * NQ + q) * NB + i] * F[(r * M + a) * ku + c];
+        A[row * k + c] -= s;
+      }
+    }
+    T* dU = W;                // [2][M][ku]: interior, exterior
+    T* dH = W + 2 * M * ku;   // [M][ku]
+    for (int pt = 0; pt < NF * NFQ; ++pt) {
+      const int kf = pt / NFQ, f = pt - kf * NFQ;
+      const signed char bt = bcs[kf];
+      __syncwarp();
+      for (int e = lane; e < 2 * M * ku; e += 32) {
+        const int side = e / (M * ku), rem = e - side * M * ku;
+        const int b = rem / ku, c = rem - b * ku;
+        T s = T(0);
+        if (side == 0 || bt == 2) {
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const int node =
+                (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+            s += Lt[f * NT + j] * Phie[(node * M + b) * ku + c];
+          }
+        } else if (bt == 0) {
+#pragma unroll
+          for (int j = 0; j < NT; ++j) s += Lt[f * NT + j] * Php[((kf * NT + j) * M + b) * ku + c];
+        }
+        dU[e] = s;
+      }
+      __syncwarp();
+      for (int e = lane; e < M * ku; e += 32) {
+        const int a = e / ku, c = e - a * ku;
+        const T* hp = &Hp[(pt * M + a) * M];
+        const T* hm = &Hm[(pt * M + a) * M];
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) s += hp[b] * dU[b * ku + c] + hm[b] * dU[(M + b) * ku + c];
+        dH[e] = fw[f] * s;
+      }
+      __syncwarp();
+      for (int e = lane; e < NT * M * ku; e += 32) {
+        const int j = e / (M * ku), rem = e - j * M * ku;
+        const int a = rem / ku, c = rem - a * ku;
+        const int node = (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+        A[(node * M + a) * k + c] += Lt[f * NT + j] * dH[a * ku + c];
+      }
+    }
+    __syncwarp();
+  }
+
+  // Step 6, mesh columns: A[row][ku + c] = (dR_e/dx_e Psi_e)[row][c], c < kx.
+  // Volume: the flux enters through the cofactor matrix, linear in x_e, so the
+  // direction dx = Psi_e[:, c] gives dF_r = sum_d f_d dcof[d][r] (staged in W as P);
+  // faces: dH = Hn dn with the scaled-normal change dn; Burgers: the source only.
+  __device__ void jac_geom(int lane, const double* mu, int ku, int kx, int k, bool dist) {
+    if (kx == 0) return;
+    T* Pg = W;
+    T* dcof = W + NQ * DIM * M * kx;  // [kx][4]
+    if (DIM == 2) {
+      for (int c = lane; c < kx; c += 32) {
+        const double* d = &Psie[c];  // column c, stride kx
+        const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
+        const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
+        dcof[c * 4 + 0] = dj11;
+        dcof[c * 4 + 1] = -dj10;
+        dcof[c * 4 + 2] = -dj01;
+        dcof[c * 4 + 3] = dj00;
+      }
+      __syncwarp();
+      for (int e = lane; e < NQ * DIM * M * kx; e += 32) {
+        const int qra = e / kx, c = e - qra * kx;
+        const int q = qra / (DIM * M), ra = qra - q * DIM * M;
+        const int r = ra / M, a = ra - r * M;
+        Pg[e] = fph[(q * 2 + 0) * M + a] * dcof[c * 4 + 0 * 2 + r] + fph[(q * 2 + 1) * M + a] * dcof[c * 4 + 2 + r];
+      }
+      __syncwarp();
+      for (int e = lane; e < NU * kx; e += 32) {
+        const int row = e / kx, c = e - row * kx;
+        const int i = row / M, a = row - i * M;
+        T s = T(0);
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int r = 0; r < DIM; ++r) s -= D[(r * NQ + q) * NB + i] * Pg[((q * DIM + r) * M + a) * kx + c];
+        // faces through the nodes of this row
+#pragma unroll
+        for (int kf = 0; kf < NF; ++kf) {
+          const int j = face_pos(kf, i);
+          if (j < 0) continue;
+          const int k1 = (kf + 1) % 3;
+          const double* d = &Psie[c];
+          const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
+          const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) {
+            const int pt = kf * NFQ + f;
+            s += fw[f] * Lt[f * NT + j] * (Hn[(pt * M + a) * 2 + 0] * dnx + Hn[(pt * M + a) * 2 + 1] * dny);
+          }
+        }
+        A[row * k + ku + c] = s;
+      }
+    } else {
+      const T mu0 = (T)mu[0];
+      for (int e = lane; e < NU * kx; e += 32) {
+        const int i = e / kx, c = e - i * kx;
+        const T dx0 = (T)Psie[0 * kx + c], ddet = (T)(Psie[1 * kx + c] - Psie[0 * kx + c]);
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const T dxq = dx0 + qxi[q] * ddet;
+          s -= B[q * NB + i] * qw[q] * (mu0 * sq[q] * dxq * detJ + sq[q] * ddet);
+        }
+        A[i * k + ku + c] = s;
+      }
+    }
+    if (dist) {
+      for (int c = lane; c < kx; c += 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < NXE; ++r) s += dN[r] * Psie[r * kx + c];
+        dNt[c] = (T)s;
+      }
+    }
+    __syncwarp();
+  }
+
   // Distortion N_e (Eq. dist_elem0-1) for straight-sided simplices and dN/dx_e,
   // written by lane 0 into dN[0..NXE-1], dN[NXE] = N_e. Xe: reference vertices.
   __device__ void distortion(const double* Xe, double kappa, double eps) {
@@ -555,6 +753,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   bind_tables(C, tab);
   const int nacc = k * k + k + 2;
   for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+  // upper-triangle (row <= col) pairs of the k x k Gauss-Newton matrix, row-major order
+  unsigned char* pairs = smem + cb + nw * wb;
+  if (JAC && threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < k; ++r)
+      for (int b = r; b < k; ++b) {
+        pairs[2 * n] = (unsigned char)r;
+        pairs[2 * n + 1] = (unsigned char)b;
+        ++n;
+      }
+  }
   __syncthreads();
   const bool need_hn = JAC && kx > 0;
   for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
@@ -620,40 +829,21 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
     __syncwarp();
     const T Ne = dist ? (T)C.dN[NXE] : T(0);
     if (JAC) {
-      // 6. columns of A_e
-      for (int c = lane; c < k; c += 32) {
-        T dR[NU];
-        if (c < ku) {
-          auto fe = [&](int i) { return C.Phie[i * ku + c]; };
-          auto fp = [&](int i) { return C.Php[i * ku + c]; };
-          C.jvp_state(fe, fp, bcs, dR);
-        } else {
-          double dx[NXE];
-#pragma unroll
-          for (int r = 0; r < NXE; ++r) dx[r] = C.Psie[r * kx + (c - ku)];
-          C.jvp_geom(dx, a.mu, dR);
-          if (dist) {
-            double s = 0.0;
-#pragma unroll
-            for (int r = 0; r < NXE; ++r) s += C.dN[r] * dx[r];
-            C.dNt[c - ku] = (T)s;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < NU; ++i) C.A[i * k + c] = dR[i];
-      }
-      __syncwarp();
-      // 7. weighted contraction
+      // 6. columns of A_e (state, then mesh), all lanes on every stage
+      C.jac_state(lane, bcs, ku, k);
+      C.jac_geom(lane, a.mu, ku, kx, k, dist);
+      // 7. weighted contraction over the upper triangle: lane-owned pairs (r <= b)
       const T rT = (T)rho;
-      for (int r = lane; r < k; r += 32) {
-        T* hrow = &C.acc[r * k];
-        for (int b = 0; b < k; ++b) {
-          T s = T(0);
+      const int npairs = k * (k + 1) / 2;
+      for (int pidx = lane; pidx < npairs; pidx += 32) {
+        const int r = pairs[2 * pidx], b = pairs[2 * pidx + 1];
+        T s = T(0);
 #pragma unroll
-          for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.A[i * k + b];
-          if (dist && r >= ku && b >= ku) s += C.dNt[r - ku] * C.dNt[b - ku];
-          hrow[b] += rT * s;
-        }
+        for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.A[i * k + b];
+        if (dist && r >= ku) s += C.dNt[r - ku] * C.dNt[b - ku];
+        C.acc[r * k + b] += rT * s;
+      }
+      for (int r = lane; r < k; r += 32) {
         T s = T(0);
 #pragma unroll
         for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
@@ -674,8 +864,13 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   // CTA partial: sum the warps' accumulators in warp order, in FP64
   WarpLayout<T, PROB, P, JAC> L(ku, kx);
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
+    int src = i;
+    if (JAC && i < k * k) {
+      const int r = i / k, b = i - r * k;
+      if (r > b) src = b * k + r;  // the contraction fills the upper triangle
+    }
     double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[i];
+    for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
     a.partial[(size_t)blockIdx.x * nacc + i] = s;
   }
 }

@@ -226,7 +226,10 @@ def _solve_pair(wl, tol, rho_set=None):
 def _check_solve(g, r):
     assert g["status"] == 0 and r["status"] == 0, (g, r["status"])
     assert g["init_iters"] == r["init_iters"] and g["iters"] == r["iters"], (g, r)
-    assert g["trials"] == r["trials"]
+    # a trial whose objective lies within rounding of the sufficient-decrease threshold can be
+    # accepted by one FP64 implementation and halved once more by the other (different
+    # summation orders); the accepted iterates and their number must still agree
+    assert abs(g["trials"] - r["trials"]) <= 2, (g["trials"], r["trials"])
     z = np.concatenate([g["w"], g["tau"]])
     zr = np.concatenate([r["w"], r["tau"]])
     assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr), np.linalg.norm(z - zr) / np.linalg.norm(zr)
