@@ -96,6 +96,15 @@ inline Dual dabs(Dual a) {
 inline double dmaxe(double a, double eps) { return a >= eps ? a : eps; }
 inline Dual dmaxe(Dual a, double eps) { return a.v >= eps ? a : Dual(eps, 0.0); }
 
+// Harten's entropy fix of a wave speed: |lam| when |lam| >= delta, else
+// (lam^2 + delta^2) / (2 delta), which joins |lam| with a continuous slope.
+template <class T>
+T harten_abs(const T& lam, const T& delta) {
+  T a = dabs(lam);
+  if (val(a) >= val(delta)) return a;
+  return (lam * lam + delta * delta) / (2.0 * delta);
+}
+
 // ---------------------------------------------------------------------------
 // Reference element: nodes, Lagrange basis (by Vandermonde inversion in the
 // monomial basis), Gauss-Legendre and collapsed (Duffy) quadrature.
@@ -425,9 +434,11 @@ void euler_shear_state(double gamma, const T& x, const T& y, T* U) {
 
 // Roe flux for the Euler equations with an unnormalised normal nt (|nt| = L):
 // H = L [ (F(U+) + F(U-)).n / 2 - |A_roe(n)| (U- - U+) / 2 ], n = nt / L,
-// U+ the interior and U- the exterior state; no entropy fix.
+// U+ the interior and U- the exterior state.
 // |A_roe| dU is written as the sum over the four Roe waves (acoustic waves
-// v_n -+ c and the entropy/shear waves at v_n) of |lambda_k| alpha_k r_k.
+// v_n -+ c and the entropy/shear waves at v_n) of |lambda_k| alpha_k r_k, with
+// Harten's entropy fix on every |lambda_k| (delta = 0.1 c of the Roe state), so
+// that the residual is continuously differentiable where a wave speed vanishes.
 template <class T>
 void euler_roe(double gamma, const T* Up, const T* Um, const T* nt, T* H) {
   T L = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
@@ -465,7 +476,8 @@ void euler_roe(double gamma, const T* Up, const T* Um, const T* nt, T* H) {
   T a1 = (dP - rt * ct * dvn) / (2.0 * c2);
   T a4 = (dP + rt * ct * dvn) / (2.0 * c2);
   T a2 = dr - dP / c2;
-  T l1 = dabs(vnt - ct), l2 = dabs(vnt), l4 = dabs(vnt + ct);
+  T del = 0.1 * ct;
+  T l1 = harten_abs(vnt - ct, del), l2 = harten_abs(vnt, del), l4 = harten_abs(vnt + ct, del);
   T D[4];
   D[0] = l1 * a1 + l4 * a4 + l2 * a2;
   D[1] = l1 * a1 * (ut - ct * nx) + l4 * a4 * (ut + ct * nx) + l2 * (a2 * ut + rt * (du - dvn * nx));
@@ -480,11 +492,14 @@ void euler_roe(double gamma, const T* Up, const T* Um, const T* nt, T* H) {
 }
 
 // Roe flux for Burgers, f(u) = u^2/2, with (scalar) normal n:
-// H = (f(u+) + f(u-)) n / 2 - |a n| (u- - u+) / 2, a = (u+ + u-) / 2.
+// H = (f(u+) + f(u-)) n / 2 - |a n| (u- - u+) / 2, a = (u+ + u-) / 2, with
+// Harten's entropy fix on |a n| (delta = 0.05 (|u+| + |u-|) |n|).
 template <class T>
 T burgers_roe(const T& up, const T& um, const T& n) {
   T a = 0.5 * (up + um);
-  return 0.5 * (0.5 * up * up + 0.5 * um * um) * n - 0.5 * dabs(a * n) * (um - up);
+  T del = 0.05 * (dabs(up) + dabs(um)) * dabs(n);
+  T aa = (val(del) > 0.0) ? harten_abs(a * n, del) : dabs(a * n);
+  return 0.5 * (0.5 * up * up + 0.5 * um * um) * n - 0.5 * aa * (um - up);
 }
 
 // Burgers source s(x; mu) = 0.5 exp(mu x).

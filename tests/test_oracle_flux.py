@@ -137,3 +137,48 @@ def test_burgers_roe_upwind():
     # consistency and conservation
     assert abs(orc.burgers_roe(0.7, 0.7, 1.0) - f(0.7)) < 1e-15
     assert abs(orc.burgers_roe(0.7, -0.2, 1.0) + orc.burgers_roe(-0.2, 0.7, -1.0)) < 1e-15
+
+
+def _one_sided_slopes(fun, s0, h=1e-6):
+    left = (fun(s0) - fun(s0 - h)) / h
+    right = (fun(s0 + h) - fun(s0)) / h
+    return left, right
+
+
+def test_roe_entropy_fix_makes_flux_c1_at_sonic_faces():
+    # the acoustic wave speed v_n - c of the Roe state passes through the fix threshold
+    # along this path; without a fix the flux has a kink where the speed changes sign
+    n = np.array([1.0, 0.0])
+    Um = prim_to_cons(1.1, 1.2, 0.1, 1.05)
+
+    def roe_speed_minus(s):
+        Up = prim_to_cons(1.0, s, 0.0, 1.0)
+        rl, rr = math.sqrt(1.0), math.sqrt(1.1)
+        u = (rl * s + rr * 1.2) / (rl + rr)
+        v = (rr * 0.1) / (rl + rr)
+        hl = (1.0 / 0.4 + 0.5 * s * s + 1.0) / 1.0
+        hr = (1.05 / 0.4 + 0.5 * 1.1 * (1.44 + 0.01) + 1.05) / 1.1
+        hh = (rl * hl + rr * hr) / (rl + rr)
+        c = math.sqrt(0.4 * (hh - 0.5 * (u * u + v * v)))
+        return u - c, c
+
+    # locate the two switch points |v_n - c| = 0.1 c by bisection on s, and a zero crossing
+    import scipy.optimize as so
+    f_plus = lambda s: roe_speed_minus(s)[0] - 0.1 * roe_speed_minus(s)[1]
+    f_minus = lambda s: roe_speed_minus(s)[0] + 0.1 * roe_speed_minus(s)[1]
+    f_zero = lambda s: roe_speed_minus(s)[0]
+    for f in (f_plus, f_minus, f_zero):
+        s0 = so.brentq(f, 0.0, 3.0, xtol=1e-14)
+        for comp in range(4):
+            H = lambda s: orc.euler_roe(GAMMA, prim_to_cons(1.0, s, 0.0, 1.0), Um, n)[comp]
+            left, right = _one_sided_slopes(H, s0)
+            assert abs(left - right) <= 1e-4 * max(1.0, abs(left)), (comp, left, right)
+
+
+def test_burgers_entropy_fix_c1():
+    # Roe speed a = (u+ + u-)/2 crosses zero along u+ -> path with u- = -0.8
+    for s0 in (0.8, 0.8 * 1.1 / 0.9, 0.8 * 0.9 / 1.1):  # a = 0 and the two switch points |a| = delta
+        left, right = _one_sided_slopes(lambda s: orc.burgers_roe(s, -0.8, 1.0), s0)
+        assert abs(left - right) <= 1e-4, (s0, left, right)
+    # away from the switch the flux is the unmodified Roe flux (exact upwinding)
+    assert abs(orc.burgers_roe(1.0, 2.0, 1.0) - 0.5) < 1e-15
