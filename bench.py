@@ -348,6 +348,56 @@ def run_assembly(args):
     return 0
 
 
+def run_batched(args):
+    """256 parameter queries with uneven hyperreduced weight sets, solved in one graph."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+    from paper_2305_15661_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    ift.load()
+    B = 256
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
+    sets = W.eq_weight_sets(wl, B, seed=3)
+    stream = torch.cuda.Stream(device=dev)
+    prec = ift.FP64 if args.precision == "fp64" else ift.FP32
+    ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    ctx.set_eq_weights_batched(sets)
+    mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
+    y = torch.zeros((B, wl.ku), dtype=torch.float64, device=dev)
+    z = torch.zeros((B, wl.kx), dtype=torch.float64, device=dev)
+    st = torch.zeros(B, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    info = ctx.solve_rom_batched(wl.mus)
+    for _ in range(args.warmup):
+        ctx.solve_rom_batched_dev(mus, y, z, st, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_rom_batched_dev(mus, y, z, st, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    conv = int((st == 0).sum().item())
+    evals = sum(len(sets[q][0]) * (1 + info["info"][q]["trials"]) for q in range(B))
+    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    t = sum(ms) / 1e3
+    print(json.dumps({"mode": "batched", "precision": args.precision, "queries": B,
+                      "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
+                      "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
+                      "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
+                      "achieved_tflops": evals * fl * args.steps / t / 1e12,
+                      "mean_iters": float(np.mean([i["init_iters"] + i["iters"] for i in info["info"]]))}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,7 +405,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched"], default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly")
@@ -366,6 +416,8 @@ def main():
         return run_reference(args)
     if args.mode == "assembly":
         return run_assembly(args)
+    if args.mode == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -163,6 +163,33 @@ ift_status ift_solve_rom(ift_ctx* ctx, const double* mu, double* y, double* z, i
 ift_status ift_solve_rom_dev(ift_ctx* ctx, const double* mu, double* y, double* z, ift_solve_info* info_host,
                              void* stream);
 
+/* Many queries (Sec. 3.2.1 for each parameter value): query q has its own
+   sparse weight set, elements elem[offsets[q] .. offsets[q+1]) with weights rho
+   (offsets has B+1 entries, offsets[0] = 0, every query non-empty, elements
+   distinct within a query, rho > 0). Only the listed elements and their
+   neighbours' trace rows are read (the hyperreduced gather). Replaces an earlier
+   batched set; ift_set_bases clears it. */
+ift_status ift_set_eq_weights_batched(ift_ctx* ctx, int B, const int64_t* offsets, const int32_t* elem,
+                                      const double* rho);
+
+/* S~, T~, H, J~ of every query at its own point: mu (B x n_mu), y (B x k_u),
+   z (B x k_x) in; S (B x k_u), T (B x k_x), H (B x k x k), J (B) out (host).
+   IFT_ERR_NONPHYSICAL if any query is non-physical (its J is +inf). */
+ift_status ift_reduced_residual_jacobian_batched(ift_ctx* ctx, const double* mu, const double* y, const double* z,
+                                                 double* S, double* T, double* H, double* J);
+
+/* LM solves of all B queries in one CUDA graph: every loop body assembles all
+   unfinished queries in one launch, reduces per query, steps each query's LM
+   and tests whether any query is still running. Same iteration as
+   ift_solve_rom per query. y (B x k_u), z (B x k_x) out (and in with
+   IFT_INIT_GIVEN); info (B). Returns IFT_OK if every query converged, else the
+   first error, else the first warning (each query's status is in info). */
+ift_status ift_solve_rom_batched(ift_ctx* ctx, const double* mu, double* y, double* z, ift_solve_info* info);
+/* Device-pointer variant: mu, y, z and status (B int32, may be NULL) are device
+   pointers; asynchronous on stream (NULL: the context's stream). */
+ift_status ift_solve_rom_batched_dev(ift_ctx* ctx, const double* mu, double* y, double* z, int32_t* status,
+                                     void* stream);
+
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
    cannot call cudaMalloc when they need the reduced system: code that is
    capturing a stream into a CUDA graph, code that owns all device memory

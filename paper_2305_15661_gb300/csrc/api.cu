@@ -30,6 +30,15 @@ __global__ void reduce_partials_kernel(const double* partial, int nparts, int na
 __global__ void phit_u_partial_kernel(const double* Phi, long Nu, int ku, int m, int problem, double gamma,
                                       const double* mu, long chunk, double* part);
 __global__ void sum_columns_kernel(const double* part, int nparts, int ku, double* w);
+__global__ void lm_step_batched_kernel(LMState* states, const double* res, int nacc, LMConsts c);
+__global__ void batch_condition_kernel(const LMState* states, int B, int* active, unsigned long long cond_handle,
+                                       int use_cond);
+__global__ void reduce_chunks_kernel(const double* partial, const int* qchunk, int nacc, const LMState* states,
+                                     double* res);
+__global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, int m, int problem, double gamma,
+                                       const double* mu, int mustride, const double* colsum, const double* y0,
+                                       const double* z0, int phase);
+__global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum);
 }  // namespace ift
 
 using namespace ift;
@@ -37,6 +46,7 @@ using namespace ift;
 namespace {
 
 constexpr int kWarpsPerCta = 2;
+constexpr int kChunk = 32;  // elements per chunk of the batched path
 constexpr int kPhitBlocks = 256;
 thread_local std::string g_create_error;
 
@@ -99,6 +109,27 @@ struct ift_ctx {
   int plan_grid[2] = {0, 0};
   size_t plan_smem[2] = {0, 0};
   int plan_epoch = -1;
+  // batched queries (per-query weight sets split into chunks)
+  int B = 0;
+  int n_chunks = 0;
+  int* d_chunk_start = nullptr;
+  int* d_chunk_query = nullptr;
+  int* d_qchunk = nullptr;
+  int* d_belems = nullptr;
+  double* d_brho = nullptr;
+  double* d_bmu = nullptr;
+  double* d_bw = nullptr;
+  double* d_bres = nullptr;
+  double* d_bpartial = nullptr;
+  LMState* d_blm = nullptr;
+  int* d_active = nullptr;
+  double* d_colsum = nullptr;
+  int bplan_grid[2] = {0, 0};
+  size_t bplan_smem[2] = {0, 0};
+  int bplan_epoch = -1;
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bgraph_exec = nullptr;
+  int bgraph_epoch = -1;
   // solve graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -393,6 +424,20 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_partial);
   dfree(c->d_phit);
   dfree(c->d_lm);
+  if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
+  if (c->bgraph) cudaGraphDestroy(c->bgraph);
+  dfree(c->d_chunk_start);
+  dfree(c->d_chunk_query);
+  dfree(c->d_qchunk);
+  dfree(c->d_belems);
+  dfree(c->d_brho);
+  dfree(c->d_bmu);
+  dfree(c->d_bw);
+  dfree(c->d_bres);
+  dfree(c->d_bpartial);
+  dfree(c->d_blm);
+  dfree(c->d_active);
+  dfree(c->d_colsum);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return IFT_OK;
@@ -521,6 +566,11 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   const int nacc = c->nacc();
   CK(dalloc(c->d_res, nacc), "alloc result");
   CK(dalloc(c->d_partial, (size_t)c->max_parts * nacc), "alloc partials");
+  CK(dalloc(c->d_colsum, (size_t)4 * k_u), "alloc column sums");
+  phi_colsum_kernel<<<k_u, 256, 0, c->stream>>>(c->d_Phi, (long)N_u, k_u, c->m, c->d_colsum);
+  CK(cudaGetLastError(), "column sums");
+  CK(cudaStreamSynchronize(c->stream), "column sums");
+  c->B = 0;  // batched weight sets are sized for the bases: set them again
   c->have_bases = true;
   c->epoch++;
   return IFT_OK;
@@ -854,6 +904,331 @@ ift_status ift_solve_rom_dev(ift_ctx* c, const double* mu, double* y, double* z,
     fill_info(hs, info_host, c->ku, c->kx);
     return (ift_status)hs.status;
   }
+  return IFT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched queries: many parameter values, each with its own sparse weight set,
+// assembled by one launch over query chunks and solved by one graph.
+// ---------------------------------------------------------------------------
+namespace {
+
+ift_status plan_batched(ift_ctx* c) {
+  const KernelSet& ks = c->ksP;
+  const int block = 32 * kWarpsPerCta;
+  for (int j = 0; j < 2; ++j) {
+    const bool jac = j == 1;
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, kWarpsPerCta);
+    cudaError_t e = ks.prepare_batched(jac, smem);
+    if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel attributes");
+    const int bps = ks.blocks_per_sm_batched(jac, block, smem);
+    if (bps < 1) return c->fail(IFT_ERR_CUDA, "batched kernel does not fit on an SM (%zu bytes shared)", smem);
+    long grid = (long)c->sm_count * bps;
+    const long need = (c->n_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->bplan_grid[j] = (int)grid;
+    c->bplan_smem[j] = smem;
+  }
+  c->bplan_epoch = c->epoch;
+  return IFT_OK;
+}
+
+// Batched element pass over all chunks of unfinished queries, then the per-query reduction.
+ift_status launch_batched(ift_ctx* c, bool jac, const double* w, long wstride, const int* done, long donestride,
+                          const LMState* states, cudaStream_t s) {
+  if (c->bplan_epoch != c->epoch) {
+    ift_status st = plan_batched(c);
+    if (st != IFT_OK) return st;
+  }
+  const KernelSet& ks = c->ksP;
+  const int block = 32 * kWarpsPerCta;
+  const int j = jac ? 1 : 0;
+  BatchArgs b;
+  b.chunk_start = c->d_chunk_start;
+  b.chunk_query = c->d_chunk_query;
+  b.n_chunks = c->n_chunks;
+  b.w = w;
+  b.wstride = wstride;
+  b.mu = c->d_bmu;
+  b.mustride = 2;
+  b.done = done;
+  b.donestride = donestride;
+  cudaError_t e;
+  if (c->cfg.precision == IFT_FP32) {
+    AsmArgs<float> a = make_args<float>(c, c->d_Phi32, w, w + c->ku, c->d_bmu, false, nullptr);
+    a.elems = c->d_belems;
+    a.rho = c->d_brho;
+    a.partial = c->d_bpartial;
+    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[j], block, c->bplan_smem[j], s);
+  } else {
+    AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, w + c->ku, c->d_bmu, false, nullptr);
+    a.elems = c->d_belems;
+    a.rho = c->d_brho;
+    a.partial = c->d_bpartial;
+    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[j], block, c->bplan_smem[j], s);
+  }
+  if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel launch");
+  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, c->nacc(), states, c->d_bres);
+  CK(cudaGetLastError(), "chunk reduction launch");
+  return IFT_OK;
+}
+
+ift_status enqueue_batched_body(ift_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+  const double* trial = (const double*)((char*)c->d_blm + offsetof(LMState, trial));
+  const int* done = (const int*)((char*)c->d_blm + offsetof(LMState, done));
+  ift_status st = launch_batched(c, true, trial, (long)(sizeof(LMState) / sizeof(double)), done,
+                                 (long)(sizeof(LMState) / sizeof(int)), c->d_blm, s);
+  if (st != IFT_OK) return st;
+  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), lm_consts(c));
+  batch_condition_kernel<<<1, 256, 0, s>>>(c->d_blm, c->B, c->d_active, handle, use_cond);
+  CK(cudaGetLastError(), "batched LM launch");
+  return IFT_OK;
+}
+
+ift_status build_batched_graph(ift_ctx* c) {
+  if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
+  if (c->bgraph) cudaGraphDestroy(c->bgraph);
+  c->bgraph_exec = nullptr;
+  c->bgraph = nullptr;
+  if (c->bplan_epoch != c->epoch) {
+    ift_status st = plan_batched(c);
+    if (st != IFT_OK) return st;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0), "graph create");
+  c->bgraph = g;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(pbuf, 0, sizeof(pbuf));
+  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = h;
+  p->conditional.type = cudaGraphCondTypeWhile;
+  p->conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, p), "while node");
+  cudaGraph_t body = p->conditional.phGraph_out[0];
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return c->cuda_fail(e, "begin capture");
+  }
+  ift_status st = enqueue_batched_body(c, cs, (unsigned long long)h, 1);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (st != IFT_OK) return st;
+  if (e != cudaSuccess) return c->cuda_fail(e, "end capture");
+  CK(cudaGraphInstantiate(&c->bgraph_exec, g, 0), "graph instantiate");
+  c->bgraph_epoch = c->epoch;
+  return IFT_OK;
+}
+
+ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
+  static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
+  if (no_graph) {
+    const LMConsts k = lm_consts(c);
+    for (int b = 0; b <= k.body_limit; b += 8) {
+      for (int j = 0; j < 8; ++j) {
+        ift_status st = enqueue_batched_body(c, s, 0ull, 0);
+        if (st != IFT_OK) return st;
+      }
+      int active = 0;
+      CK(cudaMemcpyAsync(&active, c->d_active, sizeof(int), cudaMemcpyDeviceToHost, s), "read active count");
+      CK(cudaStreamSynchronize(s), "batched solve loop");
+      if (!active) return IFT_OK;
+    }
+    return IFT_OK;
+  }
+  if (c->bgraph_epoch != c->epoch || !c->bgraph_exec) {
+    ift_status st = build_batched_graph(c);
+    if (st != IFT_OK) return st;
+  }
+  CK(cudaGraphLaunch(c->bgraph_exec, s), "batched graph launch");
+  return IFT_OK;
+}
+
+ift_status check_batched(ift_ctx* c) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (c->B < 1) return c->fail(IFT_ERR_STATE, "ift_set_eq_weights_batched must come first");
+  return IFT_OK;
+}
+
+// mu rows of the host (B x n_mu) packed as B x 2 on the device
+ift_status upload_mu_rows(ift_ctx* c, const double* mu, cudaStream_t s) {
+  const int nmu = (c->dim == 1) ? 1 : 2;
+  std::vector<double> m2((size_t)c->B * 2, 0.0);
+  for (int q = 0; q < c->B; ++q)
+    for (int i = 0; i < nmu; ++i) m2[(size_t)q * 2 + i] = mu[(size_t)q * nmu + i];
+  CK(cudaMemcpyAsync(c->d_bmu, m2.data(), m2.size() * 8, cudaMemcpyHostToDevice, s), "copy mu");
+  CK(cudaStreamSynchronize(s), "copy mu");
+  return IFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ift_status ift_set_eq_weights_batched(ift_ctx* c, int B, const int64_t* offsets, const int32_t* elem,
+                                      const double* rho) {
+  if (!c) return IFT_ERR_ARG;
+  if (!c->have_mesh || !c->have_bases) return c->fail(IFT_ERR_STATE, "set_mesh and set_bases must come first");
+  if (B < 1 || !offsets || !elem || !rho) return c->fail(IFT_ERR_ARG, "need B >= 1 and non-null arrays");
+  if (offsets[0] != 0) return c->fail(IFT_ERR_ARG, "offsets[0] must be 0");
+  for (int q = 0; q < B; ++q)
+    if (offsets[q + 1] <= offsets[q]) return c->fail(IFT_ERR_ARG, "query %d has no elements", q);
+  const int64_t total = offsets[B];
+  if (total > ((int64_t)1 << 31) - 1) return c->fail(IFT_ERR_ARG, "too many weight entries");
+  std::vector<int> stamp(c->n_elems, -1);
+  for (int q = 0; q < B; ++q)
+    for (int64_t i = offsets[q]; i < offsets[q + 1]; ++i) {
+      if (elem[i] < 0 || elem[i] >= c->n_elems) return c->fail(IFT_ERR_ARG, "weight element out of range");
+      if (stamp[elem[i]] == q) return c->fail(IFT_ERR_ARG, "element %d listed twice in query %d", elem[i], q);
+      stamp[elem[i]] = q;
+      if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return c->fail(IFT_ERR_ARG, "weights must be positive and finite");
+    }
+  std::vector<int> cstart, cquery, qchunk(B + 1);
+  for (int q = 0; q < B; ++q) {
+    qchunk[q] = (int)cquery.size();
+    for (int64_t i = offsets[q]; i < offsets[q + 1]; i += kChunk) {
+      cstart.push_back((int)i);
+      cquery.push_back(q);
+    }
+  }
+  qchunk[B] = (int)cquery.size();
+  cstart.push_back((int)total);
+  const int nchunks = (int)cquery.size();
+  const int nacc = c->nacc(), k = c->ku + c->kx;
+  drop_graph(c);
+  c->B = 0;
+  CK(dalloc(c->d_chunk_start, cstart.size()), "alloc chunks");
+  CK(dalloc(c->d_chunk_query, cquery.size()), "alloc chunks");
+  CK(dalloc(c->d_qchunk, qchunk.size()), "alloc chunks");
+  CK(dalloc(c->d_belems, (size_t)total), "alloc batched weights");
+  CK(dalloc(c->d_brho, (size_t)total), "alloc batched weights");
+  CK(dalloc(c->d_bmu, (size_t)B * 2), "alloc mu");
+  CK(dalloc(c->d_bw, (size_t)B * k), "alloc points");
+  CK(dalloc(c->d_bres, (size_t)B * nacc), "alloc results");
+  CK(dalloc(c->d_bpartial, (size_t)nchunks * nacc), "alloc chunk partials");
+  CK(dalloc(c->d_blm, (size_t)B), "alloc solver states");
+  CK(dalloc(c->d_active, 1), "alloc active count");
+  CK(cudaMemcpy(c->d_chunk_start, cstart.data(), cstart.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  CK(cudaMemcpy(c->d_chunk_query, cquery.data(), cquery.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  CK(cudaMemcpy(c->d_qchunk, qchunk.data(), qchunk.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  CK(cudaMemcpy(c->d_belems, elem, (size_t)total * 4, cudaMemcpyHostToDevice), "copy weights");
+  CK(cudaMemcpy(c->d_brho, rho, (size_t)total * 8, cudaMemcpyHostToDevice), "copy weights");
+  CK(cudaMemset(c->d_blm, 0, (size_t)B * sizeof(LMState)), "clear states");
+  c->B = B;
+  c->n_chunks = nchunks;
+  c->epoch++;
+  return IFT_OK;
+}
+
+ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, const double* y, const double* z,
+                                                 double* S, double* T, double* H, double* J) {
+  ift_status st = check_batched(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
+  const int B = c->B, ku = c->ku, kx = c->kx, k = ku + kx, nacc = c->nacc();
+  cudaStream_t s = c->stream;
+  std::vector<double> w((size_t)B * k);
+  for (int q = 0; q < B; ++q) {
+    for (int i = 0; i < ku; ++i) w[(size_t)q * k + i] = y[(size_t)q * ku + i];
+    for (int i = 0; i < kx; ++i) w[(size_t)q * k + ku + i] = z[(size_t)q * kx + i];
+  }
+  st = upload_mu_rows(c, mu, s);
+  if (st != IFT_OK) return st;
+  CK(cudaMemcpyAsync(c->d_bw, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s), "copy points");
+  st = launch_batched(c, true, c->d_bw, k, nullptr, 0, nullptr, s);
+  if (st != IFT_OK) return st;
+  std::vector<double> res((size_t)B * nacc);
+  CK(cudaMemcpyAsync(res.data(), c->d_bres, res.size() * 8, cudaMemcpyDeviceToHost, s), "copy results");
+  CK(cudaStreamSynchronize(s), "batched assembly");
+  bool bad = false;
+  for (int q = 0; q < B; ++q) {
+    const double* r = &res[(size_t)q * nacc];
+    if (H) std::memcpy(H + (size_t)q * k * k, r, (size_t)k * k * 8);
+    if (S) std::memcpy(S + (size_t)q * ku, r + k * k, ku * 8);
+    if (T && kx > 0) std::memcpy(T + (size_t)q * kx, r + k * k + ku, kx * 8);
+    const bool bq = r[k * k + k + 1] > 0.0;
+    if (J) J[q] = bq ? INFINITY : r[k * k + k];
+    bad = bad || bq;
+  }
+  if (bad) return c->fail(IFT_ERR_NONPHYSICAL, "some queries are non-physical at their points");
+  return IFT_OK;
+}
+
+ift_status ift_solve_rom_batched(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info) {
+  ift_status st = check_batched(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
+  const int B = c->B, ku = c->ku, kx = c->kx;
+  cudaStream_t s = c->stream;
+  st = upload_mu_rows(c, mu, s);
+  if (st != IFT_OK) return st;
+  const bool given = c->cfg.lm_init == IFT_INIT_GIVEN;
+  if (given) {
+    CK(cudaMemcpyAsync(c->d_bw, y, (size_t)B * ku * 8, cudaMemcpyHostToDevice, s), "copy y");
+    if (kx > 0) CK(cudaMemcpyAsync(c->d_bw + (size_t)B * ku, z, (size_t)B * kx * 8, cudaMemcpyHostToDevice, s), "copy z");
+  }
+  lm_init_batched_kernel<<<B, 64, 0, s>>>(c->d_blm, B, ku, kx, c->m, c->cfg.problem, c->cfg.gamma, c->d_bmu, 2,
+                                          c->d_colsum, c->d_bw, c->d_bw + (size_t)B * ku, given ? 1 : 0);
+  CK(cudaGetLastError(), "batched init");
+  st = run_batched_solve(c, s);
+  if (st != IFT_OK) return st;
+  std::vector<LMState> hs(B);
+  CK(cudaMemcpyAsync(hs.data(), c->d_blm, (size_t)B * sizeof(LMState), cudaMemcpyDeviceToHost, s), "copy states");
+  CK(cudaStreamSynchronize(s), "batched solve");
+  // overall status: OK if every query converged, else the first error, else the first warning
+  int first_err = IFT_OK, first_warn = IFT_OK;
+  for (int q = 0; q < B; ++q) {
+    for (int i = 0; i < ku; ++i) y[(size_t)q * ku + i] = hs[q].z[i];
+    for (int i = 0; i < kx; ++i) z[(size_t)q * kx + i] = hs[q].z[ku + i];
+    if (info) fill_info(hs[q], &info[q], ku, kx);
+    if (hs[q].status < 0 && first_err == IFT_OK) first_err = hs[q].status;
+    if (hs[q].status > 0 && first_warn == IFT_OK) first_warn = hs[q].status;
+  }
+  return (ift_status)(first_err != IFT_OK ? first_err : first_warn);
+}
+
+ift_status ift_solve_rom_batched_dev(ift_ctx* c, const double* mu, double* y, double* z, int32_t* status,
+                                     void* stream) {
+  ift_status st = check_batched(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
+  const int B = c->B, ku = c->ku, kx = c->kx;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  const int nmu = (c->dim == 1) ? 1 : 2;
+  CK(cudaMemcpy2DAsync(c->d_bmu, 2 * 8, mu, nmu * 8, nmu * 8, B, cudaMemcpyDeviceToDevice, s), "copy mu");
+  const bool given = c->cfg.lm_init == IFT_INIT_GIVEN;
+  if (given) {
+    CK(cudaMemcpyAsync(c->d_bw, y, (size_t)B * ku * 8, cudaMemcpyDeviceToDevice, s), "copy y");
+    if (kx > 0) CK(cudaMemcpyAsync(c->d_bw + (size_t)B * ku, z, (size_t)B * kx * 8, cudaMemcpyDeviceToDevice, s), "copy z");
+  }
+  lm_init_batched_kernel<<<B, 64, 0, s>>>(c->d_blm, B, ku, kx, c->m, c->cfg.problem, c->cfg.gamma, c->d_bmu, 2,
+                                          c->d_colsum, c->d_bw, c->d_bw + (size_t)B * ku, given ? 1 : 0);
+  CK(cudaGetLastError(), "batched init");
+  st = run_batched_solve(c, s);
+  if (st != IFT_OK) return st;
+  const size_t stride = sizeof(LMState);
+  const char* base = (const char*)c->d_blm;
+  CK(cudaMemcpy2DAsync(y, ku * 8, base + offsetof(LMState, z), stride, ku * 8, B, cudaMemcpyDeviceToDevice, s),
+     "copy y");
+  if (kx > 0)
+    CK(cudaMemcpy2DAsync(z, kx * 8, base + offsetof(LMState, z) + ku * 8, stride, kx * 8, B,
+                         cudaMemcpyDeviceToDevice, s),
+       "copy z");
+  if (status)
+    CK(cudaMemcpy2DAsync(status, sizeof(int), base + offsetof(LMState, status), stride, sizeof(int), B,
+                         cudaMemcpyDeviceToDevice, s),
+       "copy status");
   return IFT_OK;
 }
 

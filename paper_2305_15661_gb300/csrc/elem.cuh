@@ -74,7 +74,7 @@ struct WarpLayout {
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
   size_t oxe, oPsie, odN, oPhie, oPhp, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
-      oW, oacc, bytes;
+      oW, owq, otq, oacc, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
     const int k = ku + kx;
     size_t b = 0;
@@ -111,6 +111,8 @@ struct WarpLayout {
       if (w3 > w) w = w3;
       oW = put(JAC ? w : 1, sizeof(T));
     }
+    owq = put(ku > 0 ? ku : 1, sizeof(T));
+    otq = put(kx > 0 ? kx : 1, 8);
     oacc = put((size_t)k * k + k + 2, sizeof(T));
     bytes = b;
   }
@@ -732,43 +734,17 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
   C.qxi = C.qw + TB::nqw;
 }
 
-// The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false).
+// One element of the pass: steps 1-7 for element e with weight rho at the state
+// (wT, tauD) and parameters mu; accumulates into the warp's C.acc.
 template <class T, int PROB, int P, bool JAC>
-__global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
+__device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
+                                             const T* wT, const double* tauD, const double* mu,
+                                             const unsigned char* pairs, int lane) {
   using Dd = Disc<PROB, P>;
-  using Core = ElemCore<T, PROB, P, JAC>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (a.skip != nullptr && *(volatile const int*)a.skip) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ku = a.ku, kx = a.kx, k = ku + kx;
-  T *tab, *wT;
-  double* tauD;
-  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
-  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
-  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
-  Core C;
-  C.carve(smem + cb + warp * wb, ku, kx);
-  bind_tables(C, tab);
-  const int nacc = k * k + k + 2;
-  for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
-  // upper-triangle (row <= col) pairs of the k x k Gauss-Newton matrix, row-major order
-  unsigned char* pairs = smem + cb + nw * wb;
-  if (JAC && threadIdx.x == 0) {
-    int n = 0;
-    for (int r = 0; r < k; ++r)
-      for (int b = r; b < k; ++b) {
-        pairs[2 * n] = (unsigned char)r;
-        pairs[2 * n + 1] = (unsigned char)b;
-        ++n;
-      }
-  }
-  __syncthreads();
   const bool need_hn = JAC && kx > 0;
-  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
-    const int e = a.elems ? a.elems[it] : (int)it;
-    const double rho = a.rho ? a.rho[it] : 1.0;
     const int* vv = &a.ev[(long)e * NV];
     // 1. gather
     const T* phe = a.Phi + (size_t)e * NU * ku;
@@ -816,7 +792,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
-    bad |= C.pointwise(lane, bcs, a.mu, a.gamma, need_hn);
+    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn);
     __syncwarp();
     bad |= C.residual(lane);
     // distortion
@@ -831,7 +807,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
     if (JAC) {
       // 6. columns of A_e (state, then mesh), all lanes on every stage
       C.jac_state(lane, bcs, ku, k);
-      C.jac_geom(lane, a.mu, ku, kx, k, dist);
+      C.jac_geom(lane, mu, ku, kx, k, dist);
       // 7. weighted contraction over the upper triangle: lane-owned pairs (r <= b)
       const T rT = (T)rho;
       const int npairs = k * (k + 1) / 2;
@@ -859,19 +835,119 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
       if (bad) C.acc[k * k + k + 1] += T(1);
     }
     __syncwarp();
+}
+
+// Upper-triangle (row <= col) pairs of the k x k Gauss-Newton matrix, row-major order.
+__device__ inline void build_pairs(unsigned char* pairs, int k) {
+  int n = 0;
+  for (int r = 0; r < k; ++r)
+    for (int b = r; b < k; ++b) {
+      pairs[2 * n] = (unsigned char)r;
+      pairs[2 * n + 1] = (unsigned char)b;
+      ++n;
+    }
+}
+
+// Accumulator entry i of the full [H | g | J | count] vector (H mirrored from its upper triangle).
+__device__ inline int acc_source(int i, int k, bool jac) {
+  if (jac && i < k * k) {
+    const int r = i / k, b = i - r * k;
+    if (r > b) return b * k + r;
+  }
+  return i;
+}
+
+// The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false)
+// for one query: a grid-stride loop of warps over the items; one FP64 partial per CTA.
+template <class T, int PROB, int P, bool JAC>
+__global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
+  using Core = ElemCore<T, PROB, P, JAC>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (a.skip != nullptr && *(volatile const int*)a.skip) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  T *tab, *wT;
+  double* tauD;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
+  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, ku, kx);
+  bind_tables(C, tab);
+  const int nacc = k * k + k + 2;
+  for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+  unsigned char* pairs = smem + cb + nw * wb;
+  if (JAC && threadIdx.x == 0) build_pairs(pairs, k);
+  __syncthreads();
+  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
+    const int e = a.elems ? a.elems[it] : (int)it;
+    const double rho = a.rho ? a.rho[it] : 1.0;
+    element_pass<T, PROB, P, JAC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
   }
   __syncthreads();
   // CTA partial: sum the warps' accumulators in warp order, in FP64
   WarpLayout<T, PROB, P, JAC> L(ku, kx);
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
-    int src = i;
-    if (JAC && i < k * k) {
-      const int r = i / k, b = i - r * k;
-      if (r > b) src = b * k + r;  // the contraction fills the upper triangle
-    }
+    const int src = acc_source(i, k, JAC);
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
     a.partial[(size_t)blockIdx.x * nacc + i] = s;
+  }
+}
+
+// Many queries at once (the batched hyperreduced path): every query has its own
+// element list, weights, evaluation point and parameters. The items of query q
+// are split into chunks of at most a few dozen elements; one warp evaluates one
+// chunk and writes one FP64 partial row for it. Chunks of finished queries are
+// skipped.
+struct BatchArgs {
+  const int* chunk_start;  // n_chunks + 1 offsets into the item arrays (elems, rho)
+  const int* chunk_query;  // query of each chunk
+  int n_chunks;
+  const double* w;         // evaluation point of query q at w + q * wstride (tau follows at + ku)
+  long wstride;
+  const double* mu;        // parameters of query q at mu + q * mustride
+  int mustride;
+  const int* done;         // finished flag of query q at done + q * donestride (may be null)
+  long donestride;
+};
+
+template <class T, int PROB, int P, bool JAC>
+__global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
+  using Core = ElemCore<T, PROB, P, JAC>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  T *tab, *wT_unused;
+  double* tau_unused;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT_unused, tau_unused);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
+  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+  WarpLayout<T, PROB, P, JAC> L(ku, kx);
+  unsigned char* wbase = smem + cb + warp * wb;
+  Core C;
+  C.carve(wbase, ku, kx);
+  bind_tables(C, tab);
+  T* wq = (T*)(wbase + L.owq);
+  double* tq = (double*)(wbase + L.otq);
+  const int nacc = k * k + k + 2;
+  unsigned char* pairs = smem + cb + nw * wb;
+  if (JAC && threadIdx.x == 0) build_pairs(pairs, k);
+  __syncthreads();
+  for (int ch = blockIdx.x * nw + warp; ch < b.n_chunks; ch += gridDim.x * nw) {
+    const int q = b.chunk_query[ch];
+    if (b.done != nullptr && *(volatile const int*)(b.done + (long)q * b.donestride)) continue;
+    const double* wsrc = b.w + (long)q * b.wstride;
+    for (int i = lane; i < ku; i += 32) wq[i] = (T)wsrc[i];
+    for (int i = lane; i < kx; i += 32) tq[i] = wsrc[ku + i];
+    for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+    __syncwarp();
+    const double* muq = b.mu + (long)q * b.mustride;
+    for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it)
+      element_pass<T, PROB, P, JAC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+    __syncwarp();
+    for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k, JAC)];
+    __syncwarp();
   }
 }
 

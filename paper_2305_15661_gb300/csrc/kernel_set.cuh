@@ -44,6 +44,30 @@ struct KernelSetImpl {
     inspect_kernel<T, PROB, P><<<grid, block, smem, s>>>(a, U, x, R, J, N, dN);
     return cudaGetLastError();
   }
+  static cudaError_t assemble_batched(const void* args, const void* bargs, bool jac, int grid, int block,
+                                      size_t smem, cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    const BatchArgs& b = *(const BatchArgs*)bargs;
+    if (jac)
+      assemble_batched_kernel<T, PROB, P, true><<<grid, block, smem, s>>>(a, b);
+    else
+      assemble_batched_kernel<T, PROB, P, false><<<grid, block, smem, s>>>(a, b);
+    return cudaGetLastError();
+  }
+  static cudaError_t prepare_batched(bool jac, size_t smem) {
+    return jac ? cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  static int blocks_per_sm_batched(bool jac, int block, size_t smem) {
+    int n = 0;
+    cudaError_t e = jac ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &n, assemble_batched_kernel<T, PROB, P, true>, block, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &n, assemble_batched_kernel<T, PROB, P, false>, block, smem);
+    return e == cudaSuccess ? n : 0;
+  }
   static KernelSet make() {
     KernelSet k;
     k.valid = true;
@@ -52,6 +76,9 @@ struct KernelSetImpl {
     k.prepare = &prepare;
     k.blocks_per_sm = &blocks_per_sm;
     k.inspect = &inspect;
+    k.assemble_batched = &assemble_batched;
+    k.prepare_batched = &prepare_batched;
+    k.blocks_per_sm_batched = &blocks_per_sm_batched;
     return k;
   }
 };

@@ -16,6 +16,11 @@ struct KernelSet {
   int (*blocks_per_sm)(bool jac, int block, size_t smem) = nullptr;
   cudaError_t (*inspect)(const void* args, const double* U, const double* x, double* R, double* J, double* N,
                          double* dN, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
+  // batched fused assembly over query chunks; bargs points to a BatchArgs
+  cudaError_t (*assemble_batched)(const void* args, const void* bargs, bool jac, int grid, int block, size_t smem,
+                                  cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_batched)(bool jac, size_t smem) = nullptr;
+  int (*blocks_per_sm_batched)(bool jac, int block, size_t smem) = nullptr;
 };
 
 // precision: 0 = FP64, 1 = FP32

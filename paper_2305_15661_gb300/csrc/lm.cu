@@ -85,13 +85,9 @@ __device__ bool decide(LMState& s, const LMConsts& c) {
   }
 }
 
-// One LM step, single warp. res = [H (k*k) | g (k) | J | nonphysical count] at s.trial.
-__global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
-                               int use_cond) {
-  __shared__ double Ms[LM_KMAX * LM_KMAX];
-  __shared__ double rhs[LM_KMAX];
-  const int lane = threadIdx.x;
-  LMState& s = *sp;
+// One LM step of one query by one warp. res = [H (k*k) | g (k) | J | nonphysical count]
+// at s.trial; Ms (LM_KMAX^2) and rhs (LM_KMAX) are the warp's shared buffers.
+__device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, double* Ms, double* rhs, int lane) {
   const int ku = c.ku, kx = c.kx, k = ku + kx;
   const double* Hr = res;
   const double* gr = res + k * k;
@@ -223,9 +219,61 @@ __global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsig
     need_solve = __shfl_sync(0xffffffffu, again, 0);
   }
   __syncwarp();
-  // inside the solve graph: keep looping while the solve is not finished
-  if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, s.done ? 0u : 1u);
 }
+
+// One LM step, single warp (the single-query solve).
+__global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
+                               int use_cond) {
+  __shared__ double Ms[LM_KMAX * LM_KMAX];
+  __shared__ double rhs[LM_KMAX];
+  const int lane = threadIdx.x;
+  lm_step_warp(*sp, res, c, Ms, rhs, lane);
+  // inside the solve graph: keep looping while the solve is not finished
+  if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, sp->done ? 0u : 1u);
+}
+
+// One LM step for each of B queries: block q (one warp) steps query q with its
+// reduced result res + q * nacc.
+__global__ void lm_step_batched_kernel(LMState* states, const double* res, int nacc, LMConsts c) {
+  __shared__ double Ms[LM_KMAX * LM_KMAX];
+  __shared__ double rhs[LM_KMAX];
+  const int q = blockIdx.x;
+  lm_step_warp(states[q], res + (size_t)q * nacc, c, Ms, rhs, threadIdx.x);
+}
+
+// Loop condition of the batched solve: keep looping while any query is unfinished.
+__global__ void batch_condition_kernel(const LMState* states, int B, int* active, unsigned long long cond_handle,
+                                       int use_cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int q = threadIdx.x; q < B; q += blockDim.x) mine += states[q].done ? 0 : 1;
+  if (mine) atomicAdd(&any, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *active = any;
+    if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, any ? 1u : 0u);
+  }
+}
+
+// Per-query sum of the chunk partials: res[q][i] = sum over the chunks of q (in order).
+__global__ void reduce_chunks_kernel(const double* partial, const int* qchunk, int nacc, const LMState* states,
+                                     double* res) {
+  const int q = blockIdx.x;
+  if (states != nullptr && states[q].done) return;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
+    double t = 0.0;
+    for (int ch = qchunk[q]; ch < qchunk[q + 1]; ++ch) t += partial[(size_t)ch * nacc + i];
+    res[(size_t)q * nacc + i] = t;
+  }
+}
+
+// Starting states of B queries: w0 = sum_a U_inf,a(mu_q) colsum[a][c] (= Phi^T U_guess(mu_q)),
+// tau0 = 0, phase 0 (paper) ; or the given (y, z) rows, phase 1.
+__global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, int m, int problem, double gamma,
+                                       const double* mu, int mustride, const double* colsum, const double* y0,
+                                       const double* z0, int phase);
 
 // Starting state: z = trial = (w0, tau0), phase 0 (paper initialisation) or 1 (given start).
 __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0, int ku, int kx, int phase) {
@@ -256,6 +304,66 @@ __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0
     s.g0 = 0.0;
     s.thresh = 0.0;
   }
+}
+
+__global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, int m, int problem, double gamma,
+                                       const double* mu, int mustride, const double* colsum, const double* y0,
+                                       const double* z0, int phase) {
+  const int q = blockIdx.x;
+  if (q >= B) return;
+  LMState& s = states[q];
+  const int k = ku + kx;
+  double Ug[4] = {1.0, 0.0, 0.0, 0.0};
+  if (phase == 0 && problem == 2) euler_farfield(gamma, mu[(size_t)q * mustride], mu[(size_t)q * mustride + 1], Ug);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double v;
+    if (phase == 0) {
+      v = 0.0;
+      if (i < ku)
+        for (int a = 0; a < m; ++a) v += Ug[a] * colsum[a * ku + i];
+    } else {
+      v = (i < ku) ? y0[(size_t)q * ku + i] : z0[(size_t)q * kx + (i - ku)];
+    }
+    s.z[i] = v;
+    s.trial[i] = v;
+    s.dz[i] = 0.0;
+    s.g[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    s.phase = phase;
+    s.state = 0;
+    s.status = IFT_NOT_CONVERGED;
+    s.init_status = IFT_OK;
+    s.iters[0] = s.iters[1] = 0;
+    s.trials = 0;
+    s.shifts = 0;
+    s.h = 0;
+    s.bodies = 0;
+    s.done = 0;
+    s.lam = kLam0;
+    s.alpha = 1.0;
+    s.J = 0.0;
+    s.slope = 0.0;
+    s.g0 = 0.0;
+    s.thresh = 0.0;
+  }
+}
+
+// colsum[a][c] = sum over the rows r of Phi with r mod m = a of Phi[r][c] (one block per column).
+__global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum) {
+  __shared__ double red[4][256];
+  const int c = blockIdx.x;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long r = threadIdx.x; r < Nu; r += blockDim.x) t[r % m] += Phi[r * ku + c];
+  for (int a = 0; a < 4; ++a) red[a][threadIdx.x] = t[a];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+      for (int a = 0; a < 4; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int a = 0; a < m; ++a) colsum[a * ku + c] = red[a][0];
 }
 
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {

@@ -83,11 +83,26 @@ __device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double dabs(double a) { return fabs(a); }
 __device__ __forceinline__ float dabs(float a) { return fabsf(a); }
 
+template <class T>
+__device__ __forceinline__ T value_of(T a) { return a; }
+template <class T, int N>
+__device__ __forceinline__ T value_of(const Dual<T, N>& a) { return a.v; }
+
+// Harten's entropy fix of a wave speed: |lam| when |lam| >= del, else
+// (lam^2 + del^2) / (2 del), which meets |lam| with a continuous slope.
+template <class S>
+__device__ __forceinline__ S harten_abs(const S& lam, const S& del) {
+  S a = dabs(lam);
+  if (value_of(a) >= value_of(del)) return a;
+  return (lam * lam + del * del) / (del + del);
+}
+
 // Roe flux H(U+, U-; nt) for the scaled normal nt (|nt| = face measure factor):
 // the average of the two normal fluxes minus half the Roe-matrix upwinding,
 // |A_roe| dU = sum over the acoustic, entropy and shear waves of
-// |eigenvalue| x strength x eigenvector, with Roe averages weighted by sqrt(rho).
-// No entropy fix. S is T or a Dual over T.
+// |eigenvalue| x strength x eigenvector, with Roe averages weighted by sqrt(rho),
+// and Harten's entropy fix (delta = 0.1 c of the Roe state) on every |eigenvalue|.
+// S is T or a Dual over T.
 template <class S, class T>
 __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const S nt[2], T g1, S H[4]) {
   const T half = T(0.5);
@@ -129,7 +144,8 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const S 
   S am = half * (dp - rcd) * ic2;  // eigenvalue vn - c
   S ap = half * (dp + rcd) * ic2;  // eigenvalue vn + c
   S ae = drho - dp * ic2;          // entropy wave, eigenvalue vn
-  S lm = dabs(vna - ca), lp = dabs(vna + ca), l0 = dabs(vna);
+  S del = T(0.1) * ca;
+  S lm = harten_abs(vna - ca, del), lp = harten_abs(vna + ca, del), l0 = harten_abs(vna, del);
   S wm = lm * am, wp = lp * ap, we = l0 * ae, ws = l0 * rhoa;
   S cnx = ca * nx, cny = ca * ny, cvn = ca * vna;
   S d0 = wm + wp + we;
@@ -161,19 +177,32 @@ __device__ __forceinline__ void euler_farfield(double gamma, double mach, double
 
 // ---------------------------------------------------------------------------
 // Burgers: f(u) = u^2/2, Roe speed a = (u+ + u-)/2, flux
-// H = (f(u+) + f(u-)) n / 2 - |a n| (u- - u+) / 2, and its two partial derivatives.
+// H = (f(u+) + f(u-)) n / 2 - |a n|_fix (u- - u+) / 2 with Harten's entropy fix
+// (delta = 0.05 (|u+| + |u-|) |n|), and its two partial derivatives.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void burgers_roe(T ui, T uo, T n, T& H, T& Hi, T& Ho) {
-  T an = T(0.5) * (ui + uo) * n;
-  T s = (an > T(0)) ? T(1) : ((an < T(0)) ? T(-1) : T(0));
-  T aa = fabs(an);
-  T jump = uo - ui;
+  const T an = T(0.5) * (ui + uo) * n;
+  const T sa = (an > T(0)) ? T(1) : ((an < T(0)) ? T(-1) : T(0));
+  const T an_n = T(0.5) * n;  // d(a n)/du for either side
+  const T del = T(0.05) * (fabs(ui) + fabs(uo)) * fabs(n);
+  T aa, daa_i, daa_o;
+  if (del > T(0) && fabs(an) < del) {
+    aa = (an * an + del * del) / (del + del);
+    const T d_an = an / del, d_del = T(0.5) - an * an / (T(2) * del * del);
+    const T si = (ui > T(0)) ? T(1) : ((ui < T(0)) ? T(-1) : T(0));
+    const T so = (uo > T(0)) ? T(1) : ((uo < T(0)) ? T(-1) : T(0));
+    daa_i = d_an * an_n + d_del * T(0.05) * si * fabs(n);
+    daa_o = d_an * an_n + d_del * T(0.05) * so * fabs(n);
+  } else {
+    aa = fabs(an);
+    daa_i = sa * an_n;
+    daa_o = sa * an_n;
+  }
+  const T jump = uo - ui;
   H = T(0.25) * (ui * ui + uo * uo) * n - T(0.5) * aa * jump;
-  // d|a n|/du = sign(a n) n / 2 for either side
-  T dabs_du = T(0.5) * s * n;
-  Hi = T(0.5) * ui * n - T(0.5) * dabs_du * jump + T(0.5) * aa;
-  Ho = T(0.5) * uo * n - T(0.5) * dabs_du * jump - T(0.5) * aa;
+  Hi = T(0.5) * ui * n - T(0.5) * daa_i * jump + T(0.5) * aa;
+  Ho = T(0.5) * uo * n - T(0.5) * daa_o * jump - T(0.5) * aa;
 }
 
 }  // namespace ift

@@ -52,7 +52,9 @@ _lib = None
 EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", "ift_create_error",
            "ift_reference_nodes", "ift_sizes", "ift_set_mesh", "ift_set_bases", "ift_set_eq_weights",
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
-           "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static"]
+           "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
+           "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
+           "ift_solve_rom_batched_dev"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -84,6 +86,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_element_eval": (i32, [vp, pd, pd, pd, i64, pi, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_dev": (i32, [vp, vp, vp, vp, P(SolveInfo), vp]),
+        "ift_set_eq_weights_batched": (i32, [vp, i32, pl, pi, pd]),
+        "ift_reduced_residual_jacobian_batched": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
+        "ift_solve_rom_batched": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
+        "ift_solve_rom_batched_dev": (i32, [vp, vp, vp, vp, vp, vp]),
         "ift_reduced_residual_jacobian_static": (i32, [i32, i32, i64, vp, i64, vp, vp, vp, vp, vp, i32, vp, i32,
                                                        i64, vp, vp, vp, vp, vp, dbl, dbl, dbl, vp, vp, vp, vp,
                                                        vp]),
@@ -152,6 +158,7 @@ class Context:
         self.dim = 1 if problem == BURGERS1D else 2
         self.n_mu = 1 if problem == BURGERS1D else 2
         self.ku = self.kx = 0
+        self.B = 0
 
     def close(self):
         if getattr(self, "_h", None):
@@ -250,6 +257,46 @@ class Context:
         return {"status": int(st), "w": y, "tau": z[:self.kx], "init_iters": info.init_iters, "iters": info.iters,
                 "trials": info.trials, "shifts": info.shifts, "J": info.J, "normS": info.normS,
                 "normT": info.normT, "g0": info.g0}
+
+    # -- batched queries ---------------------------------------------------
+    def set_eq_weights_batched(self, sets):
+        """sets: list of (elems, rho) per query."""
+        offsets = np.zeros(len(sets) + 1, dtype=np.int64)
+        offsets[1:] = np.cumsum([len(e) for e, _ in sets])
+        elems = np.ascontiguousarray(np.concatenate([e for e, _ in sets]), dtype=np.int32)
+        rho = _f64(np.concatenate([r for _, r in sets]))
+        self.B = len(sets)
+        self._check(load().ift_set_eq_weights_batched(self._h, self.B, offsets.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int64)), _pi(elems), _pd(rho)))
+
+    def reduced_residual_jacobian_batched(self, mus, ys, zs):
+        B, k = self.B, self.ku + self.kx
+        S = np.zeros(B * self.ku)
+        T = np.zeros(max(B * self.kx, 1))
+        H = np.zeros(B * k * k)
+        J = np.zeros(B)
+        zz = _f64(zs) if self.kx else np.zeros(1)
+        st = load().ift_reduced_residual_jacobian_batched(self._h, _pd(_f64(mus)), _pd(_f64(ys)), _pd(zz), _pd(S),
+                                                          _pd(T), _pd(H), _pd(J))
+        if st not in (IFT_OK, -5):
+            self._check(st)
+        return {"S": S.reshape(B, self.ku), "T": T[:B * self.kx].reshape(B, self.kx), "H": H.reshape(B, k, k),
+                "J": J, "status": int(st)}
+
+    def solve_rom_batched(self, mus, y0=None, z0=None):
+        B = self.B
+        y = np.zeros(B * self.ku) if y0 is None else _f64(y0).ravel().copy()
+        z = np.zeros(max(B * self.kx, 1)) if z0 is None else np.concatenate([_f64(z0).ravel(), np.zeros(1)])
+        info = (SolveInfo * B)()
+        st = load().ift_solve_rom_batched(self._h, _pd(_f64(mus)), _pd(y), _pd(z), info)
+        self._check(st, allow_positive=True)
+        return {"status": int(st), "w": y.reshape(B, self.ku), "tau": z[:B * self.kx].reshape(B, self.kx),
+                "info": [{"status": i.status, "init_iters": i.init_iters, "iters": i.iters, "trials": i.trials,
+                          "J": i.J, "normS": i.normS, "normT": i.normT, "g0": i.g0} for i in info]}
+
+    def solve_rom_batched_dev(self, mus, y, z, status=None, stream=None):
+        self._check(load().ift_solve_rom_batched_dev(self._h, _tptr(mus), _tptr(y), _tptr(z), _tptr(status),
+                                                     ctypes.c_void_p(stream) if stream else None))
 
     def solve_rom_dev(self, mu, y, z, stream=None, want_info=True):
         info = SolveInfo()
