@@ -244,7 +244,7 @@ def run_ours(args):
     assert out["status"] == 0
     e2e_value = world * e2e_steps / e2e_s
     h2d = 8 * len(wl.mus[0])
-    d2h = 2144  # solver state read back for y, z and the solve info (sizeof of the device state)
+    d2h = 2152  # solver state read back for y, z and the solve info (sizeof of the device state)
 
     # isolated assembly timing (device pointers), for the per-launch duration
     S = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
@@ -361,7 +361,7 @@ def run_batched(args):
     wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
     sets = W.eq_weight_sets(wl, B, seed=3)
     stream = torch.cuda.Stream(device=dev)
-    prec = ift.FP64 if args.precision == "fp64" else ift.FP32
+    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
     ctx.set_eq_weights_batched(sets)
     mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
@@ -393,7 +393,8 @@ def run_batched(args):
                       "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
                       "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
                       "achieved_tflops": evals * fl * args.steps / t / 1e12,
-                      "mean_iters": float(np.mean([i["init_iters"] + i["iters"] for i in info["info"]]))}))
+                      "mean_iters": float(np.mean([i["init_iters"] + i["iters"] + i["fp32_iters"] for i in info["info"]])),
+                      "mean_fp64_iters": float(np.mean([i["iters"] for i in info["info"]]))}))
     ctx.close()
     return 0
 
@@ -407,7 +408,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--mode", choices=["solve", "assembly", "batched"], default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -59,10 +59,14 @@ typedef enum {
 
 enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
 /* Arithmetic of the element evaluation and contraction. IFT_FP64: all FP64.
-   IFT_FP32: FP32 element kernels and contraction with FP32 accumulation of each
-   element's products, FP64 accumulation across elements. The LM normal
-   equations, line search and stopping test are FP64 in every mode. */
-enum { IFT_FP64 = 0, IFT_FP32 = 1 };
+   IFT_FP32: FP32 element kernels and contraction, FP32 sums within a warp's
+   elements, FP64 sums across warps and CTAs. IFT_MIXED: evaluation calls as
+   IFT_FP32; solves run the LM with FP32 assemblies to a relative optimality of
+   1e-6 (or tol if larger), or until a line search needs more than 8 halvings
+   (FP32 rounding in J~ ends the FP32 stage), then continue from that point with
+   FP64 assemblies to tol. The LM normal equations, line search and stopping test
+   are FP64 in every mode. */
+enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2 };
 /* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
    LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */
 enum { IFT_INIT_PAPER = 0, IFT_INIT_GIVEN = 1 };
@@ -70,7 +74,7 @@ enum { IFT_INIT_PAPER = 0, IFT_INIT_GIVEN = 1 };
 typedef struct {
   int problem;        /* IFT_BURGERS1D or IFT_EULER2D */
   int p;              /* DG degree: Burgers 1..3, Euler 1..3 */
-  int precision;      /* IFT_FP64 or IFT_FP32 */
+  int precision;      /* IFT_FP64, IFT_FP32 or IFT_MIXED */
   double gamma;       /* ratio of specific heats (Euler) */
   double kappa;       /* distortion weight kappa of Eq. dist_elem0 (>= 0) */
   double eps_g;       /* epsilon of Eq. dist_elem1 (the paper uses 1e-8) */
@@ -152,6 +156,8 @@ typedef struct {
   double J;            /* final objective */
   double normS, normT; /* final |S~|, |T~| */
   double g0;           /* |[S~;T~]| at the start of the joint iteration */
+  int fp32_iters;      /* mixed precision: joint-phase steps of the FP32 stage (iters counts the FP64 stage) */
+  int fp32_trials;     /* mixed precision: objective evaluations of the FP32 stage */
 } ift_solve_info;
 
 /* Levenberg-Marquardt solve of the hyperreduced problem (Sec. 3.2.3):

@@ -7,6 +7,7 @@
 // step kernel sets the loop condition, so a whole solve is one graph launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,6 +40,7 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
                                        const double* mu, int mustride, const double* colsum, const double* y0,
                                        const double* z0, int phase);
 __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum);
+__global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
 }  // namespace ift
 
 using namespace ift;
@@ -75,7 +77,7 @@ struct ift_ctx {
   std::string err;
   RefTables T;
   int dim = 1, m = 1, nv = 2, nb = 0, nu = 0, nup = 0, nxe = 0, nface = 0, ntrace = 0, nq = 0, nfq = 0;
-  KernelSet ks64, ksP;
+  KernelSet ks[2];  // element kernels: [0] FP64, [1] FP32 (FP32 and mixed contexts)
   int sm_count = 0;
   double* d_tables = nullptr;
   // mesh
@@ -105,10 +107,10 @@ struct ift_ctx {
   int max_parts = 0;
   double* d_phit = nullptr;     // kPhitBlocks * LM_KMAX
   LMState* d_lm = nullptr;
-  // launch plan of the element kernels, index 0: objective only, 1: fused assembly
-  int plan_grid[2] = {0, 0};
-  size_t plan_smem[2] = {0, 0};
-  int plan_epoch = -1;
+  // launch plans of the element kernels, [working precision][0: objective only, 1: fused assembly]
+  int plan_grid[2][2] = {{0, 0}, {0, 0}};
+  size_t plan_smem[2][2] = {{0, 0}, {0, 0}};
+  int plan_epoch[2] = {-1, -1};
   // batched queries (per-query weight sets split into chunks)
   int B = 0;
   int n_chunks = 0;
@@ -124,16 +126,16 @@ struct ift_ctx {
   LMState* d_blm = nullptr;
   int* d_active = nullptr;
   double* d_colsum = nullptr;
-  int bplan_grid[2] = {0, 0};
-  size_t bplan_smem[2] = {0, 0};
-  int bplan_epoch = -1;
-  cudaGraph_t bgraph = nullptr;
-  cudaGraphExec_t bgraph_exec = nullptr;
-  int bgraph_epoch = -1;
-  // solve graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  int graph_epoch = -1;
+  int bplan_grid[2][2] = {{0, 0}, {0, 0}};
+  size_t bplan_smem[2][2] = {{0, 0}, {0, 0}};
+  int bplan_epoch[2] = {-1, -1};
+  cudaGraph_t bgraph[2] = {nullptr, nullptr};
+  cudaGraphExec_t bgraph_exec[2] = {nullptr, nullptr};
+  int bgraph_epoch[2] = {-1, -1};
+  // solve graphs, per working precision
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int graph_epoch[2] = {-1, -1};
   int epoch = 0;
   bool graph_failed = false;
 
@@ -150,6 +152,8 @@ struct ift_ctx {
     return fail(e == cudaErrorMemoryAllocation ? IFT_ERR_OOM : IFT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   }
   int nacc() const { return (ku + kx) * (ku + kx) + ku + kx + 2; }
+  // working precision of the evaluation calls: FP64 contexts 0, FP32 and mixed contexts 1
+  int eval_wp() const { return cfg.precision == IFT_FP64 ? 0 : 1; }
 };
 
 #define CK(call, what)                          \
@@ -173,11 +177,13 @@ cudaError_t dalloc(P*& p, size_t n) {
 }
 
 void drop_graph(ift_ctx* c) {
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
-  c->graph_exec = nullptr;
-  c->graph = nullptr;
-  c->graph_epoch = -1;
+  for (int wp = 0; wp < 2; ++wp) {
+    if (c->graph_exec[wp]) cudaGraphExecDestroy(c->graph_exec[wp]);
+    if (c->graph[wp]) cudaGraphDestroy(c->graph[wp]);
+    c->graph_exec[wp] = nullptr;
+    c->graph[wp] = nullptr;
+    c->graph_epoch[wp] = -1;
+  }
 }
 
 // Fill the kernel arguments for the configured precision (or FP64 if force64).
@@ -218,8 +224,8 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
 // Grid and shared memory of the element kernels for the current bases and
 // weights: as many CTAs as fit on the GPU at once, but no more than the items
 // need; the shape is fixed per configuration, so sums are reproducible.
-ift_status plan_launch(ift_ctx* c) {
-  const KernelSet& ks = c->ksP;
+ift_status plan_launch(ift_ctx* c, int wp) {
+  const KernelSet& ks = c->ks[wp];
   const int block = 32 * kWarpsPerCta;
   const long items = (c->nnz < 0) ? c->n_elems : c->nnz;
   for (int j = 0; j < 2; ++j) {
@@ -234,33 +240,33 @@ ift_status plan_launch(ift_ctx* c) {
     if (grid > need) grid = need;
     if (grid > c->max_parts) grid = c->max_parts;
     if (grid < 1) grid = 1;
-    c->plan_grid[j] = (int)grid;
-    c->plan_smem[j] = smem;
+    c->plan_grid[wp][j] = (int)grid;
+    c->plan_smem[wp][j] = smem;
   }
   // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
   const size_t ismem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
-  if (ismem > c->plan_smem[1]) {
+  if (ismem > c->plan_smem[wp][1]) {
     cudaError_t e = ks.prepare(true, ismem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
   }
-  c->plan_epoch = c->epoch;
+  c->plan_epoch[wp] = c->epoch;
   return IFT_OK;
 }
 
-// Launch the element pass (jac: fused assembly, else objective only) and the
-// partial reduction into out. Uses the configured precision.
-ift_status launch_assemble(ift_ctx* c, bool jac, const double* w, const double* tau, const double* mu, double* out,
-                           const int* skip, cudaStream_t s) {
-  if (c->plan_epoch != c->epoch) {
-    ift_status st = plan_launch(c);
+// Launch the element pass (jac: fused assembly, else objective only) in working
+// precision wp and the partial reduction into out.
+ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const double* tau, const double* mu,
+                           double* out, const int* skip, cudaStream_t s) {
+  if (c->plan_epoch[wp] != c->epoch) {
+    ift_status st = plan_launch(c, wp);
     if (st != IFT_OK) return st;
   }
-  const KernelSet& ks = c->ksP;
+  const KernelSet& ks = c->ks[wp];
   const int block = 32 * kWarpsPerCta;
-  const int grid = c->plan_grid[jac ? 1 : 0];
-  const size_t smem = c->plan_smem[jac ? 1 : 0];
+  const int grid = c->plan_grid[wp][jac ? 1 : 0];
+  const size_t smem = c->plan_smem[wp][jac ? 1 : 0];
   cudaError_t e;
-  if (c->cfg.precision == IFT_FP32) {
+  if (wp == 1) {
     AsmArgs<float> a = make_args<float>(c, c->d_Phi32, w, tau, mu, false, skip);
     e = ks.assemble(&a, jac, grid, block, smem, s);
   } else {
@@ -316,8 +322,8 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     g_create_error = "degree p must be 1, 2 or 3";
     return IFT_ERR_ARG;
   }
-  if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32) {
-    g_create_error = "precision must be IFT_FP64 or IFT_FP32";
+  if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32 && cfg->precision != IFT_MIXED) {
+    g_create_error = "precision must be IFT_FP64, IFT_FP32 or IFT_MIXED";
     return IFT_ERR_ARG;
   }
   if (!(cfg->gamma > 1.0) || !(cfg->kappa >= 0.0) || !(cfg->eps_g > 0.0) || !(cfg->tol >= 0.0) ||
@@ -350,9 +356,9 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   c->nxe = c->nv * dim;
   c->nq = c->T.nq;
   c->nfq = c->T.nfq;
-  c->ks64 = (dim == 1) ? burgers_kernels(cfg->p, 0) : euler_kernels(cfg->p, 0);
-  c->ksP = (dim == 1) ? burgers_kernels(cfg->p, cfg->precision) : euler_kernels(cfg->p, cfg->precision);
-  if (!c->ks64.valid || !c->ksP.valid) {
+  c->ks[0] = (dim == 1) ? burgers_kernels(cfg->p, 0) : euler_kernels(cfg->p, 0);
+  if (cfg->precision != IFT_FP64) c->ks[1] = (dim == 1) ? burgers_kernels(cfg->p, 1) : euler_kernels(cfg->p, 1);
+  if (!c->ks[0].valid || (cfg->precision != IFT_FP64 && !c->ks[1].valid)) {
     delete c;
     g_create_error = "kernels for this problem/degree/precision are not built";
     return IFT_ERR_NOTIMPL;
@@ -424,8 +430,10 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_partial);
   dfree(c->d_phit);
   dfree(c->d_lm);
-  if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
-  if (c->bgraph) cudaGraphDestroy(c->bgraph);
+  for (int wp = 0; wp < 2; ++wp) {
+    if (c->bgraph_exec[wp]) cudaGraphExecDestroy(c->bgraph_exec[wp]);
+    if (c->bgraph[wp]) cudaGraphDestroy(c->bgraph[wp]);
+  }
   dfree(c->d_chunk_start);
   dfree(c->d_chunk_query);
   dfree(c->d_qchunk);
@@ -553,7 +561,7 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   c->have_bases = false;
   CK(dalloc(c->d_Phi, (size_t)N_u * k_u), "alloc Phi");
   CK(cudaMemcpy(c->d_Phi, Phi, (size_t)N_u * k_u * 8, cudaMemcpyHostToDevice), "copy Phi");
-  if (c->cfg.precision == IFT_FP32) {
+  if (c->cfg.precision != IFT_FP64) {
     std::vector<float> p32((size_t)N_u * k_u);
     for (size_t i = 0; i < p32.size(); ++i) p32[i] = (float)Phi[i];
     CK(dalloc(c->d_Phi32, p32.size()), "alloc Phi (FP32)");
@@ -608,7 +616,7 @@ ift_status ift_reduced_residual_jacobian_dev(ift_ctx* c, const double* mu, const
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
   cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-  st = launch_assemble(c, true, y, c->kx > 0 ? z : c->d_tau, mu, c->d_res, nullptr, s);
+  st = launch_assemble(c, c->eval_wp(), true, y, c->kx > 0 ? z : c->d_tau, mu, c->d_res, nullptr, s);
   if (st != IFT_OK) return st;
   const int nacc = c->nacc();
   unpack_kernel<<<(nacc + 255) / 256, 256, 0, s>>>(c->d_res, c->ku, c->kx, S, T, H, J);
@@ -625,7 +633,7 @@ ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const dou
   CK(cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s), "copy mu");
   CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice, s), "copy y");
   if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice, s), "copy z");
-  st = launch_assemble(c, true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
+  st = launch_assemble(c, c->eval_wp(), true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
   if (st != IFT_OK) return st;
   const int nacc = c->nacc(), k = c->ku + c->kx;
   std::vector<double> res(nacc);
@@ -674,13 +682,14 @@ ift_status ift_element_eval(ift_ctx* c, const double* mu, const double* U, const
   cudaMemcpyAsync(dx, x, Nx * 8, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(dl, elems, (size_t)n * 4, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s);
-  const KernelSet& ks = c->ksP;
+  const int wp = c->eval_wp();
+  const KernelSet& ks = c->ks[wp];
   const int block = 32 * kWarpsPerCta;
   const size_t smem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
-  e = ks.prepare(true, c->have_bases && c->plan_smem[1] > smem ? c->plan_smem[1] : smem);
+  e = ks.prepare(true, c->have_bases && c->plan_smem[wp][1] > smem ? c->plan_smem[wp][1] : smem);
   if (e == cudaSuccess) {
     const int grid = (int)((n + kWarpsPerCta - 1) / kWarpsPerCta);
-    if (c->cfg.precision == IFT_FP32) {
+    if (wp == 1) {
       AsmArgs<float> a = make_args<float>(c, c->d_Phi32, c->d_w, c->d_tau, c->d_mu, true, nullptr);
       a.ku = 1;
       a.kx = 0;
@@ -743,38 +752,52 @@ ift_status solve_prologue(ift_ctx* c, const double* d_mu, const double* d_y0, co
   return IFT_OK;
 }
 
-LMConsts lm_consts(ift_ctx* c) {
+// Stage 1 of a mixed-precision solve: FP32 iterations until this relative optimality,
+// or until FP32 rounding in J stalls the line search (after a few halvings), then
+// FP64 iterations finish from that point.
+constexpr double kMixedStage1Tol = 1e-6;
+constexpr int kMaxHalvings = 30, kMixedStage1Halvings = 8;
+
+LMConsts lm_consts(ift_ctx* c, double tol) {
   LMConsts k;
-  k.tol = c->cfg.tol;
+  k.tol = tol;
   k.max_iters = c->cfg.max_iters;
   k.ku = c->ku;
   k.kx = c->kx;
   k.body_limit = (2 * c->cfg.max_iters + 4) * 34;
+  k.max_halvings = kMaxHalvings;
+  return k;
+}
+
+// Tolerance of the LM run in working precision wp: the final tolerance, except for
+// the FP32 stage of a mixed-precision solve.
+double stage_tol(ift_ctx* c, int wp) {
+  return (c->cfg.precision == IFT_MIXED && wp == 1) ? std::max(c->cfg.tol, kMixedStage1Tol) : c->cfg.tol;
+}
+
+LMConsts stage_consts(ift_ctx* c, int wp) {
+  LMConsts k = lm_consts(c, stage_tol(c, wp));
+  if (c->cfg.precision == IFT_MIXED && wp == 1) k.max_halvings = kMixedStage1Halvings;
   return k;
 }
 
 // The loop body: assemble at the trial point, reduce, LM step.
-ift_status enqueue_body(ift_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+ift_status enqueue_body(ift_ctx* c, int wp, cudaStream_t s, unsigned long long handle, int use_cond) {
   double* trial = (double*)((char*)c->d_lm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
-  ift_status st = launch_assemble(c, true, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
+  ift_status st = launch_assemble(c, wp, true, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
   if (st != IFT_OK) return st;
-  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, lm_consts(c), handle, use_cond);
+  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, stage_consts(c, wp), handle, use_cond);
   CK(cudaGetLastError(), "LM step launch");
   return IFT_OK;
 }
 
-// Build (once per configuration) the solve graph: one while node whose body is
-// the loop body above, with the LM step kernel setting the loop condition.
-ift_status build_graph(ift_ctx* c) {
-  drop_graph(c);
-  if (c->plan_epoch != c->epoch) {
-    ift_status st = plan_launch(c);
-    if (st != IFT_OK) return st;
-  }
+// A while-loop graph whose body is produced by enqueue(stream, handle).
+template <class F>
+ift_status build_while_graph(ift_ctx* c, cudaGraph_t* out_graph, cudaGraphExec_t* out_exec, F enqueue) {
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0), "graph create");
-  c->graph = g;
+  *out_graph = g;
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
   // the parameter struct holds a union without a default constructor: build it in zeroed storage
@@ -795,26 +818,44 @@ ift_status build_graph(ift_ctx* c) {
     cudaStreamDestroy(cs);
     return c->cuda_fail(e, "begin capture");
   }
-  ift_status st = enqueue_body(c, cs, (unsigned long long)h, 1);
+  ift_status st = enqueue(cs, (unsigned long long)h);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
   if (st != IFT_OK) return st;
   if (e != cudaSuccess) return c->cuda_fail(e, "end capture");
-  CK(cudaGraphInstantiate(&c->graph_exec, g, 0), "graph instantiate");
-  c->graph_epoch = c->epoch;
+  CK(cudaGraphInstantiate(out_exec, g, 0), "graph instantiate");
+  return IFT_OK;
+}
+
+// Build (once per configuration) the solve graph of working precision wp: one while
+// node whose body is the loop body above, the LM step kernel setting the condition.
+ift_status build_graph(ift_ctx* c, int wp) {
+  if (c->graph_exec[wp]) cudaGraphExecDestroy(c->graph_exec[wp]);
+  if (c->graph[wp]) cudaGraphDestroy(c->graph[wp]);
+  c->graph_exec[wp] = nullptr;
+  c->graph[wp] = nullptr;
+  if (c->plan_epoch[wp] != c->epoch) {
+    ift_status st = plan_launch(c, wp);
+    if (st != IFT_OK) return st;
+  }
+  ift_status st = build_while_graph(c, &c->graph[wp], &c->graph_exec[wp], [&](cudaStream_t cs, unsigned long long h) {
+    return enqueue_body(c, wp, cs, h, 1);
+  });
+  if (st != IFT_OK) return st;
+  c->graph_epoch[wp] = c->epoch;
   return IFT_OK;
 }
 
 // Host-driven loop over the same body (no graph): used when IFT_SOLVE_NO_GRAPH is set,
 // e.g. so that a profiler that does not enter conditional graph nodes sees every launch.
 // Bodies are enqueued in groups of 8; after a group the done flag is read back.
-ift_status run_solve_loop(ift_ctx* c, cudaStream_t s) {
-  const LMConsts k = lm_consts(c);
+ift_status run_solve_loop(ift_ctx* c, int wp, cudaStream_t s) {
+  const LMConsts k = lm_consts(c, stage_tol(c, wp));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
   for (int b = 0; b <= k.body_limit; b += 8) {
     for (int j = 0; j < 8; ++j) {
-      ift_status st = enqueue_body(c, s, 0ull, 0);
+      ift_status st = enqueue_body(c, wp, s, 0ull, 0);
       if (st != IFT_OK) return st;
     }
     int h = 0;
@@ -825,15 +866,27 @@ ift_status run_solve_loop(ift_ctx* c, cudaStream_t s) {
   return IFT_OK;
 }
 
-ift_status run_solve(ift_ctx* c, cudaStream_t s) {
+ift_status run_stage(ift_ctx* c, int wp, cudaStream_t s) {
   static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
-  if (no_graph) return run_solve_loop(c, s);
-  if (c->graph_epoch != c->epoch || !c->graph_exec) {
-    ift_status st = build_graph(c);
+  if (no_graph) return run_solve_loop(c, wp, s);
+  if (c->graph_epoch[wp] != c->epoch || !c->graph_exec[wp]) {
+    ift_status st = build_graph(c, wp);
     if (st != IFT_OK) return st;
   }
-  CK(cudaGraphLaunch(c->graph_exec, s), "graph launch");
+  CK(cudaGraphLaunch(c->graph_exec[wp], s), "graph launch");
   return IFT_OK;
+}
+
+// The whole solve after the prologue: one stage in the context's precision, or for
+// mixed precision an FP32 stage to the stage-1 tolerance followed by an FP64 stage
+// restarted (joint phase) at the FP32 stage's final point.
+ift_status run_solve(ift_ctx* c, cudaStream_t s) {
+  if (c->cfg.precision == IFT_FP64) return run_stage(c, 0, s);
+  ift_status st = run_stage(c, 1, s);
+  if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
+  lm_restart_kernel<<<1, 64, 0, s>>>(c->d_lm, 1, c->ku, c->kx);
+  CK(cudaGetLastError(), "stage restart");
+  return run_stage(c, 0, s);
 }
 
 void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
@@ -850,6 +903,8 @@ void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
   info->normS = std::sqrt(ns);
   info->normT = std::sqrt(nt);
   info->g0 = st.g0;
+  info->fp32_iters = st.iters32;
+  info->fp32_trials = st.trials32;
 }
 
 }  // namespace
@@ -915,8 +970,8 @@ ift_status ift_solve_rom_dev(ift_ctx* c, const double* mu, double* y, double* z,
 // ---------------------------------------------------------------------------
 namespace {
 
-ift_status plan_batched(ift_ctx* c) {
-  const KernelSet& ks = c->ksP;
+ift_status plan_batched(ift_ctx* c, int wp) {
+  const KernelSet& ks = c->ks[wp];
   const int block = 32 * kWarpsPerCta;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
@@ -929,21 +984,21 @@ ift_status plan_batched(ift_ctx* c) {
     const long need = (c->n_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    c->bplan_grid[j] = (int)grid;
-    c->bplan_smem[j] = smem;
+    c->bplan_grid[wp][j] = (int)grid;
+    c->bplan_smem[wp][j] = smem;
   }
-  c->bplan_epoch = c->epoch;
+  c->bplan_epoch[wp] = c->epoch;
   return IFT_OK;
 }
 
 // Batched element pass over all chunks of unfinished queries, then the per-query reduction.
-ift_status launch_batched(ift_ctx* c, bool jac, const double* w, long wstride, const int* done, long donestride,
-                          const LMState* states, cudaStream_t s) {
-  if (c->bplan_epoch != c->epoch) {
-    ift_status st = plan_batched(c);
+ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long wstride, const int* done,
+                          long donestride, const LMState* states, cudaStream_t s) {
+  if (c->bplan_epoch[wp] != c->epoch) {
+    ift_status st = plan_batched(c, wp);
     if (st != IFT_OK) return st;
   }
-  const KernelSet& ks = c->ksP;
+  const KernelSet& ks = c->ks[wp];
   const int block = 32 * kWarpsPerCta;
   const int j = jac ? 1 : 0;
   BatchArgs b;
@@ -957,18 +1012,18 @@ ift_status launch_batched(ift_ctx* c, bool jac, const double* w, long wstride, c
   b.done = done;
   b.donestride = donestride;
   cudaError_t e;
-  if (c->cfg.precision == IFT_FP32) {
+  if (wp == 1) {
     AsmArgs<float> a = make_args<float>(c, c->d_Phi32, w, w + c->ku, c->d_bmu, false, nullptr);
     a.elems = c->d_belems;
     a.rho = c->d_brho;
     a.partial = c->d_bpartial;
-    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[j], block, c->bplan_smem[j], s);
+    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[wp][j], block, c->bplan_smem[wp][j], s);
   } else {
     AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, w + c->ku, c->d_bmu, false, nullptr);
     a.elems = c->d_belems;
     a.rho = c->d_brho;
     a.partial = c->d_bpartial;
-    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[j], block, c->bplan_smem[j], s);
+    e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[wp][j], block, c->bplan_smem[wp][j], s);
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel launch");
   reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, c->nacc(), states, c->d_bres);
@@ -976,67 +1031,43 @@ ift_status launch_batched(ift_ctx* c, bool jac, const double* w, long wstride, c
   return IFT_OK;
 }
 
-ift_status enqueue_batched_body(ift_ctx* c, cudaStream_t s, unsigned long long handle, int use_cond) {
+ift_status enqueue_batched_body(ift_ctx* c, int wp, cudaStream_t s, unsigned long long handle, int use_cond) {
   const double* trial = (const double*)((char*)c->d_blm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_blm + offsetof(LMState, done));
-  ift_status st = launch_batched(c, true, trial, (long)(sizeof(LMState) / sizeof(double)), done,
+  ift_status st = launch_batched(c, wp, true, trial, (long)(sizeof(LMState) / sizeof(double)), done,
                                  (long)(sizeof(LMState) / sizeof(int)), c->d_blm, s);
   if (st != IFT_OK) return st;
-  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), lm_consts(c));
+  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), stage_consts(c, wp));
   batch_condition_kernel<<<1, 256, 0, s>>>(c->d_blm, c->B, c->d_active, handle, use_cond);
   CK(cudaGetLastError(), "batched LM launch");
   return IFT_OK;
 }
 
-ift_status build_batched_graph(ift_ctx* c) {
-  if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
-  if (c->bgraph) cudaGraphDestroy(c->bgraph);
-  c->bgraph_exec = nullptr;
-  c->bgraph = nullptr;
-  if (c->bplan_epoch != c->epoch) {
-    ift_status st = plan_batched(c);
+ift_status build_batched_graph(ift_ctx* c, int wp) {
+  if (c->bgraph_exec[wp]) cudaGraphExecDestroy(c->bgraph_exec[wp]);
+  if (c->bgraph[wp]) cudaGraphDestroy(c->bgraph[wp]);
+  c->bgraph_exec[wp] = nullptr;
+  c->bgraph[wp] = nullptr;
+  if (c->bplan_epoch[wp] != c->epoch) {
+    ift_status st = plan_batched(c, wp);
     if (st != IFT_OK) return st;
   }
-  cudaGraph_t g = nullptr;
-  CK(cudaGraphCreate(&g, 0), "graph create");
-  c->bgraph = g;
-  cudaGraphConditionalHandle h;
-  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
-  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
-  std::memset(pbuf, 0, sizeof(pbuf));
-  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(pbuf);
-  p->type = cudaGraphNodeTypeConditional;
-  p->conditional.handle = h;
-  p->conditional.type = cudaGraphCondTypeWhile;
-  p->conditional.size = 1;
-  cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, p), "while node");
-  cudaGraph_t body = p->conditional.phGraph_out[0];
-  cudaStream_t cs = nullptr;
-  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(cs);
-    return c->cuda_fail(e, "begin capture");
-  }
-  ift_status st = enqueue_batched_body(c, cs, (unsigned long long)h, 1);
-  cudaGraph_t captured = nullptr;
-  e = cudaStreamEndCapture(cs, &captured);
-  cudaStreamDestroy(cs);
+  ift_status st = build_while_graph(c, &c->bgraph[wp], &c->bgraph_exec[wp],
+                                    [&](cudaStream_t cs, unsigned long long h) {
+                                      return enqueue_batched_body(c, wp, cs, h, 1);
+                                    });
   if (st != IFT_OK) return st;
-  if (e != cudaSuccess) return c->cuda_fail(e, "end capture");
-  CK(cudaGraphInstantiate(&c->bgraph_exec, g, 0), "graph instantiate");
-  c->bgraph_epoch = c->epoch;
+  c->bgraph_epoch[wp] = c->epoch;
   return IFT_OK;
 }
 
-ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
+ift_status run_batched_stage(ift_ctx* c, int wp, cudaStream_t s) {
   static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
   if (no_graph) {
-    const LMConsts k = lm_consts(c);
+    const LMConsts k = lm_consts(c, stage_tol(c, wp));
     for (int b = 0; b <= k.body_limit; b += 8) {
       for (int j = 0; j < 8; ++j) {
-        ift_status st = enqueue_batched_body(c, s, 0ull, 0);
+        ift_status st = enqueue_batched_body(c, wp, s, 0ull, 0);
         if (st != IFT_OK) return st;
       }
       int active = 0;
@@ -1046,12 +1077,21 @@ ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
     }
     return IFT_OK;
   }
-  if (c->bgraph_epoch != c->epoch || !c->bgraph_exec) {
-    ift_status st = build_batched_graph(c);
+  if (c->bgraph_epoch[wp] != c->epoch || !c->bgraph_exec[wp]) {
+    ift_status st = build_batched_graph(c, wp);
     if (st != IFT_OK) return st;
   }
-  CK(cudaGraphLaunch(c->bgraph_exec, s), "batched graph launch");
+  CK(cudaGraphLaunch(c->bgraph_exec[wp], s), "batched graph launch");
   return IFT_OK;
+}
+
+ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
+  if (c->cfg.precision == IFT_FP64) return run_batched_stage(c, 0, s);
+  ift_status st = run_batched_stage(c, 1, s);
+  if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
+  lm_restart_kernel<<<c->B, 64, 0, s>>>(c->d_blm, c->B, c->ku, c->kx);
+  CK(cudaGetLastError(), "stage restart");
+  return run_batched_stage(c, 0, s);
 }
 
 ift_status check_batched(ift_ctx* c) {
@@ -1146,7 +1186,7 @@ ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, c
   st = upload_mu_rows(c, mu, s);
   if (st != IFT_OK) return st;
   CK(cudaMemcpyAsync(c->d_bw, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s), "copy points");
-  st = launch_batched(c, true, c->d_bw, k, nullptr, 0, nullptr, s);
+  st = launch_batched(c, c->eval_wp(), true, c->d_bw, k, nullptr, 0, nullptr, s);
   if (st != IFT_OK) return st;
   std::vector<double> res((size_t)B * nacc);
   CK(cudaMemcpyAsync(res.data(), c->d_bres, res.size() * 8, cudaMemcpyDeviceToHost, s), "copy results");

@@ -16,7 +16,7 @@ namespace {
 // the diagonal is shifted by 1e-14 trace/k, times 10 per retry, at most 10 times.
 constexpr double kLam0 = 1e-4, kLamMin = 1e-12, kLamMax = 1e8, kC1 = 1e-4;
 constexpr double kRound = 16.0 * 2.220446049250313e-16;
-constexpr int kMaxHalvings = 30, kMaxShifts = 10;
+constexpr int kMaxShifts = 10;
 
 __device__ double active_norm(const LMState& s, int ku, int kx, bool full) {
   double t = 0.0;
@@ -125,7 +125,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
         s.J = Jr;
         s.iters[s.phase] += 1;
         need_solve = decide(s, c);
-      } else if (s.h + 1 > kMaxHalvings) {
+      } else if (s.h + 1 > c.max_halvings) {
         // line search failed: this phase ends at the current iterate
         if (s.phase == 0) {
           s.init_status = IFT_LINESEARCH_FAILED;
@@ -297,6 +297,8 @@ __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0
     s.h = 0;
     s.bodies = 0;
     s.done = 0;
+    s.iters32 = 0;
+    s.trials32 = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -340,6 +342,8 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
     s.h = 0;
     s.bodies = 0;
     s.done = 0;
+    s.iters32 = 0;
+    s.trials32 = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -364,6 +368,37 @@ __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, dou
   }
   if (threadIdx.x == 0)
     for (int a = 0; a < m; ++a) colsum[a * ku + c] = red[a][0];
+}
+
+// Restart B solver states at their own current iterate in the joint phase (the FP64
+// stage of a mixed-precision solve): the FP32 stage's joint-phase counts are kept in
+// iters32 / trials32, the iteration restarts from lambda_0 with a fresh assembly.
+__global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
+  const int q = blockIdx.x;
+  if (q >= B) return;
+  LMState& s = states[q];
+  const int k = ku + kx;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    s.trial[i] = s.z[i];
+    s.dz[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    s.iters32 = s.iters[1];
+    s.trials32 = s.trials;
+    s.iters[1] = 0;
+    s.trials = 0;
+    // a query stopped by a non-physical start stays stopped
+    if (s.status != IFT_ERR_NONPHYSICAL) {
+      s.phase = 1;
+      s.state = 0;
+      s.status = IFT_NOT_CONVERGED;
+      s.h = 0;
+      s.bodies = 0;
+      s.done = 0;
+      s.lam = kLam0;
+      s.alpha = 1.0;
+    }
+  }
 }
 
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {

@@ -20,6 +20,7 @@ struct LMConsts {
   int max_iters;
   int ku, kx;
   int body_limit;   // hard bound on loop bodies (then IFT_ERR_TIMEOUT)
+  int max_halvings; // line-search halvings before the phase ends (30; fewer in the FP32 stage of a mixed solve)
 };
 
 // Device-resident solver state (one per query).
@@ -30,6 +31,7 @@ struct LMState {
   int init_status;  // status at the end of phase 0
   int iters[2];     // accepted steps per phase
   int trials, shifts, h, bodies, done;
+  int iters32, trials32;  // joint-phase steps and trials of the FP32 stage of a mixed solve
   double lam, alpha, J, slope, g0, thresh;
   double z[LM_KMAX];      // current iterate (w | tau)
   double dz[LM_KMAX];     // step
