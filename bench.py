@@ -197,6 +197,7 @@ def run_ours(args):
     wl = make_workload()
     stream = torch.cuda.Stream(device=dev)
     ctx = ift.Context.from_workload(wl, tol=1e-8, stream=stream.cuda_stream)
+    shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
     mu_d = torch.as_tensor(wl.mus[0], dtype=torch.float64, device=dev)
     y_d = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
     z_d = torch.zeros(wl.kx, dtype=torch.float64, device=dev)
@@ -290,7 +291,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "elements": n_el, "p": 2, "k_u": wl.ku, "k_x": wl.kx,
                            "tol": 1e-8, "l2": "flushed between steps (512 MB write)",
-                           "assemblies_per_solve": assemblies, "parallelism": f"replicas{world}"},
+                           "assemblies_per_solve": assemblies, "parallelism": f"replicas{world}",
+                           "launch_shapes": {"warps_per_cta": shapes[0]}},
                 "element_rj_evals_per_s": evals_per_s,
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -364,6 +366,7 @@ def run_batched(args):
     prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
     ctx.set_eq_weights_batched(sets)
+    shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
     mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
     y = torch.zeros((B, wl.ku), dtype=torch.float64, device=dev)
     z = torch.zeros((B, wl.kx), dtype=torch.float64, device=dev)
@@ -388,7 +391,7 @@ def run_batched(args):
     evals = sum(len(sets[q][0]) * (1 + info["info"][q]["trials"]) for q in range(B))
     fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
     t = sum(ms) / 1e3
-    print(json.dumps({"mode": "batched", "precision": args.precision, "queries": B,
+    print(json.dumps({"mode": "batched", "precision": args.precision, "queries": B, "launch_shapes": shapes,
                       "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
                       "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
                       "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,

@@ -196,6 +196,16 @@ ift_status ift_solve_rom_batched(ift_ctx* ctx, const double* mu, double* y, doub
 ift_status ift_solve_rom_batched_dev(ift_ctx* ctx, const double* mu, double* y, double* z, int32_t* status,
                                      void* stream);
 
+/* Launch-shape autotuner (not part of the paper's method). Times the fused
+   assembly of this context's workload at (mu, y, z) for 1, 2 and 4 warps per CTA
+   and, when batched weights are set, the batched assembly for chunk sizes 4, 8,
+   16, 32 elements x 1, 2, 4 warps per CTA (scored on a full batch plus a tail with
+   2% of the queries running), keeps the fastest shapes in the context and writes
+   them to chosen[0..2] = (warps per CTA, batched warps per CTA, chunk size).
+   Results change only by reduction order (all shapes compute the same sums).
+   Default shapes without tuning: 2, 2, 8. */
+ift_status ift_autotune(ift_ctx* ctx, const double* mu, const double* y, const double* z, int32_t* chosen);
+
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
    cannot call cudaMalloc when they need the reduced system: code that is
    capturing a stream into a CUDA graph, code that owns all device memory

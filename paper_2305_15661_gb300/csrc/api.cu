@@ -47,8 +47,8 @@ using namespace ift;
 
 namespace {
 
-constexpr int kWarpsPerCta = 2;
-constexpr int kChunk = 32;  // elements per chunk of the batched path
+constexpr int kWarpsPerCta = 2;  // default warps per CTA of the element kernels
+constexpr int kChunk = 8;        // default elements per chunk of the batched path
 constexpr int kPhitBlocks = 256;
 thread_local std::string g_create_error;
 
@@ -111,7 +111,11 @@ struct ift_ctx {
   int plan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t plan_smem[2][2] = {{0, 0}, {0, 0}};
   int plan_epoch[2] = {-1, -1};
+  // launch shapes (set by ift_autotune): warps per CTA of the single-query and the
+  // batched element kernels, elements per chunk of the batched path
+  int wpc = kWarpsPerCta, bwpc = kWarpsPerCta, chunk = kChunk;
   // batched queries (per-query weight sets split into chunks)
+  std::vector<int64_t> h_offsets;  // host copy of the per-query offsets (to re-chunk)
   int B = 0;
   int n_chunks = 0;
   int* d_chunk_start = nullptr;
@@ -226,17 +230,17 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
 // need; the shape is fixed per configuration, so sums are reproducible.
 ift_status plan_launch(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * kWarpsPerCta;
+  const int block = 32 * c->wpc;
   const long items = (c->nnz < 0) ? c->n_elems : c->nnz;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, kWarpsPerCta);
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->wpc);
     cudaError_t e = ks.prepare(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
     const int bps = ks.blocks_per_sm(jac, block, smem);
     if (bps < 1) return c->fail(IFT_ERR_CUDA, "element kernel does not fit on an SM (%zu bytes shared)", smem);
     long grid = (long)c->sm_count * bps;
-    const long need = (items + kWarpsPerCta - 1) / kWarpsPerCta;
+    const long need = (items + c->wpc - 1) / c->wpc;
     if (grid > need) grid = need;
     if (grid > c->max_parts) grid = c->max_parts;
     if (grid < 1) grid = 1;
@@ -244,7 +248,7 @@ ift_status plan_launch(ift_ctx* c, int wp) {
     c->plan_smem[wp][j] = smem;
   }
   // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
-  const size_t ismem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
+  const size_t ismem = ks.smem_bytes(true, 1, 0, c->wpc);
   if (ismem > c->plan_smem[wp][1]) {
     cudaError_t e = ks.prepare(true, ismem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
@@ -262,7 +266,7 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
     if (st != IFT_OK) return st;
   }
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * kWarpsPerCta;
+  const int block = 32 * c->wpc;
   const int grid = c->plan_grid[wp][jac ? 1 : 0];
   const size_t smem = c->plan_smem[wp][jac ? 1 : 0];
   cudaError_t e;
@@ -684,11 +688,11 @@ ift_status ift_element_eval(ift_ctx* c, const double* mu, const double* U, const
   cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s);
   const int wp = c->eval_wp();
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * kWarpsPerCta;
-  const size_t smem = ks.smem_bytes(true, 1, 0, kWarpsPerCta);
+  const int block = 32 * c->wpc;
+  const size_t smem = ks.smem_bytes(true, 1, 0, c->wpc);
   e = ks.prepare(true, c->have_bases && c->plan_smem[wp][1] > smem ? c->plan_smem[wp][1] : smem);
   if (e == cudaSuccess) {
-    const int grid = (int)((n + kWarpsPerCta - 1) / kWarpsPerCta);
+    const int grid = (int)((n + c->wpc - 1) / c->wpc);
     if (wp == 1) {
       AsmArgs<float> a = make_args<float>(c, c->d_Phi32, c->d_w, c->d_tau, c->d_mu, true, nullptr);
       a.ku = 1;
@@ -972,16 +976,16 @@ namespace {
 
 ift_status plan_batched(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * kWarpsPerCta;
+  const int block = 32 * c->bwpc;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, kWarpsPerCta);
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->bwpc);
     cudaError_t e = ks.prepare_batched(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel attributes");
     const int bps = ks.blocks_per_sm_batched(jac, block, smem);
     if (bps < 1) return c->fail(IFT_ERR_CUDA, "batched kernel does not fit on an SM (%zu bytes shared)", smem);
     long grid = (long)c->sm_count * bps;
-    const long need = (c->n_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+    const long need = (c->n_chunks + c->bwpc - 1) / c->bwpc;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     c->bplan_grid[wp][j] = (int)grid;
@@ -999,7 +1003,7 @@ ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long ws
     if (st != IFT_OK) return st;
   }
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * kWarpsPerCta;
+  const int block = 32 * c->bwpc;
   const int j = jac ? 1 : 0;
   BatchArgs b;
   b.chunk_start = c->d_chunk_start;
@@ -1094,6 +1098,32 @@ ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
   return run_batched_stage(c, 0, s);
 }
 
+// Split every query's items into chunks of c->chunk elements (one warp each) and size
+// the chunk partials; called when the weights or the chunk size change.
+ift_status rechunk(ift_ctx* c) {
+  const int B = c->B;
+  std::vector<int> cstart, cquery, qchunk(B + 1);
+  for (int q = 0; q < B; ++q) {
+    qchunk[q] = (int)cquery.size();
+    for (int64_t i = c->h_offsets[q]; i < c->h_offsets[q + 1]; i += c->chunk) {
+      cstart.push_back((int)i);
+      cquery.push_back(q);
+    }
+  }
+  qchunk[B] = (int)cquery.size();
+  cstart.push_back((int)c->h_offsets[B]);
+  CK(dalloc(c->d_chunk_start, cstart.size()), "alloc chunks");
+  CK(dalloc(c->d_chunk_query, cquery.size()), "alloc chunks");
+  CK(dalloc(c->d_qchunk, qchunk.size()), "alloc chunks");
+  CK(dalloc(c->d_bpartial, cquery.size() * (size_t)c->nacc()), "alloc chunk partials");
+  CK(cudaMemcpy(c->d_chunk_start, cstart.data(), cstart.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  CK(cudaMemcpy(c->d_chunk_query, cquery.data(), cquery.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  CK(cudaMemcpy(c->d_qchunk, qchunk.data(), qchunk.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
+  c->n_chunks = (int)cquery.size();
+  c->epoch++;
+  return IFT_OK;
+}
+
 ift_status check_batched(ift_ctx* c) {
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
@@ -1134,41 +1164,22 @@ ift_status ift_set_eq_weights_batched(ift_ctx* c, int B, const int64_t* offsets,
       stamp[elem[i]] = q;
       if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return c->fail(IFT_ERR_ARG, "weights must be positive and finite");
     }
-  std::vector<int> cstart, cquery, qchunk(B + 1);
-  for (int q = 0; q < B; ++q) {
-    qchunk[q] = (int)cquery.size();
-    for (int64_t i = offsets[q]; i < offsets[q + 1]; i += kChunk) {
-      cstart.push_back((int)i);
-      cquery.push_back(q);
-    }
-  }
-  qchunk[B] = (int)cquery.size();
-  cstart.push_back((int)total);
-  const int nchunks = (int)cquery.size();
   const int nacc = c->nacc(), k = c->ku + c->kx;
   drop_graph(c);
   c->B = 0;
-  CK(dalloc(c->d_chunk_start, cstart.size()), "alloc chunks");
-  CK(dalloc(c->d_chunk_query, cquery.size()), "alloc chunks");
-  CK(dalloc(c->d_qchunk, qchunk.size()), "alloc chunks");
   CK(dalloc(c->d_belems, (size_t)total), "alloc batched weights");
   CK(dalloc(c->d_brho, (size_t)total), "alloc batched weights");
   CK(dalloc(c->d_bmu, (size_t)B * 2), "alloc mu");
   CK(dalloc(c->d_bw, (size_t)B * k), "alloc points");
   CK(dalloc(c->d_bres, (size_t)B * nacc), "alloc results");
-  CK(dalloc(c->d_bpartial, (size_t)nchunks * nacc), "alloc chunk partials");
   CK(dalloc(c->d_blm, (size_t)B), "alloc solver states");
   CK(dalloc(c->d_active, 1), "alloc active count");
-  CK(cudaMemcpy(c->d_chunk_start, cstart.data(), cstart.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
-  CK(cudaMemcpy(c->d_chunk_query, cquery.data(), cquery.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
-  CK(cudaMemcpy(c->d_qchunk, qchunk.data(), qchunk.size() * 4, cudaMemcpyHostToDevice), "copy chunks");
   CK(cudaMemcpy(c->d_belems, elem, (size_t)total * 4, cudaMemcpyHostToDevice), "copy weights");
   CK(cudaMemcpy(c->d_brho, rho, (size_t)total * 8, cudaMemcpyHostToDevice), "copy weights");
   CK(cudaMemset(c->d_blm, 0, (size_t)B * sizeof(LMState)), "clear states");
+  c->h_offsets.assign(offsets, offsets + B + 1);
   c->B = B;
-  c->n_chunks = nchunks;
-  c->epoch++;
-  return IFT_OK;
+  return rechunk(c);
 }
 
 ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, const double* y, const double* z,
@@ -1273,3 +1284,122 @@ ift_status ift_solve_rom_batched_dev(ift_ctx* c, const double* mu, double* y, do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shapes.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Median of reps timed runs of fn (after one warm-up); +inf if a launch fails.
+template <class F>
+float time_launch(ift_ctx* c, cudaStream_t s, int reps, F fn) {
+  if (fn() != IFT_OK) return INFINITY;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<float> t;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, s);
+    ift_status st = fn();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (st != IFT_OK) ms = INFINITY;
+    t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::sort(t.begin(), t.end());
+  (void)c;
+  return t[t.size() / 2];
+}
+
+}  // namespace
+
+extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y, const double* z, int32_t* chosen) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
+  cudaStream_t s = c->stream;
+  const int wp = c->eval_wp();
+  const int nmu = (c->dim == 1) ? 1 : 2, k = c->ku + c->kx;
+  CK(cudaMemcpy(c->d_mu, mu, nmu * 8, cudaMemcpyHostToDevice), "copy mu");
+  CK(cudaMemcpy(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice), "copy y");
+  if (c->kx > 0) CK(cudaMemcpy(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice), "copy z");
+  const int cand_w[3] = {1, 2, 4};
+  // single-query fused assembly: warps per CTA
+  float best = INFINITY;
+  int best_w = c->wpc;
+  for (int w : cand_w) {
+    c->wpc = w;
+    c->epoch++;
+    const float t = time_launch(c, s, 3, [&]() {
+      return launch_assemble(c, wp, true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
+    });
+    if (t < best) {
+      best = t;
+      best_w = w;
+    }
+  }
+  c->wpc = best_w;
+  c->epoch++;
+  if (c->B > 0) {
+    // batched assembly: chunk size x warps per CTA, scored on a full batch plus a tail
+    // in which only every 50th query is still running (weight 8: tails have more bodies)
+    std::vector<double> wrep((size_t)c->B * k), mrep((size_t)c->B * 2, 0.0);
+    for (int q = 0; q < c->B; ++q) {
+      for (int i = 0; i < c->ku; ++i) wrep[(size_t)q * k + i] = y[i];
+      for (int i = 0; i < c->kx; ++i) wrep[(size_t)q * k + c->ku + i] = z[i];
+      for (int i = 0; i < nmu; ++i) mrep[(size_t)q * 2 + i] = mu[i];
+    }
+    std::vector<int> tail(c->B);
+    for (int q = 0; q < c->B; ++q) tail[q] = (q % 50 == 0) ? 0 : 1;
+    int* d_tail = nullptr;
+    CK(dalloc(d_tail, (size_t)c->B), "alloc tail flags");
+    CK(cudaMemcpy(d_tail, tail.data(), tail.size() * 4, cudaMemcpyHostToDevice), "copy tail flags");
+    CK(cudaMemcpy(c->d_bw, wrep.data(), wrep.size() * 8, cudaMemcpyHostToDevice), "copy points");
+    CK(cudaMemcpy(c->d_bmu, mrep.data(), mrep.size() * 8, cudaMemcpyHostToDevice), "copy mu");
+    const int cand_c[4] = {4, 8, 16, 32};
+    float bscore = INFINITY;
+    int bc = c->chunk, bw = c->bwpc;
+    for (int ch : cand_c) {
+      c->chunk = ch;
+      st = rechunk(c);
+      if (st != IFT_OK) {
+        dfree(d_tail);
+        return st;
+      }
+      for (int w : cand_w) {
+        c->bwpc = w;
+        c->epoch++;
+        const float tf = time_launch(c, s, 3, [&]() {
+          return launch_batched(c, wp, true, c->d_bw, k, nullptr, 0, nullptr, s);
+        });
+        const float tt = time_launch(c, s, 3, [&]() {
+          return launch_batched(c, wp, true, c->d_bw, k, d_tail, 1, nullptr, s);
+        });
+        const float score = tf + 8.0f * tt;
+        if (score < bscore) {
+          bscore = score;
+          bc = ch;
+          bw = w;
+        }
+      }
+    }
+    dfree(d_tail);
+    c->chunk = bc;
+    c->bwpc = bw;
+    st = rechunk(c);
+    if (st != IFT_OK) return st;
+  }
+  c->err.clear();
+  c->epoch++;
+  if (chosen) {
+    chosen[0] = c->wpc;
+    chosen[1] = c->bwpc;
+    chosen[2] = c->chunk;
+  }
+  CK(cudaStreamSynchronize(s), "autotune");
+  return IFT_OK;
+}

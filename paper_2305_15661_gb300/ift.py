@@ -56,7 +56,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
-           "ift_solve_rom_batched_dev"]
+           "ift_solve_rom_batched_dev", "ift_autotune"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_solve_rom": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_dev": (i32, [vp, vp, vp, vp, P(SolveInfo), vp]),
         "ift_set_eq_weights_batched": (i32, [vp, i32, pl, pi, pd]),
+        "ift_autotune": (i32, [vp, pd, pd, pd, pi]),
         "ift_reduced_residual_jacobian_batched": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom_batched": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_batched_dev": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -259,6 +260,13 @@ class Context:
         return {"status": int(st), "w": y, "tau": z[:self.kx], "init_iters": info.init_iters, "iters": info.iters,
                 "trials": info.trials, "shifts": info.shifts, "J": info.J, "normS": info.normS,
                 "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters, "fp32_trials": info.fp32_trials}
+
+    def autotune(self, mu, y, z):
+        """Pick the launch shapes by timing this workload; returns (warps, batched warps, chunk)."""
+        out = np.zeros(3, dtype=np.int32)
+        zz = _f64(z) if self.kx else np.zeros(1)
+        self._check(load().ift_autotune(self._h, _pd(_f64(mu)), _pd(_f64(y)), _pd(zz), _pi(out)))
+        return tuple(int(v) for v in out)
 
     # -- batched queries ---------------------------------------------------
     def set_eq_weights_batched(self, sets):

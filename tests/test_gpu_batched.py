@@ -89,3 +89,23 @@ def test_batched_errors():
         ctx.set_eq_weights_batched([(np.array([0, 0]), np.array([1.0, 1.0]))])
     with pytest.raises(ift.IFTError):
         ctx.set_eq_weights_batched([(np.array([0]), np.array([1.0])), (np.array([], dtype=np.int32), np.array([]))])
+
+
+def test_autotune_keeps_results():
+    wl = W.euler_workload(n=20, p=2, k_u=10, k_x=4, seed=15, n_mu=6, mu_box=True)
+    sets = W.eq_weight_sets(wl, 6, seed=16, lo=30, hi=200)
+    ctx = ift.Context.from_workload(wl)
+    before = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    ctx.set_eq_weights_batched(sets)
+    ys, zs = np.stack([wl.w_eval] * 6), np.stack([wl.tau_eval] * 6)
+    bb = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    w, bw, ch = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert w in (1, 2, 4) and bw in (1, 2, 4) and ch in (4, 8, 16, 32)
+    after = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    ba = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    for key in ("S", "T", "H"):
+        assert _fro(after[key], before[key]) < 1e-12
+        assert _fro(ba[key], bb[key]) < 1e-12
+    assert abs(after["J"] - before["J"]) <= 1e-13 * before["J"]
+    res = ctx.solve_rom_batched(wl.mus)
+    assert all(i["status"] in (0, 1, 2) for i in res["info"])
