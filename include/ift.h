@@ -240,6 +240,56 @@ ift_status ift_reduced_residual_jacobian_static(
     const double* y, const double* z, double gamma, double kappa, double eps_g, double* S, double* T,
     double* H, double* J, void* stream);
 
+/* ---- Learned warm start of the LM solve --------------------------------------
+   The paper starts every LM solve from the projected guess (Remark rem:solver).
+   The calls below add an optional learned start: a fully connected network
+   x (n_in) -> width (x depth hidden layers, GELU(z) = z (1 + erf(z / sqrt 2)) / 2)
+   -> n_out (linear), trained on pairs (mu, [w; tau]) from converged solves and
+   evaluated at new mu to give the (y, z) of an IFT_INIT_GIVEN solve. All
+   network arithmetic runs in FP32 on the device (forward, backward, loss,
+   Adam); host arrays are FP64 and are converted at the boundary.
+
+   Parameters are flattened layer by layer as W_l (in x out, row-major, so a
+   row of inputs times W_l gives the layer's pre-activation) followed by b_l. */
+typedef struct ift_mlp ift_mlp;
+
+/* Creates a network on the current device with W ~ N(0, 1/in) (splitmix64 and
+   Box-Muller draws from seed) and b = 0. stream: cudaStream_t or NULL.
+   IFT_ERR_ARG unless n_in, n_out >= 1, 0 <= depth <= 16, width >= 1 when depth > 0. */
+ift_status ift_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed, void* stream, ift_mlp** out);
+ift_status ift_mlp_destroy(ift_mlp* net);
+ift_status ift_mlp_num_params(const ift_mlp* net, int64_t* count);
+/* Host copies of the parameters (FP64 in, FP64 out; stored as FP32). */
+ift_status ift_mlp_get_params(const ift_mlp* net, double* params);
+ift_status ift_mlp_set_params(ift_mlp* net, const double* params);
+
+/* Mean-squared-error loss L = sum (Y - t)^2 / (count n_out) of the network on
+   count rows x (count x n_in) against t (count x n_out), both taken as the
+   network's own inputs and targets (no normalisation), and its gradient with
+   respect to the flattened parameters (grad may be NULL). 1 <= count <= 2^20. */
+ift_status ift_mlp_loss_grad(ift_mlp* net, int64_t count, const double* x, const double* t, double* loss,
+                             double* grad);
+
+/* Trains on count pairs (x, t): inputs and targets are first standardised per
+   column (mean 0, standard deviation 1, kept in the network for predict), then
+   `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over
+   mini-batches of `batch` rows in a seeded random order (the last partial batch
+   of an epoch is dropped). final_loss (may be NULL): the loss over all pairs in
+   the standardised variables after training. */
+ift_status ift_mlp_train(ift_mlp* net, int64_t count, const double* x, const double* t, int epochs, int batch,
+                         double lr, uint64_t seed, double* final_loss);
+
+/* out (count x n_out) = the network at x (count x n_in), in the caller's
+   variables (standardisation applied and undone). */
+ift_status ift_mlp_predict(ift_mlp* net, int64_t count, const double* x, double* out);
+
+/* The start the learned one is compared with: for each query, the outputs of
+   the nearest training point, y_out[q] = y_train[argmin_t |scale (x_q - x_t)|]
+   (scale: n_in per-column factors, NULL = 1; the lowest index wins ties).
+   Computed on the device. */
+ift_status ift_nearest_start(int64_t n_train, int n_in, const double* x_train, int n_out, const double* y_train,
+                             int64_t n_query, const double* x_query, const double* scale, double* y_out);
+
 #ifdef __cplusplus
 }
 #endif

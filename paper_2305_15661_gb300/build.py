@@ -36,7 +36,8 @@ def _nvcc() -> str:
 
 def _units():
     units = [("api", "api.cu", []), ("lm", "lm.cu", []), ("refelem", "refelem.cpp", []),
-             ("dispatch", "dispatch.cpp", []), ("noalloc", "noalloc.cu", [])]
+             ("dispatch", "dispatch.cpp", []), ("noalloc", "noalloc.cu", []),
+             ("mlp", "mlp.cu", [])]
     for prob in (1, 2):
         for p in (1, 2, 3):
             for prec in (0, 1):

@@ -56,7 +56,9 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
-           "ift_solve_rom_batched_dev", "ift_autotune"]
+           "ift_solve_rom_batched_dev", "ift_autotune", "ift_mlp_create", "ift_mlp_destroy",
+           "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_loss_grad", "ift_mlp_train",
+           "ift_mlp_predict", "ift_nearest_start"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -96,6 +98,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_reduced_residual_jacobian_static": (i32, [i32, i32, i64, vp, i64, vp, vp, vp, vp, vp, i32, vp, i32,
                                                        i64, vp, vp, vp, vp, vp, dbl, dbl, dbl, vp, vp, vp, vp,
                                                        vp]),
+        "ift_mlp_create": (i32, [i32, i32, i32, i32, ctypes.c_uint64, vp, P(vp)]),
+        "ift_mlp_destroy": (i32, [vp]),
+        "ift_mlp_num_params": (i32, [vp, pl]),
+        "ift_mlp_get_params": (i32, [vp, pd]),
+        "ift_mlp_set_params": (i32, [vp, pd]),
+        "ift_mlp_loss_grad": (i32, [vp, i64, pd, pd, pd, pd]),
+        "ift_mlp_train": (i32, [vp, i64, pd, pd, i32, i32, dbl, ctypes.c_uint64, pd]),
+        "ift_mlp_predict": (i32, [vp, i64, pd, pd]),
+        "ift_nearest_start": (i32, [i64, i32, pd, i32, pd, i64, pd, pd, pd]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -320,3 +331,80 @@ class Context:
         return {"status": int(st), "init_iters": info.init_iters, "iters": info.iters, "trials": info.trials,
                 "J": info.J, "normS": info.normS, "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters,
                 "fp32_trials": info.fp32_trials}
+
+
+class MLP:
+    """The learned warm start: a GELU network n_in -> width^depth -> n_out trained and
+    evaluated by the library's FP32 kernels (the ift_mlp_* calls)."""
+
+    def __init__(self, n_in, width, depth, n_out, seed=0, stream=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.ift_mlp_create(n_in, width, depth, n_out, seed, ctypes.c_void_p(stream) if stream else None,
+                                ctypes.byref(h))
+        if st != IFT_OK:
+            raise IFTError(st, "ift_mlp_create failed")
+        self._h = h
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+        n = ctypes.c_int64()
+        lib.ift_mlp_num_params(h, ctypes.byref(n))
+        self.n_params = int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ift_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _check(st, what):
+        if st != IFT_OK:
+            raise IFTError(st, what + " failed")
+
+    def get_params(self):
+        out = np.zeros(self.n_params)
+        self._check(load().ift_mlp_get_params(self._h, _pd(out)), "ift_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        params = _f64(params)
+        assert params.size == self.n_params
+        self._check(load().ift_mlp_set_params(self._h, _pd(params)), "ift_mlp_set_params")
+
+    def loss_grad(self, x, t, want_grad=True):
+        x, t = _f64(x), _f64(t)
+        loss = np.zeros(1)
+        grad = np.zeros(self.n_params) if want_grad else None
+        self._check(load().ift_mlp_loss_grad(self._h, x.shape[0], _pd(x), _pd(t), _pd(loss), _pd(grad)),
+                    "ift_mlp_loss_grad")
+        return float(loss[0]), grad
+
+    def train(self, x, t, epochs, batch, lr, seed=0):
+        x, t = _f64(x), _f64(t)
+        loss = np.zeros(1)
+        self._check(load().ift_mlp_train(self._h, x.shape[0], _pd(x), _pd(t), epochs, batch, lr, seed, _pd(loss)),
+                    "ift_mlp_train")
+        return float(loss[0])
+
+    def predict(self, x):
+        x = _f64(x)
+        out = np.zeros((x.shape[0], self.n_out))
+        self._check(load().ift_mlp_predict(self._h, x.shape[0], _pd(x), _pd(out)), "ift_mlp_predict")
+        return out
+
+
+def nearest_start(x_train, y_train, x_query, scale=None):
+    """Outputs of the nearest training point for each query (computed on the device)."""
+    x_train, y_train, x_query = _f64(x_train), _f64(y_train), _f64(x_query)
+    out = np.zeros((x_query.shape[0], y_train.shape[1]))
+    st = load().ift_nearest_start(x_train.shape[0], x_train.shape[1], _pd(x_train), y_train.shape[1], _pd(y_train),
+                                  x_query.shape[0], _pd(x_query), None if scale is None else _pd(_f64(scale)),
+                                  _pd(out))
+    if st != IFT_OK:
+        raise IFTError(st, "ift_nearest_start failed")
+    return out

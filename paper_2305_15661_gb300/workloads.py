@@ -268,12 +268,21 @@ def euler_workload(n: int = 100, p: int = 2, k_u: int = 20, k_x: int = 4, seed: 
         amp *= 0.5
     tau = amp * d
     if mu_box:
-        u = uniform(seed, 25, 2 * n_mu).reshape(n_mu, 2)
-        mus = np.stack([1.8 + 0.4 * u[:, 0], math.radians(-2.0) + math.radians(4.0) * u[:, 1]], axis=1)
+        mus = mu_box_samples(seed, 25, n_mu)
     else:
         mus = np.tile(np.array([[mach, alpha]]), (n_mu, 1))
     return Workload(name=name, problem=PROB_EULER2D, p=p, X=X, ev=ev, Phi=Phi, Psi=Psi, gamma=gamma,
                     mus=mus, w_eval=w, tau_eval=tau, U_guess=U_inf, rho_sets=None)
+
+
+MU_BOX_LO = np.array([1.8, math.radians(-2.0)])
+MU_BOX_WIDTH = np.array([0.4, math.radians(4.0)])
+
+
+def mu_box_samples(seed: int, stream: int, n: int) -> np.ndarray:
+    """n parameter points (Mach, angle) uniform in [1.8, 2.2] x [-2 deg, 2 deg]."""
+    u = uniform(seed, stream, 2 * n).reshape(n, 2)
+    return MU_BOX_LO + MU_BOX_WIDTH * u
 
 
 def eq_weight_sets(wl: Workload, n_sets: int, seed: int, lo: int = 100, hi: int = 2000,
