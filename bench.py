@@ -402,6 +402,140 @@ def run_batched(args):
     return 0
 
 
+def _time_batched(ctx, stream, mus, y0, z0, y, z, st, steps):
+    """CUDA-event time of `steps` batched solves from the starts (y0, z0); the
+    start is copied into (y, z) before each step, outside the events."""
+    import torch
+
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            y.copy_(y0)
+            z.copy_(z0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_rom_batched_dev(mus, y, z, st, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def run_warmstart(args):
+    """Learned warm start: 2,048 training solves by the method on the 20,000-element
+    Euler mesh (p = 2, k_u = 40, k_x = 8, one shared weight set on 2% of the
+    elements), a 2 -> 128 -> 128 -> 128 -> 48 GELU network trained on them by the
+    library's kernels, then 4,096 batched queries started from the network, from
+    the nearest training point and from the projected guess; and the plain FP64
+    one-query solve of a sample of the same queries for comparison."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift
+    from paper_2305_15661_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    ift.load()
+    n_train, n_query = args.train_solves, args.queries
+    wl = W.euler_workload(n=100, p=2, k_u=40, k_x=8, seed=2)
+    ku, kx = wl.ku, wl.kx
+    rho_set = W.eq_weight_sets(wl, 1, seed=3, lo=400, hi=401)[0]
+    mu_t = W.mu_box_samples(5, 1, n_train)
+    mu_q = W.mu_box_samples(6, 1, n_query)
+    stream = torch.cuda.Stream(device=dev)
+    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
+    out = {"mode": "warmstart", "precision": args.precision, "train_solves": n_train, "queries": n_query,
+           "rho_nnz": int(len(rho_set[0])), "k_u": ku, "k_x": kx}
+
+    # training data: the method's own solves from the projected guess
+    gen = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    gen.set_eq_weights_batched([rho_set] * n_train)
+    out["launch_shapes"] = gen.autotune(mu_t[0], wl.w_eval, wl.tau_eval)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = gen.solve_rom_batched(mu_t)
+    out["train_data_s"] = time.perf_counter() - t0
+    ok = np.array([i["status"] == 0 for i in res["info"]])
+    out["train_converged"] = int(ok.sum())
+    y_t = np.concatenate([res["w"], res["tau"]], axis=1)[ok]
+    gen.close()
+
+    net = ift.MLP(2, 128, 3, ku + kx, seed=7, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out["train_loss"] = net.train(mu_t[ok], y_t, epochs=args.epochs, batch=64, lr=1e-3, seed=8)
+    out["train_s"] = time.perf_counter() - t0
+    out["epochs"] = args.epochs
+    t0 = time.perf_counter()
+    start_mlp = net.predict(mu_q)
+    out["predict_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    start_nn = ift.nearest_start(mu_t[ok], y_t, mu_q, scale=1.0 / W.MU_BOX_WIDTH)
+    out["nearest_ms"] = 1e3 * (time.perf_counter() - t0)
+
+    given = ift.Context.from_workload(wl, precision=prec, tol=1e-8, lm_init=ift.INIT_GIVEN,
+                                      stream=stream.cuda_stream)
+    given.set_eq_weights_batched([rho_set] * n_query)
+    given.set_launch_shapes(*out["launch_shapes"])
+    paper = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    paper.set_eq_weights_batched([rho_set] * n_query)
+    paper.set_launch_shapes(*out["launch_shapes"])
+    ref = paper.solve_rom_batched(mu_q)
+    z_ref = np.concatenate([ref["w"], ref["tau"]], axis=1)
+    J_ref = np.array([i["J"] for i in ref["info"]])
+    ok_ref = np.array([i["status"] == 0 for i in ref["info"]])
+
+    mus = torch.as_tensor(mu_q, dtype=torch.float64, device=dev)
+    y = torch.zeros((n_query, ku), dtype=torch.float64, device=dev)
+    z = torch.zeros((n_query, kx), dtype=torch.float64, device=dev)
+    st = torch.zeros(n_query, dtype=torch.int32, device=dev)
+    rows = {}
+    for name, ctx, s in (("projected", paper, None), ("nearest", given, start_nn), ("mlp", given, start_mlp)):
+        if s is None:
+            info = ref
+            y0 = torch.zeros_like(y)
+            z0 = torch.zeros_like(z)
+        else:
+            info = ctx.solve_rom_batched(mu_q, s[:, :ku], s[:, ku:])
+            y0 = torch.as_tensor(np.ascontiguousarray(s[:, :ku]), device=dev)
+            z0 = torch.as_tensor(np.ascontiguousarray(s[:, ku:]), device=dev)
+        ms = _time_batched(ctx, stream, mus, y0, z0, y, z, st, args.steps)
+        stat = np.array([i["status"] for i in info["info"]])
+        its = np.array([i["init_iters"] + i["iters"] + i["fp32_iters"] for i in info["info"]])
+        zf = np.concatenate([info["w"], info["tau"]], axis=1)
+        both = ok_ref & (stat == 0)
+        Jf = np.array([i["J"] for i in info["info"]])
+        row = {"ms_per_batch": statistics.median(ms), "solves_per_s": n_query / (statistics.median(ms) / 1e3),
+               "converged": int((stat == 0).sum()), "mean_lm_iters": float(its.mean()),
+               "max_iters": int(its.max()),
+               "max_rel_dz_vs_projected_start": float(np.max(np.linalg.norm(zf[both] - z_ref[both], axis=1)
+                                                              / np.linalg.norm(z_ref[both], axis=1))),
+               "max_rel_dJ_vs_projected_start": float(np.max(np.abs(Jf[both] - J_ref[both]) / J_ref[both]))}
+        if s is not None:
+            err = np.linalg.norm(s - z_ref, axis=1) / np.linalg.norm(z_ref, axis=1)
+            row["median_start_err"] = float(np.median(err))
+        rows[name] = row
+    out["starts"] = rows
+    given.close()
+    paper.close()
+
+    # the plain FP64 one-query form on a sample of the same queries
+    one = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
+    one.set_eq_weights(rho_set)
+    n1 = min(args.single_sample, n_query)
+    one.solve_rom(mu_q[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(n1):
+        one.solve_rom(mu_q[q])
+    dt = time.perf_counter() - t0
+    out["fp64_one_query"] = {"sample": n1, "solves_per_s": n1 / dt}
+    out["speedup_mlp_batched_vs_fp64_one_query"] = rows["mlp"]["solves_per_s"] / (n1 / dt)
+    one.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,10 +543,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly", "batched"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart"], default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
-                    help="element/contraction arithmetic for --mode assembly")
+                    help="element/contraction arithmetic for --mode assembly, batched and warmstart")
+    ap.add_argument("--train-solves", type=int, default=2048, help="--mode warmstart: training solves")
+    ap.add_argument("--queries", type=int, default=4096, help="--mode warmstart: served queries")
+    ap.add_argument("--epochs", type=int, default=1500, help="--mode warmstart: training epochs")
+    ap.add_argument("--single-sample", type=int, default=32, help="--mode warmstart: one-query FP64 solves timed")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -422,6 +560,8 @@ def main():
         return run_assembly(args)
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

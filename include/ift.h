@@ -205,6 +205,11 @@ ift_status ift_solve_rom_batched_dev(ift_ctx* ctx, const double* mu, double* y, 
    Results change only by reduction order (all shapes compute the same sums).
    Default shapes without tuning: 2, 2, 8. */
 ift_status ift_autotune(ift_ctx* ctx, const double* mu, const double* y, const double* z, int32_t* chosen);
+/* Sets the launch shapes directly (for instance, shapes an earlier ift_autotune
+   chose for the same workload): warps and batched_warps in {1, 2, 4}, chunk in
+   {4, 8, 16, 32}; anything else is IFT_ERR_ARG. Results change only by
+   reduction order. */
+ift_status ift_set_launch_shapes(ift_ctx* ctx, int warps, int batched_warps, int chunk);
 
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
    cannot call cudaMalloc when they need the reduced system: code that is

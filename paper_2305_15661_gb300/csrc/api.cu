@@ -1403,3 +1403,22 @@ extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y
   CK(cudaStreamSynchronize(s), "autotune");
   return IFT_OK;
 }
+
+extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_warps, int chunk) {
+  if (!c) return IFT_ERR_ARG;
+  auto ok_w = [](int w) { return w == 1 || w == 2 || w == 4; };
+  if (!ok_w(warps) || !ok_w(batched_warps) || !(chunk == 4 || chunk == 8 || chunk == 16 || chunk == 32))
+    return c->fail(IFT_ERR_ARG, "launch shapes must be warps in {1,2,4} and chunk in {4,8,16,32}");
+  c->wpc = warps;
+  c->bwpc = batched_warps;
+  if (chunk != c->chunk) {
+    c->chunk = chunk;
+    if (c->B > 0) {
+      ift_status st = rechunk(c);
+      if (st != IFT_OK) return st;
+    }
+  }
+  c->err.clear();
+  c->epoch++;
+  return IFT_OK;
+}

@@ -56,7 +56,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
-           "ift_solve_rom_batched_dev", "ift_autotune", "ift_mlp_create", "ift_mlp_destroy",
+           "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_loss_grad", "ift_mlp_train",
            "ift_mlp_predict", "ift_nearest_start"]
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_solve_rom_dev": (i32, [vp, vp, vp, vp, P(SolveInfo), vp]),
         "ift_set_eq_weights_batched": (i32, [vp, i32, pl, pi, pd]),
         "ift_autotune": (i32, [vp, pd, pd, pd, pi]),
+        "ift_set_launch_shapes": (i32, [vp, i32, i32, i32]),
         "ift_reduced_residual_jacobian_batched": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom_batched": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_batched_dev": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -278,6 +279,9 @@ class Context:
         zz = _f64(z) if self.kx else np.zeros(1)
         self._check(load().ift_autotune(self._h, _pd(_f64(mu)), _pd(_f64(y)), _pd(zz), _pi(out)))
         return tuple(int(v) for v in out)
+
+    def set_launch_shapes(self, warps, batched_warps, chunk):
+        self._check(load().ift_set_launch_shapes(self._h, warps, batched_warps, chunk))
 
     # -- batched queries ---------------------------------------------------
     def set_eq_weights_batched(self, sets):

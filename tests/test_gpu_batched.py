@@ -109,3 +109,23 @@ def test_autotune_keeps_results():
     assert abs(after["J"] - before["J"]) <= 1e-13 * before["J"]
     res = ctx.solve_rom_batched(wl.mus)
     assert all(i["status"] in (0, 1, 2) for i in res["info"])
+
+
+def test_set_launch_shapes():
+    wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=17, n_mu=4, mu_box=True)
+    sets = W.eq_weight_sets(wl, 4, seed=18, lo=30, hi=150)
+    ctx = ift.Context.from_workload(wl)
+    ctx.set_eq_weights_batched(sets)
+    ys, zs = np.stack([wl.w_eval] * 4), np.stack([wl.tau_eval] * 4)
+    base = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    one = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    for shape in ((1, 4, 4), (4, 1, 32), (2, 2, 16)):
+        ctx.set_launch_shapes(*shape)
+        b = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+        o = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+        for key in ("S", "T", "H"):
+            assert _fro(b[key], base[key]) < 1e-12
+            assert _fro(o[key], one[key]) < 1e-12
+    for bad in ((3, 2, 8), (2, 8, 8), (2, 2, 7), (2, 2, 64)):
+        with pytest.raises(ift.IFTError):
+            ctx.set_launch_shapes(*bad)
