@@ -310,18 +310,32 @@ def run_ours(args):
     return 0
 
 
+def _contraction(args):
+    from paper_2305_15661_gb300 import ift
+
+    if args.precision == "fp64":
+        return ift.CONTRACT_FP
+    return {"fp": ift.CONTRACT_FP, "tf32": ift.CONTRACT_TF32, "3xtf32": ift.CONTRACT_3XTF32}[args.contraction]
+
+
 def run_assembly(args):
     """Isolated fused assemblies of the workload at its evaluation point."""
     import torch
 
     from paper_2305_15661_gb300 import ift, perfmodel
 
+    from paper_2305_15661_gb300 import workloads as W
+
     dev = torch.device("cuda", 0)
     ift.load()
-    wl = make_workload()
+    if args.config == 4:  # p = 3 on 200 x 200 x 2 triangles, k_u = 40, k_x = 8
+        wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4)
+    else:
+        wl = make_workload()
     stream = torch.cuda.Stream(device=dev)
     prec = ift.FP64 if args.precision == "fp64" else ift.FP32
-    ctx = ift.Context.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    ctx = ift.Context.from_workload(wl, precision=prec, stream=stream.cuda_stream, contraction=_contraction(args))
+    shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval) if args.autotune else None
     k = wl.ku + wl.kx
     t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
     mu, y, z = t(wl.mus[0]), t(wl.w_eval), t(wl.tau_eval)
@@ -341,9 +355,11 @@ def run_assembly(args):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    fl = perfmodel.flops_per_element(2, wl.p, wl.ku, wl.kx)["total"]
     med = statistics.median(ms)
-    print(json.dumps({"mode": "assembly", "precision": args.precision, "elements": wl.n_elems,
+    print(json.dumps({"mode": "assembly", "precision": args.precision, "contraction": args.contraction,
+                      "elements": wl.n_elems, "p": wl.p,
+                      "k_u": wl.ku, "k_x": wl.kx, "launch_shapes": shapes,
                       "median_ms": med, "min_ms": min(ms), "element_rj_evals_per_s": wl.n_elems / (med / 1e3),
                       "achieved_tflops": fl * wl.n_elems / (med / 1e3) / 1e12, "flops_per_element": fl}))
     ctx.close()
@@ -364,7 +380,8 @@ def run_batched(args):
     sets = W.eq_weight_sets(wl, B, seed=3)
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
-    ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
+                                    contraction=_contraction(args))
     ctx.set_eq_weights_batched(sets)
     shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
     mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
@@ -391,7 +408,8 @@ def run_batched(args):
     evals = sum(len(sets[q][0]) * (1 + info["info"][q]["trials"]) for q in range(B))
     fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
     t = sum(ms) / 1e3
-    print(json.dumps({"mode": "batched", "precision": args.precision, "queries": B, "launch_shapes": shapes,
+    print(json.dumps({"mode": "batched", "precision": args.precision, "contraction": args.contraction,
+                      "queries": B, "launch_shapes": shapes,
                       "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
                       "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
                       "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
@@ -444,11 +462,12 @@ def run_warmstart(args):
     mu_q = W.mu_box_samples(6, 1, n_query)
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
-    out = {"mode": "warmstart", "precision": args.precision, "train_solves": n_train, "queries": n_query,
+    out = {"mode": "warmstart", "precision": args.precision, "contraction": args.contraction, "train_solves": n_train, "queries": n_query,
            "rho_nnz": int(len(rho_set[0])), "k_u": ku, "k_x": kx}
 
     # training data: the method's own solves from the projected guess
-    gen = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    gen = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
+                                    contraction=_contraction(args))
     gen.set_eq_weights_batched([rho_set] * n_train)
     out["launch_shapes"] = gen.autotune(mu_t[0], wl.w_eval, wl.tau_eval)
     torch.cuda.synchronize()
@@ -474,10 +493,11 @@ def run_warmstart(args):
     out["nearest_ms"] = 1e3 * (time.perf_counter() - t0)
 
     given = ift.Context.from_workload(wl, precision=prec, tol=1e-8, lm_init=ift.INIT_GIVEN,
-                                      stream=stream.cuda_stream)
+                                      stream=stream.cuda_stream, contraction=_contraction(args))
     given.set_eq_weights_batched([rho_set] * n_query)
     given.set_launch_shapes(*out["launch_shapes"])
-    paper = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+    paper = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
+                                      contraction=_contraction(args))
     paper.set_eq_weights_batched([rho_set] * n_query)
     paper.set_launch_shapes(*out["launch_shapes"])
     ref = paper.solve_rom_batched(mu_q)
@@ -547,6 +567,11 @@ def main():
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly, batched and warmstart")
+    ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32"], default="fp",
+                    help="FP32/mixed contexts: form H with FP32 FMAs, TF32 or 3xTF32 tensor cores")
+    ap.add_argument("--config", type=int, choices=[2, 4], default=2,
+                    help="--mode assembly: 2 = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, k 40+8")
+    ap.add_argument("--autotune", action="store_true", help="--mode assembly: tune the launch shape first")
     ap.add_argument("--train-solves", type=int, default=2048, help="--mode warmstart: training solves")
     ap.add_argument("--queries", type=int, default=4096, help="--mode warmstart: served queries")
     ap.add_argument("--epochs", type=int, default=1500, help="--mode warmstart: training epochs")

@@ -67,6 +67,13 @@ enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
    FP64 assemblies to tol. The LM normal equations, line search and stopping test
    are FP64 in every mode. */
 enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2 };
+/* How FP32 evaluations form H += rho A_e^T A_e (Eq. levmarq-elem): FP = FP32
+   fused multiply-adds; TF32 = tensor cores with TF32 inputs (10-bit mantissa)
+   and FP32 accumulation, H to about 1e-3 relative; 3XTF32 = tensor cores with
+   each operand split into two TF32 parts (three products), H to about FP32
+   accuracy. S~, T~ and J~ are FP32 fused multiply-adds in every mode, so the
+   optimum of a solve does not depend on this choice (H only steers the step). */
+enum { IFT_CONTRACT_FP = 0, IFT_CONTRACT_TF32 = 1, IFT_CONTRACT_3XTF32 = 2 };
 /* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
    LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */
 enum { IFT_INIT_PAPER = 0, IFT_INIT_GIVEN = 1 };
@@ -81,10 +88,11 @@ typedef struct {
   double tol;         /* stop when |[S~;T~]| <= tol * max(1, |[S~;T~]| at phase start) */
   int max_iters;      /* per LM phase */
   int lm_init;        /* IFT_INIT_PAPER or IFT_INIT_GIVEN */
+  int contraction;    /* IFT_CONTRACT_FP, _TF32 or _3XTF32 (the last two need IFT_FP32 or IFT_MIXED) */
 } ift_config;
 
 /* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,
-   max_iters 200, FP64, IFT_INIT_PAPER. */
+   max_iters 200, FP64, IFT_INIT_PAPER, IFT_CONTRACT_FP. */
 void ift_config_default(ift_config* cfg);
 
 /* Creates a context on the current CUDA device. stream: a cudaStream_t to run on

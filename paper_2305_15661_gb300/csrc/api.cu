@@ -79,6 +79,7 @@ struct ift_ctx {
   int dim = 1, m = 1, nv = 2, nb = 0, nu = 0, nup = 0, nxe = 0, nface = 0, ntrace = 0, nq = 0, nfq = 0;
   KernelSet ks[2];  // element kernels: [0] FP64, [1] FP32 (FP32 and mixed contexts)
   int sm_count = 0;
+  int smem_optin = 0;  // largest dynamic shared memory a CTA may opt into
   double* d_tables = nullptr;
   // mesh
   bool have_mesh = false;
@@ -153,6 +154,7 @@ struct ift_ctx {
     return st;
   }
   ift_status cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // the status is returned here; leave no error behind for the caller's next CUDA call
     return fail(e == cudaErrorMemoryAllocation ? IFT_ERR_OOM : IFT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   }
   int nacc() const { return (ku + kx) * (ku + kx) + ku + kx + 2; }
@@ -222,12 +224,21 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
   a.eps = c->cfg.eps_g;
   a.partial = c->d_partial;
   a.skip = skip;
+  a.contraction = c->cfg.contraction;
   return a;
 }
 
 // Grid and shared memory of the element kernels for the current bases and
 // weights: as many CTAs as fit on the GPU at once, but no more than the items
 // need; the shape is fixed per configuration, so sums are reproducible.
+// Largest dynamic shared memory of the element kernels of this context for w warps per CTA.
+size_t shapes_smem(const ift_ctx* c, int w) {
+  size_t m = 0;
+  for (int wp = 0; wp < 2; ++wp)
+    if (c->ks[wp].valid) m = std::max(m, c->ks[wp].smem_bytes(true, c->ku, c->kx, w));
+  return m;
+}
+
 ift_status plan_launch(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
   const int block = 32 * c->wpc;
@@ -235,6 +246,9 @@ ift_status plan_launch(ift_ctx* c, int wp) {
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
     const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->wpc);
+    if (smem > (size_t)c->smem_optin)
+      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", c->wpc, smem,
+                     c->smem_optin);
     cudaError_t e = ks.prepare(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
     const int bps = ks.blocks_per_sm(jac, block, smem);
@@ -307,6 +321,7 @@ void ift_config_default(ift_config* cfg) {
   cfg->tol = 1e-8;
   cfg->max_iters = 200;
   cfg->lm_init = IFT_INIT_PAPER;
+  cfg->contraction = IFT_CONTRACT_FP;
 }
 
 const char* ift_create_error(void) { return g_create_error.c_str(); }
@@ -328,6 +343,15 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   }
   if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32 && cfg->precision != IFT_MIXED) {
     g_create_error = "precision must be IFT_FP64, IFT_FP32 or IFT_MIXED";
+    return IFT_ERR_ARG;
+  }
+  if (cfg->contraction != IFT_CONTRACT_FP && cfg->contraction != IFT_CONTRACT_TF32 &&
+      cfg->contraction != IFT_CONTRACT_3XTF32) {
+    g_create_error = "contraction must be IFT_CONTRACT_FP, IFT_CONTRACT_TF32 or IFT_CONTRACT_3XTF32";
+    return IFT_ERR_ARG;
+  }
+  if (cfg->contraction != IFT_CONTRACT_FP && cfg->precision == IFT_FP64) {
+    g_create_error = "tensor-core contraction needs IFT_FP32 or IFT_MIXED";
     return IFT_ERR_ARG;
   }
   if (!(cfg->gamma > 1.0) || !(cfg->kappa >= 0.0) || !(cfg->eps_g > 0.0) || !(cfg->tol >= 0.0) ||
@@ -368,6 +392,7 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     return IFT_ERR_NOTIMPL;
   }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (stream) {
     c->stream = (cudaStream_t)stream;
   } else {
@@ -584,6 +609,10 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   CK(cudaStreamSynchronize(c->stream), "column sums");
   c->B = 0;  // batched weight sets are sized for the bases: set them again
   c->have_bases = true;
+  // default launch shapes that fit these bases: fewer warps per CTA for large k
+  for (int* w : {&c->wpc, &c->bwpc}) {
+    while (*w > 1 && shapes_smem(c, *w) > (size_t)c->smem_optin) *w /= 2;
+  }
   c->epoch++;
   return IFT_OK;
 }
@@ -980,6 +1009,9 @@ ift_status plan_batched(ift_ctx* c, int wp) {
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
     const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->bwpc);
+    if (smem > (size_t)c->smem_optin)
+      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", c->bwpc, smem,
+                     c->smem_optin);
     cudaError_t e = ks.prepare_batched(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel attributes");
     const int bps = ks.blocks_per_sm_batched(jac, block, smem);
@@ -1409,6 +1441,9 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
   auto ok_w = [](int w) { return w == 1 || w == 2 || w == 4; };
   if (!ok_w(warps) || !ok_w(batched_warps) || !(chunk == 4 || chunk == 8 || chunk == 16 || chunk == 32))
     return c->fail(IFT_ERR_ARG, "launch shapes must be warps in {1,2,4} and chunk in {4,8,16,32}");
+  if (c->have_bases && (shapes_smem(c, warps) > (size_t)c->smem_optin ||
+                        shapes_smem(c, batched_warps) > (size_t)c->smem_optin))
+    return c->fail(IFT_ERR_ARG, "these warps per CTA need more shared memory than a CTA may have for these bases");
   c->wpc = warps;
   c->bwpc = batched_warps;
   if (chunk != c->chunk) {

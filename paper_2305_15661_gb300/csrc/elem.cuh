@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "physics.cuh"
 
 namespace ift {
@@ -55,7 +57,71 @@ struct AsmArgs {
   double* partial;
   // optional: a device flag; when non-zero the kernel returns at once (a finished solve)
   const int* skip;
+  // T = float only: how H += rho A^T A is formed (0: FP32 FMA, 1: TF32 tensor cores,
+  // 2: 3xTF32 tensor cores, i.e. hi/lo splits of each operand, about FP32 accuracy)
+  int contraction;
 };
+
+// H += rho A^T A on the tensor cores (warp-level mma.m16n8k8, TF32 inputs, FP32
+// accumulation), upper triangle only. A is the warp's n_u x k row-major block in
+// shared memory; rows are the contraction index. A tile covers 16 rows r (the
+// columns of A read as A^T) by 8 columns b of H; only tiles that meet r <= b are
+// formed. SPLIT: each operand is split as hi + lo (both TF32) and the product
+// taken as hi*hi + hi*lo + lo*hi, which restores about FP32 accuracy.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int NU, bool SPLIT>
+__device__ __forceinline__ void syrk_upper_tf32(const float* A, int k, float* acc, float rho, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  constexpr int KS = (NU + 7) / 8;
+  const int mtiles = (k + 15) / 16, ntiles = (k + 7) / 8;
+  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * k + col] : 0.0f; };
+  for (int mt = 0; mt < mtiles; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+    for (int nt = 2 * mt; nt < ntiles; ++nt) {
+      const int bc = nt * 8 + g;
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int i0 = ks * 8 + t, i1 = i0 + 4;
+        const float av[4] = {ld(i0, r0), ld(i0, r1), ld(i1, r0), ld(i1, r1)};
+        const float bv[2] = {ld(i0, bc), ld(i1, bc)};
+        uint32_t ah[4], bh[2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ah[j] = to_tf32(av[j]);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) bh[j] = to_tf32(bv[j]);
+        if (SPLIT) {
+          uint32_t al[4], bl[2];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) al[j] = to_tf32(av[j] - __uint_as_float(ah[j]));
+#pragma unroll
+          for (int j = 0; j < 2; ++j) bl[j] = to_tf32(bv[j] - __uint_as_float(bh[j]));
+          mma_tf32(c, al, bh);
+          mma_tf32(c, ah, bl);
+        }
+        mma_tf32(c, ah, bh);
+      }
+      const int cb = nt * 8 + 2 * t;
+      const int rr[4] = {r0, r0, r1, r1}, cc[4] = {cb, cb + 1, cb, cb + 1};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (rr[j] <= cc[j] && cc[j] < k) acc[rr[j] * k + cc[j]] += rho * c[j];
+    }
+  }
+}
 
 template <class T, int PROB, int P>
 struct Tabs {
@@ -808,9 +874,32 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       // 6. columns of A_e (state, then mesh), all lanes on every stage
       C.jac_state(lane, bcs, ku, k);
       C.jac_geom(lane, mu, ku, kx, k, dist);
-      // 7. weighted contraction over the upper triangle: lane-owned pairs (r <= b)
+      // 7. weighted contraction over the upper triangle: lane-owned pairs (r <= b),
+      // or tensor-core tiles (FP32 contexts that ask for them)
       const T rT = (T)rho;
-      const int npairs = k * (k + 1) / 2;
+      bool simt_h = true;
+      if constexpr (std::is_same<T, float>::value) {
+        if (a.contraction != 0) {
+          __syncwarp();
+          if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.acc, rT, lane);
+          else syrk_upper_tf32<NU, false>(C.A, k, C.acc, rT, lane);
+          if (dist) {
+            // distortion block of the mesh columns, Eq. levmarq-elem
+            const int np = kx * (kx + 1) / 2;
+            for (int pidx = lane; pidx < np; pidx += 32) {
+              int r = 0, rem = pidx;
+              while (rem >= kx - r) {
+                rem -= kx - r;
+                ++r;
+              }
+              const int b = r + rem;
+              C.acc[(ku + r) * k + ku + b] += rT * (C.dNt[r] * C.dNt[b]);
+            }
+          }
+          simt_h = false;
+        }
+      }
+      const int npairs = simt_h ? k * (k + 1) / 2 : 0;
       for (int pidx = lane; pidx < npairs; pidx += 32) {
         const int r = pairs[2 * pidx], b = pairs[2 * pidx + 1];
         T s = T(0);

@@ -28,6 +28,9 @@ FP32 = 1
 MIXED = 2
 INIT_PAPER = 0
 INIT_GIVEN = 1
+CONTRACT_FP = 0
+CONTRACT_TF32 = 1
+CONTRACT_3XTF32 = 2
 
 
 class IFTError(RuntimeError):
@@ -39,7 +42,8 @@ class IFTError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("problem", ctypes.c_int), ("p", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("eps_g", ctypes.c_double),
-                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("lm_init", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("lm_init", ctypes.c_int),
+                ("contraction", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -154,13 +158,13 @@ class Context:
 
     def __init__(self, problem: int, p: int, precision: int = FP64, gamma: float = 1.4, kappa: float = 0.0,
                  eps_g: float = 1e-8, tol: float = 1e-8, max_iters: int = 200, lm_init: int = INIT_PAPER,
-                 stream=None):
+                 contraction: int = CONTRACT_FP, stream=None):
         lib = load()
         cfg = Config()
         lib.ift_config_default(ctypes.byref(cfg))
         cfg.problem, cfg.p, cfg.precision = problem, p, precision
         cfg.gamma, cfg.kappa, cfg.eps_g, cfg.tol = gamma, kappa, eps_g, tol
-        cfg.max_iters, cfg.lm_init = max_iters, lm_init
+        cfg.max_iters, cfg.lm_init, cfg.contraction = max_iters, lm_init, contraction
         h = ctypes.c_void_p()
         st = lib.ift_create(ctypes.byref(cfg), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
         if st != IFT_OK:

@@ -13,7 +13,9 @@ A_e^T A_e, A_e^T R_e, |R_e|^2. One fused multiply-add counts as 2 FLOPs.
     faces, per face point: two traces 4 n_t m, Roe flux C_roe and its 8 state
     derivatives 8 C_roe, test 2 n_t m, face Jacobian blocks 4 n_t^2 m^2.
 (b) reduction (the survey's contraction count plus g and J):
-    2 n_u k_u (n_u + n_u') + 2 n_u k_x n_x + 2 n_u k^2 + 2 n_u k + 2 n_u.
+    2 n_u k_u (n_u + n_u') + 2 n_u k_x n_x + n_u k (k + 1) + 2 n_u k + 2 n_u,
+    where n_u k (k + 1) is the symmetric product A_e^T A_e (its k (k + 1) / 2
+    distinct entries, each a length-n_u dot product).
 C_f = 20, C_A = 40, C_roe = 200 for Euler (operation counts of the pointwise
 routines); Burgers: C_f = 1, C_A = 0, C_roe = 12, plus the source
 (exp and 4 flops per point).
@@ -52,7 +54,7 @@ def flops_per_element(problem: int, p: int, ku: int, kx: int, jac: bool = True) 
     if jac:
         a += nq * (ca + 2 * d * d * m * m) + 2 * nq * d * nb * nb * m * m
         a += nf * nfq * (8 * croe + 4 * nt * nt * m * m)
-        b += 2 * nu * ku * (nu + nup) + 2 * nu * kx * nx + 2 * nu * k * k + 2 * nu * k
+        b += 2 * nu * ku * (nu + nup) + 2 * nu * kx * nx + nu * k * (k + 1) + 2 * nu * k
     return {"element": a, "reduction": b, "total": a + b}
 
 

@@ -126,10 +126,20 @@ def freestream_state(gamma: float, mach: float, alpha: float) -> np.ndarray:
 
 
 def _orthonormal_columns(A: np.ndarray) -> np.ndarray:
-    Q, R = np.linalg.qr(A)
-    s = np.sign(np.diag(R))
-    s[s == 0] = 1.0
-    return Q * s
+    """Q of A = QR with diag(R) > 0 (unique for full column rank). Tall matrices
+    use Cholesky QR applied twice (Gram matrix, Cholesky factor, triangular
+    solve), which is BLAS-3 and orthogonal to rounding for the well-conditioned
+    bases generated here; small ones use Householder QR."""
+    if A.shape[0] < 100000 or A.shape[1] == 0:
+        Q, R = np.linalg.qr(A)
+        s = np.sign(np.diag(R))
+        s[s == 0] = 1.0
+        return Q * s
+    Q = A
+    for _ in range(2):
+        L = np.linalg.cholesky(Q.T @ Q)  # Q^T Q = L L^T, R = L^T
+        Q = Q @ np.linalg.inv(L.T)
+    return Q
 
 
 # ---------------------------------------------------------------------------

@@ -91,3 +91,60 @@ def test_p3_k48_batched_sampled_queries_full_mesh():
         assert _fro(g["H"][q], r["H"]) < 1e-5
         assert _fro(np.concatenate([g["S"][q], g["T"][q]]), np.concatenate([r["S"], r["T"]])) < 1e-3
         assert abs(g["J"][q] - r["J"]) <= 1e-5 * r["J"]
+
+
+@pytest.mark.parametrize("contraction,tol", [(ift.CONTRACT_TF32, 5e-3), (ift.CONTRACT_3XTF32, 1e-5)])
+@pytest.mark.parametrize("p,ku,kx,kappa", [(2, 20, 4, 0.0), (3, 40, 8, 0.1), (1, 7, 3, 0.1)])
+def test_tensor_core_contraction(contraction, tol, p, ku, kx, kappa):
+    # H on the tensor cores: TF32 to its 10-bit mantissa, 3xTF32 to FP32 accuracy;
+    # S~, T~, J~ do not go through the tensor cores and equal the FP32 context's bit for bit.
+    # p = 1 has n_u = 12 rows (a ragged last 8-row step) and k = 10 (partial tiles).
+    wl = W.euler_workload(n=8, p=p, k_u=ku, k_x=kx, seed=23)
+    O = orc.Oracle.from_workload(wl, kappa=kappa)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0])
+    f32 = ift.Context.from_workload(wl, precision=ift.FP32, kappa=kappa)
+    tc = ift.Context.from_workload(wl, precision=ift.FP32, kappa=kappa, contraction=contraction)
+    a = f32.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    b = tc.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert _fro(b["H"], r["H"]) < tol
+    assert np.array_equal(b["H"], b["H"].T)
+    for key in ("S", "T"):
+        assert np.array_equal(a[key], b[key]), key
+    assert a["J"] == b["J"]
+
+
+def test_tensor_core_contraction_sparse_and_batched():
+    wl = W.euler_workload(n=12, p=2, k_u=16, k_x=4, seed=24, n_mu=3, mu_box=True)
+    sets = W.eq_weight_sets(wl, 3, seed=25, lo=40, hi=120)
+    O = orc.Oracle.from_workload(wl)
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32, contraction=ift.CONTRACT_3XTF32)
+    ctx.set_eq_weights(sets[0])
+    g = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0], rho_set=sets[0])
+    assert _fro(g["H"], r["H"]) < 1e-5
+    ctx.set_eq_weights_batched(sets)
+    ys, zs = np.stack([wl.w_eval] * 3), np.stack([wl.tau_eval] * 3)
+    gb = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    for q in range(3):
+        r = O.reduced(wl.Phi, wl.Psi, ys[q], zs[q], wl.mus[q], rho_set=sets[q])
+        assert _fro(gb["H"][q], r["H"]) < 1e-5
+
+
+def test_mixed_solve_with_tf32_contraction():
+    # H only steers the step: a mixed solve whose FP32 stage takes H from TF32 tensor
+    # cores converges to the FP64 oracle's optimum
+    wl = W.euler_workload(n=10, p=2, k_u=10, k_x=4, seed=21)
+    mu = wl.mus[0]
+    O = orc.Oracle.from_workload(wl)
+    ref = O.solve(wl.Phi, wl.Psi, mu, wl.Phi.T @ W.replicate_guess(wl, wl.U_guess), tol=1e-8)
+    ctx = ift.Context.from_workload(wl, precision=ift.MIXED, tol=1e-8, contraction=ift.CONTRACT_TF32)
+    g = ctx.solve_rom(mu)
+    assert g["status"] == 0 and g["fp32_iters"] > 0
+    _certify(O, wl, mu, None, g["w"], g["tau"], ref, 1e-8)
+
+
+def test_contraction_option_errors():
+    with pytest.raises(ift.IFTError):
+        ift.Context(ift.EULER2D, 2, precision=ift.FP64, contraction=ift.CONTRACT_TF32)
+    with pytest.raises(ift.IFTError):
+        ift.Context(ift.EULER2D, 2, precision=ift.FP32, contraction=7)
