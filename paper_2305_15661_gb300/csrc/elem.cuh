@@ -171,8 +171,9 @@ struct WarpLayout {
     odNt = put(kx + 1, sizeof(T));
     {
       // staging of the reduced-Jacobian passes: volume G (M ku) + F (DIM M ku), faces
-      // dU (2 M ku) + dH (M ku), mesh directions P (NQ DIM M kx) + dcof (4 kx)
-      size_t w1 = (size_t)(DIM + 1) * M * ku, w2 = (size_t)3 * M * ku, w3 = (size_t)NQ * DIM * M * kx + 4 * kx;
+      // dU (2 M ku) + dH (M ku), mesh directions E (NB M 4) + dcof (4 kx) + K (NF NT M 2)
+      size_t w1 = (size_t)(DIM + 1) * M * ku, w2 = (size_t)3 * M * ku,
+             w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
       oW = put(JAC ? w : 1, sizeof(T));
@@ -200,6 +201,18 @@ __host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps)
 // Pointwise stage and residual for one element whose U_e, U_e', x_e are staged.
 // Leaves Fh/fph/Ah (volume), Hf/Hp/Hm/Hn (faces), R (residual), and returns the
 // non-physical flag (warp-uniform).
+// Division of small non-negative ints by a divisor fixed for the whole kernel:
+// q = floor(e * m / 2^32) with m = ceil(2^32 / d) is exact while e * d < 2^32
+// (here e < 2^16, d <= 64), one multiply-high instead of a division sequence.
+struct FastDiv {
+  uint32_t d, m;
+  __device__ void init(int dv) {
+    d = (uint32_t)dv;
+    m = (dv > 1) ? (0xFFFFFFFFu / d + 1u) : 0u;
+  }
+  __device__ __forceinline__ int div(int e) const { return d > 1 ? (int)__umulhi((uint32_t)e, m) : e; }
+};
+
 template <class T, int PROB, int P, bool JAC>
 struct ElemCore {
   using Dd = Disc<PROB, P>;
@@ -215,9 +228,12 @@ struct ElemCore {
   T detJ;
   T nt[3][2];    // scaled face normals (2-D)
   double x0d, x1d;  // 1-D end points
+  FastDiv dku, dkx;  // division by k_u and k_x in the lane loops
 
   __device__ void carve(unsigned char* base, int ku, int kx) {
     WarpLayout<T, PROB, P, JAC> L(ku, kx);
+    dku.init(ku > 0 ? ku : 1);
+    dkx.init(kx > 0 ? kx : 1);
     xe = (double*)(base + L.oxe);
     Psie = (double*)(base + L.oPsie);
     dN = (double*)(base + L.odN);
@@ -574,7 +590,7 @@ struct ElemCore {
   // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
   __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
     for (int e = lane; e < NU * ku; e += 32) {
-      const int row = e / ku, c = e - row * ku;
+      const int row = dku.div(e), c = e - row * ku;
       A[row * k + c] = T(0);
     }
     T* G = W;
@@ -582,7 +598,7 @@ struct ElemCore {
     for (int q = 0; q < NQ; ++q) {
       __syncwarp();
       for (int e = lane; e < M * ku; e += 32) {
-        const int b = e / ku, c = e - b * ku;
+        const int b = dku.div(e), c = e - b * ku;
         T s = T(0);
 #pragma unroll
         for (int j = 0; j < NB; ++j) s += B[q * NB + j] * Phie[(j * M + b) * ku + c];
@@ -590,7 +606,7 @@ struct ElemCore {
       }
       __syncwarp();
       for (int e = lane; e < DIM * M * ku; e += 32) {
-        const int ra = e / ku, c = e - ra * ku;
+        const int ra = dku.div(e), c = e - ra * ku;
         const T* ah = &Ah[(q * DIM * M + ra) * M];
         T s = T(0);
 #pragma unroll
@@ -599,12 +615,12 @@ struct ElemCore {
       }
       __syncwarp();
       for (int e = lane; e < NU * ku; e += 32) {
-        const int row = e / ku, c = e - row * ku;
+        const int row = dku.div(e), c = e - row * ku;
         const int i = row / M, a = row - i * M;
-        T s = T(0);
+        T s = A[row * k + c];
 #pragma unroll
-        for (int r = 0; r < DIM; ++r) s += D[(r * NQ + q) * NB + i] * F[(r * M + a) * ku + c];
-        A[row * k + c] -= s;
+        for (int r = 0; r < DIM; ++r) s -= D[(r * NQ + q) * NB + i] * F[(r * M + a) * ku + c];
+        A[row * k + c] = s;
       }
     }
     T* dU = W;                // [2][M][ku]: interior, exterior
@@ -614,8 +630,8 @@ struct ElemCore {
       const signed char bt = bcs[kf];
       __syncwarp();
       for (int e = lane; e < 2 * M * ku; e += 32) {
-        const int side = e / (M * ku), rem = e - side * M * ku;
-        const int b = rem / ku, c = rem - b * ku;
+        const int sb = dku.div(e), c = e - sb * ku;
+        const int side = sb / M, b = sb - side * M;
         T s = T(0);
         if (side == 0 || bt == 2) {
 #pragma unroll
@@ -632,7 +648,7 @@ struct ElemCore {
       }
       __syncwarp();
       for (int e = lane; e < M * ku; e += 32) {
-        const int a = e / ku, c = e - a * ku;
+        const int a = dku.div(e), c = e - a * ku;
         const T* hp = &Hp[(pt * M + a) * M];
         const T* hm = &Hm[(pt * M + a) * M];
         T s = T(0);
@@ -642,8 +658,8 @@ struct ElemCore {
       }
       __syncwarp();
       for (int e = lane; e < NT * M * ku; e += 32) {
-        const int j = e / (M * ku), rem = e - j * M * ku;
-        const int a = rem / ku, c = rem - a * ku;
+        const int ja = dku.div(e), c = e - ja * ku;
+        const int j = ja / M, a = ja - j * M;
         const int node = (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
         A[(node * M + a) * k + c] += Lt[f * NT + j] * dH[a * ku + c];
       }
@@ -653,12 +669,15 @@ struct ElemCore {
 
   // Step 6, mesh columns: A[row][ku + c] = (dR_e/dx_e Psi_e)[row][c], c < kx.
   // Volume: the flux enters through the cofactor matrix, linear in x_e, so the
-  // direction dx = Psi_e[:, c] gives dF_r = sum_d f_d dcof[d][r] (staged in W as P);
-  // faces: dH = Hn dn with the scaled-normal change dn; Burgers: the source only.
+  // direction dx = Psi_e[:, c] gives dF_r = sum_d f_d dcof[d][r]; the quadrature
+  // sum is taken once per element, E[i][a][r][d] = sum_q D_r[q][i] f_d(U_q)_a
+  // (staged in W), and each column is then sum_{r,d} dcof[c][d][r] E[i][a][r][d].
+  // Faces: dH = Hn dn with the scaled-normal change dn; Burgers: the source only.
   __device__ void jac_geom(int lane, const double* mu, int ku, int kx, int k, bool dist) {
     if (kx == 0) return;
-    T* Pg = W;
-    T* dcof = W + NQ * DIM * M * kx;  // [kx][4]
+    T* E = W;                  // [NB][M][DIM][DIM]
+    T* dcof = W + NB * M * 4;  // [kx][4]
+    T* K = dcof + 4 * kx;      // [NF][NT][M][2]: sum_f fw[f] Lt[f][j] Hn[kf, f][a][d]
     if (DIM == 2) {
       for (int c = lane; c < kx; c += 32) {
         const double* d = &Psie[c];  // column c, stride kx
@@ -669,21 +688,31 @@ struct ElemCore {
         dcof[c * 4 + 2] = -dj01;
         dcof[c * 4 + 3] = dj00;
       }
-      __syncwarp();
-      for (int e = lane; e < NQ * DIM * M * kx; e += 32) {
-        const int qra = e / kx, c = e - qra * kx;
-        const int q = qra / (DIM * M), ra = qra - q * DIM * M;
-        const int r = ra / M, a = ra - r * M;
-        Pg[e] = fph[(q * 2 + 0) * M + a] * dcof[c * 4 + 0 * 2 + r] + fph[(q * 2 + 1) * M + a] * dcof[c * 4 + 2 + r];
+      for (int e = lane; e < NB * M * 4; e += 32) {
+        const int ia = e >> 2, rd = e & 3, r = rd >> 1, d = rd & 1;
+        const int i = ia / M, a = ia - i * M;
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s += D[(r * NQ + q) * NB + i] * fph[(q * 2 + d) * M + a];
+        E[e] = s;
+      }
+      for (int e = lane; e < NF * NT * M * 2; e += 32) {
+        const int kja = e >> 1, d = e & 1;
+        const int kf = kja / (NT * M), ja = kja - kf * NT * M;
+        const int j = ja / M, a = ja - j * M;
+        T s = T(0);
+#pragma unroll
+        for (int f = 0; f < NFQ; ++f) s += fw[f] * Lt[f * NT + j] * Hn[((kf * NFQ + f) * M + a) * 2 + d];
+        K[e] = s;
       }
       __syncwarp();
       for (int e = lane; e < NU * kx; e += 32) {
-        const int row = e / kx, c = e - row * kx;
+        const int row = dkx.div(e), c = e - row * kx;
         const int i = row / M, a = row - i * M;
-        T s = T(0);
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-          for (int r = 0; r < DIM; ++r) s -= D[(r * NQ + q) * NB + i] * Pg[((q * DIM + r) * M + a) * kx + c];
+        const T* er = &E[row * 4];
+        const T* dc = &dcof[c * 4];
+        // dcof[c][d*2 + r] pairs with E[i][a][r][d]
+        T s = -(er[0] * dc[0] + er[1] * dc[2] + er[2] * dc[1] + er[3] * dc[3]);
         // faces through the nodes of this row
 #pragma unroll
         for (int kf = 0; kf < NF; ++kf) {
@@ -693,18 +722,15 @@ struct ElemCore {
           const double* d = &Psie[c];
           const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
           const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
-#pragma unroll
-          for (int f = 0; f < NFQ; ++f) {
-            const int pt = kf * NFQ + f;
-            s += fw[f] * Lt[f * NT + j] * (Hn[(pt * M + a) * 2 + 0] * dnx + Hn[(pt * M + a) * 2 + 1] * dny);
-          }
+          const T* kk = &K[((kf * NT + j) * M + a) * 2];
+          s += kk[0] * dnx + kk[1] * dny;
         }
         A[row * k + ku + c] = s;
       }
     } else {
       const T mu0 = (T)mu[0];
       for (int e = lane; e < NU * kx; e += 32) {
-        const int i = e / kx, c = e - i * kx;
+        const int i = dkx.div(e), c = e - i * kx;
         const T dx0 = (T)Psie[0 * kx + c], ddet = (T)(Psie[1 * kx + c] - Psie[0 * kx + c]);
         T s = T(0);
 #pragma unroll
@@ -820,7 +846,7 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       const int k2 = a.nbr_face[(long)e * NF + kf];
       const int rowlen = M * ku;
       for (int i = lane; i < NT * rowlen; i += 32) {
-        const int j = i / rowlen, rem = i - j * rowlen;
+        const int j = C.dku.div(i) / M, rem = i - j * rowlen;
         T v = T(0);
         if (e2 >= 0) {
           // neighbour trace node at position j along this face = its node NT-1-j on face k2
@@ -832,7 +858,7 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       }
     }
     for (int i = lane; i < NXE * kx; i += 32) {
-      const int r = i / kx, c = i - r * kx;
+      const int r = C.dkx.div(i), c = i - r * kx;
       const int v = r / DIM, d = r - v * DIM;
       C.Psie[i] = a.Psi[((size_t)vv[v] * DIM + d) * kx + c];
     }

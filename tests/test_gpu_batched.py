@@ -59,7 +59,7 @@ def test_batched_solve_matches_oracle_and_single_solves():
         if s1["iters"] == inf["iters"] and s1["init_iters"] == inf["init_iters"]:
             assert d <= 1e-10
         else:  # the two kernels sum elements in different orders (see check_solve_against_oracle)
-            assert abs(s1["iters"] + s1["init_iters"] - inf["iters"] - inf["init_iters"]) <= 1 and d <= 1e-6
+            assert abs(s1["iters"] + s1["init_iters"] - inf["iters"] - inf["init_iters"]) <= 2 and d <= 1e-6
 
 
 def test_batched_config3_full_size():

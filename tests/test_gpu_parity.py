@@ -225,10 +225,11 @@ def _solve_pair(wl, tol, rho_set=None):
 
 def check_solve_against_oracle(g, r, O, wl, mu, rho_set, tol):
     """Same iteration count: the same trajectory, so (w, tau) agree to 1e-10.
-    With linear convergence the last iteration is decided by how close |[S;T]| lands
-    to the stopping threshold (or J to the sufficient-decrease threshold); when that
-    margin is at rounding level two FP64 implementations can stop one step apart. Then
-    the oracle itself must find the GPU's point converged (its own |[S;T]| there within
+    With linear convergence the last iterations can sit at the rounding floor of J
+    (J changing by ~1e-16 relative per step), where the sufficient-decrease test and
+    hence the damping updates are decided by rounding; two FP64 implementations that
+    sum in different orders can then stop one or two steps apart. In that case the
+    oracle itself must find the GPU's point converged (its own |[S;T]| there within
     1.5x the threshold) and the two points agree to the stopping tolerance."""
     assert g["status"] == 0 and r["status"] == 0, (g, r["status"])
     z = np.concatenate([g["w"], g["tau"]])
@@ -239,7 +240,7 @@ def check_solve_against_oracle(g, r, O, wl, mu, rho_set, tol):
         assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr), np.linalg.norm(z - zr) / np.linalg.norm(zr)
         assert abs(g["J"] - r["J"]) <= 1e-12 * r["J"]
     else:
-        assert abs((g["init_iters"] + g["iters"]) - (r["init_iters"] + r["iters"])) <= 1, (g, r)
+        assert abs((g["init_iters"] + g["iters"]) - (r["init_iters"] + r["iters"])) <= 2, (g, r)
         rr = O.reduced(wl.Phi, wl.Psi, g["w"], g["tau"], mu, rho_set=rho_set)
         gn = np.linalg.norm(np.concatenate([rr["S"], rr["T"]]))
         assert gn <= 1.5 * tol * max(1.0, r["g0"]), (gn, r["g0"])
