@@ -375,9 +375,14 @@ def run_batched(args):
 
     dev = torch.device("cuda", 0)
     ift.load()
-    B = 256
-    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
-    sets = W.eq_weight_sets(wl, B, seed=3)
+    if args.config == 4:  # p = 3, 80,000 elements, k_u = 40, k_x = 8, 1,024 queries
+        B = 1024
+        wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4, n_mu=B, mu_box=True)
+        sets = W.eq_weight_sets(wl, B, seed=5)
+    else:  # p = 2, 20,000 elements, k_u = 20, k_x = 4, 256 queries
+        B = 256
+        wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
+        sets = W.eq_weight_sets(wl, B, seed=3)
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
@@ -406,16 +411,39 @@ def run_batched(args):
         ms.append(e0.elapsed_time(e1))
     conv = int((st == 0).sum().item())
     evals = sum(len(sets[q][0]) * (1 + info["info"][q]["trials"]) for q in range(B))
-    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    fl = perfmodel.flops_per_element(2, wl.p, wl.ku, wl.kx)["total"]
     t = sum(ms) / 1e3
-    print(json.dumps({"mode": "batched", "precision": args.precision, "contraction": args.contraction,
-                      "queries": B, "launch_shapes": shapes,
-                      "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
-                      "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
-                      "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
-                      "achieved_tflops": evals * fl * args.steps / t / 1e12,
-                      "mean_iters": float(np.mean([i["init_iters"] + i["iters"] + i["fp32_iters"] for i in info["info"]])),
-                      "mean_fp64_iters": float(np.mean([i["iters"] for i in info["info"]]))}))
+    out = {"mode": "batched", "config": args.config, "elements": wl.n_elems, "p": wl.p,
+           "k_u": wl.ku, "k_x": wl.kx, "precision": args.precision, "contraction": args.contraction,
+           "queries": B, "launch_shapes": shapes,
+           "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
+           "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
+           "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
+           "achieved_tflops": evals * fl * args.steps / t / 1e12,
+           "mean_iters": float(np.mean([i["init_iters"] + i["iters"] + i["fp32_iters"] for i in info["info"]])),
+           "mean_fp64_iters": float(np.mean([i["iters"] for i in info["info"]]))}
+    if args.compare_fp64 and prec != ift.FP64:
+        # the same queries solved with FP64 assemblies throughout: converged points and objectives
+        ref_ctx = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
+        ref_ctx.set_eq_weights_batched(sets)
+        try:
+            ref_ctx.set_launch_shapes(*shapes)
+        except ift.IFTError:
+            pass  # the FP64 kernels do not fit these warps: keep their default shapes
+        t0 = time.perf_counter()
+        ref = ref_ctx.solve_rom_batched(wl.mus)
+        out["fp64_batch_s"] = time.perf_counter() - t0
+        ok = np.array([a["status"] == 0 and b["status"] == 0 for a, b in zip(info["info"], ref["info"])])
+        z1 = np.concatenate([info["w"], info["tau"]], axis=1)[ok]
+        z0 = np.concatenate([ref["w"], ref["tau"]], axis=1)[ok]
+        J1 = np.array([i["J"] for i in info["info"]])[ok]
+        J0 = np.array([i["J"] for i in ref["info"]])[ok]
+        dz = np.linalg.norm(z1 - z0, axis=1) / np.linalg.norm(z0, axis=1)
+        out["vs_fp64"] = {"both_converged": int(ok.sum()), "median_rel_dz": float(np.median(dz)),
+                          "max_rel_dz": float(np.max(dz)), "max_rel_dJ": float(np.max(np.abs(J1 - J0) / J0)),
+                          "fp64_mean_iters": float(np.mean([i["init_iters"] + i["iters"] for i in ref["info"]]))}
+        ref_ctx.close()
+    print(json.dumps(out))
     ctx.close()
     return 0
 
@@ -556,6 +584,53 @@ def run_warmstart(args):
     return 0
 
 
+def run_greedy(args):
+    """Greedy search (Eq. greedy0) over 256 candidate parameters on the 20,000-element
+    mesh: batched hyperreduced solves with one shared weight set, then the full HDM
+    residual norm (every element, no Jacobians) at each solution."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+    from paper_2305_15661_gb300 import workloads as W
+
+    ift.load()
+    B = args.candidates
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+    rho = W.eq_weight_sets(wl, 1, seed=3, lo=400, hi=401)[0]
+    mus = W.mu_box_samples(7, 1, B)
+    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
+    stream = torch.cuda.Stream(device=torch.device("cuda", 0))
+    ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
+                                    contraction=_contraction(args))
+    ctx.set_eq_weights_batched([rho] * B)
+    shapes = ctx.autotune(mus[0], wl.w_eval, wl.tau_eval)
+    res = ctx.solve_rom_batched(mus)
+    ys, zs = res["w"], res["tau"]
+    for _ in range(args.warmup):
+        ctx.hdm_residual_norms(mus, ys, zs)
+    ts, tn = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = ctx.solve_rom_batched(mus)
+        t1 = time.perf_counter()
+        norms = ctx.hdm_residual_norms(mus, res["w"], res["tau"])
+        t2 = time.perf_counter()
+        ts.append(t1 - t0)
+        tn.append(t2 - t1)
+    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx, jac=False)["total"]
+    tnm = statistics.median(tn)
+    print(json.dumps({"mode": "greedy", "precision": args.precision, "candidates": B, "elements": wl.n_elems,
+                      "rho_nnz": int(len(rho[0])), "launch_shapes": shapes,
+                      "solve_s": statistics.median(ts), "indicator_s": tnm,
+                      "indicator_element_evals_per_s": B * wl.n_elems / tnm,
+                      "indicator_tflops": B * wl.n_elems * fl / tnm / 1e12, "flops_per_element_residual": fl,
+                      "argmax": int(np.argmax(norms)), "max_norm": float(np.max(norms)),
+                      "median_norm": float(np.median(norms)),
+                      "converged": int(sum(i["status"] == 0 for i in res["info"]))}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -563,17 +638,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy"], default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly, batched and warmstart")
     ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32"], default="fp",
                     help="FP32/mixed contexts: form H with FP32 FMAs, TF32 or 3xTF32 tensor cores")
-    ap.add_argument("--config", type=int, choices=[2, 4], default=2,
-                    help="--mode assembly: 2 = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, k 40+8")
+    ap.add_argument("--config", type=int, choices=[2, 3, 4], default=2,
+                    help="--mode assembly: 2 (or 3) = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, "
+                         "k 40+8; --mode batched: 3 = 256 queries on the first mesh, 4 = 1,024 on the second")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="--mode batched: also solve the queries with FP64 assemblies and compare")
     ap.add_argument("--autotune", action="store_true", help="--mode assembly: tune the launch shape first")
     ap.add_argument("--train-solves", type=int, default=2048, help="--mode warmstart: training solves")
     ap.add_argument("--queries", type=int, default=4096, help="--mode warmstart: served queries")
+    ap.add_argument("--candidates", type=int, default=256, help="--mode greedy: candidate parameters")
     ap.add_argument("--epochs", type=int, default=1500, help="--mode warmstart: training epochs")
     ap.add_argument("--single-sample", type=int, default=32, help="--mode warmstart: one-query FP64 solves timed")
     args = ap.parse_args()
@@ -587,6 +666,8 @@ def main():
         return run_batched(args)
     if args.mode == "warmstart":
         return run_warmstart(args)
+    if args.mode == "greedy":
+        return run_greedy(args)
     return run_ours(args)
 
 

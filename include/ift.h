@@ -205,19 +205,35 @@ ift_status ift_solve_rom_batched_dev(ift_ctx* ctx, const double* mu, double* y, 
                                      void* stream);
 
 /* Launch-shape autotuner (not part of the paper's method). Times the fused
-   assembly of this context's workload at (mu, y, z) for 1, 2 and 4 warps per CTA
-   and, when batched weights are set, the batched assembly for chunk sizes 4, 8,
-   16, 32 elements x 1, 2, 4 warps per CTA (scored on a full batch plus a tail with
-   2% of the queries running), keeps the fastest shapes in the context and writes
-   them to chosen[0..2] = (warps per CTA, batched warps per CTA, chunk size).
-   Results change only by reduction order (all shapes compute the same sums).
-   Default shapes without tuning: 2, 2, 8. */
+   assembly of this context's workload at (mu, y, z) for 1, 2 and 4 warps per CTA,
+   separately for each precision the context runs (mixed contexts run FP32 and
+   FP64 kernels) and, when batched weights are set, the batched assembly for chunk
+   sizes 4, 8, 16, 32 elements x 1, 2, 4 warps per CTA (scored on a full batch plus
+   a tail with 2% of the queries running; the chunk size on the precision that
+   dominates a solve, FP64 for mixed contexts), keeps the fastest shapes in the
+   context and writes the evaluation precision's to chosen[0..2] = (warps per CTA,
+   batched warps per CTA, chunk size). Shapes that need more shared memory than a
+   CTA may have are skipped. Results change only by reduction order (all shapes
+   compute the same sums). Default shapes without tuning: 2, 2, 8, fewer warps
+   where the bases need more shared memory. */
 ift_status ift_autotune(ift_ctx* ctx, const double* mu, const double* y, const double* z, int32_t* chosen);
 /* Sets the launch shapes directly (for instance, shapes an earlier ift_autotune
    chose for the same workload): warps and batched_warps in {1, 2, 4}, chunk in
-   {4, 8, 16, 32}; anything else is IFT_ERR_ARG. Results change only by
+   {4, 8, 16, 32}; anything else, or warps whose shared memory does not fit the
+   evaluation precision's kernels, is IFT_ERR_ARG. The FP64 kernels of a mixed
+   context take the most warps up to these that fit. Results change only by
    reduction order. */
 ift_status ift_set_launch_shapes(ift_ctx* ctx, int warps, int batched_warps, int chunk);
+
+/* HDM residual norms at B points (the greedy-search indicator of Eq. greedy0):
+   norms[q] = |R(Phi y_q, X + Psi z_q; mu_q)|_2, the full DG residual (every
+   element, no empirical-quadrature weights, no distortion term) at the state and
+   mesh of query q. mu (B x n_mu), y (B x k_u), z (B x k_x) in, norms (B) out; host
+   pointers. A non-physical point gives +inf. FP64 contexts evaluate in FP64,
+   FP32 and mixed contexts in FP32 (sums of squares in FP64). The greedy search
+   takes the argmax over candidates of these norms at their hyperreduced solutions. */
+ift_status ift_hdm_residual_norms(ift_ctx* ctx, int B, const double* mu, const double* y, const double* z,
+                                  double* norms);
 
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
    cannot call cudaMalloc when they need the reduced system: code that is

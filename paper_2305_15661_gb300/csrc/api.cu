@@ -41,6 +41,7 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
                                        const double* z0, int phase);
 __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum);
 __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
+__global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 }  // namespace ift
 
 using namespace ift;
@@ -114,7 +115,7 @@ struct ift_ctx {
   int plan_epoch[2] = {-1, -1};
   // launch shapes (set by ift_autotune): warps per CTA of the single-query and the
   // batched element kernels, elements per chunk of the batched path
-  int wpc = kWarpsPerCta, bwpc = kWarpsPerCta, chunk = kChunk;
+  int wpc[2] = {kWarpsPerCta, kWarpsPerCta}, bwpc[2] = {kWarpsPerCta, kWarpsPerCta}, chunk = kChunk;
   // batched queries (per-query weight sets split into chunks)
   std::vector<int64_t> h_offsets;  // host copy of the per-query offsets (to re-chunk)
   int B = 0;
@@ -131,6 +132,12 @@ struct ift_ctx {
   LMState* d_blm = nullptr;
   int* d_active = nullptr;
   double* d_colsum = nullptr;
+  // HDM residual norms (greedy-search indicator): points, parameters, chunk partials, norms
+  double* d_rn_pts = nullptr;
+  double* d_rn_mu = nullptr;
+  double* d_rn_part = nullptr;
+  double* d_rn_norms = nullptr;
+  size_t rn_cap_B = 0, rn_cap_parts = 0;
   int bplan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t bplan_smem[2][2] = {{0, 0}, {0, 0}};
   int bplan_epoch[2] = {-1, -1};
@@ -231,30 +238,27 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
 // Grid and shared memory of the element kernels for the current bases and
 // weights: as many CTAs as fit on the GPU at once, but no more than the items
 // need; the shape is fixed per configuration, so sums are reproducible.
-// Largest dynamic shared memory of the element kernels of this context for w warps per CTA.
-size_t shapes_smem(const ift_ctx* c, int w) {
-  size_t m = 0;
-  for (int wp = 0; wp < 2; ++wp)
-    if (c->ks[wp].valid) m = std::max(m, c->ks[wp].smem_bytes(true, c->ku, c->kx, w));
-  return m;
+// Dynamic shared memory of the fused element kernel of precision wp for w warps per CTA.
+size_t shapes_smem(const ift_ctx* c, int wp, int w) {
+  return c->ks[wp].valid ? c->ks[wp].smem_bytes(true, c->ku, c->kx, w) : 0;
 }
 
 ift_status plan_launch(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * c->wpc;
+  const int wpc = c->wpc[wp], block = 32 * wpc;
   const long items = (c->nnz < 0) ? c->n_elems : c->nnz;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->wpc);
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, wpc);
     if (smem > (size_t)c->smem_optin)
-      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", c->wpc, smem,
+      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", wpc, smem,
                      c->smem_optin);
     cudaError_t e = ks.prepare(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
     const int bps = ks.blocks_per_sm(jac, block, smem);
     if (bps < 1) return c->fail(IFT_ERR_CUDA, "element kernel does not fit on an SM (%zu bytes shared)", smem);
     long grid = (long)c->sm_count * bps;
-    const long need = (items + c->wpc - 1) / c->wpc;
+    const long need = (items + wpc - 1) / wpc;
     if (grid > need) grid = need;
     if (grid > c->max_parts) grid = c->max_parts;
     if (grid < 1) grid = 1;
@@ -262,7 +266,7 @@ ift_status plan_launch(ift_ctx* c, int wp) {
     c->plan_smem[wp][j] = smem;
   }
   // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
-  const size_t ismem = ks.smem_bytes(true, 1, 0, c->wpc);
+  const size_t ismem = ks.smem_bytes(true, 1, 0, wpc);
   if (ismem > c->plan_smem[wp][1]) {
     cudaError_t e = ks.prepare(true, ismem);
     if (e != cudaSuccess) return c->cuda_fail(e, "kernel attributes");
@@ -280,7 +284,7 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
     if (st != IFT_OK) return st;
   }
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * c->wpc;
+  const int block = 32 * c->wpc[wp];
   const int grid = c->plan_grid[wp][jac ? 1 : 0];
   const size_t smem = c->plan_smem[wp][jac ? 1 : 0];
   cudaError_t e;
@@ -475,6 +479,10 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_blm);
   dfree(c->d_active);
   dfree(c->d_colsum);
+  dfree(c->d_rn_pts);
+  dfree(c->d_rn_mu);
+  dfree(c->d_rn_part);
+  dfree(c->d_rn_norms);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return IFT_OK;
@@ -610,9 +618,9 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   c->B = 0;  // batched weight sets are sized for the bases: set them again
   c->have_bases = true;
   // default launch shapes that fit these bases: fewer warps per CTA for large k
-  for (int* w : {&c->wpc, &c->bwpc}) {
-    while (*w > 1 && shapes_smem(c, *w) > (size_t)c->smem_optin) *w /= 2;
-  }
+  for (int wp = 0; wp < 2; ++wp)
+    for (int* w : {&c->wpc[wp], &c->bwpc[wp]})
+      while (*w > 1 && shapes_smem(c, wp, *w) > (size_t)c->smem_optin) *w /= 2;
   c->epoch++;
   return IFT_OK;
 }
@@ -717,11 +725,11 @@ ift_status ift_element_eval(ift_ctx* c, const double* mu, const double* U, const
   cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s);
   const int wp = c->eval_wp();
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * c->wpc;
-  const size_t smem = ks.smem_bytes(true, 1, 0, c->wpc);
+  const int wpc = c->wpc[wp], block = 32 * wpc;
+  const size_t smem = ks.smem_bytes(true, 1, 0, wpc);
   e = ks.prepare(true, c->have_bases && c->plan_smem[wp][1] > smem ? c->plan_smem[wp][1] : smem);
   if (e == cudaSuccess) {
-    const int grid = (int)((n + c->wpc - 1) / c->wpc);
+    const int grid = (int)((n + wpc - 1) / wpc);
     if (wp == 1) {
       AsmArgs<float> a = make_args<float>(c, c->d_Phi32, c->d_w, c->d_tau, c->d_mu, true, nullptr);
       a.ku = 1;
@@ -1005,19 +1013,19 @@ namespace {
 
 ift_status plan_batched(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * c->bwpc;
+  const int bwpc = c->bwpc[wp], block = 32 * bwpc;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, c->bwpc);
+    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, bwpc);
     if (smem > (size_t)c->smem_optin)
-      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", c->bwpc, smem,
+      return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", bwpc, smem,
                      c->smem_optin);
     cudaError_t e = ks.prepare_batched(jac, smem);
     if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel attributes");
     const int bps = ks.blocks_per_sm_batched(jac, block, smem);
     if (bps < 1) return c->fail(IFT_ERR_CUDA, "batched kernel does not fit on an SM (%zu bytes shared)", smem);
     long grid = (long)c->sm_count * bps;
-    const long need = (c->n_chunks + c->bwpc - 1) / c->bwpc;
+    const long need = (c->n_chunks + bwpc - 1) / bwpc;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     c->bplan_grid[wp][j] = (int)grid;
@@ -1035,7 +1043,7 @@ ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long ws
     if (st != IFT_OK) return st;
   }
   const KernelSet& ks = c->ks[wp];
-  const int block = 32 * c->bwpc;
+  const int block = 32 * c->bwpc[wp];
   const int j = jac ? 1 : 0;
   BatchArgs b;
   b.chunk_start = c->d_chunk_start;
@@ -1067,6 +1075,8 @@ ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long ws
   return IFT_OK;
 }
 
+// The batched loop body in working precision wp: assemble every unfinished query,
+// reduce per query, one LM step per query, loop condition.
 ift_status enqueue_batched_body(ift_ctx* c, int wp, cudaStream_t s, unsigned long long handle, int use_cond) {
   const double* trial = (const double*)((char*)c->d_blm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_blm + offsetof(LMState, done));
@@ -1121,6 +1131,10 @@ ift_status run_batched_stage(ift_ctx* c, int wp, cudaStream_t s) {
   return IFT_OK;
 }
 
+// Mixed solves run the FP32 stage of every query, then the FP64 stage of every
+// query. (Moving each query to FP64 on its own, with both kernels in every loop
+// body, measured slower on the hyperreduced batch: the second launch and chunk
+// scan per body cost more than the overlap of the two stages' tails saved.)
 ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
   if (c->cfg.precision == IFT_FP64) return run_batched_stage(c, 0, s);
   ift_status st = run_batched_stage(c, 1, s);
@@ -1318,6 +1332,77 @@ ift_status ift_solve_rom_batched_dev(ift_ctx* c, const double* mu, double* y, do
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// HDM residual norms at many points: the greedy-search indicator (Eq. greedy0).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNormChunk = 64;  // elements per warp work item
+
+ift_status launch_residual_norms(ift_ctx* c, int B, const double* d_pts, const double* d_mu, double* d_norms,
+                                 cudaStream_t s) {
+  const int wp = c->eval_wp();
+  const KernelSet& ks = c->ks[wp];
+  const int warps = 4, block = 32 * warps;
+  const size_t smem = ks.smem_bytes(false, c->ku, c->kx, warps);
+  if (smem > (size_t)c->smem_optin) return c->fail(IFT_ERR_ARG, "residual-norm kernel does not fit (%zu bytes)", smem);
+  cudaError_t e = ks.prepare_norms(smem);
+  if (e != cudaSuccess) return c->cuda_fail(e, "norm kernel attributes");
+  const int bps = ks.blocks_per_sm_norms(block, smem);
+  if (bps < 1) return c->fail(IFT_ERR_CUDA, "residual-norm kernel does not fit on an SM");
+  const int nchunk = (int)((c->n_elems + kNormChunk - 1) / kNormChunk);
+  const size_t parts = (size_t)B * nchunk;
+  if (parts > c->rn_cap_parts) {
+    CK(dalloc(c->d_rn_part, parts), "alloc norm partials");
+    c->rn_cap_parts = parts;
+  }
+  long grid = (long)c->sm_count * bps;
+  const long need = ((long)parts + warps - 1) / warps;
+  if (grid > need) grid = need;
+  const int k = c->ku + c->kx;
+  if (wp == 1) {
+    AsmArgs<float> a = make_args<float>(c, c->d_Phi32, d_pts, d_pts + c->ku, d_mu, true, nullptr);
+    e = ks.residual_norms(&a, d_pts, k, d_mu, 2, B, nchunk, kNormChunk, c->d_rn_part, (int)grid, block, smem, s);
+  } else {
+    AsmArgs<double> a = make_args<double>(c, c->d_Phi, d_pts, d_pts + c->ku, d_mu, true, nullptr);
+    e = ks.residual_norms(&a, d_pts, k, d_mu, 2, B, nchunk, kNormChunk, c->d_rn_part, (int)grid, block, smem, s);
+  }
+  if (e != cudaSuccess) return c->cuda_fail(e, "residual-norm kernel launch");
+  residual_norms_finish_kernel<<<(B + 127) / 128, 128, 0, s>>>(c->d_rn_part, B, nchunk, d_norms);
+  CK(cudaGetLastError(), "residual-norm finish");
+  return IFT_OK;
+}
+
+}  // namespace
+
+extern "C" ift_status ift_hdm_residual_norms(ift_ctx* c, int B, const double* mu, const double* y, const double* z,
+                                             double* norms) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (B < 1 || !mu || !y || (c->kx > 0 && !z) || !norms) return c->fail(IFT_ERR_ARG, "bad argument");
+  const int ku = c->ku, kx = c->kx, k = ku + kx, nmu = (c->dim == 1) ? 1 : 2;
+  cudaStream_t s = c->stream;
+  if ((size_t)B > c->rn_cap_B) {
+    CK(dalloc(c->d_rn_pts, (size_t)B * k), "alloc norm points");
+    CK(dalloc(c->d_rn_mu, (size_t)B * 2), "alloc norm parameters");
+    CK(dalloc(c->d_rn_norms, (size_t)B), "alloc norms");
+    c->rn_cap_B = (size_t)B;
+  }
+  std::vector<double> pts((size_t)B * k), mus((size_t)B * 2, 0.0);
+  for (int q = 0; q < B; ++q) {
+    for (int i = 0; i < ku; ++i) pts[(size_t)q * k + i] = y[(size_t)q * ku + i];
+    for (int i = 0; i < kx; ++i) pts[(size_t)q * k + ku + i] = z[(size_t)q * kx + i];
+    for (int i = 0; i < nmu; ++i) mus[(size_t)q * 2 + i] = mu[(size_t)q * nmu + i];
+  }
+  CK(cudaMemcpyAsync(c->d_rn_pts, pts.data(), pts.size() * 8, cudaMemcpyHostToDevice, s), "copy points");
+  CK(cudaMemcpyAsync(c->d_rn_mu, mus.data(), mus.size() * 8, cudaMemcpyHostToDevice, s), "copy parameters");
+  st = launch_residual_norms(c, B, c->d_rn_pts, c->d_rn_mu, c->d_rn_norms, s);
+  if (st != IFT_OK) return st;
+  CK(cudaMemcpyAsync(norms, c->d_rn_norms, (size_t)B * 8, cudaMemcpyDeviceToHost, s), "copy norms");
+  CK(cudaStreamSynchronize(s), "residual norms");
+  return IFT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Autotuner of the launch shapes.
 // ---------------------------------------------------------------------------
 namespace {
@@ -1360,25 +1445,30 @@ extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y
   CK(cudaMemcpy(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice), "copy y");
   if (c->kx > 0) CK(cudaMemcpy(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice), "copy z");
   const int cand_w[3] = {1, 2, 4};
-  // single-query fused assembly: warps per CTA
-  float best = INFINITY;
-  int best_w = c->wpc;
-  for (int w : cand_w) {
-    c->wpc = w;
-    c->epoch++;
-    const float t = time_launch(c, s, 3, [&]() {
-      return launch_assemble(c, wp, true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
-    });
-    if (t < best) {
-      best = t;
-      best_w = w;
+  // single-query fused assembly: warps per CTA, for each precision the context runs
+  for (int tp = 0; tp < 2; ++tp) {
+    if (!c->ks[tp].valid) continue;
+    float best = INFINITY;
+    int best_w = c->wpc[tp];
+    for (int w : cand_w) {
+      c->wpc[tp] = w;
+      c->epoch++;
+      const float t = time_launch(c, s, 3, [&]() {
+        return launch_assemble(c, tp, true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
+      });
+      if (t < best) {
+        best = t;
+        best_w = w;
+      }
     }
+    c->wpc[tp] = best_w;
+    c->epoch++;
   }
-  c->wpc = best_w;
-  c->epoch++;
   if (c->B > 0) {
     // batched assembly: chunk size x warps per CTA, scored on a full batch plus a tail
-    // in which only every 50th query is still running (weight 8: tails have more bodies)
+    // in which only every 50th query is still running (weight 8: tails have more bodies).
+    // The chunk size is tuned on the precision that dominates a solve (FP64 for mixed
+    // contexts: its stage evaluates at the full cost), then the other precision's warps.
     std::vector<double> wrep((size_t)c->B * k), mrep((size_t)c->B * 2, 0.0);
     for (int q = 0; q < c->B; ++q) {
       for (int i = 0; i < c->ku; ++i) wrep[(size_t)q * k + i] = y[i];
@@ -1392,9 +1482,19 @@ extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y
     CK(cudaMemcpy(d_tail, tail.data(), tail.size() * 4, cudaMemcpyHostToDevice), "copy tail flags");
     CK(cudaMemcpy(c->d_bw, wrep.data(), wrep.size() * 8, cudaMemcpyHostToDevice), "copy points");
     CK(cudaMemcpy(c->d_bmu, mrep.data(), mrep.size() * 8, cudaMemcpyHostToDevice), "copy mu");
+    auto score_of = [&](int tp) {
+      const float tf = time_launch(c, s, 3, [&]() {
+        return launch_batched(c, tp, true, c->d_bw, k, nullptr, 0, nullptr, s);
+      });
+      const float tt = time_launch(c, s, 3, [&]() {
+        return launch_batched(c, tp, true, c->d_bw, k, d_tail, 1, nullptr, s);
+      });
+      return tf + 8.0f * tt;
+    };
+    const int primary = (c->cfg.precision == IFT_FP32) ? 1 : 0;
     const int cand_c[4] = {4, 8, 16, 32};
     float bscore = INFINITY;
-    int bc = c->chunk, bw = c->bwpc;
+    int bc = c->chunk, bw = c->bwpc[primary];
     for (int ch : cand_c) {
       c->chunk = ch;
       st = rechunk(c);
@@ -1403,15 +1503,9 @@ extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y
         return st;
       }
       for (int w : cand_w) {
-        c->bwpc = w;
+        c->bwpc[primary] = w;
         c->epoch++;
-        const float tf = time_launch(c, s, 3, [&]() {
-          return launch_batched(c, wp, true, c->d_bw, k, nullptr, 0, nullptr, s);
-        });
-        const float tt = time_launch(c, s, 3, [&]() {
-          return launch_batched(c, wp, true, c->d_bw, k, d_tail, 1, nullptr, s);
-        });
-        const float score = tf + 8.0f * tt;
+        const float score = score_of(primary);
         if (score < bscore) {
           bscore = score;
           bc = ch;
@@ -1419,17 +1513,35 @@ extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y
         }
       }
     }
-    dfree(d_tail);
     c->chunk = bc;
-    c->bwpc = bw;
+    c->bwpc[primary] = bw;
     st = rechunk(c);
-    if (st != IFT_OK) return st;
+    if (st != IFT_OK) {
+      dfree(d_tail);
+      return st;
+    }
+    const int other = 1 - primary;
+    if (c->ks[other].valid) {
+      float best = INFINITY;
+      int best_w = c->bwpc[other];
+      for (int w : cand_w) {
+        c->bwpc[other] = w;
+        c->epoch++;
+        const float score = score_of(other);
+        if (score < best) {
+          best = score;
+          best_w = w;
+        }
+      }
+      c->bwpc[other] = best_w;
+    }
+    dfree(d_tail);
   }
   c->err.clear();
   c->epoch++;
   if (chosen) {
-    chosen[0] = c->wpc;
-    chosen[1] = c->bwpc;
+    chosen[0] = c->wpc[wp];
+    chosen[1] = c->bwpc[wp];
     chosen[2] = c->chunk;
   }
   CK(cudaStreamSynchronize(s), "autotune");
@@ -1441,11 +1553,23 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
   auto ok_w = [](int w) { return w == 1 || w == 2 || w == 4; };
   if (!ok_w(warps) || !ok_w(batched_warps) || !(chunk == 4 || chunk == 8 || chunk == 16 || chunk == 32))
     return c->fail(IFT_ERR_ARG, "launch shapes must be warps in {1,2,4} and chunk in {4,8,16,32}");
-  if (c->have_bases && (shapes_smem(c, warps) > (size_t)c->smem_optin ||
-                        shapes_smem(c, batched_warps) > (size_t)c->smem_optin))
+  // each precision the context runs takes these warps, or the most that fit its shared memory
+  int w1[2], w2[2];
+  for (int tp = 0; tp < 2; ++tp) {
+    w1[tp] = warps;
+    w2[tp] = batched_warps;
+    if (c->have_bases) {
+      while (w1[tp] > 1 && shapes_smem(c, tp, w1[tp]) > (size_t)c->smem_optin) w1[tp] /= 2;
+      while (w2[tp] > 1 && shapes_smem(c, tp, w2[tp]) > (size_t)c->smem_optin) w2[tp] /= 2;
+    }
+  }
+  const int ewp = c->eval_wp();
+  if (w1[ewp] != warps || w2[ewp] != batched_warps)
     return c->fail(IFT_ERR_ARG, "these warps per CTA need more shared memory than a CTA may have for these bases");
-  c->wpc = warps;
-  c->bwpc = batched_warps;
+  for (int tp = 0; tp < 2; ++tp) {
+    c->wpc[tp] = w1[tp];
+    c->bwpc[tp] = w2[tp];
+  }
   if (chunk != c->chunk) {
     c->chunk = chunk;
     if (c->B > 0) {

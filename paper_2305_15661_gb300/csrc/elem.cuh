@@ -133,6 +133,13 @@ struct Tabs {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// Elements whose volume Jacobian dR_e/dU_e (n_u x n_u) fits in 18 registers per lane
+// form it explicitly and multiply by Phi_e; larger ones (p = 3 Euler) take
+// Jacobian-vector products per quadrature point.
+__host__ __device__ constexpr bool kExplicitVolume(int nu) { return nu * nu <= 576; }
+// Entries of Jv per register pass (9 doubles per lane).
+constexpr int kJvPass = 288;
+
 // Per-warp shared-memory layout.
 template <class T, int PROB, int P, bool JAC>
 struct WarpLayout {
@@ -176,6 +183,11 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
+      if (kExplicitVolume(NU)) {  // T_q (RP M) and one pass of Jv rows (RP NU)
+        const int np = (NU * NU + kJvPass - 1) / kJvPass, rp = NU / np;
+        const size_t we = (size_t)rp * (M + NU);
+        if (we > w) w = we;
+      }
       oW = put(JAC ? w : 1, sizeof(T));
     }
     owq = put(ku > 0 ? ku : 1, sizeof(T));
@@ -375,20 +387,19 @@ struct ElemCore {
 #pragma unroll
           for (int a = 0; a < 4; ++a) hf[a] = H[a];
         } else {
-          Dual<T, 4> di[4], dd[4], dn[2], H[4];
+          Dual<T, 4> di[4], dd[4], H[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             di[a] = dconst<T, 4>(Uin[a]);
             dd[a] = dconst<T, 4>(Uout[a]);
           }
-          dn[0] = dconst<T, 4>(nt[k][0]);
-          dn[1] = dconst<T, 4>(nt[k][1]);
+          const T n2[2] = {nt[k][0], nt[k][1]};
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             if (grp == 0) di[a].d[a] = T(1);
             else dd[a].d[a] = T(1);
           }
-          euler_roe<Dual<T, 4>, T>(di, dd, dn, g1, H);
+          euler_roe<Dual<T, 4>, T>(di, dd, n2, g1, H);
           T* dst = (grp == 0) ? &Hp[pt * 16] : &Hm[pt * 16];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
@@ -589,6 +600,67 @@ struct ElemCore {
   // (DIM M x ku) in W, then every lane updates its own flattened (row, c) entries;
   // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
   __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
+    if constexpr (kExplicitVolume(NU)) {
+      // volume part of dR_e/dU_e: Jv[(i,a)][(j,b)] = -sum_q B_q[j] T_q[(i,a)][b] with
+      // T_q[(i,a)][b] = sum_r D_r[q][i] Ahat_qr[a][b], formed in passes of RP rows whose
+      // entries are lane-owned registers, then A_vol = Jv Phi_e for those rows
+      constexpr int NPASS = (NU * NU + kJvPass - 1) / kJvPass;
+      static_assert(NU % NPASS == 0, "rows must split evenly into passes");
+      constexpr int RP = NU / NPASS, NJ = (RP * NU + 31) / 32;
+      T* Tq = W;            // [RP][M]
+      T* Jp = W + RP * M;   // [RP][NU]
+#pragma unroll 1
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const int r0 = pass * RP;
+        T jv[NJ];
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) jv[t] = T(0);
+        for (int q = 0; q < NQ; ++q) {
+          __syncwarp();
+          for (int e = lane; e < RP * M; e += 32) {
+            const int rl = e / M, b = e - rl * M;
+            const int row = r0 + rl, i = row / M, a = row - i * M;
+            T s = T(0);
+#pragma unroll
+            for (int r = 0; r < DIM; ++r) s += D[(r * NQ + q) * NB + i] * Ah[((q * DIM + r) * M + a) * M + b];
+            Tq[e] = s;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int t = 0; t < NJ; ++t) {
+            const int e = lane + 32 * t;
+            if (e < RP * NU) {
+              const int rl = e / NU, col = e - rl * NU;
+              const int j = col / M, b = col - j * M;
+              jv[t] -= B[q * NB + j] * Tq[rl * M + b];
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+          const int e = lane + 32 * t;
+          if (e < RP * NU) Jp[e] = jv[t];
+        }
+        __syncwarp();
+        for (int e = lane; e < RP * ku; e += 32) {
+          const int rl = dku.div(e), c = e - rl * ku;
+          const T* jr = &Jp[rl * NU];
+          T s = T(0);
+#pragma unroll
+          for (int col = 0; col < NU; ++col) s += jr[col] * Phie[col * ku + c];
+          A[(r0 + rl) * k + c] = s;
+        }
+        __syncwarp();
+      }
+    } else {
+      jac_state_volume_jvp(lane, ku, k);
+    }
+    jac_state_faces(lane, bcs, ku, k);
+  }
+
+  // Volume part of the state columns by Jacobian-vector products: per volume point,
+  // G = B_q Phi_e (M x ku), F_r = Ahat_qr G (DIM M x ku), A -= D_r[q] F_r.
+  __device__ void jac_state_volume_jvp(int lane, int ku, int k) {
     for (int e = lane; e < NU * ku; e += 32) {
       const int row = dku.div(e), c = e - row * ku;
       A[row * k + c] = T(0);
@@ -623,6 +695,12 @@ struct ElemCore {
         A[row * k + c] = s;
       }
     }
+  }
+
+  // Face part of the state columns: per face point, the trace directions dU+ (this
+  // element's Phi rows) and dU- (the neighbour's trace rows), dH = Hp dU+ + Hm dU-,
+  // lifted onto the face's nodes.
+  __device__ void jac_state_faces(int lane, const signed char* bcs, int ku, int k) {
     T* dU = W;                // [2][M][ku]: interior, exterior
     T* dH = W + 2 * M * ku;   // [M][ku]
     for (int pt = 0; pt < NF * NFQ; ++pt) {
@@ -826,16 +904,18 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
   C.qxi = C.qw + TB::nqw;
 }
 
-// One element of the pass: steps 1-7 for element e with weight rho at the state
-// (wT, tauD) and parameters mu; accumulates into the warp's C.acc.
+// Steps 1-5 for element e at the state (wT, tauD) and parameters mu: gather,
+// reconstruction, geometry, pointwise fluxes (and their derivatives when JAC)
+// and R_e in C.R. bcs receives the element's face types. Returns true if the
+// element is non-physical or R_e is not finite.
 template <class T, int PROB, int P, bool JAC>
-__device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
-                                             const T* wT, const double* tauD, const double* mu,
-                                             const unsigned char* pairs, int lane) {
+__device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e,
+                                              const T* wT, const double* tauD, const double* mu, int lane,
+                                              signed char* bcs) {
   using Dd = Disc<PROB, P>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
-  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  const int ku = a.ku, kx = a.kx;
   const bool need_hn = JAC && kx > 0;
     const int* vv = &a.ev[(long)e * NV];
     // 1. gather
@@ -880,13 +960,27 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
     __syncwarp();
     // 3. geometry
     bool bad = !C.geometry();
-    signed char bcs[NF];
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
     bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn);
     __syncwarp();
     bad |= C.residual(lane);
+    return bad;
+}
+
+// One element of the pass: steps 1-7 for element e with weight rho at the state
+// (wT, tauD) and parameters mu; accumulates into the warp's C.acc.
+template <class T, int PROB, int P, bool JAC>
+__device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
+                                             const T* wT, const double* tauD, const double* mu,
+                                             const unsigned char* pairs, int lane) {
+  using Dd = Disc<PROB, P>;
+  constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+    const int* vv = &a.ev[(long)e * NV];
+    signed char bcs[NF];
+    bool bad = element_front<T, PROB, P, JAC>(C, a, e, wT, tauD, mu, lane, bcs);
     // distortion
     const bool dist = a.kappa != 0.0;
     if (dist && lane == 0) {
@@ -1065,6 +1159,63 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
     __syncwarp();
   }
 }
+
+// HDM residual norms at many points (the greedy-search indicator, Eq. greedy0):
+// rho = 1 on every element, no Jacobians. Work item t = (query q, element chunk c)
+// of `chunk` consecutive elements: one warp evaluates R_e on the chunk at query
+// q's point (w | tau at wpts + q wstride, parameters at mu + q mustride) and
+// writes sum_e |R_e|^2 in FP64 to out[t] (+inf if an element is non-physical).
+template <class T, int PROB, int P>
+__global__ void __launch_bounds__(128) residual_norms_kernel(AsmArgs<T> a, const double* wpts, long wstride,
+                                                             const double* mu, int mustride, int B, int nchunk,
+                                                             int chunk, double* out) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, false>;
+  constexpr int NU = Dd::NU, NF = Dd::NFACE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, kx = a.kx;
+  T *tab, *wT_unused;
+  double* tau_unused;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT_unused, tau_unused);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
+  const size_t wb = WarpLayout<T, PROB, P, false>(ku, kx).bytes;
+  WarpLayout<T, PROB, P, false> L(ku, kx);
+  unsigned char* wbase = smem + cb + warp * wb;
+  Core C;
+  C.carve(wbase, ku, kx);
+  bind_tables(C, tab);
+  T* wq = (T*)(wbase + L.owq);
+  double* tq = (double*)(wbase + L.otq);
+  __syncthreads();
+  const long total = (long)B * nchunk;
+  for (long t = (long)blockIdx.x * nw + warp; t < total; t += (long)gridDim.x * nw) {
+    const int q = (int)(t / nchunk), c = (int)(t - (long)q * nchunk);
+    const double* wsrc = wpts + (long)q * wstride;
+    for (int i = lane; i < ku; i += 32) wq[i] = (T)wsrc[i];
+    for (int i = lane; i < kx; i += 32) tq[i] = wsrc[ku + i];
+    __syncwarp();
+    const double* muq = mu + (long)q * mustride;
+    const long e0 = (long)c * chunk, e1 = (e0 + chunk < a.n_items) ? e0 + chunk : a.n_items;
+    double s = 0.0;
+    bool bad = false;
+    for (long e = e0; e < e1; ++e) {
+      signed char bcs[NF];
+      bad |= element_front<T, PROB, P, false>(C, a, (int)e, wq, tq, muq, lane, bcs);
+      double r2 = 0.0;
+      for (int i = lane; i < NU; i += 32) r2 += (double)C.R[i] * (double)C.R[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      s += r2;
+      __syncwarp();
+    }
+    if (lane == 0) out[t] = bad ? (double)INFINITY : s;
+    __syncwarp();
+  }
+}
+
+// norms[q] = sqrt(sum_c part[q * nchunk + c]), summed in chunk order.
+__global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 
 // Sum of the per-CTA partials in CTA order: out[i] = sum_c partial[c][i].
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);

@@ -68,6 +68,23 @@ struct KernelSetImpl {
                               &n, assemble_batched_kernel<T, PROB, P, false>, block, smem);
     return e == cudaSuccess ? n : 0;
   }
+  static cudaError_t residual_norms(const void* args, const double* wpts, long wstride, const double* mu,
+                                    int mustride, int B, int nchunk, int chunk, double* out, int grid, int block,
+                                    size_t smem, cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    residual_norms_kernel<T, PROB, P><<<grid, block, smem, s>>>(a, wpts, wstride, mu, mustride, B, nchunk, chunk,
+                                                                 out);
+    return cudaGetLastError();
+  }
+  static cudaError_t prepare_norms(size_t smem) {
+    return cudaFuncSetAttribute(residual_norms_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  }
+  static int blocks_per_sm_norms(int block, size_t smem) {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_norms_kernel<T, PROB, P>, block, smem);
+    return e == cudaSuccess ? n : 0;
+  }
   static KernelSet make() {
     KernelSet k;
     k.valid = true;
@@ -79,6 +96,9 @@ struct KernelSetImpl {
     k.assemble_batched = &assemble_batched;
     k.prepare_batched = &prepare_batched;
     k.blocks_per_sm_batched = &blocks_per_sm_batched;
+    k.residual_norms = &residual_norms;
+    k.prepare_norms = &prepare_norms;
+    k.blocks_per_sm_norms = &blocks_per_sm_norms;
     return k;
   }
 };

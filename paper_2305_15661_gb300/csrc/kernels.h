@@ -21,6 +21,12 @@ struct KernelSet {
                                   cudaStream_t s) = nullptr;
   cudaError_t (*prepare_batched)(bool jac, size_t smem) = nullptr;
   int (*blocks_per_sm_batched)(bool jac, int block, size_t smem) = nullptr;
+  // HDM residual norms of many points (rho = 1, no Jacobians); args as for assemble
+  cudaError_t (*residual_norms)(const void* args, const double* wpts, long wstride, const double* mu, int mustride,
+                                int B, int nchunk, int chunk, double* out, int grid, int block, size_t smem,
+                                cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_norms)(size_t smem) = nullptr;
+  int (*blocks_per_sm_norms)(int block, size_t smem) = nullptr;
 };
 
 // precision: 0 = FP64, 1 = FP32

@@ -370,19 +370,17 @@ __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, dou
     for (int a = 0; a < m; ++a) colsum[a * ku + c] = red[a][0];
 }
 
-// Restart B solver states at their own current iterate in the joint phase (the FP64
-// stage of a mixed-precision solve): the FP32 stage's joint-phase counts are kept in
-// iters32 / trials32, the iteration restarts from lambda_0 with a fresh assembly.
-__global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
-  const int q = blockIdx.x;
-  if (q >= B) return;
-  LMState& s = states[q];
-  const int k = ku + kx;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+// Hand a query over from the FP32 stage of a mixed solve to the FP64 stage: the
+// joint iteration restarts at the FP32 stage's last iterate with lambda_0 and a new
+// reference norm (taken from the first FP64 assembly there); the FP32 stage's
+// joint-phase counts are kept in iters32 / trials32. tid/nthreads: the calling
+// threads of one query.
+__device__ void restart_fp64(LMState& s, int k, int tid, int nthreads) {
+  for (int i = tid; i < k; i += nthreads) {
     s.trial[i] = s.z[i];
     s.dz[i] = 0.0;
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     s.iters32 = s.iters[1];
     s.trials32 = s.trials;
     s.iters[1] = 0;
@@ -399,6 +397,21 @@ __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
       s.alpha = 1.0;
     }
   }
+}
+
+// The hand-over for B queries, one block each.
+__global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
+  const int q = blockIdx.x;
+  if (q >= B) return;
+  restart_fp64(states[q], ku + kx, threadIdx.x, blockDim.x);
+}
+
+__global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)q * nchunk + c];
+  norms[q] = sqrt(s);
 }
 
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {

@@ -102,13 +102,14 @@ __device__ __forceinline__ S harten_abs(const S& lam, const S& del) {
 // |A_roe| dU = sum over the acoustic, entropy and shear waves of
 // |eigenvalue| x strength x eigenvector, with Roe averages weighted by sqrt(rho),
 // and Harten's entropy fix (delta = 0.1 c of the Roe state) on every |eigenvalue|.
-// S is T or a Dual over T.
+// S is T or a Dual over T (derivatives with respect to the states only: the
+// normal is a plain value).
 template <class S, class T>
-__device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const S nt[2], T g1, S H[4]) {
+__device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T nt[2], T g1, S H[4]) {
   const T half = T(0.5);
-  S len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
-  S il = recip(len);
-  S nx = nt[0] * il, ny = nt[1] * il;
+  const T len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
+  const T il = T(1) / len;
+  const T nx = nt[0] * il, ny = nt[1] * il;
   // interior side
   S ri = recip(Ui[0]);
   S ui = Ui[1] * ri, vi = Ui[2] * ri;
@@ -158,7 +159,7 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const S 
   S f1 = Ui[1] * vni + pi * nx + Uo[1] * vno + po * nx;
   S f2 = Ui[2] * vni + pi * ny + Uo[2] * vno + po * ny;
   S f3 = ehi * vni + eho * vno;
-  S hl = half * len;
+  const T hl = half * len;
   H[0] = hl * (f0 - d0);
   H[1] = hl * (f1 - d1);
   H[2] = hl * (f2 - d2);

@@ -60,7 +60,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
-           "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_mlp_create", "ift_mlp_destroy",
+           "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_loss_grad", "ift_mlp_train",
            "ift_mlp_predict", "ift_nearest_start"]
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_set_eq_weights_batched": (i32, [vp, i32, pl, pi, pd]),
         "ift_autotune": (i32, [vp, pd, pd, pd, pi]),
         "ift_set_launch_shapes": (i32, [vp, i32, i32, i32]),
+        "ift_hdm_residual_norms": (i32, [vp, i32, pd, pd, pd, pd]),
         "ift_reduced_residual_jacobian_batched": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom_batched": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_batched_dev": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -286,6 +287,23 @@ class Context:
 
     def set_launch_shapes(self, warps, batched_warps, chunk):
         self._check(load().ift_set_launch_shapes(self._h, warps, batched_warps, chunk))
+
+    def hdm_residual_norms(self, mus, ys, zs):
+        """|R(Phi y_q, X + Psi z_q; mu_q)|_2 over every element, for each row q."""
+        mus = _f64(mus).reshape(len(ys), -1)
+        ys = _f64(ys)
+        zz = _f64(zs) if self.kx else np.zeros(1)
+        out = np.zeros(len(ys))
+        self._check(load().ift_hdm_residual_norms(self._h, len(ys), _pd(mus), _pd(ys), _pd(zz), _pd(out)))
+        return out
+
+    def greedy_search(self, mus):
+        """Eq. greedy0 over candidate parameters mus with the batched weight sets
+        already set (one per candidate): solve every candidate, evaluate the HDM
+        residual norm at each solution, return (argmax, norms, solve result)."""
+        res = self.solve_rom_batched(mus)
+        norms = self.hdm_residual_norms(mus, res["w"], res["tau"])
+        return int(np.argmax(norms)), norms, res
 
     # -- batched queries ---------------------------------------------------
     def set_eq_weights_batched(self, sets):
