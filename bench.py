@@ -386,7 +386,7 @@ def run_batched(args):
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
-                                    contraction=_contraction(args))
+                                    contraction=_contraction(args), max_iters=args.max_iters)
     ctx.set_eq_weights_batched(sets)
     shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
     mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
@@ -415,7 +415,8 @@ def run_batched(args):
     t = sum(ms) / 1e3
     out = {"mode": "batched", "config": args.config, "elements": wl.n_elems, "p": wl.p,
            "k_u": wl.ku, "k_x": wl.kx, "precision": args.precision, "contraction": args.contraction,
-           "queries": B, "launch_shapes": shapes,
+           "queries": B, "launch_shapes": shapes, "max_iters": args.max_iters,
+           "converged_solves_per_s": conv * args.steps / t,
            "elements_per_query_mean": float(np.mean([len(s[0]) for s in sets])),
            "converged": conv, "ms_per_batch": 1e3 * t / args.steps,
            "solves_per_s": B * args.steps / t, "element_rj_evals_per_batch": evals,
@@ -424,7 +425,8 @@ def run_batched(args):
            "mean_fp64_iters": float(np.mean([i["iters"] for i in info["info"]]))}
     if args.compare_fp64 and prec != ift.FP64:
         # the same queries solved with FP64 assemblies throughout: converged points and objectives
-        ref_ctx = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
+        ref_ctx = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream,
+                                            max_iters=args.max_iters)
         ref_ctx.set_eq_weights_batched(sets)
         try:
             ref_ctx.set_launch_shapes(*shapes)
@@ -584,6 +586,52 @@ def run_warmstart(args):
     return 0
 
 
+def run_burgers(args):
+    """Config 1: steady Burgers, p = 2, 200 elements, k_u = 5, k_x = 2, rho = 1, one
+    ROM solve to a relative optimality of 1e-10 per step (a latency-bound solve:
+    about 20 LM bodies over 200 elements)."""
+    import torch
+
+    import oracle as orc
+    from paper_2305_15661_gb300 import ift
+    from paper_2305_15661_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    ift.load()
+    wl = W.burgers_workload(n_elems=200, p=2, k_u=5, seed=1)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ift.Context.from_workload(wl, tol=1e-10, stream=stream.cuda_stream)
+    mu_d = torch.as_tensor(wl.mus[0], dtype=torch.float64, device=dev)
+    y_d = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
+    z_d = torch.zeros(wl.kx, dtype=torch.float64, device=dev)
+    info = None
+    for _ in range(args.warmup):
+        info = ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=True)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    O = orc.Oracle.from_workload(wl)
+    t0 = time.perf_counter()
+    r = O.solve(wl.Phi, wl.Psi, wl.mus[0], wl.Phi.T @ W.replicate_guess(wl, wl.U_guess), tol=1e-10)
+    cpu_s = time.perf_counter() - t0
+    z = np.concatenate([y_d.cpu().numpy(), z_d.cpu().numpy()])
+    zr = np.concatenate([r["w"], r["tau"]])
+    print(json.dumps({"mode": "burgers", "elements": wl.n_elems, "p": wl.p, "k_u": wl.ku, "k_x": wl.kx,
+                      "tol": 1e-10, "median_ms": statistics.median(ms), "solves_per_s": 1e3 / statistics.median(ms),
+                      "lm_steps": info["init_iters"] + info["iters"], "oracle_lm_steps": r["init_iters"] + r["iters"],
+                      "rel_dz_vs_oracle": float(np.linalg.norm(z - zr) / np.linalg.norm(zr)),
+                      "cpu_oracle_s": cpu_s, "cpu_oracle_cores": orc.num_threads()}))
+    ctx.close()
+    return 0
+
+
 def run_greedy(args):
     """Greedy search (Eq. greedy0) over 256 candidate parameters on the 20,000-element
     mesh: batched hyperreduced solves with one shared weight set, then the full HDM
@@ -638,7 +686,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers"],
+                    default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly, batched and warmstart")
@@ -647,6 +696,8 @@ def main():
     ap.add_argument("--config", type=int, choices=[2, 3, 4], default=2,
                     help="--mode assembly: 2 (or 3) = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, "
                          "k 40+8; --mode batched: 3 = 256 queries on the first mesh, 4 = 1,024 on the second")
+    ap.add_argument("--max-iters", type=int, default=200,
+                    help="--mode batched: LM iterations per phase before a query stops unconverged")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="--mode batched: also solve the queries with FP64 assemblies and compare")
     ap.add_argument("--autotune", action="store_true", help="--mode assembly: tune the launch shape first")
@@ -668,6 +719,8 @@ def main():
         return run_warmstart(args)
     if args.mode == "greedy":
         return run_greedy(args)
+    if args.mode == "burgers":
+        return run_burgers(args)
     return run_ours(args)
 
 

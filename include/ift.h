@@ -235,6 +235,18 @@ ift_status ift_set_launch_shapes(ift_ctx* ctx, int warps, int batched_warps, int
 ift_status ift_hdm_residual_norms(ift_ctx* ctx, int B, const double* mu, const double* y, const double* z,
                                   double* norms);
 
+/* Per-element contributions to the reduced residuals (the columns of the EQP
+   linear program, Eq. eqp-con): at (y, z) = (w, tau) and mu, for each of the n
+   listed elements (n = -1: every element, in order) one row of k + 1 values,
+   [S^(e) (k_u) | T^(e) (k_x) | J^(e)], such that the weighted residuals of
+   Eq. ift-eqp-res0 are S~ = sum_e rho_e S^(e), T~ = sum_e rho_e T^(e) and
+   J~ = sum_e rho_e J^(e) for any weights rho. out: host, n x (k + 1) (n_elems x
+   (k + 1) for n = -1). The weights set on the context are not used. Returns
+   IFT_ERR_NONPHYSICAL (rows of non-physical elements NaN, J^(e) = +inf) when an
+   element is non-physical at (y, z). */
+ift_status ift_element_gradients(ift_ctx* ctx, const double* mu, const double* y, const double* z, int64_t n,
+                                 const int32_t* elems, double* out);
+
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
    cannot call cudaMalloc when they need the reduced system: code that is
    capturing a stream into a CUDA graph, code that owns all device memory

@@ -297,7 +297,7 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "element kernel launch");
   const int nacc = c->nacc();
-  reduce_partials_kernel<<<(nacc + 127) / 128, 128, 0, s>>>(c->d_partial, grid, nacc, out);
+  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(c->d_partial, grid, nacc, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "reduce launch");
   return IFT_OK;
@@ -1399,6 +1399,61 @@ extern "C" ift_status ift_hdm_residual_norms(ift_ctx* c, int B, const double* mu
   if (st != IFT_OK) return st;
   CK(cudaMemcpyAsync(norms, c->d_rn_norms, (size_t)B * 8, cudaMemcpyDeviceToHost, s), "copy norms");
   CK(cudaStreamSynchronize(s), "residual norms");
+  return IFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-element reduced-residual contributions: columns of the EQP linear program.
+// ---------------------------------------------------------------------------
+extern "C" ift_status ift_element_gradients(ift_ctx* c, const double* mu, const double* y, const double* z,
+                                            int64_t n, const int32_t* elems, double* out) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !y || (c->kx > 0 && !z) || !out || n < -1 || n == 0 || (n > 0 && !elems))
+    return c->fail(IFT_ERR_ARG, "bad argument");
+  const int64_t items = (n < 0) ? c->n_elems : n;
+  if (n > 0)
+    for (int64_t i = 0; i < n; ++i)
+      if (elems[i] < 0 || elems[i] >= c->n_elems) return c->fail(IFT_ERR_ARG, "element index out of range");
+  const int wp = c->eval_wp(), k = c->ku + c->kx, nmu = (c->dim == 1) ? 1 : 2;
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->d_mu, mu, nmu * 8, cudaMemcpyHostToDevice, s), "copy mu");
+  CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice, s), "copy y");
+  if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice, s), "copy z");
+  int* d_el = nullptr;
+  double* d_out = nullptr;
+  auto cleanup = [&]() {
+    dfree(d_el);
+    dfree(d_out);
+  };
+  if (n > 0 && dalloc(d_el, (size_t)n) != cudaSuccess) return c->fail(IFT_ERR_OOM, "element list");
+  if (dalloc(d_out, (size_t)items * (k + 1)) != cudaSuccess) {
+    cleanup();
+    return c->fail(IFT_ERR_OOM, "output rows");
+  }
+  if (n > 0) cudaMemcpyAsync(d_el, elems, (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  const KernelSet& ks = c->ks[wp];
+  const int warps = c->wpc[wp], block = 32 * warps;
+  const size_t smem = ks.smem_bytes(true, c->ku, c->kx, warps);
+  const long grid = std::min<long>((items + warps - 1) / warps, (long)c->sm_count * 8);
+  cudaError_t e;
+  if (wp == 1) {
+    AsmArgs<float> a = make_args<float>(c, c->d_Phi32, c->d_w, c->d_tau, c->d_mu, true, nullptr);
+    a.elems = d_el;
+    a.n_items = items;
+    e = ks.element_gradients(&a, d_out, (int)grid, block, smem, s);
+  } else {
+    AsmArgs<double> a = make_args<double>(c, c->d_Phi, c->d_w, c->d_tau, c->d_mu, true, nullptr);
+    a.elems = d_el;
+    a.n_items = items;
+    e = ks.element_gradients(&a, d_out, (int)grid, block, smem, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, (size_t)items * (k + 1) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return c->cuda_fail(e, "element gradients");
+  for (int64_t i = 0; i < items; ++i)
+    if (std::isinf(out[i * (k + 1) + k])) return c->fail(IFT_ERR_NONPHYSICAL, "non-physical element at (y, z)");
   return IFT_OK;
 }
 

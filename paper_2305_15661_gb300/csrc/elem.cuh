@@ -17,7 +17,7 @@
 //      H += rho A^T A, g += rho A^T R, J += rho |R|^2/2 (+ distortion terms)
 //      into the warp's accumulators (Eqs. ift-eqp-res0, levmarq-elem, ift-opt-eqp2).
 // At the end each CTA sums its warps' accumulators in warp order and writes one
-// FP64 partial; a second kernel sums the partials in CTA order. The result is
+// FP64 partial; a second kernel sums the partials in a fixed order. The result is
 // deterministic for a fixed launch shape.
 #pragma once
 #include <cuda_runtime.h>
@@ -28,6 +28,12 @@
 #include "physics.cuh"
 
 namespace ift {
+
+// Per-warp accumulators: the upper triangle of H row by row (k (k + 1) / 2 entries),
+// then g (k), J and the non-physical count. Position of H[r][b], r <= b:
+__host__ __device__ inline int acc_h(int r, int b, int k) { return r * k - (r * (r - 1)) / 2 + (b - r); }
+__host__ __device__ inline int acc_tail(int k) { return k * (k + 1) / 2; }
+__host__ __device__ inline int acc_count(int k) { return k * (k + 1) / 2 + k + 2; }
 
 // Element-list items, state and problem data shared by the element kernels.
 template <class T>
@@ -118,7 +124,7 @@ __device__ __forceinline__ void syrk_upper_tf32(const float* A, int k, float* ac
       const int rr[4] = {r0, r0, r1, r1}, cc[4] = {cb, cb + 1, cb, cb + 1};
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (rr[j] <= cc[j] && cc[j] < k) acc[rr[j] * k + cc[j]] += rho * c[j];
+        if (rr[j] <= cc[j] && cc[j] < k) acc[acc_h(rr[j], cc[j], k)] += rho * c[j];
     }
   }
 }
@@ -133,10 +139,12 @@ struct Tabs {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// Elements whose volume Jacobian dR_e/dU_e (n_u x n_u) fits in 18 registers per lane
-// form it explicitly and multiply by Phi_e; larger ones (p = 3 Euler) take
+// FP64 elements whose volume Jacobian dR_e/dU_e (n_u x n_u) fits in 18 registers
+// per lane form it explicitly and multiply by Phi_e (fewer FP64 operations, the
+// bound of the FP64 kernels); larger ones (p = 3 Euler) and the FP32 kernels
+// (bound by issue and latency, where the extra registers cost occupancy) take
 // Jacobian-vector products per quadrature point.
-__host__ __device__ constexpr bool kExplicitVolume(int nu) { return nu * nu <= 576; }
+__host__ __device__ constexpr bool kExplicitVolume(int nu, int word) { return word == 8 && nu * nu <= 576; }
 // Entries of Jv per register pass (9 doubles per lane).
 constexpr int kJvPass = 288;
 
@@ -146,7 +154,7 @@ struct WarpLayout {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
-  size_t oxe, oPsie, odN, oPhie, oPhp, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
+  size_t oxe, oPsie, odN, oPhie, oPoff, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
       oW, owq, otq, oacc, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
     const int k = ku + kx;
@@ -160,7 +168,9 @@ struct WarpLayout {
     oPsie = put((size_t)NXE * (kx > 0 ? kx : 1), 8);
     odN = put(NXE + 2, 8);
     oPhie = put((size_t)NU * ku, sizeof(T));
-    oPhp = put((size_t)NUP * ku, sizeof(T));
+    // neighbour trace rows are read from Phi in global memory (L1/L2): per face and
+    // trace position, the offset of the row block in Phi (-1 on boundary faces)
+    oPoff = put((size_t)NF * Dd::NTRACE, 8);
     oUe = put(NU, sizeof(T));
     oUp = put(NUP, sizeof(T));
     oFh = put(NQ * DIM * M, sizeof(T));
@@ -183,7 +193,7 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
-      if (kExplicitVolume(NU)) {  // T_q (RP M) and one pass of Jv rows (RP NU)
+      if (kExplicitVolume(NU, sizeof(T))) {  // T_q (RP M) and one pass of Jv rows (RP NU)
         const int np = (NU * NU + kJvPass - 1) / kJvPass, rp = NU / np;
         const size_t we = (size_t)rp * (M + NU);
         if (we > w) w = we;
@@ -192,7 +202,7 @@ struct WarpLayout {
     }
     owq = put(ku > 0 ? ku : 1, sizeof(T));
     otq = put(kx > 0 ? kx : 1, 8);
-    oacc = put((size_t)k * k + k + 2, sizeof(T));
+    oacc = put((size_t)acc_count(k), sizeof(T));
     bytes = b;
   }
 };
@@ -234,12 +244,14 @@ struct ElemCore {
   const T *D, *B, *Lt, *fw, *qw, *qxi;
   // warp buffers
   double *xe, *Psie, *dN;
-  T *Phie, *Php, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
+  T *Phie, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
   // geometry (registers, identical on all lanes)
   T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
   T detJ;
   T nt[3][2];    // scaled face normals (2-D)
   double x0d, x1d;  // 1-D end points
+  const T* PhiG;     // Phi in global memory (neighbour trace rows)
+  long long* poff;   // per face and trace position: row-block offset in PhiG, -1 on boundary faces
   FastDiv dku, dkx;  // division by k_u and k_x in the lane loops
 
   __device__ void carve(unsigned char* base, int ku, int kx) {
@@ -250,7 +262,7 @@ struct ElemCore {
     Psie = (double*)(base + L.oPsie);
     dN = (double*)(base + L.odN);
     Phie = (T*)(base + L.oPhie);
-    Php = (T*)(base + L.oPhp);
+    poff = (long long*)(base + L.oPoff);
     Ue = (T*)(base + L.oUe);
     Up = (T*)(base + L.oUp);
     Fh = (T*)(base + L.oFh);
@@ -600,7 +612,7 @@ struct ElemCore {
   // (DIM M x ku) in W, then every lane updates its own flattened (row, c) entries;
   // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
   __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
-    if constexpr (kExplicitVolume(NU)) {
+    if constexpr (kExplicitVolume(NU, sizeof(T))) {
       // volume part of dR_e/dU_e: Jv[(i,a)][(j,b)] = -sum_q B_q[j] T_q[(i,a)][b] with
       // T_q[(i,a)][b] = sum_r D_r[q][i] Ahat_qr[a][b], formed in passes of RP rows whose
       // entries are lane-owned registers, then A_vol = Jv Phi_e for those rows
@@ -720,7 +732,7 @@ struct ElemCore {
           }
         } else if (bt == 0) {
 #pragma unroll
-          for (int j = 0; j < NT; ++j) s += Lt[f * NT + j] * Php[((kf * NT + j) * M + b) * ku + c];
+          for (int j = 0; j < NT; ++j) s += Lt[f * NT + j] * PhiG[poff[kf * NT + j] + b * ku + c];
         }
         dU[e] = s;
       }
@@ -921,22 +933,20 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
     // 1. gather
     const T* phe = a.Phi + (size_t)e * NU * ku;
     for (int i = lane; i < NU * ku; i += 32) C.Phie[i] = phe[i];
-    for (int kf = 0; kf < NF; ++kf) {
+    if (lane < NF * NT) {
+      const int kf = lane / NT, j = lane - kf * NT;
       const int e2 = a.nbr[(long)e * NF + kf];
       const int k2 = a.nbr_face[(long)e * NF + kf];
-      const int rowlen = M * ku;
-      for (int i = lane; i < NT * rowlen; i += 32) {
-        const int j = C.dku.div(i) / M, rem = i - j * rowlen;
-        T v = T(0);
-        if (e2 >= 0) {
-          // neighbour trace node at position j along this face = its node NT-1-j on face k2
-          const int jj = NT - 1 - j;
-          const int node = (k2 == 0) ? Dd::face_node(0, jj) : ((k2 == 1) ? Dd::face_node(1, jj) : Dd::face_node(2, jj));
-          v = a.Phi[((size_t)e2 * NU + node * M) * ku + rem];
-        }
-        C.Php[(kf * NT + j) * rowlen + rem] = v;
+      long long off = -1;
+      if (e2 >= 0) {
+        // neighbour trace node at position j along this face = its node NT-1-j on face k2
+        const int jj = NT - 1 - j;
+        const int node = (k2 == 0) ? Dd::face_node(0, jj) : ((k2 == 1) ? Dd::face_node(1, jj) : Dd::face_node(2, jj));
+        off = ((long long)e2 * NU + node * M) * ku;
       }
+      C.poff[lane] = off;
     }
+    C.PhiG = a.Phi;
     for (int i = lane; i < NXE * kx; i += 32) {
       const int r = C.dkx.div(i), c = i - r * kx;
       const int v = r / DIM, d = r - v * DIM;
@@ -945,11 +955,20 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
     __syncwarp();
     // 2. reconstruction
     for (int i = lane; i < NU + NUP; i += 32) {
-      const T* row = (i < NU) ? &C.Phie[i * ku] : &C.Php[(i - NU) * ku];
       T s = T(0);
-      for (int c = 0; c < ku; ++c) s += row[c] * wT[c];
-      if (i < NU) C.Ue[i] = s;
-      else C.Up[i - NU] = s;
+      if (i < NU) {
+        const T* row = &C.Phie[i * ku];
+        for (int c = 0; c < ku; ++c) s += row[c] * wT[c];
+        C.Ue[i] = s;
+      } else {
+        const int r = i - NU, kj = r / M, b = r - kj * M;
+        const long long off = C.poff[kj];
+        if (off >= 0) {
+          const T* row = C.PhiG + off + b * ku;
+          for (int c = 0; c < ku; ++c) s += row[c] * wT[c];
+        }
+        C.Up[r] = s;
+      }
     }
     if (lane < NXE) {
       const int v = lane / DIM, d = lane - v * DIM;
@@ -970,8 +989,10 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 }
 
 // One element of the pass: steps 1-7 for element e with weight rho at the state
-// (wT, tauD) and parameters mu; accumulates into the warp's C.acc.
-template <class T, int PROB, int P, bool JAC>
+// (wT, tauD) and parameters mu; accumulates into the warp's C.acc. TC: H on the
+// tensor cores (FP32 only; a separate instantiation, so the FP32 FMA kernel does
+// not carry the tensor-core code's registers).
+template <class T, int PROB, int P, bool JAC, bool TC = false>
 __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
                                              const T* wT, const double* tauD, const double* mu,
                                              const unsigned char* pairs, int lane) {
@@ -998,8 +1019,8 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       // or tensor-core tiles (FP32 contexts that ask for them)
       const T rT = (T)rho;
       bool simt_h = true;
-      if constexpr (std::is_same<T, float>::value) {
-        if (a.contraction != 0) {
+      if constexpr (std::is_same<T, float>::value && TC) {
+        {
           __syncwarp();
           if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.acc, rT, lane);
           else syrk_upper_tf32<NU, false>(C.A, k, C.acc, rT, lane);
@@ -1013,7 +1034,7 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
                 ++r;
               }
               const int b = r + rem;
-              C.acc[(ku + r) * k + ku + b] += rT * (C.dNt[r] * C.dNt[b]);
+              C.acc[acc_h(ku + r, ku + b, k)] += rT * (C.dNt[r] * C.dNt[b]);
             }
           }
           simt_h = false;
@@ -1026,22 +1047,22 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
 #pragma unroll
         for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.A[i * k + b];
         if (dist && r >= ku) s += C.dNt[r - ku] * C.dNt[b - ku];
-        C.acc[r * k + b] += rT * s;
+        C.acc[pidx] += rT * s;  // pairs run over the upper triangle in accumulator order
       }
       for (int r = lane; r < k; r += 32) {
         T s = T(0);
 #pragma unroll
         for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
         if (dist && r >= ku) s += C.dNt[r - ku] * Ne;
-        C.acc[k * k + r] += rT * s;
+        C.acc[acc_tail(k) + r] += rT * s;
       }
     }
     if (lane == 0) {
       T s = T(0);
 #pragma unroll
       for (int i = 0; i < NU; ++i) s += C.R[i] * C.R[i];
-      C.acc[k * k + k] += T(0.5) * (T)rho * (s + Ne * Ne);
-      if (bad) C.acc[k * k + k + 1] += T(1);
+      C.acc[acc_tail(k) + k] += T(0.5) * (T)rho * (s + Ne * Ne);
+      if (bad) C.acc[acc_tail(k) + k + 1] += T(1);
     }
     __syncwarp();
 }
@@ -1058,17 +1079,22 @@ __device__ inline void build_pairs(unsigned char* pairs, int k) {
 }
 
 // Accumulator entry i of the full [H | g | J | count] vector (H mirrored from its upper triangle).
-__device__ inline int acc_source(int i, int k, bool jac) {
-  if (jac && i < k * k) {
-    const int r = i / k, b = i - r * k;
-    if (r > b) return b * k + r;
+__device__ inline int acc_source(int i, int k) {
+  if (i < k * k) {
+    int r = i / k, b = i - r * k;
+    if (r > b) {
+      const int t = r;
+      r = b;
+      b = t;
+    }
+    return acc_h(r, b, k);
   }
-  return i;
+  return acc_tail(k) + (i - k * k);
 }
 
 // The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false)
 // for one query: a grid-stride loop of warps over the items; one FP64 partial per CTA.
-template <class T, int PROB, int P, bool JAC>
+template <class T, int PROB, int P, bool JAC, bool TC = false>
 __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1083,21 +1109,21 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   Core C;
   C.carve(smem + cb + warp * wb, ku, kx);
   bind_tables(C, tab);
-  const int nacc = k * k + k + 2;
-  for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+  const int nacc = k * k + k + 2;  // entries of a partial row (full H)
+  for (int i = lane; i < acc_count(k); i += 32) C.acc[i] = T(0);
   unsigned char* pairs = smem + cb + nw * wb;
   if (JAC && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
     const int e = a.elems ? a.elems[it] : (int)it;
     const double rho = a.rho ? a.rho[it] : 1.0;
-    element_pass<T, PROB, P, JAC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
+    element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
   }
   __syncthreads();
   // CTA partial: sum the warps' accumulators in warp order, in FP64
   WarpLayout<T, PROB, P, JAC> L(ku, kx);
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
-    const int src = acc_source(i, k, JAC);
+    const int src = acc_source(i, k);
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
     a.partial[(size_t)blockIdx.x * nacc + i] = s;
@@ -1121,7 +1147,7 @@ struct BatchArgs {
   long donestride;
 };
 
-template <class T, int PROB, int P, bool JAC>
+template <class T, int PROB, int P, bool JAC, bool TC = false>
 __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1149,13 +1175,14 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
     const double* wsrc = b.w + (long)q * b.wstride;
     for (int i = lane; i < ku; i += 32) wq[i] = (T)wsrc[i];
     for (int i = lane; i < kx; i += 32) tq[i] = wsrc[ku + i];
-    for (int i = lane; i < nacc; i += 32) C.acc[i] = T(0);
+    for (int i = lane; i < acc_count(k); i += 32) C.acc[i] = T(0);
     __syncwarp();
     const double* muq = b.mu + (long)q * b.mustride;
+#pragma unroll 1
     for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it)
-      element_pass<T, PROB, P, JAC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+      element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
     __syncwarp();
-    for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k, JAC)];
+    for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k)];
     __syncwarp();
   }
 }
@@ -1214,10 +1241,66 @@ __global__ void __launch_bounds__(128) residual_norms_kernel(AsmArgs<T> a, const
   }
 }
 
+// Per-element reduced-residual contributions (the columns of the EQP linear
+// program, Eq. eqp-con): for each listed element e, out[e][0..k) = [S^(e); T^(e)]
+// with S~ = sum_e rho_e S^(e), T~ = sum_e rho_e T^(e) (Eq. ift-eqp-res0): the
+// element's A_e^T R_e plus, in the mesh rows, Psi_e^T dN_e^T N_e. One warp per
+// element; out[e][k] = (|R_e|^2 + N_e^2) / 2, the element's share of J~.
+template <class T, int PROB, int P>
+__global__ void __launch_bounds__(128) element_gradients_kernel(AsmArgs<T> a, double* out) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, true>;
+  constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  T *tab, *wT;
+  double* tauD;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
+  const size_t wb = WarpLayout<T, PROB, P, true>(ku, kx).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, ku, kx);
+  bind_tables(C, tab);
+  __syncthreads();
+  const bool dist = a.kappa != 0.0;
+  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
+    const int e = a.elems ? a.elems[it] : (int)it;
+    const int* vv = &a.ev[(long)e * NV];
+    signed char bcs[NF];
+    const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, a.mu, lane, bcs);
+    if (dist && lane == 0) {
+      double Xe[6];
+      for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+      C.distortion(Xe, a.kappa, a.eps);
+    }
+    __syncwarp();
+    const T Ne = dist ? (T)C.dN[NXE] : T(0);
+    C.jac_state(lane, bcs, ku, k);
+    C.jac_geom(lane, a.mu, ku, kx, k, dist);
+    double* row = out + (size_t)it * (k + 1);
+    for (int r = lane; r < k; r += 32) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
+      if (dist && r >= ku) s += C.dNt[r - ku] * Ne;
+      row[r] = bad ? (double)NAN : (double)s;
+    }
+    if (lane == 0) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) s += C.R[i] * C.R[i];
+      row[k] = bad ? (double)INFINITY : 0.5 * (double)(s + Ne * Ne);
+    }
+    __syncwarp();
+  }
+}
+
 // norms[q] = sqrt(sum_c part[q * nchunk + c]), summed in chunk order.
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 
-// Sum of the per-CTA partials in CTA order: out[i] = sum_c partial[c][i].
+// Sum of the per-CTA partials: out[i] = sum_c partial[c][i], in a fixed order
+// (eight contiguous runs of CTAs, then the eight run sums in order).
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);
 
 // Per-element inspection: R_e and [dR_e/dU_e | dR_e/dU_e' | dR_e/dx_e], N_e, dN_e

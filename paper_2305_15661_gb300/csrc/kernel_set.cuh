@@ -1,5 +1,7 @@
 // Builds a KernelSet for one (problem, degree, precision) instantiation.
 #pragma once
+#include <type_traits>
+
 #include "elem.cuh"
 #include "kernels.h"
 
@@ -7,12 +9,22 @@ namespace ift {
 
 template <class T, int PROB, int P>
 struct KernelSetImpl {
+  // FP32 sets also hold the tensor-core contraction variants of the fused kernels
+  static constexpr bool kTC = std::is_same<T, float>::value;
+
   static cudaError_t assemble(const void* args, bool jac, int grid, int block, size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
-    if (jac)
+    if (jac) {
+      if constexpr (kTC) {
+        if (a.contraction != 0) {
+          assemble_kernel<T, PROB, P, true, true><<<grid, block, smem, s>>>(a);
+          return cudaGetLastError();
+        }
+      }
       assemble_kernel<T, PROB, P, true><<<grid, block, smem, s>>>(a);
-    else
+    } else {
       assemble_kernel<T, PROB, P, false><<<grid, block, smem, s>>>(a);
+    }
     return cudaGetLastError();
   }
   static size_t smem_bytes(bool jac, int ku, int kx, int warps) {
@@ -24,6 +36,11 @@ struct KernelSetImpl {
       cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
+      if constexpr (kTC) {
+        e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+      }
       return cudaFuncSetAttribute(inspect_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem);
     }
@@ -48,17 +65,31 @@ struct KernelSetImpl {
                                       size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     const BatchArgs& b = *(const BatchArgs*)bargs;
-    if (jac)
+    if (jac) {
+      if constexpr (kTC) {
+        if (a.contraction != 0) {
+          assemble_batched_kernel<T, PROB, P, true, true><<<grid, block, smem, s>>>(a, b);
+          return cudaGetLastError();
+        }
+      }
       assemble_batched_kernel<T, PROB, P, true><<<grid, block, smem, s>>>(a, b);
-    else
+    } else {
       assemble_batched_kernel<T, PROB, P, false><<<grid, block, smem, s>>>(a, b);
+    }
     return cudaGetLastError();
   }
   static cudaError_t prepare_batched(bool jac, size_t smem) {
-    return jac ? cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-               : cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!jac)
+      return cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (kTC) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    return e;
   }
   static int blocks_per_sm_batched(bool jac, int block, size_t smem) {
     int n = 0;
@@ -74,6 +105,15 @@ struct KernelSetImpl {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     residual_norms_kernel<T, PROB, P><<<grid, block, smem, s>>>(a, wpts, wstride, mu, mustride, B, nchunk, chunk,
                                                                  out);
+    return cudaGetLastError();
+  }
+  static cudaError_t element_gradients(const void* args, double* out, int grid, int block, size_t smem,
+                                       cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    cudaError_t e = cudaFuncSetAttribute(element_gradients_kernel<T, PROB, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    element_gradients_kernel<T, PROB, P><<<grid, block, smem, s>>>(a, out);
     return cudaGetLastError();
   }
   static cudaError_t prepare_norms(size_t smem) {
@@ -98,6 +138,7 @@ struct KernelSetImpl {
     k.blocks_per_sm_batched = &blocks_per_sm_batched;
     k.residual_norms = &residual_norms;
     k.prepare_norms = &prepare_norms;
+    k.element_gradients = &element_gradients;
     k.blocks_per_sm_norms = &blocks_per_sm_norms;
     return k;
   }

@@ -26,6 +26,9 @@ struct KernelSet {
                                 int B, int nchunk, int chunk, double* out, int grid, int block, size_t smem,
                                 cudaStream_t s) = nullptr;
   cudaError_t (*prepare_norms)(size_t smem) = nullptr;
+  // per-element [S^(e); T^(e); J^(e)] rows; args as for assemble
+  cudaError_t (*element_gradients)(const void* args, double* out, int grid, int block, size_t smem,
+                                   cudaStream_t s) = nullptr;
   int (*blocks_per_sm_norms)(int block, size_t smem) = nullptr;
 };
 

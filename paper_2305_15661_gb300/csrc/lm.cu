@@ -414,12 +414,25 @@ __global__ void residual_norms_finish_kernel(const double* part, int B, int nchu
   norms[q] = sqrt(s);
 }
 
+// Block b sums columns [32 b, 32 b + 32) of the partials: its 8 warps each sum one
+// contiguous eighth of the rows (coalesced 32-column reads), then the eight
+// segment sums are added in segment order (the order is fixed for a launch shape).
 __global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nacc) return;
+  __shared__ double seg[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int per = (nparts + 7) / 8, c0 = w * per, c1 = min(nparts, c0 + per);
   double s = 0.0;
-  for (int c = 0; c < nparts; ++c) s += partial[(size_t)c * nacc + i];
-  out[i] = s;
+  if (i < nacc)
+    for (int c = c0; c < c1; ++c) s += partial[(size_t)c * nacc + i];
+  seg[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && i < nacc) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += seg[k][lane];
+    out[i] = t;
+  }
 }
 
 // w_guess = Phi^T U_guess, U_guess the constant state (Burgers u = 1, Euler U_inf(mu))

@@ -60,7 +60,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_reduced_residual_jacobian", "ift_reduced_residual_jacobian_dev", "ift_element_eval",
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
-           "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_mlp_create", "ift_mlp_destroy",
+           "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_element_gradients", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_loss_grad", "ift_mlp_train",
            "ift_mlp_predict", "ift_nearest_start"]
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_autotune": (i32, [vp, pd, pd, pd, pi]),
         "ift_set_launch_shapes": (i32, [vp, i32, i32, i32]),
         "ift_hdm_residual_norms": (i32, [vp, i32, pd, pd, pd, pd]),
+        "ift_element_gradients": (i32, [vp, pd, pd, pd, i64, pi, pd]),
         "ift_reduced_residual_jacobian_batched": (i32, [vp, pd, pd, pd, pd, pd, pd, pd]),
         "ift_solve_rom_batched": (i32, [vp, pd, pd, pd, P(SolveInfo)]),
         "ift_solve_rom_batched_dev": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -295,6 +296,18 @@ class Context:
         zz = _f64(zs) if self.kx else np.zeros(1)
         out = np.zeros(len(ys))
         self._check(load().ift_hdm_residual_norms(self._h, len(ys), _pd(mus), _pd(ys), _pd(zz), _pd(out)))
+        return out
+
+    def element_gradients(self, mu, y, z, elems=None):
+        """Rows [S^(e) | T^(e) | J^(e)] per element (every element if elems is None)."""
+        n = -1 if elems is None else len(elems)
+        rows = self.n_elems if elems is None else len(elems)
+        out = np.zeros((rows, self.ku + self.kx + 1))
+        el = None if elems is None else np.ascontiguousarray(elems, dtype=np.int32)
+        zz = _f64(z) if self.kx else np.zeros(1)
+        st = load().ift_element_gradients(self._h, _pd(_f64(mu)), _pd(_f64(y)), _pd(zz), n, _pi(el), _pd(out))
+        if st not in (IFT_OK, -5):
+            self._check(st)
         return out
 
     def greedy_search(self, mus):
