@@ -39,6 +39,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "ROM solves/sec at rel. resid 1e-8 vs FP64 oracle; element R+J evals/sec"
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused FP64
+# assembly kernel of this workload, from an ncu capture of the current kernel
+# (78.75 MB + 11.16 MB); set to None when the kernel changes until it is re-taken.
+FP64_ASSEMBLY_DRAM_BYTES = 89.91e6
 WORKLOAD = "euler2d_p2_20000el_ku20_kx4_rho1_fp64"
 
 
@@ -298,7 +302,8 @@ def run_ours(args):
                         "d2h_bytes_per_step": d2h},
                 "roofline": {"bound": "alu", "kernel": "assemble_kernel<double,Euler,p=2,JAC>",
                              "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                             "frac": achieved_tf / peak_tf if peak_tf else None, "traffic": None,
+                             "frac": achieved_tf / peak_tf if peak_tf else None,
+                             "traffic": FP64_ASSEMBLY_DRAM_BYTES,
                              "peak_source": "FP64 FMA probe on this GPU (measured)",
                              "flops_per_element": fl, "isolated_assembly_ms": iso_ms,
                              "isolated_achieved": iso_tf},
