@@ -304,6 +304,14 @@ ift_status ift_mlp_num_params(const ift_mlp* net, int64_t* count);
 ift_status ift_mlp_get_params(const ift_mlp* net, double* params);
 ift_status ift_mlp_set_params(ift_mlp* net, const double* params);
 
+/* Per-column standardisation of inputs and targets (set by ift_mlp_train, used by
+   ift_mlp_predict; identity after ift_mlp_create): means and standard deviations,
+   n_in and n_out values each. set: standard deviations must be positive, means
+   finite, else IFT_ERR_ARG. With the parameters they restore a trained network. */
+ift_status ift_mlp_get_scaling(const ift_mlp* net, double* x_mean, double* x_std, double* t_mean, double* t_std);
+ift_status ift_mlp_set_scaling(ift_mlp* net, const double* x_mean, const double* x_std, const double* t_mean,
+                               const double* t_std);
+
 /* Mean-squared-error loss L = sum (Y - t)^2 / (count n_out) of the network on
    count rows x (count x n_in) against t (count x n_out), both taken as the
    network's own inputs and targets (no normalisation), and its gradient with

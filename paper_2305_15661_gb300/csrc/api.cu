@@ -6,6 +6,7 @@
 // [assemble at the trial point -> reduce the CTA partials -> LM step]; the LM
 // step kernel sets the loop condition, so a whole solve is one graph launch.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -45,6 +46,16 @@ __global__ void residual_norms_finish_kernel(const double* part, int B, int nchu
 }  // namespace ift
 
 using namespace ift;
+
+namespace {
+
+// A named range for profilers (NVTX) around each public call that launches work.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+}  // namespace
 
 namespace {
 
@@ -653,6 +664,7 @@ ift_status ift_set_eq_weights(ift_ctx* c, int64_t nnz, const int32_t* elem, cons
 
 ift_status ift_reduced_residual_jacobian_dev(ift_ctx* c, const double* mu, const double* y, const double* z,
                                              double* S, double* T, double* H, double* J, void* stream) {
+  NvtxRange nvtx_range("ift_reduced_residual_jacobian_dev");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
@@ -667,6 +679,7 @@ ift_status ift_reduced_residual_jacobian_dev(ift_ctx* c, const double* mu, const
 
 ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const double* y, const double* z, double* S,
                                          double* T, double* H, double* J) {
+  NvtxRange nvtx_range("ift_reduced_residual_jacobian");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
@@ -692,6 +705,7 @@ ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const dou
 ift_status ift_element_eval(ift_ctx* c, const double* mu, const double* U, const double* x, int64_t n,
                             const int32_t* elems, double* R, double* JU, double* JUp, double* Jx, double* N,
                             double* dN) {
+  NvtxRange nvtx_range("ift_element_eval");
   if (!c) return IFT_ERR_ARG;
   if (!c->have_mesh) return c->fail(IFT_ERR_STATE, "set_mesh must come first");
   if (!mu || !U || !x || !elems || n < 1) return c->fail(IFT_ERR_ARG, "bad inspection arguments");
@@ -953,6 +967,7 @@ void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
 extern "C" {
 
 ift_status ift_solve_rom(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info) {
+  NvtxRange nvtx_range("ift_solve_rom");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
@@ -977,6 +992,7 @@ ift_status ift_solve_rom(ift_ctx* c, const double* mu, double* y, double* z, ift
 
 ift_status ift_solve_rom_dev(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info_host,
                              void* stream) {
+  NvtxRange nvtx_range("ift_solve_rom_dev");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
@@ -1230,6 +1246,7 @@ ift_status ift_set_eq_weights_batched(ift_ctx* c, int B, const int64_t* offsets,
 
 ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, const double* y, const double* z,
                                                  double* S, double* T, double* H, double* J) {
+  NvtxRange nvtx_range("ift_reduced_residual_jacobian_batched");
   ift_status st = check_batched(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
@@ -1263,6 +1280,7 @@ ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, c
 }
 
 ift_status ift_solve_rom_batched(ift_ctx* c, const double* mu, double* y, double* z, ift_solve_info* info) {
+  NvtxRange nvtx_range("ift_solve_rom_batched");
   ift_status st = check_batched(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
@@ -1297,6 +1315,7 @@ ift_status ift_solve_rom_batched(ift_ctx* c, const double* mu, double* y, double
 
 ift_status ift_solve_rom_batched_dev(ift_ctx* c, const double* mu, double* y, double* z, int32_t* status,
                                      void* stream) {
+  NvtxRange nvtx_range("ift_solve_rom_batched_dev");
   ift_status st = check_batched(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null argument");
@@ -1376,6 +1395,7 @@ ift_status launch_residual_norms(ift_ctx* c, int B, const double* d_pts, const d
 
 extern "C" ift_status ift_hdm_residual_norms(ift_ctx* c, int B, const double* mu, const double* y, const double* z,
                                              double* norms) {
+  NvtxRange nvtx_range("ift_hdm_residual_norms");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (B < 1 || !mu || !y || (c->kx > 0 && !z) || !norms) return c->fail(IFT_ERR_ARG, "bad argument");
@@ -1407,6 +1427,7 @@ extern "C" ift_status ift_hdm_residual_norms(ift_ctx* c, int B, const double* mu
 // ---------------------------------------------------------------------------
 extern "C" ift_status ift_element_gradients(ift_ctx* c, const double* mu, const double* y, const double* z,
                                             int64_t n, const int32_t* elems, double* out) {
+  NvtxRange nvtx_range("ift_element_gradients");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z) || !out || n < -1 || n == 0 || (n > 0 && !elems))
@@ -1490,6 +1511,7 @@ float time_launch(ift_ctx* c, cudaStream_t s, int reps, F fn) {
 }  // namespace
 
 extern "C" ift_status ift_autotune(ift_ctx* c, const double* mu, const double* y, const double* z, int32_t* chosen) {
+  NvtxRange nvtx_range("ift_autotune");
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");

@@ -497,7 +497,7 @@ struct ElemCore {
   __device__ void jvp_state(FE dUe, FP dUp, const signed char* bcs, T dR[NU]) {
 #pragma unroll
     for (int i = 0; i < NU; ++i) dR[i] = T(0);
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NQ; ++q) {
       T du[M];
 #pragma unroll
@@ -612,6 +612,24 @@ struct ElemCore {
   // (DIM M x ku) in W, then every lane updates its own flattened (row, c) entries;
   // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
   __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
+    if constexpr (sizeof(T) == 4) {
+      // FP32 (issue-bound): one lane per column of Phi_e, the whole derivative of R_e
+      // along it by Jacobian-vector products with no index arithmetic and no staging
+      for (int c = lane; c < ku; c += 32) {
+        T dR[NU];
+        auto fe = [&](int i) { return Phie[i * ku + c]; };
+        auto fp = [&](int i) {
+          const int kj = i / M, b = i - kj * M;
+          const long long off = poff[kj];
+          return off >= 0 ? PhiG[off + b * ku + c] : T(0);
+        };
+        jvp_state(fe, fp, bcs, dR);
+#pragma unroll
+        for (int i = 0; i < NU; ++i) A[i * k + c] = dR[i];
+      }
+      __syncwarp();
+      return;
+    }
     if constexpr (kExplicitVolume(NU, sizeof(T))) {
       // volume part of dR_e/dU_e: Jv[(i,a)][(j,b)] = -sum_q B_q[j] T_q[(i,a)][b] with
       // T_q[(i,a)][b] = sum_r D_r[q][i] Ahat_qr[a][b], formed in passes of RP rows whose

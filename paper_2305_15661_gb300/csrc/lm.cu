@@ -27,28 +27,46 @@ __device__ double active_norm(const LMState& s, int ku, int kx, bool full) {
 }
 
 // Cholesky of the n x n matrix in shared memory A (row-major, lower triangle used),
-// done by one warp: for each column, lane-parallel updates of the rows below.
+// done by one warp, right-looking: for each column j, the pivot, the column below
+// it, then the trailing lower triangle updated row by row (lane-owned rows).
 __device__ bool warp_cholesky(double* A, int n, int lane) {
   for (int j = 0; j < n; ++j) {
-    double d = 0.0;
-    if (lane == 0) {
-      double s = A[j * n + j];
-      for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-      d = s;
-    }
-    d = __shfl_sync(0xffffffffu, d, 0);
+    __syncwarp();
+    const double d = A[j * n + j];
     if (!(d > 0.0)) return false;
     const double r = sqrt(d);
     __syncwarp();
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      double t = A[i * n + j];
-      for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
-      A[i * n + j] = t / r;
-    }
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * n + j] /= r;
     if (lane == 0) A[j * n + j] = r;
     __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      const double lij = A[i * n + j];
+      for (int l = j + 1; l <= i; ++l) A[i * n + l] -= lij * A[l * n + j];
+    }
   }
+  __syncwarp();
   return true;
+}
+
+// Solves L L^T x = b in place in rhs (n values, shared memory) with the factor in
+// the lower triangle of L, by one warp: column-oriented forward and backward
+// substitution (one pivot per step, lane-parallel updates of the remaining rows).
+__device__ void warp_cholesky_solve(const double* L, int n, double* rhs, int lane) {
+  for (int j = 0; j < n; ++j) {  // L y = b
+    __syncwarp();
+    const double yj = rhs[j] / L[j * n + j];
+    __syncwarp();
+    if (lane == 0) rhs[j] = yj;
+    for (int i = j + 1 + lane; i < n; i += 32) rhs[i] -= L[i * n + j] * yj;
+  }
+  for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+    __syncwarp();
+    const double xi = rhs[i] / L[i * n + i];
+    __syncwarp();
+    if (lane == 0) rhs[i] = xi;
+    for (int j = lane; j < i; j += 32) rhs[j] -= L[i * n + j] * xi;
+  }
+  __syncwarp();
 }
 
 }  // namespace
@@ -180,21 +198,14 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
       ++nsh;
     }
     __syncwarp();
+    if (ok) {
+      for (int i = lane; i < ka; i += 32) rhs[i] = -s.g[i];
+      warp_cholesky_solve(Ms, ka, rhs, lane);
+    }
     int again = 0;
     if (lane == 0) {
       s.shifts += nsh;
       if (ok) {
-        for (int i = 0; i < ka; ++i) rhs[i] = -s.g[i];
-        for (int i = 0; i < ka; ++i) {  // L y = -g
-          double t = rhs[i];
-          for (int j = 0; j < i; ++j) t -= Ms[i * ka + j] * rhs[j];
-          rhs[i] = t / Ms[i * ka + i];
-        }
-        for (int i = ka - 1; i >= 0; --i) {  // L^T dz = y
-          double t = rhs[i];
-          for (int j = i + 1; j < ka; ++j) t -= Ms[j * ka + i] * rhs[j];
-          rhs[i] = t / Ms[i * ka + i];
-        }
         double slope = 0.0;
         for (int i = 0; i < ka; ++i) {
           s.dz[i] = rhs[i];

@@ -336,6 +336,37 @@ ift_status ift_mlp_set_params(ift_mlp* n, const double* params) {
   return IFT_OK;
 }
 
+ift_status ift_mlp_get_scaling(const ift_mlp* n, double* x_mean, double* x_std, double* t_mean, double* t_std) {
+  if (!n || !x_mean || !x_std || !t_mean || !t_std) return IFT_ERR_ARG;
+  for (int j = 0; j < n->n_in; ++j) {
+    x_mean[j] = n->xm[j];
+    x_std[j] = n->xs[j];
+  }
+  for (int j = 0; j < n->n_out; ++j) {
+    t_mean[j] = n->tm[j];
+    t_std[j] = n->ts[j];
+  }
+  return IFT_OK;
+}
+
+ift_status ift_mlp_set_scaling(ift_mlp* n, const double* x_mean, const double* x_std, const double* t_mean,
+                               const double* t_std) {
+  if (!n || !x_mean || !x_std || !t_mean || !t_std) return IFT_ERR_ARG;
+  for (int j = 0; j < n->n_in; ++j)
+    if (!(x_std[j] > 0.0) || !std::isfinite(x_mean[j])) return IFT_ERR_ARG;
+  for (int j = 0; j < n->n_out; ++j)
+    if (!(t_std[j] > 0.0) || !std::isfinite(t_mean[j])) return IFT_ERR_ARG;
+  for (int j = 0; j < n->n_in; ++j) {
+    n->xm[j] = x_mean[j];
+    n->xs[j] = x_std[j];
+  }
+  for (int j = 0; j < n->n_out; ++j) {
+    n->tm[j] = t_mean[j];
+    n->ts[j] = t_std[j];
+  }
+  return IFT_OK;
+}
+
 ift_status ift_mlp_loss_grad(ift_mlp* n, int64_t count, const double* x, const double* t, double* loss, double* grad) {
   if (!n || count < 1 || count > (1 << 20) || !x || !t) return IFT_ERR_ARG;
   const int b = (int)count;

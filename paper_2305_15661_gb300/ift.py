@@ -61,7 +61,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_solve_rom", "ift_solve_rom_dev", "ift_reduced_residual_jacobian_static",
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
            "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_element_gradients", "ift_mlp_create", "ift_mlp_destroy",
-           "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_loss_grad", "ift_mlp_train",
+           "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_get_scaling", "ift_mlp_set_scaling", "ift_mlp_loss_grad", "ift_mlp_train",
            "ift_mlp_predict", "ift_nearest_start"]
 
 
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_mlp_num_params": (i32, [vp, pl]),
         "ift_mlp_get_params": (i32, [vp, pd]),
         "ift_mlp_set_params": (i32, [vp, pd]),
+        "ift_mlp_get_scaling": (i32, [vp, pd, pd, pd, pd]),
+        "ift_mlp_set_scaling": (i32, [vp, pd, pd, pd, pd]),
         "ift_mlp_loss_grad": (i32, [vp, i64, pd, pd, pd, pd]),
         "ift_mlp_train": (i32, [vp, i64, pd, pd, i32, i32, dbl, ctypes.c_uint64, pd]),
         "ift_mlp_predict": (i32, [vp, i64, pd, pd]),
@@ -274,7 +276,8 @@ class Context:
         z = np.zeros(max(self.kx, 1)) if z0 is None else np.concatenate([_f64(z0), np.zeros(1)])
         info = SolveInfo()
         st = load().ift_solve_rom(self._h, _pd(_f64(mu)), _pd(y), _pd(z), ctypes.byref(info))
-        self._check(st, allow_positive=True)
+        if st != -5:  # a non-physical start is a result of the solve, reported in status
+            self._check(st, allow_positive=True)
         return {"status": int(st), "w": y, "tau": z[:self.kx], "init_iters": info.init_iters, "iters": info.iters,
                 "trials": info.trials, "shifts": info.shifts, "J": info.J, "normS": info.normS,
                 "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters, "fp32_trials": info.fp32_trials}
@@ -349,7 +352,8 @@ class Context:
         z = np.zeros(max(B * self.kx, 1)) if z0 is None else np.concatenate([_f64(z0).ravel(), np.zeros(1)])
         info = (SolveInfo * B)()
         st = load().ift_solve_rom_batched(self._h, _pd(_f64(mus)), _pd(y), _pd(z), info)
-        self._check(st, allow_positive=True)
+        if st != -5:  # non-physical queries are reported per query in info
+            self._check(st, allow_positive=True)
         return {"status": int(st), "w": y.reshape(B, self.ku), "tau": z[:B * self.kx].reshape(B, self.kx),
                 "info": [{"status": i.status, "init_iters": i.init_iters, "iters": i.iters, "trials": i.trials,
                           "J": i.J, "normS": i.normS, "normT": i.normT, "g0": i.g0, "fp32_iters": i.fp32_iters,
@@ -414,6 +418,15 @@ class MLP:
         params = _f64(params)
         assert params.size == self.n_params
         self._check(load().ift_mlp_set_params(self._h, _pd(params)), "ift_mlp_set_params")
+
+    def get_scaling(self):
+        xm, xs, tm, ts = np.zeros(self.n_in), np.zeros(self.n_in), np.zeros(self.n_out), np.zeros(self.n_out)
+        self._check(load().ift_mlp_get_scaling(self._h, _pd(xm), _pd(xs), _pd(tm), _pd(ts)), "ift_mlp_get_scaling")
+        return xm, xs, tm, ts
+
+    def set_scaling(self, xm, xs, tm, ts):
+        xm, xs, tm, ts = (_f64(v) for v in (xm, xs, tm, ts))
+        self._check(load().ift_mlp_set_scaling(self._h, _pd(xm), _pd(xs), _pd(tm), _pd(ts)), "ift_mlp_set_scaling")
 
     def loss_grad(self, x, t, want_grad=True):
         x, t = _f64(x), _f64(t)

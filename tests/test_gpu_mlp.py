@@ -183,3 +183,19 @@ def test_warm_start_beats_nearest_training_point():
     # the learned start is closer to the solution and needs fewer LM iterations
     assert np.median(m["start_err"]) < 0.5 * np.median(nn["start_err"])
     assert m["iters"][ok].mean() < nn["iters"][ok].mean()
+
+
+def test_trained_network_checkpoint_roundtrip(tmp_path):
+    from paper_2305_15661_gb300 import checkpoint as ck
+
+    mus = W.mu_box_samples(70, 1, 128)
+    t = np.stack([mus[:, 0] * (3 + k) + np.sin(40 * mus[:, 1]) for k in range(4)], axis=1)
+    net = ift.MLP(2, 32, 2, 4, seed=71)
+    net.train(mus, t, epochs=50, batch=32, lr=3e-3, seed=72)
+    wl = W.euler_workload(n=4, p=1, k_u=3, k_x=1, seed=5)
+    ck.save_model(str(tmp_path / "m"), wl, mlp=net, train_mu=mus, train_y=t)
+    arrays, meta = ck.load(str(tmp_path / "m"))
+    net2 = ck.restore_mlp(arrays, meta)
+    q = W.mu_box_samples(73, 1, 17)
+    np.testing.assert_array_equal(net2.predict(q), net.predict(q))
+    np.testing.assert_array_equal(arrays["train_y"], t)
