@@ -315,6 +315,12 @@ def run_ours(args):
     return 0
 
 
+def _precision(args):
+    from paper_2305_15661_gb300 import ift
+
+    return {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED, "fp32jac": ift.FP32_JACOBIAN}[args.precision]
+
+
 def _contraction(args):
     from paper_2305_15661_gb300 import ift
 
@@ -338,7 +344,7 @@ def run_assembly(args):
     else:
         wl = make_workload()
     stream = torch.cuda.Stream(device=dev)
-    prec = ift.FP64 if args.precision == "fp64" else ift.FP32
+    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.FP32, "fp32jac": ift.FP32_JACOBIAN}[args.precision]
     ctx = ift.Context.from_workload(wl, precision=prec, stream=stream.cuda_stream, contraction=_contraction(args))
     shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval) if args.autotune else None
     k = wl.ku + wl.kx
@@ -389,7 +395,7 @@ def run_batched(args):
         wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
         sets = W.eq_weight_sets(wl, B, seed=3)
     stream = torch.cuda.Stream(device=dev)
-    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
+    prec = _precision(args)
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
                                     contraction=_contraction(args), max_iters=args.max_iters)
     ctx.set_eq_weights_batched(sets)
@@ -496,7 +502,7 @@ def run_warmstart(args):
     mu_t = W.mu_box_samples(5, 1, n_train)
     mu_q = W.mu_box_samples(6, 1, n_query)
     stream = torch.cuda.Stream(device=dev)
-    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
+    prec = _precision(args)
     out = {"mode": "warmstart", "precision": args.precision, "contraction": args.contraction, "train_solves": n_train, "queries": n_query,
            "rho_nnz": int(len(rho_set[0])), "k_u": ku, "k_x": kx}
 
@@ -637,6 +643,53 @@ def run_burgers(args):
     return 0
 
 
+def run_precisions(args):
+    """Single-query ROM solves of the benchmark workload (20,000 elements, p = 2,
+    k = 20 + 4, rho = 1, tol 1e-8) in each precision mode: FP64; FP32 Jacobians and
+    contraction with the FP64 residual and gradient at every iteration; the
+    two-stage mixed solve. Converged points compared with the FP64 solve."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift
+
+    dev = torch.device("cuda", 0)
+    ift.load()
+    wl = make_workload()
+    stream = torch.cuda.Stream(device=dev)
+    out = {"mode": "precisions", "workload": WORKLOAD, "tol": 1e-8, "solves": {}}
+    ref = None
+    for name, prec, contr in (("fp64", ift.FP64, ift.CONTRACT_FP), ("fp32jac", ift.FP32_JACOBIAN, ift.CONTRACT_FP),
+                              ("fp32jac_tf32", ift.FP32_JACOBIAN, ift.CONTRACT_TF32),
+                              ("mixed", ift.MIXED, ift.CONTRACT_FP)):
+        ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream, contraction=contr)
+        ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
+        mu_d = torch.as_tensor(wl.mus[0], dtype=torch.float64, device=dev)
+        y = torch.zeros(wl.ku, dtype=torch.float64, device=dev)
+        z = torch.zeros(wl.kx, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            info = ctx.solve_rom_dev(mu_d, y, z, stream=stream.cuda_stream, want_info=True)
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.solve_rom_dev(mu_d, y, z, stream=stream.cuda_stream, want_info=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        zz = np.concatenate([y.cpu().numpy(), z.cpu().numpy()])
+        row = {"ms": statistics.median(ms), "solves_per_s": 1e3 / statistics.median(ms), "status": info["status"],
+               "lm_steps": info["init_iters"] + info["iters"] + info["fp32_iters"], "J": info["J"]}
+        if ref is None:
+            ref = zz
+        else:
+            row["rel_dz_vs_fp64"] = float(np.linalg.norm(zz - ref) / np.linalg.norm(ref))
+        out["solves"][name] = row
+        ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_greedy(args):
     """Greedy search (Eq. greedy0) over 256 candidate parameters on the 20,000-element
     mesh: batched hyperreduced solves with one shared weight set, then the full HDM
@@ -651,7 +704,7 @@ def run_greedy(args):
     wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
     rho = W.eq_weight_sets(wl, 1, seed=3, lo=400, hi=401)[0]
     mus = W.mu_box_samples(7, 1, B)
-    prec = {"fp64": ift.FP64, "fp32": ift.FP32, "mixed": ift.MIXED}[args.precision]
+    prec = _precision(args)
     stream = torch.cuda.Stream(device=torch.device("cuda", 0))
     ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
                                     contraction=_contraction(args))
@@ -691,10 +744,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers"],
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers", "precisions"],
                     default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "fp32", "mixed", "fp32jac"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly, batched and warmstart")
     ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32"], default="fp",
                     help="FP32/mixed contexts: form H with FP32 FMAs, TF32 or 3xTF32 tensor cores")
@@ -726,6 +779,8 @@ def main():
         return run_greedy(args)
     if args.mode == "burgers":
         return run_burgers(args)
+    if args.mode == "precisions":
+        return run_precisions(args)
     return run_ours(args)
 
 

@@ -63,10 +63,17 @@ enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
    elements, FP64 sums across warps and CTAs. IFT_MIXED: evaluation calls as
    IFT_FP32; solves run the LM with FP32 assemblies to a relative optimality of
    1e-6 (or tol if larger), or until a line search needs more than 8 halvings
-   (FP32 rounding in J~ ends the FP32 stage), then continue from that point with
-   FP64 assemblies to tol. The LM normal equations, line search and stopping test
-   are FP64 in every mode. */
-enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2 };
+   (FP32 rounding in J~ ends the FP32 stage), then continue from that point to
+   tol with the IFT_FP32_JACOBIAN evaluation (H from FP32, S~, T~, J~ in FP64).
+   The LM normal equations, line search and stopping test are FP64 in every mode. */
+enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2, IFT_FP32_JACOBIAN = 3 };
+/* IFT_FP32_JACOBIAN: every LM iteration (and every evaluation call) takes the
+   Gauss-Newton matrix H from the FP32 element Jacobians and contraction (tensor
+   cores with IFT_CONTRACT_TF32 / _3XTF32) and S~, T~, J~ from an FP64 pass that
+   evaluates R_e and applies the transposed element Jacobian to it (no Jacobian
+   columns formed). The optimality test, the line search and the normal
+   equations are FP64, so a solve converges to the FP64 optimum; H only steers the
+   step. */
 /* How FP32 evaluations form H += rho A_e^T A_e (Eq. levmarq-elem): FP = FP32
    fused multiply-adds; TF32 = tensor cores with TF32 inputs (10-bit mantissa)
    and FP32 accumulation, H to about 1e-3 relative; 3XTF32 = tensor cores with

@@ -43,6 +43,7 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
 __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum);
 __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
+__global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states);
 }  // namespace ift
 
 using namespace ift;
@@ -152,13 +153,17 @@ struct ift_ctx {
   int bplan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t bplan_smem[2][2] = {{0, 0}, {0, 0}};
   int bplan_epoch[2] = {-1, -1};
-  cudaGraph_t bgraph[2] = {nullptr, nullptr};
-  cudaGraphExec_t bgraph_exec[2] = {nullptr, nullptr};
-  int bgraph_epoch[2] = {-1, -1};
+  cudaGraph_t bgraph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t bgraph_exec[3] = {nullptr, nullptr, nullptr};
+  int bgraph_epoch[3] = {-1, -1, -1};
+  // FP64 gradient pass results: [g | J | count] for the single query (k + 2) and per query (B x (k + 2))
+  double* d_gres = nullptr;
+  double* d_bgres = nullptr;
   // solve graphs, per working precision
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-  int graph_epoch[2] = {-1, -1};
+  // solve graphs per body kind: [0] FP64, [1] FP32, [2] FP32 Jacobians + FP64 gradient
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
+  int graph_epoch[3] = {-1, -1, -1};
   int epoch = 0;
   bool graph_failed = false;
 
@@ -178,6 +183,8 @@ struct ift_ctx {
   int nacc() const { return (ku + kx) * (ku + kx) + ku + kx + 2; }
   // working precision of the evaluation calls: FP64 contexts 0, FP32 and mixed contexts 1
   int eval_wp() const { return cfg.precision == IFT_FP64 ? 0 : 1; }
+  // body kind of an evaluation call: FP64, FP32, or FP32 Jacobians with the FP64 gradient
+  int eval_slot() const { return cfg.precision == IFT_FP32_JACOBIAN ? 2 : eval_wp(); }
 };
 
 #define CK(call, what)                          \
@@ -201,7 +208,7 @@ cudaError_t dalloc(P*& p, size_t n) {
 }
 
 void drop_graph(ift_ctx* c) {
-  for (int wp = 0; wp < 2; ++wp) {
+  for (int wp = 0; wp < 3; ++wp) {
     if (c->graph_exec[wp]) cudaGraphExecDestroy(c->graph_exec[wp]);
     if (c->graph[wp]) cudaGraphDestroy(c->graph[wp]);
     c->graph_exec[wp] = nullptr;
@@ -314,6 +321,36 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   return IFT_OK;
 }
 
+// The FP64 gradient pass at (w, tau): S~, T~, J~ and the non-physical count into
+// the [g | J | count] part of out (the H part is left as it is).
+ift_status launch_grad(ift_ctx* c, const double* w, const double* tau, const double* mu, double* out,
+                       const int* skip, cudaStream_t s) {
+  if (c->plan_epoch[0] != c->epoch) {
+    ift_status st = plan_launch(c, 0);
+    if (st != IFT_OK) return st;
+  }
+  const KernelSet& ks = c->ks[0];
+  const int k = c->ku + c->kx, grid = c->plan_grid[0][1];
+  AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
+  cudaError_t e = ks.assemble_grad(&a, grid, 32 * c->wpc[0], c->plan_smem[0][1], s);
+  if (e != cudaSuccess) return c->cuda_fail(e, "gradient pass launch");
+  reduce_partials_kernel<<<(k + 2 + 31) / 32, 256, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres);
+  merge_grad_kernel<<<1, 64, 0, s>>>(c->d_gres, k, c->nacc(), out, nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return c->cuda_fail(e, "gradient reduce launch");
+  return IFT_OK;
+}
+
+// Evaluation for a loop body or an evaluation call: slot 0/1 the FP64 / FP32 fused
+// assembly; slot 2 the FP32 fused assembly (H) followed by the FP64 gradient pass.
+ift_status launch_eval(ift_ctx* c, int slot, const double* w, const double* tau, const double* mu, double* out,
+                       const int* skip, cudaStream_t s) {
+  if (slot < 2) return launch_assemble(c, slot, true, w, tau, mu, out, skip, s);
+  ift_status st = launch_assemble(c, 1, true, w, tau, mu, out, skip, s);
+  if (st != IFT_OK) return st;
+  return launch_grad(c, w, tau, mu, out, skip, s);
+}
+
 ift_status check_ready(ift_ctx* c) {
   if (!c) return IFT_ERR_ARG;
   if (!c->have_mesh || !c->have_bases) return c->fail(IFT_ERR_STATE, "set_mesh and set_bases must come first");
@@ -356,8 +393,9 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     g_create_error = "degree p must be 1, 2 or 3";
     return IFT_ERR_ARG;
   }
-  if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32 && cfg->precision != IFT_MIXED) {
-    g_create_error = "precision must be IFT_FP64, IFT_FP32 or IFT_MIXED";
+  if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32 && cfg->precision != IFT_MIXED &&
+      cfg->precision != IFT_FP32_JACOBIAN) {
+    g_create_error = "precision must be IFT_FP64, IFT_FP32, IFT_MIXED or IFT_FP32_JACOBIAN";
     return IFT_ERR_ARG;
   }
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->contraction != IFT_CONTRACT_TF32 &&
@@ -474,10 +512,12 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_partial);
   dfree(c->d_phit);
   dfree(c->d_lm);
-  for (int wp = 0; wp < 2; ++wp) {
+  for (int wp = 0; wp < 3; ++wp) {
     if (c->bgraph_exec[wp]) cudaGraphExecDestroy(c->bgraph_exec[wp]);
     if (c->bgraph[wp]) cudaGraphDestroy(c->bgraph[wp]);
   }
+  dfree(c->d_gres);
+  dfree(c->d_bgres);
   dfree(c->d_chunk_start);
   dfree(c->d_chunk_query);
   dfree(c->d_qchunk);
@@ -623,6 +663,7 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   CK(dalloc(c->d_res, nacc), "alloc result");
   CK(dalloc(c->d_partial, (size_t)c->max_parts * nacc), "alloc partials");
   CK(dalloc(c->d_colsum, (size_t)4 * k_u), "alloc column sums");
+  CK(dalloc(c->d_gres, (size_t)nacc), "alloc gradient result");
   phi_colsum_kernel<<<k_u, 256, 0, c->stream>>>(c->d_Phi, (long)N_u, k_u, c->m, c->d_colsum);
   CK(cudaGetLastError(), "column sums");
   CK(cudaStreamSynchronize(c->stream), "column sums");
@@ -669,7 +710,7 @@ ift_status ift_reduced_residual_jacobian_dev(ift_ctx* c, const double* mu, const
   if (st != IFT_OK) return st;
   if (!mu || !y || (c->kx > 0 && !z)) return c->fail(IFT_ERR_ARG, "null input pointer");
   cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-  st = launch_assemble(c, c->eval_wp(), true, y, c->kx > 0 ? z : c->d_tau, mu, c->d_res, nullptr, s);
+  st = launch_eval(c, c->eval_slot(), y, c->kx > 0 ? z : c->d_tau, mu, c->d_res, nullptr, s);
   if (st != IFT_OK) return st;
   const int nacc = c->nacc();
   unpack_kernel<<<(nacc + 255) / 256, 256, 0, s>>>(c->d_res, c->ku, c->kx, S, T, H, J);
@@ -687,7 +728,7 @@ ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const dou
   CK(cudaMemcpyAsync(c->d_mu, mu, (c->dim == 1 ? 1 : 2) * 8, cudaMemcpyHostToDevice, s), "copy mu");
   CK(cudaMemcpyAsync(c->d_w, y, c->ku * 8, cudaMemcpyHostToDevice, s), "copy y");
   if (c->kx > 0) CK(cudaMemcpyAsync(c->d_tau, z, c->kx * 8, cudaMemcpyHostToDevice, s), "copy z");
-  st = launch_assemble(c, c->eval_wp(), true, c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
+  st = launch_eval(c, c->eval_slot(), c->d_w, c->d_tau, c->d_mu, c->d_res, nullptr, s);
   if (st != IFT_OK) return st;
   const int nacc = c->nacc(), k = c->ku + c->kx;
   std::vector<double> res(nacc);
@@ -837,12 +878,14 @@ LMConsts stage_consts(ift_ctx* c, int wp) {
 }
 
 // The loop body: assemble at the trial point, reduce, LM step.
-ift_status enqueue_body(ift_ctx* c, int wp, cudaStream_t s, unsigned long long handle, int use_cond) {
+// slot 0/1: FP64 / FP32 assembly; slot 2: FP32 assembly for H, then the FP64
+// gradient pass for S~, T~, J~ (the LM runs with the FP64 constants).
+ift_status enqueue_body(ift_ctx* c, int slot, cudaStream_t s, unsigned long long handle, int use_cond) {
   double* trial = (double*)((char*)c->d_lm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
-  ift_status st = launch_assemble(c, wp, true, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
+  ift_status st = launch_eval(c, slot, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
   if (st != IFT_OK) return st;
-  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, stage_consts(c, wp), handle, use_cond);
+  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, stage_consts(c, slot == 2 ? 0 : slot), handle, use_cond);
   CK(cudaGetLastError(), "LM step launch");
   return IFT_OK;
 }
@@ -890,9 +933,11 @@ ift_status build_graph(ift_ctx* c, int wp) {
   if (c->graph[wp]) cudaGraphDestroy(c->graph[wp]);
   c->graph_exec[wp] = nullptr;
   c->graph[wp] = nullptr;
-  if (c->plan_epoch[wp] != c->epoch) {
-    ift_status st = plan_launch(c, wp);
-    if (st != IFT_OK) return st;
+  for (int tp = 0; tp < 2; ++tp) {
+    if ((tp == wp || wp == 2) && c->plan_epoch[tp] != c->epoch) {
+      ift_status st = plan_launch(c, tp);
+      if (st != IFT_OK) return st;
+    }
   }
   ift_status st = build_while_graph(c, &c->graph[wp], &c->graph_exec[wp], [&](cudaStream_t cs, unsigned long long h) {
     return enqueue_body(c, wp, cs, h, 1);
@@ -906,7 +951,7 @@ ift_status build_graph(ift_ctx* c, int wp) {
 // e.g. so that a profiler that does not enter conditional graph nodes sees every launch.
 // Bodies are enqueued in groups of 8; after a group the done flag is read back.
 ift_status run_solve_loop(ift_ctx* c, int wp, cudaStream_t s) {
-  const LMConsts k = lm_consts(c, stage_tol(c, wp));
+  const LMConsts k = lm_consts(c, stage_tol(c, wp == 2 ? 0 : wp));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
   for (int b = 0; b <= k.body_limit; b += 8) {
     for (int j = 0; j < 8; ++j) {
@@ -937,11 +982,13 @@ ift_status run_stage(ift_ctx* c, int wp, cudaStream_t s) {
 // restarted (joint phase) at the FP32 stage's final point.
 ift_status run_solve(ift_ctx* c, cudaStream_t s) {
   if (c->cfg.precision == IFT_FP64) return run_stage(c, 0, s);
+  if (c->cfg.precision == IFT_FP32_JACOBIAN) return run_stage(c, 2, s);
   ift_status st = run_stage(c, 1, s);
   if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
   lm_restart_kernel<<<1, 64, 0, s>>>(c->d_lm, 1, c->ku, c->kx);
   CK(cudaGetLastError(), "stage restart");
-  return run_stage(c, 0, s);
+  // the finishing stage: FP64 residual, gradient and objective, H from FP32
+  return run_stage(c, 2, s);
 }
 
 void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
@@ -1091,15 +1138,54 @@ ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long ws
   return IFT_OK;
 }
 
+// The FP64 gradient pass of every unfinished query at its trial point: chunk rows
+// of [g | J | count], summed per query and merged into the query's result row.
+ift_status launch_batched_grad(ift_ctx* c, const double* w, long wstride, const int* done, long donestride,
+                               const LMState* states, cudaStream_t s) {
+  if (c->bplan_epoch[0] != c->epoch) {
+    ift_status st = plan_batched(c, 0);
+    if (st != IFT_OK) return st;
+  }
+  const int k = c->ku + c->kx;
+  BatchArgs b;
+  b.chunk_start = c->d_chunk_start;
+  b.chunk_query = c->d_chunk_query;
+  b.n_chunks = c->n_chunks;
+  b.w = w;
+  b.wstride = wstride;
+  b.mu = c->d_bmu;
+  b.mustride = 2;
+  b.done = done;
+  b.donestride = donestride;
+  AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, w + c->ku, c->d_bmu, false, nullptr);
+  a.elems = c->d_belems;
+  a.rho = c->d_brho;
+  a.partial = c->d_bpartial;
+  cudaError_t e = c->ks[0].assemble_batched_grad(&a, &b, c->bplan_grid[0][1], 32 * c->bwpc[0],
+                                                  c->bplan_smem[0][1], s);
+  if (e != cudaSuccess) return c->cuda_fail(e, "batched gradient pass launch");
+  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, k + 2, states, c->d_bgres);
+  merge_grad_kernel<<<c->B, 64, 0, s>>>(c->d_bgres, k, c->nacc(), c->d_bres, states);
+  CK(cudaGetLastError(), "batched gradient reduce launch");
+  return IFT_OK;
+}
+
 // The batched loop body in working precision wp: assemble every unfinished query,
 // reduce per query, one LM step per query, loop condition.
-ift_status enqueue_batched_body(ift_ctx* c, int wp, cudaStream_t s, unsigned long long handle, int use_cond) {
+// slot 0/1: FP64 / FP32 batched assembly; slot 2: FP32 assembly for H, then the FP64
+// gradient pass for S~, T~, J~ of every unfinished query.
+ift_status enqueue_batched_body(ift_ctx* c, int slot, cudaStream_t s, unsigned long long handle, int use_cond) {
   const double* trial = (const double*)((char*)c->d_blm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_blm + offsetof(LMState, done));
-  ift_status st = launch_batched(c, wp, true, trial, (long)(sizeof(LMState) / sizeof(double)), done,
-                                 (long)(sizeof(LMState) / sizeof(int)), c->d_blm, s);
+  const long wstride = (long)(sizeof(LMState) / sizeof(double)), istride = (long)(sizeof(LMState) / sizeof(int));
+  const int wp = slot == 2 ? 1 : slot;
+  ift_status st = launch_batched(c, wp, true, trial, wstride, done, istride, c->d_blm, s);
   if (st != IFT_OK) return st;
-  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), stage_consts(c, wp));
+  if (slot == 2) {
+    st = launch_batched_grad(c, trial, wstride, done, istride, c->d_blm, s);
+    if (st != IFT_OK) return st;
+  }
+  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), stage_consts(c, slot == 2 ? 0 : slot));
   batch_condition_kernel<<<1, 256, 0, s>>>(c->d_blm, c->B, c->d_active, handle, use_cond);
   CK(cudaGetLastError(), "batched LM launch");
   return IFT_OK;
@@ -1110,9 +1196,11 @@ ift_status build_batched_graph(ift_ctx* c, int wp) {
   if (c->bgraph[wp]) cudaGraphDestroy(c->bgraph[wp]);
   c->bgraph_exec[wp] = nullptr;
   c->bgraph[wp] = nullptr;
-  if (c->bplan_epoch[wp] != c->epoch) {
-    ift_status st = plan_batched(c, wp);
-    if (st != IFT_OK) return st;
+  for (int tp = 0; tp < 2; ++tp) {
+    if ((tp == wp || wp == 2) && c->bplan_epoch[tp] != c->epoch) {
+      ift_status st = plan_batched(c, tp);
+      if (st != IFT_OK) return st;
+    }
   }
   ift_status st = build_while_graph(c, &c->bgraph[wp], &c->bgraph_exec[wp],
                                     [&](cudaStream_t cs, unsigned long long h) {
@@ -1126,7 +1214,7 @@ ift_status build_batched_graph(ift_ctx* c, int wp) {
 ift_status run_batched_stage(ift_ctx* c, int wp, cudaStream_t s) {
   static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
   if (no_graph) {
-    const LMConsts k = lm_consts(c, stage_tol(c, wp));
+    const LMConsts k = lm_consts(c, stage_tol(c, wp == 2 ? 0 : wp));
     for (int b = 0; b <= k.body_limit; b += 8) {
       for (int j = 0; j < 8; ++j) {
         ift_status st = enqueue_batched_body(c, wp, s, 0ull, 0);
@@ -1153,11 +1241,13 @@ ift_status run_batched_stage(ift_ctx* c, int wp, cudaStream_t s) {
 // scan per body cost more than the overlap of the two stages' tails saved.)
 ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
   if (c->cfg.precision == IFT_FP64) return run_batched_stage(c, 0, s);
+  if (c->cfg.precision == IFT_FP32_JACOBIAN) return run_batched_stage(c, 2, s);
   ift_status st = run_batched_stage(c, 1, s);
   if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
   lm_restart_kernel<<<c->B, 64, 0, s>>>(c->d_blm, c->B, c->ku, c->kx);
   CK(cudaGetLastError(), "stage restart");
-  return run_batched_stage(c, 0, s);
+  // the finishing stage: FP64 residual, gradient and objective, H from FP32
+  return run_batched_stage(c, 2, s);
 }
 
 // Split every query's items into chunks of c->chunk elements (one warp each) and size
@@ -1234,6 +1324,7 @@ ift_status ift_set_eq_weights_batched(ift_ctx* c, int B, const int64_t* offsets,
   CK(dalloc(c->d_bmu, (size_t)B * 2), "alloc mu");
   CK(dalloc(c->d_bw, (size_t)B * k), "alloc points");
   CK(dalloc(c->d_bres, (size_t)B * nacc), "alloc results");
+  CK(dalloc(c->d_bgres, (size_t)B * (c->ku + c->kx + 2)), "alloc gradient results");
   CK(dalloc(c->d_blm, (size_t)B), "alloc solver states");
   CK(dalloc(c->d_active, 1), "alloc active count");
   CK(cudaMemcpy(c->d_belems, elem, (size_t)total * 4, cudaMemcpyHostToDevice), "copy weights");
@@ -1261,6 +1352,7 @@ ift_status ift_reduced_residual_jacobian_batched(ift_ctx* c, const double* mu, c
   if (st != IFT_OK) return st;
   CK(cudaMemcpyAsync(c->d_bw, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s), "copy points");
   st = launch_batched(c, c->eval_wp(), true, c->d_bw, k, nullptr, 0, nullptr, s);
+  if (st == IFT_OK && c->eval_slot() == 2) st = launch_batched_grad(c, c->d_bw, k, nullptr, 0, nullptr, s);
   if (st != IFT_OK) return st;
   std::vector<double> res((size_t)B * nacc);
   CK(cudaMemcpyAsync(res.data(), c->d_bres, res.size() * 8, cudaMemcpyDeviceToHost, s), "copy results");

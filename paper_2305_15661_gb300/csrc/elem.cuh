@@ -193,6 +193,10 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
+      {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), dU_e, dU_e' (NU + NU')
+        const size_t wa = (size_t)NQ * M + (size_t)2 * NF * NFQ * M + NU + NUP;
+        if (wa > w) w = wa;
+      }
       if (kExplicitVolume(NU, sizeof(T))) {  // T_q (RP M) and one pass of Jv rows (RP NU)
         const int np = (NU * NU + kJvPass - 1) / kJvPass, rp = NU / np;
         const size_t we = (size_t)rp * (M + NU);
@@ -461,6 +465,100 @@ struct ElemCore {
       }
     }
     return __any_sync(0xffffffffu, bad);
+  }
+
+  // Adjoint of steps 4-5 (the transposed element Jacobian applied to R_e):
+  // dUe = (dR_e/dU_e)^T R_e (n_u values) and dUp = (dR_e/dU_e')^T R_e (n_u'), from the
+  // pointwise flux Jacobians of step 4. Volume: dR[i][a] = -sum_q sum_r D_r[q][i]
+  // (Ahat_qr dU_q)[a] with dU_q = B_q dU_e, so the adjoint is dUe[j][b] -= sum_q B_q[j]
+  // t_q[b], t_q = sum_r Ahat_qr^T (D_r[q]^T R). Faces: dR[node][a] += fw Lt (Hp dU+ +
+  // Hm dU-)[a]; with lam_pt = sum_j fw Lt[j] R[node_j] the adjoint lifts Hp^T lam onto
+  // the interior trace nodes and Hm^T lam onto the neighbour's (or, on outflow faces,
+  // where U- = U+, onto the interior ones too). dUe and dUp live in W after the staging.
+  __device__ void adj_state(int lane, const signed char* bcs, T*& dUe, T*& dUp) {
+    constexpr int NPT = NF * NFQ;
+    T* tq = W;                  // [NQ][M]
+    T* mp = W + NQ * M;         // [NPT][M]: Hp^T lam
+    T* mm = mp + NPT * M;       // [NPT][M]: Hm^T lam
+    dUe = mm + NPT * M;         // [NU]
+    dUp = dUe + NU;             // [NUP]
+    for (int t = lane; t < NQ + NPT; t += 32) {
+      if (t < NQ) {
+        const int q = t;
+        T sr[DIM][M];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r)
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) v += D[(r * NQ + q) * NB + i] * R[i * M + a];
+            sr[r][a] = v;
+          }
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          T v = T(0);
+#pragma unroll
+          for (int r = 0; r < DIM; ++r)
+#pragma unroll
+            for (int a = 0; a < M; ++a) v += Ah[((q * DIM + r) * M + a) * M + b] * sr[r][a];
+          tq[q * M + b] = v;
+        }
+      } else {
+        const int pt = t - NQ, kf = pt / NFQ, f = pt - kf * NFQ;
+        T lam[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          T v = T(0);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const int node = (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+            v += Lt[f * NT + j] * R[node * M + a];
+          }
+          lam[a] = fw[f] * v;
+        }
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          T vp = T(0), vm = T(0);
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            vp += Hp[(pt * M + a) * M + b] * lam[a];
+            vm += Hm[(pt * M + a) * M + b] * lam[a];
+          }
+          mp[pt * M + b] = vp;
+          mm[pt * M + b] = vm;
+        }
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < NU + NUP; e += 32) {
+      T v = T(0);
+      if (e < NU) {
+        const int j = e / M, b = e - j * M;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v -= B[q * NB + j] * tq[q * M + b];
+#pragma unroll
+        for (int kf = 0; kf < NF; ++kf) {
+          const int jj = face_pos(kf, j);
+          if (jj < 0) continue;
+          const bool outflow = bcs[kf] == 2;
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) {
+            const int pt = kf * NFQ + f;
+            v += Lt[f * NT + jj] * (mp[pt * M + b] + (outflow ? mm[pt * M + b] : T(0)));
+          }
+        }
+        dUe[e] = v;
+      } else {
+        const int i = e - NU, kj = i / M, b = i - kj * M, kf = kj / NT, jj = kj - kf * NT;
+        if (bcs[kf] == 0) {
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) v += Lt[f * NT + jj] * mm[(kf * NFQ + f) * M + b];
+        }
+        dUp[i] = v;
+      }
+    }
+    __syncwarp();
   }
 
   // Step 5: residual entries.
@@ -1085,6 +1183,66 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
     __syncwarp();
 }
 
+// One element of the gradient pass (FP64 residual, gradient and objective for LM
+// iterations whose Gauss-Newton matrix comes from an FP32 assembly): R_e, then
+// g += rho [Phi_e^T dUe + Phi_e'^T dUp ; Psi_e^T (dR_e/dx_e^T R_e + dN_e^T N_e)] with
+// (dUe, dUp) the adjoint of the state Jacobians applied to R_e (no Jacobian
+// columns are formed for the state), J += rho (|R_e|^2 + N_e^2) / 2.
+template <class T, int PROB, int P>
+__device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C, const AsmArgs<T>& a, int e,
+                                                  double rho, const T* wT, const double* tauD, const double* mu,
+                                                  int lane) {
+  using Dd = Disc<PROB, P>;
+  constexpr int DIM = Dd::DIM, M = Dd::M, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
+                NV = Dd::NV;
+  const int ku = a.ku, kx = a.kx, k = ku + kx;
+  const int* vv = &a.ev[(long)e * NV];
+  signed char bcs[NF];
+  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs);
+  const bool dist = a.kappa != 0.0;
+  if (dist && lane == 0) {
+    double Xe[6];
+    for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+    C.distortion(Xe, a.kappa, a.eps);
+  }
+  __syncwarp();
+  const T Ne = dist ? (T)C.dN[NXE] : T(0);
+  const T rT = (T)rho;
+  T *dUe, *dUp;
+  C.adj_state(lane, bcs, dUe, dUp);
+  T* g = C.acc + acc_tail(k);
+  for (int c = lane; c < ku; c += 32) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) s += C.Phie[i * ku + c] * dUe[i];
+#pragma unroll
+    for (int i = 0; i < NUP; ++i) {
+      const long long off = C.poff[i / M];
+      if (off >= 0) s += C.PhiG[off + (i % M) * ku + c] * dUp[i];
+    }
+    g[c] += rT * s;
+  }
+  __syncwarp();
+  if (kx > 0) {
+    C.jac_geom(lane, mu, ku, kx, k, dist);  // mesh columns of A_e (overwrites the adjoint staging)
+    for (int c = lane; c < kx; c += 32) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) s += C.A[i * k + ku + c] * C.R[i];
+      if (dist) s += C.dNt[c] * Ne;
+      g[ku + c] += rT * s;
+    }
+  }
+  if (lane == 0) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) s += C.R[i] * C.R[i];
+    g[k] += T(0.5) * rT * (s + Ne * Ne);
+    if (bad) g[k + 1] += T(1);
+  }
+  __syncwarp();
+}
+
 // Upper-triangle (row <= col) pairs of the k x k Gauss-Newton matrix, row-major order.
 __device__ inline void build_pairs(unsigned char* pairs, int k) {
   int n = 0;
@@ -1112,7 +1270,7 @@ __device__ inline int acc_source(int i, int k) {
 
 // The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false)
 // for one query: a grid-stride loop of warps over the items; one FP64 partial per CTA.
-template <class T, int PROB, int P, bool JAC, bool TC = false>
+template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
 __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1135,16 +1293,19 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
     const int e = a.elems ? a.elems[it] : (int)it;
     const double rho = a.rho ? a.rho[it] : 1.0;
-    element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
+    if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, lane);
+    else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
   }
   __syncthreads();
-  // CTA partial: sum the warps' accumulators in warp order, in FP64
+  // CTA partial: sum the warps' accumulators in warp order, in FP64 (gradient pass:
+  // rows of [g | J | count] only)
   WarpLayout<T, PROB, P, JAC> L(ku, kx);
-  for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
-    const int src = acc_source(i, k);
+  const int nrow = GRAD ? k + 2 : nacc;
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+    const int src = GRAD ? acc_tail(k) + i : acc_source(i, k);
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
-    a.partial[(size_t)blockIdx.x * nacc + i] = s;
+    a.partial[(size_t)blockIdx.x * nrow + i] = s;
   }
 }
 
@@ -1165,7 +1326,7 @@ struct BatchArgs {
   long donestride;
 };
 
-template <class T, int PROB, int P, bool JAC, bool TC = false>
+template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
 __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1197,10 +1358,16 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
     __syncwarp();
     const double* muq = b.mu + (long)q * b.mustride;
 #pragma unroll 1
-    for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it)
-      element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+    for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it) {
+      if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, a.elems[it], a.rho[it], wq, tq, muq, lane);
+      else element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+    }
     __syncwarp();
-    for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k)];
+    if (GRAD) {
+      for (int i = lane; i < k + 2; i += 32) a.partial[(size_t)ch * (k + 2) + i] = (double)C.acc[acc_tail(k) + i];
+    } else {
+      for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k)];
+    }
     __syncwarp();
   }
 }

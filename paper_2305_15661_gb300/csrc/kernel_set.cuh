@@ -125,6 +125,24 @@ struct KernelSetImpl {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_norms_kernel<T, PROB, P>, block, smem);
     return e == cudaSuccess ? n : 0;
   }
+  static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    assemble_kernel<T, PROB, P, true, false, true><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t assemble_batched_grad(const void* args, const void* bargs, int grid, int block, size_t smem,
+                                           cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    const BatchArgs& b = *(const BatchArgs*)bargs;
+    cudaError_t e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    assemble_batched_kernel<T, PROB, P, true, false, true><<<grid, block, smem, s>>>(a, b);
+    return cudaGetLastError();
+  }
   static KernelSet make() {
     KernelSet k;
     k.valid = true;
@@ -139,6 +157,10 @@ struct KernelSetImpl {
     k.residual_norms = &residual_norms;
     k.prepare_norms = &prepare_norms;
     k.element_gradients = &element_gradients;
+    if constexpr (!kTC) {
+      k.assemble_grad = &assemble_grad;
+      k.assemble_batched_grad = &assemble_batched_grad;
+    }
     k.blocks_per_sm_norms = &blocks_per_sm_norms;
     return k;
   }

@@ -26,6 +26,10 @@ struct KernelSet {
                                 int B, int nchunk, int chunk, double* out, int grid, int block, size_t smem,
                                 cudaStream_t s) = nullptr;
   cudaError_t (*prepare_norms)(size_t smem) = nullptr;
+  // FP64 sets: the gradient pass (rows of [g | J | count] per CTA or per chunk)
+  cudaError_t (*assemble_grad)(const void* args, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
+  cudaError_t (*assemble_batched_grad)(const void* args, const void* bargs, int grid, int block, size_t smem,
+                                       cudaStream_t s) = nullptr;
   // per-element [S^(e); T^(e); J^(e)] rows; args as for assemble
   cudaError_t (*element_gradients)(const void* args, double* out, int grid, int block, size_t smem,
                                    cudaStream_t s) = nullptr;

@@ -417,6 +417,20 @@ __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
   restart_fp64(states[q], ku + kx, threadIdx.x, blockDim.x);
 }
 
+// Block q: the FP64 gradient pass's [g | J | count] of query q (rows of k + 2 at g)
+// into the [g | J | count] part of its full result row (res + q nacc); the
+// non-physical counts of the two passes add up. Finished queries are skipped.
+__global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states) {
+  const int q = blockIdx.x;
+  if (states != nullptr && states[q].done) return;
+  const double* src = g + (size_t)q * (k + 2);
+  double* dst = res + (size_t)q * nacc + (size_t)k * k;
+  for (int i = threadIdx.x; i < k + 2; i += blockDim.x) {
+    if (i <= k) dst[i] = src[i];
+    else dst[i] += src[i];
+  }
+}
+
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B) return;

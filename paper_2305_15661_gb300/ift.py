@@ -26,6 +26,7 @@ EULER2D = 2
 FP64 = 0
 FP32 = 1
 MIXED = 2
+FP32_JACOBIAN = 3
 INIT_PAPER = 0
 INIT_GIVEN = 1
 CONTRACT_FP = 0

@@ -148,3 +148,70 @@ def test_contraction_option_errors():
         ift.Context(ift.EULER2D, 2, precision=ift.FP64, contraction=ift.CONTRACT_TF32)
     with pytest.raises(ift.IFTError):
         ift.Context(ift.EULER2D, 2, precision=ift.FP32, contraction=7)
+
+
+@pytest.mark.parametrize("p,kappa,contraction", [(2, 0.0, ift.CONTRACT_FP), (3, 0.1, ift.CONTRACT_TF32),
+                                                 (1, 0.0, ift.CONTRACT_3XTF32)])
+def test_fp32_jacobian_mode_gradient_is_fp64(p, kappa, contraction):
+    # H from the FP32 element Jacobians; S~, T~, J~ from the FP64 residual-and-adjoint pass
+    wl = W.euler_workload(n=8, p=p, k_u=9, k_x=3, seed=81)
+    O = orc.Oracle.from_workload(wl, kappa=kappa)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0])
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN, kappa=kappa, contraction=contraction)
+    g = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert _fro(g["S"], r["S"]) < 1e-10 and _fro(g["T"], r["T"]) < 1e-10
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+    assert _fro(g["H"], r["H"]) < (5e-3 if contraction == ift.CONTRACT_TF32 else 1e-5)
+
+
+def test_fp32_jacobian_mode_sparse_weights_and_burgers():
+    wl = W.euler_workload(n=10, p=2, k_u=8, k_x=2, seed=82)
+    rho = W.eq_weight_sets(wl, 1, seed=83, lo=40, hi=41)[0]
+    O = orc.Oracle.from_workload(wl)
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN)
+    ctx.set_eq_weights(rho)
+    g = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0], rho_set=rho)
+    assert _fro(np.concatenate([g["S"], g["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-10
+    wb = W.burgers_workload(n_elems=40, p=2, k_u=4, seed=3)
+    Ob = orc.Oracle.from_workload(wb)
+    rb = Ob.reduced(wb.Phi, wb.Psi, wb.w_eval, wb.tau_eval, wb.mus[0])
+    gb = ift.Context.from_workload(wb, precision=ift.FP32_JACOBIAN).reduced_residual_jacobian(
+        wb.mus[0], wb.w_eval, wb.tau_eval)
+    assert _fro(np.concatenate([gb["S"], gb["T"]]), np.concatenate([rb["S"], rb["T"]])) < 1e-10
+    assert abs(gb["J"] - rb["J"]) <= 1e-10 * rb["J"]
+
+
+def test_fp32_jacobian_mode_solves_reach_the_fp64_optimum():
+    wl = W.euler_workload(n=10, p=2, k_u=10, k_x=4, seed=21)
+    mu = wl.mus[0]
+    O = orc.Oracle.from_workload(wl)
+    ref = O.solve(wl.Phi, wl.Psi, mu, wl.Phi.T @ W.replicate_guess(wl, wl.U_guess), tol=1e-8)
+    for contraction in (ift.CONTRACT_FP, ift.CONTRACT_TF32):
+        ctx = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN, tol=1e-8, contraction=contraction)
+        g = ctx.solve_rom(mu)
+        assert g["status"] == 0
+        # the iteration is the FP64 one up to the rounding of H: the same number of steps, give or take
+        assert abs(g["iters"] + g["init_iters"] - ref["iters"] - ref["init_iters"]) <= 2
+        _certify(O, wl, mu, None, g["w"], g["tau"], ref, 1e-8)
+
+
+def test_fp32_jacobian_mode_batched():
+    wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=6, n_mu=4, mu_box=True)
+    sets = W.eq_weight_sets(wl, 4, seed=7, lo=96, hi=200)
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN, tol=1e-8)
+    ctx.set_eq_weights_batched(sets)
+    ys, zs = np.stack([wl.w_eval] * 4), np.stack([wl.tau_eval] * 4)
+    gb = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    O = orc.Oracle.from_workload(wl)
+    for q in range(4):
+        r = O.reduced(wl.Phi, wl.Psi, ys[q], zs[q], wl.mus[q], rho_set=sets[q])
+        assert _fro(np.concatenate([gb["S"][q], gb["T"][q]]), np.concatenate([r["S"], r["T"]])) < 1e-10
+        assert abs(gb["J"][q] - r["J"]) <= 1e-10 * r["J"]
+    res = ctx.solve_rom_batched(wl.mus)
+    for q in range(4):
+        mu = wl.mus[q]
+        wg = wl.Phi.T @ W.replicate_guess(wl, W.freestream_state(wl.gamma, mu[0], mu[1]))
+        ref = O.solve(wl.Phi, wl.Psi, mu, wg, rho_set=sets[q], tol=1e-8)
+        assert res["info"][q]["status"] == ref["status"] == 0
+        _certify(O, wl, mu, sets[q], res["w"][q], res["tau"][q], ref, 1e-8)
