@@ -193,8 +193,10 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
-      {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), dU_e, dU_e' (NU + NU')
-        const size_t wa = (size_t)NQ * M + (size_t)2 * NF * NFQ * M + NU + NUP;
+      {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), nu (2 NF NFQ),
+         // eps per volume point (4 NQ), dU_e, dU_e' (NU + NU'), eps (4)
+        const size_t wa = (size_t)NQ * M + (size_t)2 * NF * NFQ * M + (size_t)2 * NF * NFQ + (size_t)4 * NQ + NU +
+                          NUP + 4;
         if (wa > w) w = wa;
       }
       if (kExplicitVolume(NU, sizeof(T))) {  // T_q (RP M) and one pass of Jv rows (RP NU)
@@ -315,7 +317,11 @@ struct ElemCore {
   }
 
   // Step 4: pointwise quantities. bcs: per-face boundary type.
-  __device__ bool pointwise(int lane, const signed char* bcs, const double* mu, double gamma, bool need_hn) {
+  // face_jac = false: face fluxes only (the FP64 gradient pass takes their adjoint by
+  // reverse mode instead of forming dH/dU+ and dH/dU-); the volume Jacobians still follow JAC.
+  __device__ bool pointwise(int lane, const signed char* bcs, const double* mu, double gamma, bool need_hn,
+                            bool face_jac = true) {
+    const bool fj = JAC && face_jac;
     bool bad = false;
     const T g1 = (T)(gamma - 1.0);
     // volume points
@@ -359,7 +365,7 @@ struct ElemCore {
     }
     // face points: task t -> (group, face point); group 0: H and dH/dU+, group 1: dH/dU-
     const int npts = NF * NFQ;
-    const int ngroups = (PROB == PROB_EULER && JAC) ? 2 : 1;
+    const int ngroups = (PROB == PROB_EULER && fj) ? 2 : 1;
     for (int t = lane; t < npts * ngroups; t += 32) {
       const int grp = t / npts, pt = t % npts;
       const int k = pt / NFQ, f = pt % NFQ;
@@ -396,7 +402,7 @@ struct ElemCore {
             Uo[pt * 4 + a] = Uout[a];
           }
         }
-        if (!JAC) {
+        if (!fj) {
           T n2[2] = {nt[k][0], nt[k][1]};
           T H[4];
           euler_roe<T, T>(Uin, Uout, n2, g1, H);
@@ -438,7 +444,7 @@ struct ElemCore {
         }
       }
     }
-    if (PROB == PROB_EULER && JAC && need_hn) {
+    if (PROB == PROB_EULER && fj && need_hn) {
       __syncwarp();
       // dH/dn from two identities of the Roe flux: homogeneity, dH/dn . n = H, and
       // rotational invariance, dH/dn . (J n) = G(H) - dH/dU+ G(U+) - dH/dU- G(U-),
@@ -556,6 +562,122 @@ struct ElemCore {
           for (int f = 0; f < NFQ; ++f) v += Lt[f * NT + jj] * mm[(kf * NFQ + f) * M + b];
         }
         dUp[i] = v;
+      }
+    }
+    __syncwarp();
+  }
+
+  // The adjoint for Euler elements with the face Jacobians left out of step 4: at
+  // each face point one forward and one reverse sweep of the Roe flux give
+  // mup = Hp^T lam and mum = Hm^T lam directly, and with them the normal derivative
+  // lam^T dH/dn from the homogeneity and rotation identities; the volume part is as in
+  // adj_state and also gives eps[r][d] = sum_q sum_a (D_r[q]^T R)_a f_d(U_q)_a, the
+  // volume term of R_e^T dR_e/dx_e. Outputs (in W): dUe, dUp, eps (4), nu (n_face n_fq x 2).
+  __device__ void adj_state_vjp(int lane, const signed char* bcs, double gamma, T*& dUe, T*& dUp, T*& eps,
+                                T*& nu) {
+    constexpr int NPT = NF * NFQ;
+    const T g1 = (T)(gamma - 1.0);
+    T* tq = W;                  // [NQ][M]
+    T* mp = W + NQ * M;         // [NPT][M]
+    T* mm = mp + NPT * M;       // [NPT][M]
+    nu = mm + NPT * M;          // [NPT][2]
+    T* eq = nu + NPT * 2;       // [NQ][4]
+    dUe = eq + NQ * 4;          // [NU]
+    dUp = dUe + NU;             // [NUP]
+    eps = dUp + NUP;            // [4]
+    for (int t = lane; t < NQ + NPT; t += 32) {
+      if (t < NQ) {
+        const int q = t;
+        T sr[DIM][M];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r)
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) v += D[(r * NQ + q) * NB + i] * R[i * M + a];
+            sr[r][a] = v;
+          }
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          T v = T(0);
+#pragma unroll
+          for (int r = 0; r < DIM; ++r)
+#pragma unroll
+            for (int a = 0; a < M; ++a) v += Ah[((q * DIM + r) * M + a) * M + b] * sr[r][a];
+          tq[q * M + b] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < DIM; ++r)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            T v = T(0);
+#pragma unroll
+            for (int a = 0; a < M; ++a) v += sr[r][a] * fph[(q * DIM + d) * M + a];
+            eq[q * 4 + r * 2 + d] = v;
+          }
+      } else {
+        const int pt = t - NQ, kf = pt / NFQ, f = pt - kf * NFQ;
+        T lam[4], Uin[4], Uout[4], Hv[4], up[4], um[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T v = T(0);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const int node = (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
+            v += Lt[f * NT + j] * R[node * M + a];
+          }
+          lam[a] = fw[f] * v;
+          Uin[a] = Ui[pt * 4 + a];
+          Uout[a] = Uo[pt * 4 + a];
+        }
+        const T n2[2] = {nt[kf][0], nt[kf][1]};
+        euler_roe_vjp<T>(Uin, Uout, n2, g1, lam, Hv, up, um);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          mp[pt * 4 + b] = up[b];
+          mm[pt * 4 + b] = um[b];
+        }
+        // lam^T Hn from [Hn n, Hn Jn] = [H, G(H) - Hp G(U+) - Hm G(U-)], G(V) = (0, -V_2, V_1, 0)
+        const T lh = lam[0] * Hv[0] + lam[1] * Hv[1] + lam[2] * Hv[2] + lam[3] * Hv[3];
+        const T lk = (-lam[1] * Hv[2] + lam[2] * Hv[1]) - (-up[1] * Uin[2] + up[2] * Uin[1]) -
+                     (-um[1] * Uout[2] + um[2] * Uout[1]);
+        const T inv = T(1) / (n2[0] * n2[0] + n2[1] * n2[1]);
+        nu[pt * 2 + 0] = (lh * n2[0] - lk * n2[1]) * inv;
+        nu[pt * 2 + 1] = (lh * n2[1] + lk * n2[0]) * inv;
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < NU + NUP + 4; e += 32) {
+      T v = T(0);
+      if (e < NU) {
+        const int j = e / M, b = e - j * M;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v -= B[q * NB + j] * tq[q * M + b];
+#pragma unroll
+        for (int kf = 0; kf < NF; ++kf) {
+          const int jj = face_pos(kf, j);
+          if (jj < 0) continue;
+          const bool outflow = bcs[kf] == 2;
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) {
+            const int pt = kf * NFQ + f;
+            v += Lt[f * NT + jj] * (mp[pt * M + b] + (outflow ? mm[pt * M + b] : T(0)));
+          }
+        }
+        dUe[e] = v;
+      } else if (e < NU + NUP) {
+        const int i = e - NU, kj = i / M, b = i - kj * M, kf = kj / NT, jj = kj - kf * NT;
+        if (bcs[kf] == 0) {
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) v += Lt[f * NT + jj] * mm[(kf * NFQ + f) * M + b];
+        }
+        dUp[i] = v;
+      } else {
+        const int rd = e - NU - NUP;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v += eq[q * 4 + rd];
+        eps[rd] = v;
       }
     }
     __syncwarp();
@@ -1039,12 +1161,12 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
 template <class T, int PROB, int P, bool JAC>
 __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e,
                                               const T* wT, const double* tauD, const double* mu, int lane,
-                                              signed char* bcs) {
+                                              signed char* bcs, bool face_jac = true) {
   using Dd = Disc<PROB, P>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
   const int ku = a.ku, kx = a.kx;
-  const bool need_hn = JAC && kx > 0;
+  const bool need_hn = JAC && kx > 0 && face_jac;
     const int* vv = &a.ev[(long)e * NV];
     // 1. gather
     const T* phe = a.Phi + (size_t)e * NU * ku;
@@ -1098,7 +1220,7 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
-    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn);
+    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn, face_jac);
     __syncwarp();
     bad |= C.residual(lane);
     return bad;
@@ -1194,11 +1316,12 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
                                                   int lane) {
   using Dd = Disc<PROB, P>;
   constexpr int DIM = Dd::DIM, M = Dd::M, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
-                NV = Dd::NV;
+                NFQ = Dd::NFQ, NV = Dd::NV;
+  constexpr bool kVJP = PROB == PROB_EULER;  // Euler: reverse-mode face adjoint, no face Jacobians
   const int ku = a.ku, kx = a.kx, k = ku + kx;
   const int* vv = &a.ev[(long)e * NV];
   signed char bcs[NF];
-  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs);
+  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP);
   const bool dist = a.kappa != 0.0;
   if (dist && lane == 0) {
     double Xe[6];
@@ -1208,8 +1331,9 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
   __syncwarp();
   const T Ne = dist ? (T)C.dN[NXE] : T(0);
   const T rT = (T)rho;
-  T *dUe, *dUp;
-  C.adj_state(lane, bcs, dUe, dUp);
+  T *dUe, *dUp, *eps = nullptr, *nu = nullptr;
+  if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu);
+  else C.adj_state(lane, bcs, dUe, dUp);
   T* g = C.acc + acc_tail(k);
   for (int c = lane; c < ku; c += 32) {
     T s = T(0);
@@ -1222,15 +1346,45 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
     }
     g[c] += rT * s;
   }
-  __syncwarp();
   if (kx > 0) {
-    C.jac_geom(lane, mu, ku, kx, k, dist);  // mesh columns of A_e (overwrites the adjoint staging)
-    for (int c = lane; c < kx; c += 32) {
-      T s = T(0);
+    if constexpr (kVJP) {
+      // R_e^T dR_e/dx_e Psi_e[:, c]: the volume term through the cofactor change of the
+      // direction, the face term through the scaled-normal change, plus distortion
+      for (int c = lane; c < kx; c += 32) {
+        const double* d = &C.Psie[c];  // column c, stride kx
+        const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
+        const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
+        // dcof[d*2 + r] = (dj11, -dj10, -dj01, dj00) pairs with eps[r*2 + d]
+        T s = -(eps[0] * dj11 + eps[1] * (-dj01) + eps[2] * (-dj10) + eps[3] * dj00);
 #pragma unroll
-      for (int i = 0; i < NU; ++i) s += C.A[i * k + ku + c] * C.R[i];
-      if (dist) s += C.dNt[c] * Ne;
-      g[ku + c] += rT * s;
+        for (int kf = 0; kf < NF; ++kf) {
+          const int k1 = (kf + 1) % 3;
+          const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
+          const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+#pragma unroll
+          for (int f = 0; f < NFQ; ++f) {
+            const int pt = kf * NFQ + f;
+            s += nu[pt * 2 + 0] * dnx + nu[pt * 2 + 1] * dny;
+          }
+        }
+        if (dist) {
+          double dn = 0.0;
+#pragma unroll
+          for (int r = 0; r < NXE; ++r) dn += C.dN[r] * d[r * kx];
+          s += (T)dn * Ne;
+        }
+        g[ku + c] += rT * s;
+      }
+    } else {
+      __syncwarp();
+      C.jac_geom(lane, mu, ku, kx, k, dist);  // mesh columns of A_e (overwrites the adjoint staging)
+      for (int c = lane; c < kx; c += 32) {
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < NU; ++i) s += C.A[i * k + ku + c] * C.R[i];
+        if (dist) s += C.dNt[c] * Ne;
+        g[ku + c] += rT * s;
+      }
     }
   }
   if (lane == 0) {

@@ -166,6 +166,208 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
   H[3] = hl * (f3 - d3);
 }
 
+// The Roe flux H(U+, U-; nt) of euler_roe together with the vector-Jacobian
+// products mup = (dH/dU+)^T lam and mum = (dH/dU-)^T lam, by one forward sweep and
+// one reverse (adjoint) sweep through the same operations in reverse order. The
+// derivative of Harten's |.| is taken like the dual-number version: sign(x) above
+// the threshold (sign(0) = 0), else the derivative of (x^2 + del^2) / (2 del).
+template <class T>
+__device__ __forceinline__ void harten_abs_d(T x, T del, T& v, T& dx, T& ddel) {
+  const T ax = dabs(x);
+  if (ax >= del) {
+    v = ax;
+    dx = (x > T(0)) ? T(1) : ((x < T(0)) ? T(-1) : T(0));
+    ddel = T(0);
+  } else {
+    const T i2d = T(1) / (del + del);
+    v = (x * x + del * del) * i2d;
+    dx = (x + x) * i2d;
+    ddel = T(1) - v / del;  // d/ddel (x^2 + del^2) / (2 del) = (del^2 - x^2) / (2 del^2)
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void euler_roe_vjp(const T Ui[4], const T Uo[4], const T nt[2], T g1, const T lam[4],
+                                              T H[4], T mup[4], T mum[4]) {
+  const T half = T(0.5);
+  const T len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
+  const T il = T(1) / len;
+  const T nx = nt[0] * il, ny = nt[1] * il;
+  // ---- forward sweep (the operations of euler_roe) ----
+  const T ri = T(1) / Ui[0];
+  const T ui = Ui[1] * ri, vi = Ui[2] * ri;
+  const T qi = Ui[1] * ui + Ui[2] * vi;
+  const T pi = g1 * (Ui[3] - half * qi);
+  const T hi = (Ui[3] + pi) * ri;
+  const T vni = ui * nx + vi * ny;
+  const T ro = T(1) / Uo[0];
+  const T uo = Uo[1] * ro, vo = Uo[2] * ro;
+  const T qo = Uo[1] * uo + Uo[2] * vo;
+  const T po = g1 * (Uo[3] - half * qo);
+  const T ho = (Uo[3] + po) * ro;
+  const T vno = uo * nx + vo * ny;
+  const T si = dsqrt(Ui[0]), so = dsqrt(Uo[0]);
+  const T iw = T(1) / (si + so);
+  const T nu_ = si * ui + so * uo, nv_ = si * vi + so * vo, nh_ = si * hi + so * ho;
+  const T ua = nu_ * iw, va = nv_ * iw, ha = nh_ * iw;
+  const T rhoa = si * so;
+  const T qa = half * (ua * ua + va * va);
+  const T c2 = g1 * (ha - qa);
+  const T ca = dsqrt(c2);
+  const T ic2 = T(1) / c2;
+  const T vna = ua * nx + va * ny;
+  const T drho = Uo[0] - Ui[0];
+  const T dp = po - pi;
+  const T du = uo - ui, dv = vo - vi;
+  const T dvn = du * nx + dv * ny;
+  const T dtx = du - dvn * nx, dty = dv - dvn * ny;
+  const T rcd = rhoa * ca * dvn;
+  const T am = half * (dp - rcd) * ic2;
+  const T ap = half * (dp + rcd) * ic2;
+  const T ae = drho - dp * ic2;
+  const T del = T(0.1) * ca;
+  T lm, lmx, lmd, lp, lpx, lpd, l0, l0x, l0d;
+  harten_abs_d(vna - ca, del, lm, lmx, lmd);
+  harten_abs_d(vna + ca, del, lp, lpx, lpd);
+  harten_abs_d(vna, del, l0, l0x, l0d);
+  const T wm = lm * am, wp = lp * ap, we = l0 * ae, ws = l0 * rhoa;
+  const T cnx = ca * nx, cny = ca * ny, cvn = ca * vna;
+  const T tdot = ua * dtx + va * dty;
+  const T d0 = wm + wp + we;
+  const T d1 = wm * (ua - cnx) + wp * (ua + cnx) + we * ua + ws * dtx;
+  const T d2 = wm * (va - cny) + wp * (va + cny) + we * va + ws * dty;
+  const T d3 = wm * (ha - cvn) + wp * (ha + cvn) + we * qa + ws * tdot;
+  const T ehi = Ui[3] + pi, eho = Uo[3] + po;
+  const T f0 = Ui[0] * vni + Uo[0] * vno;
+  const T f1 = Ui[1] * vni + pi * nx + Uo[1] * vno + po * nx;
+  const T f2 = Ui[2] * vni + pi * ny + Uo[2] * vno + po * ny;
+  const T f3 = ehi * vni + eho * vno;
+  const T hl = half * len;
+  H[0] = hl * (f0 - d0);
+  H[1] = hl * (f1 - d1);
+  H[2] = hl * (f2 - d2);
+  H[3] = hl * (f3 - d3);
+  // ---- reverse sweep ----
+  T bU[4] = {T(0), T(0), T(0), T(0)}, bO[4] = {T(0), T(0), T(0), T(0)};
+  const T bf0 = hl * lam[0], bf1 = hl * lam[1], bf2 = hl * lam[2], bf3 = hl * lam[3];
+  const T bd0 = -bf0, bd1 = -bf1, bd2 = -bf2, bd3 = -bf3;
+  // normal fluxes
+  T bvni = bf0 * Ui[0] + bf1 * Ui[1] + bf2 * Ui[2] + bf3 * ehi;
+  T bvno = bf0 * Uo[0] + bf1 * Uo[1] + bf2 * Uo[2] + bf3 * eho;
+  bU[0] += bf0 * vni;
+  bO[0] += bf0 * vno;
+  bU[1] += bf1 * vni;
+  bO[1] += bf1 * vno;
+  bU[2] += bf2 * vni;
+  bO[2] += bf2 * vno;
+  T bpi = bf1 * nx + bf2 * ny + bf3 * vni;  // through f1, f2 and ehi
+  T bpo = bf1 * nx + bf2 * ny + bf3 * vno;
+  bU[3] += bf3 * vni;
+  bO[3] += bf3 * vno;
+  // dissipation
+  T bwm = bd0 + bd1 * (ua - cnx) + bd2 * (va - cny) + bd3 * (ha - cvn);
+  T bwp = bd0 + bd1 * (ua + cnx) + bd2 * (va + cny) + bd3 * (ha + cvn);
+  T bwe = bd0 + bd1 * ua + bd2 * va + bd3 * qa;
+  T bws = bd1 * dtx + bd2 * dty + bd3 * tdot;
+  const T wsum = wm + wp + we;
+  T bua = bd1 * wsum + bd3 * ws * dtx;
+  T bva = bd2 * wsum + bd3 * ws * dty;
+  T bha = bd3 * (wm + wp);
+  T bqa = bd3 * we;
+  T bcnx = bd1 * (wp - wm), bcny = bd2 * (wp - wm), bcvn = bd3 * (wp - wm);
+  T bdtx = bd1 * ws + bd3 * ws * ua;
+  T bdty = bd2 * ws + bd3 * ws * va;
+  T bca = bcnx * nx + bcny * ny + bcvn * vna;
+  T bvna = bcvn * ca;
+  // wave weights
+  const T blm = bwm * am, bam = bwm * lm;
+  const T blp = bwp * ap, bap = bwp * lp;
+  T bl0 = bwe * ae + bws * rhoa;
+  const T bae = bwe * l0;
+  T brhoa = bws * l0;
+  // Harten |.|
+  T bdel = blm * lmd + blp * lpd + bl0 * l0d;
+  bvna += blm * lmx + blp * lpx + bl0 * l0x;
+  bca += -blm * lmx + blp * lpx;
+  bca += T(0.1) * bdel;
+  // strengths
+  T bdp = half * ic2 * (bam + bap) - ic2 * bae;
+  const T brcd = half * ic2 * (bap - bam);
+  T bic2 = half * ((dp - rcd) * bam + (dp + rcd) * bap) - dp * bae;
+  const T bdrho = bae;
+  brhoa += brcd * ca * dvn;
+  bca += brcd * rhoa * dvn;
+  T bdvn = brcd * rhoa * ca;
+  // jumps
+  T bdu = bdtx, bdv = bdty;
+  bdvn -= bdtx * nx + bdty * ny;
+  bdu += bdvn * nx;
+  bdv += bdvn * ny;
+  T bui = -bdu, buo = bdu, bvi = -bdv, bvo = bdv;
+  bpi -= bdp;
+  bpo += bdp;
+  bU[0] -= bdrho;
+  bO[0] += bdrho;
+  // Roe averages
+  bua += bvna * nx;
+  bva += bvna * ny;
+  T bc2 = -ic2 * ic2 * bic2 + bca * half / ca;
+  bha += g1 * bc2;
+  bqa -= g1 * bc2;
+  bua += bqa * ua;
+  bva += bqa * va;
+  T bsi = brhoa * so, bso = brhoa * si;
+  const T biw = bua * nu_ + bva * nv_ + bha * nh_;
+  bsi += (bua * ui + bva * vi + bha * hi) * iw - iw * iw * biw;
+  bso += (bua * uo + bva * vo + bha * ho) * iw - iw * iw * biw;
+  bui += bua * si * iw;
+  buo += bua * so * iw;
+  bvi += bva * si * iw;
+  bvo += bva * so * iw;
+  T bhi = bha * si * iw, bho = bha * so * iw;
+  bU[0] += bsi * half / si;
+  bO[0] += bso * half / so;
+  // interior side
+  bui += bvni * nx;
+  bvi += bvni * ny;
+  bU[3] += bhi * ri;
+  bpi += bhi * ri;
+  T bri = bhi * ehi;
+  bU[3] += g1 * bpi;
+  const T bqi = -half * g1 * bpi;
+  bU[1] += bqi * ui;
+  bui += bqi * Ui[1];
+  bU[2] += bqi * vi;
+  bvi += bqi * Ui[2];
+  bU[1] += bui * ri;
+  bri += bui * Ui[1];
+  bU[2] += bvi * ri;
+  bri += bvi * Ui[2];
+  bU[0] -= ri * ri * bri;
+  // exterior side
+  buo += bvno * nx;
+  bvo += bvno * ny;
+  bO[3] += bho * ro;
+  bpo += bho * ro;
+  T bro = bho * eho;
+  bO[3] += g1 * bpo;
+  const T bqo = -half * g1 * bpo;
+  bO[1] += bqo * uo;
+  buo += bqo * Uo[1];
+  bO[2] += bqo * vo;
+  bvo += bqo * Uo[2];
+  bO[1] += buo * ro;
+  bro += buo * Uo[1];
+  bO[2] += bvo * ro;
+  bro += bvo * Uo[2];
+  bO[0] -= ro * ro * bro;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    mup[a] = bU[a];
+    mum[a] = bO[a];
+  }
+}
+
 // Far-field state U_inf(mu): rho = 1, P = 1, c = sqrt(gamma), velocity M c (cos a, sin a).
 __device__ __forceinline__ void euler_farfield(double gamma, double mach, double ang, double U[4]) {
   double c = sqrt(gamma);
