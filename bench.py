@@ -351,7 +351,8 @@ def _contraction(args):
 
     if args.precision == "fp64":
         return ift.CONTRACT_FP
-    return {"fp": ift.CONTRACT_FP, "tf32": ift.CONTRACT_TF32, "3xtf32": ift.CONTRACT_3XTF32}[args.contraction]
+    return {"fp": ift.CONTRACT_FP, "tf32": ift.CONTRACT_TF32, "3xtf32": ift.CONTRACT_3XTF32,
+            "bf16": ift.CONTRACT_BF16}[args.contraction]
 
 
 def run_assembly(args):
@@ -774,7 +775,7 @@ def main():
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed", "fp32jac"], default="fp64",
                     help="element/contraction arithmetic for --mode assembly, batched and warmstart")
-    ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32"], default="fp",
+    ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32", "bf16"], default="fp",
                     help="FP32/mixed contexts: form H with FP32 FMAs, TF32 or 3xTF32 tensor cores")
     ap.add_argument("--config", type=int, choices=[2, 3, 4], default=2,
                     help="--mode assembly: 2 (or 3) = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, "

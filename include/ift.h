@@ -78,9 +78,11 @@ enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2, IFT_FP32_JACOBIAN = 3 };
    fused multiply-adds; TF32 = tensor cores with TF32 inputs (10-bit mantissa)
    and FP32 accumulation, H to about 1e-3 relative; 3XTF32 = tensor cores with
    each operand split into two TF32 parts (three products), H to about FP32
-   accuracy. S~, T~ and J~ are FP32 fused multiply-adds in every mode, so the
-   optimum of a solve does not depend on this choice (H only steers the step). */
-enum { IFT_CONTRACT_FP = 0, IFT_CONTRACT_TF32 = 1, IFT_CONTRACT_3XTF32 = 2 };
+   accuracy; BF16 = tensor cores with BF16 inputs (7-bit mantissa) and FP32
+   accumulation, H to a few 1e-3 relative. S~, T~ and J~ are FP32 fused
+   multiply-adds in every mode, so the optimum of a solve does not depend on this
+   choice (H only steers the step). */
+enum { IFT_CONTRACT_FP = 0, IFT_CONTRACT_TF32 = 1, IFT_CONTRACT_3XTF32 = 2, IFT_CONTRACT_BF16 = 3 };
 /* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
    LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */
 enum { IFT_INIT_PAPER = 0, IFT_INIT_GIVEN = 1 };
@@ -95,7 +97,7 @@ typedef struct {
   double tol;         /* stop when |[S~;T~]| <= tol * max(1, |[S~;T~]| at phase start) */
   int max_iters;      /* per LM phase */
   int lm_init;        /* IFT_INIT_PAPER or IFT_INIT_GIVEN */
-  int contraction;    /* IFT_CONTRACT_FP, _TF32 or _3XTF32 (the last two need IFT_FP32 or IFT_MIXED) */
+  int contraction;    /* IFT_CONTRACT_FP, _TF32, _3XTF32 or _BF16 (all but FP need a precision other than IFT_FP64) */
 } ift_config;
 
 /* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,

@@ -399,8 +399,8 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     return IFT_ERR_ARG;
   }
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->contraction != IFT_CONTRACT_TF32 &&
-      cfg->contraction != IFT_CONTRACT_3XTF32) {
-    g_create_error = "contraction must be IFT_CONTRACT_FP, IFT_CONTRACT_TF32 or IFT_CONTRACT_3XTF32";
+      cfg->contraction != IFT_CONTRACT_3XTF32 && cfg->contraction != IFT_CONTRACT_BF16) {
+    g_create_error = "contraction must be IFT_CONTRACT_FP, _TF32, _3XTF32 or _BF16";
     return IFT_ERR_ARG;
   }
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->precision == IFT_FP64) {

@@ -64,7 +64,8 @@ struct AsmArgs {
   // optional: a device flag; when non-zero the kernel returns at once (a finished solve)
   const int* skip;
   // T = float only: how H += rho A^T A is formed (0: FP32 FMA, 1: TF32 tensor cores,
-  // 2: 3xTF32 tensor cores, i.e. hi/lo splits of each operand, about FP32 accuracy)
+  // 2: 3xTF32 tensor cores, i.e. hi/lo splits of each operand, about FP32 accuracy,
+  // 3: BF16 tensor cores)
   int contraction;
 };
 
@@ -119,6 +120,52 @@ __device__ __forceinline__ void syrk_upper_tf32(const float* A, int k, float* ac
           mma_tf32(c, ah, bl);
         }
         mma_tf32(c, ah, bh);
+      }
+      const int cb = nt * 8 + 2 * t;
+      const int rr[4] = {r0, r0, r1, r1}, cc[4] = {cb, cb + 1, cb, cb + 1};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (rr[j] <= cc[j] && cc[j] < k) acc[acc_h(rr[j], cc[j], k)] += rho * c[j];
+    }
+  }
+}
+
+// The same upper-triangle product with BF16 operands (mma.m16n8k16, FP32
+// accumulation): a 7-bit mantissa per operand, so H carries a relative error of
+// a few 1e-3. Fragment layout as above with k = 16: each 32-bit register holds two
+// consecutive contraction indices, the lower index in the lower half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int NU>
+__device__ __forceinline__ void syrk_upper_bf16(const float* A, int k, float* acc, float rho, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  constexpr int KS = (NU + 15) / 16;
+  const int mtiles = (k + 15) / 16, ntiles = (k + 7) / 8;
+  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * k + col] : 0.0f; };
+  for (int mt = 0; mt < mtiles; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+    for (int nt = 2 * mt; nt < ntiles; ++nt) {
+      const int bc = nt * 8 + g;
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int i0 = ks * 16 + 2 * t, i1 = i0 + 8;
+        const uint32_t av[4] = {pack_bf16x2(ld(i0, r0), ld(i0 + 1, r0)), pack_bf16x2(ld(i0, r1), ld(i0 + 1, r1)),
+                                pack_bf16x2(ld(i1, r0), ld(i1 + 1, r0)), pack_bf16x2(ld(i1, r1), ld(i1 + 1, r1))};
+        const uint32_t bv[2] = {pack_bf16x2(ld(i0, bc), ld(i0 + 1, bc)), pack_bf16x2(ld(i1, bc), ld(i1 + 1, bc))};
+        mma_bf16(c, av, bv);
       }
       const int cb = nt * 8 + 2 * t;
       const int rr[4] = {r0, r0, r1, r1}, cc[4] = {cb, cb + 1, cb, cb + 1};
@@ -1260,7 +1307,8 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       if constexpr (std::is_same<T, float>::value && TC) {
         {
           __syncwarp();
-          if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.acc, rT, lane);
+          if (a.contraction == 3) syrk_upper_bf16<NU>(C.A, k, C.acc, rT, lane);
+          else if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.acc, rT, lane);
           else syrk_upper_tf32<NU, false>(C.A, k, C.acc, rT, lane);
           if (dist) {
             // distortion block of the mesh columns, Eq. levmarq-elem

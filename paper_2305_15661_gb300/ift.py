@@ -32,6 +32,7 @@ INIT_GIVEN = 1
 CONTRACT_FP = 0
 CONTRACT_TF32 = 1
 CONTRACT_3XTF32 = 2
+CONTRACT_BF16 = 3
 
 
 class IFTError(RuntimeError):
