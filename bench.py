@@ -249,7 +249,7 @@ def run_ours(args):
     assert out["status"] == 0
     e2e_value = world * e2e_steps / e2e_s
     h2d = 8 * len(wl.mus[0])
-    d2h = 2152  # solver state read back for y, z and the solve info (sizeof of the device state)
+    d2h = 2160  # solver state read back for y, z and the solve info (sizeof of the device state)
 
     # isolated assembly timing (device pointers), for the per-launch duration
     S = torch.zeros(wl.ku, dtype=torch.float64, device=dev)

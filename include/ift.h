@@ -64,7 +64,9 @@ enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
    IFT_FP32; solves run the LM with FP32 assemblies to a relative optimality of
    1e-6 (or tol if larger), or until a line search needs more than 8 halvings
    (FP32 rounding in J~ ends the FP32 stage), then continue from that point to
-   tol with the IFT_FP32_JACOBIAN evaluation (H from FP32, S~, T~, J~ in FP64).
+   tol with the IFT_FP32_JACOBIAN evaluation (H from FP32, S~, T~, J~ in FP64),
+   where H is recomputed only at the first point of that stage and after a
+   rejected or shortened step (a full step keeps it: H only steers the step).
    The LM normal equations, line search and stopping test are FP64 in every mode. */
 enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2, IFT_FP32_JACOBIAN = 3 };
 /* IFT_FP32_JACOBIAN: every LM iteration (and every evaluation call) takes the
@@ -175,6 +177,8 @@ typedef struct {
   double g0;           /* |[S~;T~]| at the start of the joint iteration */
   int fp32_iters;      /* mixed precision: joint-phase steps of the FP32 stage (iters counts the FP64 stage) */
   int fp32_trials;     /* mixed precision: objective evaluations of the FP32 stage */
+  int h_evals;         /* mixed precision: evaluations of the FP64 stage that recomputed H (FP32
+                          Jacobian pass); the others kept the H of an earlier one */
 } ift_solve_info;
 
 /* Levenberg-Marquardt solve of the hyperreduced problem (Sec. 3.2.3):

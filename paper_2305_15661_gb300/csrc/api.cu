@@ -28,7 +28,7 @@ namespace ift {
 __global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
                                int use_cond);
 __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0, int ku, int kx, int phase);
-__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out, const int* skip);
 __global__ void phit_u_partial_kernel(const double* Phi, long Nu, int ku, int m, int problem, double gamma,
                                       const double* mu, long chunk, double* part);
 __global__ void sum_columns_kernel(const double* part, int nparts, int ku, double* w);
@@ -36,7 +36,7 @@ __global__ void lm_step_batched_kernel(LMState* states, const double* res, int n
 __global__ void batch_condition_kernel(const LMState* states, int B, int* active, unsigned long long cond_handle,
                                        int use_cond);
 __global__ void reduce_chunks_kernel(const double* partial, const int* qchunk, int nacc, const LMState* states,
-                                     double* res);
+                                     double* res, int skip_kept);
 __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, int m, int problem, double gamma,
                                        const double* mu, int mustride, const double* colsum, const double* y0,
                                        const double* z0, int phase);
@@ -153,17 +153,17 @@ struct ift_ctx {
   int bplan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t bplan_smem[2][2] = {{0, 0}, {0, 0}};
   int bplan_epoch[2] = {-1, -1};
-  cudaGraph_t bgraph[3] = {nullptr, nullptr, nullptr};
-  cudaGraphExec_t bgraph_exec[3] = {nullptr, nullptr, nullptr};
-  int bgraph_epoch[3] = {-1, -1, -1};
+  cudaGraph_t bgraph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t bgraph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int bgraph_epoch[4] = {-1, -1, -1, -1};
   // FP64 gradient pass results: [g | J | count] for the single query (k + 2) and per query (B x (k + 2))
   double* d_gres = nullptr;
   double* d_bgres = nullptr;
   // solve graphs, per working precision
   // solve graphs per body kind: [0] FP64, [1] FP32, [2] FP32 Jacobians + FP64 gradient
-  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
-  int graph_epoch[3] = {-1, -1, -1};
+  cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_epoch[4] = {-1, -1, -1, -1};
   int epoch = 0;
   bool graph_failed = false;
 
@@ -315,16 +315,17 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "element kernel launch");
   const int nacc = c->nacc();
-  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(c->d_partial, grid, nacc, out);
+  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(c->d_partial, grid, nacc, out, skip);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "reduce launch");
   return IFT_OK;
 }
 
 // The FP64 gradient pass at (w, tau): S~, T~, J~ and the non-physical count into
-// the [g | J | count] part of out (the H part is left as it is).
+// the [g | J | count] part of out (the H part is left as it is). states (optional):
+// the solve's LM state, whose flags say whether the FP32 pass ran in this body.
 ift_status launch_grad(ift_ctx* c, const double* w, const double* tau, const double* mu, double* out,
-                       const int* skip, cudaStream_t s) {
+                       const int* skip, cudaStream_t s, const LMState* states = nullptr) {
   if (c->plan_epoch[0] != c->epoch) {
     ift_status st = plan_launch(c, 0);
     if (st != IFT_OK) return st;
@@ -334,21 +335,24 @@ ift_status launch_grad(ift_ctx* c, const double* w, const double* tau, const dou
   AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
   cudaError_t e = ks.assemble_grad(&a, grid, 32 * c->wpc[0], c->plan_smem[0][1], s);
   if (e != cudaSuccess) return c->cuda_fail(e, "gradient pass launch");
-  reduce_partials_kernel<<<(k + 2 + 31) / 32, 256, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres);
-  merge_grad_kernel<<<1, 64, 0, s>>>(c->d_gres, k, c->nacc(), out, nullptr);
+  reduce_partials_kernel<<<(k + 2 + 31) / 32, 256, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres, skip);
+  merge_grad_kernel<<<1, 64, 0, s>>>(c->d_gres, k, c->nacc(), out, states);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "gradient reduce launch");
   return IFT_OK;
 }
 
 // Evaluation for a loop body or an evaluation call: slot 0/1 the FP64 / FP32 fused
-// assembly; slot 2 the FP32 fused assembly (H) followed by the FP64 gradient pass.
+// assembly; slot 2 the FP32 fused assembly (H) followed by the FP64 gradient pass;
+// slot 3 as slot 2, with the FP32 pass (and its reduction) skipped while the LM state
+// keeps H (hskip: its flag; states: the LM state).
 ift_status launch_eval(ift_ctx* c, int slot, const double* w, const double* tau, const double* mu, double* out,
-                       const int* skip, cudaStream_t s) {
+                       const int* skip, cudaStream_t s, const int* hskip = nullptr,
+                       const LMState* states = nullptr) {
   if (slot < 2) return launch_assemble(c, slot, true, w, tau, mu, out, skip, s);
-  ift_status st = launch_assemble(c, 1, true, w, tau, mu, out, skip, s);
+  ift_status st = launch_assemble(c, 1, true, w, tau, mu, out, slot == 3 ? hskip : skip, s);
   if (st != IFT_OK) return st;
-  return launch_grad(c, w, tau, mu, out, skip, s);
+  return launch_grad(c, w, tau, mu, out, skip, s, slot == 3 ? states : nullptr);
 }
 
 ift_status check_ready(ift_ctx* c) {
@@ -856,6 +860,7 @@ constexpr int kMaxHalvings = 30, kMixedStage1Halvings = 8;
 
 LMConsts lm_consts(ift_ctx* c, double tol) {
   LMConsts k;
+  k.keep_h = 0;
   k.tol = tol;
   k.max_iters = c->cfg.max_iters;
   k.ku = c->ku;
@@ -877,15 +882,25 @@ LMConsts stage_consts(ift_ctx* c, int wp) {
   return k;
 }
 
+// LM constants of a loop body in evaluation slot 0..3 (slots 2 and 3 run the LM with
+// the FP64 constants; slot 3 keeps H after full steps).
+LMConsts slot_consts(ift_ctx* c, int slot) {
+  LMConsts k = stage_consts(c, slot >= 2 ? 0 : slot);
+  k.keep_h = slot == 3 ? 1 : 0;
+  return k;
+}
+
 // The loop body: assemble at the trial point, reduce, LM step.
 // slot 0/1: FP64 / FP32 assembly; slot 2: FP32 assembly for H, then the FP64
-// gradient pass for S~, T~, J~ (the LM runs with the FP64 constants).
+// gradient pass for S~, T~, J~ (the LM runs with the FP64 constants); slot 3: as
+// slot 2, the FP32 pass skipped while H is kept (the finishing stage of a mixed solve).
 ift_status enqueue_body(ift_ctx* c, int slot, cudaStream_t s, unsigned long long handle, int use_cond) {
   double* trial = (double*)((char*)c->d_lm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
-  ift_status st = launch_eval(c, slot, trial, trial + c->ku, c->d_mu, c->d_res, done, s);
+  const int* hkeep = (const int*)((char*)c->d_lm + offsetof(LMState, hkeep));
+  ift_status st = launch_eval(c, slot, trial, trial + c->ku, c->d_mu, c->d_res, done, s, hkeep, c->d_lm);
   if (st != IFT_OK) return st;
-  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, stage_consts(c, slot == 2 ? 0 : slot), handle, use_cond);
+  lm_step_kernel<<<1, 32, 0, s>>>(c->d_lm, c->d_res, slot_consts(c, slot), handle, use_cond);
   CK(cudaGetLastError(), "LM step launch");
   return IFT_OK;
 }
@@ -934,7 +949,7 @@ ift_status build_graph(ift_ctx* c, int wp) {
   c->graph_exec[wp] = nullptr;
   c->graph[wp] = nullptr;
   for (int tp = 0; tp < 2; ++tp) {
-    if ((tp == wp || wp == 2) && c->plan_epoch[tp] != c->epoch) {
+    if ((tp == wp || wp >= 2) && c->plan_epoch[tp] != c->epoch) {
       ift_status st = plan_launch(c, tp);
       if (st != IFT_OK) return st;
     }
@@ -951,7 +966,7 @@ ift_status build_graph(ift_ctx* c, int wp) {
 // e.g. so that a profiler that does not enter conditional graph nodes sees every launch.
 // Bodies are enqueued in groups of 8; after a group the done flag is read back.
 ift_status run_solve_loop(ift_ctx* c, int wp, cudaStream_t s) {
-  const LMConsts k = lm_consts(c, stage_tol(c, wp == 2 ? 0 : wp));
+  const LMConsts k = lm_consts(c, stage_tol(c, wp >= 2 ? 0 : wp));
   const int* done = (const int*)((char*)c->d_lm + offsetof(LMState, done));
   for (int b = 0; b <= k.body_limit; b += 8) {
     for (int j = 0; j < 8; ++j) {
@@ -987,8 +1002,9 @@ ift_status run_solve(ift_ctx* c, cudaStream_t s) {
   if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
   lm_restart_kernel<<<1, 64, 0, s>>>(c->d_lm, 1, c->ku, c->kx);
   CK(cudaGetLastError(), "stage restart");
-  // the finishing stage: FP64 residual, gradient and objective, H from FP32
-  return run_stage(c, 2, s);
+  // the finishing stage: FP64 residual, gradient and objective, H from FP32 (kept
+  // across full steps)
+  return run_stage(c, 3, s);
 }
 
 void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
@@ -1007,6 +1023,7 @@ void fill_info(const LMState& st, ift_solve_info* info, int ku, int kx) {
   info->g0 = st.g0;
   info->fp32_iters = st.iters32;
   info->fp32_trials = st.trials32;
+  info->h_evals = st.hevals;
 }
 
 }  // namespace
@@ -1100,7 +1117,7 @@ ift_status plan_batched(ift_ctx* c, int wp) {
 
 // Batched element pass over all chunks of unfinished queries, then the per-query reduction.
 ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long wstride, const int* done,
-                          long donestride, const LMState* states, cudaStream_t s) {
+                          long donestride, const LMState* states, cudaStream_t s, int skip_kept = 0) {
   if (c->bplan_epoch[wp] != c->epoch) {
     ift_status st = plan_batched(c, wp);
     if (st != IFT_OK) return st;
@@ -1133,7 +1150,7 @@ ift_status launch_batched(ift_ctx* c, int wp, bool jac, const double* w, long ws
     e = ks.assemble_batched(&a, &b, jac, c->bplan_grid[wp][j], block, c->bplan_smem[wp][j], s);
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "batched kernel launch");
-  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, c->nacc(), states, c->d_bres);
+  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, c->nacc(), states, c->d_bres, skip_kept);
   CK(cudaGetLastError(), "chunk reduction launch");
   return IFT_OK;
 }
@@ -1164,7 +1181,7 @@ ift_status launch_batched_grad(ift_ctx* c, const double* w, long wstride, const 
   cudaError_t e = c->ks[0].assemble_batched_grad(&a, &b, c->bplan_grid[0][1], 32 * c->bwpc[0],
                                                   c->bplan_smem[0][1], s);
   if (e != cudaSuccess) return c->cuda_fail(e, "batched gradient pass launch");
-  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, k + 2, states, c->d_bgres);
+  reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, k + 2, states, c->d_bgres, 0);
   merge_grad_kernel<<<c->B, 64, 0, s>>>(c->d_bgres, k, c->nacc(), c->d_bres, states);
   CK(cudaGetLastError(), "batched gradient reduce launch");
   return IFT_OK;
@@ -1173,19 +1190,22 @@ ift_status launch_batched_grad(ift_ctx* c, const double* w, long wstride, const 
 // The batched loop body in working precision wp: assemble every unfinished query,
 // reduce per query, one LM step per query, loop condition.
 // slot 0/1: FP64 / FP32 batched assembly; slot 2: FP32 assembly for H, then the FP64
-// gradient pass for S~, T~, J~ of every unfinished query.
+// gradient pass for S~, T~, J~ of every unfinished query; slot 3: as slot 2, the
+// FP32 pass skipped for the queries that keep H.
 ift_status enqueue_batched_body(ift_ctx* c, int slot, cudaStream_t s, unsigned long long handle, int use_cond) {
   const double* trial = (const double*)((char*)c->d_blm + offsetof(LMState, trial));
   const int* done = (const int*)((char*)c->d_blm + offsetof(LMState, done));
+  const int* hkeep = (const int*)((char*)c->d_blm + offsetof(LMState, hkeep));
   const long wstride = (long)(sizeof(LMState) / sizeof(double)), istride = (long)(sizeof(LMState) / sizeof(int));
-  const int wp = slot == 2 ? 1 : slot;
-  ift_status st = launch_batched(c, wp, true, trial, wstride, done, istride, c->d_blm, s);
+  const int wp = slot >= 2 ? 1 : slot;
+  ift_status st = launch_batched(c, wp, true, trial, wstride, slot == 3 ? hkeep : done, istride, c->d_blm, s,
+                                 slot == 3 ? 1 : 0);
   if (st != IFT_OK) return st;
-  if (slot == 2) {
+  if (slot >= 2) {
     st = launch_batched_grad(c, trial, wstride, done, istride, c->d_blm, s);
     if (st != IFT_OK) return st;
   }
-  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), stage_consts(c, slot == 2 ? 0 : slot));
+  lm_step_batched_kernel<<<c->B, 32, 0, s>>>(c->d_blm, c->d_bres, c->nacc(), slot_consts(c, slot));
   batch_condition_kernel<<<1, 256, 0, s>>>(c->d_blm, c->B, c->d_active, handle, use_cond);
   CK(cudaGetLastError(), "batched LM launch");
   return IFT_OK;
@@ -1197,7 +1217,7 @@ ift_status build_batched_graph(ift_ctx* c, int wp) {
   c->bgraph_exec[wp] = nullptr;
   c->bgraph[wp] = nullptr;
   for (int tp = 0; tp < 2; ++tp) {
-    if ((tp == wp || wp == 2) && c->bplan_epoch[tp] != c->epoch) {
+    if ((tp == wp || wp >= 2) && c->bplan_epoch[tp] != c->epoch) {
       ift_status st = plan_batched(c, tp);
       if (st != IFT_OK) return st;
     }
@@ -1214,7 +1234,7 @@ ift_status build_batched_graph(ift_ctx* c, int wp) {
 ift_status run_batched_stage(ift_ctx* c, int wp, cudaStream_t s) {
   static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
   if (no_graph) {
-    const LMConsts k = lm_consts(c, stage_tol(c, wp == 2 ? 0 : wp));
+    const LMConsts k = lm_consts(c, stage_tol(c, wp >= 2 ? 0 : wp));
     for (int b = 0; b <= k.body_limit; b += 8) {
       for (int j = 0; j < 8; ++j) {
         ift_status st = enqueue_batched_body(c, wp, s, 0ull, 0);
@@ -1246,8 +1266,9 @@ ift_status run_batched_solve(ift_ctx* c, cudaStream_t s) {
   if (st != IFT_OK || c->cfg.precision == IFT_FP32) return st;
   lm_restart_kernel<<<c->B, 64, 0, s>>>(c->d_blm, c->B, c->ku, c->kx);
   CK(cudaGetLastError(), "stage restart");
-  // the finishing stage: FP64 residual, gradient and objective, H from FP32
-  return run_batched_stage(c, 2, s);
+  // the finishing stage: FP64 residual, gradient and objective, H from FP32 (kept
+  // across full steps)
+  return run_batched_stage(c, 3, s);
 }
 
 // Split every query's items into chunks of c->chunk elements (one warp each) and size

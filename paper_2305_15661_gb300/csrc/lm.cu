@@ -112,8 +112,10 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
   const double Jr = res[k * k + k];
   const double npr = res[k * k + k + 1];
   int need_solve = 0;
+  bool refresh_h = false;  // the next evaluation recomputes H (after a shortened step)
   if (lane == 0 && !s.done) {
     s.bodies += 1;
+    if (c.keep_h && !s.hkeep) s.hevals += 1;
     if (s.bodies > c.body_limit) {
       s.status = IFT_ERR_TIMEOUT;
       s.done = 1;
@@ -135,6 +137,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
     } else {
       const bool ok = npr == 0.0 && isfinite(Jr) && Jr <= s.J + kC1 * s.alpha * s.slope + kRound * fabs(s.J);
       if (ok) {
+        refresh_h = s.h != 0;
         s.lam = (s.h == 0) ? fmax(s.lam / 10.0, kLamMin) : fmin(s.lam * 10.0, kLamMax);
         for (int i = 0; i < k; ++i) {
           s.z[i] = s.trial[i];
@@ -155,6 +158,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
           s.done = 1;
         }
       } else {
+        refresh_h = true;
         s.h += 1;
         s.alpha *= 0.5;
         const int ka = (s.phase == 1) ? k : ku;
@@ -229,6 +233,11 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
     }
     need_solve = __shfl_sync(0xffffffffu, again, 0);
   }
+  // Finishing stage of a mixed solve: H only steers the step, so after a full step
+  // the next evaluation keeps the H it has (the FP64 gradient, objective and
+  // tests are recomputed at every point); a rejected or shortened step refreshes
+  // it, and a finished query skips the FP32 pass.
+  if (lane == 0 && c.keep_h) s.hkeep = (s.done || !refresh_h) ? 1 : 0;
   __syncwarp();
 }
 
@@ -269,10 +278,11 @@ __global__ void batch_condition_kernel(const LMState* states, int B, int* active
 }
 
 // Per-query sum of the chunk partials: res[q][i] = sum over the chunks of q (in order).
+// Finished queries are skipped, and with skip_kept also those whose H is kept.
 __global__ void reduce_chunks_kernel(const double* partial, const int* qchunk, int nacc, const LMState* states,
-                                     double* res) {
+                                     double* res, int skip_kept) {
   const int q = blockIdx.x;
-  if (states != nullptr && states[q].done) return;
+  if (states != nullptr && (states[q].done || (skip_kept && states[q].hkeep))) return;
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
     double t = 0.0;
     for (int ch = qchunk[q]; ch < qchunk[q + 1]; ++ch) t += partial[(size_t)ch * nacc + i];
@@ -310,6 +320,8 @@ __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0
     s.done = 0;
     s.iters32 = 0;
     s.trials32 = 0;
+    s.hkeep = 0;
+    s.hevals = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -355,6 +367,8 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
     s.done = 0;
     s.iters32 = 0;
     s.trials32 = 0;
+    s.hkeep = 0;
+    s.hevals = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -392,6 +406,7 @@ __device__ void restart_fp64(LMState& s, int k, int tid, int nthreads) {
     s.dz[i] = 0.0;
   }
   if (tid == 0) {
+    s.hkeep = 0;
     s.iters32 = s.iters[1];
     s.trials32 = s.trials;
     s.iters[1] = 0;
@@ -419,14 +434,16 @@ __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx) {
 
 // Block q: the FP64 gradient pass's [g | J | count] of query q (rows of k + 2 at g)
 // into the [g | J | count] part of its full result row (res + q nacc); the
-// non-physical counts of the two passes add up. Finished queries are skipped.
+// non-physical counts of the two passes add up (the FP64 count alone when the FP32
+// pass was skipped because H is kept). Finished queries are skipped.
 __global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states) {
   const int q = blockIdx.x;
   if (states != nullptr && states[q].done) return;
+  const bool kept = states != nullptr && states[q].hkeep;
   const double* src = g + (size_t)q * (k + 2);
   double* dst = res + (size_t)q * nacc + (size_t)k * k;
   for (int i = threadIdx.x; i < k + 2; i += blockDim.x) {
-    if (i <= k) dst[i] = src[i];
+    if (i <= k || kept) dst[i] = src[i];
     else dst[i] += src[i];
   }
 }
@@ -442,7 +459,10 @@ __global__ void residual_norms_finish_kernel(const double* part, int B, int nchu
 // Block b sums columns [32 b, 32 b + 32) of the partials: its 8 warps each sum one
 // contiguous eighth of the rows (coalesced 32-column reads), then the eight
 // segment sums are added in segment order (the order is fixed for a launch shape).
-__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out) {
+// skip (optional): a device flag; when non-zero the block returns at once and out is
+// left as it is (a finished solve, or an evaluation that keeps H).
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out, const int* skip) {
+  if (skip != nullptr && *skip) return;
   __shared__ double seg[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;

@@ -21,6 +21,7 @@ struct LMConsts {
   int ku, kx;
   int body_limit;   // hard bound on loop bodies (then IFT_ERR_TIMEOUT)
   int max_halvings; // line-search halvings before the phase ends (30; fewer in the FP32 stage of a mixed solve)
+  int keep_h;       // 1: after a full step, the next evaluation keeps H (the finishing stage of a mixed solve)
 };
 
 // Device-resident solver state (one per query).
@@ -32,6 +33,8 @@ struct LMState {
   int iters[2];     // accepted steps per phase
   int trials, shifts, h, bodies, done;
   int iters32, trials32;  // joint-phase steps and trials of the FP32 stage of a mixed solve
+  int hkeep;        // 1: the next evaluation leaves H as it is (no FP32 Jacobian pass)
+  int hevals;       // evaluations with keep_h that recomputed H
   double lam, alpha, J, slope, g0, thresh;
   double z[LM_KMAX];      // current iterate (w | tau)
   double dz[LM_KMAX];     // step

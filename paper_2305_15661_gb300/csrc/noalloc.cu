@@ -34,7 +34,7 @@
 #include "refelem.h"
 
 namespace ift {
-__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out);
+__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out, const int* skip);
 }  // namespace ift
 
 using namespace ift;
@@ -180,7 +180,7 @@ extern "C" ift_status ift_reduced_residual_jacobian_static(
   a.skip = nullptr;
   a.contraction = 0;
   if (ks.assemble(&a, true, (int)grid, block, smem, s) != cudaSuccess) return IFT_ERR_CUDA;
-  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(scratch + o_part, (int)grid, nacc, scratch + o_res);
+  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(scratch + o_part, (int)grid, nacc, scratch + o_res, nullptr);
   static_unpack_kernel<<<(nacc + 255) / 256, 256, 0, s>>>(scratch + o_res, k_u, k_x, S, T, H, J);
   if (cudaGetLastError() != cudaSuccess) return IFT_ERR_CUDA;
   return IFT_OK;

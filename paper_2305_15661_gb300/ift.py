@@ -52,7 +52,7 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("init_iters", ctypes.c_int), ("iters", ctypes.c_int),
                 ("trials", ctypes.c_int), ("shifts", ctypes.c_int), ("J", ctypes.c_double),
                 ("normS", ctypes.c_double), ("normT", ctypes.c_double), ("g0", ctypes.c_double),
-                ("fp32_iters", ctypes.c_int), ("fp32_trials", ctypes.c_int)]
+                ("fp32_iters", ctypes.c_int), ("fp32_trials", ctypes.c_int), ("h_evals", ctypes.c_int)]
 
 
 _lib = None
@@ -282,7 +282,8 @@ class Context:
             self._check(st, allow_positive=True)
         return {"status": int(st), "w": y, "tau": z[:self.kx], "init_iters": info.init_iters, "iters": info.iters,
                 "trials": info.trials, "shifts": info.shifts, "J": info.J, "normS": info.normS,
-                "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters, "fp32_trials": info.fp32_trials}
+                "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters, "fp32_trials": info.fp32_trials,
+                "h_evals": info.h_evals}
 
     def autotune(self, mu, y, z):
         """Pick the launch shapes by timing this workload; returns (warps, batched warps, chunk)."""
@@ -359,7 +360,7 @@ class Context:
         return {"status": int(st), "w": y.reshape(B, self.ku), "tau": z[:B * self.kx].reshape(B, self.kx),
                 "info": [{"status": i.status, "init_iters": i.init_iters, "iters": i.iters, "trials": i.trials,
                           "J": i.J, "normS": i.normS, "normT": i.normT, "g0": i.g0, "fp32_iters": i.fp32_iters,
-                          "fp32_trials": i.fp32_trials} for i in info]}
+                          "fp32_trials": i.fp32_trials, "h_evals": i.h_evals} for i in info]}
 
     def solve_rom_batched_dev(self, mus, y, z, status=None, stream=None):
         self._check(load().ift_solve_rom_batched_dev(self._h, _tptr(mus), _tptr(y), _tptr(z), _tptr(status),
@@ -375,7 +376,7 @@ class Context:
             return None
         return {"status": int(st), "init_iters": info.init_iters, "iters": info.iters, "trials": info.trials,
                 "J": info.J, "normS": info.normS, "normT": info.normT, "g0": info.g0, "fp32_iters": info.fp32_iters,
-                "fp32_trials": info.fp32_trials}
+                "fp32_trials": info.fp32_trials, "h_evals": info.h_evals}
 
 
 class MLP:

@@ -40,7 +40,36 @@ def test_mixed_solve_dense_matches_fp64_oracle():
     assert g["status"] == 0 and ref["status"] == 0
     # part of the joint iteration runs in FP32 and the FP64 stage is shorter than an FP64 solve
     assert g["fp32_iters"] > 0 and g["iters"] < ref["iters"]
+    # the FP64 stage recomputes H at its first point and after shortened steps only
+    assert 1 <= g["h_evals"] <= g["trials"] + 1
     _certify(O, wl, mu, None, g["w"], g["tau"], ref, 1e-8)
+
+
+def test_mixed_finishing_stage_keeps_h():
+    # A finishing stage of several full steps: H is recomputed at its first point
+    # (and after any shortened step) only, the point still certified by the oracle.
+    wl = W.euler_workload(n=12, p=2, k_u=12, k_x=4, seed=31, n_mu=3, mu_box=True)
+    sets = W.eq_weight_sets(wl, 3, seed=32, lo=150, hi=250)
+    ctx = ift.Context.from_workload(wl, precision=ift.MIXED, tol=1e-9)
+    ctx.set_eq_weights_batched(sets)
+    res = ctx.solve_rom_batched(wl.mus)
+    O = orc.Oracle.from_workload(wl)
+    kept = 0
+    for q in range(3):
+        i = res["info"][q]
+        assert i["status"] == 0
+        evals = i["trials"] + 1  # the restart point, then every trial point (new steps and halvings)
+        assert 1 <= i["h_evals"] <= evals
+        kept += evals - i["h_evals"]
+        mu = wl.mus[q]
+        wg = wl.Phi.T @ W.replicate_guess(wl, W.freestream_state(wl.gamma, mu[0], mu[1]))
+        ref = O.solve(wl.Phi, wl.Psi, mu, wg, rho_set=sets[q], tol=1e-9)
+        _certify(O, wl, mu, sets[q], res["w"][q], res["tau"][q], ref, 1e-9)
+    assert kept > 0
+    # the FP32-Jacobian mode recomputes H at every evaluation
+    f = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN, tol=1e-9)
+    f.set_eq_weights_batched(sets)
+    assert all(i["h_evals"] == 0 for i in f.solve_rom_batched(wl.mus)["info"])
 
 
 def test_mixed_batched_matches_fp64_oracle():
