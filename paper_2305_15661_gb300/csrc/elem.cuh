@@ -3,8 +3,9 @@
 // One warp evaluates one element at a time (a grid-stride loop over a list of
 // (element, weight) items, so the same kernel serves the full assembly with
 // rho = 1 and the hyperreduced gather over the sampled elements):
-//   1. gather Phi_e, the neighbours' trace rows Phi_e', Psi_e and X_e into the
-//      warp's shared memory (coalesced row blocks);
+//   1. gather Phi_e and Psi_e into the warp's shared memory by asynchronous
+//      copies (cp.async, all in flight at once); the neighbours' trace rows
+//      Phi_e' are read from global memory (mostly L2 hits) where they are used;
 //   2. U_e = Phi_e w, U_e' = Phi_e' w, x_e = X_e + Psi_e tau        (Sec. 3.1)
 //   3. straight-sided geometry: cofactor matrix g J^{-T} of the element map
 //      and scaled face normals (Eq. p2r-flux; Nanson's formula);
@@ -28,6 +29,40 @@
 #include "physics.cuh"
 
 namespace ift {
+
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): a lane issues
+// its copies, then commit + wait; every copy of the group is in flight at once.
+// 16-byte copies need both addresses 16-byte aligned; the 4- and 8-byte forms need
+// their own size alignment.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy n values of T from global src to shared dst (dst 16-byte aligned) by the warp's
+// lanes with cp.async: 16-byte pieces when src is 16-byte aligned and n T fill whole
+// pieces, else one value per copy. The caller waits (cp_async_wait_all + __syncwarp).
+template <class T>
+__device__ __forceinline__ void warp_copy_async(T* dst, const T* src, int n, int lane) {
+  constexpr int V = 16 / sizeof(T);
+  if (((uintptr_t)src & 15) == 0 && n % V == 0) {
+    for (int i = lane * V; i < n; i += 32 * V) cp_async16(dst + i, src + i);
+  } else {
+    for (int i = lane; i < n; i += 32) {
+      if (sizeof(T) == 8) cp_async8(dst + i, src + i);
+      else cp_async4(dst + i, src + i);
+    }
+  }
+}
 
 // Per-warp accumulators: the upper triangle of H row by row (k (k + 1) / 2 entries),
 // then g (k), J and the non-physical count. Position of H[r][b], r <= b:
@@ -1215,9 +1250,14 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
   const int ku = a.ku, kx = a.kx;
   const bool need_hn = JAC && kx > 0 && face_jac;
     const int* vv = &a.ev[(long)e * NV];
-    // 1. gather
-    const T* phe = a.Phi + (size_t)e * NU * ku;
-    for (int i = lane; i < NU * ku; i += 32) C.Phie[i] = phe[i];
+    // 1. gather: Phi_e and Psi_e by asynchronous copies (all in flight at once),
+    // overlapped with the neighbour offsets
+    warp_copy_async(C.Phie, a.Phi + (size_t)e * NU * ku, NU * ku, lane);
+    for (int i = lane; i < NXE * kx; i += 32) {
+      const int r = C.dkx.div(i), c = i - r * kx;
+      const int v = r / DIM, d = r - v * DIM;
+      cp_async8(&C.Psie[i], &a.Psi[((size_t)vv[v] * DIM + d) * kx + c]);
+    }
     if (lane < NF * NT) {
       const int kf = lane / NT, j = lane - kf * NT;
       const int e2 = a.nbr[(long)e * NF + kf];
@@ -1232,11 +1272,7 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
       C.poff[lane] = off;
     }
     C.PhiG = a.Phi;
-    for (int i = lane; i < NXE * kx; i += 32) {
-      const int r = C.dkx.div(i), c = i - r * kx;
-      const int v = r / DIM, d = r - v * DIM;
-      C.Psie[i] = a.Psi[((size_t)vv[v] * DIM + d) * kx + c];
-    }
+    cp_async_wait_all();
     __syncwarp();
     // 2. reconstruction
     for (int i = lane; i < NU + NUP; i += 32) {
