@@ -261,6 +261,19 @@ size_t shapes_smem(const ift_ctx* c, int wp, int w) {
   return c->ks[wp].valid ? c->ks[wp].smem_bytes(true, c->ku, c->kx, w) : 0;
 }
 
+// Warps of the fused element kernel of precision wp resident per SM with w warps per CTA
+// (0 if a CTA does not fit).
+int resident_warps(ift_ctx* c, int wp, int w) {
+  if (!c->ks[wp].valid) return 0;
+  const size_t smem = shapes_smem(c, wp, w);
+  if (smem > (size_t)c->smem_optin) return 0;
+  if (c->ks[wp].prepare(true, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return w * c->ks[wp].blocks_per_sm(true, 32 * w, smem);
+}
+
 ift_status plan_launch(ift_ctx* c, int wp) {
   const KernelSet& ks = c->ks[wp];
   const int wpc = c->wpc[wp], block = 32 * wpc;
@@ -673,10 +686,20 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   CK(cudaStreamSynchronize(c->stream), "column sums");
   c->B = 0;  // batched weight sets are sized for the bases: set them again
   c->have_bases = true;
-  // default launch shapes that fit these bases: fewer warps per CTA for large k
-  for (int wp = 0; wp < 2; ++wp)
-    for (int* w : {&c->wpc[wp], &c->bwpc[wp]})
-      while (*w > 1 && shapes_smem(c, wp, *w) > (size_t)c->smem_optin) *w /= 2;
+  // default launch shapes for these bases: the warps per CTA (at most the default)
+  // that keep the most warps resident per SM; large k need fewer warps per CTA,
+  // both to fit and because shared memory is handed out CTA by CTA
+  for (int wp = 0; wp < 2; ++wp) {
+    int best = 1, best_res = -1;
+    for (int w = kWarpsPerCta; w >= 1; w /= 2) {
+      const int res = resident_warps(c, wp, w);
+      if (res > best_res) {
+        best = w;
+        best_res = res;
+      }
+    }
+    c->wpc[wp] = c->bwpc[wp] = best;
+  }
   c->epoch++;
   return IFT_OK;
 }

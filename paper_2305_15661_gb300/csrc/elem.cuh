@@ -400,9 +400,11 @@ struct ElemCore {
 
   // Step 4: pointwise quantities. bcs: per-face boundary type.
   // face_jac = false: face fluxes only (the FP64 gradient pass takes their adjoint by
-  // reverse mode instead of forming dH/dU+ and dH/dU-); the volume Jacobians still follow JAC.
+  // reverse mode instead of forming dH/dU+ and dH/dU-); vol_jac = false (Euler): the
+  // volume flux Jacobians are not formed either, and the states U_q are kept in
+  // Ah[q][0..3] for the adjoint's vector-Jacobian products.
   __device__ bool pointwise(int lane, const signed char* bcs, const double* mu, double gamma, bool need_hn,
-                            bool face_jac = true) {
+                            bool face_jac = true, bool vol_jac = true) {
     const bool fj = JAC && face_jac;
     bool bad = false;
     const T g1 = (T)(gamma - 1.0);
@@ -427,13 +429,16 @@ struct ElemCore {
 #pragma unroll
           for (int r = 0; r < 2; ++r) Fh[(q * 2 + r) * 4 + a] = fx[a] * cof[0 * 2 + r] + fy[a] * cof[1 * 2 + r];
         }
-        if (JAC) {
+        if (JAC && vol_jac) {
           T Ax[16], Ay[16];
           euler_flux_jac(U, g1, Ax, Ay);
 #pragma unroll
           for (int r = 0; r < 2; ++r)
 #pragma unroll
             for (int ab = 0; ab < 16; ++ab) Ah[(q * 2 + r) * 16 + ab] = Ax[ab] * cof[r] + Ay[ab] * cof[2 + r];
+        } else if (JAC) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) Ah[q * 4 + a] = U[a];
         }
       } else {
         T f = T(0.5) * U[0] * U[0];
@@ -680,15 +685,19 @@ struct ElemCore {
             for (int i = 0; i < NB; ++i) v += D[(r * NQ + q) * NB + i] * R[i * M + a];
             sr[r][a] = v;
           }
+        // t_q = sum_r Ahat_qr^T s_r with Ahat_qr = Ax cof[r] + Ay cof[2 + r]: the transposed
+        // flux Jacobians at U_q (kept in Ah[q][0..3] by step 4) applied to
+        // v_x = sum_r cof[r] s_r and v_y = sum_r cof[2 + r] s_r
+        T vx[4], vy[4], Uq[4], tb[4];
 #pragma unroll
-        for (int b = 0; b < M; ++b) {
-          T v = T(0);
-#pragma unroll
-          for (int r = 0; r < DIM; ++r)
-#pragma unroll
-            for (int a = 0; a < M; ++a) v += Ah[((q * DIM + r) * M + a) * M + b] * sr[r][a];
-          tq[q * M + b] = v;
+        for (int a = 0; a < 4; ++a) {
+          vx[a] = cof[0] * sr[0][a] + cof[1] * sr[1][a];
+          vy[a] = cof[2] * sr[0][a] + cof[3] * sr[1][a];
+          Uq[a] = Ah[q * 4 + a];
         }
+        euler_flux_vjp(Uq, g1, vx, vy, tb);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tq[q * M + b] = tb[b];
 #pragma unroll
         for (int r = 0; r < DIM; ++r)
 #pragma unroll
@@ -1243,7 +1252,7 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
 template <class T, int PROB, int P, bool JAC>
 __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e,
                                               const T* wT, const double* tauD, const double* mu, int lane,
-                                              signed char* bcs, bool face_jac = true) {
+                                              signed char* bcs, bool face_jac = true, bool vol_jac = true) {
   using Dd = Disc<PROB, P>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
@@ -1303,7 +1312,7 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
-    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn, face_jac);
+    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn, face_jac, vol_jac);
     __syncwarp();
     bad |= C.residual(lane);
     return bad;
@@ -1405,7 +1414,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
   const int ku = a.ku, kx = a.kx, k = ku + kx;
   const int* vv = &a.ev[(long)e * NV];
   signed char bcs[NF];
-  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP);
+  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP, !kVJP);
   const bool dist = a.kappa != 0.0;
   if (dist && lane == 0) {
     double Xe[6];

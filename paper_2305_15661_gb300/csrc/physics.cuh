@@ -75,6 +75,32 @@ __device__ __forceinline__ void euler_flux_jac(const T U[4], T g1, T Ax[16], T A
   Ay[12] = v * (g1 * k - Hs); Ay[13] = -g1 * u * v; Ay[14] = Hs - g1 * v * v; Ay[15] = gam * v;
 }
 
+// Transposed flux Jacobians applied to two vectors: out = Ax^T vx + Ay^T vy with
+// Ax, Ay the Jacobians of euler_flux_jac (row a = flux component, column b = state
+// component), without forming them: the vector-Jacobian product of the volume
+// flux in the adjoint pass.
+template <class T>
+__device__ __forceinline__ void euler_flux_vjp(const T U[4], T g1, const T vx[4], const T vy[4], T out[4]) {
+  const T ir = T(1) / U[0];
+  const T u = U[1] * ir, v = U[2] * ir;
+  const T k = T(0.5) * (u * u + v * v);
+  const T P = g1 * (U[3] - U[0] * k);
+  const T Hs = (U[3] + P) * ir;
+  const T gam = g1 + T(1), tg = T(3) - gam;
+  const T gk = g1 * k, uv = u * v;
+  // column 0
+  out[0] = (gk - u * u) * vx[1] - uv * vx[2] + u * (gk - Hs) * vx[3] - uv * vy[1] + (gk - v * v) * vy[2] +
+           v * (gk - Hs) * vy[3];
+  // column 1
+  out[1] = vx[0] + tg * u * vx[1] + v * vx[2] + (Hs - g1 * u * u) * vx[3] + v * vy[1] - g1 * u * vy[2] -
+           g1 * uv * vy[3];
+  // column 2
+  out[2] = -g1 * v * vx[1] + u * vx[2] - g1 * uv * vx[3] + vy[0] + u * vy[1] + tg * v * vy[2] +
+           (Hs - g1 * v * v) * vy[3];
+  // column 3
+  out[3] = g1 * (vx[1] + vy[2]) + gam * (u * vx[3] + v * vy[3]);
+}
+
 // Plain-value overloads so euler_roe<T, T> compiles with the same helpers.
 template <class T>
 __device__ __forceinline__ T recip(T a) { return T(1) / a; }
@@ -88,13 +114,53 @@ __device__ __forceinline__ T value_of(T a) { return a; }
 template <class T, int N>
 __device__ __forceinline__ T value_of(const Dual<T, N>& a) { return a.v; }
 
+__device__ __forceinline__ double drsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ float drsqrt(float a) { return rsqrtf(a); }
+
+// sqrt(a) and 1/a from one reciprocal square root r = a^(-1/2): s = a r, i = r r;
+// r itself (= 1/s) is returned in rs. The dual version carries ds = (r / 2) da and
+// di = -i^2 da. One reciprocal square root replaces a square root and a division.
+template <class T>
+__device__ __forceinline__ void sqrt_recip(T a, T& s, T& i, T& rs) {
+  const T r = drsqrt(a);
+  s = a * r;
+  i = r * r;
+  rs = r;
+}
+template <class T, int N>
+__device__ __forceinline__ void sqrt_recip(const Dual<T, N>& a, Dual<T, N>& s, Dual<T, N>& i, T& rs) {
+  const T r = drsqrt(a.v);
+  s.v = a.v * r;
+  i.v = r * r;
+  rs = r;
+  const T hs = T(0.5) * r, hi = -i.v * i.v;
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    s.d[n] = hs * a.d[n];
+    i.d[n] = hi * a.d[n];
+  }
+}
+// 1/b given the value inv = 1/b.v (no division)
+template <class T>
+__device__ __forceinline__ T recip_known(T, T inv) { return inv; }
+template <class T, int N>
+__device__ __forceinline__ Dual<T, N> recip_known(const Dual<T, N>& b, T inv) {
+  Dual<T, N> r;
+  r.v = inv;
+  const T m = -inv * inv;
+#pragma unroll
+  for (int n = 0; n < N; ++n) r.d[n] = m * b.d[n];
+  return r;
+}
+
 // Harten's entropy fix of a wave speed: |lam| when |lam| >= del, else
 // (lam^2 + del^2) / (2 del), which meets |lam| with a continuous slope.
+// i2d = 1 / (2 del), computed once by the caller.
 template <class S>
-__device__ __forceinline__ S harten_abs(const S& lam, const S& del) {
+__device__ __forceinline__ S harten_abs(const S& lam, const S& del, const S& i2d) {
   S a = dabs(lam);
   if (value_of(a) >= value_of(del)) return a;
-  return (lam * lam + del * del) / (del + del);
+  return (lam * lam + del * del) * i2d;
 }
 
 // Roe flux H(U+, U-; nt) for the scaled normal nt (|nt| = face measure factor):
@@ -107,23 +173,27 @@ __device__ __forceinline__ S harten_abs(const S& lam, const S& del) {
 template <class S, class T>
 __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T nt[2], T g1, S H[4]) {
   const T half = T(0.5);
-  const T len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
-  const T il = T(1) / len;
+  const T nn = nt[0] * nt[0] + nt[1] * nt[1];
+  const T il = drsqrt(nn);
+  const T len = nn * il;
   const T nx = nt[0] * il, ny = nt[1] * il;
-  // interior side
-  S ri = recip(Ui[0]);
+  // interior side (sqrt(rho) and 1/rho from one reciprocal square root)
+  S si, ri;
+  T rsi;
+  sqrt_recip(Ui[0], si, ri, rsi);
   S ui = Ui[1] * ri, vi = Ui[2] * ri;
   S pi = g1 * (Ui[3] - half * (Ui[1] * ui + Ui[2] * vi));
   S hi = (Ui[3] + pi) * ri;
   S vni = ui * nx + vi * ny;
   // exterior side
-  S ro = recip(Uo[0]);
+  S so, ro;
+  T rso;
+  sqrt_recip(Uo[0], so, ro, rso);
   S uo = Uo[1] * ro, vo = Uo[2] * ro;
   S po = g1 * (Uo[3] - half * (Uo[1] * uo + Uo[2] * vo));
   S ho = (Uo[3] + po) * ro;
   S vno = uo * nx + vo * ny;
   // Roe averages
-  S si = dsqrt(Ui[0]), so = dsqrt(Uo[0]);
   S iw = recip(si + so);
   S ua = (si * ui + so * uo) * iw;
   S va = (si * vi + so * vo) * iw;
@@ -131,8 +201,9 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
   S rhoa = si * so;
   S qa = half * (ua * ua + va * va);
   S c2 = g1 * (ha - qa);
-  S ca = dsqrt(c2);
-  S ic2 = recip(c2);
+  S ca, ic2;
+  T rca;
+  sqrt_recip(c2, ca, ic2, rca);
   S vna = ua * nx + va * ny;
   // jumps (exterior minus interior)
   S drho = Uo[0] - Ui[0];
@@ -146,7 +217,8 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
   S ap = half * (dp + rcd) * ic2;  // eigenvalue vn + c
   S ae = drho - dp * ic2;          // entropy wave, eigenvalue vn
   S del = T(0.1) * ca;
-  S lm = harten_abs(vna - ca, del), lp = harten_abs(vna + ca, del), l0 = harten_abs(vna, del);
+  const S i2d = T(5) * recip_known(ca, rca);  // 1 / (2 del)
+  S lm = harten_abs(vna - ca, del, i2d), lp = harten_abs(vna + ca, del, i2d), l0 = harten_abs(vna, del, i2d);
   S wm = lm * am, wp = lp * ap, we = l0 * ae, ws = l0 * rhoa;
   S cnx = ca * nx, cny = ca * ny, cvn = ca * vna;
   S d0 = wm + wp + we;
@@ -171,18 +243,19 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
 // one reverse (adjoint) sweep through the same operations in reverse order. The
 // derivative of Harten's |.| is taken like the dual-number version: sign(x) above
 // the threshold (sign(0) = 0), else the derivative of (x^2 + del^2) / (2 del).
+// idel = 1 / del, computed once by the caller.
 template <class T>
-__device__ __forceinline__ void harten_abs_d(T x, T del, T& v, T& dx, T& ddel) {
+__device__ __forceinline__ void harten_abs_d(T x, T del, T idel, T& v, T& dx, T& ddel) {
   const T ax = dabs(x);
   if (ax >= del) {
     v = ax;
     dx = (x > T(0)) ? T(1) : ((x < T(0)) ? T(-1) : T(0));
     ddel = T(0);
   } else {
-    const T i2d = T(1) / (del + del);
+    const T i2d = T(0.5) * idel;
     v = (x * x + del * del) * i2d;
     dx = (x + x) * i2d;
-    ddel = T(1) - v / del;  // d/ddel (x^2 + del^2) / (2 del) = (del^2 - x^2) / (2 del^2)
+    ddel = T(1) - v * idel;  // d/ddel (x^2 + del^2) / (2 del) = (del^2 - x^2) / (2 del^2)
   }
 }
 
@@ -190,31 +263,32 @@ template <class T>
 __device__ __forceinline__ void euler_roe_vjp(const T Ui[4], const T Uo[4], const T nt[2], T g1, const T lam[4],
                                               T H[4], T mup[4], T mum[4]) {
   const T half = T(0.5);
-  const T len = dsqrt(nt[0] * nt[0] + nt[1] * nt[1]);
-  const T il = T(1) / len;
+  const T nn = nt[0] * nt[0] + nt[1] * nt[1];
+  const T il = drsqrt(nn);
+  const T len = nn * il;
   const T nx = nt[0] * il, ny = nt[1] * il;
   // ---- forward sweep (the operations of euler_roe) ----
-  const T ri = T(1) / Ui[0];
+  T si, ri, rsi, so, ro, rso;
+  sqrt_recip(Ui[0], si, ri, rsi);
+  sqrt_recip(Uo[0], so, ro, rso);
   const T ui = Ui[1] * ri, vi = Ui[2] * ri;
   const T qi = Ui[1] * ui + Ui[2] * vi;
   const T pi = g1 * (Ui[3] - half * qi);
   const T hi = (Ui[3] + pi) * ri;
   const T vni = ui * nx + vi * ny;
-  const T ro = T(1) / Uo[0];
   const T uo = Uo[1] * ro, vo = Uo[2] * ro;
   const T qo = Uo[1] * uo + Uo[2] * vo;
   const T po = g1 * (Uo[3] - half * qo);
   const T ho = (Uo[3] + po) * ro;
   const T vno = uo * nx + vo * ny;
-  const T si = dsqrt(Ui[0]), so = dsqrt(Uo[0]);
   const T iw = T(1) / (si + so);
   const T nu_ = si * ui + so * uo, nv_ = si * vi + so * vo, nh_ = si * hi + so * ho;
   const T ua = nu_ * iw, va = nv_ * iw, ha = nh_ * iw;
   const T rhoa = si * so;
   const T qa = half * (ua * ua + va * va);
   const T c2 = g1 * (ha - qa);
-  const T ca = dsqrt(c2);
-  const T ic2 = T(1) / c2;
+  T ca, ic2, rca;
+  sqrt_recip(c2, ca, ic2, rca);
   const T vna = ua * nx + va * ny;
   const T drho = Uo[0] - Ui[0];
   const T dp = po - pi;
@@ -225,11 +299,11 @@ __device__ __forceinline__ void euler_roe_vjp(const T Ui[4], const T Uo[4], cons
   const T am = half * (dp - rcd) * ic2;
   const T ap = half * (dp + rcd) * ic2;
   const T ae = drho - dp * ic2;
-  const T del = T(0.1) * ca;
+  const T del = T(0.1) * ca, idel = T(10) * rca;
   T lm, lmx, lmd, lp, lpx, lpd, l0, l0x, l0d;
-  harten_abs_d(vna - ca, del, lm, lmx, lmd);
-  harten_abs_d(vna + ca, del, lp, lpx, lpd);
-  harten_abs_d(vna, del, l0, l0x, l0d);
+  harten_abs_d(vna - ca, del, idel, lm, lmx, lmd);
+  harten_abs_d(vna + ca, del, idel, lp, lpx, lpd);
+  harten_abs_d(vna, del, idel, l0, l0x, l0d);
   const T wm = lm * am, wp = lp * ap, we = l0 * ae, ws = l0 * rhoa;
   const T cnx = ca * nx, cny = ca * ny, cvn = ca * vna;
   const T tdot = ua * dtx + va * dty;
@@ -311,7 +385,7 @@ __device__ __forceinline__ void euler_roe_vjp(const T Ui[4], const T Uo[4], cons
   // Roe averages
   bua += bvna * nx;
   bva += bvna * ny;
-  T bc2 = -ic2 * ic2 * bic2 + bca * half / ca;
+  T bc2 = -ic2 * ic2 * bic2 + bca * half * rca;
   bha += g1 * bc2;
   bqa -= g1 * bc2;
   bua += bqa * ua;
@@ -325,8 +399,8 @@ __device__ __forceinline__ void euler_roe_vjp(const T Ui[4], const T Uo[4], cons
   bvi += bva * si * iw;
   bvo += bva * so * iw;
   T bhi = bha * si * iw, bho = bha * so * iw;
-  bU[0] += bsi * half / si;
-  bO[0] += bso * half / so;
+  bU[0] += bsi * half * rsi;
+  bO[0] += bso * half * rso;
   // interior side
   bui += bvni * nx;
   bvi += bvni * ny;
