@@ -1371,6 +1371,48 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
           simt_h = false;
         }
       }
+      if constexpr (std::is_same<T, float>::value) {
+        if (simt_h && k % 4 == 0) {
+          // FP32 (issue-bound): each lane forms a 4 x 4 block of H's upper block
+          // triangle with float4 loads of A's rows, 16 FMA per 2 shared loads
+          __syncwarp();
+          const int nb = k / 4, nblk = nb * (nb + 1) / 2;
+          for (int blk = lane; blk < nblk; blk += 32) {
+            int R = 0, rem = blk;
+            while (rem >= nb - R) {
+              rem -= nb - R;
+              ++R;
+            }
+            const int Bc = R + rem;
+            float h[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) h[x][y] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NU; ++i) {
+              const float4 ar = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * R]);
+              const float4 bc = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * Bc]);
+              const float av[4] = {ar.x, ar.y, ar.z, ar.w}, bv[4] = {bc.x, bc.y, bc.z, bc.w};
+#pragma unroll
+              for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) h[x][y] += av[x] * bv[y];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) {
+                const int r = 4 * R + x, b = 4 * Bc + y;
+                if (r > b) continue;
+                float v = h[x][y];
+                if (dist && r >= ku) v += C.dNt[r - ku] * C.dNt[b - ku];
+                C.acc[acc_h(r, b, k)] += rT * v;
+              }
+          }
+          simt_h = false;
+        }
+      }
       const int npairs = simt_h ? k * (k + 1) / 2 : 0;
       for (int pidx = lane; pidx < npairs; pidx += 32) {
         const int r = pairs[2 * pidx], b = pairs[2 * pidx + 1];
