@@ -124,6 +124,8 @@ struct ift_ctx {
   // launch plans of the element kernels, [working precision][0: objective only, 1: fused assembly]
   int plan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t plan_smem[2][2] = {{0, 0}, {0, 0}};
+  int plan_grid_grad = 0;    // the FP64 gradient pass (its own shared-memory layout)
+  size_t plan_smem_grad = 0;
   int plan_epoch[2] = {-1, -1};
   // launch shapes (set by ift_autotune): warps per CTA of the single-query and the
   // batched element kernels, elements per chunk of the batched path
@@ -152,6 +154,8 @@ struct ift_ctx {
   size_t rn_cap_B = 0, rn_cap_parts = 0;
   int bplan_grid[2][2] = {{0, 0}, {0, 0}};
   size_t bplan_smem[2][2] = {{0, 0}, {0, 0}};
+  int bplan_grid_grad = 0;
+  size_t bplan_smem_grad = 0;
   int bplan_epoch[2] = {-1, -1};
   cudaGraph_t bgraph[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t bgraph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -296,6 +300,19 @@ ift_status plan_launch(ift_ctx* c, int wp) {
     c->plan_grid[wp][j] = (int)grid;
     c->plan_smem[wp][j] = smem;
   }
+  if (ks.smem_bytes_grad) {
+    // the gradient pass: same warps per CTA, its own (smaller) layout and occupancy
+    const size_t smem = ks.smem_bytes_grad(c->ku, c->kx, wpc);
+    const int bps = smem <= (size_t)c->smem_optin ? ks.blocks_per_sm_grad(false, block, smem) : 0;
+    if (bps < 1) return c->fail(IFT_ERR_CUDA, "gradient kernel does not fit on an SM (%zu bytes shared)", smem);
+    long grid = (long)c->sm_count * bps;
+    const long need = (items + wpc - 1) / wpc;
+    if (grid > need) grid = need;
+    if (grid > c->max_parts) grid = c->max_parts;
+    if (grid < 1) grid = 1;
+    c->plan_grid_grad = (int)grid;
+    c->plan_smem_grad = smem;
+  }
   // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
   const size_t ismem = ks.smem_bytes(true, 1, 0, wpc);
   if (ismem > c->plan_smem[wp][1]) {
@@ -344,9 +361,9 @@ ift_status launch_grad(ift_ctx* c, const double* w, const double* tau, const dou
     if (st != IFT_OK) return st;
   }
   const KernelSet& ks = c->ks[0];
-  const int k = c->ku + c->kx, grid = c->plan_grid[0][1];
+  const int k = c->ku + c->kx, grid = c->plan_grid_grad;
   AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
-  cudaError_t e = ks.assemble_grad(&a, grid, 32 * c->wpc[0], c->plan_smem[0][1], s);
+  cudaError_t e = ks.assemble_grad(&a, grid, 32 * c->wpc[0], c->plan_smem_grad, s);
   if (e != cudaSuccess) return c->cuda_fail(e, "gradient pass launch");
   reduce_partials_kernel<<<(k + 2 + 31) / 32, 256, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres, skip);
   merge_grad_kernel<<<1, 64, 0, s>>>(c->d_gres, k, c->nacc(), out, states);
@@ -1134,6 +1151,17 @@ ift_status plan_batched(ift_ctx* c, int wp) {
     c->bplan_grid[wp][j] = (int)grid;
     c->bplan_smem[wp][j] = smem;
   }
+  if (ks.smem_bytes_grad) {
+    const size_t smem = ks.smem_bytes_grad(c->ku, c->kx, bwpc);
+    const int bps = smem <= (size_t)c->smem_optin ? ks.blocks_per_sm_grad(true, block, smem) : 0;
+    if (bps < 1) return c->fail(IFT_ERR_CUDA, "batched gradient kernel does not fit on an SM (%zu bytes shared)", smem);
+    long grid = (long)c->sm_count * bps;
+    const long need = (c->n_chunks + bwpc - 1) / bwpc;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    c->bplan_grid_grad = (int)grid;
+    c->bplan_smem_grad = smem;
+  }
   c->bplan_epoch[wp] = c->epoch;
   return IFT_OK;
 }
@@ -1201,8 +1229,8 @@ ift_status launch_batched_grad(ift_ctx* c, const double* w, long wstride, const 
   a.elems = c->d_belems;
   a.rho = c->d_brho;
   a.partial = c->d_bpartial;
-  cudaError_t e = c->ks[0].assemble_batched_grad(&a, &b, c->bplan_grid[0][1], 32 * c->bwpc[0],
-                                                  c->bplan_smem[0][1], s);
+  cudaError_t e = c->ks[0].assemble_batched_grad(&a, &b, c->bplan_grid_grad, 32 * c->bwpc[0],
+                                                  c->bplan_smem_grad, s);
   if (e != cudaSuccess) return c->cuda_fail(e, "batched gradient pass launch");
   reduce_chunks_kernel<<<c->B, 128, 0, s>>>(c->d_bpartial, c->d_qchunk, k + 2, states, c->d_bgres, 0);
   merge_grad_kernel<<<c->B, 64, 0, s>>>(c->d_bgres, k, c->nacc(), c->d_bres, states);

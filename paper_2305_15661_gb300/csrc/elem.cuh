@@ -230,12 +230,17 @@ __host__ __device__ constexpr bool kExplicitVolume(int nu, int word) { return wo
 // Entries of Jv per register pass (9 doubles per lane).
 constexpr int kJvPass = 288;
 
-// Per-warp shared-memory layout.
-template <class T, int PROB, int P, bool JAC>
+// Per-warp shared-memory layout. GRAD: the gradient pass, which for Euler forms no
+// Jacobian columns, no face Jacobians and no volume flux Jacobians (the states U_q
+// only), and accumulates only [g | J | count] (SLIM: those buffers shrink to what it uses).
+template <class T, int PROB, int P, bool JAC, bool GRAD = false>
 struct WarpLayout {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
+  static constexpr bool SLIM = GRAD && JAC && PROB == PROB_EULER;
+  // offset of g (the tail [g | J | count]) within the accumulators
+  __host__ __device__ static int gacc_offset(int k) { return SLIM ? 0 : acc_tail(k); }
   size_t oxe, oPsie, odN, oPhie, oPoff, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
       oW, owq, otq, oacc, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
@@ -257,16 +262,16 @@ struct WarpLayout {
     oUp = put(NUP, sizeof(T));
     oFh = put(NQ * DIM * M, sizeof(T));
     ofph = put(NQ * DIM * M, sizeof(T));
-    oAh = put(JAC ? NQ * DIM * M * M : 1, sizeof(T));
+    oAh = put(JAC ? (SLIM ? NQ * M : NQ * DIM * M * M) : 1, sizeof(T));
     osq = put(NQ, sizeof(T));
     oHf = put(NF * NFQ * M, sizeof(T));
-    oHp = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
-    oHm = put(JAC ? NF * NFQ * M * M : 1, sizeof(T));
-    oHn = put(JAC ? NF * NFQ * M * 2 : 1, sizeof(T));
+    oHp = put(JAC && !SLIM ? NF * NFQ * M * M : 1, sizeof(T));
+    oHm = put(JAC && !SLIM ? NF * NFQ * M * M : 1, sizeof(T));
+    oHn = put(JAC && !SLIM ? NF * NFQ * M * 2 : 1, sizeof(T));
     oUi = put(NF * NFQ * M, sizeof(T));
     oUo = put(NF * NFQ * M, sizeof(T));
     oR = put(NU, sizeof(T));
-    oA = put(JAC ? (size_t)NU * k : 1, sizeof(T));
+    oA = put(JAC && !SLIM ? (size_t)NU * k : 1, sizeof(T));
     odNt = put(kx + 1, sizeof(T));
     {
       // staging of the reduced-Jacobian passes: volume G (M ku) + F (DIM M ku), faces
@@ -275,13 +280,14 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
+      if (SLIM) w = 0;  // the gradient pass stages only the adjoint below
       {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), nu (2 NF NFQ),
          // eps per volume point (4 NQ), dU_e, dU_e' (NU + NU'), eps (4)
         const size_t wa = (size_t)NQ * M + (size_t)2 * NF * NFQ * M + (size_t)2 * NF * NFQ + (size_t)4 * NQ + NU +
                           NUP + 4;
         if (wa > w) w = wa;
       }
-      if (kExplicitVolume(NU, sizeof(T))) {  // T_q (RP M) and one pass of Jv rows (RP NU)
+      if (kExplicitVolume(NU, sizeof(T)) && !SLIM) {  // T_q (RP M) and one pass of Jv rows (RP NU)
         const int np = (NU * NU + kJvPass - 1) / kJvPass, rp = NU / np;
         const size_t we = (size_t)rp * (M + NU);
         if (we > w) w = we;
@@ -290,7 +296,7 @@ struct WarpLayout {
     }
     owq = put(ku > 0 ? ku : 1, sizeof(T));
     otq = put(kx > 0 ? kx : 1, 8);
-    oacc = put((size_t)acc_count(k), sizeof(T));
+    oacc = put(SLIM ? (size_t)k + 2 : (size_t)acc_count(k), sizeof(T));
     bytes = b;
   }
 };
@@ -301,11 +307,11 @@ __host__ __device__ inline size_t cta_bytes(int ku, int kx) {
          align16((size_t)(kx > 0 ? kx : 1) * 8);
 }
 
-template <class T, int PROB, int P, bool JAC>
+template <class T, int PROB, int P, bool JAC, bool GRAD = false>
 __host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps) {
   const int k = ku + kx;
-  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC>(ku, kx).bytes +
-         align16((size_t)k * (k + 1));  // upper-triangle pair table
+  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC, GRAD>(ku, kx).bytes +
+         (GRAD ? 0 : align16((size_t)k * (k + 1)));  // upper-triangle pair table
 }
 
 // Pointwise stage and residual for one element whose U_e, U_e', x_e are staged.
@@ -333,6 +339,7 @@ struct ElemCore {
   // warp buffers
   double *xe, *Psie, *dN;
   T *Phie, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
+  T* gacc;  // [g | J | count] within acc
   // geometry (registers, identical on all lanes)
   T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
   T detJ;
@@ -342,8 +349,9 @@ struct ElemCore {
   long long* poff;   // per face and trace position: row-block offset in PhiG, -1 on boundary faces
   FastDiv dku, dkx;  // division by k_u and k_x in the lane loops
 
+  template <bool GRAD = false>
   __device__ void carve(unsigned char* base, int ku, int kx) {
-    WarpLayout<T, PROB, P, JAC> L(ku, kx);
+    WarpLayout<T, PROB, P, JAC, GRAD> L(ku, kx);
     dku.init(ku > 0 ? ku : 1);
     dkx.init(kx > 0 ? kx : 1);
     xe = (double*)(base + L.oxe);
@@ -368,6 +376,7 @@ struct ElemCore {
     A = (T*)(base + L.oA);
     dNt = (T*)(base + L.odNt);
     acc = (T*)(base + L.oacc);
+    gacc = acc + L.gacc_offset(ku + kx);
   }
 
   // Geometry from xe (FP64). Returns false if the element is inverted.
@@ -480,8 +489,9 @@ struct ElemCore {
         }
         T* hf = &Hf[pt * 4];
         if (grp == 0) {
-          T Pi = g1 * (Uin[3] - T(0.5) * (Uin[1] * Uin[1] + Uin[2] * Uin[2]) / Uin[0]);
-          T Po = g1 * (Uout[3] - T(0.5) * (Uout[1] * Uout[1] + Uout[2] * Uout[2]) / Uout[0]);
+          // P > 0 with rho > 0 <=> rho E rho - |rho v|^2 / 2 > 0 (no division)
+          const T Pi = Uin[3] * Uin[0] - T(0.5) * (Uin[1] * Uin[1] + Uin[2] * Uin[2]);
+          const T Po = Uout[3] * Uout[0] - T(0.5) * (Uout[1] * Uout[1] + Uout[2] * Uout[2]);
           if (!(Uin[0] > T(0)) || !(Pi > T(0)) || !(Uout[0] > T(0)) || !(Po > T(0))) bad = true;
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
@@ -1469,7 +1479,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
   T *dUe, *dUp, *eps = nullptr, *nu = nullptr;
   if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu);
   else C.adj_state(lane, bcs, dUe, dUp);
-  T* g = C.acc + acc_tail(k);
+  T* g = C.gacc;
   for (int c = lane; c < ku; c += 32) {
     T s = T(0);
 #pragma unroll
@@ -1569,15 +1579,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   T *tab, *wT;
   double* tauD;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
-  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
+  const size_t wb = Lay(ku, kx).bytes;
   Core C;
-  C.carve(smem + cb + warp * wb, ku, kx);
+  C.template carve<GRAD>(smem + cb + warp * wb, ku, kx);
   bind_tables(C, tab);
   const int nacc = k * k + k + 2;  // entries of a partial row (full H)
-  for (int i = lane; i < acc_count(k); i += 32) C.acc[i] = T(0);
+  const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
+  for (int i = lane; i < nzero; i += 32) C.acc[i] = T(0);
   unsigned char* pairs = smem + cb + nw * wb;
-  if (JAC && threadIdx.x == 0) build_pairs(pairs, k);
+  if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
     const int e = a.elems ? a.elems[it] : (int)it;
@@ -1588,10 +1600,10 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   __syncthreads();
   // CTA partial: sum the warps' accumulators in warp order, in FP64 (gradient pass:
   // rows of [g | J | count] only)
-  WarpLayout<T, PROB, P, JAC> L(ku, kx);
+  Lay L(ku, kx);
   const int nrow = GRAD ? k + 2 : nacc;
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-    const int src = GRAD ? acc_tail(k) + i : acc_source(i, k);
+    const int src = GRAD ? Lay::gacc_offset(k) + i : acc_source(i, k);
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
     a.partial[(size_t)blockIdx.x * nrow + i] = s;
@@ -1624,18 +1636,20 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
   T *tab, *wT_unused;
   double* tau_unused;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT_unused, tau_unused);
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
-  const size_t wb = WarpLayout<T, PROB, P, JAC>(ku, kx).bytes;
-  WarpLayout<T, PROB, P, JAC> L(ku, kx);
+  const size_t wb = Lay(ku, kx).bytes;
+  Lay L(ku, kx);
   unsigned char* wbase = smem + cb + warp * wb;
   Core C;
-  C.carve(wbase, ku, kx);
+  C.template carve<GRAD>(wbase, ku, kx);
   bind_tables(C, tab);
   T* wq = (T*)(wbase + L.owq);
   double* tq = (double*)(wbase + L.otq);
   const int nacc = k * k + k + 2;
+  const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
   unsigned char* pairs = smem + cb + nw * wb;
-  if (JAC && threadIdx.x == 0) build_pairs(pairs, k);
+  if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   for (int ch = blockIdx.x * nw + warp; ch < b.n_chunks; ch += gridDim.x * nw) {
     const int q = b.chunk_query[ch];
@@ -1643,7 +1657,7 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
     const double* wsrc = b.w + (long)q * b.wstride;
     for (int i = lane; i < ku; i += 32) wq[i] = (T)wsrc[i];
     for (int i = lane; i < kx; i += 32) tq[i] = wsrc[ku + i];
-    for (int i = lane; i < acc_count(k); i += 32) C.acc[i] = T(0);
+    for (int i = lane; i < nzero; i += 32) C.acc[i] = T(0);
     __syncwarp();
     const double* muq = b.mu + (long)q * b.mustride;
 #pragma unroll 1
@@ -1653,7 +1667,7 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
     }
     __syncwarp();
     if (GRAD) {
-      for (int i = lane; i < k + 2; i += 32) a.partial[(size_t)ch * (k + 2) + i] = (double)C.acc[acc_tail(k) + i];
+      for (int i = lane; i < k + 2; i += 32) a.partial[(size_t)ch * (k + 2) + i] = (double)C.gacc[i];
     } else {
       for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k)];
     }

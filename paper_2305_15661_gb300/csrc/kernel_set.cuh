@@ -125,6 +125,23 @@ struct KernelSetImpl {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_norms_kernel<T, PROB, P>, block, smem);
     return e == cudaSuccess ? n : 0;
   }
+  // the gradient pass (FP64 sets): its own, smaller shared-memory layout
+  static size_t smem_bytes_grad(int ku, int kx, int warps) {
+    return assemble_smem_bytes<T, PROB, P, true, true>(ku, kx, warps);
+  }
+  static int blocks_per_sm_grad(bool batched, int block, size_t smem) {
+    int n = 0;
+    cudaError_t e = batched ? cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, false, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return 0;
+    e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      &n, assemble_batched_kernel<T, PROB, P, true, false, true>, block, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, assemble_kernel<T, PROB, P, true, false, true>,
+                                                                block, smem);
+    return e == cudaSuccess ? n : 0;
+  }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
@@ -160,6 +177,8 @@ struct KernelSetImpl {
     if constexpr (!kTC) {
       k.assemble_grad = &assemble_grad;
       k.assemble_batched_grad = &assemble_batched_grad;
+      k.smem_bytes_grad = &smem_bytes_grad;
+      k.blocks_per_sm_grad = &blocks_per_sm_grad;
     }
     k.blocks_per_sm_norms = &blocks_per_sm_norms;
     return k;

@@ -30,6 +30,8 @@ struct KernelSet {
   cudaError_t (*assemble_grad)(const void* args, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
   cudaError_t (*assemble_batched_grad)(const void* args, const void* bargs, int grid, int block, size_t smem,
                                        cudaStream_t s) = nullptr;
+  size_t (*smem_bytes_grad)(int ku, int kx, int warps) = nullptr;
+  int (*blocks_per_sm_grad)(bool batched, int block, size_t smem) = nullptr;
   // per-element [S^(e); T^(e); J^(e)] rows; args as for assemble
   cudaError_t (*element_gradients)(const void* args, double* out, int grid, int block, size_t smem,
                                    cudaStream_t s) = nullptr;
