@@ -71,6 +71,16 @@ __device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N>& a, T s) {
   return r;
 }
 template <class T, int N>
+__device__ __forceinline__ Dual<T, N> operator+(T s, const Dual<T, N>& a) {
+  return a + s;
+}
+template <class T, int N>
+__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a, T s) {
+  Dual<T, N> r = a;
+  r.v -= s;
+  return r;
+}
+template <class T, int N>
 __device__ __forceinline__ Dual<T, N> operator-(T s, const Dual<T, N>& a) {
   Dual<T, N> r;
   r.v = s - a.v;

@@ -502,29 +502,31 @@ struct ElemCore {
         if (!fj) {
           T n2[2] = {nt[k][0], nt[k][1]};
           T H[4];
-          euler_roe<T, T>(Uin, Uout, n2, g1, H);
+          euler_roe<T, T, T>(Uin, Uout, n2, g1, H);
 #pragma unroll
           for (int a = 0; a < 4; ++a) hf[a] = H[a];
         } else {
-          Dual<T, 4> di[4], dd[4], H[4];
+          // group 0: dH/dU+ with U+ as the dual side; group 1: dH/dU- from the same
+          // code on the swapped states and reversed normal (H(U+, U-; n) = -H(U-, U+; -n)),
+          // so both groups run in lockstep and the other side stays plain
+          const bool sw = grp != 0;
+          const T sg = sw ? T(-1) : T(1);
+          Dual<T, 4> dA[4], H[4];
+          T B[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            di[a] = dconst<T, 4>(Uin[a]);
-            dd[a] = dconst<T, 4>(Uout[a]);
+            dA[a] = dconst<T, 4>(sw ? Uout[a] : Uin[a]);
+            dA[a].d[a] = T(1);
+            B[a] = sw ? Uin[a] : Uout[a];
           }
-          const T n2[2] = {nt[k][0], nt[k][1]};
+          const T n2[2] = {sg * nt[k][0], sg * nt[k][1]};
+          euler_roe<Dual<T, 4>, T, T>(dA, B, n2, g1, H);
+          T* dst = sw ? &Hm[pt * 16] : &Hp[pt * 16];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            if (grp == 0) di[a].d[a] = T(1);
-            else dd[a].d[a] = T(1);
-          }
-          euler_roe<Dual<T, 4>, T>(di, dd, n2, g1, H);
-          T* dst = (grp == 0) ? &Hp[pt * 16] : &Hm[pt * 16];
+            if (!sw) hf[a] = H[a].v;
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (grp == 0) hf[a] = H[a].v;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) dst[a * 4 + b] = H[a].d[b];
+            for (int b = 0; b < 4; ++b) dst[a * 4 + b] = sg * H[a].d[b];
           }
         }
       } else {

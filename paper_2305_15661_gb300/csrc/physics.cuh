@@ -101,7 +101,7 @@ __device__ __forceinline__ void euler_flux_vjp(const T U[4], T g1, const T vx[4]
   out[3] = g1 * (vx[1] + vy[2]) + gam * (u * vx[3] + v * vy[3]);
 }
 
-// Plain-value overloads so euler_roe<T, T> compiles with the same helpers.
+// Plain-value overloads so euler_roe<T, T, T> compiles with the same helpers.
 template <class T>
 __device__ __forceinline__ T recip(T a) { return T(1) / a; }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
@@ -168,10 +168,13 @@ __device__ __forceinline__ S harten_abs(const S& lam, const S& del, const S& i2d
 // |A_roe| dU = sum over the acoustic, entropy and shear waves of
 // |eigenvalue| x strength x eigenvector, with Roe averages weighted by sqrt(rho),
 // and Harten's entropy fix (delta = 0.1 c of the Roe state) on every |eigenvalue|.
-// S is T or a Dual over T (derivatives with respect to the states only: the
-// normal is a plain value).
-template <class S, class T>
-__device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T nt[2], T g1, S H[4]) {
+// S is the interior state's type and R the exterior's: T, or a Dual over T
+// (derivatives with respect to that state; the normal is a plain value). With R = T
+// only the interior side carries derivatives. The flux is conservative,
+// H(U+, U-; n) = -H(U-, U+; -n), so dH/dU- is -d/dU+ of the flux with the states
+// swapped and the normal reversed.
+template <class S, class R, class T>
+__device__ __forceinline__ void euler_roe(const S Ui[4], const R Uo[4], const T nt[2], T g1, S H[4]) {
   const T half = T(0.5);
   const T nn = nt[0] * nt[0] + nt[1] * nt[1];
   const T il = drsqrt(nn);
@@ -186,13 +189,13 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
   S hi = (Ui[3] + pi) * ri;
   S vni = ui * nx + vi * ny;
   // exterior side
-  S so, ro;
+  R so, ro;
   T rso;
   sqrt_recip(Uo[0], so, ro, rso);
-  S uo = Uo[1] * ro, vo = Uo[2] * ro;
-  S po = g1 * (Uo[3] - half * (Uo[1] * uo + Uo[2] * vo));
-  S ho = (Uo[3] + po) * ro;
-  S vno = uo * nx + vo * ny;
+  R uo = Uo[1] * ro, vo = Uo[2] * ro;
+  R po = g1 * (Uo[3] - half * (Uo[1] * uo + Uo[2] * vo));
+  R ho = (Uo[3] + po) * ro;
+  R vno = uo * nx + vo * ny;
   // Roe averages
   S iw = recip(si + so);
   S ua = (si * ui + so * uo) * iw;
@@ -226,7 +229,8 @@ __device__ __forceinline__ void euler_roe(const S Ui[4], const S Uo[4], const T 
   S d2 = wm * (va - cny) + wp * (va + cny) + we * va + ws * dty;
   S d3 = wm * (ha - cvn) + wp * (ha + cvn) + we * qa + ws * (ua * dtx + va * dty);
   // normal fluxes
-  S ehi = Ui[3] + pi, eho = Uo[3] + po;
+  S ehi = Ui[3] + pi;
+  R eho = Uo[3] + po;
   S f0 = Ui[0] * vni + Uo[0] * vno;
   S f1 = Ui[1] * vni + pi * nx + Uo[1] * vno + po * nx;
   S f2 = Ui[2] * vni + pi * ny + Uo[2] * vno + po * ny;
