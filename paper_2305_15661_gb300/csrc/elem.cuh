@@ -52,16 +52,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // lanes with cp.async: 16-byte pieces when src is 16-byte aligned and n T fill whole
 // pieces, else one value per copy. The caller waits (cp_async_wait_all + __syncwarp).
 template <class T>
-__device__ __forceinline__ void warp_copy_async(T* dst, const T* src, int n, int lane) {
+__device__ __forceinline__ void warp_copy_async(T* dst, const T* src, int n, int lane, int step = 32) {
   constexpr int V = 16 / sizeof(T);
   if (((uintptr_t)src & 15) == 0 && n % V == 0) {
-    for (int i = lane * V; i < n; i += 32 * V) cp_async16(dst + i, src + i);
+    for (int i = lane * V; i < n; i += step * V) cp_async16(dst + i, src + i);
   } else {
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < n; i += step) {
       if (sizeof(T) == 8) cp_async8(dst + i, src + i);
       else cp_async4(dst + i, src + i);
     }
   }
+}
+
+// Lanes that work on one element: the whole warp (step 32, lane = 0..31) or, where a
+// warp carries two elements (the gradient pass), the calling lane's half-warp (step 16,
+// lane = 0..15 within it). Any over those lanes; every lane of the warp must call it.
+__device__ __forceinline__ bool group_any(bool v, int step) {
+  if (step == 32) return __any_sync(0xffffffffu, v);
+  const unsigned m = __ballot_sync(0xffffffffu, v);
+  return ((threadIdx.x & 16) ? (m >> 16) : (m & 0xffffu)) != 0;
 }
 
 // Per-warp accumulators: the upper triangle of H row by row (k (k + 1) / 2 entries),
@@ -239,6 +248,9 @@ struct WarpLayout {
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
   static constexpr bool SLIM = GRAD && JAC && PROB == PROB_EULER;
+  // elements a warp evaluates at once: two (one per half-warp, each with its own
+  // copy of this layout) in the Euler gradient pass, else one
+  static constexpr int PER_WARP = SLIM ? 2 : 1;
   // offset of g (the tail [g | J | count]) within the accumulators
   __host__ __device__ static int gacc_offset(int k) { return SLIM ? 0 : acc_tail(k); }
   size_t oxe, oPsie, odN, oPhie, oPoff, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
@@ -310,7 +322,8 @@ __host__ __device__ inline size_t cta_bytes(int ku, int kx) {
 template <class T, int PROB, int P, bool JAC, bool GRAD = false>
 __host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps) {
   const int k = ku + kx;
-  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * WarpLayout<T, PROB, P, JAC, GRAD>(ku, kx).bytes +
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * Lay::PER_WARP * Lay(ku, kx).bytes +
          (GRAD ? 0 : align16((size_t)k * (k + 1)));  // upper-triangle pair table
 }
 
@@ -413,12 +426,12 @@ struct ElemCore {
   // volume flux Jacobians are not formed either, and the states U_q are kept in
   // Ah[q][0..3] for the adjoint's vector-Jacobian products.
   __device__ bool pointwise(int lane, const signed char* bcs, const double* mu, double gamma, bool need_hn,
-                            bool face_jac = true, bool vol_jac = true) {
+                            bool face_jac = true, bool vol_jac = true, int step = 32) {
     const bool fj = JAC && face_jac;
     bool bad = false;
     const T g1 = (T)(gamma - 1.0);
     // volume points
-    for (int q = lane; q < NQ; q += 32) {
+    for (int q = lane; q < NQ; q += step) {
       T U[4];
 #pragma unroll
       for (int a = 0; a < M; ++a) {
@@ -462,7 +475,7 @@ struct ElemCore {
     // face points: task t -> (group, face point); group 0: H and dH/dU+, group 1: dH/dU-
     const int npts = NF * NFQ;
     const int ngroups = (PROB == PROB_EULER && fj) ? 2 : 1;
-    for (int t = lane; t < npts * ngroups; t += 32) {
+    for (int t = lane; t < npts * ngroups; t += step) {
       const int grp = t / npts, pt = t % npts;
       const int k = pt / NFQ, f = pt % NFQ;
       T Uin[4], Uout[4];
@@ -548,7 +561,7 @@ struct ElemCore {
       // dH/dn from two identities of the Roe flux: homogeneity, dH/dn . n = H, and
       // rotational invariance, dH/dn . (J n) = G(H) - dH/dU+ G(U+) - dH/dU- G(U-),
       // with J the 90-degree rotation and G(V) = (0, -V_2, V_1, 0) its action on a state.
-      for (int pt = lane; pt < npts; pt += 32) {
+      for (int pt = lane; pt < npts; pt += step) {
         const int k = pt / NFQ;
         const T nx = nt[k][0], ny = nt[k][1];
         const T inv = T(1) / (nx * nx + ny * ny);
@@ -569,7 +582,7 @@ struct ElemCore {
         }
       }
     }
-    return __any_sync(0xffffffffu, bad);
+    return group_any(bad, step);
   }
 
   // Adjoint of steps 4-5 (the transposed element Jacobian applied to R_e):
@@ -673,7 +686,7 @@ struct ElemCore {
   // adj_state and also gives eps[r][d] = sum_q sum_a (D_r[q]^T R)_a f_d(U_q)_a, the
   // volume term of R_e^T dR_e/dx_e. Outputs (in W): dUe, dUp, eps (4), nu (n_face n_fq x 2).
   __device__ void adj_state_vjp(int lane, const signed char* bcs, double gamma, T*& dUe, T*& dUp, T*& eps,
-                                T*& nu) {
+                                T*& nu, int step = 32) {
     constexpr int NPT = NF * NFQ;
     const T g1 = (T)(gamma - 1.0);
     T* tq = W;                  // [NQ][M]
@@ -684,7 +697,7 @@ struct ElemCore {
     dUe = eq + NQ * 4;          // [NU]
     dUp = dUe + NU;             // [NUP]
     eps = dUp + NUP;            // [4]
-    for (int t = lane; t < NQ + NPT; t += 32) {
+    for (int t = lane; t < NQ + NPT; t += step) {
       if (t < NQ) {
         const int q = t;
         T sr[DIM][M];
@@ -751,7 +764,7 @@ struct ElemCore {
       }
     }
     __syncwarp();
-    for (int e = lane; e < NU + NUP + 4; e += 32) {
+    for (int e = lane; e < NU + NUP + 4; e += step) {
       T v = T(0);
       if (e < NU) {
         const int j = e / M, b = e - j * M;
@@ -787,9 +800,9 @@ struct ElemCore {
   }
 
   // Step 5: residual entries.
-  __device__ bool residual(int lane) {
+  __device__ bool residual(int lane, int step = 32) {
     bool bad = false;
-    for (int ia = lane; ia < NU; ia += 32) {
+    for (int ia = lane; ia < NU; ia += step) {
       const int i = ia / M, a = ia % M;
       T s = T(0);
 #pragma unroll
@@ -811,7 +824,7 @@ struct ElemCore {
       R[ia] = s;
       if (!isfinite((double)s)) bad = true;
     }
-    return __any_sync(0xffffffffu, bad);
+    return group_any(bad, step);
   }
 
   // Step 6a: derivative of R_e along a state direction (dUe: n_u values, dUp: n_u'
@@ -1264,7 +1277,8 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
 template <class T, int PROB, int P, bool JAC>
 __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e,
                                               const T* wT, const double* tauD, const double* mu, int lane,
-                                              signed char* bcs, bool face_jac = true, bool vol_jac = true) {
+                                              signed char* bcs, bool face_jac = true, bool vol_jac = true,
+                                              int step = 32) {
   using Dd = Disc<PROB, P>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
@@ -1273,14 +1287,14 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
     const int* vv = &a.ev[(long)e * NV];
     // 1. gather: Phi_e and Psi_e by asynchronous copies (all in flight at once),
     // overlapped with the neighbour offsets
-    warp_copy_async(C.Phie, a.Phi + (size_t)e * NU * ku, NU * ku, lane);
-    for (int i = lane; i < NXE * kx; i += 32) {
+    warp_copy_async(C.Phie, a.Phi + (size_t)e * NU * ku, NU * ku, lane, step);
+    for (int i = lane; i < NXE * kx; i += step) {
       const int r = C.dkx.div(i), c = i - r * kx;
       const int v = r / DIM, d = r - v * DIM;
       cp_async8(&C.Psie[i], &a.Psi[((size_t)vv[v] * DIM + d) * kx + c]);
     }
-    if (lane < NF * NT) {
-      const int kf = lane / NT, j = lane - kf * NT;
+    for (int t = lane; t < NF * NT; t += step) {
+      const int kf = t / NT, j = t - kf * NT;
       const int e2 = a.nbr[(long)e * NF + kf];
       const int k2 = a.nbr_face[(long)e * NF + kf];
       long long off = -1;
@@ -1290,13 +1304,13 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
         const int node = (k2 == 0) ? Dd::face_node(0, jj) : ((k2 == 1) ? Dd::face_node(1, jj) : Dd::face_node(2, jj));
         off = ((long long)e2 * NU + node * M) * ku;
       }
-      C.poff[lane] = off;
+      C.poff[t] = off;
     }
     C.PhiG = a.Phi;
     cp_async_wait_all();
     __syncwarp();
     // 2. reconstruction
-    for (int i = lane; i < NU + NUP; i += 32) {
+    for (int i = lane; i < NU + NUP; i += step) {
       T s = T(0);
       if (i < NU) {
         const T* row = &C.Phie[i * ku];
@@ -1312,11 +1326,11 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
         C.Up[r] = s;
       }
     }
-    if (lane < NXE) {
-      const int v = lane / DIM, d = lane - v * DIM;
+    for (int t = lane; t < NXE; t += step) {
+      const int v = t / DIM, d = t - v * DIM;
       double s = a.X[(size_t)vv[v] * DIM + d];
-      for (int c = 0; c < kx; ++c) s += C.Psie[lane * kx + c] * tauD[c];
-      C.xe[lane] = s;
+      for (int c = 0; c < kx; ++c) s += C.Psie[t * kx + c] * tauD[c];
+      C.xe[t] = s;
     }
     __syncwarp();
     // 3. geometry
@@ -1324,9 +1338,9 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
-    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn, face_jac, vol_jac);
+    bad |= C.pointwise(lane, bcs, mu, a.gamma, need_hn, face_jac, vol_jac, step);
     __syncwarp();
-    bad |= C.residual(lane);
+    bad |= C.residual(lane, step);
     return bad;
 }
 
@@ -1458,9 +1472,12 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
 // (dUe, dUp) the adjoint of the state Jacobians applied to R_e (no Jacobian
 // columns are formed for the state), J += rho (|R_e|^2 + N_e^2) / 2.
 template <class T, int PROB, int P>
+// step 16 (Euler): the calling half-warp evaluates this element (lane = 0..15 in it)
+// while the other half evaluates another; count = false: an idle half's stand-in
+// element (rho = 0), whose non-physical flag is not counted.
 __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C, const AsmArgs<T>& a, int e,
                                                   double rho, const T* wT, const double* tauD, const double* mu,
-                                                  int lane) {
+                                                  int lane, int step = 32, bool count = true) {
   using Dd = Disc<PROB, P>;
   constexpr int DIM = Dd::DIM, M = Dd::M, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NFQ = Dd::NFQ, NV = Dd::NV;
@@ -1468,7 +1485,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
   const int ku = a.ku, kx = a.kx, k = ku + kx;
   const int* vv = &a.ev[(long)e * NV];
   signed char bcs[NF];
-  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP, !kVJP);
+  const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP, !kVJP, step);
   const bool dist = a.kappa != 0.0;
   if (dist && lane == 0) {
     double Xe[6];
@@ -1479,10 +1496,10 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
   const T Ne = dist ? (T)C.dN[NXE] : T(0);
   const T rT = (T)rho;
   T *dUe, *dUp, *eps = nullptr, *nu = nullptr;
-  if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu);
+  if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu, step);
   else C.adj_state(lane, bcs, dUe, dUp);
   T* g = C.gacc;
-  for (int c = lane; c < ku; c += 32) {
+  for (int c = lane; c < ku; c += step) {
     T s = T(0);
 #pragma unroll
     for (int i = 0; i < NU; ++i) s += C.Phie[i * ku + c] * dUe[i];
@@ -1497,7 +1514,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
     if constexpr (kVJP) {
       // R_e^T dR_e/dx_e Psi_e[:, c]: the volume term through the cofactor change of the
       // direction, the face term through the scaled-normal change, plus distortion
-      for (int c = lane; c < kx; c += 32) {
+      for (int c = lane; c < kx; c += step) {
         const double* d = &C.Psie[c];  // column c, stride kx
         const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
         const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
@@ -1539,7 +1556,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
 #pragma unroll
     for (int i = 0; i < NU; ++i) s += C.R[i] * C.R[i];
     g[k] += T(0.5) * rT * (s + Ne * Ne);
-    if (bad) g[k + 1] += T(1);
+    if (bad && count) g[k + 1] += T(1);
   }
   __syncwarp();
 }
@@ -1582,32 +1599,47 @@ __global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
   double* tauD;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
   using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  constexpr int PW = Lay::PER_WARP;  // 2: two elements per warp, one per half-warp
+  const int half = PW == 2 ? (lane >> 4) : 0, sub = PW == 2 ? (lane & 15) : lane, step = 32 / PW;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
-  const size_t wb = Lay(ku, kx).bytes;
+  const size_t eb = Lay(ku, kx).bytes;  // one element's region; a warp holds PW of them
   Core C;
-  C.template carve<GRAD>(smem + cb + warp * wb, ku, kx);
+  C.template carve<GRAD>(smem + cb + (warp * PW + half) * eb, ku, kx);
   bind_tables(C, tab);
   const int nacc = k * k + k + 2;  // entries of a partial row (full H)
   const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
-  for (int i = lane; i < nzero; i += 32) C.acc[i] = T(0);
-  unsigned char* pairs = smem + cb + nw * wb;
+  for (int i = sub; i < nzero; i += step) C.acc[i] = T(0);
+  unsigned char* pairs = smem + cb + nw * PW * eb;
   if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
-  for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
-    const int e = a.elems ? a.elems[it] : (int)it;
-    const double rho = a.rho ? a.rho[it] : 1.0;
-    if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, lane);
-    else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
+  if constexpr (PW == 2) {
+    // both halves take the same number of trips; a half without an element of its
+    // own re-evaluates its partner's with rho = 0
+    for (long base = ((long)blockIdx.x * nw + warp) * 2; base < a.n_items; base += (long)gridDim.x * nw * 2) {
+      const long it = base + half;
+      const bool real = it < a.n_items;
+      const long ir = real ? it : base;
+      const int e = a.elems ? a.elems[ir] : (int)ir;
+      const double rho = real ? (a.rho ? a.rho[ir] : 1.0) : 0.0;
+      element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, sub, 16, real);
+    }
+  } else {
+    for (long it = (long)blockIdx.x * nw + warp; it < a.n_items; it += (long)gridDim.x * nw) {
+      const int e = a.elems ? a.elems[it] : (int)it;
+      const double rho = a.rho ? a.rho[it] : 1.0;
+      if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, lane);
+      else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
+    }
   }
   __syncthreads();
-  // CTA partial: sum the warps' accumulators in warp order, in FP64 (gradient pass:
-  // rows of [g | J | count] only)
+  // CTA partial: sum the accumulators of the CTA's element regions in order, in FP64
+  // (gradient pass: rows of [g | J | count] only)
   Lay L(ku, kx);
   const int nrow = GRAD ? k + 2 : nacc;
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
     const int src = GRAD ? Lay::gacc_offset(k) + i : acc_source(i, k);
     double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += (double)((const T*)(smem + cb + w * wb + L.oacc))[src];
+    for (int w = 0; w < nw * PW; ++w) s += (double)((const T*)(smem + cb + w * eb + L.oacc))[src];
     a.partial[(size_t)blockIdx.x * nrow + i] = s;
   }
 }
@@ -1639,10 +1671,12 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
   double* tau_unused;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT_unused, tau_unused);
   using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  constexpr int PW = Lay::PER_WARP;  // 2: two elements per warp, one per half-warp
+  const int half = PW == 2 ? (lane >> 4) : 0, sub = PW == 2 ? (lane & 15) : lane, step = 32 / PW;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
-  const size_t wb = Lay(ku, kx).bytes;
+  const size_t eb = Lay(ku, kx).bytes;
   Lay L(ku, kx);
-  unsigned char* wbase = smem + cb + warp * wb;
+  unsigned char* wbase = smem + cb + (warp * PW + half) * eb;
   Core C;
   C.template carve<GRAD>(wbase, ku, kx);
   bind_tables(C, tab);
@@ -1650,26 +1684,45 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
   double* tq = (double*)(wbase + L.otq);
   const int nacc = k * k + k + 2;
   const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
-  unsigned char* pairs = smem + cb + nw * wb;
+  unsigned char* pairs = smem + cb + nw * PW * eb;
   if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   for (int ch = blockIdx.x * nw + warp; ch < b.n_chunks; ch += gridDim.x * nw) {
     const int q = b.chunk_query[ch];
     if (b.done != nullptr && *(volatile const int*)(b.done + (long)q * b.donestride)) continue;
     const double* wsrc = b.w + (long)q * b.wstride;
-    for (int i = lane; i < ku; i += 32) wq[i] = (T)wsrc[i];
-    for (int i = lane; i < kx; i += 32) tq[i] = wsrc[ku + i];
-    for (int i = lane; i < nzero; i += 32) C.acc[i] = T(0);
+    for (int i = sub; i < ku; i += step) wq[i] = (T)wsrc[i];
+    for (int i = sub; i < kx; i += step) tq[i] = wsrc[ku + i];
+    for (int i = sub; i < nzero; i += step) C.acc[i] = T(0);
     __syncwarp();
     const double* muq = b.mu + (long)q * b.mustride;
+    if constexpr (PW == 2) {
+      // the chunk's items in pairs, one per half-warp; an odd last item leaves the
+      // second half re-evaluating it with rho = 0
+      const int i0 = b.chunk_start[ch], i1 = b.chunk_start[ch + 1];
 #pragma unroll 1
-    for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it) {
-      if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, a.elems[it], a.rho[it], wq, tq, muq, lane);
-      else element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+      for (int it = i0; it < i1; it += 2) {
+        const int my = it + half;
+        const bool real = my < i1;
+        const int ir = real ? my : it;
+        element_grad_pass<T, PROB, P>(C, a, a.elems[ir], real ? a.rho[ir] : 0.0, wq, tq, muq, sub, 16, real);
+      }
+    } else {
+#pragma unroll 1
+      for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it) {
+        if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, a.elems[it], a.rho[it], wq, tq, muq, lane);
+        else element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+      }
     }
     __syncwarp();
     if (GRAD) {
-      for (int i = lane; i < k + 2; i += 32) a.partial[(size_t)ch * (k + 2) + i] = (double)C.gacc[i];
+      // both halves' accumulators (one region when PW = 1)
+      const unsigned char* r0 = smem + cb + warp * PW * eb;
+      for (int i = lane; i < k + 2; i += 32) {
+        double v = 0.0;
+        for (int h = 0; h < PW; ++h) v += (double)((const T*)(r0 + h * eb + L.oacc))[Lay::gacc_offset(k) + i];
+        a.partial[(size_t)ch * (k + 2) + i] = v;
+      }
     } else {
       for (int i = lane; i < nacc; i += 32) a.partial[(size_t)ch * nacc + i] = (double)C.acc[acc_source(i, k)];
     }
