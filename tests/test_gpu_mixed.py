@@ -214,6 +214,32 @@ def test_fp32_jacobian_mode_sparse_weights_and_burgers():
     assert abs(gb["J"] - rb["J"]) <= 1e-10 * rb["J"]
 
 
+@pytest.mark.parametrize("p,count,kappa", [(2, 37, 0.0), (3, 11, 0.1), (1, 5, 0.0)])
+def test_gradient_pass_odd_element_counts(p, count, kappa):
+    # The FP64 gradient pass evaluates two elements per warp (one per half-warp); with
+    # an odd number of sampled elements a half re-evaluates its partner's element
+    # with weight 0. S~, T~, J~ must still be the oracle's to 1e-10, the non-physical
+    # count must stay 0, and a chunked batch with odd chunk tails must agree too.
+    wl = W.euler_workload(n=8, p=p, k_u=9, k_x=3, seed=91, n_mu=3, mu_box=True)
+    sets = W.eq_weight_sets(wl, 3, seed=92, lo=count, hi=count + 1)
+    assert all(len(e) % 2 == 1 for e, _ in sets)
+    O = orc.Oracle.from_workload(wl, kappa=kappa)
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32_JACOBIAN, kappa=kappa)
+    ctx.set_eq_weights(sets[0])
+    g = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0], rho_set=sets[0])
+    assert _fro(np.concatenate([g["S"], g["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-10
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+    ctx.set_eq_weights_batched(sets)
+    ctx.set_launch_shapes(2, 2, 4)  # chunks of 4: odd tails in every query
+    ys, zs = np.stack([wl.w_eval] * 3), np.stack([wl.tau_eval] * 3)
+    gb = ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs)
+    for q in range(3):
+        r = O.reduced(wl.Phi, wl.Psi, ys[q], zs[q], wl.mus[q], rho_set=sets[q])
+        assert _fro(np.concatenate([gb["S"][q], gb["T"][q]]), np.concatenate([r["S"], r["T"]])) < 1e-10
+        assert abs(gb["J"][q] - r["J"]) <= 1e-10 * r["J"]
+
+
 def test_fp32_jacobian_mode_solves_reach_the_fp64_optimum():
     wl = W.euler_workload(n=10, p=2, k_u=10, k_x=4, seed=21)
     mu = wl.mus[0]
