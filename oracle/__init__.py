@@ -47,7 +47,7 @@ def _load():
         pd, pi, pl = P(d), P(i), P(l)
         vp = ctypes.c_void_p
         sig = {
-            "orc_create": (vp, [i, i, l, pd, l, pi, d, d, d, i]),
+            "orc_create": (vp, [i, i, l, pd, l, pi, d, d, d, i, i]),
             "orc_destroy": (None, [vp]),
             "orc_sizes": (None, [vp, pl]),
             "orc_neighbors": (None, [vp, pi, pi]),
@@ -142,10 +142,13 @@ def freestream(gamma, mu):
 class Oracle:
     """One problem instance: mesh, reference element and connectivity."""
 
-    def __init__(self, problem, p, X, ev, gamma=1.4, kappa=0.0, eps=1e-8, bc_mode=BC_DEFAULT):
+    def __init__(self, problem, p, X, ev, gamma=1.4, kappa=0.0, eps=1e-8, bc_mode=BC_DEFAULT, q=1):
+        """q: geometry degree, 1 (straight-sided, ev = vertices) or 2 (2-D curved, ev = the
+        three vertices then the midpoint nodes of edges 0-1, 1-2, 2-0)."""
         lib = _load()
         self.problem = problem
         self.p = p
+        self.q = q
         self.X = _f64(X)
         self.ev = np.ascontiguousarray(ev, dtype=np.int32)
         self.dim = 1 if problem == PROB_BURGERS1D else 2
@@ -153,7 +156,7 @@ class Oracle:
         n_verts = self.X.shape[0]
         n_elems = self.ev.shape[0]
         self._h = lib.orc_create(problem, p, n_verts, _pd(self.X), n_elems, _pi(self.ev), gamma, kappa, eps,
-                                 bc_mode)
+                                 bc_mode, q)
         if not self._h:
             raise ValueError("oracle: bad problem, degree or mesh")
         s = np.zeros(10, dtype=np.int64)
@@ -166,7 +169,7 @@ class Oracle:
     @classmethod
     def from_workload(cls, wl, kappa=None, bc_mode=BC_DEFAULT):
         return cls(wl.problem, wl.p, wl.X, wl.ev, gamma=wl.gamma, kappa=wl.kappa if kappa is None else kappa,
-                   bc_mode=bc_mode)
+                   bc_mode=bc_mode, q=getattr(wl, "q", 1))
 
     def __del__(self):
         if getattr(self, "_h", None):

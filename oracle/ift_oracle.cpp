@@ -366,17 +366,20 @@ enum { BC_DEFAULT = 0, BC_SHEAR_TEST = 2 };
 
 struct Oracle {
   int problem = 0, dim = 1, m = 1, p = 1;
+  int q = 1;                        // geometry degree: 1 straight-sided, 2 curved (2-D)
   RefElem re;
+  RefElem geo;                      // q = 2: the six-node quadratic map (vertices, edge midpoints)
   long n_verts = 0, n_elems = 0;
-  std::vector<double> X;            // n_verts x dim, reference mesh nodes
-  std::vector<int> ev;              // n_elems x (dim+1)
+  std::vector<double> X;            // n_verts x dim, reference mesh nodes (all geometry nodes)
+  std::vector<int> ev;              // n_elems x nv(): element geometry nodes
   std::vector<int> nbr;             // n_elems x nface: neighbour element or -1
   std::vector<int> nbr_face;        // n_elems x nface: neighbour's local face
   double gamma = 1.4, kappa = 0.0, eps = 1e-8;
   int bc_mode = BC_DEFAULT;
   int nu() const { return re.nb * m; }
   int nup() const { return re.nface * re.ntrace * m; }
-  int nxe() const { return (dim + 1) * dim; }
+  int nv() const { return q == 1 ? dim + 1 : 6; }  // geometry nodes per element
+  int nxe() const { return nv() * dim; }
   long Nu() const { return n_elems * (long)nu(); }
   long Nx() const { return n_verts * (long)dim; }
 };
@@ -574,6 +577,56 @@ void phys_point(const Geom<T>& gm, const double* xi, T* x) {
   }
 }
 
+// Curved (q = 2, 2-D) element geometry at the master point xi. The element map is
+// the six-node quadratic Lagrange map x(xi) = sum_j N_j(xi) x_j over the vertices
+// and edge midpoints, and likewise X(xi) for the reference mesh, so
+// JX = dX/dxi and Jx = dx/dxi vary over the element; G = Jx JX^{-1}, g = det G.
+template <class T>
+void point_geometry(const Oracle& O, long e, const T* xe, const double* xi, Geom<T>& gm) {
+  gm.dim = 2;
+  const int* vv = &O.ev[e * 6];
+  double dN[6][2];
+  for (int j = 0; j < 6; ++j)
+    for (int c = 0; c < 2; ++c) dN[j][c] = O.geo.dphi(j, xi, c);
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) {
+      double sX = 0.0;
+      T sx = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        sX += O.X[vv[j] * 2 + r] * dN[j][c];
+        sx += xe[j * 2 + r] * dN[j][c];
+      }
+      gm.JX[r * 2 + c] = sX;
+      gm.Jx[r * 2 + c] = sx;
+    }
+  gm.detJX = gm.JX[0] * gm.JX[3] - gm.JX[1] * gm.JX[2];
+  gm.JXinv[0] = gm.JX[3] / gm.detJX;
+  gm.JXinv[1] = -gm.JX[1] / gm.detJX;
+  gm.JXinv[2] = -gm.JX[2] / gm.detJX;
+  gm.JXinv[3] = gm.JX[0] / gm.detJX;
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) {
+      T s = 0.0;
+      for (int k = 0; k < 2; ++k) s += gm.Jx[r * 2 + k] * gm.JXinv[k * 2 + c];
+      gm.G[r * 2 + c] = s;
+    }
+  gm.g = gm.G[0] * gm.G[3] - gm.G[1] * gm.G[2];
+  gm.Ginv[0] = gm.G[3] / gm.g;
+  gm.Ginv[1] = -gm.G[1] / gm.g;
+  gm.Ginv[2] = -gm.G[2] / gm.g;
+  gm.Ginv[3] = gm.G[0] / gm.g;
+}
+
+// Physical point x(xi) = sum_j N_j(xi) x_j of the curved element map.
+template <class T>
+void phys_point_q2(const Oracle& O, const T* xe, const double* xi, T* x) {
+  for (int r = 0; r < 2; ++r) {
+    T s = 0.0;
+    for (int j = 0; j < 6; ++j) s += O.geo.phi(j, xi) * xe[j * 2 + r];
+    x[r] = s;
+  }
+}
+
 inline bool bad(double a) { return !std::isfinite(a); }
 
 // Element residual R_e(U_e, U_e', x_e; mu) of the transformed law (Eq. p2r-flux)
@@ -590,13 +643,19 @@ void element_residual(const Oracle& O, long e, const T* Ue, const T* Up, const T
   const int dim = O.dim, m = O.m, nb = re.nb;
   for (int i = 0; i < nb * m; ++i) Re[i] = T(0.0);
   Geom<T> gm;
-  element_geometry(O, e, xe, gm);
-  if (!(val(gm.g) > 0.0)) *nonphys = true;
+  if (O.q == 1) {
+    element_geometry(O, e, xe, gm);
+    if (!(val(gm.g) > 0.0)) *nonphys = true;
+  }
   // volume integral
   for (int q = 0; q < re.nq(); ++q) {
     const double* xi = &re.vq[q * dim];
     const double* phi = &re.tv_phi[q * nb];
     const double* dphi = &re.tv_dphi[q * nb * dim];
+    if (O.q == 2) {  // curved: the geometry of this point
+      point_geometry(O, e, xe, xi, gm);
+      if (!(val(gm.g) > 0.0) || !(gm.detJX > 0.0)) *nonphys = true;
+    }
     double dX = gm.detJX * re.vw[q];
     T U[4];
     for (int a = 0; a < m; ++a) {
@@ -648,6 +707,17 @@ void element_residual(const Oracle& O, long e, const T* Ue, const T* Up, const T
       if (dim == 1) {
         N[0] = (k == 0) ? -1.0 : 1.0;
         dS0 = re.fw[fq];
+      } else if (O.q == 2) {
+        // curved: the reference tangent dX/dt = JX (V_{k+1} - V_k) at this face point
+        point_geometry(O, e, xe, xi, gm);
+        if (!(val(gm.g) > 0.0) || !(gm.detJX > 0.0)) *nonphys = true;
+        int k1 = (k + 1) % 3;
+        double dv[2] = {re.mvert[2 * k1] - re.mvert[2 * k], re.mvert[2 * k1 + 1] - re.mvert[2 * k + 1]};
+        double E[2] = {gm.JX[0] * dv[0] + gm.JX[1] * dv[1], gm.JX[2] * dv[0] + gm.JX[3] * dv[1]};
+        double Ln = std::sqrt(E[0] * E[0] + E[1] * E[1]);
+        N[0] = E[1] / Ln;
+        N[1] = -E[0] / Ln;
+        dS0 = Ln * re.fw[fq];
       } else {
         int k1 = (k + 1) % 3;
         const int* vv = &O.ev[e * 3];
@@ -685,7 +755,8 @@ void element_residual(const Oracle& O, long e, const T* Ue, const T* Up, const T
         Uout[0] = (N[0] < 0.0) ? T(1.0) : Uin[0];
       } else if (O.bc_mode == BC_SHEAR_TEST) {
         T xp[2] = {T(0.0), T(0.0)};
-        phys_point(gm, xi, xp);
+        if (O.q == 2) phys_point_q2(O, xe, xi, xp);
+        else phys_point(gm, xi, xp);
         euler_shear_state(O.gamma, xp[0], xp[1], Uout);
       } else {
         double Uf[4];
@@ -806,6 +877,17 @@ void element_residual_physical(const Oracle& O, long e, const double* Ue, const 
 template <class T>
 T distortion_eta(const Oracle& O, long e, const T* xe) {
   Geom<T> gm;
+  if (O.q == 2) {  // curved: G varies, one geometry per volume point
+    T eta = 0.0;
+    for (int q = 0; q < O.re.nq(); ++q) {
+      point_geometry(O, e, xe, &O.re.vq[q * 2], gm);
+      T nrm2 = 0.0;
+      for (int i = 0; i < 4; ++i) nrm2 += gm.G[i] * gm.G[i];
+      T ratio = nrm2 / dmaxe(gm.g, O.eps);  // max(g, eps)^{2/d}, d = 2
+      eta += ratio * ratio * (gm.detJX * O.re.vw[q]);
+    }
+    return eta;
+  }
   element_geometry(O, e, xe, gm);
   T nrm2 = 0.0;
   for (int i = 0; i < O.dim * O.dim; ++i) nrm2 += gm.G[i] * gm.G[i];
@@ -822,8 +904,8 @@ template <class T>
 T distortion_N(const Oracle& O, long e, const T* xe) {
   int nx = O.nxe();
   std::vector<T> Xe(nx);
-  const int* vv = &O.ev[e * (O.dim + 1)];
-  for (int v = 0; v <= O.dim; ++v)
+  const int* vv = &O.ev[e * O.nv()];
+  for (int v = 0; v < O.nv(); ++v)
     for (int c = 0; c < O.dim; ++c) Xe[v * O.dim + c] = T(O.X[vv[v] * O.dim + c]);
   return O.kappa * (distortion_eta(O, e, xe) - distortion_eta(O, e, Xe.data()));
 }
@@ -889,8 +971,8 @@ void gather(const Oracle& O, const double* U, const double* x, long e, double* U
     }
   }
   if (xe) {
-    const int* vv = &O.ev[e * (O.dim + 1)];
-    for (int v = 0; v <= O.dim; ++v)
+    const int* vv = &O.ev[e * O.nv()];
+    for (int v = 0; v < O.nv(); ++v)
       for (int c = 0; c < O.dim; ++c) xe[v * O.dim + c] = x[vv[v] * O.dim + c];
   }
 }
@@ -916,8 +998,8 @@ void gather_rows(const Oracle& O, int ku, const double* Phi, int kx, const doubl
         }
       }
   }
-  const int* vv = &O.ev[e * (O.dim + 1)];
-  for (int v = 0; v <= O.dim; ++v)
+  const int* vv = &O.ev[e * O.nv()];
+  for (int v = 0; v < O.nv(); ++v)
     for (int c = 0; c < O.dim; ++c)
       for (int j = 0; j < kx; ++j) Psie[(v * O.dim + c) * kx + j] = Psi[(vv[v] * (long)O.dim + c) * kx + j];
 }
@@ -941,8 +1023,8 @@ void element_reduced(const Oracle& O, int ku, const double* Phi, int kx, const d
     for (int c = 0; c < ku; ++c) Ue[i] += Phie[i * ku + c] * w[c];
   for (int i = 0; i < nup; ++i)
     for (int c = 0; c < ku; ++c) Up[i] += Phip[i * ku + c] * w[c];
-  const int* vv = &O.ev[e * (O.dim + 1)];
-  for (int v = 0; v <= O.dim; ++v)
+  const int* vv = &O.ev[e * O.nv()];
+  for (int v = 0; v < O.nv(); ++v)
     for (int c = 0; c < O.dim; ++c) {
       int r = v * O.dim + c;
       double s = O.X[vv[v] * O.dim + c];
@@ -1240,7 +1322,7 @@ bool build_neighbors(Oracle& O) {
     std::map<std::pair<int, int>, std::pair<long, int>> seen;
     for (long e = 0; e < O.n_elems; ++e)
       for (int k = 0; k < 3; ++k) {
-        int a = O.ev[e * 3 + k], b = O.ev[e * 3 + (k + 1) % 3];
+        int a = O.ev[e * O.nv() + k], b = O.ev[e * O.nv() + (k + 1) % 3];
         std::pair<int, int> key(a < b ? a : b, a < b ? b : a);
         auto it = seen.find(key);
         if (it == seen.end()) {
@@ -1267,7 +1349,7 @@ bool build_neighbors(Oracle& O) {
 extern "C" {
 
 void* orc_create(int problem, int p, long n_verts, const double* X, long n_elems, const int* ev,
-                 double gamma, double kappa, double eps, int bc_mode) {
+                 double gamma, double kappa, double eps, int bc_mode, int q) {
   Oracle* O = new Oracle();
   O->problem = problem;
   O->dim = (problem == PROB_BURGERS1D) ? 1 : 2;
@@ -1277,14 +1359,16 @@ void* orc_create(int problem, int p, long n_verts, const double* X, long n_elems
   O->kappa = kappa;
   O->eps = eps;
   O->bc_mode = bc_mode;
-  if ((problem != PROB_BURGERS1D && problem != PROB_EULER2D) || !build_ref(O->dim, p, O->re)) {
+  O->q = q;
+  if ((problem != PROB_BURGERS1D && problem != PROB_EULER2D) || !build_ref(O->dim, p, O->re) ||
+      (q != 1 && q != 2) || (q == 2 && (O->dim != 2 || !build_ref(2, 2, O->geo)))) {
     delete O;
     return nullptr;
   }
   O->n_verts = n_verts;
   O->n_elems = n_elems;
   O->X.assign(X, X + n_verts * O->dim);
-  O->ev.assign(ev, ev + n_elems * (O->dim + 1));
+  O->ev.assign(ev, ev + n_elems * O->nv());
   if (!build_neighbors(*O)) {
     delete O;
     return nullptr;
@@ -1439,12 +1523,12 @@ int orc_global_jacobian(void* h, const double* U, const double* x, const double*
             dRdU[gi * Nu + gj] += JUp[i * nup + (k * nt + j) * m + a];
           }
       }
-      const int* vv = &O->ev[e * (O->dim + 1)];
-      for (int v = 0; v <= O->dim; ++v)
+      const int* vv = &O->ev[e * O->nv()];
+      for (int v = 0; v < O->nv(); ++v)
         for (int c = 0; c < O->dim; ++c) dRdx[gi * Nx + vv[v] * O->dim + c] += Jx[i * nx + v * O->dim + c];
     }
-    const int* vv = &O->ev[e * (O->dim + 1)];
-    for (int v = 0; v <= O->dim; ++v)
+    const int* vv = &O->ev[e * O->nv()];
+    for (int v = 0; v < O->nv(); ++v)
       for (int c = 0; c < O->dim; ++c) dNdx[e * Nx + vv[v] * O->dim + c] += dN[v * O->dim + c];
   }
   return bad_count;

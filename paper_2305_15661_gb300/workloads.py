@@ -102,6 +102,38 @@ def square_tri_mesh(n: int):
     return X, ev
 
 
+def square_tri_mesh_q2(n: int, curve: float = 0.0):
+    """Six-node (q = 2) triangles: the triangles of square_tri_mesh with a node at the
+    midpoint of every edge (per element: the three vertices, then the midpoints of edges
+    0-1, 1-2 and 2-0), after which every node moves by the smooth map
+    x -> x + curve / (2 pi) (sin(pi x) sin(pi y), sin(pi x) sin(2 pi y)).
+    The map fixes the boundary of the unit square and bends the interior edges into
+    parabolas; curve = 0 leaves straight-sided elements with midpoint nodes.
+    """
+    X, ev = square_tri_mesh(n)
+    nv = X.shape[0]
+    ne = ev.shape[0]
+    ev6 = np.empty((ne, 6), dtype=np.int32)
+    ev6[:, :3] = ev
+    edge_id = {}
+    mids = []
+    for e in range(ne):
+        for k in range(3):
+            a, b = int(ev[e, k]), int(ev[e, (k + 1) % 3])
+            key = (a, b) if a < b else (b, a)
+            if key not in edge_id:
+                edge_id[key] = nv + len(mids)
+                mids.append(0.5 * (X[a] + X[b]))
+            ev6[e, 3 + k] = edge_id[key]
+    Xq = np.concatenate([X, np.asarray(mids)], axis=0)
+    if curve:
+        x, y = Xq[:, 0], Xq[:, 1]
+        d = np.stack([np.sin(math.pi * x) * np.sin(math.pi * y), np.sin(math.pi * x) * np.sin(2 * math.pi * y)],
+                     axis=1)
+        Xq = Xq + curve / (2 * math.pi) * d
+    return Xq, ev6
+
+
 def boundary_elements(X: np.ndarray, ev: np.ndarray, tol: float = 1e-12):
     """Per side of the unit square (x=0, x=1, y=0, y=1), the elements with an edge on it."""
     out = []
@@ -157,8 +189,8 @@ class Workload:
     name: str
     problem: int
     p: int
-    X: np.ndarray            # n_verts x dim reference nodes
-    ev: np.ndarray           # n_elems x (dim+1) int32
+    X: np.ndarray            # n_verts x dim reference nodes (all geometry nodes)
+    ev: np.ndarray           # n_elems x (dim+1) int32 (q = 2: n_elems x 6, vertices then edge midpoints)
     Phi: np.ndarray          # N_u x k_u, row-major, element-major rows
     Psi: np.ndarray          # N_x x k_x
     gamma: float = 1.4
@@ -168,6 +200,7 @@ class Workload:
     tau_eval: np.ndarray = None
     U_guess: np.ndarray = None  # per-query constant state used by the paper's initialisation
     rho_sets: list = None       # per query: (elems int32, rho float64) or None for rho = 1
+    q: int = 1                  # geometry degree (2: curved six-node triangles)
 
     @property
     def dim(self):
@@ -244,15 +277,16 @@ def _bump_modes(X: np.ndarray, k_x: int) -> np.ndarray:
 
 def euler_workload(n: int = 100, p: int = 2, k_u: int = 20, k_x: int = 4, seed: int = 2,
                    mach: float = 2.0, alpha: float = 0.0, n_mu: int = 1, mu_box: bool = False,
-                   gamma: float = 1.4, name: str = "euler2d") -> Workload:
+                   gamma: float = 1.4, name: str = "euler2d", q: int = 1, curve: float = 0.0) -> Workload:
     """2-D steady Euler on the unit square with a Mach-2 free stream.
 
     Phi = QR([U_pert, G]) with U_pert = U_inf (1 + 1e-2 xi), G ~ N(0, 1); the
     first column is U_pert/|U_pert| with positive sign. Psi = QR of smooth bump
     modes. The evaluation point (w, tau) keeps every triangle's area above half
-    its reference value.
+    its reference value. q = 2: curved six-node triangles (square_tri_mesh_q2 with
+    the given curve); the mesh modes act on every geometry node.
     """
-    X, ev = square_tri_mesh(n)
+    X, ev = square_tri_mesh(n) if q == 1 else square_tri_mesh_q2(n, curve)
     ne = ev.shape[0]
     nb = (p + 1) * (p + 2) // 2
     Nu = ne * nb * 4
@@ -282,7 +316,7 @@ def euler_workload(n: int = 100, p: int = 2, k_u: int = 20, k_x: int = 4, seed: 
     else:
         mus = np.tile(np.array([[mach, alpha]]), (n_mu, 1))
     return Workload(name=name, problem=PROB_EULER2D, p=p, X=X, ev=ev, Phi=Phi, Psi=Psi, gamma=gamma,
-                    mus=mus, w_eval=w, tau_eval=tau, U_guess=U_inf, rho_sets=None)
+                    mus=mus, w_eval=w, tau_eval=tau, U_guess=U_inf, rho_sets=None, q=q)
 
 
 MU_BOX_LO = np.array([1.8, math.radians(-2.0)])
