@@ -100,6 +100,9 @@ typedef struct {
   int max_iters;      /* per LM phase */
   int lm_init;        /* IFT_INIT_PAPER or IFT_INIT_GIVEN */
   int contraction;    /* IFT_CONTRACT_FP, _TF32, _3XTF32 or _BF16 (all but FP need a precision other than IFT_FP64) */
+  int q;              /* geometry degree: 1 straight-sided, 2 curved six-node triangles (IFT_EULER2D only;
+                         ift_set_mesh then takes the three vertices and the midpoint nodes of edges
+                         0-1, 1-2, 2-0 of every element, and the mesh modes act on all those nodes) */
 } ift_config;
 
 /* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,

@@ -38,7 +38,7 @@ def _units():
     units = [("api", "api.cu", []), ("lm", "lm.cu", []), ("refelem", "refelem.cpp", []),
              ("dispatch", "dispatch.cpp", []), ("noalloc", "noalloc.cu", []),
              ("mlp", "mlp.cu", [])]
-    for prob in (1, 2):
+    for prob in (1, 2, 3):
         for p in (1, 2, 3):
             for prec in (0, 1):
                 units.append((f"asm_{prob}_{p}_{prec}", "asm_inst.cu",

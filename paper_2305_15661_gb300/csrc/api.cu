@@ -399,6 +399,7 @@ void ift_config_default(ift_config* cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->problem = IFT_EULER2D;
+  cfg->q = 1;
   cfg->p = 2;
   cfg->precision = IFT_FP64;
   cfg->gamma = 1.4;
@@ -425,6 +426,10 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   }
   if (cfg->p < 1 || cfg->p > 3) {
     g_create_error = "degree p must be 1, 2 or 3";
+    return IFT_ERR_ARG;
+  }
+  if (cfg->q != 1 && !(cfg->q == 2 && cfg->problem == IFT_EULER2D)) {
+    g_create_error = "geometry degree q must be 1, or 2 for IFT_EULER2D";
     return IFT_ERR_ARG;
   }
   if (cfg->precision != IFT_FP64 && cfg->precision != IFT_FP32 && cfg->precision != IFT_MIXED &&
@@ -462,7 +467,7 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   }
   c->dim = dim;
   c->m = (dim == 1) ? 1 : 4;
-  c->nv = dim + 1;
+  c->nv = (cfg->q == 2) ? 6 : dim + 1;
   c->nb = c->T.nb;
   c->nu = c->nb * c->m;
   c->nface = c->T.nface;
@@ -471,8 +476,12 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   c->nxe = c->nv * dim;
   c->nq = c->T.nq;
   c->nfq = c->T.nfq;
-  c->ks[0] = (dim == 1) ? burgers_kernels(cfg->p, 0) : euler_kernels(cfg->p, 0);
-  if (cfg->precision != IFT_FP64) c->ks[1] = (dim == 1) ? burgers_kernels(cfg->p, 1) : euler_kernels(cfg->p, 1);
+  auto kernels_for = [&](int prec) {
+    if (dim == 1) return burgers_kernels(cfg->p, prec);
+    return cfg->q == 2 ? euler_curved_kernels(cfg->p, prec) : euler_kernels(cfg->p, prec);
+  };
+  c->ks[0] = kernels_for(0);
+  if (cfg->precision != IFT_FP64) c->ks[1] = kernels_for(1);
   if (!c->ks[0].valid || (cfg->precision != IFT_FP64 && !c->ks[1].valid)) {
     delete c;
     g_create_error = "kernels for this problem/degree/precision are not built";
@@ -502,6 +511,12 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     tab.insert(tab.end(), c->T.qxi.begin(), c->T.qxi.end());
   } else {
     tab.insert(tab.end(), (size_t)c->nq, 0.0);  // 2-D kernels do not read the 1-D point table
+  }
+  if (cfg->q == 2) {  // curved: the geometry shape-function derivatives (see refelem.h)
+    std::vector<double> gdv, gtf;
+    build_curved_tables(c->T, gdv, gtf);
+    tab.insert(tab.end(), gdv.begin(), gdv.end());
+    tab.insert(tab.end(), gtf.begin(), gtf.end());
   }
   c->max_parts = c->sm_count * 32;
   bool ok = dalloc(c->d_tables, tab.size()) == cudaSuccess &&
@@ -626,7 +641,7 @@ ift_status ift_set_mesh(ift_ctx* c, int64_t n_verts, const double* X, int64_t n_
       if (dim == 1) {
         key = (uint64_t)(uint32_t)ev[e * 2 + k];
       } else {
-        uint32_t a = (uint32_t)ev[e * 3 + k], b = (uint32_t)ev[e * 3 + (k + 1) % 3];
+        uint32_t a = (uint32_t)ev[e * nv + k], b = (uint32_t)ev[e * nv + (k + 1) % 3];
         key = ((uint64_t)(a < b ? a : b) << 32) | (uint64_t)(a < b ? b : a);
       }
       auto it = open_faces.find(key);

@@ -1,5 +1,6 @@
 // One instantiation of the element kernels, selected at compile time by
-// IFT_PROB (1 Burgers, 2 Euler), IFT_P (degree) and IFT_PREC (0 FP64, 1 FP32).
+// IFT_PROB (1 Burgers, 2 Euler, 3 Euler on curved elements), IFT_P (degree) and
+// IFT_PREC (0 FP64, 1 FP32).
 // The build compiles this file once per combination, in parallel.
 #include "kernel_set.cuh"
 

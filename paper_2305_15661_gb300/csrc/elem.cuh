@@ -225,7 +225,10 @@ struct Tabs {
   using Dd = Disc<PROB, P>;
   static constexpr int nD = Dd::DIM * Dd::NQ * Dd::NB, nB = Dd::NQ * Dd::NB, nL = Dd::NFQ * Dd::NTRACE,
                        nfw = Dd::NFQ, nqw = Dd::NQ, nqx = Dd::NQ;
-  static constexpr int total = nD + nB + nL + nfw + nqw + nqx;
+  // curved elements: dN_j/dxi_c of the six geometry shape functions at the volume
+  // points (NQ x 6 x 2), and dN_j/dt along each face at its points (NF x NFQ x 6)
+  static constexpr int nGv = Dd::CURVED ? Dd::NQ * 12 : 0, nGt = Dd::CURVED ? Dd::NFACE * Dd::NFQ * 6 : 0;
+  static constexpr int total = nD + nB + nL + nfw + nqw + nqx + nGv + nGt;
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -247,14 +250,14 @@ struct WarpLayout {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
-  static constexpr bool SLIM = GRAD && JAC && PROB == PROB_EULER;
+  static constexpr bool SLIM = GRAD && JAC && Dd::EULER;
   // elements a warp evaluates at once: two (one per half-warp, each with its own
   // copy of this layout) in the Euler gradient pass, else one
   static constexpr int PER_WARP = SLIM ? 2 : 1;
   // offset of g (the tail [g | J | count]) within the accumulators
   __host__ __device__ static int gacc_offset(int k) { return SLIM ? 0 : acc_tail(k); }
   size_t oxe, oPsie, odN, oPhie, oPoff, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
-      oW, owq, otq, oacc, bytes;
+      oW, owq, otq, oacc, ocofq, ontq, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
     const int k = ku + kx;
     size_t b = 0;
@@ -277,6 +280,9 @@ struct WarpLayout {
     oAh = put(JAC ? (SLIM ? NQ * M : NQ * DIM * M * M) : 1, sizeof(T));
     osq = put(NQ, sizeof(T));
     oHf = put(NF * NFQ * M, sizeof(T));
+    // curved elements: the cofactor at every volume point and the scaled normal at every face point
+    ocofq = put(Dd::CURVED ? NQ * 4 : 1, sizeof(T));
+    ontq = put(Dd::CURVED ? NF * NFQ * 2 : 1, sizeof(T));
     oHp = put(JAC && !SLIM ? NF * NFQ * M * M : 1, sizeof(T));
     oHm = put(JAC && !SLIM ? NF * NFQ * M * M : 1, sizeof(T));
     oHn = put(JAC && !SLIM ? NF * NFQ * M * 2 : 1, sizeof(T));
@@ -292,6 +298,11 @@ struct WarpLayout {
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
+      // curved mesh columns: dF per (volume point, column) and dH per (face point, column)
+      if (Dd::CURVED) {
+        const size_t wc = (size_t)NQ * (kx > 0 ? kx : 1) * 8 + (size_t)NF * NFQ * (kx > 0 ? kx : 1) * 4;
+        if (wc > w) w = wc;
+      }
       if (SLIM) w = 0;  // the gradient pass stages only the adjoint below
       {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), nu (2 NF NFQ),
          // eps per volume point (4 NQ), dU_e, dU_e' (NU + NU'), eps (4)
@@ -347,12 +358,13 @@ struct ElemCore {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NB = Dd::NB, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP,
                        NXE = Dd::NXE, NF = Dd::NFACE, NFQ = Dd::NFQ, NT = Dd::NTRACE;
-  // shared tables
-  const T *D, *B, *Lt, *fw, *qw, *qxi;
+  // shared tables (GdV, GtF: curved geometry shape-function derivatives)
+  const T *D, *B, *Lt, *fw, *qw, *qxi, *GdV, *GtF;
   // warp buffers
   double *xe, *Psie, *dN;
   T *Phie, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
   T* gacc;  // [g | J | count] within acc
+  T *cofq, *ntq;  // curved: cofactor per volume point (4), scaled normal per face point (2)
   // geometry (registers, identical on all lanes)
   T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
   T detJ;
@@ -390,6 +402,59 @@ struct ElemCore {
     dNt = (T*)(base + L.odNt);
     acc = (T*)(base + L.oacc);
     gacc = acc + L.gacc_offset(ku + kx);
+    cofq = (T*)(base + L.ocofq);
+    ntq = (T*)(base + L.ontq);
+  }
+
+  // Cofactor g G^{-T} (entry [d][r] at d * 2 + r) at volume point q, and the scaled
+  // normal of face k at face point pt: per point for curved elements, else the
+  // element's constants.
+  __device__ __forceinline__ T cofv(int q, int i) const {
+    if constexpr (Dd::CURVED) return cofq[q * 4 + i];
+    else return cof[i];
+  }
+  __device__ __forceinline__ T ntv(int pt, int k, int d) const {
+    if constexpr (Dd::CURVED) return ntq[pt * 2 + d];
+    else return nt[k][d];
+  }
+
+  // Curved element geometry (Eq. p2r-flux with the six-node quadratic map
+  // x(xi) = sum_j N_j(xi) x_j): at every volume point the cofactor of J = dx/dxi,
+  // at every face point the scaled normal, the tangent dx/dt of the face turned by
+  // -90 degrees (counter-clockwise elements: outward). Lanes split the points.
+  // Returns false for the lane's group if the map folds (det J <= 0 at a point).
+  __device__ bool geometry_curved(int lane, int step) {
+    bool ok = true;
+    for (int t = lane; t < NQ + NF * NFQ; t += step) {
+      if (t < NQ) {
+        const T* gd = &GdV[t * 12];
+        double J0 = 0.0, J1 = 0.0, J2 = 0.0, J3 = 0.0;  // J[r * 2 + c] = d x_r / d xi_c
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          J0 += xe[2 * j] * (double)gd[2 * j];
+          J1 += xe[2 * j] * (double)gd[2 * j + 1];
+          J2 += xe[2 * j + 1] * (double)gd[2 * j];
+          J3 += xe[2 * j + 1] * (double)gd[2 * j + 1];
+        }
+        cofq[t * 4 + 0] = (T)J3;
+        cofq[t * 4 + 1] = (T)(-J2);
+        cofq[t * 4 + 2] = (T)(-J1);
+        cofq[t * 4 + 3] = (T)J0;
+        if (!(J0 * J3 - J1 * J2 > 0.0)) ok = false;
+      } else {
+        const int pt = t - NQ;
+        const T* tw = &GtF[pt * 6];
+        double tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          tx += xe[2 * j] * (double)tw[j];
+          ty += xe[2 * j + 1] * (double)tw[j];
+        }
+        ntq[pt * 2 + 0] = (T)ty;
+        ntq[pt * 2 + 1] = (T)(-tx);
+      }
+    }
+    return !group_any(!ok, step);
   }
 
   // Geometry from xe (FP64). Returns false if the element is inverted.
@@ -440,7 +505,7 @@ struct ElemCore {
         for (int j = 0; j < NB; ++j) s += B[q * NB + j] * Ue[j * M + a];
         U[a] = s;
       }
-      if (PROB == PROB_EULER) {
+      if (Dd::EULER) {
         T fx[4], fy[4], Pq;
         euler_flux(U, g1, fx, fy, Pq);
         if (!(U[0] > T(0)) || !(Pq > T(0))) bad = true;
@@ -449,7 +514,7 @@ struct ElemCore {
           fph[(q * 2 + 0) * 4 + a] = fx[a];
           fph[(q * 2 + 1) * 4 + a] = fy[a];
 #pragma unroll
-          for (int r = 0; r < 2; ++r) Fh[(q * 2 + r) * 4 + a] = fx[a] * cof[0 * 2 + r] + fy[a] * cof[1 * 2 + r];
+          for (int r = 0; r < 2; ++r) Fh[(q * 2 + r) * 4 + a] = fx[a] * cofv(q, 0 * 2 + r) + fy[a] * cofv(q, 1 * 2 + r);
         }
         if (JAC && vol_jac) {
           T Ax[16], Ay[16];
@@ -457,7 +522,7 @@ struct ElemCore {
 #pragma unroll
           for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int ab = 0; ab < 16; ++ab) Ah[(q * 2 + r) * 16 + ab] = Ax[ab] * cof[r] + Ay[ab] * cof[2 + r];
+            for (int ab = 0; ab < 16; ++ab) Ah[(q * 2 + r) * 16 + ab] = Ax[ab] * cofv(q, r) + Ay[ab] * cofv(q, 2 + r);
         } else if (JAC) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) Ah[q * 4 + a] = U[a];
@@ -474,7 +539,7 @@ struct ElemCore {
     }
     // face points: task t -> (group, face point); group 0: H and dH/dU+, group 1: dH/dU-
     const int npts = NF * NFQ;
-    const int ngroups = (PROB == PROB_EULER && fj) ? 2 : 1;
+    const int ngroups = (Dd::EULER && fj) ? 2 : 1;
     for (int t = lane; t < npts * ngroups; t += step) {
       const int grp = t / npts, pt = t % npts;
       const int k = pt / NFQ, f = pt % NFQ;
@@ -493,7 +558,7 @@ struct ElemCore {
         Uout[a] = so;
       }
       const signed char bt = bcs[k];
-      if (PROB == PROB_EULER) {
+      if (Dd::EULER) {
         if (bt == 1) {
           double Uf[4];
           euler_farfield(gamma, mu[0], mu[1], Uf);
@@ -513,7 +578,7 @@ struct ElemCore {
           }
         }
         if (!fj) {
-          T n2[2] = {nt[k][0], nt[k][1]};
+          T n2[2] = {ntv(pt, k, 0), ntv(pt, k, 1)};
           T H[4];
           euler_roe<T, T, T>(Uin, Uout, n2, g1, H);
 #pragma unroll
@@ -532,7 +597,7 @@ struct ElemCore {
             dA[a].d[a] = T(1);
             B[a] = sw ? Uin[a] : Uout[a];
           }
-          const T n2[2] = {sg * nt[k][0], sg * nt[k][1]};
+          const T n2[2] = {sg * ntv(pt, k, 0), sg * ntv(pt, k, 1)};
           euler_roe<Dual<T, 4>, T, T>(dA, B, n2, g1, H);
           T* dst = sw ? &Hm[pt * 16] : &Hp[pt * 16];
 #pragma unroll
@@ -556,14 +621,14 @@ struct ElemCore {
         }
       }
     }
-    if (PROB == PROB_EULER && fj && need_hn) {
+    if (Dd::EULER && fj && need_hn) {
       __syncwarp();
       // dH/dn from two identities of the Roe flux: homogeneity, dH/dn . n = H, and
       // rotational invariance, dH/dn . (J n) = G(H) - dH/dU+ G(U+) - dH/dU- G(U-),
       // with J the 90-degree rotation and G(V) = (0, -V_2, V_1, 0) its action on a state.
       for (int pt = lane; pt < npts; pt += step) {
         const int k = pt / NFQ;
-        const T nx = nt[k][0], ny = nt[k][1];
+        const T nx = ntv(pt, k, 0), ny = ntv(pt, k, 1);
         const T inv = T(1) / (nx * nx + ny * ny);
         const T* h = &Hf[pt * 4];
         const T* hp = &Hp[pt * 16];
@@ -686,7 +751,7 @@ struct ElemCore {
   // adj_state and also gives eps[r][d] = sum_q sum_a (D_r[q]^T R)_a f_d(U_q)_a, the
   // volume term of R_e^T dR_e/dx_e. Outputs (in W): dUe, dUp, eps (4), nu (n_face n_fq x 2).
   __device__ void adj_state_vjp(int lane, const signed char* bcs, double gamma, T*& dUe, T*& dUp, T*& eps,
-                                T*& nu, int step = 32) {
+                                T*& nu, int step = 32, T** eq_out = nullptr) {
     constexpr int NPT = NF * NFQ;
     const T g1 = (T)(gamma - 1.0);
     T* tq = W;                  // [NQ][M]
@@ -694,6 +759,7 @@ struct ElemCore {
     T* mm = mp + NPT * M;       // [NPT][M]
     nu = mm + NPT * M;          // [NPT][2]
     T* eq = nu + NPT * 2;       // [NQ][4]
+    if (eq_out) *eq_out = eq;
     dUe = eq + NQ * 4;          // [NU]
     dUp = dUe + NU;             // [NUP]
     eps = dUp + NUP;            // [4]
@@ -716,8 +782,8 @@ struct ElemCore {
         T vx[4], vy[4], Uq[4], tb[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          vx[a] = cof[0] * sr[0][a] + cof[1] * sr[1][a];
-          vy[a] = cof[2] * sr[0][a] + cof[3] * sr[1][a];
+          vx[a] = cofv(q, 0) * sr[0][a] + cofv(q, 1) * sr[1][a];
+          vy[a] = cofv(q, 2) * sr[0][a] + cofv(q, 3) * sr[1][a];
           Uq[a] = Ah[q * 4 + a];
         }
         euler_flux_vjp(Uq, g1, vx, vy, tb);
@@ -747,7 +813,7 @@ struct ElemCore {
           Uin[a] = Ui[pt * 4 + a];
           Uout[a] = Uo[pt * 4 + a];
         }
-        const T n2[2] = {nt[kf][0], nt[kf][1]};
+        const T n2[2] = {ntv(pt, kf, 0), ntv(pt, kf, 1)};
         euler_roe_vjp<T>(Uin, Uout, n2, g1, lam, Hv, up, um);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -884,11 +950,70 @@ struct ElemCore {
     }
   }
 
+  // Curved geometry derivatives along a direction dx of the six nodes (12 values):
+  // dJ at volume point q gives the cofactor change dcof (4), the tangent change at
+  // face point pt the scaled-normal change dnt (2); both are linear in dx.
+  __device__ __forceinline__ void dcof_curved(const double* dx, int stride, int q, T dcof[4]) const {
+    const T* gd = &GdV[q * 12];
+    T J0 = T(0), J1 = T(0), J2 = T(0), J3 = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const T x0 = (T)dx[(2 * j) * stride], x1 = (T)dx[(2 * j + 1) * stride];
+      J0 += x0 * gd[2 * j];
+      J1 += x0 * gd[2 * j + 1];
+      J2 += x1 * gd[2 * j];
+      J3 += x1 * gd[2 * j + 1];
+    }
+    dcof[0] = J3;
+    dcof[1] = -J2;
+    dcof[2] = -J1;
+    dcof[3] = J0;
+  }
+  __device__ __forceinline__ void dnt_curved(const double* dx, int stride, int pt, T dn[2]) const {
+    const T* tw = &GtF[pt * 6];
+    T tx = T(0), ty = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      tx += (T)dx[(2 * j) * stride] * tw[j];
+      ty += (T)dx[(2 * j + 1) * stride] * tw[j];
+    }
+    dn[0] = ty;
+    dn[1] = -tx;
+  }
+
   // Step 6b: derivative of R_e along a mesh direction dx (n_x values, FP64).
   __device__ void jvp_geom(const double* dx, const double* mu, T dR[NU]) {
 #pragma unroll
     for (int i = 0; i < NU; ++i) dR[i] = T(0);
-    if (DIM == 2) {
+    if constexpr (Dd::CURVED) {
+#pragma unroll 1
+      for (int q = 0; q < NQ; ++q) {
+        T dcof[4];
+        dcof_curved(dx, 1, q, dcof);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T dF = fph[(q * 2 + 0) * M + a] * dcof[0 * 2 + r] + fph[(q * 2 + 1) * M + a] * dcof[1 * 2 + r];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) dR[i * M + a] -= D[(r * NQ + q) * NB + i] * dF;
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int f = 0; f < NFQ; ++f) {
+          const int pt = k * NFQ + f;
+          T dn[2];
+          dnt_curved(dx, 1, pt, dn);
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            T dH = Hn[(pt * M + a) * 2 + 0] * dn[0] + Hn[(pt * M + a) * 2 + 1] * dn[1];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) dR[Dd::face_node(k, j) * M + a] += fw[f] * Lt[f * NT + j] * dH;
+          }
+        }
+    } else if (DIM == 2) {
       T dj00 = (T)(dx[2] - dx[0]), dj01 = (T)(dx[4] - dx[0]);
       T dj10 = (T)(dx[3] - dx[1]), dj11 = (T)(dx[5] - dx[1]);
       T dcof[4] = {dj11, -dj10, -dj01, dj00};
@@ -1117,8 +1242,123 @@ struct ElemCore {
   // sum is taken once per element, E[i][a][r][d] = sum_q D_r[q][i] f_d(U_q)_a
   // (staged in W), and each column is then sum_{r,d} dcof[c][d][r] E[i][a][r][d].
   // Faces: dH = Hn dn with the scaled-normal change dn; Burgers: the source only.
+  // Mesh columns of A_e on curved elements: the cofactor and the normals vary by
+  // point, so the quadrature sum cannot be factored out of the columns as for
+  // straight sides. Per (volume point, column) the flux change dF_r = sum_d f_d
+  // dcof[d][r], per (face point, column) the flux change dH = Hn dnt are staged in
+  // W; each entry (row, column) is then -sum_q sum_r D_r[q][i] dF + the lifted dH.
+  __device__ void jac_geom_curved(int lane, int ku, int kx, int k, bool dist) {
+    T* dF = W;                     // [NQ][kx][M][2]
+    T* dHf = W + NQ * kx * M * 2;  // [NF NFQ][kx][M]
+    for (int t = lane; t < NQ * kx; t += 32) {
+      const int q = dkx.div(t), c = t - q * kx;
+      T dcof[4];
+      dcof_curved(&Psie[c], kx, q, dcof);
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          dF[(t * M + a) * 2 + r] = fph[(q * 2 + 0) * M + a] * dcof[0 * 2 + r] + fph[(q * 2 + 1) * M + a] * dcof[1 * 2 + r];
+    }
+    for (int t = lane; t < NF * NFQ * kx; t += 32) {
+      const int pt = dkx.div(t), c = t - pt * kx;
+      T dn[2];
+      dnt_curved(&Psie[c], kx, pt, dn);
+#pragma unroll
+      for (int a = 0; a < M; ++a) dHf[t * M + a] = Hn[(pt * M + a) * 2 + 0] * dn[0] + Hn[(pt * M + a) * 2 + 1] * dn[1];
+    }
+    __syncwarp();
+    for (int e = lane; e < NU * kx; e += 32) {
+      const int row = dkx.div(e), c = e - row * kx;
+      const int i = row / M, a = row - i * M;
+      T s = T(0);
+#pragma unroll 4
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) s -= D[(r * NQ + q) * NB + i] * dF[((q * kx + c) * M + a) * 2 + r];
+#pragma unroll
+      for (int kf = 0; kf < NF; ++kf) {
+        const int j = face_pos(kf, i);
+        if (j < 0) continue;
+#pragma unroll
+        for (int f = 0; f < NFQ; ++f) s += fw[f] * Lt[f * NT + j] * dHf[(((kf * NFQ + f) * kx) + c) * M + a];
+      }
+      A[row * k + ku + c] = s;
+    }
+    if (dist) {
+      for (int c = lane; c < kx; c += 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < NXE; ++r) s += dN[r] * Psie[r * kx + c];
+        dNt[c] = (T)s;
+      }
+    }
+    __syncwarp();
+  }
+
+  // Distortion of a curved element (Eqs. dist_elem0-1): eta_e = sum_q w_q det JX_q
+  // (|G_q|_F^2 / max(g_q, eps))^2 with G_q = Jx_q JX_q^{-1} (d = 2), and its
+  // derivative through dJx_q / dx_js = delta_rs dN_j/dxi; written by one lane into
+  // dN[0..NXE-1] and dN[NXE] = kappa (eta(x_e) - eta(X_e)). Xe: reference nodes.
+  __device__ void distortion_curved(const double* Xe, double kappa, double eps) {
+    double eta = 0.0, eta0 = 0.0, de[NXE];
+#pragma unroll
+    for (int r = 0; r < NXE; ++r) de[r] = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      const T* gd = &GdV[q * 12];
+      double A4[4] = {0.0, 0.0, 0.0, 0.0}, J4[4] = {0.0, 0.0, 0.0, 0.0};  // [r * 2 + c]
+      for (int j = 0; j < 6; ++j)
+        for (int r = 0; r < 2; ++r)
+          for (int c = 0; c < 2; ++c) {
+            A4[r * 2 + c] += Xe[2 * j + r] * (double)gd[2 * j + c];
+            J4[r * 2 + c] += xe[2 * j + r] * (double)gd[2 * j + c];
+          }
+      const double dA = A4[0] * A4[3] - A4[1] * A4[2];
+      const double Ai[4] = {A4[3] / dA, -A4[1] / dA, -A4[2] / dA, A4[0] / dA};
+      const double w = (double)qw[q] * dA;
+      // value at the reference nodes (G = I) and at x_e
+      for (int pass = 0; pass < 2; ++pass) {
+        const double* Jx = pass == 0 ? A4 : J4;
+        double G[4];
+        for (int r = 0; r < 2; ++r)
+          for (int c = 0; c < 2; ++c) G[r * 2 + c] = Jx[r * 2] * Ai[c] + Jx[r * 2 + 1] * Ai[2 + c];
+        const double n2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2] + G[3] * G[3];
+        const double g = G[0] * G[3] - G[1] * G[2];
+        const double den = g >= eps ? g : eps;
+        const double ratio = n2 / den;
+        if (pass == 0) {
+          eta0 += w * ratio * ratio;
+          continue;
+        }
+        eta += w * ratio * ratio;
+        // d ratio / d Jx[r][k]: |G|^2 through G = Jx Ai, g = det Jx / det JX (the g-branch only)
+        const double cofJ[4] = {Jx[3], -Jx[2], -Jx[1], Jx[0]};  // d det Jx / d Jx[r][k]
+        for (int r = 0; r < 2; ++r)
+          for (int k2 = 0; k2 < 2; ++k2) {
+            const double dn2 = 2.0 * (G[r * 2] * Ai[k2 * 2] + G[r * 2 + 1] * Ai[k2 * 2 + 1]);
+            const double dg = g >= eps ? cofJ[r * 2 + k2] / dA : 0.0;
+            const double dratio = dn2 / den - n2 / (den * den) * dg;
+            const double dval = w * 2.0 * ratio * dratio;
+            for (int j = 0; j < 6; ++j) de[2 * j + r] += dval * (double)gd[2 * j + k2];
+          }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NXE; ++r) dN[r] = kappa * de[r];
+    dN[NXE] = kappa * (eta - eta0);
+  }
+
+  __device__ void distortion_any(const double* Xe, double kappa, double eps) {
+    if constexpr (Dd::CURVED) distortion_curved(Xe, kappa, eps);
+    else distortion(Xe, kappa, eps);
+  }
+
   __device__ void jac_geom(int lane, const double* mu, int ku, int kx, int k, bool dist) {
     if (kx == 0) return;
+    if constexpr (Dd::CURVED) {
+      jac_geom_curved(lane, ku, kx, k, dist);
+      return;
+    }
     T* E = W;                  // [NB][M][DIM][DIM]
     T* dcof = W + NB * M * 4;  // [kx][4]
     T* K = dcof + 4 * kx;      // [NF][NT][M][2]: sum_f fw[f] Lt[f][j] Hn[kf, f][a][d]
@@ -1268,6 +1508,8 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
   C.fw = C.Lt + TB::nL;
   C.qw = C.fw + TB::nfw;
   C.qxi = C.qw + TB::nqw;
+  C.GdV = C.qxi + TB::nqx;
+  C.GtF = C.GdV + TB::nGv;
 }
 
 // Steps 1-5 for element e at the state (wT, tauD) and parameters mu: gather,
@@ -1334,7 +1576,13 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
     }
     __syncwarp();
     // 3. geometry
-    bool bad = !C.geometry();
+    bool bad;
+    if constexpr (Dd::CURVED) {
+      bad = !C.geometry_curved(lane, step);
+      __syncwarp();
+    } else {
+      bad = !C.geometry();
+    }
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
     // 4. pointwise, 5. residual
@@ -1361,9 +1609,9 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
     // distortion
     const bool dist = a.kappa != 0.0;
     if (dist && lane == 0) {
-      double Xe[6];
+      double Xe[NXE];
       for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
-      C.distortion(Xe, a.kappa, a.eps);
+      C.distortion_any(Xe, a.kappa, a.eps);
     }
     __syncwarp();
     const T Ne = dist ? (T)C.dN[NXE] : T(0);
@@ -1480,23 +1728,23 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
                                                   int lane, int step = 32, bool count = true) {
   using Dd = Disc<PROB, P>;
   constexpr int DIM = Dd::DIM, M = Dd::M, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
-                NFQ = Dd::NFQ, NV = Dd::NV;
-  constexpr bool kVJP = PROB == PROB_EULER;  // Euler: reverse-mode face adjoint, no face Jacobians
+                NFQ = Dd::NFQ, NV = Dd::NV, NQ = Dd::NQ;
+  constexpr bool kVJP = Dd::EULER;  // Euler: reverse-mode face adjoint, no face Jacobians
   const int ku = a.ku, kx = a.kx, k = ku + kx;
   const int* vv = &a.ev[(long)e * NV];
   signed char bcs[NF];
   const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, mu, lane, bcs, !kVJP, !kVJP, step);
   const bool dist = a.kappa != 0.0;
   if (dist && lane == 0) {
-    double Xe[6];
+    double Xe[NXE];
     for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
-    C.distortion(Xe, a.kappa, a.eps);
+    C.distortion_any(Xe, a.kappa, a.eps);
   }
   __syncwarp();
   const T Ne = dist ? (T)C.dN[NXE] : T(0);
   const T rT = (T)rho;
-  T *dUe, *dUp, *eps = nullptr, *nu = nullptr;
-  if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu, step);
+  T *dUe, *dUp, *eps = nullptr, *nu = nullptr, *eq = nullptr;
+  if constexpr (kVJP) C.adj_state_vjp(lane, bcs, a.gamma, dUe, dUp, eps, nu, step, &eq);
   else C.adj_state(lane, bcs, dUe, dUp);
   T* g = C.gacc;
   for (int c = lane; c < ku; c += step) {
@@ -1516,19 +1764,37 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
       // direction, the face term through the scaled-normal change, plus distortion
       for (int c = lane; c < kx; c += step) {
         const double* d = &C.Psie[c];  // column c, stride kx
-        const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
-        const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
-        // dcof[d*2 + r] = (dj11, -dj10, -dj01, dj00) pairs with eps[r*2 + d]
-        T s = -(eps[0] * dj11 + eps[1] * (-dj01) + eps[2] * (-dj10) + eps[3] * dj00);
+        T s = T(0);
+        if constexpr (Dd::CURVED) {
+          // per point: eq[q][r][d] = (D_r[q]^T R) . f_d(U_q) against the cofactor change,
+          // nu[pt] against the scaled-normal change
+#pragma unroll 1
+          for (int q = 0; q < NQ; ++q) {
+            T dcof[4];
+            C.dcof_curved(d, kx, q, dcof);
+            s -= eq[q * 4 + 0] * dcof[0] + eq[q * 4 + 1] * dcof[2] + eq[q * 4 + 2] * dcof[1] + eq[q * 4 + 3] * dcof[3];
+          }
 #pragma unroll
-        for (int kf = 0; kf < NF; ++kf) {
-          const int k1 = (kf + 1) % 3;
-          const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
-          const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+          for (int pt = 0; pt < NF * NFQ; ++pt) {
+            T dn[2];
+            C.dnt_curved(d, kx, pt, dn);
+            s += nu[pt * 2 + 0] * dn[0] + nu[pt * 2 + 1] * dn[1];
+          }
+        } else {
+          const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
+          const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
+          // dcof[d*2 + r] = (dj11, -dj10, -dj01, dj00) pairs with eps[r*2 + d]
+          s = -(eps[0] * dj11 + eps[1] * (-dj01) + eps[2] * (-dj10) + eps[3] * dj00);
 #pragma unroll
-          for (int f = 0; f < NFQ; ++f) {
-            const int pt = kf * NFQ + f;
-            s += nu[pt * 2 + 0] * dnx + nu[pt * 2 + 1] * dny;
+          for (int kf = 0; kf < NF; ++kf) {
+            const int k1 = (kf + 1) % 3;
+            const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
+            const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+#pragma unroll
+            for (int f = 0; f < NFQ; ++f) {
+              const int pt = kf * NFQ + f;
+              s += nu[pt * 2 + 0] * dnx + nu[pt * 2 + 1] * dny;
+            }
           }
         }
         if (dist) {
@@ -1813,9 +2079,9 @@ __global__ void __launch_bounds__(128) element_gradients_kernel(AsmArgs<T> a, do
     signed char bcs[NF];
     const bool bad = element_front<T, PROB, P, true>(C, a, e, wT, tauD, a.mu, lane, bcs);
     if (dist && lane == 0) {
-      double Xe[6];
+      double Xe[NXE];
       for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
-      C.distortion(Xe, a.kappa, a.eps);
+      C.distortion_any(Xe, a.kappa, a.eps);
     }
     __syncwarp();
     const T Ne = dist ? (T)C.dN[NXE] : T(0);
@@ -1886,7 +2152,12 @@ __global__ void __launch_bounds__(128) inspect_kernel(AsmArgs<T> a, const double
     }
     if (lane < NXE) C.xe[lane] = x[(size_t)vv[lane / DIM] * DIM + (lane % DIM)];
     __syncwarp();
-    C.geometry();
+    if constexpr (Dd::CURVED) {
+      C.geometry_curved(lane, 32);
+      __syncwarp();
+    } else {
+      C.geometry();
+    }
     signed char bcs[NF];
 #pragma unroll
     for (int kf = 0; kf < NF; ++kf) bcs[kf] = a.bc[(long)e * NF + kf];
@@ -1894,9 +2165,9 @@ __global__ void __launch_bounds__(128) inspect_kernel(AsmArgs<T> a, const double
     __syncwarp();
     C.residual(lane);
     if (lane == 0) {
-      double Xe[6];
+      double Xe[NXE];
       for (int r = 0; r < NXE; ++r) Xe[r] = a.X[(size_t)vv[r / DIM] * DIM + (r % DIM)];
-      C.distortion(Xe, a.kappa, a.eps);
+      C.distortion_any(Xe, a.kappa, a.eps);
     }
     __syncwarp();
     for (int c = lane; c < ND; c += 32) {

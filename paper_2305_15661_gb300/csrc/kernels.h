@@ -40,6 +40,8 @@ struct KernelSet {
 
 // precision: 0 = FP64, 1 = FP32
 KernelSet euler_kernels(int p, int precision);
+// Euler on curved (q = 2) six-node triangles
+KernelSet euler_curved_kernels(int p, int precision);
 KernelSet burgers_kernels(int p, int precision);
 
 }  // namespace ift

@@ -12,12 +12,16 @@ namespace ift {
 
 constexpr int PROB_BURGERS = 1;
 constexpr int PROB_EULER = 2;
+// Euler on curved (q = 2) elements: six-node quadratic element maps, so the
+// cofactor of the map and the scaled face normals vary over the element
+constexpr int PROB_EULER_Q2 = 3;
 
 template <int PROB, int P>
 struct Disc;
 
 template <int P>
 struct Disc<PROB_BURGERS, P> {
+  static constexpr bool EULER = false, CURVED = false;
   static constexpr int M = 1, DIM = 1, NB = P + 1, NQ = P + 2, NFACE = 2, NTRACE = 1, NFQ = 1, NV = 2;
   static constexpr int NU = NB * M, NUP = NFACE * NTRACE * M, NXE = NV * DIM;
   // trace node j of face k (faces are the left and right end points)
@@ -26,6 +30,7 @@ struct Disc<PROB_BURGERS, P> {
 
 template <int P>
 struct Disc<PROB_EULER, P> {
+  static constexpr bool EULER = true, CURVED = false;
   static constexpr int M = 4, DIM = 2, NB = (P + 1) * (P + 2) / 2, NQ = (P + 2) * (P + 2), NFACE = 3,
                        NTRACE = P + 1, NFQ = P + 2, NV = 3;
   static constexpr int NU = NB * M, NUP = NFACE * NTRACE * M, NXE = NV * DIM;
@@ -33,6 +38,15 @@ struct Disc<PROB_EULER, P> {
   __host__ __device__ static constexpr int face_node(int k, int j) {
     return j == 0 ? k : (j == P ? (k + 1) % 3 : 3 + k * (P - 1) + (j - 1));
   }
+};
+
+// Curved Euler: the same discretisation with six geometry nodes per element (the
+// vertices, then the midpoints of edges 0-1, 1-2, 2-0).
+template <int P>
+struct Disc<PROB_EULER_Q2, P> : Disc<PROB_EULER, P> {
+  static constexpr bool CURVED = true;
+  static constexpr int NV = 6;
+  static constexpr int NXE = NV * 2;
 };
 
 // ---------------------------------------------------------------------------

@@ -232,4 +232,45 @@ bool build_tables(int dim, int p, RefTables& t) {
   return true;
 }
 
+// Quadratic Lagrange shape functions on the triangle in barycentric form, with
+// l0 = 1 - r - s, l1 = r, l2 = s: vertices N_v = l_v (2 l_v - 1), edge midpoints
+// N = 4 l_a l_b; their gradients with respect to (r, s).
+static void quad_shape_grad(double r, double s, double g[6][2]) {
+  const double l0 = 1.0 - r - s, l1 = r, l2 = s;
+  g[0][0] = -(4.0 * l0 - 1.0);
+  g[0][1] = -(4.0 * l0 - 1.0);
+  g[1][0] = 4.0 * l1 - 1.0;
+  g[1][1] = 0.0;
+  g[2][0] = 0.0;
+  g[2][1] = 4.0 * l2 - 1.0;
+  g[3][0] = 4.0 * (l0 - l1);  // edge 0-1: 4 l0 l1
+  g[3][1] = -4.0 * l1;
+  g[4][0] = 4.0 * l2;         // edge 1-2: 4 l1 l2
+  g[4][1] = 4.0 * l1;
+  g[5][0] = -4.0 * l2;        // edge 2-0: 4 l2 l0
+  g[5][1] = 4.0 * (l0 - l2);
+}
+
+void build_curved_tables(const RefTables& t, std::vector<double>& gdv, std::vector<double>& gtf) {
+  static const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  gdv.assign((size_t)t.nq * 12, 0.0);
+  for (int q = 0; q < t.nq; ++q) {
+    double g[6][2];
+    quad_shape_grad(t.qxi[2 * q], t.qxi[2 * q + 1], g);
+    for (int j = 0; j < 6; ++j)
+      for (int c = 0; c < 2; ++c) gdv[(q * 6 + j) * 2 + c] = g[j][c];
+  }
+  gtf.assign((size_t)3 * t.nfq * 6, 0.0);
+  for (int k = 0; k < 3; ++k) {
+    const int k1 = (k + 1) % 3;
+    const double dv[2] = {V[k1][0] - V[k][0], V[k1][1] - V[k][1]};
+    for (int f = 0; f < t.nfq; ++f) {
+      const double tt = t.ft[f];
+      double g[6][2];
+      quad_shape_grad(V[k][0] + tt * dv[0], V[k][1] + tt * dv[1], g);
+      for (int j = 0; j < 6; ++j) gtf[(k * t.nfq + f) * 6 + j] = g[j][0] * dv[0] + g[j][1] * dv[1];
+    }
+  }
+}
+
 }  // namespace ift

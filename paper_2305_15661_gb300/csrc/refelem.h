@@ -28,4 +28,10 @@ void gauss_legendre_gw(int n, std::vector<double>& x, std::vector<double>& w);
 
 bool build_tables(int dim, int p, RefTables& t);
 
+// Curved (q = 2) triangles: derivatives of the six quadratic geometry shape
+// functions N_j (vertices, then the midpoints of edges 0-1, 1-2, 2-0) at the volume
+// points of t, gdv[(q * 6 + j) * 2 + c] = dN_j/dxi_c, and along each face k at its
+// points, gtf[((k * nfq + f) * 6 + j] = dN_j/dt with xi(t) = V_k + t (V_{k+1} - V_k).
+void build_curved_tables(const RefTables& t, std::vector<double>& gdv, std::vector<double>& gtf);
+
 }  // namespace ift

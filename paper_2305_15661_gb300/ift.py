@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
     _fields_ = [("problem", ctypes.c_int), ("p", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("eps_g", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("lm_init", ctypes.c_int),
-                ("contraction", ctypes.c_int)]
+                ("contraction", ctypes.c_int), ("q", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -164,11 +164,11 @@ class Context:
 
     def __init__(self, problem: int, p: int, precision: int = FP64, gamma: float = 1.4, kappa: float = 0.0,
                  eps_g: float = 1e-8, tol: float = 1e-8, max_iters: int = 200, lm_init: int = INIT_PAPER,
-                 contraction: int = CONTRACT_FP, stream=None):
+                 contraction: int = CONTRACT_FP, stream=None, q: int = 1):
         lib = load()
         cfg = Config()
         lib.ift_config_default(ctypes.byref(cfg))
-        cfg.problem, cfg.p, cfg.precision = problem, p, precision
+        cfg.problem, cfg.p, cfg.precision, cfg.q = problem, p, precision, q
         cfg.gamma, cfg.kappa, cfg.eps_g, cfg.tol = gamma, kappa, eps_g, tol
         cfg.max_iters, cfg.lm_init, cfg.contraction = max_iters, lm_init, contraction
         h = ctypes.c_void_p()
@@ -233,6 +233,7 @@ class Context:
 
     @classmethod
     def from_workload(cls, wl, precision=FP64, **kw):
+        kw.setdefault("q", getattr(wl, "q", 1))
         ctx = cls(wl.problem, wl.p, precision=precision, gamma=wl.gamma, kappa=kw.pop("kappa", wl.kappa), **kw)
         ctx.set_mesh(wl.X, wl.ev)
         ctx.set_bases(wl.Phi, wl.Psi)
