@@ -366,7 +366,9 @@ def run_assembly(args):
     dev = torch.device("cuda", 0)
     ift.load()
     if args.config == 4:  # p = 3 on 200 x 200 x 2 triangles, k_u = 40, k_x = 8
-        wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4)
+        wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4, q=args.q, curve=0.4 if args.q == 2 else 0.0)
+    elif args.q == 2:  # the same p = 2 workload on curved six-node triangles
+        wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, q=2, curve=0.4)
     else:
         wl = make_workload()
     stream = torch.cuda.Stream(device=dev)
@@ -395,7 +397,7 @@ def run_assembly(args):
     fl = perfmodel.flops_per_element(2, wl.p, wl.ku, wl.kx)["total"]
     med = statistics.median(ms)
     print(json.dumps({"mode": "assembly", "precision": args.precision, "contraction": args.contraction,
-                      "elements": wl.n_elems, "p": wl.p,
+                      "elements": wl.n_elems, "p": wl.p, "q": wl.q,
                       "k_u": wl.ku, "k_x": wl.kx, "launch_shapes": shapes,
                       "median_ms": med, "min_ms": min(ms), "element_rj_evals_per_s": wl.n_elems / (med / 1e3),
                       "achieved_tflops": fl * wl.n_elems / (med / 1e3) / 1e12, "flops_per_element": fl}))
@@ -785,6 +787,8 @@ def main():
     ap.add_argument("--compare-fp64", action="store_true",
                     help="--mode batched: also solve the queries with FP64 assemblies and compare")
     ap.add_argument("--autotune", action="store_true", help="--mode assembly: tune the launch shape first")
+    ap.add_argument("--q", type=int, choices=[1, 2], default=1,
+                    help="--mode assembly: geometry degree (2: curved six-node triangles, the same sizes)")
     ap.add_argument("--train-solves", type=int, default=2048, help="--mode warmstart: training solves")
     ap.add_argument("--queries", type=int, default=4096, help="--mode warmstart: served queries")
     ap.add_argument("--candidates", type=int, default=256, help="--mode greedy: candidate parameters")
