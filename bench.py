@@ -53,6 +53,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself
+    when the job has one rank. device: where the collective's tensor lives (a CUDA
+    device for NCCL, "cpu" for gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling: every
+    rank processes the same number of independent units)."""
+    return world * units_per_rank / max_seconds
+
+
 def make_workload():
     from paper_2305_15661_gb300 import workloads as W
 
@@ -232,12 +252,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
+    value = whole_job_rate(args.steps, world, total_s)
 
     # end to end through the host API: host mu in, y, z and info out
     e2e_steps = max(3, args.steps)
