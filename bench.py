@@ -781,6 +781,47 @@ def run_greedy(args):
     return 0
 
 
+def run_align(args):
+    """Snapshot alignment (Eq. align0) on the 20,000-element p = 2 mesh: a fixed
+    number of full-space Levenberg-Marquardt steps on (w, interior mesh nodes) from
+    the reference mesh, every element weighted 1. Each conjugate-gradient
+    iteration applies J v and J^T v element by element; the line uses wall time
+    per alignment through the public call (host buffers in and out)."""
+    from paper_2305_15661_gb300 import ift, perfmodel
+    from paper_2305_15661_gb300 import workloads as W
+
+    ift.load()
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = wl.mus[0]
+    inner = np.all((wl.X > 1e-12) & (wl.X < 1 - 1e-12), axis=1)
+    mask = np.repeat(inner, 2)
+    x0 = wl.X.ravel()
+    iters = args.align_iters
+    for _ in range(args.warmup):
+        ctx.align(mu, wl.w_eval, x0, mask, tol=0.0, max_iters=iters)
+    ts, infos = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = ctx.align(mu, wl.w_eval, x0, mask, tol=0.0, max_iters=iters)
+        ts.append(time.perf_counter() - t0)
+        infos.append(r)
+    t = statistics.median(ts)
+    r = infos[-1]
+    # element passes: the residual and J^T F at the start, one J v and one J^T v
+    # per CG iteration, one residual per line-search trial, one J^T F per accepted step
+    fl = perfmodel.flops_per_element(2, 2, 1, 0, jac=False)["total"]
+    passes = 2 + 2 * r["cg_iters"] + r["trials"] + r["iters"]
+    print(json.dumps({"mode": "align", "elements": wl.n_elems, "p": 2, "k_u": wl.ku,
+                      "free_coordinates": int(mask.sum()), "lm_steps": r["iters"], "cg_iters": r["cg_iters"],
+                      "trials": r["trials"], "s_per_alignment": t, "ms_per_cg_iter": 1e3 * t / max(r["cg_iters"], 1),
+                      "element_passes": passes, "element_evals_per_s": passes * wl.n_elems / t,
+                      "J": r["J"], "gnorm_over_g0": r["gnorm"] / r["g0"], "status": r["status"],
+                      "residual_flops_per_element": fl}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -788,7 +829,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers", "precisions"],
+    ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers", "precisions",
+                                           "align"],
                     default="solve",
                     help="assembly: only time isolated fused assemblies (for profiler captures)")
     ap.add_argument("--precision", choices=["fp64", "fp32", "mixed", "fp32jac"], default="fp64",
@@ -810,6 +852,7 @@ def main():
     ap.add_argument("--candidates", type=int, default=256, help="--mode greedy: candidate parameters")
     ap.add_argument("--epochs", type=int, default=1500, help="--mode warmstart: training epochs")
     ap.add_argument("--single-sample", type=int, default=32, help="--mode warmstart: one-query FP64 solves timed")
+    ap.add_argument("--align-iters", type=int, default=5, help="--mode align: Levenberg-Marquardt steps per alignment")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -827,6 +870,8 @@ def main():
         return run_burgers(args)
     if args.mode == "precisions":
         return run_precisions(args)
+    if args.mode == "align":
+        return run_align(args)
     return run_ours(args)
 
 

@@ -355,6 +355,46 @@ ift_status ift_mlp_predict(ift_mlp* net, int64_t count, const double* x, double*
 ift_status ift_nearest_start(int64_t n_train, int n_in, const double* x_train, int n_out, const double* y_train,
                              int64_t n_query, const double* x_query, const double* scale, double* y_out);
 
+/* ------------------------------------------------------------------------
+   Snapshot alignment (Eq. align0): the full-space problem
+     min over (w, x) of (1/2) |F(Phi w, x; mu)|^2,  F = [R(Phi w, x; mu); N(x)],
+   every element with weight 1, the free mesh coordinates x (all nodes, N_x =
+   n_verts x dim values, the coordinate entries whose free_mask byte is non-zero)
+   and w (k_u) unknown. Needs set_mesh and set_bases (Psi is not used: the mesh
+   moves freely); FP64 in every precision.
+   ------------------------------------------------------------------------ */
+typedef struct {
+  int status;    /* IFT_OK, IFT_NOT_CONVERGED (max_iters), IFT_LINESEARCH_FAILED */
+  int iters;     /* accepted Levenberg-Marquardt steps */
+  int cg_iters;  /* conjugate-gradient iterations over all steps (one J v and one J^T v each) */
+  int trials;    /* objective evaluations in line searches */
+  double J;      /* final (1/2)|F|^2 */
+  double gnorm;  /* final |J^T F| over the unknowns */
+  double g0;     /* |J^T F| at the start */
+} ift_align_info;
+
+/* F = [R (N_u); N (n_elems)] at (w, x) (host pointers; x: N_x reference-layout
+   coordinates of the current mesh; the distortion compares with the mesh of
+   ift_set_mesh). */
+ift_status ift_align_residual(ift_ctx* ctx, const double* mu, const double* w, const double* x, double* F);
+
+/* dF = J (dU, dx) = [dR/dU dU + dR/dx dx; dN/dx dx] at (w, x): dU (N_u), dx (N_x). */
+ift_status ift_align_jvp(ift_ctx* ctx, const double* mu, const double* w, const double* x, const double* dU,
+                         const double* dx, double* dF);
+
+/* (gU, gx) = J^T v: gU = (dR/dU)^T v_R (N_u), gx = (dR/dx)^T v_R + (dN/dx)^T v_N (N_x),
+   v = [v_R (N_u); v_N (n_elems)]. */
+ift_status ift_align_vjp(ift_ctx* ctx, const double* mu, const double* w, const double* x, const double* v,
+                         double* gU, double* gx);
+
+/* Levenberg-Marquardt on (w, free x) from the given (w, x) (both in/out): each step
+   solves (J^T J + lambda D) d = -J^T F (D = 1 on the mesh coordinates, 0 on w) by
+   conjugate gradients with J v and J^T v applied element by element, then a
+   backtracking line search on (1/2)|F|^2; lambda rules as ift_solve_rom. Stops
+   when |J^T F| <= tol max(1, |J^T F| at the start). Returns info->status. */
+ift_status ift_align(ift_ctx* ctx, const double* mu, double* w, double* x, const uint8_t* free_mask, double tol,
+                     int max_iters, ift_align_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -295,6 +295,73 @@ class Oracle:
         vals = np.concatenate(vals)
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.Nu, self.Nu))
 
+    # -- snapshot alignment (Eq. align0) --------------------------------------
+    def align(self, Phi, mu, w0, x0, free_mask, tol=1e-8, max_iters=100):
+        """min over (w, x_free) of (1/2)|F|^2, F = [R(Phi w, x; mu); N(x)], every element
+        weight 1, by Levenberg-Marquardt on the dense global Jacobians (small meshes
+        only). The step solves (J^T J + lambda D) d = -J^T F exactly (D = 1 on the mesh
+        coordinates, 0 on w), with the damping and line-search rules of the reduced
+        solve (lambda_0 = 1e-4, /10 after a full step, x10 after a shortened one,
+        Armijo 1e-4 with 16 ulp of |J|, at most 30 halvings); stops when
+        |J^T F| <= tol max(1, |J^T F| at the start)."""
+        Phi = np.asarray(Phi, dtype=np.float64)
+        free = np.nonzero(np.asarray(free_mask).ravel())[0]
+        w = np.array(w0, dtype=np.float64)
+        x = np.array(x0, dtype=np.float64).ravel()
+        ku, nf = Phi.shape[1], len(free)
+
+        def F_of(w, x):
+            R, N, bad = self.residual(Phi @ w, x, mu)
+            return np.concatenate([R, N]), bad
+
+        def jac(w, x):
+            dRdU, dRdx, dNdx = self.jacobian_dense(Phi @ w, x, mu)
+            top = np.concatenate([dRdU @ Phi, dRdx[:, free]], axis=1)
+            bot = np.concatenate([np.zeros((self.n_elems, ku)), dNdx[:, free]], axis=1)
+            return np.concatenate([top, bot], axis=0)
+
+        F, bad = F_of(w, x)
+        J = 0.5 * F @ F
+        Jm = jac(w, x)
+        g = Jm.T @ F
+        g0 = np.linalg.norm(g)
+        thresh = tol * max(1.0, g0)
+        lam, iters, trials, status = 1e-4, 0, 0, 1
+        D = np.concatenate([np.zeros(ku), np.ones(nf)])
+        while True:
+            if np.linalg.norm(g) <= thresh:
+                status = 0
+                break
+            if iters >= max_iters:
+                break
+            d = np.linalg.solve(Jm.T @ Jm + lam * np.diag(D), -g)
+            slope = g @ d
+            alpha, h, accepted = 1.0, 0, False
+            while True:
+                wt = w + alpha * d[:ku]
+                xt = x.copy()
+                xt[free] += alpha * d[ku:]
+                Ft, bad = F_of(wt, xt)
+                Jt = 0.5 * Ft @ Ft
+                trials += 1
+                if bad == 0 and np.isfinite(Jt) and Jt <= J + 1e-4 * alpha * slope + 16 * 2.220446049250313e-16 * abs(J):
+                    accepted = True
+                    break
+                h += 1
+                if h > 30:
+                    break
+                alpha *= 0.5
+            if not accepted:
+                status = 2
+                break
+            lam = max(lam / 10, 1e-12) if h == 0 else min(lam * 10, 1e8)
+            w, x, F, J = wt, xt, Ft, Jt
+            iters += 1
+            Jm = jac(w, x)
+            g = Jm.T @ F
+        return {"status": status, "w": w, "x": x, "J": J, "gnorm": float(np.linalg.norm(g)), "g0": float(g0),
+                "iters": iters, "trials": trials}
+
     # -- reduced level -----------------------------------------------------
     @staticmethod
     def _rho_args(rho_set):

@@ -44,6 +44,15 @@ __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, dou
 __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 __global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states);
+__global__ void phi_matvec_kernel(const double* Phi, long Nu, int ku, const double* v, double* out);
+__global__ void phit_vec_partial_kernel(const double* Phi, long Nu, int ku, const double* g, long chunk,
+                                        double* part);
+__global__ void dot_partial_kernel(const double* a, const double* b, long n, double* part);
+__global__ void axpy_kernel(long n, double alpha, const double* x, double* y);
+__global__ void xpby_kernel(long n, const double* x, double beta, double* y);
+__global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x);
+__global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
+                                   double* out);
 }  // namespace ift
 
 using namespace ift;
@@ -254,6 +263,7 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
   a.partial = c->d_partial;
   a.skip = skip;
   a.contraction = c->cfg.contraction;
+  a.need_hn = 0;
   return a;
 }
 
@@ -1836,4 +1846,312 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
   c->err.clear();
   c->epoch++;
   return IFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Snapshot alignment (Eq. align0): min over (w, x) of (1/2)|F(Phi w, x; mu)|^2,
+// F = [R; N] over every element (rho = 1), with the free mesh coordinates x
+// unknowns. Levenberg-Marquardt on the full space, each normal-equation solve by
+// conjugate gradients with J v and J^T v applied element by element
+// (align_kernel), never forming J.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kDotBlocks = 120;
+
+struct AlignWork {
+  long Nu = 0, Ne = 0, Nx = 0;
+  int ku = 0, nfree = 0;
+  double *w = nullptr, *x = nullptr, *F = nullptr, *dU = nullptr, *dx = nullptr, *dF = nullptr, *gU = nullptr,
+         *gx = nullptr, *wt = nullptr, *xt = nullptr, *Ft = nullptr, *part = nullptr, *nbad = nullptr;
+  double *g = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;  // unknowns' space
+  int* free_idx = nullptr;
+  ~AlignWork() {
+    for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap})
+      dfree(*q);
+    dfree(free_idx);
+  }
+  cudaError_t alloc() {
+    const long n = ku + nfree;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](double*& q, long m) {
+      if (e == cudaSuccess) e = dalloc(q, (size_t)(m > 0 ? m : 1));
+    };
+    A(w, LM_KMAX);
+    A(wt, LM_KMAX);
+    A(x, Nx);
+    A(xt, Nx);
+    A(F, Nu + Ne);
+    A(Ft, Nu + Ne);
+    A(dF, Nu + Ne);
+    A(dU, Nu);
+    A(gU, Nu);
+    A(dx, Nx);
+    A(gx, Nx);
+    A(part, kDotBlocks);
+    A(nbad, 1);
+    A(g, n);
+    A(d, n);
+    A(r, n);
+    A(p, n);
+    A(Ap, n);
+    if (e == cudaSuccess) e = dalloc(free_idx, (size_t)(nfree > 0 ? nfree : 1));
+    return e;
+  }
+};
+
+// Sum of the block partials in block order (deterministic for a fixed grid).
+double align_dot(const AlignWork& W, const double* a, const double* b, long n, cudaStream_t s) {
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(a, b, n, W.part);
+  double h[kDotBlocks];
+  cudaMemcpyAsync(h, W.part, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  double t = 0.0;
+  for (int i = 0; i < kDotBlocks; ++i) t += h[i];
+  return t;
+}
+
+int vec_grid(long n) {
+  long g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
+}
+
+// One element pass of align_kernel in FP64 at (w, x): mode 0 F, 1 J v, 2 J^T v.
+ift_status align_pass(ift_ctx* c, int mode, const double* w, const double* x, const double* vU, const double* vx,
+                      const double* vN, double* outU, double* outX, cudaStream_t s) {
+  const KernelSet& ks = c->ks[0];
+  if (!ks.align) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
+  AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, c->d_tau, c->d_mu, true, nullptr);
+  a.X = x;  // the current mesh in place of the reference nodes, no mesh basis
+  a.kx = 0;
+  a.Psi = nullptr;
+  a.need_hn = 1;
+  const int warps = 2, block = 32 * warps;
+  const size_t smem = ks.smem_bytes(true, c->ku, 0, warps);
+  if (smem > (size_t)c->smem_optin) return c->fail(IFT_ERR_ARG, "alignment pass needs too much shared memory");
+  long grid = (c->n_elems + warps - 1) / warps;
+  if (grid > (long)c->sm_count * 8) grid = (long)c->sm_count * 8;
+  cudaError_t e = ks.align(mode, &a, c->d_X, vU, vx, vN, outU, outX, (int)grid, block, smem, s);
+  if (e != cudaSuccess) return c->cuda_fail(e, "alignment pass");
+  return IFT_OK;
+}
+
+// out = J^T f in the unknowns' space (w rows: Phi^T (dR/dU)^T f_R; free rows: the
+// free coordinates of (dR/dx)^T f_R + (dN/dx)^T f_N), plus lam v on the free rows.
+ift_status align_grad(ift_ctx* c, AlignWork& W, const double* w, const double* x, const double* f, const double* v,
+                      double lam, double* out, cudaStream_t s) {
+  CK(cudaMemsetAsync(W.gU, 0, W.Nu * 8, s), "zero gU");
+  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
+  ift_status st = align_pass(c, 2, w, x, f, nullptr, f + W.Nu, W.gU, W.gx, s);
+  if (st != IFT_OK) return st;
+  const long chunk = (W.Nu + kPhitBlocks - 1) / kPhitBlocks;
+  int block = 256;
+  if (block < W.ku) block = W.ku;
+  phit_vec_partial_kernel<<<kPhitBlocks, block, block * sizeof(double), s>>>(c->d_Phi, W.Nu, W.ku, W.gU, chunk,
+                                                                             c->d_phit);
+  sum_columns_kernel<<<1, 64, 0, s>>>(c->d_phit, kPhitBlocks, W.ku, out);
+  if (W.nfree > 0)
+    gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, v ? v + W.ku : nullptr, lam,
+                                                         out + W.ku);
+  CK(cudaGetLastError(), "alignment gradient");
+  return IFT_OK;
+}
+
+// out = (J^T J + lam D) v, D = diag(0 on w, 1 on the free coordinates)
+ift_status align_normal(ift_ctx* c, AlignWork& W, const double* v, double lam, double* out, cudaStream_t s) {
+  phi_matvec_kernel<<<vec_grid(W.Nu), 256, 0, s>>>(c->d_Phi, W.Nu, W.ku, v, W.dU);
+  CK(cudaMemsetAsync(W.dx, 0, W.Nx * 8, s), "zero dx");
+  if (W.nfree > 0) scatter_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, v + W.ku, W.dx);
+  ift_status st = align_pass(c, 1, W.w, W.x, W.dU, W.dx, nullptr, W.dF, nullptr, s);
+  if (st != IFT_OK) return st;
+  return align_grad(c, W, W.w, W.x, W.dF, v, lam, out, s);
+}
+
+ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double* w, const double* x) {
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!mu || !w || !x) return c->fail(IFT_ERR_ARG, "null input pointer");
+  W.Nu = c->n_elems * (long)c->nu;
+  W.Ne = c->n_elems;
+  W.Nx = c->n_verts * (long)c->dim;
+  W.ku = c->ku;
+  CK(W.alloc(), "alignment buffers");
+  const int nmu = (c->dim == 1) ? 1 : 2;
+  CK(cudaMemcpy(c->d_mu, mu, nmu * 8, cudaMemcpyHostToDevice), "copy mu");
+  CK(cudaMemcpy(W.w, w, W.ku * 8, cudaMemcpyHostToDevice), "copy w");
+  CK(cudaMemcpy(W.x, x, W.Nx * 8, cudaMemcpyHostToDevice), "copy x");
+  return IFT_OK;
+}
+
+}  // namespace
+
+extern "C" ift_status ift_align_residual(ift_ctx* c, const double* mu, const double* w, const double* x, double* F) {
+  AlignWork W;
+  ift_status st = align_setup(c, W, mu, w, x);
+  if (st != IFT_OK) return st;
+  if (!F) return c->fail(IFT_ERR_ARG, "null output pointer");
+  cudaStream_t s = c->stream;
+  st = align_pass(c, 0, W.w, W.x, nullptr, nullptr, nullptr, W.F, nullptr, s);
+  if (st != IFT_OK) return st;
+  CK(cudaMemcpyAsync(F, W.F, (W.Nu + W.Ne) * 8, cudaMemcpyDeviceToHost, s), "copy F");
+  CK(cudaStreamSynchronize(s), "alignment residual");
+  return IFT_OK;
+}
+
+extern "C" ift_status ift_align_jvp(ift_ctx* c, const double* mu, const double* w, const double* x, const double* dU,
+                                    const double* dx, double* dF) {
+  AlignWork W;
+  ift_status st = align_setup(c, W, mu, w, x);
+  if (st != IFT_OK) return st;
+  if (!dU || !dx || !dF) return c->fail(IFT_ERR_ARG, "null pointer");
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(W.dU, dU, W.Nu * 8, cudaMemcpyHostToDevice, s), "copy dU");
+  CK(cudaMemcpyAsync(W.dx, dx, W.Nx * 8, cudaMemcpyHostToDevice, s), "copy dx");
+  st = align_pass(c, 1, W.w, W.x, W.dU, W.dx, nullptr, W.dF, nullptr, s);
+  if (st != IFT_OK) return st;
+  CK(cudaMemcpyAsync(dF, W.dF, (W.Nu + W.Ne) * 8, cudaMemcpyDeviceToHost, s), "copy dF");
+  CK(cudaStreamSynchronize(s), "alignment J v");
+  return IFT_OK;
+}
+
+extern "C" ift_status ift_align_vjp(ift_ctx* c, const double* mu, const double* w, const double* x, const double* v,
+                                    double* gU, double* gx) {
+  AlignWork W;
+  ift_status st = align_setup(c, W, mu, w, x);
+  if (st != IFT_OK) return st;
+  if (!v || !gU || !gx) return c->fail(IFT_ERR_ARG, "null pointer");
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(W.dF, v, (W.Nu + W.Ne) * 8, cudaMemcpyHostToDevice, s), "copy v");
+  CK(cudaMemsetAsync(W.gU, 0, W.Nu * 8, s), "zero gU");
+  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
+  st = align_pass(c, 2, W.w, W.x, W.dF, nullptr, W.dF + W.Nu, W.gU, W.gx, s);
+  if (st != IFT_OK) return st;
+  CK(cudaMemcpyAsync(gU, W.gU, W.Nu * 8, cudaMemcpyDeviceToHost, s), "copy gU");
+  CK(cudaMemcpyAsync(gx, W.gx, W.Nx * 8, cudaMemcpyDeviceToHost, s), "copy gx");
+  CK(cudaStreamSynchronize(s), "alignment J^T v");
+  return IFT_OK;
+}
+
+extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double* x, const uint8_t* free_mask,
+                                double tol, int max_iters, ift_align_info* info) {
+  NvtxRange nvtx_range("ift_align");
+  AlignWork W;
+  if (!free_mask && c) return c->fail(IFT_ERR_ARG, "null free-coordinate mask");
+  if (c && c->have_mesh) {
+    for (long i = 0; i < c->n_verts * (long)c->dim; ++i) W.nfree += free_mask[i] ? 1 : 0;
+  }
+  ift_status st = align_setup(c, W, mu, w, x);
+  if (st != IFT_OK) return st;
+  if (!(tol >= 0.0) || max_iters < 0) return c->fail(IFT_ERR_ARG, "tol >= 0 and max_iters >= 0 required");
+  {
+    std::vector<int> idx;
+    for (long i = 0; i < W.Nx; ++i)
+      if (free_mask[i]) idx.push_back((int)i);
+    if (!idx.empty()) CK(cudaMemcpy(W.free_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice), "copy idx");
+  }
+  cudaStream_t s = c->stream;
+  const long n = W.ku + W.nfree, nF = W.Nu + W.Ne;
+  // readings of Sec. 3.2.3 as for the reduced solve: lambda_0 = 1e-4, /10 after a
+  // full step, x10 after a shortened one, Armijo 1e-4, at most 30 halvings; damping
+  // on the mesh block only (Eq. levmarq-step)
+  const double c1 = 1e-4, round_tol = 16.0 * 2.220446049250313e-16;
+  double lam = 1e-4;
+  // (1/2)|F|^2 at (ww, xx); +inf where an element is non-physical (such a trial is
+  // rejected, as in the reduced solve)
+  auto objective = [&](const double* ww, const double* xx, double* FF, double& Jv) -> ift_status {
+    CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
+    ift_status q = align_pass(c, 0, ww, xx, nullptr, nullptr, nullptr, FF, W.nbad, s);
+    if (q != IFT_OK) return q;
+    Jv = 0.5 * align_dot(W, FF, FF, nF, s);
+    double nb = 0.0;
+    CK(cudaMemcpy(&nb, W.nbad, 8, cudaMemcpyDeviceToHost), "read count");
+    if (nb > 0.0) Jv = INFINITY;
+    return IFT_OK;
+  };
+  double J = 0.0;
+  st = objective(W.w, W.x, W.F, J);
+  if (st != IFT_OK) return st;
+  if (!std::isfinite(J)) return c->fail(IFT_ERR_NONPHYSICAL, "the starting point is not physical");
+  st = align_grad(c, W, W.w, W.x, W.F, nullptr, 0.0, W.g, s);
+  if (st != IFT_OK) return st;
+  double gnorm = std::sqrt(align_dot(W, W.g, W.g, n, s));
+  const double g0 = gnorm, thresh = tol * std::max(1.0, g0);
+  int status = IFT_NOT_CONVERGED, iters = 0, cg_total = 0, trials = 0;
+  const int max_cg = (int)std::min<long>(4 * n + 20, 2000);
+  for (;;) {
+    if (gnorm <= thresh) {
+      status = IFT_OK;
+      break;
+    }
+    if (iters >= max_iters) break;
+    // CG on (J^T J + lam D) d = -g, from d = 0
+    CK(cudaMemsetAsync(W.d, 0, n * 8, s), "zero d");
+    CK(cudaMemcpyAsync(W.r, W.g, n * 8, cudaMemcpyDeviceToDevice, s), "r = g");
+    axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, -2.0, W.g, W.r);  // r = -g
+    CK(cudaMemcpyAsync(W.p, W.r, n * 8, cudaMemcpyDeviceToDevice, s), "p = r");
+    double rr = align_dot(W, W.r, W.r, n, s);
+    const double rr0 = rr;
+    for (int k = 0; k < max_cg; ++k) {
+      st = align_normal(c, W, W.p, lam, W.Ap, s);
+      if (st != IFT_OK) return st;
+      const double pAp = align_dot(W, W.p, W.Ap, n, s);
+      ++cg_total;
+      if (!(pAp > 0.0)) break;
+      const double alpha = rr / pAp;
+      axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, alpha, W.p, W.d);
+      axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, -alpha, W.Ap, W.r);
+      const double rr1 = align_dot(W, W.r, W.r, n, s);
+      if (std::sqrt(rr1) <= 1e-12 * std::sqrt(rr0)) break;
+      xpby_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.r, rr1 / rr, W.p);
+      rr = rr1;
+    }
+    const double slope = align_dot(W, W.g, W.d, n, s);
+    // backtracking line search on (1/2)|F|^2
+    double alpha = 1.0, Jt = 0.0;
+    int h = 0;
+    bool accepted = false;
+    for (;;) {
+      CK(cudaMemcpyAsync(W.wt, W.w, W.ku * 8, cudaMemcpyDeviceToDevice, s), "wt = w");
+      axpy_kernel<<<1, 64, 0, s>>>(W.ku, alpha, W.d, W.wt);
+      CK(cudaMemsetAsync(W.dx, 0, W.Nx * 8, s), "zero dx");
+      if (W.nfree > 0) scatter_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.d + W.ku, W.dx);
+      CK(cudaMemcpyAsync(W.xt, W.x, W.Nx * 8, cudaMemcpyDeviceToDevice, s), "xt = x");
+      axpy_kernel<<<vec_grid(W.Nx), 256, 0, s>>>(W.Nx, alpha, W.dx, W.xt);
+      st = objective(W.wt, W.xt, W.Ft, Jt);
+      if (st != IFT_OK) return st;
+      ++trials;
+      if (std::isfinite(Jt) && Jt <= J + c1 * alpha * slope + round_tol * std::fabs(J)) {
+        accepted = true;
+        break;
+      }
+      if (++h > 30) break;
+      alpha *= 0.5;
+    }
+    if (!accepted) {
+      status = IFT_LINESEARCH_FAILED;
+      break;
+    }
+    lam = (h == 0) ? std::max(lam / 10.0, 1e-12) : std::min(lam * 10.0, 1e8);
+    std::swap(W.w, W.wt);
+    std::swap(W.x, W.xt);
+    std::swap(W.F, W.Ft);
+    J = Jt;
+    ++iters;
+    st = align_grad(c, W, W.w, W.x, W.F, nullptr, 0.0, W.g, s);
+    if (st != IFT_OK) return st;
+    gnorm = std::sqrt(align_dot(W, W.g, W.g, n, s));
+  }
+  CK(cudaMemcpyAsync(w, W.w, W.ku * 8, cudaMemcpyDeviceToHost, s), "copy w");
+  CK(cudaMemcpyAsync(x, W.x, W.Nx * 8, cudaMemcpyDeviceToHost, s), "copy x");
+  CK(cudaStreamSynchronize(s), "alignment");
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->cg_iters = cg_total;
+    info->trials = trials;
+    info->J = J;
+    info->gnorm = gnorm;
+    info->g0 = g0;
+  }
+  return (ift_status)status;
 }

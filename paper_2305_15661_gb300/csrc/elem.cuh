@@ -111,6 +111,9 @@ struct AsmArgs {
   // 2: 3xTF32 tensor cores, i.e. hi/lo splits of each operand, about FP32 accuracy,
   // 3: BF16 tensor cores)
   int contraction;
+  // form dH/dn at face points even without mesh columns (the snapshot alignment
+  // applies dR/dx to full mesh directions)
+  int need_hn;
 };
 
 // H += rho A^T A on the tensor cores (warp-level mma.m16n8k8, TF32 inputs, FP32
@@ -1525,7 +1528,7 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
   const int ku = a.ku, kx = a.kx;
-  const bool need_hn = JAC && kx > 0 && face_jac;
+  const bool need_hn = JAC && (kx > 0 || a.need_hn) && face_jac;
     const int* vv = &a.ev[(long)e * NV];
     // 1. gather: Phi_e and Psi_e by asynchronous copies (all in flight at once),
     // overlapped with the neighbour offsets
@@ -2188,6 +2191,112 @@ __global__ void __launch_bounds__(128) inspect_kernel(AsmArgs<T> a, const double
     for (int i = lane; i < NU; i += 32) Rout[(size_t)it * NU + i] = (double)C.R[i];
     if (lane < NXE) dNout[(size_t)it * NXE + lane] = C.dN[lane];
     if (lane == 0) Nout[it] = C.dN[NXE];
+    __syncwarp();
+  }
+}
+
+// Snapshot alignment (Eq. align0): the full-space objective (1/2)|F|^2 with
+// F = [R(Phi w, x; mu); N(x)] over the state coefficients w and every mesh node x.
+// The element pass runs at (w, x) with x in place of the reference nodes (no mesh
+// basis), and per element, one warp:
+//   MODE 0: F_e = (R_e, N_e) into F (R rows e n_u.., N at n_elems n_u + e), and the
+//           number of non-physical elements added to outX[0];
+//   MODE 1: J v for v = (dU = Phi dw, dx): dF_e = dR_e/dU_e dU_e + dR_e/dU_e' dU_e'
+//           + dR_e/dx_e dx_e, dN_e . dx_e (one lane per product);
+//   MODE 2: J^T v: (dR_e/dU_e)^T v_e added to gU's rows of e, (dR_e/dU_e')^T v_e to
+//           the neighbours' trace rows, (dR_e/dx_e)^T v_e + dN_e v_N,e to gx's nodes
+//           (atomic adds: neighbouring elements share rows and nodes).
+// Xref: the reference nodes of the distortion N_e = kappa (eta(x_e) - eta(X_e)).
+template <class T, int PROB, int P, int MODE>
+__global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* Xref, const double* vU,
+                                                    const double* vx, const double* vN, double* outU,
+                                                    double* outX) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, true>;
+  constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
+                NT = Dd::NTRACE, NV = Dd::NV;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku;
+  T *tab, *wT;
+  double* tauD;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(a.ku, a.kx);
+  const size_t wb = WarpLayout<T, PROB, P, true>(a.ku, a.kx).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, a.ku, a.kx);
+  bind_tables(C, tab);
+  __syncthreads();
+  const long Nu = (long)a.n_items * NU;
+  for (long e = (long)blockIdx.x * nw + warp; e < a.n_items; e += (long)gridDim.x * nw) {
+    const int* vv = &a.ev[e * NV];
+    signed char bcs[NF];
+    const bool bad = element_front<T, PROB, P, true>(C, a, (int)e, wT, tauD, a.mu, lane, bcs);
+    if (lane == 0) {
+      double Xe[NXE];
+      for (int r = 0; r < NXE; ++r) Xe[r] = Xref[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+      C.distortion_any(Xe, a.kappa, a.eps);  // dN[0..NXE-1], N_e = dN[NXE] (kappa = 0: zero)
+    }
+    __syncwarp();
+    if constexpr (MODE == 0) {
+      for (int i = lane; i < NU; i += 32) outU[e * NU + i] = (double)C.R[i];
+      if (lane == 0) {
+        outU[Nu + e] = C.dN[NXE];
+        if (bad && outX) atomicAdd(outX, 1.0);
+      }
+    } else if constexpr (MODE == 1) {
+      // lane 0: the state product, lane 1: the mesh product; summed through W
+      T* part = C.W;
+      if (lane < 2) {
+        T dR[NU];
+        if (lane == 0) {
+          auto fe = [&](int i) { return (T)vU[e * NU + i]; };
+          auto fp = [&](int i) {
+            const int kj = i / M, b = i - kj * M;
+            const long long off = C.poff[kj];
+            return off >= 0 ? (T)vU[off / ku + b] : T(0);
+          };
+          C.jvp_state(fe, fp, bcs, dR);
+        } else {
+          double dx[NXE];
+          for (int r = 0; r < NXE; ++r) dx[r] = vx[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+          C.jvp_geom(dx, a.mu, dR);
+        }
+#pragma unroll
+        for (int i = 0; i < NU; ++i) part[lane * NU + i] = dR[i];
+      }
+      __syncwarp();
+      for (int i = lane; i < NU; i += 32) outU[e * NU + i] = (double)(part[i] + part[NU + i]);
+      if (lane == 0) {
+        double s = 0.0;
+        for (int r = 0; r < NXE; ++r) s += C.dN[r] * vx[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+        outU[Nu + e] = s;
+      }
+    } else {
+      // the transposed element Jacobian applied to v_e (v_e replaces R_e)
+      for (int i = lane; i < NU; i += 32) C.R[i] = (T)vU[e * NU + i];
+      __syncwarp();
+      // mesh coordinates first (jvp_geom per unit direction; it reads pointwise data only)
+      for (int r = lane; r < NXE; r += 32) {
+        double dx[NXE];
+        for (int t = 0; t < NXE; ++t) dx[t] = (t == r) ? 1.0 : 0.0;
+        T dR[NU];
+        C.jvp_geom(dx, a.mu, dR);
+        double s = C.dN[r] * vN[e];
+#pragma unroll
+        for (int i = 0; i < NU; ++i) s += (double)dR[i] * (double)C.R[i];
+        atomicAdd(&outX[(size_t)vv[r / DIM] * DIM + (r % DIM)], s);
+      }
+      __syncwarp();
+      T *dUe, *dUp;
+      C.adj_state(lane, bcs, dUe, dUp);
+      for (int i = lane; i < NU; i += 32) atomicAdd(&outU[e * NU + i], (double)dUe[i]);
+      for (int i = lane; i < NUP; i += 32) {
+        const int kj = i / M, b = i - kj * M;
+        const long long off = C.poff[kj];
+        if (off >= 0) atomicAdd(&outU[off / ku + b], (double)dUp[i]);
+      }
+    }
     __syncwarp();
   }
 }

@@ -142,6 +142,24 @@ struct KernelSetImpl {
                                                                 block, smem);
     return e == cudaSuccess ? n : 0;
   }
+  template <int MODE>
+  static cudaError_t align_mode(const AsmArgs<T>& a, const double* Xref, const double* vU, const double* vx,
+                                const double* vN, double* outU, double* outX, int grid, int block, size_t smem,
+                                cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(align_kernel<T, PROB, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    align_kernel<T, PROB, P, MODE><<<grid, block, smem, s>>>(a, Xref, vU, vx, vN, outU, outX);
+    return cudaGetLastError();
+  }
+  static cudaError_t align(int mode, const void* args, const double* Xref, const double* vU, const double* vx,
+                           const double* vN, double* outU, double* outX, int grid, int block, size_t smem,
+                           cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    if (mode == 0) return align_mode<0>(a, Xref, vU, vx, vN, outU, outX, grid, block, smem, s);
+    if (mode == 1) return align_mode<1>(a, Xref, vU, vx, vN, outU, outX, grid, block, smem, s);
+    return align_mode<2>(a, Xref, vU, vx, vN, outU, outX, grid, block, smem, s);
+  }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
@@ -178,6 +196,7 @@ struct KernelSetImpl {
       k.assemble_grad = &assemble_grad;
       k.assemble_batched_grad = &assemble_batched_grad;
       k.smem_bytes_grad = &smem_bytes_grad;
+      k.align = &align;
       k.blocks_per_sm_grad = &blocks_per_sm_grad;
     }
     k.blocks_per_sm_norms = &blocks_per_sm_norms;

@@ -31,6 +31,11 @@ struct KernelSet {
   cudaError_t (*assemble_batched_grad)(const void* args, const void* bargs, int grid, int block, size_t smem,
                                        cudaStream_t s) = nullptr;
   size_t (*smem_bytes_grad)(int ku, int kx, int warps) = nullptr;
+  // FP64 sets: the snapshot-alignment element pass (mode 0 residual, 1 J v, 2 J^T v;
+  // see align_kernel), shared memory as the fused kernel's with kx = 0
+  cudaError_t (*align)(int mode, const void* args, const double* Xref, const double* vU, const double* vx,
+                       const double* vN, double* outU, double* outX, int grid, int block, size_t smem,
+                       cudaStream_t s) = nullptr;
   int (*blocks_per_sm_grad)(bool batched, int block, size_t smem) = nullptr;
   // per-element [S^(e); T^(e); J^(e)] rows; args as for assemble
   cudaError_t (*element_gradients)(const void* args, double* out, int grid, int block, size_t smem,

@@ -515,4 +515,78 @@ __global__ void sum_columns_kernel(const double* part, int nparts, int ku, doubl
   w[c] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Vector kernels of the snapshot alignment's conjugate-gradient solve.
+// ---------------------------------------------------------------------------
+
+// out[i] = sum_c Phi[i][c] v[c] (Phi row-major N_u x ku)
+__global__ void phi_matvec_kernel(const double* Phi, long Nu, int ku, const double* v, double* out) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < Nu; i += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < ku; ++c) s += Phi[i * ku + c] * v[c];
+    out[i] = s;
+  }
+}
+
+// Block b: partial column sums of Phi^T g over rows [b chunk, (b + 1) chunk) into
+// part[b][c] (summed in block order by sum_columns_kernel).
+__global__ void phit_vec_partial_kernel(const double* Phi, long Nu, int ku, const double* g, long chunk,
+                                        double* part) {
+  extern __shared__ double sh[];
+  const long r0 = (long)blockIdx.x * chunk;
+  const long r1 = (r0 + chunk < Nu) ? r0 + chunk : Nu;
+  const int lanes_per_col = blockDim.x / ku;
+  const int c = threadIdx.x % ku, sub = threadIdx.x / ku;
+  double s = 0.0;
+  if (sub < lanes_per_col)
+    for (long r = r0 + sub; r < r1; r += lanes_per_col) s += Phi[r * ku + c] * g[r];
+  sh[threadIdx.x] = (sub < lanes_per_col) ? s : 0.0;
+  __syncthreads();
+  if (threadIdx.x < ku) {
+    double t = 0.0;
+    for (int j = 0; j < lanes_per_col; ++j) t += sh[j * ku + threadIdx.x];
+    part[(size_t)blockIdx.x * ku + threadIdx.x] = t;
+  }
+}
+
+// Block b: the partial dot product of a and b over its grid-stride share, into part[b]
+// (summed on the host in block order).
+__global__ void dot_partial_kernel(const double* a, const double* b, long n, double* part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// y = y + alpha x
+__global__ void axpy_kernel(long n, double alpha, const double* x, double* y) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] += alpha * x[i];
+}
+
+// y = x + beta y
+__global__ void xpby_kernel(long n, const double* x, double beta, double* y) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = x[i] + beta * y[i];
+}
+
+// x[idx[j]] = v[j] (the free mesh coordinates of a step in the unknowns' space)
+__global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) x[idx[j]] = v[j];
+}
+
+// out[j] = gx[idx[j]] + lam v[j] (the free-coordinate rows of J^T J v + lambda v)
+__global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
+                                   double* out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x)
+    out[j] = gx[idx[j]] + (v ? lam * v[j] : 0.0);
+}
+
 }  // namespace ift

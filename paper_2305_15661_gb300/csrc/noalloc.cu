@@ -179,6 +179,7 @@ extern "C" ift_status ift_reduced_residual_jacobian_static(
   a.partial = scratch + o_part;
   a.skip = nullptr;
   a.contraction = 0;
+  a.need_hn = 0;
   if (ks.assemble(&a, true, (int)grid, block, smem, s) != cudaSuccess) return IFT_ERR_CUDA;
   reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(scratch + o_part, (int)grid, nacc, scratch + o_res, nullptr);
   static_unpack_kernel<<<(nacc + 255) / 256, 256, 0, s>>>(scratch + o_res, k_u, k_x, S, T, H, J);

@@ -48,6 +48,12 @@ class Config(ctypes.Structure):
                 ("contraction", ctypes.c_int), ("q", ctypes.c_int)]
 
 
+class AlignInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("trials", ctypes.c_int), ("J", ctypes.c_double), ("gnorm", ctypes.c_double),
+                ("g0", ctypes.c_double)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("init_iters", ctypes.c_int), ("iters", ctypes.c_int),
                 ("trials", ctypes.c_int), ("shifts", ctypes.c_int), ("J", ctypes.c_double),
@@ -64,7 +70,8 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
            "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_element_gradients", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_get_scaling", "ift_mlp_set_scaling", "ift_mlp_loss_grad", "ift_mlp_train",
-           "ift_mlp_predict", "ift_nearest_start"]
+           "ift_mlp_predict", "ift_nearest_start", "ift_align_residual", "ift_align_jvp", "ift_align_vjp",
+           "ift_align"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -118,6 +125,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_mlp_train": (i32, [vp, i64, pd, pd, i32, i32, dbl, ctypes.c_uint64, pd]),
         "ift_mlp_predict": (i32, [vp, i64, pd, pd]),
         "ift_nearest_start": (i32, [i64, i32, pd, i32, pd, i64, pd, pd, pd]),
+        "ift_align_residual": (i32, [vp, pd, pd, pd, pd]),
+        "ift_align_jvp": (i32, [vp, pd, pd, pd, pd, pd, pd]),
+        "ift_align_vjp": (i32, [vp, pd, pd, pd, pd, pd, pd]),
+        "ift_align": (i32, [vp, pd, pd, pd, ctypes.POINTER(ctypes.c_uint8), dbl, i32, P(AlignInfo)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -273,6 +284,45 @@ class Context:
         return {"R": R.reshape(n, self.nu), "JU": JU.reshape(n, self.nu, self.nu),
                 "JUp": JUp.reshape(n, self.nu, self.nup), "Jx": Jx.reshape(n, self.nu, self.nxe), "N": N,
                 "dN": dN.reshape(n, self.nxe)}
+
+    # -- snapshot alignment (Eq. align0) ------------------------------------
+    def _align_sizes(self):
+        return self.n_elems * self.nu, self.n_elems, self.n_verts * self.dim
+
+    def align_residual(self, mu, w, x):
+        """F = [R; N] at (w, x) over every element (x: all mesh coordinates)."""
+        Nu, Ne, _ = self._align_sizes()
+        F = np.zeros(Nu + Ne)
+        self._check(load().ift_align_residual(self._h, _pd(_f64(mu)), _pd(_f64(w)), _pd(_f64(x)), _pd(F)))
+        return F
+
+    def align_jvp(self, mu, w, x, dU, dx):
+        Nu, Ne, _ = self._align_sizes()
+        dF = np.zeros(Nu + Ne)
+        self._check(load().ift_align_jvp(self._h, _pd(_f64(mu)), _pd(_f64(w)), _pd(_f64(x)), _pd(_f64(dU)),
+                                         _pd(_f64(dx)), _pd(dF)))
+        return dF
+
+    def align_vjp(self, mu, w, x, v):
+        Nu, _, Nx = self._align_sizes()
+        gU, gx = np.zeros(Nu), np.zeros(Nx)
+        self._check(load().ift_align_vjp(self._h, _pd(_f64(mu)), _pd(_f64(w)), _pd(_f64(x)), _pd(_f64(v)),
+                                         _pd(gU), _pd(gx)))
+        return gU, gx
+
+    def align(self, mu, w0, x0, free_mask, tol=1e-8, max_iters=100):
+        """Levenberg-Marquardt on (w, free mesh coordinates) for Eq. align0; returns
+        the aligned (w, x) and the solver's counts."""
+        w = _f64(w0).copy()
+        x = _f64(x0).copy()
+        mask = np.ascontiguousarray(free_mask, dtype=np.uint8)
+        info = AlignInfo()
+        st = load().ift_align(self._h, _pd(_f64(mu)), _pd(w), _pd(x),
+                              mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), tol, max_iters,
+                              ctypes.byref(info))
+        self._check(st, allow_positive=True)
+        return {"status": int(st), "w": w, "x": x, "iters": info.iters, "cg_iters": info.cg_iters,
+                "trials": info.trials, "J": info.J, "gnorm": info.gnorm, "g0": info.g0}
 
     def solve_rom(self, mu, y0=None, z0=None):
         y = np.zeros(self.ku) if y0 is None else _f64(y0).copy()
