@@ -371,6 +371,10 @@ typedef struct {
   double J;      /* final (1/2)|F|^2 */
   double gnorm;  /* final |J^T F| over the unknowns */
   double g0;     /* |J^T F| at the start */
+  /* device time (ms, CUDA events on the context's stream) of the phases: forming the
+     stored element blocks with F, J^T F and diag(J^T J) at each accepted point; the
+     conjugate-gradient solves; the line searches */
+  double ms_form, ms_cg, ms_search;
 } ift_align_info;
 
 /* F = [R (N_u); N (n_elems)] at (w, x) (host pointers; x: N_x reference-layout

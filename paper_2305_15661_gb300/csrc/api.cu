@@ -53,6 +53,20 @@ __global__ void xpby_kernel(long n, const double* x, double beta, double* y);
 __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x);
 __global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
                                    double* out);
+__global__ void sum_columns_warp_kernel(const double* part, int nparts, int ku, double* out);
+__global__ void cg_start_kernel(long n, int ku, const double* g, const double* diag, const CGState* st, double* d,
+                                double* r, double* z, double* p, double* part);
+__global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st);
+__global__ void cg_alpha_kernel(const double* part, int nblk, CGState* st);
+__global__ void cg_update_kernel(long n, int ku, const CGState* st, const double* p, const double* Ap,
+                                 const double* diag, double* d, double* r, double* z, double* part);
+__global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsigned long long cond_handle,
+                               int use_cond);
+__global__ void cg_dir_kernel(long n, const CGState* st, const double* z, double* p);
+__global__ void gather_free_lam_kernel(const int* idx, int nfree, const double* gx, const double* v,
+                                       const CGState* st, double* out);
+__global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, const int* pos, const double* vfree,
+                                 double* xdir);
 }  // namespace ift
 
 using namespace ift;
@@ -221,7 +235,7 @@ cudaError_t dalloc(P*& p, size_t n) {
 }
 
 void drop_graph(ift_ctx* c) {
-  for (int wp = 0; wp < 3; ++wp) {
+  for (int wp = 0; wp < 4; ++wp) {
     if (c->graph_exec[wp]) cudaGraphExecDestroy(c->graph_exec[wp]);
     if (c->graph[wp]) cudaGraphDestroy(c->graph[wp]);
     c->graph_exec[wp] = nullptr;
@@ -571,7 +585,7 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_partial);
   dfree(c->d_phit);
   dfree(c->d_lm);
-  for (int wp = 0; wp < 3; ++wp) {
+  for (int wp = 0; wp < 4; ++wp) {
     if (c->bgraph_exec[wp]) cudaGraphExecDestroy(c->bgraph_exec[wp]);
     if (c->bgraph[wp]) cudaGraphDestroy(c->bgraph[wp]);
   }
@@ -1851,9 +1865,13 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
 // ---------------------------------------------------------------------------
 // Snapshot alignment (Eq. align0): min over (w, x) of (1/2)|F(Phi w, x; mu)|^2,
 // F = [R; N] over every element (rho = 1), with the free mesh coordinates x
-// unknowns. Levenberg-Marquardt on the full space, each normal-equation solve by
-// conjugate gradients with J v and J^T v applied element by element
-// (align_kernel), never forming J.
+// unknowns. Levenberg-Marquardt on the full space. At each accepted point one
+// element pass stores every element's share of the Gauss-Newton system, M_e =
+// A_e^T A_e (+ the distortion term) and g_e = A_e^T R_e (+ dN_e N_e), with
+// A_e = [dR_e/dw | dR_e/dx_e], in HBM (align_jac_kernel); the normal equations are
+// then solved by Jacobi-preconditioned conjugate gradients whose products J^T J v
+// read those blocks once each (align_apply_kernel), the whole solve one CUDA graph
+// with a device-side loop. The line search evaluates F alone (align_kernel mode 0).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1861,40 +1879,62 @@ constexpr int kDotBlocks = 120;
 
 struct AlignWork {
   long Nu = 0, Ne = 0, Nx = 0;
-  int ku = 0, nfree = 0;
+  int ku = 0, nfree = 0, nu = 0, nxe = 0, agrid = 1, awarps = 1;
   double *w = nullptr, *x = nullptr, *F = nullptr, *dU = nullptr, *dx = nullptr, *dF = nullptr, *gU = nullptr,
          *gx = nullptr, *wt = nullptr, *xt = nullptr, *Ft = nullptr, *part = nullptr, *nbad = nullptr;
-  double *g = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;  // unknowns' space
-  int* free_idx = nullptr;
+  double *g = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr,
+         *diag = nullptr;                                  // unknowns' space
+  double *M = nullptr, *ge = nullptr, *apart = nullptr;  // element systems, CTA partials of the w rows
+  double* xdir = nullptr;                                  // a mesh direction in element order
+  CGState* cg = nullptr;
+  int *free_idx = nullptr, *pos = nullptr;  // free coordinates; free position of each coordinate (-1: fixed)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
   ~AlignWork() {
-    for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap})
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap, &z,
+                       &diag, &M, &ge, &apart, &xdir})
       dfree(*q);
+    dfree(cg);
     dfree(free_idx);
+    dfree(pos);
   }
-  cudaError_t alloc() {
+  // stored: the buffers of the Levenberg-Marquardt solve as well
+  cudaError_t alloc(bool stored) {
     const long n = ku + nfree;
     cudaError_t e = cudaSuccess;
-    auto A = [&](double*& q, long m) {
+    auto B = [&](double*& q, long m) {
       if (e == cudaSuccess) e = dalloc(q, (size_t)(m > 0 ? m : 1));
     };
-    A(w, LM_KMAX);
-    A(wt, LM_KMAX);
-    A(x, Nx);
-    A(xt, Nx);
-    A(F, Nu + Ne);
-    A(Ft, Nu + Ne);
-    A(dF, Nu + Ne);
-    A(dU, Nu);
-    A(gU, Nu);
-    A(dx, Nx);
-    A(gx, Nx);
-    A(part, kDotBlocks);
-    A(nbad, 1);
-    A(g, n);
-    A(d, n);
-    A(r, n);
-    A(p, n);
-    A(Ap, n);
+    B(w, LM_KMAX);
+    B(wt, LM_KMAX);
+    B(x, Nx);
+    B(xt, Nx);
+    B(F, Nu + Ne);
+    B(Ft, Nu + Ne);
+    B(dF, Nu + Ne);
+    B(dU, Nu);
+    B(gU, Nu);
+    B(dx, Nx);
+    B(gx, Nx);
+    B(part, 2 * kDotBlocks);
+    B(nbad, 1);
+    if (stored) {
+      B(g, n);
+      B(d, n);
+      B(r, n);
+      B(p, n);
+      B(Ap, n);
+      B(z, n);
+      B(diag, n);
+      B(M, Ne * (long)(ku + nxe) * (ku + nxe));
+      B(ge, Ne * (long)(ku + nxe));
+      B(apart, (long)agrid * ku);
+      B(xdir, Ne * nxe);
+      if (e == cudaSuccess) e = dalloc(cg, 1);
+      if (e == cudaSuccess) e = dalloc(pos, (size_t)(Nx > 0 ? Nx : 1));
+    }
     if (e == cudaSuccess) e = dalloc(free_idx, (size_t)(nfree > 0 ? nfree : 1));
     return e;
   }
@@ -1916,18 +1956,25 @@ int vec_grid(long n) {
   return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
 }
 
+// FP64 kernel arguments of the alignment passes at (w, x): the current mesh in
+// place of the reference nodes, no mesh basis, face-normal Jacobians formed.
+AsmArgs<double> align_args(ift_ctx* c, const double* w, const double* x) {
+  AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, c->d_tau, c->d_mu, true, nullptr);
+  a.X = x;
+  a.kx = 0;
+  a.Psi = nullptr;
+  a.need_hn = 1;
+  return a;
+}
+
 // One element pass of align_kernel in FP64 at (w, x): mode 0 F, 1 J v, 2 J^T v.
 ift_status align_pass(ift_ctx* c, int mode, const double* w, const double* x, const double* vU, const double* vx,
                       const double* vN, double* outU, double* outX, cudaStream_t s) {
   const KernelSet& ks = c->ks[0];
   if (!ks.align) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
-  AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, c->d_tau, c->d_mu, true, nullptr);
-  a.X = x;  // the current mesh in place of the reference nodes, no mesh basis
-  a.kx = 0;
-  a.Psi = nullptr;
-  a.need_hn = 1;
-  const int warps = 2, block = 32 * warps;
-  const size_t smem = ks.smem_bytes(true, c->ku, 0, warps);
+  AsmArgs<double> a = align_args(c, w, x);
+  const int warps = mode == 0 ? 4 : 2, block = 32 * warps;
+  const size_t smem = ks.smem_bytes(mode != 0, c->ku, 0, warps);
   if (smem > (size_t)c->smem_optin) return c->fail(IFT_ERR_ARG, "alignment pass needs too much shared memory");
   long grid = (c->n_elems + warps - 1) / warps;
   if (grid > (long)c->sm_count * 8) grid = (long)c->sm_count * 8;
@@ -1936,38 +1983,8 @@ ift_status align_pass(ift_ctx* c, int mode, const double* w, const double* x, co
   return IFT_OK;
 }
 
-// out = J^T f in the unknowns' space (w rows: Phi^T (dR/dU)^T f_R; free rows: the
-// free coordinates of (dR/dx)^T f_R + (dN/dx)^T f_N), plus lam v on the free rows.
-ift_status align_grad(ift_ctx* c, AlignWork& W, const double* w, const double* x, const double* f, const double* v,
-                      double lam, double* out, cudaStream_t s) {
-  CK(cudaMemsetAsync(W.gU, 0, W.Nu * 8, s), "zero gU");
-  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
-  ift_status st = align_pass(c, 2, w, x, f, nullptr, f + W.Nu, W.gU, W.gx, s);
-  if (st != IFT_OK) return st;
-  const long chunk = (W.Nu + kPhitBlocks - 1) / kPhitBlocks;
-  int block = 256;
-  if (block < W.ku) block = W.ku;
-  phit_vec_partial_kernel<<<kPhitBlocks, block, block * sizeof(double), s>>>(c->d_Phi, W.Nu, W.ku, W.gU, chunk,
-                                                                             c->d_phit);
-  sum_columns_kernel<<<1, 64, 0, s>>>(c->d_phit, kPhitBlocks, W.ku, out);
-  if (W.nfree > 0)
-    gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, v ? v + W.ku : nullptr, lam,
-                                                         out + W.ku);
-  CK(cudaGetLastError(), "alignment gradient");
-  return IFT_OK;
-}
-
-// out = (J^T J + lam D) v, D = diag(0 on w, 1 on the free coordinates)
-ift_status align_normal(ift_ctx* c, AlignWork& W, const double* v, double lam, double* out, cudaStream_t s) {
-  phi_matvec_kernel<<<vec_grid(W.Nu), 256, 0, s>>>(c->d_Phi, W.Nu, W.ku, v, W.dU);
-  CK(cudaMemsetAsync(W.dx, 0, W.Nx * 8, s), "zero dx");
-  if (W.nfree > 0) scatter_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, v + W.ku, W.dx);
-  ift_status st = align_pass(c, 1, W.w, W.x, W.dU, W.dx, nullptr, W.dF, nullptr, s);
-  if (st != IFT_OK) return st;
-  return align_grad(c, W, W.w, W.x, W.dF, v, lam, out, s);
-}
-
-ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double* w, const double* x) {
+ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double* w, const double* x,
+                       bool stored = false) {
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!mu || !w || !x) return c->fail(IFT_ERR_ARG, "null input pointer");
@@ -1975,11 +1992,69 @@ ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double*
   W.Ne = c->n_elems;
   W.Nx = c->n_verts * (long)c->dim;
   W.ku = c->ku;
-  CK(W.alloc(), "alignment buffers");
+  W.nu = c->nu;
+  W.nxe = c->nxe;
+  if (stored) {
+    if (!c->ks[0].align_apply_plan) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
+    CK(c->ks[0].align_apply_plan(W.ku, W.Ne, c->sm_count, &W.awarps, &W.agrid), "alignment product shape");
+  }
+  CK(W.alloc(stored), "alignment buffers");
   const int nmu = (c->dim == 1) ? 1 : 2;
   CK(cudaMemcpy(c->d_mu, mu, nmu * 8, cudaMemcpyHostToDevice), "copy mu");
   CK(cudaMemcpy(W.w, w, W.ku * 8, cudaMemcpyHostToDevice), "copy w");
   CK(cudaMemcpy(W.x, x, W.Nx * 8, cudaMemcpyHostToDevice), "copy x");
+  return IFT_OK;
+}
+
+// The element systems, F and the non-physical count at (W.w, W.x); J = (1/2)|F|^2
+// (+inf where an element is non-physical).
+ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
+  const KernelSet& ks = c->ks[0];
+  if (!ks.align_jac) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
+  if (ks.align_jac_smem(c->ku, 2) > (size_t)c->smem_optin)
+    return c->fail(IFT_ERR_ARG, "alignment Jacobian pass needs too much shared memory");
+  AsmArgs<double> a = align_args(c, W.w, W.x);
+  CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
+  CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, 2, c->sm_count, s), "alignment Jacobian pass");
+  J = 0.5 * align_dot(W, W.F, W.F, W.Nu + W.Ne, s);
+  double nb = 0.0;
+  CK(cudaMemcpy(&nb, W.nbad, 8, cudaMemcpyDeviceToHost), "read count");
+  if (nb > 0.0) J = INFINITY;
+  return IFT_OK;
+}
+
+// out (unknowns' space) from the stored blocks: mode 0 J^T J v (+ lam v on the
+// free rows, lam from the solve's scalars), 1 J^T F, 2 diag(J^T J).
+ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, const double* v, double* out, cudaStream_t s) {
+  const KernelSet& ks = c->ks[0];
+  if (mode == 0)
+    align_dir_kernel<<<vec_grid(W.Ne * W.nxe), 256, 0, s>>>(c->d_ev, W.Ne, c->nv, c->dim, W.pos, v + W.ku, W.xdir);
+  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
+  CK(ks.align_apply(mode, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, v, W.apart, W.gx, W.agrid, W.awarps, s),
+     "alignment product");
+  sum_columns_warp_kernel<<<(W.ku + 7) / 8, 256, 0, s>>>(W.apart, W.agrid, W.ku, out);
+  if (W.nfree > 0) {
+    if (mode == 0)
+      gather_free_lam_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, v + W.ku, W.cg,
+                                                               out + W.ku);
+    else
+      gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, nullptr, 0.0, out + W.ku);
+  }
+  CK(cudaGetLastError(), "alignment product");
+  return IFT_OK;
+}
+
+// The CG loop body: Ap = (J^T J + lam D) p, then one preconditioned CG update.
+ift_status align_cg_body(ift_ctx* c, AlignWork& W, cudaStream_t s, unsigned long long handle, int use_cond) {
+  const long n = W.ku + W.nfree;
+  ift_status st = align_apply(c, W, 0, W.p, W.Ap, s);
+  if (st != IFT_OK) return st;
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(W.p, W.Ap, n, W.part);
+  cg_alpha_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg);
+  cg_update_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.cg, W.p, W.Ap, W.diag, W.d, W.r, W.z, W.part);
+  cg_beta_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg, handle, use_cond);
+  cg_dir_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.cg, W.z, W.p);
+  CK(cudaGetLastError(), "conjugate-gradient step");
   return IFT_OK;
 }
 
@@ -2040,72 +2115,132 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
   if (c && c->have_mesh) {
     for (long i = 0; i < c->n_verts * (long)c->dim; ++i) W.nfree += free_mask[i] ? 1 : 0;
   }
-  ift_status st = align_setup(c, W, mu, w, x);
+  if (c && c->ku + c->nxe > 96) return c->fail(IFT_ERR_ARG, "alignment supports k_u + n_xe <= 96");
+  ift_status st = align_setup(c, W, mu, w, x, true);
   if (st != IFT_OK) return st;
   if (!(tol >= 0.0) || max_iters < 0) return c->fail(IFT_ERR_ARG, "tol >= 0 and max_iters >= 0 required");
   {
-    std::vector<int> idx;
+    std::vector<int> idx, pos((size_t)W.Nx, -1);
     for (long i = 0; i < W.Nx; ++i)
-      if (free_mask[i]) idx.push_back((int)i);
+      if (free_mask[i]) {
+        pos[(size_t)i] = (int)idx.size();
+        idx.push_back((int)i);
+      }
     if (!idx.empty()) CK(cudaMemcpy(W.free_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice), "copy idx");
+    CK(cudaMemcpy(W.pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice), "copy positions");
   }
   cudaStream_t s = c->stream;
-  const long n = W.ku + W.nfree, nF = W.Nu + W.Ne;
+  const long n = W.ku + W.nfree;
   // readings of Sec. 3.2.3 as for the reduced solve: lambda_0 = 1e-4, /10 after a
   // full step, x10 after a shortened one, Armijo 1e-4, at most 30 halvings; damping
   // on the mesh block only (Eq. levmarq-step)
   const double c1 = 1e-4, round_tol = 16.0 * 2.220446049250313e-16;
   double lam = 1e-4;
-  // (1/2)|F|^2 at (ww, xx); +inf where an element is non-physical (such a trial is
-  // rejected, as in the reduced solve)
+  CGState cg0{};
+  cg0.tol = 1e-12;
+  cg0.max_iters = (int)std::min<long>(4 * n + 20, 2000);
+  cg0.done = 1;
+  // (1/2)|F|^2 at (ww, xx) by the residual-only pass; +inf where an element is
+  // non-physical (such a trial is rejected, as in the reduced solve)
   auto objective = [&](const double* ww, const double* xx, double* FF, double& Jv) -> ift_status {
     CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
     ift_status q = align_pass(c, 0, ww, xx, nullptr, nullptr, nullptr, FF, W.nbad, s);
     if (q != IFT_OK) return q;
-    Jv = 0.5 * align_dot(W, FF, FF, nF, s);
+    Jv = 0.5 * align_dot(W, FF, FF, W.Nu + W.Ne, s);
     double nb = 0.0;
     CK(cudaMemcpy(&nb, W.nbad, 8, cudaMemcpyDeviceToHost), "read count");
     if (nb > 0.0) Jv = INFINITY;
     return IFT_OK;
   };
-  double J = 0.0;
-  st = objective(W.w, W.x, W.F, J);
+  // at an accepted point: the stored blocks, F, the gradient and the preconditioner
+  auto form = [&](double& Jv, double& gn) -> ift_status {
+    ift_status q = align_form(c, W, Jv, s);
+    if (q != IFT_OK) return q;
+    if (!std::isfinite(Jv)) return IFT_OK;
+    q = align_apply(c, W, 1, nullptr, W.g, s);
+    if (q != IFT_OK) return q;
+    q = align_apply(c, W, 2, nullptr, W.diag, s);
+    if (q != IFT_OK) return q;
+    gn = std::sqrt(align_dot(W, W.g, W.g, n, s));
+    return IFT_OK;
+  };
+  cg0.lam = lam;
+  CK(cudaMemcpy(W.cg, &cg0, sizeof(CGState), cudaMemcpyHostToDevice), "copy solve scalars");
+  // one conjugate-gradient solve = one launch of a while-loop graph (or, with
+  // IFT_SOLVE_NO_GRAPH set, the same body enqueued from the host in groups of 8)
+  static const bool no_graph = getenv("IFT_SOLVE_NO_GRAPH") != nullptr;
+  if (!no_graph) {
+    st = build_while_graph(c, &W.graph, &W.exec, [&](cudaStream_t cs, unsigned long long h) {
+      return align_cg_body(c, W, cs, h, 1);
+    });
+    if (st != IFT_OK) return st;
+  }
+  auto run_cg = [&]() -> ift_status {
+    if (!no_graph) {
+      CK(cudaGraphLaunch(W.exec, s), "conjugate-gradient graph");
+      return IFT_OK;
+    }
+    for (int b = 0; b <= cg0.max_iters; b += 8) {
+      for (int j = 0; j < 8; ++j) {
+        ift_status q = align_cg_body(c, W, s, 0ull, 0);
+        if (q != IFT_OK) return q;
+      }
+      int dn = 0;
+      CK(cudaMemcpyAsync(&dn, (const char*)W.cg + offsetof(CGState, done), sizeof(int), cudaMemcpyDeviceToHost, s),
+         "read done flag");
+      CK(cudaStreamSynchronize(s), "conjugate-gradient loop");
+      if (dn) break;
+    }
+    return IFT_OK;
+  };
+  // device time of the phases (CUDA events on the solve's stream)
+  cudaEvent_t ev[2];
+  CK(cudaEventCreate(&ev[0]), "event");
+  CK(cudaEventCreate(&ev[1]), "event");
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  } ev_guard{ev};
+  double ms_form = 0.0, ms_cg = 0.0, ms_search = 0.0;
+  auto lap = [&](double& acc) -> ift_status {
+    CK(cudaEventRecord(ev[1], s), "event");
+    CK(cudaEventSynchronize(ev[1]), "event");
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ev[0], ev[1]), "event time");
+    acc += t;
+    return IFT_OK;
+  };
+  double J = 0.0, gnorm = 0.0;
+  CK(cudaEventRecord(ev[0], s), "event");
+  st = form(J, gnorm);
   if (st != IFT_OK) return st;
   if (!std::isfinite(J)) return c->fail(IFT_ERR_NONPHYSICAL, "the starting point is not physical");
-  st = align_grad(c, W, W.w, W.x, W.F, nullptr, 0.0, W.g, s);
-  if (st != IFT_OK) return st;
-  double gnorm = std::sqrt(align_dot(W, W.g, W.g, n, s));
+  if ((st = lap(ms_form)) != IFT_OK) return st;
   const double g0 = gnorm, thresh = tol * std::max(1.0, g0);
   int status = IFT_NOT_CONVERGED, iters = 0, cg_total = 0, trials = 0;
-  const int max_cg = (int)std::min<long>(4 * n + 20, 2000);
   for (;;) {
     if (gnorm <= thresh) {
       status = IFT_OK;
       break;
     }
     if (iters >= max_iters) break;
-    // CG on (J^T J + lam D) d = -g, from d = 0
-    CK(cudaMemsetAsync(W.d, 0, n * 8, s), "zero d");
-    CK(cudaMemcpyAsync(W.r, W.g, n * 8, cudaMemcpyDeviceToDevice, s), "r = g");
-    axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, -2.0, W.g, W.r);  // r = -g
-    CK(cudaMemcpyAsync(W.p, W.r, n * 8, cudaMemcpyDeviceToDevice, s), "p = r");
-    double rr = align_dot(W, W.r, W.r, n, s);
-    const double rr0 = rr;
-    for (int k = 0; k < max_cg; ++k) {
-      st = align_normal(c, W, W.p, lam, W.Ap, s);
-      if (st != IFT_OK) return st;
-      const double pAp = align_dot(W, W.p, W.Ap, n, s);
-      ++cg_total;
-      if (!(pAp > 0.0)) break;
-      const double alpha = rr / pAp;
-      axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, alpha, W.p, W.d);
-      axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, -alpha, W.Ap, W.r);
-      const double rr1 = align_dot(W, W.r, W.r, n, s);
-      if (std::sqrt(rr1) <= 1e-12 * std::sqrt(rr0)) break;
-      xpby_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.r, rr1 / rr, W.p);
-      rr = rr1;
-    }
-    const double slope = align_dot(W, W.g, W.d, n, s);
+    // (J^T J + lam D) d = -g by preconditioned CG from d = 0, on the device
+    cg0.lam = lam;
+    CK(cudaEventRecord(ev[0], s), "event");
+    CK(cudaMemcpyAsync(W.cg, &cg0, sizeof(CGState), cudaMemcpyHostToDevice, s), "copy solve scalars");
+    cg_start_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.g, W.diag, W.cg, W.d, W.r, W.z, W.p, W.part);
+    cg_start_finish_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg);
+    CK(cudaGetLastError(), "conjugate-gradient start");
+    if ((st = run_cg()) != IFT_OK) return st;
+    CGState cgr{};
+    CK(cudaMemcpyAsync(&cgr, W.cg, sizeof(CGState), cudaMemcpyDeviceToHost, s), "read solve scalars");
+    const double slope = align_dot(W, W.g, W.d, n, s);  // synchronises the stream
+    if ((st = lap(ms_cg)) != IFT_OK) return st;
+    cg_total += cgr.iters;
+    CK(cudaEventRecord(ev[0], s), "event");
     // backtracking line search on (1/2)|F|^2
     double alpha = 1.0, Jt = 0.0;
     int h = 0;
@@ -2113,10 +2248,10 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     for (;;) {
       CK(cudaMemcpyAsync(W.wt, W.w, W.ku * 8, cudaMemcpyDeviceToDevice, s), "wt = w");
       axpy_kernel<<<1, 64, 0, s>>>(W.ku, alpha, W.d, W.wt);
-      CK(cudaMemsetAsync(W.dx, 0, W.Nx * 8, s), "zero dx");
-      if (W.nfree > 0) scatter_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.d + W.ku, W.dx);
+      CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero step");
+      if (W.nfree > 0) scatter_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.d + W.ku, W.gx);
       CK(cudaMemcpyAsync(W.xt, W.x, W.Nx * 8, cudaMemcpyDeviceToDevice, s), "xt = x");
-      axpy_kernel<<<vec_grid(W.Nx), 256, 0, s>>>(W.Nx, alpha, W.dx, W.xt);
+      axpy_kernel<<<vec_grid(W.Nx), 256, 0, s>>>(W.Nx, alpha, W.gx, W.xt);
       st = objective(W.wt, W.xt, W.Ft, Jt);
       if (st != IFT_OK) return st;
       ++trials;
@@ -2127,6 +2262,7 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
       if (++h > 30) break;
       alpha *= 0.5;
     }
+    if ((st = lap(ms_search)) != IFT_OK) return st;
     if (!accepted) {
       status = IFT_LINESEARCH_FAILED;
       break;
@@ -2134,12 +2270,13 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     lam = (h == 0) ? std::max(lam / 10.0, 1e-12) : std::min(lam * 10.0, 1e8);
     std::swap(W.w, W.wt);
     std::swap(W.x, W.xt);
-    std::swap(W.F, W.Ft);
-    J = Jt;
     ++iters;
-    st = align_grad(c, W, W.w, W.x, W.F, nullptr, 0.0, W.g, s);
+    double Jf = 0.0;
+    CK(cudaEventRecord(ev[0], s), "event");
+    st = form(Jf, gnorm);
     if (st != IFT_OK) return st;
-    gnorm = std::sqrt(align_dot(W, W.g, W.g, n, s));
+    if ((st = lap(ms_form)) != IFT_OK) return st;
+    J = Jt;
   }
   CK(cudaMemcpyAsync(w, W.w, W.ku * 8, cudaMemcpyDeviceToHost, s), "copy w");
   CK(cudaMemcpyAsync(x, W.x, W.Nx * 8, cudaMemcpyDeviceToHost, s), "copy x");
@@ -2152,6 +2289,9 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     info->J = J;
     info->gnorm = gnorm;
     info->g0 = g0;
+    info->ms_form = ms_form;
+    info->ms_cg = ms_cg;
+    info->ms_search = ms_search;
   }
   return (ift_status)status;
 }

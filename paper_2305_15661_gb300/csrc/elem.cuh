@@ -47,6 +47,9 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// every committed group but the newest has landed (this thread's copies)
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Copy n values of T from global src to shared dst (dst 16-byte aligned) by the warp's
 // lanes with cp.async: 16-byte pieces when src is 16-byte aligned and n T fill whole
@@ -2212,7 +2215,9 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
                                                     const double* vx, const double* vN, double* outU,
                                                     double* outX) {
   using Dd = Disc<PROB, P>;
-  using Core = ElemCore<T, PROB, P, true>;
+  // the residual (mode 0) needs no Jacobian data: the objective-only layout and front
+  constexpr bool JK = MODE != 0;
+  using Core = ElemCore<T, PROB, P, JK>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2222,7 +2227,7 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
   double* tauD;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
   const size_t cb = cta_bytes<T, PROB, P>(a.ku, a.kx);
-  const size_t wb = WarpLayout<T, PROB, P, true>(a.ku, a.kx).bytes;
+  const size_t wb = WarpLayout<T, PROB, P, JK>(a.ku, a.kx).bytes;
   Core C;
   C.carve(smem + cb + warp * wb, a.ku, a.kx);
   bind_tables(C, tab);
@@ -2231,7 +2236,7 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
   for (long e = (long)blockIdx.x * nw + warp; e < a.n_items; e += (long)gridDim.x * nw) {
     const int* vv = &a.ev[e * NV];
     signed char bcs[NF];
-    const bool bad = element_front<T, PROB, P, true>(C, a, (int)e, wT, tauD, a.mu, lane, bcs);
+    const bool bad = element_front<T, PROB, P, JK>(C, a, (int)e, wT, tauD, a.mu, lane, bcs);
     if (lane == 0) {
       double Xe[NXE];
       for (int r = 0; r < NXE; ++r) Xe[r] = Xref[(size_t)vv[r / DIM] * DIM + (r % DIM)];
@@ -2298,6 +2303,192 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
       }
     }
     __syncwarp();
+  }
+}
+
+// Snapshot alignment with stored element blocks: per element, one warp forms
+//   A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' | dR_e/dx_e]   (n_u x k, k = k_u + n_xe),
+// the fused assembly's columns with the unit directions of the element's node
+// coordinates in place of Psi_e (an identity Psi_e in shared memory), at (w, x) with
+// x in place of the reference nodes, and stores the element's share of the
+// Gauss-Newton system of (1/2)|F|^2, F = [R; N]:
+//   M_e = A_e^T A_e + [0 0; 0 dN_e^T dN_e]   (k x k, row-major, Mout[e]),
+//   g_e = A_e^T R_e + [0; dN_e^T N_e]        (k, gout[e]),
+// with R_e and N_e into F (as align_kernel mode 0) and the non-physical count into
+// nbad[0]. J^T J = sum_e M_e and J^T F = sum_e g_e over the elements' unknowns, so
+// every product of the Levenberg-Marquardt step reads these blocks
+// (align_apply_kernel) instead of differentiating the element again; M_e holds
+// half the arithmetic of applying A_e and A_e^T in turn (the FP64 pipe bounds it).
+// Lane c forms column c of M_e (and g_c); rows are written coalesced.
+template <class T, int PROB, int P>
+__global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const double* Xref, double* Mout,
+                                                        double* gout, double* F, double* nbad) {
+  using Dd = Disc<PROB, P>;
+  using Core = ElemCore<T, PROB, P, true>;
+  constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ku = a.ku, k = ku + NXE;
+  T *tab, *wT;
+  double* tauD;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
+  const size_t cb = cta_bytes<T, PROB, P>(ku, a.kx);
+  const size_t wb = WarpLayout<T, PROB, P, true>(ku, NXE).bytes;
+  Core C;
+  C.carve(smem + cb + warp * wb, ku, NXE);
+  bind_tables(C, tab);
+  for (int i = lane; i < NXE * NXE; i += 32) C.Psie[i] = (i / NXE == i % NXE) ? 1.0 : 0.0;
+  __syncthreads();
+  const long Nu = (long)a.n_items * NU;
+  for (long e = (long)blockIdx.x * nw + warp; e < a.n_items; e += (long)gridDim.x * nw) {
+    const int* vv = &a.ev[e * NV];
+    signed char bcs[NF];
+    const bool bad = element_front<T, PROB, P, true>(C, a, (int)e, wT, tauD, a.mu, lane, bcs);
+    if (lane == 0) {
+      double Xe[NXE];
+      for (int r = 0; r < NXE; ++r) Xe[r] = Xref[(size_t)vv[r / DIM] * DIM + (r % DIM)];
+      C.distortion_any(Xe, a.kappa, a.eps);
+    }
+    C.jac_state(lane, bcs, ku, k);
+    C.jac_geom(lane, a.mu, ku, NXE, k, false);
+    __syncwarp();
+    const double Ne = C.dN[NXE];
+    double* Me = Mout + (size_t)e * k * k;
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int c = c0 + lane;
+      if (c < k) {
+        const double dnc = c >= ku ? C.dN[c - ku] : 0.0;
+        double gc = dnc * Ne;
+        for (int i = 0; i < NU; ++i) gc += (double)C.A[i * k + c] * (double)C.R[i];
+        gout[(size_t)e * k + c] = gc;
+      }
+      for (int j = 0; j < k; ++j) {
+        if (c < k) {
+          double m = 0.0;
+#pragma unroll 8
+          for (int i = 0; i < NU; ++i) m += (double)C.A[i * k + j] * (double)C.A[i * k + c];
+          if (c >= ku && j >= ku) m += C.dN[j - ku] * C.dN[c - ku];
+          Me[(size_t)j * k + c] = m;
+        }
+      }
+    }
+    for (int i = lane; i < NU; i += 32) F[e * NU + i] = (double)C.R[i];
+    if (lane == 0) {
+      F[Nu + e] = Ne;
+      if (bad) atomicAdd(nbad, 1.0);
+    }
+    __syncwarp();
+  }
+}
+
+// Shared memory of align_apply_kernel, in doubles: one staging buffer (M_e rows at
+// an odd stride kp = (k_u + n_xe) | 1, the element's mesh direction, the node
+// indices), and per warp two buffers plus v (kp).
+__host__ __device__ inline int align_apply_buf(int nxe, int nv, int ku) {
+  const int kp = (ku + nxe) | 1;
+  return (ku + nxe) * kp + nxe + (nv + 1) / 2;
+}
+__host__ __device__ inline int align_apply_warp_doubles(int nxe, int nv, int ku) {
+  const int kp = (ku + nxe) | 1;
+  return 2 * align_apply_buf(nxe, nv, ku) + kp;
+}
+
+// Products with the stored element systems of align_jac_kernel over the unknowns
+// (w, x) (J^T J = sum_e M_e, J^T F = sum_e g_e):
+//   MODE 0: y = J^T J v for v = (dw, dx), the mesh part given per element in xdir
+//           (n_xe values per element, zero on fixed coordinates): y_e = M_e v_e;
+//   MODE 1: y = J^T F: y_e = g_e;
+//   MODE 2: y = diag(J^T J): y_e = diag(M_e).
+// MODE 0: one warp per element, elements strided over the grid; each M_e is staged
+// in shared memory by cp.async, double-buffered (the next element's copies are in
+// flight while the warp works on this one), and lane c forms y_c from column c
+// (= row c; rows at an odd stride of doubles, free of bank conflicts). MODES 1-2
+// read their k values directly. The w rows of y are summed per CTA into
+// part[block][0..ku) (summed over blocks in block order afterwards), the mesh rows
+// added to gx at the element's node coordinates. k_u + n_xe <= 96.
+template <int NXE, int DIM, int MODE>
+__global__ void __launch_bounds__(256) align_apply_kernel(const double* __restrict__ M,
+                                                          const double* __restrict__ g, const int* __restrict__ ev,
+                                                          const double* __restrict__ xdir, long n_elems, int ku,
+                                                          const double* __restrict__ dw, double* part, double* gx) {
+  constexpr int NV = NXE / DIM;
+  extern __shared__ __align__(16) double dsm[];
+  __shared__ double sw[96];
+  __shared__ double red[8][96];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int k = ku + NXE, kp = k | 1;
+  const int bufd = align_apply_buf(NXE, NV, ku);
+  double* base = dsm + (size_t)warp * align_apply_warp_doubles(NXE, NV, ku);
+  double* v = base + 2 * bufd;
+  if (MODE == 0)
+    for (int i = threadIdx.x; i < ku; i += blockDim.x) sw[i] = dw[i];
+  __syncthreads();
+  auto stage = [&](long ee, double* b) {
+    const double* src = M + (size_t)ee * k * k;
+    for (int j = 0; j < k; ++j)
+      for (int c = lane; c < k; c += 32) cp_async8(&b[j * kp + c], &src[(size_t)j * k + c]);
+    double* o = b + k * kp;
+    if (lane < NXE) cp_async8(&o[lane], &xdir[ee * NXE + lane]);
+    int* vi = (int*)(o + NXE);
+    if (lane < NV) cp_async4(&vi[lane], &ev[ee * NV + lane]);
+  };
+  double accw[3] = {0.0, 0.0, 0.0};
+  const long stride = (long)gridDim.x * nw;
+  long e = (long)blockIdx.x * nw + warp;
+  int cur = 0;
+  if (MODE == 0) {
+    if (e < n_elems) stage(e, base);
+    cp_async_commit();
+  }
+  for (; e < n_elems; e += stride) {
+    const int* vi;
+    const double* Mb = nullptr;
+    if constexpr (MODE == 0) {
+      const long en = e + stride;
+      if (en < n_elems) stage(en, base + (cur ^ 1) * bufd);
+      cp_async_commit();
+      cp_async_wait_prev();
+      __syncwarp();
+      Mb = base + cur * bufd;
+      const double* o = Mb + k * kp;
+      vi = (const int*)(o + NXE);
+      for (int c = lane; c < k; c += 32) v[c] = c < ku ? sw[c] : o[c - ku];
+      __syncwarp();
+    } else {
+      vi = ev + e * NV;
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const int c = ch * 32 + lane;
+      if (c < k) {
+        double y;
+        if constexpr (MODE == 0) {
+          y = 0.0;
+#pragma unroll 8
+          for (int j = 0; j < k; ++j) y += Mb[j * kp + c] * v[j];
+        } else if constexpr (MODE == 1) {
+          y = g[(size_t)e * k + c];
+        } else {
+          y = M[(size_t)e * k * k + (size_t)c * k + c];
+        }
+        const int r = c - ku;
+        if (r >= 0) atomicAdd(&gx[vi[r / DIM] * DIM + (r % DIM)], y);
+        else accw[ch] += y;
+      }
+    }
+    if constexpr (MODE == 0) {
+      __syncwarp();
+      cur ^= 1;
+    }
+  }
+  if (MODE == 0) cp_async_wait_all();
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) red[warp][ch * 32 + lane] = accw[ch];
+  __syncthreads();
+  for (int c = threadIdx.x; c < ku; c += blockDim.x) {
+    double s = 0.0;
+    for (int wi = 0; wi < nw; ++wi) s += red[wi][c];
+    part[(size_t)blockIdx.x * ku + c] = s;
   }
 }
 

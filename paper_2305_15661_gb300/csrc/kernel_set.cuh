@@ -160,6 +160,68 @@ struct KernelSetImpl {
     if (mode == 1) return align_mode<1>(a, Xref, vU, vx, vN, outU, outX, grid, block, smem, s);
     return align_mode<2>(a, Xref, vU, vx, vN, outU, outX, grid, block, smem, s);
   }
+  // snapshot alignment with stored element systems (FP64 sets)
+  static size_t align_jac_smem(int ku, int warps) {
+    return cta_bytes<T, PROB, P>(ku, 0) + (size_t)warps * WarpLayout<T, PROB, P, true>(ku, Disc<PROB, P>::NXE).bytes;
+  }
+  static cudaError_t align_jac(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
+                               int warps, int sm_count, cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    const size_t smem = align_jac_smem(a.ku, warps);
+    cudaError_t e = cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, align_jac_kernel<T, PROB, P>, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long grid = (a.n_items + warps - 1) / warps;
+    if (grid > (long)sm_count * occ) grid = (long)sm_count * occ;
+    if (grid < 1) grid = 1;
+    align_jac_kernel<T, PROB, P><<<(int)grid, 32 * warps, smem, s>>>(a, Xref, M, g, F, nbad);
+    return cudaGetLastError();
+  }
+  static size_t align_apply_smem(int ku, int warps) {
+    using Dd = Disc<PROB, P>;
+    return (size_t)warps * align_apply_warp_doubles(Dd::NXE, Dd::NXE / Dd::DIM, ku) * sizeof(double);
+  }
+  // warps per CTA (as many as fit 200 KB of staging, at most 8) and the grid (resident
+  // CTAs of the product kernel on sm_count SMs, at most one warp per element)
+  static cudaError_t align_apply_plan(int ku, long n, int sm_count, int* warps, int* grid) {
+    const size_t per = align_apply_smem(ku, 1);
+    int w = (int)((200u * 1024u) / (per > 0 ? per : 1));
+    w = w < 1 ? 1 : (w > 8 ? 8 : w);
+    const size_t smem = align_apply_smem(ku, w);
+    using Dd = Disc<PROB, P>;
+    auto kern = align_apply_kernel<Dd::NXE, Dd::DIM, 0>;
+    // the shared-memory limit, set here (before any graph capture)
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * w, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long g = (n + w - 1) / w;
+    if (g > (long)sm_count * occ) g = (long)sm_count * occ;
+    *warps = w;
+    *grid = (int)(g < 1 ? 1 : g);
+    return cudaSuccess;
+  }
+  static cudaError_t align_apply(int mode, const double* M, const double* g, const int* ev, const double* xdir,
+                                 long n, int ku, const double* dw, double* part, double* gx, int grid, int warps,
+                                 cudaStream_t s) {
+    using Dd = Disc<PROB, P>;
+    if (ku + Dd::NXE > 96 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
+    const int block = 32 * warps;
+    if (mode == 0)
+      align_apply_kernel<Dd::NXE, Dd::DIM, 0><<<grid, block, align_apply_smem(ku, warps), s>>>(M, g, ev, xdir, n,
+                                                                                                 ku, dw, part, gx);
+    else if (mode == 1)
+      align_apply_kernel<Dd::NXE, Dd::DIM, 1><<<grid, block, 0, s>>>(M, g, ev, xdir, n, ku, dw, part, gx);
+    else
+      align_apply_kernel<Dd::NXE, Dd::DIM, 2><<<grid, block, 0, s>>>(M, g, ev, xdir, n, ku, dw, part, gx);
+    return cudaGetLastError();
+  }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
@@ -197,6 +259,10 @@ struct KernelSetImpl {
       k.assemble_batched_grad = &assemble_batched_grad;
       k.smem_bytes_grad = &smem_bytes_grad;
       k.align = &align;
+      k.align_jac = &align_jac;
+      k.align_jac_smem = &align_jac_smem;
+      k.align_apply = &align_apply;
+      k.align_apply_plan = &align_apply_plan;
       k.blocks_per_sm_grad = &blocks_per_sm_grad;
     }
     k.blocks_per_sm_norms = &blocks_per_sm_norms;

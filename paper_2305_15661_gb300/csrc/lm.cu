@@ -582,6 +582,179 @@ __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, 
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) x[idx[j]] = v[j];
 }
 
+// out[c] = sum_b part[b][c] in block order, one warp per column (lanes take
+// strided rows, then a fixed butterfly: deterministic for a fixed nparts)
+__global__ void sum_columns_warp_kernel(const double* part, int nparts, int ku, double* out) {
+  const int lane = threadIdx.x & 31, c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ku) return;
+  double s = 0.0;
+  for (int b = lane; b < nparts; b += 32) s += part[(size_t)b * ku + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
+}
+
+// Preconditioned conjugate gradients on (J^T J + lam D) d = -g with the Jacobi
+// preconditioner m = diag(J^T J) + lam D (D = 1 on the mesh rows, the first ku
+// rows are the state coefficients). The scalars stay on the device; once done is
+// set an iteration changes nothing, and cg_beta_kernel ends the graph's loop.
+__device__ __forceinline__ double cg_precond(const double* diag, const CGState* st, long i, int ku) {
+  const double m = diag[i] + (i >= ku ? st->lam : 0.0);
+  return m > 0.0 ? 1.0 / m : 1.0;
+}
+
+// Block partial sums of (a . a, a . b) into part[2 blk], part[2 blk + 1]
+__device__ __forceinline__ void block_dot2(double s0, double s1, double* part) {
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = s0;
+  sh[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh[0][0];
+    part[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+// d = 0, r = -g, z = M^{-1} r, p = z; partials of r . r and r . z (256 threads per block)
+__global__ void cg_start_kernel(long n, int ku, const double* g, const double* diag, const CGState* st, double* d,
+                                double* r, double* z, double* p, double* part) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double ri = -g[i], zi = ri * cg_precond(diag, st, i, ku);
+    d[i] = 0.0;
+    r[i] = ri;
+    z[i] = zi;
+    p[i] = zi;
+    s0 += ri * ri;
+    s1 += ri * zi;
+  }
+  block_dot2(s0, s1, part);
+}
+
+// Sums of the pair partials (a . a, a . b) by one warp in a fixed order
+__device__ __forceinline__ void warp_sum2(const double* part, int nblk, double& s0, double& s1) {
+  const int lane = threadIdx.x & 31;
+  s0 = 0.0;
+  s1 = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    s0 += part[2 * b];
+    s1 += part[2 * b + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+}
+
+// (one warp)
+__global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st) {
+  double rr, rz;
+  warp_sum2(part, nblk, rr, rz);
+  if (threadIdx.x != 0) return;
+  st->rr0 = rr;
+  st->rz = rz;
+  st->alpha = 0.0;
+  st->beta = 0.0;
+  st->iters = 0;
+  st->done = (rr > 0.0 && rz > 0.0) ? 0 : 1;
+}
+
+// alpha = r.z / p.Ap from the partials of p . Ap (dot_partial_kernel; one warp)
+__global__ void cg_alpha_kernel(const double* part, int nblk, CGState* st) {
+  double pap = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 32) pap += part[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pap += __shfl_xor_sync(0xffffffffu, pap, o);
+  if (threadIdx.x != 0) return;
+  st->alpha = 0.0;
+  if (st->done) return;
+  ++st->iters;
+  if (!(pap > 0.0)) {
+    st->done = 1;
+    return;
+  }
+  st->alpha = st->rz / pap;
+}
+
+// d += alpha p, r -= alpha Ap, z = M^{-1} r; partials of r . r and r . z
+__global__ void cg_update_kernel(long n, int ku, const CGState* st, const double* p, const double* Ap,
+                                 const double* diag, double* d, double* r, double* z, double* part) {
+  const double a = st->alpha;
+  const bool live = !st->done;
+  double s0 = 0.0, s1 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double ri = r[i];
+    if (live) {
+      d[i] += a * p[i];
+      ri -= a * Ap[i];
+      r[i] = ri;
+      const double zi = ri * cg_precond(diag, st, i, ku);
+      z[i] = zi;
+      s1 += ri * zi;
+    }
+    s0 += ri * ri;
+  }
+  block_dot2(s0, s1, part);
+}
+
+// convergence test and beta; inside the solve's graph (use_cond) sets its loop
+// condition: continue while not done (one warp)
+__global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsigned long long cond_handle,
+                               int use_cond) {
+  double rr, rz;
+  warp_sum2(part, nblk, rr, rz);
+  if (threadIdx.x != 0) return;
+  st->beta = 0.0;
+  if (!st->done) {
+    if (!(rr <= st->tol * st->tol * st->rr0) && rr == rr && rz > 0.0 && st->iters < st->max_iters) {
+      st->beta = rz / st->rz;
+      st->rz = rz;
+    } else {
+      st->done = 1;
+    }
+  }
+  if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, st->done ? 0u : 1u);
+}
+
+// p = z + beta p
+__global__ void cg_dir_kernel(long n, const CGState* st, const double* z, double* p) {
+  if (st->done) return;
+  const double b = st->beta;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = z[i] + b * p[i];
+}
+
+// xdir[e][r] = the entry of the free-coordinate vector vfree at element e's mesh
+// coordinate r (node ev[e][r / dim], direction r % dim), 0 on fixed coordinates
+// (pos: the free position of each coordinate, -1 if fixed)
+__global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, const int* pos, const double* vfree,
+                                 double* xdir) {
+  const int nxe = nv * dim;
+  const long total = n_elems * nxe;
+  for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (long)gridDim.x * blockDim.x) {
+    const long e = j / nxe;
+    const int r = (int)(j - e * nxe);
+    const int q = pos[(long)ev[e * nv + r / dim] * dim + r % dim];
+    xdir[j] = q >= 0 ? vfree[q] : 0.0;
+  }
+}
+
+// out[j] = gx[idx[j]] + lam v[j] with lam read from the solve's scalars
+__global__ void gather_free_lam_kernel(const int* idx, int nfree, const double* gx, const double* v,
+                                       const CGState* st, double* out) {
+  const double lam = st->lam;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x)
+    out[j] = gx[idx[j]] + lam * v[j];
+}
+
 // out[j] = gx[idx[j]] + lam v[j] (the free-coordinate rows of J^T J v + lambda v)
 __global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
                                    double* out) {

@@ -42,4 +42,19 @@ struct LMState {
   double trial[LM_KMAX];  // point of the next assembly (w | tau)
 };
 
+// Device-resident scalars of the snapshot alignment's preconditioned conjugate-
+// gradient solve (one CUDA graph per Levenberg-Marquardt step; see cg_*_kernel).
+struct CGState {
+  double lam;    // damping of the mesh rows
+  double tol;    // stop when |r| <= tol |r_0|
+  double rz;     // r . z of the current iterate
+  double rr0;    // |r_0|^2
+  double alpha;  // step length of the current iteration (0 once done)
+  double beta;   // direction update of the current iteration
+  int done;      // converged, broken down or out of iterations: later iterations change nothing
+  int iters;     // products with the normal matrix taken
+  int max_iters;
+  int pad;
+};
+
 }  // namespace ift

@@ -51,7 +51,8 @@ class Config(ctypes.Structure):
 class AlignInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("trials", ctypes.c_int), ("J", ctypes.c_double), ("gnorm", ctypes.c_double),
-                ("g0", ctypes.c_double)]
+                ("g0", ctypes.c_double), ("ms_form", ctypes.c_double), ("ms_cg", ctypes.c_double),
+                ("ms_search", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -322,7 +323,8 @@ class Context:
                               ctypes.byref(info))
         self._check(st, allow_positive=True)
         return {"status": int(st), "w": w, "x": x, "iters": info.iters, "cg_iters": info.cg_iters,
-                "trials": info.trials, "J": info.J, "gnorm": info.gnorm, "g0": info.g0}
+                "trials": info.trials, "J": info.J, "gnorm": info.gnorm, "g0": info.g0,
+                "ms_form": info.ms_form, "ms_cg": info.ms_cg, "ms_search": info.ms_search}
 
     def solve_rom(self, mu, y0=None, z0=None):
         y = np.zeros(self.ku) if y0 is None else _f64(y0).copy()
