@@ -53,20 +53,22 @@ __global__ void xpby_kernel(long n, const double* x, double beta, double* y);
 __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x);
 __global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
                                    double* out);
-__global__ void sum_columns_warp_kernel(const double* part, int nparts, int ku, double* out);
 __global__ void cg_start_kernel(long n, int ku, const double* g, const double* diag, const CGState* st, double* d,
                                 double* r, double* z, double* p, double* part);
 __global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st);
-__global__ void cg_alpha_kernel(const double* part, int nblk, CGState* st);
-__global__ void cg_update_kernel(long n, int ku, const CGState* st, const double* p, const double* Ap,
-                                 const double* diag, double* d, double* r, double* z, double* part);
+__global__ void cg_update_kernel(long n, int ku, const double* pap_part, int nblk, CGState* st, const double* p,
+                                 const double* Ap, const double* diag, double* d, double* r, double* z,
+                                 double* part);
+__global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
+                                    const int* idx, int nfree, const double* gx, const CGState* st, double* Ap,
+                                    double* dotpart);
 __global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsigned long long cond_handle,
                                int use_cond);
 __global__ void cg_dir_kernel(long n, const CGState* st, const double* z, double* p);
-__global__ void gather_free_lam_kernel(const int* idx, int nfree, const double* gx, const double* v,
-                                       const CGState* st, double* out);
 __global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, const int* pos, const double* vfree,
                                  double* xdir);
+__global__ void align_wrows_kernel(const double* part, int nparts, int ku, const double* H, const double* dw,
+                                   int mode, double* out);
 }  // namespace ift
 
 using namespace ift;
@@ -1868,10 +1870,13 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
 // unknowns. Levenberg-Marquardt on the full space. At each accepted point one
 // element pass stores every element's share of the Gauss-Newton system, M_e =
 // A_e^T A_e (+ the distortion term) and g_e = A_e^T R_e (+ dN_e N_e), with
-// A_e = [dR_e/dw | dR_e/dx_e], in HBM (align_jac_kernel); the normal equations are
+// A_e = [dR_e/dw | dR_e/dx_e], in HBM: the blocks that touch the element's mesh
+// coordinates per element, the state block summed over the elements (H_ww, the
+// state coefficients being shared) (align_jac_kernel). The normal equations are
 // then solved by Jacobi-preconditioned conjugate gradients whose products J^T J v
-// read those blocks once each (align_apply_kernel), the whole solve one CUDA graph
-// with a device-side loop. The line search evaluates F alone (align_kernel mode 0).
+// read those blocks once each (align_apply_kernel, align_wrows_kernel), the whole
+// solve one CUDA graph with a device-side loop. The line search evaluates F alone
+// (align_kernel mode 0).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1879,12 +1884,14 @@ constexpr int kDotBlocks = 120;
 
 struct AlignWork {
   long Nu = 0, Ne = 0, Nx = 0;
-  int ku = 0, nfree = 0, nu = 0, nxe = 0, agrid = 1, awarps = 1;
+  int ku = 0, nfree = 0, nu = 0, nxe = 0, agrid = 1, awarps = 1, jgrid = 1;
   double *w = nullptr, *x = nullptr, *F = nullptr, *dU = nullptr, *dx = nullptr, *dF = nullptr, *gU = nullptr,
          *gx = nullptr, *wt = nullptr, *xt = nullptr, *Ft = nullptr, *part = nullptr, *nbad = nullptr;
   double *g = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr,
          *diag = nullptr;                                  // unknowns' space
   double *M = nullptr, *ge = nullptr, *apart = nullptr;  // element systems, CTA partials of the w rows
+  double *H = nullptr, *hpart = nullptr;                 // H_ww (packed) and its CTA partials
+  double* part2 = nullptr;                               // CG partials of r . r and r . z
   double* xdir = nullptr;                                  // a mesh direction in element order
   CGState* cg = nullptr;
   int *free_idx = nullptr, *pos = nullptr;  // free coordinates; free position of each coordinate (-1: fixed)
@@ -1894,7 +1901,7 @@ struct AlignWork {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap, &z,
-                       &diag, &M, &ge, &apart, &xdir})
+                       &diag, &M, &ge, &apart, &xdir, &H, &hpart, &part2})
       dfree(*q);
     dfree(cg);
     dfree(free_idx);
@@ -1928,8 +1935,11 @@ struct AlignWork {
       B(Ap, n);
       B(z, n);
       B(diag, n);
-      B(M, Ne * (long)(ku + nxe) * (ku + nxe));
+      B(M, Ne * (long)(ku * nxe + nxe * nxe));
       B(ge, Ne * (long)(ku + nxe));
+      B(H, (long)ku * (ku + 1) / 2);
+      B(part2, 2 * kDotBlocks);
+      B(hpart, (long)jgrid * ku * (ku + 1) / 2);
       B(apart, (long)agrid * ku);
       B(xdir, Ne * nxe);
       if (e == cudaSuccess) e = dalloc(cg, 1);
@@ -1997,6 +2007,7 @@ ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double*
   if (stored) {
     if (!c->ks[0].align_apply_plan) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
     CK(c->ks[0].align_apply_plan(W.ku, W.Ne, c->sm_count, &W.awarps, &W.agrid), "alignment product shape");
+    CK(c->ks[0].align_jac_plan(W.ku, W.Ne, 2, c->sm_count, &W.jgrid), "alignment Jacobian pass shape");
   }
   CK(W.alloc(stored), "alignment buffers");
   const int nmu = (c->dim == 1) ? 1 : 2;
@@ -2015,7 +2026,10 @@ ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
     return c->fail(IFT_ERR_ARG, "alignment Jacobian pass needs too much shared memory");
   AsmArgs<double> a = align_args(c, W.w, W.x);
   CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
-  CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, 2, c->sm_count, s), "alignment Jacobian pass");
+  CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, W.hpart, 2, W.jgrid, s), "alignment Jacobian pass");
+  const int nh = W.ku * (W.ku + 1) / 2;
+  reduce_partials_kernel<<<(nh + 31) / 32, 256, 0, s>>>(W.hpart, W.jgrid, nh, W.H, nullptr);
+  CK(cudaGetLastError(), "H_ww");
   J = 0.5 * align_dot(W, W.F, W.F, W.Nu + W.Ne, s);
   double nb = 0.0;
   CK(cudaMemcpy(&nb, W.nbad, 8, cudaMemcpyDeviceToHost), "read count");
@@ -2023,36 +2037,34 @@ ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
   return IFT_OK;
 }
 
-// out (unknowns' space) from the stored blocks: mode 0 J^T J v (+ lam v on the
-// free rows, lam from the solve's scalars), 1 J^T F, 2 diag(J^T J).
-ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, const double* v, double* out, cudaStream_t s) {
+// out (unknowns' space) from the element systems: mode 1 J^T F, 2 diag(J^T J)
+// (the CG body forms mode 0, J^T J v, itself).
+ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, double* out, cudaStream_t s) {
   const KernelSet& ks = c->ks[0];
-  if (mode == 0)
-    align_dir_kernel<<<vec_grid(W.Ne * W.nxe), 256, 0, s>>>(c->d_ev, W.Ne, c->nv, c->dim, W.pos, v + W.ku, W.xdir);
   CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
-  CK(ks.align_apply(mode, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, v, W.apart, W.gx, W.agrid, W.awarps, s),
+  CK(ks.align_apply(mode, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, nullptr, W.apart, W.gx, W.agrid, W.awarps, s),
      "alignment product");
-  sum_columns_warp_kernel<<<(W.ku + 7) / 8, 256, 0, s>>>(W.apart, W.agrid, W.ku, out);
-  if (W.nfree > 0) {
-    if (mode == 0)
-      gather_free_lam_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, v + W.ku, W.cg,
-                                                               out + W.ku);
-    else
-      gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, nullptr, 0.0, out + W.ku);
-  }
+  align_wrows_kernel<<<(W.ku + 7) / 8, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, nullptr, mode, out);
+  if (W.nfree > 0)
+    gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, nullptr, 0.0, out + W.ku);
   CK(cudaGetLastError(), "alignment product");
   return IFT_OK;
 }
 
-// The CG loop body: Ap = (J^T J + lam D) p, then one preconditioned CG update.
+// The CG loop body: Ap = (J^T J + lam D) p with the partials of p . Ap, then one
+// preconditioned CG update (the r partials in a second buffer).
 ift_status align_cg_body(ift_ctx* c, AlignWork& W, cudaStream_t s, unsigned long long handle, int use_cond) {
+  const KernelSet& ks = c->ks[0];
   const long n = W.ku + W.nfree;
-  ift_status st = align_apply(c, W, 0, W.p, W.Ap, s);
-  if (st != IFT_OK) return st;
-  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(W.p, W.Ap, n, W.part);
-  cg_alpha_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg);
-  cg_update_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.cg, W.p, W.Ap, W.diag, W.d, W.r, W.z, W.part);
-  cg_beta_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg, handle, use_cond);
+  align_dir_kernel<<<vec_grid(W.Ne * W.nxe), 256, 0, s>>>(c->d_ev, W.Ne, c->nv, c->dim, W.pos, W.p + W.ku, W.xdir);
+  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
+  CK(ks.align_apply(0, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, W.p, W.apart, W.gx, W.agrid, W.awarps, s),
+     "alignment product");
+  align_finish_kernel<<<kDotBlocks, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, W.p, W.free_idx, W.nfree, W.gx, W.cg,
+                                                 W.Ap, W.part);
+  cg_update_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.part, kDotBlocks, W.cg, W.p, W.Ap, W.diag, W.d, W.r, W.z,
+                                              W.part2);
+  cg_beta_kernel<<<1, 32, 0, s>>>(W.part2, kDotBlocks, W.cg, handle, use_cond);
   cg_dir_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.cg, W.z, W.p);
   CK(cudaGetLastError(), "conjugate-gradient step");
   return IFT_OK;
@@ -2157,9 +2169,9 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     ift_status q = align_form(c, W, Jv, s);
     if (q != IFT_OK) return q;
     if (!std::isfinite(Jv)) return IFT_OK;
-    q = align_apply(c, W, 1, nullptr, W.g, s);
+    q = align_apply(c, W, 1, W.g, s);
     if (q != IFT_OK) return q;
-    q = align_apply(c, W, 2, nullptr, W.diag, s);
+    q = align_apply(c, W, 2, W.diag, s);
     if (q != IFT_OK) return q;
     gn = std::sqrt(align_dot(W, W.g, W.g, n, s));
     return IFT_OK;

@@ -2306,38 +2306,41 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
   }
 }
 
-// Snapshot alignment with stored element blocks: per element, one warp forms
+// Snapshot alignment with stored element systems: per element, one warp forms
 //   A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' | dR_e/dx_e]   (n_u x k, k = k_u + n_xe),
 // the fused assembly's columns with the unit directions of the element's node
 // coordinates in place of Psi_e (an identity Psi_e in shared memory), at (w, x) with
-// x in place of the reference nodes, and stores the element's share of the
-// Gauss-Newton system of (1/2)|F|^2, F = [R; N]:
-//   M_e = A_e^T A_e + [0 0; 0 dN_e^T dN_e]   (k x k, row-major, Mout[e]),
-//   g_e = A_e^T R_e + [0; dN_e^T N_e]        (k, gout[e]),
-// with R_e and N_e into F (as align_kernel mode 0) and the non-physical count into
-// nbad[0]. J^T J = sum_e M_e and J^T F = sum_e g_e over the elements' unknowns, so
-// every product of the Levenberg-Marquardt step reads these blocks
-// (align_apply_kernel) instead of differentiating the element again; M_e holds
-// half the arithmetic of applying A_e and A_e^T in turn (the FP64 pipe bounds it).
-// Lane c forms column c of M_e (and g_c); rows are written coalesced.
+// x in place of the reference nodes. The element's share of the Gauss-Newton
+// system of (1/2)|F|^2, F = [R; N], is M_e = A_e^T A_e + [0 0; 0 dN_e^T dN_e] and
+// g_e = A_e^T R_e + [0; dN_e^T N_e]. The state coefficients w are shared by every
+// element, so the w-w blocks enter the products only through their sum
+//   H_ww = sum_e (M_e)_ww   (the reduced Gauss-Newton matrix of the state block),
+// accumulated per warp and written per CTA (packed upper triangle, acc_h order)
+// into hpart[block]; per element the kernel stores
+//   (M_e)_wx (k_u x n_xe, row-major) then (M_e)_xx (n_xe x n_xe) into Mout[e]
+//   (k_u n_xe + n_xe^2 doubles), g_e into gout[e] (k),
+// R_e and N_e into F (as align_kernel mode 0) and the non-physical count into nbad[0].
 template <class T, int PROB, int P>
 __global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const double* Xref, double* Mout,
-                                                        double* gout, double* F, double* nbad) {
+                                                        double* gout, double* F, double* nbad, double* hpart) {
   using Dd = Disc<PROB, P>;
   using Core = ElemCore<T, PROB, P, true>;
+  using Lay = WarpLayout<T, PROB, P, true>;
   constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int ku = a.ku, k = ku + NXE;
+  const int ku = a.ku, k = ku + NXE, nh = ku * (ku + 1) / 2, S = ku * NXE + NXE * NXE;
   T *tab, *wT;
   double* tauD;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
   const size_t cb = cta_bytes<T, PROB, P>(ku, a.kx);
-  const size_t wb = WarpLayout<T, PROB, P, true>(ku, NXE).bytes;
+  const Lay L(ku, NXE);
   Core C;
-  C.carve(smem + cb + warp * wb, ku, NXE);
+  C.carve(smem + cb + warp * L.bytes, ku, NXE);
   bind_tables(C, tab);
   for (int i = lane; i < NXE * NXE; i += 32) C.Psie[i] = (i / NXE == i % NXE) ? 1.0 : 0.0;
+  T* hacc = C.acc;  // this warp's H_ww (nh <= acc_count(k) entries)
+  for (int i = lane; i < nh; i += 32) hacc[i] = T(0);
   __syncthreads();
   const long Nu = (long)a.n_items * NU;
   for (long e = (long)blockIdx.x * nw + warp; e < a.n_items; e += (long)gridDim.x * nw) {
@@ -2353,23 +2356,27 @@ __global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const doub
     C.jac_geom(lane, a.mu, ku, NXE, k, false);
     __syncwarp();
     const double Ne = C.dN[NXE];
-    double* Me = Mout + (size_t)e * k * k;
-    for (int c0 = 0; c0 < k; c0 += 32) {
-      const int c = c0 + lane;
-      if (c < k) {
-        const double dnc = c >= ku ? C.dN[c - ku] : 0.0;
-        double gc = dnc * Ne;
-        for (int i = 0; i < NU; ++i) gc += (double)C.A[i * k + c] * (double)C.R[i];
-        gout[(size_t)e * k + c] = gc;
-      }
-      for (int j = 0; j < k; ++j) {
-        if (c < k) {
-          double m = 0.0;
+    double* Me = Mout + (size_t)e * S;
+    auto dot = [&](int j, int c) {
+      double m = 0.0;
 #pragma unroll 8
-          for (int i = 0; i < NU; ++i) m += (double)C.A[i * k + j] * (double)C.A[i * k + c];
-          if (c >= ku && j >= ku) m += C.dN[j - ku] * C.dN[c - ku];
-          Me[(size_t)j * k + c] = m;
-        }
+      for (int i = 0; i < NU; ++i) m += (double)C.A[i * k + j] * (double)C.A[i * k + c];
+      return m;
+    };
+    for (int c = lane; c < k; c += 32) {
+      const double dnc = c >= ku ? C.dN[c - ku] : 0.0;
+      double gc = dnc * Ne;
+      for (int i = 0; i < NU; ++i) gc += (double)C.A[i * k + c] * (double)C.R[i];
+      gout[(size_t)e * k + c] = gc;
+      if (c < ku) {
+        // column c of H_ww (rows j <= c), the row c of (M_e)_wx
+        for (int j = 0; j <= c; ++j) hacc[acc_h(j, c, ku)] += (T)dot(j, c);
+#pragma unroll
+        for (int r = 0; r < NXE; ++r) Me[c * NXE + r] = dot(c, ku + r);
+      } else {
+        const int r = c - ku;
+#pragma unroll
+        for (int q = 0; q < NXE; ++q) Me[ku * NXE + q * NXE + r] = dot(ku + q, c) + C.dN[q] * C.dN[r];
       }
     }
     for (int i = lane; i < NU; i += 32) F[e * NU + i] = (double)C.R[i];
@@ -2379,116 +2386,149 @@ __global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const doub
     }
     __syncwarp();
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    double sacc = 0.0;
+    for (int wi = 0; wi < nw; ++wi) sacc += (double)((const T*)(smem + cb + wi * L.bytes + L.oacc))[i];
+    hpart[(size_t)blockIdx.x * nh + i] = sacc;
+  }
 }
 
-// Shared memory of align_apply_kernel, in doubles: one staging buffer (M_e rows at
-// an odd stride kp = (k_u + n_xe) | 1, the element's mesh direction, the node
-// indices), and per warp two buffers plus v (kp).
+// Elements per warp group of align_apply_kernel mode 0, and its shared memory in
+// doubles: one staging buffer holds the group's (M_e)_wx rows at the odd stride
+// nxp = n_xe | 1, its (M_e)_xx, mesh directions and node indices; a warp has two.
+__host__ __device__ inline int align_group(int nxe) { return 32 / nxe; }
 __host__ __device__ inline int align_apply_buf(int nxe, int nv, int ku) {
-  const int kp = (ku + nxe) | 1;
-  return (ku + nxe) * kp + nxe + (nv + 1) / 2;
+  const int E = align_group(nxe), nxp = nxe | 1;
+  return E * ku * nxp + E * nxe * nxe + E * nxe + (E * nv + 1) / 2;
 }
 __host__ __device__ inline int align_apply_warp_doubles(int nxe, int nv, int ku) {
-  const int kp = (ku + nxe) | 1;
-  return 2 * align_apply_buf(nxe, nv, ku) + kp;
+  return 2 * align_apply_buf(nxe, nv, ku);
 }
 
 // Products with the stored element systems of align_jac_kernel over the unknowns
-// (w, x) (J^T J = sum_e M_e, J^T F = sum_e g_e):
-//   MODE 0: y = J^T J v for v = (dw, dx), the mesh part given per element in xdir
-//           (n_xe values per element, zero on fixed coordinates): y_e = M_e v_e;
-//   MODE 1: y = J^T F: y_e = g_e;
-//   MODE 2: y = diag(J^T J): y_e = diag(M_e).
-// MODE 0: one warp per element, elements strided over the grid; each M_e is staged
-// in shared memory by cp.async, double-buffered (the next element's copies are in
-// flight while the warp works on this one), and lane c forms y_c from column c
-// (= row c; rows at an odd stride of doubles, free of bank conflicts). MODES 1-2
-// read their k values directly. The w rows of y are summed per CTA into
-// part[block][0..ku) (summed over blocks in block order afterwards), the mesh rows
-// added to gx at the element's node coordinates. k_u + n_xe <= 96.
+// (w, x), J^T J = [H_ww, sum_e (M_e)_wx; sum_e (M_e)_xw, sum_e (M_e)_xx] (the mesh
+// blocks at the element's coordinates) and J^T F = sum_e g_e. This kernel forms
+// every part but the H_ww terms (align_wrows_kernel adds those):
+//   MODE 0: for v = (dw, dx), the mesh part given per element in xdir (n_xe values
+//           per element, zero on fixed coordinates):
+//             w rows  sum_e (M_e)_wx dx_e,
+//             mesh rows of element e  (M_e)_xw dw + (M_e)_xx dx_e;
+//   MODE 1: y = g_e (w rows and mesh rows);
+//   MODE 2: the mesh rows of diag(J^T J): diag((M_e)_xx).
+// MODE 0 takes the elements in groups of E = 32 / n_xe consecutive elements per
+// warp (groups strided over the grid), staged in shared memory by cp.async,
+// double-buffered: lane (s, r) forms mesh row r of the group's element s (k_u + n_xe
+// FMAs), lane c accumulates w row c over the group (E n_xe FMAs), so all lanes work
+// on both parts. MODES 1-2: one warp per element, reading their values directly.
+// The w rows are summed per CTA into part[block][0..ku) (summed over blocks in block
+// order afterwards), the mesh rows added to gx at the element's node coordinates.
+// k_u <= 96.
 template <int NXE, int DIM, int MODE>
 __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restrict__ M,
                                                           const double* __restrict__ g, const int* __restrict__ ev,
                                                           const double* __restrict__ xdir, long n_elems, int ku,
                                                           const double* __restrict__ dw, double* part, double* gx) {
-  constexpr int NV = NXE / DIM;
+  constexpr int NV = NXE / DIM, E = 32 / NXE, NXP = NXE | 1;
   extern __shared__ __align__(16) double dsm[];
   __shared__ double sw[96];
   __shared__ double red[8][96];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int k = ku + NXE, kp = k | 1;
-  const int bufd = align_apply_buf(NXE, NV, ku);
-  double* base = dsm + (size_t)warp * align_apply_warp_doubles(NXE, NV, ku);
-  double* v = base + 2 * bufd;
-  if (MODE == 0)
-    for (int i = threadIdx.x; i < ku; i += blockDim.x) sw[i] = dw[i];
-  __syncthreads();
-  auto stage = [&](long ee, double* b) {
-    const double* src = M + (size_t)ee * k * k;
-    for (int j = 0; j < k; ++j)
-      for (int c = lane; c < k; c += 32) cp_async8(&b[j * kp + c], &src[(size_t)j * k + c]);
-    double* o = b + k * kp;
-    if (lane < NXE) cp_async8(&o[lane], &xdir[ee * NXE + lane]);
-    int* vi = (int*)(o + NXE);
-    if (lane < NV) cp_async4(&vi[lane], &ev[ee * NV + lane]);
-  };
+  const int k = ku + NXE, S = ku * NXE + NXE * NXE;
   double accw[3] = {0.0, 0.0, 0.0};
-  const long stride = (long)gridDim.x * nw;
-  long e = (long)blockIdx.x * nw + warp;
-  int cur = 0;
-  if (MODE == 0) {
-    if (e < n_elems) stage(e, base);
+  if constexpr (MODE == 0) {
+    for (int i = threadIdx.x; i < ku; i += blockDim.x) sw[i] = dw[i];
+    __syncthreads();
+    const int bufd = align_apply_buf(NXE, NV, ku);
+    double* base = dsm + (size_t)warp * align_apply_warp_doubles(NXE, NV, ku);
+    // buffer layout: Mwx [E][ku][NXP] | Mxx [E][NXE][NXE] | xd [E][NXE] | node ints [E][NV]
+    auto stage = [&](long e0, int cnt, double* b) {
+      const double* src = M + (size_t)e0 * S;
+      for (int t = lane; t < cnt * S; t += 32) {
+        const int sl = t / S, o = t - sl * S;
+        if (o < ku * NXE) {
+          const int c = o / NXE, r = o - c * NXE;
+          cp_async8(&b[(sl * ku + c) * NXP + r], &src[t]);
+        } else {
+          cp_async8(&b[E * ku * NXP + sl * NXE * NXE + (o - ku * NXE)], &src[t]);
+        }
+      }
+      double* xd = b + E * ku * NXP + E * NXE * NXE;
+      if (lane < cnt * NXE) cp_async8(&xd[lane], &xdir[e0 * NXE + lane]);
+      int* vi = (int*)(xd + E * NXE);
+      if (lane < cnt * NV) cp_async4(&vi[lane], &ev[e0 * NV + lane]);
+    };
+    const long ngroups = (n_elems + E - 1) / E, stride = (long)gridDim.x * nw;
+    long gi = (long)blockIdx.x * nw + warp;
+    int cur = 0;
+    auto count = [&](long gg) { return (int)min((long)E, n_elems - gg * E); };
+    if (gi < ngroups) stage(gi * E, count(gi), base);
     cp_async_commit();
-  }
-  for (; e < n_elems; e += stride) {
-    const int* vi;
-    const double* Mb = nullptr;
-    if constexpr (MODE == 0) {
-      const long en = e + stride;
-      if (en < n_elems) stage(en, base + (cur ^ 1) * bufd);
+    for (; gi < ngroups; gi += stride) {
+      const long gn = gi + stride;
+      if (gn < ngroups) stage(gn * E, count(gn), base + (cur ^ 1) * bufd);
       cp_async_commit();
       cp_async_wait_prev();
       __syncwarp();
-      Mb = base + cur * bufd;
-      const double* o = Mb + k * kp;
-      vi = (const int*)(o + NXE);
-      for (int c = lane; c < k; c += 32) v[c] = c < ku ? sw[c] : o[c - ku];
-      __syncwarp();
-    } else {
-      vi = ev + e * NV;
-    }
+      const int cnt = count(gi);
+      const double* Mwx = base + cur * bufd;
+      const double* Mxx = Mwx + E * ku * NXP;
+      const double* xd = Mxx + E * NXE * NXE;
+      const int* vi = (const int*)(xd + E * NXE);
+      // mesh rows: lane (sl, r)
+      if (lane < cnt * NXE) {
+        const int sl = lane / NXE, r = lane - sl * NXE;
+        const double* mw = Mwx + sl * ku * NXP + r;
+        double y = 0.0;
+#pragma unroll 4
+        for (int c = 0; c < ku; ++c) y += mw[c * NXP] * sw[c];
+        const double* mx = Mxx + sl * NXE * NXE + r;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const int c = ch * 32 + lane;
-      if (c < k) {
-        double y;
-        if constexpr (MODE == 0) {
-          y = 0.0;
-#pragma unroll 8
-          for (int j = 0; j < k; ++j) y += Mb[j * kp + c] * v[j];
-        } else if constexpr (MODE == 1) {
-          y = g[(size_t)e * k + c];
-        } else {
-          y = M[(size_t)e * k * k + (size_t)c * k + c];
-        }
-        const int r = c - ku;
-        if (r >= 0) atomicAdd(&gx[vi[r / DIM] * DIM + (r % DIM)], y);
-        else accw[ch] += y;
+        for (int q = 0; q < NXE; ++q) y += mx[q * NXE] * xd[sl * NXE + q];
+        atomicAdd(&gx[vi[sl * NV + r / DIM] * DIM + (r % DIM)], y);
       }
-    }
-    if constexpr (MODE == 0) {
+      // w rows: lane c over the group's elements
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const int c = ch * 32 + lane;
+        if (c < ku) {
+          double y = 0.0;
+          for (int sl = 0; sl < cnt; ++sl) {
+            const double* mw = Mwx + (sl * ku + c) * NXP;
+#pragma unroll
+            for (int r = 0; r < NXE; ++r) y += mw[r] * xd[sl * NXE + r];
+          }
+          accw[ch] += y;
+        }
+      }
       __syncwarp();
       cur ^= 1;
     }
+    cp_async_wait_all();
+  } else {
+    for (long e = (long)blockIdx.x * nw + warp; e < n_elems; e += (long)gridDim.x * nw) {
+      const int* vi = ev + e * NV;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const int c = ch * 32 + lane;
+        if (c < k) {
+          const int r = c - ku;
+          double y;
+          if constexpr (MODE == 1) y = g[(size_t)e * k + c];
+          else y = r >= 0 ? M[(size_t)e * S + ku * NXE + r * NXE + r] : 0.0;
+          if (r >= 0) atomicAdd(&gx[vi[r / DIM] * DIM + (r % DIM)], y);
+          else accw[ch] += y;
+        }
+      }
+    }
   }
-  if (MODE == 0) cp_async_wait_all();
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) red[warp][ch * 32 + lane] = accw[ch];
   __syncthreads();
   for (int c = threadIdx.x; c < ku; c += blockDim.x) {
-    double s = 0.0;
-    for (int wi = 0; wi < nw; ++wi) s += red[wi][c];
-    part[(size_t)blockIdx.x * ku + c] = s;
+    double sacc = 0.0;
+    for (int wi = 0; wi < nw; ++wi) sacc += red[wi][c];
+    part[(size_t)blockIdx.x * ku + c] = sacc;
   }
 }
 

@@ -164,10 +164,9 @@ struct KernelSetImpl {
   static size_t align_jac_smem(int ku, int warps) {
     return cta_bytes<T, PROB, P>(ku, 0) + (size_t)warps * WarpLayout<T, PROB, P, true>(ku, Disc<PROB, P>::NXE).bytes;
   }
-  static cudaError_t align_jac(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
-                               int warps, int sm_count, cudaStream_t s) {
-    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
-    const size_t smem = align_jac_smem(a.ku, warps);
+  // resident CTAs of `warps` warps on sm_count SMs, at most one warp per element
+  static cudaError_t align_jac_plan(int ku, long n, int warps, int sm_count, int* grid) {
+    const size_t smem = align_jac_smem(ku, warps);
     cudaError_t e = cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -175,21 +174,28 @@ struct KernelSetImpl {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, align_jac_kernel<T, PROB, P>, 32 * warps, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    long grid = (a.n_items + warps - 1) / warps;
-    if (grid > (long)sm_count * occ) grid = (long)sm_count * occ;
-    if (grid < 1) grid = 1;
-    align_jac_kernel<T, PROB, P><<<(int)grid, 32 * warps, smem, s>>>(a, Xref, M, g, F, nbad);
+    long g = (n + warps - 1) / warps;
+    if (g > (long)sm_count * occ) g = (long)sm_count * occ;
+    *grid = (int)(g < 1 ? 1 : g);
+    return cudaSuccess;
+  }
+  static cudaError_t align_jac(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
+                               double* hpart, int warps, int grid, cudaStream_t s) {
+    const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
+    align_jac_kernel<T, PROB, P><<<grid, 32 * warps, align_jac_smem(a.ku, warps), s>>>(a, Xref, M, g, F, nbad,
+                                                                                       hpart);
     return cudaGetLastError();
   }
   static size_t align_apply_smem(int ku, int warps) {
     using Dd = Disc<PROB, P>;
     return (size_t)warps * align_apply_warp_doubles(Dd::NXE, Dd::NXE / Dd::DIM, ku) * sizeof(double);
   }
-  // warps per CTA (as many as fit 200 KB of staging, at most 8) and the grid (resident
-  // CTAs of the product kernel on sm_count SMs, at most one warp per element)
+  // warps per CTA (as many as fit 96 KB of staging, so that two CTAs share an SM; at
+  // most 8) and the grid (resident CTAs of the product kernel on sm_count SMs, at
+  // most one warp per element group)
   static cudaError_t align_apply_plan(int ku, long n, int sm_count, int* warps, int* grid) {
     const size_t per = align_apply_smem(ku, 1);
-    int w = (int)((200u * 1024u) / (per > 0 ? per : 1));
+    int w = (int)((96u * 1024u) / (per > 0 ? per : 1));
     w = w < 1 ? 1 : (w > 8 ? 8 : w);
     const size_t smem = align_apply_smem(ku, w);
     using Dd = Disc<PROB, P>;
@@ -201,7 +207,8 @@ struct KernelSetImpl {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * w, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    long g = (n + w - 1) / w;
+    const long groups = (n + align_group(Dd::NXE) - 1) / align_group(Dd::NXE);
+    long g = (groups + w - 1) / w;
     if (g > (long)sm_count * occ) g = (long)sm_count * occ;
     *warps = w;
     *grid = (int)(g < 1 ? 1 : g);
@@ -211,7 +218,7 @@ struct KernelSetImpl {
                                  long n, int ku, const double* dw, double* part, double* gx, int grid, int warps,
                                  cudaStream_t s) {
     using Dd = Disc<PROB, P>;
-    if (ku + Dd::NXE > 96 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
+    if (ku > 96 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
     const int block = 32 * warps;
     if (mode == 0)
       align_apply_kernel<Dd::NXE, Dd::DIM, 0><<<grid, block, align_apply_smem(ku, warps), s>>>(M, g, ev, xdir, n,
@@ -263,6 +270,7 @@ struct KernelSetImpl {
       k.align_jac_smem = &align_jac_smem;
       k.align_apply = &align_apply;
       k.align_apply_plan = &align_apply_plan;
+      k.align_jac_plan = &align_jac_plan;
       k.blocks_per_sm_grad = &blocks_per_sm_grad;
     }
     k.blocks_per_sm_norms = &blocks_per_sm_norms;

@@ -36,14 +36,16 @@ struct KernelSet {
   cudaError_t (*align)(int mode, const void* args, const double* Xref, const double* vU, const double* vx,
                        const double* vN, double* outU, double* outX, int grid, int block, size_t smem,
                        cudaStream_t s) = nullptr;
-  // FP64 sets: snapshot alignment with stored element systems. align_jac writes
-  // M_e (k x k, k = k_u + n_xe), g_e (k) and F at the state of args (grid: resident
-  // CTAs of `warps` warps on sm_count SMs); align_apply forms mode 0 J^T J v,
-  // 1 J^T F, 2 diag(J^T J) from them (see align_apply_kernel; xdir: the mesh
-  // direction per element for mode 0; part: grid x k_u), with the launch shape of
-  // align_apply_plan
+  // FP64 sets: snapshot alignment with stored element systems. align_jac writes per
+  // element (M_e)_wx and (M_e)_xx (k_u n_xe + n_xe^2 doubles), g_e (k = k_u + n_xe)
+  // and F, and per CTA its part of H_ww (packed, hpart: grid x k_u (k_u + 1) / 2), at
+  // the state of args, in the grid of align_jac_plan; align_apply forms the
+  // non-H_ww parts of mode 0 J^T J v, 1 J^T F, 2 diag(J^T J) (see align_apply_kernel;
+  // xdir: the mesh direction per element for mode 0; part: grid x k_u), in the launch
+  // shape of align_apply_plan
+  cudaError_t (*align_jac_plan)(int ku, long n, int warps, int sm_count, int* grid) = nullptr;
   cudaError_t (*align_jac)(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
-                           int warps, int sm_count, cudaStream_t s) = nullptr;
+                           double* hpart, int warps, int grid, cudaStream_t s) = nullptr;
   size_t (*align_jac_smem)(int ku, int warps) = nullptr;
   cudaError_t (*align_apply)(int mode, const double* M, const double* g, const int* ev, const double* xdir, long n,
                              int ku, const double* dw, double* part, double* gx, int grid, int warps,

@@ -582,16 +582,27 @@ __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, 
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) x[idx[j]] = v[j];
 }
 
-// out[c] = sum_b part[b][c] in block order, one warp per column (lanes take
-// strided rows, then a fixed butterfly: deterministic for a fixed nparts)
-__global__ void sum_columns_warp_kernel(const double* part, int nparts, int ku, double* out) {
+// The w rows of the alignment products: out[c] = sum_b part[b][c] (block order) plus
+// mode 0: (H_ww dw)_c, mode 2: H_ww[c][c], mode 1: nothing (H packed upper, acc_h
+// order); one warp per row.
+__global__ void align_wrows_kernel(const double* part, int nparts, int ku, const double* H, const double* dw,
+                                   int mode, double* out) {
   const int lane = threadIdx.x & 31, c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= ku) return;
   double s = 0.0;
   for (int b = lane; b < nparts; b += 32) s += part[(size_t)b * ku + c];
+  if (mode == 0) {
+    for (int j = lane; j < ku; j += 32) {
+      const int r = j < c ? j : c, b = j < c ? c : j;
+      s += H[r * ku - (r * (r - 1)) / 2 + (b - r)] * dw[j];
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[c] = s;
+  if (lane == 0) {
+    if (mode == 2) s += H[c * ku - (c * (c - 1)) / 2];
+    out[c] = s;
+  }
 }
 
 // Preconditioned conjugate gradients on (J^T J + lam D) d = -g with the Jacobi
@@ -654,6 +665,55 @@ __device__ __forceinline__ void warp_sum2(const double* part, int nblk, double& 
   }
 }
 
+// Ap = (J^T J + lam D) p from the product kernel's outputs, and the partials of
+// p . Ap (block b into dotpart[b]; 256 threads): the free mesh rows
+// Ap[ku + j] = gx[idx[j]] + lam p[ku + j], and (block 0) the w rows
+// Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper, acc_h order).
+__global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
+                                    const int* idx, int nfree, const double* gx, const CGState* st, double* Ap,
+                                    double* dotpart) {
+  __shared__ double sh[256];
+  __shared__ double wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double lam = st->lam;
+  double s = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
+    const double a = gx[idx[j]] + lam * p[ku + j];
+    Ap[ku + j] = a;
+    s += p[ku + j] * a;
+  }
+  if (blockIdx.x == 0) {
+    double ws = 0.0;
+    for (int c = warp; c < ku; c += 8) {
+      double t = 0.0;
+      for (int b = lane; b < nparts; b += 32) t += part[(size_t)b * ku + c];
+      for (int j = lane; j < ku; j += 32) {
+        const int r = j < c ? j : c, q = j < c ? c : j;
+        t += H[r * ku - (r * (r - 1)) / 2 + (q - r)] * p[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        Ap[c] = t;
+        ws += p[c] * t;
+      }
+    }
+    if (lane == 0) wsum[warp] = ws;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double t = sh[0];
+    if (blockIdx.x == 0)
+      for (int w = 0; w < 8; ++w) t += wsum[w];
+    dotpart[blockIdx.x] = t;
+  }
+}
+
 // (one warp)
 __global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st) {
   double rr, rz;
@@ -667,28 +727,30 @@ __global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st
   st->done = (rr > 0.0 && rz > 0.0) ? 0 : 1;
 }
 
-// alpha = r.z / p.Ap from the partials of p . Ap (dot_partial_kernel; one warp)
-__global__ void cg_alpha_kernel(const double* part, int nblk, CGState* st) {
-  double pap = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += 32) pap += part[b];
+// alpha = r.z / p.Ap from the partials of p . Ap (pap_part: nblk values, reduced
+// by every block in the same order, so that all blocks take the same decision;
+// block 0 records the iteration), then d += alpha p, r -= alpha Ap,
+// z = M^{-1} r and the partials of r . r and r . z into part (256 threads)
+__global__ void cg_update_kernel(long n, int ku, const double* pap_part, int nblk, CGState* st, const double* p,
+                                 const double* Ap, const double* diag, double* d, double* r, double* z,
+                                 double* part) {
+  __shared__ double sp;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) v += pap_part[b];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) pap += __shfl_xor_sync(0xffffffffu, pap, o);
-  if (threadIdx.x != 0) return;
-  st->alpha = 0.0;
-  if (st->done) return;
-  ++st->iters;
-  if (!(pap > 0.0)) {
-    st->done = 1;
-    return;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sp = v;
   }
-  st->alpha = st->rz / pap;
-}
-
-// d += alpha p, r -= alpha Ap, z = M^{-1} r; partials of r . r and r . z
-__global__ void cg_update_kernel(long n, int ku, const CGState* st, const double* p, const double* Ap,
-                                 const double* diag, double* d, double* r, double* z, double* part) {
-  const double a = st->alpha;
-  const bool live = !st->done;
+  __syncthreads();
+  const double pap = sp;
+  const bool was_done = st->done != 0;
+  const bool live = !was_done && pap > 0.0;
+  const double a = live ? st->rz / pap : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !was_done) {
+    ++st->iters;
+    if (!live) st->done = 1;
+  }
   double s0 = 0.0, s1 = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     double ri = r[i];
@@ -745,14 +807,6 @@ __global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, c
     const int q = pos[(long)ev[e * nv + r / dim] * dim + r % dim];
     xdir[j] = q >= 0 ? vfree[q] : 0.0;
   }
-}
-
-// out[j] = gx[idx[j]] + lam v[j] with lam read from the solve's scalars
-__global__ void gather_free_lam_kernel(const int* idx, int nfree, const double* gx, const double* v,
-                                       const CGState* st, double* out) {
-  const double lam = st->lam;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x)
-    out[j] = gx[idx[j]] + lam * v[j];
 }
 
 // out[j] = gx[idx[j]] + lam v[j] (the free-coordinate rows of J^T J v + lambda v)
