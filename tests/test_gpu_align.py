@@ -139,3 +139,57 @@ def test_alignment_errors():
     ctx = ift.Context.from_workload(wl)
     with pytest.raises(ift.IFTError):
         ctx.align(wl.mus[0], wl.w_eval, wl.X.ravel(), interior_mask(wl.X), tol=-1.0)
+
+
+@pytest.mark.parametrize("n_elems", [12, 37])
+def test_alignment_burgers_first_step(n_elems):
+    # 1-D: two coordinates per element, sixteen elements per warp group of the product
+    # (12: one partial group; 37: 16 + 16 + 5)
+    wl = W.burgers_workload(n_elems=n_elems, p=2, k_u=4, seed=3)
+    O = orc.Oracle.from_workload(wl, kappa=0.1)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = wl.mus[0]
+    X = wl.X.ravel()
+    mask = (X > 1e-12) & (X < 1 - 1e-12)
+    r0 = O.align(wl.Phi, mu, wl.w_eval, X, mask, tol=0.0, max_iters=0)
+    g0 = ctx.align(mu, wl.w_eval, X, mask, tol=0.0, max_iters=0)
+    assert abs(g0["g0"] - r0["g0"]) <= 1e-10 * r0["g0"]
+    assert abs(g0["J"] - r0["J"]) <= 1e-12 * r0["J"]
+    r1 = O.align(wl.Phi, mu, wl.w_eval, X, mask, tol=0.0, max_iters=1)
+    g1 = ctx.align(mu, wl.w_eval, X, mask, tol=0.0, max_iters=1)
+    assert g1["iters"] == r1["iters"] == 1
+    assert np.linalg.norm(g1["w"] - r1["w"]) <= 1e-8 * np.linalg.norm(r1["w"])
+    assert np.abs(g1["x"] - r1["x"]).max() <= 1e-8
+
+
+def test_alignment_burgers_converges_as_the_oracle():
+    wl = W.burgers_workload(n_elems=12, p=2, k_u=4, seed=3)
+    O = orc.Oracle.from_workload(wl, kappa=0.1)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = wl.mus[0]
+    X = wl.X.ravel()
+    mask = (X > 1e-12) & (X < 1 - 1e-12)
+    ref = O.align(wl.Phi, mu, wl.w_eval, X, mask, tol=1e-7, max_iters=300)
+    assert ref["status"] == 0
+    g = ctx.align(mu, wl.w_eval, X, mask, tol=1e-7, max_iters=300)
+    assert g["status"] == 0
+    assert abs(g["J"] - ref["J"]) <= 1e-6 * ref["J"]
+    assert np.abs(g["x"] - ref["x"]).max() <= 1e-5
+    assert np.linalg.norm(g["w"] - ref["w"]) <= 1e-5 * np.linalg.norm(ref["w"])
+
+
+def test_alignment_state_only():
+    # no free mesh coordinate: Levenberg-Marquardt on w alone, the mesh unchanged
+    wl = W.euler_workload(n=3, p=1, k_u=5, k_x=2, seed=4)
+    O = orc.Oracle.from_workload(wl, kappa=0.1)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = np.array([2.1, 0.01])
+    mask = np.zeros(wl.X.size, dtype=bool)
+    ref = O.align(wl.Phi, mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-9, max_iters=100)
+    g = ctx.align(mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-9, max_iters=100)
+    assert ref["status"] == 0 and g["status"] == 0
+    # near 1e-9 the stopping test sits at the rounding floor of J^T F: two FP64
+    # implementations summing in different orders may stop one step apart
+    assert abs(g["iters"] - ref["iters"]) <= 1
+    assert np.array_equal(g["x"], wl.X.ravel())
+    assert np.linalg.norm(g["w"] - ref["w"]) <= 1e-8 * np.linalg.norm(ref["w"])
