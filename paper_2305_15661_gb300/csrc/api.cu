@@ -44,12 +44,8 @@ __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, dou
 __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 __global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states);
-__global__ void phi_matvec_kernel(const double* Phi, long Nu, int ku, const double* v, double* out);
-__global__ void phit_vec_partial_kernel(const double* Phi, long Nu, int ku, const double* g, long chunk,
-                                        double* part);
 __global__ void dot_partial_kernel(const double* a, const double* b, long n, double* part);
 __global__ void axpy_kernel(long n, double alpha, const double* x, double* y);
-__global__ void xpby_kernel(long n, const double* x, double beta, double* y);
 __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x);
 __global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
                                    double* out);

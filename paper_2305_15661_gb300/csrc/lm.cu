@@ -519,36 +519,6 @@ __global__ void sum_columns_kernel(const double* part, int nparts, int ku, doubl
 // Vector kernels of the snapshot alignment's conjugate-gradient solve.
 // ---------------------------------------------------------------------------
 
-// out[i] = sum_c Phi[i][c] v[c] (Phi row-major N_u x ku)
-__global__ void phi_matvec_kernel(const double* Phi, long Nu, int ku, const double* v, double* out) {
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < Nu; i += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < ku; ++c) s += Phi[i * ku + c] * v[c];
-    out[i] = s;
-  }
-}
-
-// Block b: partial column sums of Phi^T g over rows [b chunk, (b + 1) chunk) into
-// part[b][c] (summed in block order by sum_columns_kernel).
-__global__ void phit_vec_partial_kernel(const double* Phi, long Nu, int ku, const double* g, long chunk,
-                                        double* part) {
-  extern __shared__ double sh[];
-  const long r0 = (long)blockIdx.x * chunk;
-  const long r1 = (r0 + chunk < Nu) ? r0 + chunk : Nu;
-  const int lanes_per_col = blockDim.x / ku;
-  const int c = threadIdx.x % ku, sub = threadIdx.x / ku;
-  double s = 0.0;
-  if (sub < lanes_per_col)
-    for (long r = r0 + sub; r < r1; r += lanes_per_col) s += Phi[r * ku + c] * g[r];
-  sh[threadIdx.x] = (sub < lanes_per_col) ? s : 0.0;
-  __syncthreads();
-  if (threadIdx.x < ku) {
-    double t = 0.0;
-    for (int j = 0; j < lanes_per_col; ++j) t += sh[j * ku + threadIdx.x];
-    part[(size_t)blockIdx.x * ku + threadIdx.x] = t;
-  }
-}
-
 // Block b: the partial dot product of a and b over its grid-stride share, into part[b]
 // (summed on the host in block order).
 __global__ void dot_partial_kernel(const double* a, const double* b, long n, double* part) {
@@ -569,12 +539,6 @@ __global__ void dot_partial_kernel(const double* a, const double* b, long n, dou
 __global__ void axpy_kernel(long n, double alpha, const double* x, double* y) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     y[i] += alpha * x[i];
-}
-
-// y = x + beta y
-__global__ void xpby_kernel(long n, const double* x, double beta, double* y) {
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    y[i] = x[i] + beta * y[i];
 }
 
 // x[idx[j]] = v[j] (the free mesh coordinates of a step in the unknowns' space)

@@ -193,3 +193,30 @@ def test_alignment_state_only():
     assert abs(g["iters"] - ref["iters"]) <= 1
     assert np.array_equal(g["x"], wl.X.ravel())
     assert np.linalg.norm(g["w"] - ref["w"]) <= 1e-8 * np.linalg.norm(ref["w"])
+
+
+def test_alignment_full_size_objective():
+    # the bench's alignment (100 x 100 x 2 triangles, p = 2, k_u = 20, interior nodes free):
+    # the objective at the start and after one step equals the oracle's (1/2)|F|^2 at the
+    # GPU's points, the step descends, and the fixed coordinates do not move
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+    O = orc.Oracle.from_workload(wl, kappa=0.1)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = wl.mus[0]
+    mask = interior_mask(wl.X)
+    x0 = wl.X.ravel()
+
+    def objective(w, x):
+        R, N, bad = O.residual(wl.Phi @ w, x, mu)
+        assert bad == 0
+        return 0.5 * (R @ R + N @ N)
+
+    g0 = ctx.align(mu, wl.w_eval, x0, mask, tol=0.0, max_iters=0)
+    J0 = objective(wl.w_eval, x0)
+    assert abs(g0["J"] - J0) <= 1e-12 * J0
+    g1 = ctx.align(mu, wl.w_eval, x0, mask, tol=0.0, max_iters=1)
+    assert g1["iters"] == 1 and g1["cg_iters"] > 0
+    J1 = objective(g1["w"], g1["x"])
+    assert abs(g1["J"] - J1) <= 1e-12 * J1
+    assert J1 < J0
+    assert np.array_equal(g1["x"][~mask], x0[~mask])
