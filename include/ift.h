@@ -391,11 +391,19 @@ ift_status ift_align_jvp(ift_ctx* ctx, const double* mu, const double* w, const 
 ift_status ift_align_vjp(ift_ctx* ctx, const double* mu, const double* w, const double* x, const double* v,
                          double* gU, double* gx);
 
-/* Levenberg-Marquardt on (w, free x) from the given (w, x) (both in/out): each step
-   solves (J^T J + lambda D) d = -J^T F (D = 1 on the mesh coordinates, 0 on w) by
-   conjugate gradients with J v and J^T v applied element by element, then a
-   backtracking line search on (1/2)|F|^2; lambda rules as ift_solve_rom. Stops
-   when |J^T F| <= tol max(1, |J^T F| at the start). Returns info->status. */
+/* Levenberg-Marquardt on (w, free x) from the given (w, x) (both in/out). At each
+   accepted point one element pass stores every element's share of the Gauss-Newton
+   system on the device (the blocks coupling its mesh coordinates, and the state
+   block summed over the elements), k_u n_xe + n_xe^2 + k_u + n_xe doubles per
+   element. Each step then solves (J^T J + lambda D) d = -J^T F (D = 1 on the mesh
+   coordinates, 0 on w) by Jacobi-preconditioned conjugate gradients to a relative
+   residual of 1e-12 (at most min(4 n + 20, 2000) iterations, n the unknowns), run as
+   one CUDA graph, followed by a backtracking line search on (1/2)|F|^2; lambda rules
+   as ift_solve_rom. Stops when |J^T F| <= tol max(1, |J^T F| at the start).
+   free_mask: N_x bytes, non-zero for a free coordinate. Requires k_u + n_xe <= 96.
+   Errors: IFT_ERR_ARG (null pointers, tol < 0, max_iters < 0, sizes),
+   IFT_ERR_NONPHYSICAL (the start is not physical), IFT_ERR_CUDA / IFT_ERR_OOM.
+   Returns info->status (IFT_OK, IFT_NOT_CONVERGED or IFT_LINESEARCH_FAILED). */
 ift_status ift_align(ift_ctx* ctx, const double* mu, double* w, double* x, const uint8_t* free_mask, double tol,
                      int max_iters, ift_align_info* info);
 
