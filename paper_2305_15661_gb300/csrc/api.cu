@@ -47,22 +47,20 @@ __global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res,
 __global__ void dot_partial_kernel(const double* a, const double* b, long n, double* part);
 __global__ void axpy_kernel(long n, double alpha, const double* x, double* y);
 __global__ void scatter_free_kernel(const int* idx, int nfree, const double* v, double* x);
-__global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
-                                   double* out);
 __global__ void cg_start_kernel(long n, int ku, const double* g, const double* diag, const CGState* st, double* d,
-                                double* r, double* z, double* p, double* part);
+                                double* r, double* z, double* p, double* part, const int* off, const int* slots,
+                                double* xdir);
 __global__ void cg_start_finish_kernel(const double* part, int nblk, CGState* st);
 __global__ void cg_update_kernel(long n, int ku, const double* pap_part, int nblk, CGState* st, const double* p,
                                  const double* Ap, const double* diag, double* d, double* r, double* z,
                                  double* part);
 __global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
-                                    const int* idx, int nfree, const double* gx, const CGState* st, double* Ap,
-                                    double* dotpart);
+                                    int nfree, double* gxf, const CGState* st, double* Ap, double* dotpart);
 __global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsigned long long cond_handle,
                                int use_cond);
-__global__ void cg_dir_kernel(long n, const CGState* st, const double* z, double* p);
-__global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, const int* pos, const double* vfree,
-                                 double* xdir);
+__global__ void cg_dir_kernel(long n, int ku, const CGState* st, const double* z, double* p, const int* off,
+                              const int* slots, double* xdir);
+__global__ void take_free_kernel(int nfree, double* gxf, double* out);
 __global__ void align_wrows_kernel(const double* part, int nparts, int ku, const double* H, const double* dw,
                                    int mode, double* out);
 }  // namespace ift
@@ -1888,20 +1886,24 @@ struct AlignWork {
   double *M = nullptr, *ge = nullptr, *apart = nullptr;  // element systems, CTA partials of the w rows
   double *H = nullptr, *hpart = nullptr;                 // H_ww (packed) and its CTA partials
   double* part2 = nullptr;                               // CG partials of r . r and r . z
+  double* gxf = nullptr;                                 // free mesh rows of a product (kept zero between uses)
+  int *efree = nullptr, *soff = nullptr, *slots = nullptr;  // element coordinates' free indices; free -> slots
   double* xdir = nullptr;                                  // a mesh direction in element order
   CGState* cg = nullptr;
-  int *free_idx = nullptr, *pos = nullptr;  // free coordinates; free position of each coordinate (-1: fixed)
+  int* free_idx = nullptr;  // the free coordinates
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~AlignWork() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap, &z,
-                       &diag, &M, &ge, &apart, &xdir, &H, &hpart, &part2})
+                       &diag, &M, &ge, &apart, &xdir, &H, &hpart, &part2, &gxf})
       dfree(*q);
     dfree(cg);
     dfree(free_idx);
-    dfree(pos);
+    dfree(efree);
+    dfree(soff);
+    dfree(slots);
   }
   // stored: the buffers of the Levenberg-Marquardt solve as well
   cudaError_t alloc(bool stored) {
@@ -1935,11 +1937,14 @@ struct AlignWork {
       B(ge, Ne * (long)(ku + nxe));
       B(H, (long)ku * (ku + 1) / 2);
       B(part2, 2 * kDotBlocks);
+      B(gxf, nfree);
+      if (e == cudaSuccess) e = dalloc(efree, (size_t)(Ne * nxe > 0 ? Ne * nxe : 1));
+      if (e == cudaSuccess) e = dalloc(soff, (size_t)nfree + 1);
+      if (e == cudaSuccess) e = dalloc(slots, (size_t)(Ne * nxe > 0 ? Ne * nxe : 1));
       B(hpart, (long)jgrid * ku * (ku + 1) / 2);
       B(apart, (long)agrid * ku);
       B(xdir, Ne * nxe);
       if (e == cudaSuccess) e = dalloc(cg, 1);
-      if (e == cudaSuccess) e = dalloc(pos, (size_t)(Nx > 0 ? Nx : 1));
     }
     if (e == cudaSuccess) e = dalloc(free_idx, (size_t)(nfree > 0 ? nfree : 1));
     return e;
@@ -2037,12 +2042,10 @@ ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
 // (the CG body forms mode 0, J^T J v, itself).
 ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, double* out, cudaStream_t s) {
   const KernelSet& ks = c->ks[0];
-  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
-  CK(ks.align_apply(mode, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, nullptr, W.apart, W.gx, W.agrid, W.awarps, s),
+  CK(ks.align_apply(mode, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, nullptr, W.apart, W.gxf, W.agrid, W.awarps, s),
      "alignment product");
   align_wrows_kernel<<<(W.ku + 7) / 8, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, nullptr, mode, out);
-  if (W.nfree > 0)
-    gather_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.free_idx, W.nfree, W.gx, nullptr, 0.0, out + W.ku);
+  if (W.nfree > 0) take_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.nfree, W.gxf, out + W.ku);
   CK(cudaGetLastError(), "alignment product");
   return IFT_OK;
 }
@@ -2052,16 +2055,14 @@ ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, double* out, cudaStre
 ift_status align_cg_body(ift_ctx* c, AlignWork& W, cudaStream_t s, unsigned long long handle, int use_cond) {
   const KernelSet& ks = c->ks[0];
   const long n = W.ku + W.nfree;
-  align_dir_kernel<<<vec_grid(W.Ne * W.nxe), 256, 0, s>>>(c->d_ev, W.Ne, c->nv, c->dim, W.pos, W.p + W.ku, W.xdir);
-  CK(cudaMemsetAsync(W.gx, 0, W.Nx * 8, s), "zero gx");
-  CK(ks.align_apply(0, W.M, W.ge, c->d_ev, W.xdir, W.Ne, W.ku, W.p, W.apart, W.gx, W.agrid, W.awarps, s),
+  CK(ks.align_apply(0, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, W.p, W.apart, W.gxf, W.agrid, W.awarps, s),
      "alignment product");
-  align_finish_kernel<<<kDotBlocks, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, W.p, W.free_idx, W.nfree, W.gx, W.cg,
-                                                 W.Ap, W.part);
+  align_finish_kernel<<<kDotBlocks, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, W.p, W.nfree, W.gxf, W.cg, W.Ap,
+                                                 W.part);
   cg_update_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.part, kDotBlocks, W.cg, W.p, W.Ap, W.diag, W.d, W.r, W.z,
                                               W.part2);
   cg_beta_kernel<<<1, 32, 0, s>>>(W.part2, kDotBlocks, W.cg, handle, use_cond);
-  cg_dir_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.cg, W.z, W.p);
+  cg_dir_kernel<<<vec_grid(n), 256, 0, s>>>(n, W.ku, W.cg, W.z, W.p, W.soff, W.slots, W.xdir);
   CK(cudaGetLastError(), "conjugate-gradient step");
   return IFT_OK;
 }
@@ -2128,17 +2129,42 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
   if (st != IFT_OK) return st;
   if (!(tol >= 0.0) || max_iters < 0) return c->fail(IFT_ERR_ARG, "tol >= 0 and max_iters >= 0 required");
   {
+    // free coordinates; per element coordinate its free index (-1: fixed); per free
+    // coordinate the element slots that hold it (CSR), for the element-order direction
     std::vector<int> idx, pos((size_t)W.Nx, -1);
     for (long i = 0; i < W.Nx; ++i)
       if (free_mask[i]) {
         pos[(size_t)i] = (int)idx.size();
         idx.push_back((int)i);
       }
+    const long ns = W.Ne * W.nxe;
+    std::vector<int> ev((size_t)W.Ne * c->nv), efree((size_t)ns), off((size_t)W.nfree + 1, 0), slots;
+    CK(cudaMemcpy(ev.data(), c->d_ev, ev.size() * 4, cudaMemcpyDeviceToHost), "read elements");
+    for (long t = 0; t < ns; ++t) {
+      const long e = t / W.nxe;
+      const int r = (int)(t - e * W.nxe);
+      const int q = pos[(size_t)ev[(size_t)e * c->nv + r / c->dim] * c->dim + r % c->dim];
+      efree[(size_t)t] = q;
+      if (q >= 0) ++off[(size_t)q + 1];
+    }
+    for (int j = 0; j < W.nfree; ++j) off[(size_t)j + 1] += off[(size_t)j];
+    slots.resize((size_t)off[(size_t)W.nfree] > 0 ? (size_t)off[(size_t)W.nfree] : 1);
+    {
+      std::vector<int> fill(off.begin(), off.end() - 1);
+      for (long t = 0; t < ns; ++t)
+        if (efree[(size_t)t] >= 0) slots[(size_t)fill[(size_t)efree[(size_t)t]]++] = (int)t;
+    }
     if (!idx.empty()) CK(cudaMemcpy(W.free_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice), "copy idx");
-    CK(cudaMemcpy(W.pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice), "copy positions");
+    CK(cudaMemcpy(W.efree, efree.data(), efree.size() * 4, cudaMemcpyHostToDevice), "copy free indices");
+    CK(cudaMemcpy(W.soff, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "copy slot offsets");
+    CK(cudaMemcpy(W.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice), "copy slots");
   }
   cudaStream_t s = c->stream;
   const long n = W.ku + W.nfree;
+  // the products add into gxf and the finishing kernels zero it behind them; the
+  // fixed coordinates' slots of the element-order direction stay zero
+  CK(cudaMemsetAsync(W.gxf, 0, (W.nfree > 0 ? W.nfree : 1) * 8, s), "zero free rows");
+  CK(cudaMemsetAsync(W.xdir, 0, (W.Ne * W.nxe > 0 ? W.Ne * W.nxe : 1) * 8, s), "zero direction");
   // readings of Sec. 3.2.3 as for the reduced solve: lambda_0 = 1e-4, /10 after a
   // full step, x10 after a shortened one, Armijo 1e-4, at most 30 halvings; damping
   // on the mesh block only (Eq. levmarq-step)
@@ -2239,7 +2265,8 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     cg0.lam = lam;
     CK(cudaEventRecord(ev[0], s), "event");
     CK(cudaMemcpyAsync(W.cg, &cg0, sizeof(CGState), cudaMemcpyHostToDevice, s), "copy solve scalars");
-    cg_start_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.g, W.diag, W.cg, W.d, W.r, W.z, W.p, W.part);
+    cg_start_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.g, W.diag, W.cg, W.d, W.r, W.z, W.p, W.part, W.soff,
+                                               W.slots, W.xdir);
     cg_start_finish_kernel<<<1, 32, 0, s>>>(W.part, kDotBlocks, W.cg);
     CK(cudaGetLastError(), "conjugate-gradient start");
     if ((st = run_cg()) != IFT_OK) return st;

@@ -2396,40 +2396,40 @@ __global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const doub
 
 // Elements per warp group of align_apply_kernel mode 0, and its shared memory in
 // doubles: one staging buffer holds the group's (M_e)_wx rows at the odd stride
-// nxp = n_xe | 1, its (M_e)_xx, mesh directions and node indices; a warp has two.
+// nxp = n_xe | 1, its (M_e)_xx, mesh directions and free indices; a warp has two.
 __host__ __device__ inline int align_group(int nxe) { return 32 / nxe; }
-__host__ __device__ inline int align_apply_buf(int nxe, int nv, int ku) {
+__host__ __device__ inline int align_apply_buf(int nxe, int ku) {
   const int E = align_group(nxe), nxp = nxe | 1;
-  return E * ku * nxp + E * nxe * nxe + E * nxe + (E * nv + 1) / 2;
+  return E * ku * nxp + E * nxe * nxe + E * nxe + (E * nxe + 1) / 2;
 }
-__host__ __device__ inline int align_apply_warp_doubles(int nxe, int nv, int ku) {
-  return 2 * align_apply_buf(nxe, nv, ku);
-}
+__host__ __device__ inline int align_apply_warp_doubles(int nxe, int ku) { return 2 * align_apply_buf(nxe, ku); }
 
 // Products with the stored element systems of align_jac_kernel over the unknowns
-// (w, x), J^T J = [H_ww, sum_e (M_e)_wx; sum_e (M_e)_xw, sum_e (M_e)_xx] (the mesh
+// (w, free x), J^T J = [H_ww, sum_e (M_e)_wx; sum_e (M_e)_xw, sum_e (M_e)_xx] (the mesh
 // blocks at the element's coordinates) and J^T F = sum_e g_e. This kernel forms
-// every part but the H_ww terms (align_wrows_kernel adds those):
+// every part but the H_ww terms:
 //   MODE 0: for v = (dw, dx), the mesh part given per element in xdir (n_xe values
 //           per element, zero on fixed coordinates):
 //             w rows  sum_e (M_e)_wx dx_e,
 //             mesh rows of element e  (M_e)_xw dw + (M_e)_xx dx_e;
 //   MODE 1: y = g_e (w rows and mesh rows);
 //   MODE 2: the mesh rows of diag(J^T J): diag((M_e)_xx).
-// MODE 0 takes the elements in groups of E = 32 / n_xe consecutive elements per
-// warp (groups strided over the grid), staged in shared memory by cp.async,
-// double-buffered: lane (s, r) forms mesh row r of the group's element s (k_u + n_xe
-// FMAs), lane c accumulates w row c over the group (E n_xe FMAs), so all lanes work
-// on both parts. MODES 1-2: one warp per element, reading their values directly.
-// The w rows are summed per CTA into part[block][0..ku) (summed over blocks in block
-// order afterwards), the mesh rows added to gx at the element's node coordinates.
-// k_u <= 96.
-template <int NXE, int DIM, int MODE>
+// efree[e][r]: the free index of element e's coordinate r (-1: fixed; its rows are
+// dropped). MODE 0 takes the elements in groups of E = 32 / n_xe consecutive
+// elements per warp (groups strided over the grid), staged in shared memory by
+// cp.async, double-buffered: lane (s, r) forms mesh row r of the group's element s
+// (k_u + n_xe FMAs), lane c accumulates w row c over the group (E n_xe FMAs), so all
+// lanes work on both parts. MODES 1-2: one warp per element, reading their values
+// directly. The w rows are summed per CTA into part[block][0..ku) (summed over
+// blocks in block order afterwards), the free mesh rows added to gxf (nfree, in
+// free order). k_u <= 96.
+template <int NXE, int MODE>
 __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restrict__ M,
-                                                          const double* __restrict__ g, const int* __restrict__ ev,
+                                                          const double* __restrict__ g,
+                                                          const int* __restrict__ efree,
                                                           const double* __restrict__ xdir, long n_elems, int ku,
-                                                          const double* __restrict__ dw, double* part, double* gx) {
-  constexpr int NV = NXE / DIM, E = 32 / NXE, NXP = NXE | 1;
+                                                          const double* __restrict__ dw, double* part, double* gxf) {
+  constexpr int E = 32 / NXE, NXP = NXE | 1;
   extern __shared__ __align__(16) double dsm[];
   __shared__ double sw[96];
   __shared__ double red[8][96];
@@ -2439,9 +2439,9 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
   if constexpr (MODE == 0) {
     for (int i = threadIdx.x; i < ku; i += blockDim.x) sw[i] = dw[i];
     __syncthreads();
-    const int bufd = align_apply_buf(NXE, NV, ku);
-    double* base = dsm + (size_t)warp * align_apply_warp_doubles(NXE, NV, ku);
-    // buffer layout: Mwx [E][ku][NXP] | Mxx [E][NXE][NXE] | xd [E][NXE] | node ints [E][NV]
+    const int bufd = align_apply_buf(NXE, ku);
+    double* base = dsm + (size_t)warp * align_apply_warp_doubles(NXE, ku);
+    // buffer layout: Mwx [E][ku][NXP] | Mxx [E][NXE][NXE] | xd [E][NXE] | free indices [E][NXE]
     auto stage = [&](long e0, int cnt, double* b) {
       const double* src = M + (size_t)e0 * S;
       for (int t = lane; t < cnt * S; t += 32) {
@@ -2455,8 +2455,8 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
       }
       double* xd = b + E * ku * NXP + E * NXE * NXE;
       if (lane < cnt * NXE) cp_async8(&xd[lane], &xdir[e0 * NXE + lane]);
-      int* vi = (int*)(xd + E * NXE);
-      if (lane < cnt * NV) cp_async4(&vi[lane], &ev[e0 * NV + lane]);
+      int* fi = (int*)(xd + E * NXE);
+      if (lane < cnt * NXE) cp_async4(&fi[lane], &efree[e0 * NXE + lane]);
     };
     const long ngroups = (n_elems + E - 1) / E, stride = (long)gridDim.x * nw;
     long gi = (long)blockIdx.x * nw + warp;
@@ -2474,9 +2474,9 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
       const double* Mwx = base + cur * bufd;
       const double* Mxx = Mwx + E * ku * NXP;
       const double* xd = Mxx + E * NXE * NXE;
-      const int* vi = (const int*)(xd + E * NXE);
+      const int* fi = (const int*)(xd + E * NXE);
       // mesh rows: lane (sl, r)
-      if (lane < cnt * NXE) {
+      if (lane < cnt * NXE && fi[lane] >= 0) {
         const int sl = lane / NXE, r = lane - sl * NXE;
         const double* mw = Mwx + sl * ku * NXP + r;
         double y = 0.0;
@@ -2485,7 +2485,7 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
         const double* mx = Mxx + sl * NXE * NXE + r;
 #pragma unroll
         for (int q = 0; q < NXE; ++q) y += mx[q * NXE] * xd[sl * NXE + q];
-        atomicAdd(&gx[vi[sl * NV + r / DIM] * DIM + (r % DIM)], y);
+        atomicAdd(&gxf[fi[lane]], y);
       }
       // w rows: lane c over the group's elements
 #pragma unroll
@@ -2507,17 +2507,20 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
     cp_async_wait_all();
   } else {
     for (long e = (long)blockIdx.x * nw + warp; e < n_elems; e += (long)gridDim.x * nw) {
-      const int* vi = ev + e * NV;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         const int c = ch * 32 + lane;
         if (c < k) {
           const int r = c - ku;
-          double y;
-          if constexpr (MODE == 1) y = g[(size_t)e * k + c];
-          else y = r >= 0 ? M[(size_t)e * S + ku * NXE + r * NXE + r] : 0.0;
-          if (r >= 0) atomicAdd(&gx[vi[r / DIM] * DIM + (r % DIM)], y);
-          else accw[ch] += y;
+          if (r >= 0) {
+            const int q = efree[e * NXE + r];
+            if (q >= 0) {
+              const double y = (MODE == 1) ? g[(size_t)e * k + c] : M[(size_t)e * S + ku * NXE + r * NXE + r];
+              atomicAdd(&gxf[q], y);
+            }
+          } else if (MODE == 1) {
+            accw[ch] += g[(size_t)e * k + c];
+          }
         }
       }
     }

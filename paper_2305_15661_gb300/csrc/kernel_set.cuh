@@ -188,7 +188,7 @@ struct KernelSetImpl {
   }
   static size_t align_apply_smem(int ku, int warps) {
     using Dd = Disc<PROB, P>;
-    return (size_t)warps * align_apply_warp_doubles(Dd::NXE, Dd::NXE / Dd::DIM, ku) * sizeof(double);
+    return (size_t)warps * align_apply_warp_doubles(Dd::NXE, ku) * sizeof(double);
   }
   // warps per CTA (as many as fit 96 KB of staging, so that two CTAs share an SM; at
   // most 8) and the grid (resident CTAs of the product kernel on sm_count SMs, at
@@ -199,7 +199,7 @@ struct KernelSetImpl {
     w = w < 1 ? 1 : (w > 8 ? 8 : w);
     const size_t smem = align_apply_smem(ku, w);
     using Dd = Disc<PROB, P>;
-    auto kern = align_apply_kernel<Dd::NXE, Dd::DIM, 0>;
+    auto kern = align_apply_kernel<Dd::NXE, 0>;
     // the shared-memory limit, set here (before any graph capture)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -214,19 +214,19 @@ struct KernelSetImpl {
     *grid = (int)(g < 1 ? 1 : g);
     return cudaSuccess;
   }
-  static cudaError_t align_apply(int mode, const double* M, const double* g, const int* ev, const double* xdir,
-                                 long n, int ku, const double* dw, double* part, double* gx, int grid, int warps,
+  static cudaError_t align_apply(int mode, const double* M, const double* g, const int* efree, const double* xdir,
+                                 long n, int ku, const double* dw, double* part, double* gxf, int grid, int warps,
                                  cudaStream_t s) {
     using Dd = Disc<PROB, P>;
     if (ku > 96 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
     const int block = 32 * warps;
     if (mode == 0)
-      align_apply_kernel<Dd::NXE, Dd::DIM, 0><<<grid, block, align_apply_smem(ku, warps), s>>>(M, g, ev, xdir, n,
-                                                                                                 ku, dw, part, gx);
+      align_apply_kernel<Dd::NXE, 0><<<grid, block, align_apply_smem(ku, warps), s>>>(M, g, efree, xdir, n, ku, dw,
+                                                                                        part, gxf);
     else if (mode == 1)
-      align_apply_kernel<Dd::NXE, Dd::DIM, 1><<<grid, block, 0, s>>>(M, g, ev, xdir, n, ku, dw, part, gx);
+      align_apply_kernel<Dd::NXE, 1><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, gxf);
     else
-      align_apply_kernel<Dd::NXE, Dd::DIM, 2><<<grid, block, 0, s>>>(M, g, ev, xdir, n, ku, dw, part, gx);
+      align_apply_kernel<Dd::NXE, 2><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, gxf);
     return cudaGetLastError();
   }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {

@@ -597,9 +597,17 @@ __device__ __forceinline__ void block_dot2(double s0, double s1, double* part) {
   }
 }
 
-// d = 0, r = -g, z = M^{-1} r, p = z; partials of r . r and r . z (256 threads per block)
+// p's free mesh entry j into its element slots (CSR: slots[off[j] .. off[j + 1]) of
+// the element-order direction xdir)
+__device__ __forceinline__ void scatter_slots(const int* off, const int* slots, long j, double v, double* xdir) {
+  for (int q = off[j]; q < off[j + 1]; ++q) xdir[slots[q]] = v;
+}
+
+// d = 0, r = -g, z = M^{-1} r, p = z (its mesh part also into xdir); partials of
+// r . r and r . z (256 threads per block)
 __global__ void cg_start_kernel(long n, int ku, const double* g, const double* diag, const CGState* st, double* d,
-                                double* r, double* z, double* p, double* part) {
+                                double* r, double* z, double* p, double* part, const int* off, const int* slots,
+                                double* xdir) {
   double s0 = 0.0, s1 = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const double ri = -g[i], zi = ri * cg_precond(diag, st, i, ku);
@@ -607,6 +615,7 @@ __global__ void cg_start_kernel(long n, int ku, const double* g, const double* d
     r[i] = ri;
     z[i] = zi;
     p[i] = zi;
+    if (i >= ku) scatter_slots(off, slots, i - ku, zi, xdir);
     s0 += ri * ri;
     s1 += ri * zi;
   }
@@ -631,18 +640,19 @@ __device__ __forceinline__ void warp_sum2(const double* part, int nblk, double& 
 
 // Ap = (J^T J + lam D) p from the product kernel's outputs, and the partials of
 // p . Ap (block b into dotpart[b]; 256 threads): the free mesh rows
-// Ap[ku + j] = gx[idx[j]] + lam p[ku + j], and (block 0) the w rows
-// Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper, acc_h order).
+// Ap[ku + j] = gxf[j] + lam p[ku + j] (gxf is zeroed behind for the next product),
+// and (block 0) the w rows Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper,
+// acc_h order).
 __global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
-                                    const int* idx, int nfree, const double* gx, const CGState* st, double* Ap,
-                                    double* dotpart) {
+                                    int nfree, double* gxf, const CGState* st, double* Ap, double* dotpart) {
   __shared__ double sh[256];
   __shared__ double wsum[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double lam = st->lam;
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
-    const double a = gx[idx[j]] + lam * p[ku + j];
+    const double a = gxf[j] + lam * p[ku + j];
+    gxf[j] = 0.0;
     Ap[ku + j] = a;
     s += p[ku + j] * a;
   }
@@ -750,34 +760,24 @@ __global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsign
   if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, st->done ? 0u : 1u);
 }
 
-// p = z + beta p
-__global__ void cg_dir_kernel(long n, const CGState* st, const double* z, double* p) {
+// p = z + beta p (its mesh part also into xdir)
+__global__ void cg_dir_kernel(long n, int ku, const CGState* st, const double* z, double* p, const int* off,
+                              const int* slots, double* xdir) {
   if (st->done) return;
   const double b = st->beta;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    p[i] = z[i] + b * p[i];
-}
-
-// xdir[e][r] = the entry of the free-coordinate vector vfree at element e's mesh
-// coordinate r (node ev[e][r / dim], direction r % dim), 0 on fixed coordinates
-// (pos: the free position of each coordinate, -1 if fixed)
-__global__ void align_dir_kernel(const int* ev, long n_elems, int nv, int dim, const int* pos, const double* vfree,
-                                 double* xdir) {
-  const int nxe = nv * dim;
-  const long total = n_elems * nxe;
-  for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (long)gridDim.x * blockDim.x) {
-    const long e = j / nxe;
-    const int r = (int)(j - e * nxe);
-    const int q = pos[(long)ev[e * nv + r / dim] * dim + r % dim];
-    xdir[j] = q >= 0 ? vfree[q] : 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double v = z[i] + b * p[i];
+    p[i] = v;
+    if (i >= ku) scatter_slots(off, slots, i - ku, v, xdir);
   }
 }
 
-// out[j] = gx[idx[j]] + lam v[j] (the free-coordinate rows of J^T J v + lambda v)
-__global__ void gather_free_kernel(const int* idx, int nfree, const double* gx, const double* v, double lam,
-                                   double* out) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x)
-    out[j] = gx[idx[j]] + (v ? lam * v[j] : 0.0);
+// out[j] = gxf[j], then gxf[j] = 0 (the free mesh rows of a product, in free order)
+__global__ void take_free_kernel(int nfree, double* gxf, double* out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
+    out[j] = gxf[j];
+    gxf[j] = 0.0;
+  }
 }
 
 }  // namespace ift
