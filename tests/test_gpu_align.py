@@ -60,11 +60,13 @@ def test_residual_and_products_match_dense_jacobians(name, kw, kappa):
     assert rel(gx, dRdx.T @ v[:O.Nu] + dNdx.T @ v[O.Nu:]) < 1e-12
 
 
-# k_u + n_xe = 34 > 32: the stored blocks span two 32-column chunks per warp
+# k_u + n_xe = 34 > 32: the element gradients span two 32-column chunks per warp
 WIDE = ("euler p1 wide", dict(n=3, p=1, k_u=28, k_x=2, seed=8), 0.1)
+# p = 3: n_u = 40 rows per element block
+P3 = ("euler p3", dict(n=3, p=3, k_u=8, k_x=2, seed=9), 0.1)
 
 
-@pytest.mark.parametrize("name,kw,kappa", [CASES[0], CASES[2], WIDE])
+@pytest.mark.parametrize("name,kw,kappa", [CASES[0], CASES[2], WIDE, P3])
 def test_alignment_gradient_and_first_step(name, kw, kappa):
     # |J^T F| at the start over the unknowns, and the point after one step, as the oracle
     wl = W.euler_workload(**kw)
