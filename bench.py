@@ -782,7 +782,8 @@ def run_greedy(args):
 
 
 def run_align(args):
-    """Snapshot alignment (Eq. align0) on the 20,000-element p = 2 mesh: a fixed
+    """Snapshot alignment (Eq. align0) on the 20,000-element p = 2 mesh (--config 4:
+    80,000 elements, p = 3, k_u = 40): a fixed
     number of full-space Levenberg-Marquardt steps on (w, interior mesh nodes) from
     the reference mesh, every element weighted 1. At each accepted point one element
     pass stores every element's block A_e = [dR_e/dw | dR_e/dx_e]; each
@@ -793,7 +794,10 @@ def run_align(args):
     from paper_2305_15661_gb300 import workloads as W
 
     ift.load()
-    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
+    if args.config == 4:  # p = 3 on 200 x 200 x 2 triangles, k_u = 40
+        wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4)
+    else:
+        wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
     ctx = ift.Context.from_workload(wl, kappa=0.1)
     mu = wl.mus[0]
     inner = np.all((wl.X > 1e-12) & (wl.X < 1 - 1e-12), axis=1)
@@ -824,7 +828,7 @@ def run_align(args):
     hbm = measured_peaks().get("hbm_gbs")
     tf = cg_flops / (ms_cg_iter * 1e-3) / 1e12
     gbs = cg_bytes / (ms_cg_iter * 1e-3) / 1e9
-    print(json.dumps({"mode": "align", "elements": ne, "p": 2, "k_u": wl.ku, "free_coordinates": int(mask.sum()),
+    print(json.dumps({"mode": "align", "elements": ne, "p": wl.p, "k_u": wl.ku, "free_coordinates": int(mask.sum()),
                       "lm_steps": r["iters"], "cg_iters": r["cg_iters"], "trials": r["trials"],
                       "s_per_alignment": t, "ms_form_per_point": r["ms_form"] / (r["iters"] + 1),
                       "ms_cg_per_iter": ms_cg_iter, "ms_search_per_trial": r["ms_search"] / max(r["trials"], 1),
@@ -832,8 +836,8 @@ def run_align(args):
                       "cg_iteration": {"flops": cg_flops, "bytes": cg_bytes, "fp64_tflops": tf,
                                        "fp64_peak": fp64, "frac_fp64": tf / fp64 if fp64 else None,
                                        "gbs": gbs, "hbm_peak": hbm, "frac_hbm": gbs / hbm if hbm else None,
-                                       "note": "whole iteration (product and CG vector kernels); the element "
-                                               "systems (25 MB) stay in the 129 MB L2 between iterations"},
+                                       "note": "whole iteration (product and CG vector kernels); element "
+                                               "systems %.0f MB (L2 129 MB)" % (ne * blk * 8 / 1e6)},
                       "J": r["J"], "gnorm_over_g0": r["gnorm"] / r["g0"], "status": r["status"]}))
     ctx.close()
     return 0
@@ -855,8 +859,9 @@ def main():
     ap.add_argument("--contraction", choices=["fp", "tf32", "3xtf32", "bf16"], default="fp",
                     help="FP32/mixed contexts: form H with FP32 FMAs, TF32 or 3xTF32 tensor cores")
     ap.add_argument("--config", type=int, choices=[2, 3, 4], default=2,
-                    help="--mode assembly: 2 (or 3) = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 elements, "
-                         "k 40+8; --mode batched: 3 = 256 queries on the first mesh, 4 = 1,024 on the second")
+                    help="--mode assembly and align: 2 (or 3) = p 2, 20,000 elements, k 20+4; 4 = p 3, 80,000 "
+                         "elements, k 40+8; --mode batched: 3 = 256 queries on the first mesh, 4 = 1,024 on the "
+                         "second")
     ap.add_argument("--max-iters", type=int, default=200,
                     help="--mode batched: LM iterations per phase before a query stops unconverged")
     ap.add_argument("--compare-fp64", action="store_true",

@@ -1875,10 +1875,11 @@ extern "C" ift_status ift_set_launch_shapes(ift_ctx* c, int warps, int batched_w
 namespace {
 
 constexpr int kDotBlocks = 120;
+static_assert(kDotBlocks >= LM_KMAX, "align_finish_kernel forms one w row per block");
 
 struct AlignWork {
   long Nu = 0, Ne = 0, Nx = 0;
-  int ku = 0, nfree = 0, nu = 0, nxe = 0, agrid = 1, awarps = 1, jgrid = 1;
+  int ku = 0, nfree = 0, nu = 0, nxe = 0, agrid = 1, awarps = 1, jgrid = 1, jwarps = 1;
   double *w = nullptr, *x = nullptr, *F = nullptr, *dU = nullptr, *dx = nullptr, *dF = nullptr, *gU = nullptr,
          *gx = nullptr, *wt = nullptr, *xt = nullptr, *Ft = nullptr, *part = nullptr, *nbad = nullptr;
   double *g = nullptr, *d = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr,
@@ -2008,7 +2009,7 @@ ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double*
   if (stored) {
     if (!c->ks[0].align_apply_plan) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
     CK(c->ks[0].align_apply_plan(W.ku, W.Ne, c->sm_count, &W.awarps, &W.agrid), "alignment product shape");
-    CK(c->ks[0].align_jac_plan(W.ku, W.Ne, 2, c->sm_count, &W.jgrid), "alignment Jacobian pass shape");
+    CK(c->ks[0].align_jac_plan(W.ku, W.Ne, c->sm_count, &W.jwarps, &W.jgrid), "alignment Jacobian pass shape");
   }
   CK(W.alloc(stored), "alignment buffers");
   const int nmu = (c->dim == 1) ? 1 : 2;
@@ -2023,11 +2024,11 @@ ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double*
 ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
   const KernelSet& ks = c->ks[0];
   if (!ks.align_jac) return c->fail(IFT_ERR_NOTIMPL, "snapshot alignment kernels are not built");
-  if (ks.align_jac_smem(c->ku, 2) > (size_t)c->smem_optin)
+  if (ks.align_jac_smem(c->ku, W.jwarps) > (size_t)c->smem_optin)
     return c->fail(IFT_ERR_ARG, "alignment Jacobian pass needs too much shared memory");
   AsmArgs<double> a = align_args(c, W.w, W.x);
   CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
-  CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, W.hpart, 2, W.jgrid, s), "alignment Jacobian pass");
+  CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, W.hpart, W.jwarps, W.jgrid, s), "alignment Jacobian pass");
   const int nh = W.ku * (W.ku + 1) / 2;
   reduce_partials_kernel<<<(nh + 31) / 32, 256, 0, s>>>(W.hpart, W.jgrid, nh, W.H, nullptr);
   CK(cudaGetLastError(), "H_ww");

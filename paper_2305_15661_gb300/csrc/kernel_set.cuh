@@ -164,18 +164,36 @@ struct KernelSetImpl {
   static size_t align_jac_smem(int ku, int warps) {
     return cta_bytes<T, PROB, P>(ku, 0) + (size_t)warps * WarpLayout<T, PROB, P, true>(ku, Disc<PROB, P>::NXE).bytes;
   }
-  // resident CTAs of `warps` warps on sm_count SMs, at most one warp per element
-  static cudaError_t align_jac_plan(int ku, long n, int warps, int sm_count, int* grid) {
-    const size_t smem = align_jac_smem(ku, warps);
+  // warps per CTA (1, 2 or 4: the most warps resident on an SM, shared memory being
+  // handed out CTA by CTA) and the grid (resident CTAs on sm_count SMs, at most one
+  // warp per element)
+  static cudaError_t align_jac_plan(int ku, long n, int sm_count, int* warps, int* grid) {
+    int best_w = 0, best_occ = 0;
+    for (int w : {4, 2, 1}) {
+      const size_t smem = align_jac_smem(ku, w);
+      if (cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, align_jac_kernel<T, PROB, P>, 32 * w, smem) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (occ * w > best_occ * best_w) {
+        best_w = w;
+        best_occ = occ;
+      }
+    }
+    if (best_occ < 1) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)align_jac_smem(ku, best_w));
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, align_jac_kernel<T, PROB, P>, 32 * warps, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    long g = (n + warps - 1) / warps;
-    if (g > (long)sm_count * occ) g = (long)sm_count * occ;
+    long g = (n + best_w - 1) / best_w;
+    if (g > (long)sm_count * best_occ) g = (long)sm_count * best_occ;
+    *warps = best_w;
     *grid = (int)(g < 1 ? 1 : g);
     return cudaSuccess;
   }

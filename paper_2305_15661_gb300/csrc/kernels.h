@@ -39,12 +39,12 @@ struct KernelSet {
   // FP64 sets: snapshot alignment with stored element systems. align_jac writes per
   // element (M_e)_wx and (M_e)_xx (k_u n_xe + n_xe^2 doubles), g_e (k = k_u + n_xe)
   // and F, and per CTA its part of H_ww (packed, hpart: grid x k_u (k_u + 1) / 2), at
-  // the state of args, in the grid of align_jac_plan; align_apply forms the
+  // the state of args, in the launch shape of align_jac_plan; align_apply forms the
   // non-H_ww parts of mode 0 J^T J v, 1 J^T F, 2 diag(J^T J) (see align_apply_kernel;
   // efree: the free index of each element coordinate, -1 fixed; xdir: the mesh
   // direction per element for mode 0; part: grid x k_u; gxf: the free mesh rows), in
   // the launch shape of align_apply_plan
-  cudaError_t (*align_jac_plan)(int ku, long n, int warps, int sm_count, int* grid) = nullptr;
+  cudaError_t (*align_jac_plan)(int ku, long n, int sm_count, int* warps, int* grid) = nullptr;
   cudaError_t (*align_jac)(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
                            double* hpart, int warps, int grid, cudaStream_t s) = nullptr;
   size_t (*align_jac_smem)(int ku, int warps) = nullptr;

@@ -639,15 +639,25 @@ __device__ __forceinline__ void warp_sum2(const double* part, int nblk, double& 
 }
 
 // Ap = (J^T J + lam D) p from the product kernel's outputs, and the partials of
-// p . Ap (block b into dotpart[b]; 256 threads): the free mesh rows
+// p . Ap (block b into dotpart[b]; 256 threads, gridDim >= ku): the free mesh rows
 // Ap[ku + j] = gxf[j] + lam p[ku + j] (gxf is zeroed behind for the next product),
-// and (block 0) the w rows Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper,
-// acc_h order).
+// and block c < ku the w row Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper,
+// acc_h order). Every sum runs in a fixed order.
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
+}
+
 __global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
                                     int nfree, double* gxf, const CGState* st, double* Ap, double* dotpart) {
   __shared__ double sh[256];
-  __shared__ double wsum[8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double lam = st->lam;
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
@@ -656,36 +666,20 @@ __global__ void align_finish_kernel(const double* part, int nparts, int ku, cons
     Ap[ku + j] = a;
     s += p[ku + j] * a;
   }
-  if (blockIdx.x == 0) {
-    double ws = 0.0;
-    for (int c = warp; c < ku; c += 8) {
-      double t = 0.0;
-      for (int b = lane; b < nparts; b += 32) t += part[(size_t)b * ku + c];
-      for (int j = lane; j < ku; j += 32) {
-        const int r = j < c ? j : c, q = j < c ? c : j;
-        t += H[r * ku - (r * (r - 1)) / 2 + (q - r)] * p[j];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) {
-        Ap[c] = t;
-        ws += p[c] * t;
-      }
+  double wrow = 0.0;
+  if (blockIdx.x < ku) {
+    const int c = blockIdx.x;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) t += part[(size_t)b * ku + c];
+    for (int j = threadIdx.x; j < ku; j += blockDim.x) {
+      const int r = j < c ? j : c, q = j < c ? c : j;
+      t += H[r * ku - (r * (r - 1)) / 2 + (q - r)] * p[j];
     }
-    if (lane == 0) wsum[warp] = ws;
+    wrow = block_sum256(t, sh);
+    if (threadIdx.x == 0) Ap[c] = wrow;
   }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double t = sh[0];
-    if (blockIdx.x == 0)
-      for (int w = 0; w < 8; ++w) t += wsum[w];
-    dotpart[blockIdx.x] = t;
-  }
+  const double tot = block_sum256(s, sh);
+  if (threadIdx.x == 0) dotpart[blockIdx.x] = tot + (blockIdx.x < ku ? p[blockIdx.x] * wrow : 0.0);
 }
 
 // (one warp)
