@@ -3,9 +3,9 @@
 A fully connected network n_in -> width (x depth hidden layers, GELU) -> n_out
 (linear), with the mean-squared-error loss L = sum (Y - T)^2 / (n n_out). The
 paper has no such network: it starts the LM from the projected guess
-(Remark rem:solver); the network is the warm start asked of this build, and
-this module is the reference its CUDA forward and backward kernels are checked
-against. Parameters are flattened layer by layer as W_l (in x out, row-major)
+(Remark rem:solver). The network is the library's learned warm start (parameters
+to reduced coordinates), and this module is the reference its CUDA forward and
+backward kernels are checked against. Parameters are flattened layer by layer as W_l (in x out, row-major)
 then b_l (out).
 
 Pinned by the tests: central finite differences of the loss gradient, and GELU

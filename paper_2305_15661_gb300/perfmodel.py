@@ -12,7 +12,7 @@ A_e^T A_e, A_e^T R_e, |R_e|^2. One fused multiply-add counts as 2 FLOPs.
     volume test 2 n_q d n_b m; volume Jacobian block 2 n_q d n_b^2 m^2;
     faces, per face point: two traces 4 n_t m, Roe flux C_roe and its 8 state
     derivatives 8 C_roe, test 2 n_t m, face Jacobian blocks 4 n_t^2 m^2.
-(b) reduction (the survey's contraction count plus g and J):
+(b) reduction (the contraction count of Eq. levmarq-elem plus g and J):
     2 n_u k_u (n_u + n_u') + 2 n_u k_x n_x + n_u k (k + 1) + 2 n_u k + 2 n_u,
     where n_u k (k + 1) is the symmetric product A_e^T A_e (its k (k + 1) / 2
     distinct entries, each a length-n_u dot product).
