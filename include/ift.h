@@ -406,6 +406,11 @@ ift_status ift_align_vjp(ift_ctx* ctx, const double* mu, const double* w, const 
    Returns info->status (IFT_OK, IFT_NOT_CONVERGED or IFT_LINESEARCH_FAILED). */
 ift_status ift_align(ift_ctx* ctx, const double* mu, double* w, double* x, const uint8_t* free_mask, double tol,
                      int max_iters, ift_align_info* info);
+/* ift_align with device pointers for mu, w, x (in/out) and free_mask, on `stream`
+   (NULL: the context's). The Levenberg-Marquardt loop decides on the host, so the
+   call synchronises the stream before it returns; info_host may be NULL. */
+ift_status ift_align_dev(ift_ctx* ctx, const double* mu, double* w, double* x, const uint8_t* free_mask,
+                         double tol, int max_iters, ift_align_info* info_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -55,12 +55,13 @@ __global__ void cg_update_kernel(long n, int ku, const double* pap_part, int nbl
                                  const double* Ap, const double* diag, double* d, double* r, double* z,
                                  double* part);
 __global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
-                                    int nfree, double* gxf, const CGState* st, double* Ap, double* dotpart);
+                                    int nfree, const double* yslot, const int* off, const int* slots,
+                                    const CGState* st, double* Ap, double* dotpart);
 __global__ void cg_beta_kernel(const double* part, int nblk, CGState* st, unsigned long long cond_handle,
                                int use_cond);
 __global__ void cg_dir_kernel(long n, int ku, const CGState* st, const double* z, double* p, const int* off,
                               const int* slots, double* xdir);
-__global__ void take_free_kernel(int nfree, double* gxf, double* out);
+__global__ void take_free_kernel(int nfree, const double* yslot, const int* off, const int* slots, double* out);
 __global__ void align_wrows_kernel(const double* part, int nparts, int ku, const double* H, const double* dw,
                                    int mode, double* out);
 }  // namespace ift
@@ -1887,7 +1888,7 @@ struct AlignWork {
   double *M = nullptr, *ge = nullptr, *apart = nullptr;  // element systems, CTA partials of the w rows
   double *H = nullptr, *hpart = nullptr;                 // H_ww (packed) and its CTA partials
   double* part2 = nullptr;                               // CG partials of r . r and r . z
-  double* gxf = nullptr;                                 // free mesh rows of a product (kept zero between uses)
+  double* yslot = nullptr;                               // a product's mesh rows per element coordinate
   int *efree = nullptr, *soff = nullptr, *slots = nullptr;  // element coordinates' free indices; free -> slots
   double* xdir = nullptr;                                  // a mesh direction in element order
   CGState* cg = nullptr;
@@ -1898,7 +1899,7 @@ struct AlignWork {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (double** q : {&w, &x, &F, &dU, &dx, &dF, &gU, &gx, &wt, &xt, &Ft, &part, &nbad, &g, &d, &r, &p, &Ap, &z,
-                       &diag, &M, &ge, &apart, &xdir, &H, &hpart, &part2, &gxf})
+                       &diag, &M, &ge, &apart, &xdir, &H, &hpart, &part2, &yslot})
       dfree(*q);
     dfree(cg);
     dfree(free_idx);
@@ -1938,7 +1939,7 @@ struct AlignWork {
       B(ge, Ne * (long)(ku + nxe));
       B(H, (long)ku * (ku + 1) / 2);
       B(part2, 2 * kDotBlocks);
-      B(gxf, nfree);
+      B(yslot, Ne * nxe);
       if (e == cudaSuccess) e = dalloc(efree, (size_t)(Ne * nxe > 0 ? Ne * nxe : 1));
       if (e == cudaSuccess) e = dalloc(soff, (size_t)nfree + 1);
       if (e == cudaSuccess) e = dalloc(slots, (size_t)(Ne * nxe > 0 ? Ne * nxe : 1));
@@ -2013,9 +2014,10 @@ ift_status align_setup(ift_ctx* c, AlignWork& W, const double* mu, const double*
   }
   CK(W.alloc(stored), "alignment buffers");
   const int nmu = (c->dim == 1) ? 1 : 2;
-  CK(cudaMemcpy(c->d_mu, mu, nmu * 8, cudaMemcpyHostToDevice), "copy mu");
-  CK(cudaMemcpy(W.w, w, W.ku * 8, cudaMemcpyHostToDevice), "copy w");
-  CK(cudaMemcpy(W.x, x, W.Nx * 8, cudaMemcpyHostToDevice), "copy x");
+  // host or device inputs (unified addressing tells them apart)
+  CK(cudaMemcpy(c->d_mu, mu, nmu * 8, cudaMemcpyDefault), "copy mu");
+  CK(cudaMemcpy(W.w, w, W.ku * 8, cudaMemcpyDefault), "copy w");
+  CK(cudaMemcpy(W.x, x, W.Nx * 8, cudaMemcpyDefault), "copy x");
   return IFT_OK;
 }
 
@@ -2043,10 +2045,11 @@ ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
 // (the CG body forms mode 0, J^T J v, itself).
 ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, double* out, cudaStream_t s) {
   const KernelSet& ks = c->ks[0];
-  CK(ks.align_apply(mode, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, nullptr, W.apart, W.gxf, W.agrid, W.awarps, s),
+  CK(ks.align_apply(mode, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, nullptr, W.apart, W.yslot, W.agrid, W.awarps, s),
      "alignment product");
   align_wrows_kernel<<<(W.ku + 7) / 8, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, nullptr, mode, out);
-  if (W.nfree > 0) take_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.nfree, W.gxf, out + W.ku);
+  if (W.nfree > 0)
+    take_free_kernel<<<vec_grid(W.nfree), 256, 0, s>>>(W.nfree, W.yslot, W.soff, W.slots, out + W.ku);
   CK(cudaGetLastError(), "alignment product");
   return IFT_OK;
 }
@@ -2056,10 +2059,10 @@ ift_status align_apply(ift_ctx* c, AlignWork& W, int mode, double* out, cudaStre
 ift_status align_cg_body(ift_ctx* c, AlignWork& W, cudaStream_t s, unsigned long long handle, int use_cond) {
   const KernelSet& ks = c->ks[0];
   const long n = W.ku + W.nfree;
-  CK(ks.align_apply(0, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, W.p, W.apart, W.gxf, W.agrid, W.awarps, s),
+  CK(ks.align_apply(0, W.M, W.ge, W.efree, W.xdir, W.Ne, W.ku, W.p, W.apart, W.yslot, W.agrid, W.awarps, s),
      "alignment product");
-  align_finish_kernel<<<kDotBlocks, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, W.p, W.nfree, W.gxf, W.cg, W.Ap,
-                                                 W.part);
+  align_finish_kernel<<<kDotBlocks, 256, 0, s>>>(W.apart, W.agrid, W.ku, W.H, W.p, W.nfree, W.yslot, W.soff, W.slots,
+                                                 W.cg, W.Ap, W.part);
   cg_update_kernel<<<kDotBlocks, 256, 0, s>>>(n, W.ku, W.part, kDotBlocks, W.cg, W.p, W.Ap, W.diag, W.d, W.r, W.z,
                                               W.part2);
   cg_beta_kernel<<<1, 32, 0, s>>>(W.part2, kDotBlocks, W.cg, handle, use_cond);
@@ -2117,16 +2120,21 @@ extern "C" ift_status ift_align_vjp(ift_ctx* c, const double* mu, const double* 
   return IFT_OK;
 }
 
-extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double* x, const uint8_t* free_mask,
-                                double tol, int max_iters, ift_align_info* info) {
-  NvtxRange nvtx_range("ift_align");
+namespace {
+
+// ift_align and ift_align_dev: mu, w, x and free_mask host or device pointers (the
+// copies use unified addressing), the work on stream s, which is synchronised.
+ift_status align_run(ift_ctx* c, const double* mu, double* w, double* x, const uint8_t* free_mask, double tol,
+                     int max_iters, ift_align_info* info, cudaStream_t s) {
   AlignWork W;
-  if (!free_mask && c) return c->fail(IFT_ERR_ARG, "null free-coordinate mask");
-  if (c && c->have_mesh) {
-    for (long i = 0; i < c->n_verts * (long)c->dim; ++i) W.nfree += free_mask[i] ? 1 : 0;
-  }
-  if (c && c->ku + c->nxe > 96) return c->fail(IFT_ERR_ARG, "alignment supports k_u + n_xe <= 96");
-  ift_status st = align_setup(c, W, mu, w, x, true);
+  ift_status st = check_ready(c);
+  if (st != IFT_OK) return st;
+  if (!free_mask) return c->fail(IFT_ERR_ARG, "null free-coordinate mask");
+  std::vector<uint8_t> hmask((size_t)c->n_verts * c->dim);
+  CK(cudaMemcpy(hmask.data(), free_mask, hmask.size(), cudaMemcpyDefault), "copy free-coordinate mask");
+  for (uint8_t m : hmask) W.nfree += m ? 1 : 0;
+  if (c->ku + c->nxe > 96) return c->fail(IFT_ERR_ARG, "alignment supports k_u + n_xe <= 96");
+  st = align_setup(c, W, mu, w, x, true);
   if (st != IFT_OK) return st;
   if (!(tol >= 0.0) || max_iters < 0) return c->fail(IFT_ERR_ARG, "tol >= 0 and max_iters >= 0 required");
   {
@@ -2134,7 +2142,7 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     // coordinate the element slots that hold it (CSR), for the element-order direction
     std::vector<int> idx, pos((size_t)W.Nx, -1);
     for (long i = 0; i < W.Nx; ++i)
-      if (free_mask[i]) {
+      if (hmask[(size_t)i]) {
         pos[(size_t)i] = (int)idx.size();
         idx.push_back((int)i);
       }
@@ -2160,11 +2168,8 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     CK(cudaMemcpy(W.soff, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "copy slot offsets");
     CK(cudaMemcpy(W.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice), "copy slots");
   }
-  cudaStream_t s = c->stream;
   const long n = W.ku + W.nfree;
-  // the products add into gxf and the finishing kernels zero it behind them; the
-  // fixed coordinates' slots of the element-order direction stay zero
-  CK(cudaMemsetAsync(W.gxf, 0, (W.nfree > 0 ? W.nfree : 1) * 8, s), "zero free rows");
+  // the fixed coordinates' slots of the element-order direction stay zero
   CK(cudaMemsetAsync(W.xdir, 0, (W.Ne * W.nxe > 0 ? W.Ne * W.nxe : 1) * 8, s), "zero direction");
   // readings of Sec. 3.2.3 as for the reduced solve: lambda_0 = 1e-4, /10 after a
   // full step, x10 after a shortened one, Armijo 1e-4, at most 30 halvings; damping
@@ -2314,8 +2319,8 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     if ((st = lap(ms_form)) != IFT_OK) return st;
     J = Jt;
   }
-  CK(cudaMemcpyAsync(w, W.w, W.ku * 8, cudaMemcpyDeviceToHost, s), "copy w");
-  CK(cudaMemcpyAsync(x, W.x, W.Nx * 8, cudaMemcpyDeviceToHost, s), "copy x");
+  CK(cudaMemcpyAsync(w, W.w, W.ku * 8, cudaMemcpyDefault, s), "copy w");
+  CK(cudaMemcpyAsync(x, W.x, W.Nx * 8, cudaMemcpyDefault, s), "copy x");
   CK(cudaStreamSynchronize(s), "alignment");
   if (info) {
     info->status = status;
@@ -2330,4 +2335,19 @@ extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double*
     info->ms_search = ms_search;
   }
   return (ift_status)status;
+}
+
+}  // namespace
+
+extern "C" ift_status ift_align(ift_ctx* c, const double* mu, double* w, double* x, const uint8_t* free_mask,
+                                double tol, int max_iters, ift_align_info* info) {
+  NvtxRange nvtx_range("ift_align");
+  return align_run(c, mu, w, x, free_mask, tol, max_iters, info, c ? c->stream : nullptr);
+}
+
+extern "C" ift_status ift_align_dev(ift_ctx* c, const double* mu, double* w, double* x, const uint8_t* free_mask,
+                                    double tol, int max_iters, ift_align_info* info_host, void* stream) {
+  NvtxRange nvtx_range("ift_align_dev");
+  return align_run(c, mu, w, x, free_mask, tol, max_iters, info_host,
+                   stream ? (cudaStream_t)stream : (c ? c->stream : nullptr));
 }

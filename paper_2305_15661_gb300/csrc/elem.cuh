@@ -2415,20 +2415,20 @@ __host__ __device__ inline int align_apply_warp_doubles(int nxe, int ku) { retur
 //   MODE 1: y = g_e (w rows and mesh rows);
 //   MODE 2: the mesh rows of diag(J^T J): diag((M_e)_xx).
 // efree[e][r]: the free index of element e's coordinate r (-1: fixed; its rows are
-// dropped). MODE 0 takes the elements in groups of E = 32 / n_xe consecutive
+// dropped); a free coordinate's row goes to its own slot yslot[e][r] (no atomics:
+// the free rows are summed from the slots in a fixed order afterwards). MODE 0 takes the elements in groups of E = 32 / n_xe consecutive
 // elements per warp (groups strided over the grid), staged in shared memory by
 // cp.async, double-buffered: lane (s, r) forms mesh row r of the group's element s
 // (k_u + n_xe FMAs), lane c accumulates w row c over the group (E n_xe FMAs), so all
 // lanes work on both parts. MODES 1-2: one warp per element, reading their values
 // directly. The w rows are summed per CTA into part[block][0..ku) (summed over
-// blocks in block order afterwards), the free mesh rows added to gxf (nfree, in
-// free order). k_u <= 96.
+// blocks in block order afterwards). k_u <= 96.
 template <int NXE, int MODE>
 __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restrict__ M,
                                                           const double* __restrict__ g,
                                                           const int* __restrict__ efree,
                                                           const double* __restrict__ xdir, long n_elems, int ku,
-                                                          const double* __restrict__ dw, double* part, double* gxf) {
+                                                          const double* __restrict__ dw, double* part, double* yslot) {
   constexpr int E = 32 / NXE, NXP = NXE | 1;
   extern __shared__ __align__(16) double dsm[];
   __shared__ double sw[96];
@@ -2485,7 +2485,7 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
         const double* mx = Mxx + sl * NXE * NXE + r;
 #pragma unroll
         for (int q = 0; q < NXE; ++q) y += mx[q * NXE] * xd[sl * NXE + q];
-        atomicAdd(&gxf[fi[lane]], y);
+        yslot[gi * E * NXE + lane] = y;
       }
       // w rows: lane c over the group's elements
 #pragma unroll
@@ -2514,10 +2514,8 @@ __global__ void __launch_bounds__(256) align_apply_kernel(const double* __restri
           const int r = c - ku;
           if (r >= 0) {
             const int q = efree[e * NXE + r];
-            if (q >= 0) {
-              const double y = (MODE == 1) ? g[(size_t)e * k + c] : M[(size_t)e * S + ku * NXE + r * NXE + r];
-              atomicAdd(&gxf[q], y);
-            }
+            if (q >= 0)
+              yslot[e * NXE + r] = (MODE == 1) ? g[(size_t)e * k + c] : M[(size_t)e * S + ku * NXE + r * NXE + r];
           } else if (MODE == 1) {
             accw[ch] += g[(size_t)e * k + c];
           }

@@ -233,18 +233,18 @@ struct KernelSetImpl {
     return cudaSuccess;
   }
   static cudaError_t align_apply(int mode, const double* M, const double* g, const int* efree, const double* xdir,
-                                 long n, int ku, const double* dw, double* part, double* gxf, int grid, int warps,
-                                 cudaStream_t s) {
+                                 long n, int ku, const double* dw, double* part, double* yslot, int grid,
+                                 int warps, cudaStream_t s) {
     using Dd = Disc<PROB, P>;
     if (ku > 96 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
     const int block = 32 * warps;
     if (mode == 0)
       align_apply_kernel<Dd::NXE, 0><<<grid, block, align_apply_smem(ku, warps), s>>>(M, g, efree, xdir, n, ku, dw,
-                                                                                        part, gxf);
+                                                                                        part, yslot);
     else if (mode == 1)
-      align_apply_kernel<Dd::NXE, 1><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, gxf);
+      align_apply_kernel<Dd::NXE, 1><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, yslot);
     else
-      align_apply_kernel<Dd::NXE, 2><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, gxf);
+      align_apply_kernel<Dd::NXE, 2><<<grid, block, 0, s>>>(M, g, efree, xdir, n, ku, dw, part, yslot);
     return cudaGetLastError();
   }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {

@@ -42,14 +42,14 @@ struct KernelSet {
   // the state of args, in the launch shape of align_jac_plan; align_apply forms the
   // non-H_ww parts of mode 0 J^T J v, 1 J^T F, 2 diag(J^T J) (see align_apply_kernel;
   // efree: the free index of each element coordinate, -1 fixed; xdir: the mesh
-  // direction per element for mode 0; part: grid x k_u; gxf: the free mesh rows), in
-  // the launch shape of align_apply_plan
+  // direction per element for mode 0; part: grid x k_u; yslot: the mesh rows per
+  // element coordinate), in the launch shape of align_apply_plan
   cudaError_t (*align_jac_plan)(int ku, long n, int sm_count, int* warps, int* grid) = nullptr;
   cudaError_t (*align_jac)(const void* args, const double* Xref, double* M, double* g, double* F, double* nbad,
                            double* hpart, int warps, int grid, cudaStream_t s) = nullptr;
   size_t (*align_jac_smem)(int ku, int warps) = nullptr;
   cudaError_t (*align_apply)(int mode, const double* M, const double* g, const int* efree, const double* xdir,
-                             long n, int ku, const double* dw, double* part, double* gxf, int grid, int warps,
+                             long n, int ku, const double* dw, double* part, double* yslot, int grid, int warps,
                              cudaStream_t s) = nullptr;
   cudaError_t (*align_apply_plan)(int ku, long n, int sm_count, int* warps, int* grid) = nullptr;
   int (*blocks_per_sm_grad)(bool batched, int block, size_t smem) = nullptr;

@@ -640,7 +640,7 @@ __device__ __forceinline__ void warp_sum2(const double* part, int nblk, double& 
 
 // Ap = (J^T J + lam D) p from the product kernel's outputs, and the partials of
 // p . Ap (block b into dotpart[b]; 256 threads, gridDim >= ku): the free mesh rows
-// Ap[ku + j] = gxf[j] + lam p[ku + j] (gxf is zeroed behind for the next product),
+// Ap[ku + j] = sum of yslot over the coordinate's slots (CSR order) + lam p[ku + j],
 // and block c < ku the w row Ap[c] = sum_b part[b][c] + (H_ww p_w)_c (H packed upper,
 // acc_h order). Every sum runs in a fixed order.
 __device__ __forceinline__ double block_sum256(double v, double* sh) {
@@ -656,13 +656,14 @@ __device__ __forceinline__ double block_sum256(double v, double* sh) {
 }
 
 __global__ void align_finish_kernel(const double* part, int nparts, int ku, const double* H, const double* p,
-                                    int nfree, double* gxf, const CGState* st, double* Ap, double* dotpart) {
+                                    int nfree, const double* yslot, const int* off, const int* slots,
+                                    const CGState* st, double* Ap, double* dotpart) {
   __shared__ double sh[256];
   const double lam = st->lam;
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
-    const double a = gxf[j] + lam * p[ku + j];
-    gxf[j] = 0.0;
+    double a = lam * p[ku + j];
+    for (int q = off[j]; q < off[j + 1]; ++q) a += yslot[slots[q]];
     Ap[ku + j] = a;
     s += p[ku + j] * a;
   }
@@ -766,11 +767,13 @@ __global__ void cg_dir_kernel(long n, int ku, const CGState* st, const double* z
   }
 }
 
-// out[j] = gxf[j], then gxf[j] = 0 (the free mesh rows of a product, in free order)
-__global__ void take_free_kernel(int nfree, double* gxf, double* out) {
+// out[j] = the sum of yslot over free coordinate j's slots in CSR order (the free
+// mesh rows of a product)
+__global__ void take_free_kernel(int nfree, const double* yslot, const int* off, const int* slots, double* out) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nfree; j += gridDim.x * blockDim.x) {
-    out[j] = gxf[j];
-    gxf[j] = 0.0;
+    double a = 0.0;
+    for (int q = off[j]; q < off[j + 1]; ++q) a += yslot[slots[q]];
+    out[j] = a;
   }
 }
 

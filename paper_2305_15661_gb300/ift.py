@@ -72,7 +72,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_element_gradients", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_get_scaling", "ift_mlp_set_scaling", "ift_mlp_loss_grad", "ift_mlp_train",
            "ift_mlp_predict", "ift_nearest_start", "ift_align_residual", "ift_align_jvp", "ift_align_vjp",
-           "ift_align"]
+           "ift_align", "ift_align_dev"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_align_jvp": (i32, [vp, pd, pd, pd, pd, pd, pd]),
         "ift_align_vjp": (i32, [vp, pd, pd, pd, pd, pd, pd]),
         "ift_align": (i32, [vp, pd, pd, pd, ctypes.POINTER(ctypes.c_uint8), dbl, i32, P(AlignInfo)]),
+        "ift_align_dev": (i32, [vp, vp, vp, vp, vp, dbl, i32, P(AlignInfo), vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -325,6 +326,17 @@ class Context:
         return {"status": int(st), "w": w, "x": x, "iters": info.iters, "cg_iters": info.cg_iters,
                 "trials": info.trials, "J": info.J, "gnorm": info.gnorm, "g0": info.g0,
                 "ms_form": info.ms_form, "ms_cg": info.ms_cg, "ms_search": info.ms_search}
+
+    def align_dev(self, mu, w, x, free_mask, tol=1e-8, max_iters=100, stream=None):
+        """Device-pointer variant of align: mu, w, x (float64, w and x updated in place)
+        and free_mask (uint8) are CUDA tensors; synchronises the stream."""
+        info = AlignInfo()
+        st = load().ift_align_dev(self._h, _tptr(mu), _tptr(w), _tptr(x), _tptr(free_mask), tol, max_iters,
+                                  ctypes.byref(info), ctypes.c_void_p(stream) if stream else None)
+        self._check(st, allow_positive=True)
+        return {"status": int(st), "iters": info.iters, "cg_iters": info.cg_iters, "trials": info.trials,
+                "J": info.J, "gnorm": info.gnorm, "g0": info.g0, "ms_form": info.ms_form, "ms_cg": info.ms_cg,
+                "ms_search": info.ms_search}
 
     def solve_rom(self, mu, y0=None, z0=None):
         y = np.zeros(self.ku) if y0 is None else _f64(y0).copy()

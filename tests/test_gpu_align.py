@@ -222,3 +222,23 @@ def test_alignment_full_size_objective():
     assert abs(g1["J"] - J1) <= 1e-12 * J1
     assert J1 < J0
     assert np.array_equal(g1["x"][~mask], x0[~mask])
+
+
+def test_alignment_device_pointer_variant_matches_host():
+    import torch
+
+    wl = W.euler_workload(n=3, p=1, k_u=5, k_x=2, seed=4)
+    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    mu = np.array([2.1, 0.01])
+    mask = interior_mask(wl.X)
+    h = ctx.align(mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-9, max_iters=20)
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.asarray(a), dtype=dt, device=dev).clone()
+    w, x = t(wl.w_eval), t(wl.X.ravel())
+    stream = torch.cuda.current_stream().cuda_stream
+    d = ctx.align_dev(t(mu), w, x, t(mask, torch.uint8), tol=1e-9, max_iters=20, stream=stream)
+    torch.cuda.synchronize()
+    assert d["status"] == h["status"] and d["iters"] == h["iters"] and d["cg_iters"] == h["cg_iters"]
+    np.testing.assert_array_equal(w.cpu().numpy(), h["w"])
+    np.testing.assert_array_equal(x.cpu().numpy(), h["x"])
+    assert d["J"] == h["J"]
