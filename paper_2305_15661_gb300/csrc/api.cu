@@ -2130,6 +2130,9 @@ ift_status align_run(ift_ctx* c, const double* mu, double* w, double* x, const u
   ift_status st = check_ready(c);
   if (st != IFT_OK) return st;
   if (!free_mask) return c->fail(IFT_ERR_ARG, "null free-coordinate mask");
+  // device inputs may still be in flight on the caller's stream: the copies below
+  // read them after it
+  CK(cudaStreamSynchronize(s), "caller's stream");
   std::vector<uint8_t> hmask((size_t)c->n_verts * c->dim);
   CK(cudaMemcpy(hmask.data(), free_mask, hmask.size(), cudaMemcpyDefault), "copy free-coordinate mask");
   for (uint8_t m : hmask) W.nfree += m ? 1 : 0;

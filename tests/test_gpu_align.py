@@ -234,9 +234,11 @@ def test_alignment_device_pointer_variant_matches_host():
     h = ctx.align(mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-9, max_iters=20)
     dev = torch.device("cuda", 0)
     t = lambda a, dt=torch.float64: torch.as_tensor(np.asarray(a), dtype=dt, device=dev).clone()
-    w, x = t(wl.w_eval), t(wl.X.ravel())
-    stream = torch.cuda.current_stream().cuda_stream
-    d = ctx.align_dev(t(mu), w, x, t(mask, torch.uint8), tol=1e-9, max_iters=20, stream=stream)
+    # inputs produced on a stream of their own, which the call is given
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        w, x = t(wl.w_eval), t(wl.X.ravel())
+        d = ctx.align_dev(t(mu), w, x, t(mask, torch.uint8), tol=1e-9, max_iters=20, stream=side.cuda_stream)
     torch.cuda.synchronize()
     assert d["status"] == h["status"] and d["iters"] == h["iters"] and d["cg_iters"] == h["cg_iters"]
     np.testing.assert_array_equal(w.cpu().numpy(), h["w"])
