@@ -798,7 +798,7 @@ def run_align(args):
         wl = W.euler_workload(n=200, p=3, k_u=40, k_x=8, seed=4)
     else:
         wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2)
-    ctx = ift.Context.from_workload(wl, kappa=0.1)
+    ctx = ift.Context.from_workload(wl, kappa=0.1, align_cg_tol=args.align_cg_tol)
     mu = wl.mus[0]
     inner = np.all((wl.X > 1e-12) & (wl.X < 1 - 1e-12), axis=1)
     mask = np.repeat(inner, 2)
@@ -829,6 +829,7 @@ def run_align(args):
     tf = cg_flops / (ms_cg_iter * 1e-3) / 1e12
     gbs = cg_bytes / (ms_cg_iter * 1e-3) / 1e9
     print(json.dumps({"mode": "align", "elements": ne, "p": wl.p, "k_u": wl.ku, "free_coordinates": int(mask.sum()),
+                      "cg_tol": args.align_cg_tol,
                       "lm_steps": r["iters"], "cg_iters": r["cg_iters"], "trials": r["trials"],
                       "s_per_alignment": t, "ms_form_per_point": r["ms_form"] / (r["iters"] + 1),
                       "ms_cg_per_iter": ms_cg_iter, "ms_search_per_trial": r["ms_search"] / max(r["trials"], 1),
@@ -875,6 +876,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=1500, help="--mode warmstart: training epochs")
     ap.add_argument("--single-sample", type=int, default=32, help="--mode warmstart: one-query FP64 solves timed")
     ap.add_argument("--align-iters", type=int, default=5, help="--mode align: Levenberg-Marquardt steps per alignment")
+    ap.add_argument("--align-cg-tol", type=float, default=1e-12,
+                    help="--mode align: relative residual of the CG solves (1e-12: exact steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

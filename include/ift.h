@@ -103,10 +103,14 @@ typedef struct {
   int q;              /* geometry degree: 1 straight-sided, 2 curved six-node triangles (IFT_EULER2D only;
                          ift_set_mesh then takes the three vertices and the midpoint nodes of edges
                          0-1, 1-2, 2-0 of every element, and the mesh modes act on all those nodes) */
+  double align_cg_tol; /* ift_align: relative residual at which each conjugate-gradient solve stops,
+                          in [0, 1); 0 selects 1e-12, where every step is the exact Levenberg-Marquardt
+                          step (within rounding); larger values take inexact steps (fewer CG iterations,
+                          the same stopping test on |J^T F|) */
 } ift_config;
 
 /* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,
-   max_iters 200, FP64, IFT_INIT_PAPER, IFT_CONTRACT_FP. */
+   max_iters 200, FP64, IFT_INIT_PAPER, IFT_CONTRACT_FP, align_cg_tol 1e-12. */
 void ift_config_default(ift_config* cfg);
 
 /* Creates a context on the current CUDA device. stream: a cudaStream_t to run on

@@ -430,6 +430,7 @@ void ift_config_default(ift_config* cfg) {
   cfg->max_iters = 200;
   cfg->lm_init = IFT_INIT_PAPER;
   cfg->contraction = IFT_CONTRACT_FP;
+  cfg->align_cg_tol = 1e-12;
 }
 
 const char* ift_create_error(void) { return g_create_error.c_str(); }
@@ -461,6 +462,10 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->contraction != IFT_CONTRACT_TF32 &&
       cfg->contraction != IFT_CONTRACT_3XTF32 && cfg->contraction != IFT_CONTRACT_BF16) {
     g_create_error = "contraction must be IFT_CONTRACT_FP, _TF32, _3XTF32 or _BF16";
+    return IFT_ERR_ARG;
+  }
+  if (!(cfg->align_cg_tol >= 0.0 && cfg->align_cg_tol < 1.0)) {
+    g_create_error = "align_cg_tol must lie in [0, 1)";
     return IFT_ERR_ARG;
   }
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->precision == IFT_FP64) {
@@ -2180,7 +2185,7 @@ ift_status align_run(ift_ctx* c, const double* mu, double* w, double* x, const u
   const double c1 = 1e-4, round_tol = 16.0 * 2.220446049250313e-16;
   double lam = 1e-4;
   CGState cg0{};
-  cg0.tol = 1e-12;
+  cg0.tol = c->cfg.align_cg_tol > 0.0 ? c->cfg.align_cg_tol : 1e-12;
   cg0.max_iters = (int)std::min<long>(4 * n + 20, 2000);
   cg0.done = 1;
   // (1/2)|F|^2 at (ww, xx) by the residual-only pass; +inf where an element is

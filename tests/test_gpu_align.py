@@ -244,3 +244,30 @@ def test_alignment_device_pointer_variant_matches_host():
     np.testing.assert_array_equal(w.cpu().numpy(), h["w"])
     np.testing.assert_array_equal(x.cpu().numpy(), h["x"])
     assert d["J"] == h["J"]
+
+
+def test_inexact_cg_steps_reach_the_same_point():
+    # align_cg_tol = 1e-2: inexact Levenberg-Marquardt steps, the same stopping test on
+    # |J^T F|, so the aligned point is the oracle's (exact-step) one
+    name, kw, kappa = CASES[0]
+    wl = W.euler_workload(**kw)
+    O = orc.Oracle.from_workload(wl, kappa=kappa)
+    mu = np.array([2.1, 0.01])
+    mask = interior_mask(wl.X)
+    ref = O.align(wl.Phi, mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-7, max_iters=300)
+    exact = ift.Context.from_workload(wl, kappa=kappa).align(mu, wl.w_eval, wl.X.ravel(), mask, tol=1e-7,
+                                                              max_iters=300)
+    loose = ift.Context.from_workload(wl, kappa=kappa, align_cg_tol=1e-2).align(mu, wl.w_eval, wl.X.ravel(), mask,
+                                                                                 tol=1e-7, max_iters=300)
+    assert ref["status"] == 0 and exact["status"] == 0 and loose["status"] == 0
+    assert loose["cg_iters"] < exact["cg_iters"]
+    assert abs(loose["J"] - ref["J"]) <= 1e-6 * ref["J"]
+    assert np.abs(loose["x"] - ref["x"]).max() <= 1e-5
+    assert np.linalg.norm(loose["w"] - ref["w"]) <= 1e-5 * np.linalg.norm(ref["w"])
+
+
+def test_align_cg_tol_is_validated():
+    with pytest.raises(ift.IFTError):
+        ift.Context(ift.EULER2D, 1, align_cg_tol=1.0)
+    with pytest.raises(ift.IFTError):
+        ift.Context(ift.EULER2D, 1, align_cg_tol=-1e-3)
