@@ -421,7 +421,7 @@ struct ElemCore {
   }
   __device__ __forceinline__ T ntv(int pt, int k, int d) const {
     if constexpr (Dd::CURVED) return ntq[pt * 2 + d];
-    else return nt[k][d];
+    else return k == 0 ? nt[0][d] : (k == 1 ? nt[1][d] : nt[2][d]);  // selects: k is lane-dependent
   }
 
   // Curved element geometry (Eq. p2r-flux with the six-node quadratic map
