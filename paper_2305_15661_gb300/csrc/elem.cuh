@@ -1860,8 +1860,10 @@ __device__ inline int acc_source(int i, int k) {
 
 // The fused assembly kernel (JAC = true) and the objective-only kernel (JAC = false)
 // for one query: a grid-stride loop of warps over the items; one FP64 partial per CTA.
+// The FP32 Jacobian form is capped at 168 registers (3 CTAs of 128 threads, 6 of
+// the 64-thread CTAs it runs with); its small spill costs less than lost warps.
 template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
-__global__ void __launch_bounds__(128) assemble_kernel(AsmArgs<T> a) {
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? 3 : 0) assemble_kernel(AsmArgs<T> a) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip != nullptr && *(volatile const int*)a.skip) return;
