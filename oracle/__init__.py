@@ -67,7 +67,7 @@ def _load():
             "orc_global_jacobian": (i, [vp, pd, pd, pd, pd, pd, pd]),
             "orc_reduced": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, pd, pd, pd, pd, i]),
             "orc_objective": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, pd, i]),
-            "orc_solve": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, i, d, i, pd, pd, pd, pd, pi, i]),
+            "orc_solve": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, i, d, i, pd, pd, pd, pd, pi, i, pd, pi]),
             "orc_num_threads": (i, []),
             "orc_shear_state": (None, [d, d, d, pd]),
         }
@@ -296,14 +296,15 @@ class Oracle:
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.Nu, self.Nu))
 
     # -- snapshot alignment (Eq. align0) --------------------------------------
-    def align(self, Phi, mu, w0, x0, free_mask, tol=1e-8, max_iters=100):
+    def align(self, Phi, mu, w0, x0, free_mask, tol=1e-8, max_iters=100, trace=False):
         """min over (w, x_free) of (1/2)|F|^2, F = [R(Phi w, x; mu); N(x)], every element
         weight 1, by Levenberg-Marquardt on the dense global Jacobians (small meshes
         only). The step solves (J^T J + lambda D) d = -J^T F exactly (D = 1 on the mesh
         coordinates, 0 on w), with the damping and line-search rules of the reduced
         solve (lambda_0 = 1e-4, /10 after a full step, x10 after a shortened one,
         Armijo 1e-4 with 16 ulp of |J|, at most 30 halvings); stops when
-        |J^T F| <= tol max(1, |J^T F| at the start)."""
+        |J^T F| <= tol max(1, |J^T F| at the start). With trace=True the result carries
+        "trace": one row per accepted step, [lambda used, alpha, w..., x_free...]."""
         Phi = np.asarray(Phi, dtype=np.float64)
         free = np.nonzero(np.asarray(free_mask).ravel())[0]
         w = np.array(w0, dtype=np.float64)
@@ -327,6 +328,7 @@ class Oracle:
         g0 = np.linalg.norm(g)
         thresh = tol * max(1.0, g0)
         lam, iters, trials, status = 1e-4, 0, 0, 1
+        rows = []
         D = np.concatenate([np.zeros(ku), np.ones(nf)])
         while True:
             if np.linalg.norm(g) <= thresh:
@@ -354,13 +356,17 @@ class Oracle:
             if not accepted:
                 status = 2
                 break
+            rows.append(np.concatenate([[lam, alpha], wt, xt[free]]))
             lam = max(lam / 10, 1e-12) if h == 0 else min(lam * 10, 1e8)
             w, x, F, J = wt, xt, Ft, Jt
             iters += 1
             Jm = jac(w, x)
             g = Jm.T @ F
-        return {"status": status, "w": w, "x": x, "J": J, "gnorm": float(np.linalg.norm(g)), "g0": float(g0),
-                "iters": iters, "trials": trials}
+        out = {"status": status, "w": w, "x": x, "J": J, "gnorm": float(np.linalg.norm(g)), "g0": float(g0),
+               "iters": iters, "trials": trials}
+        if trace:
+            out["trace"] = np.array(rows).reshape(-1, 2 + ku + nf)
+        return out
 
     # -- reduced level -----------------------------------------------------
     @staticmethod
@@ -398,8 +404,10 @@ class Oracle:
         return float(J[0]), int(bad)
 
     def solve(self, Phi, Psi, mu, w_guess, tau0=None, rho_set=None, do_init=True, tol=1e-8, max_iters=200,
-              nthreads=0):
-        """Levenberg-Marquardt solve (Sec. 3.2.3, Remark rem:solver)."""
+              nthreads=0, trace=False):
+        """Levenberg-Marquardt solve (Sec. 3.2.3, Remark rem:solver). With trace=True the
+        result carries "trace": one row per accepted step, [phase (0 init, 1 joint),
+        lambda used in the step, step length alpha, w..., tau...]."""
         Phi = _f64(Phi)
         Psi = _f64(Psi)
         ku, kx = Phi.shape[1], Psi.shape[1]
@@ -410,10 +418,15 @@ class Oracle:
         hist = np.zeros(2 * (max_iters + 2))
         nh = np.zeros(1, dtype=np.int32)
         t0 = None if tau0 is None else _f64(tau0)
+        tr = np.zeros(2 * (max_iters + 1) * (ku + kx + 3)) if trace else None
+        ntr = np.zeros(1, dtype=np.int32)
         st = _load().orc_solve(self._h, ku, _pd(Phi), kx, _pd(Psi), nnz, _pi(el), _pd(rh), _pd(_f64(mu)),
                                _pd(_f64(w_guess)), _pd(t0), int(do_init), tol, max_iters, _pd(w), _pd(tau),
-                               _pd(info), _pd(hist), _pi(nh), nthreads)
-        return {"status": int(st), "w": w, "tau": tau[:kx], "init_iters": int(info[1]),
-                "iters": int(info[2]), "trials": int(info[3]), "shifts": int(info[4]), "J": info[5],
-                "normS": info[6], "normT": info[7], "g0": info[8], "init_status": int(info[9]),
-                "hist": hist[: int(nh[0])]}
+                               _pd(info), _pd(hist), _pi(nh), nthreads, _pd(tr), _pi(ntr) if trace else None)
+        out = {"status": int(st), "w": w, "tau": tau[:kx], "init_iters": int(info[1]),
+               "iters": int(info[2]), "trials": int(info[3]), "shifts": int(info[4]), "J": info[5],
+               "normS": info[6], "normT": info[7], "g0": info[8], "init_status": int(info[9]),
+               "hist": hist[: int(nh[0])]}
+        if trace:
+            out["trace"] = tr[: int(ntr[0]) * (ku + kx + 3)].reshape(-1, ku + kx + 3)
+        return out

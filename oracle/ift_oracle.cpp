@@ -1197,8 +1197,11 @@ struct PhaseStats {
 
 // One LM run. full = false optimises w alone with tau frozen (the initialisation
 // of Remark rem:solver); full = true optimises (w, tau) jointly.
+// trace (may be null) receives one row per accepted step:
+// [phase (0 init, 1 joint), lambda used in the step, step length alpha, w (ku), tau (kx)].
 void lm_phase(const Problem& P, bool full, double* w, double* tau, double tol, int max_iters,
-              PhaseStats& st, std::vector<double>& hist, double* Jout, double* S, double* T) {
+              PhaseStats& st, std::vector<double>& hist, double* Jout, double* S, double* T,
+              std::vector<double>* trace) {
   const int ku = P.ku, kx = P.kx, k = ku + kx;
   const int ka = full ? k : ku;
   std::vector<double> H(k * k);
@@ -1283,9 +1286,17 @@ void lm_phase(const Problem& P, bool full, double* w, double* tau, double tol, i
       st.status = ST_LINESEARCH;
       break;
     }
+    const double lam_used = lam;
     lam = (h == 0) ? std::max(lam / 10.0, LM_LAMBDA_MIN) : std::min(lam * 10.0, LM_LAMBDA_MAX);
     for (int c = 0; c < ku; ++c) w[c] = wt[c];
     for (int c = 0; c < kx; ++c) tau[c] = tt[c];
+    if (trace) {
+      trace->push_back(full ? 1.0 : 0.0);
+      trace->push_back(lam_used);
+      trace->push_back(alpha);
+      for (int c = 0; c < ku; ++c) trace->push_back(w[c]);
+      for (int c = 0; c < kx; ++c) trace->push_back(tau[c]);
+    }
     ++st.iters;
     reduced_assemble(*P.O, ku, P.Phi, kx, P.Psi, P.nnz, P.elems, P.rho, w, tau, P.mu, true, S, T, H.data(), &J,
                      P.nthreads);
@@ -1557,26 +1568,30 @@ int orc_objective(void* h, int ku, const double* Phi, int kx, const double* Psi,
 // info[16]: 0 status, 1 init iters, 2 main iters, 3 line-search trials, 4 shifts,
 //           5 J, 6 |S|, 7 |T|, 8 |g| at start of main phase, 9 init status.
 // hist: J after every accepted step (init then main), at most 2*(max_iters+1) values.
+// trace (may be null): rows of lm_phase's trace, at most 2*(max_iters+1) rows of ku+kx+3 values;
+// ntrace receives the row count.
 int orc_solve(void* h, int ku, const double* Phi, int kx, const double* Psi, long nnz, const int* elems,
               const double* rho, const double* mu, const double* w_guess, const double* tau0, int do_init,
               double tol, int max_iters, double* w, double* tau, double* info, double* hist, int* nhist,
-              int nthreads) {
+              int nthreads, double* trace, int* ntrace) {
   Oracle* O = (Oracle*)h;
   Problem P{O, ku, kx, Phi, Psi, nnz, elems, rho, mu, nthreads};
   for (int c = 0; c < ku; ++c) w[c] = w_guess[c];
   for (int c = 0; c < kx; ++c) tau[c] = tau0 ? tau0[c] : 0.0;
-  std::vector<double> S(ku), T(kx > 0 ? kx : 1), hv;
+  std::vector<double> S(ku), T(kx > 0 ? kx : 1), hv, tr;
+  std::vector<double>* trp = trace ? &tr : nullptr;
   double J = 0.0;
   PhaseStats s0, s1;
   if (do_init) {
-    lm_phase(P, false, w, tau, tol, max_iters, s0, hv, &J, S.data(), T.data());
+    lm_phase(P, false, w, tau, tol, max_iters, s0, hv, &J, S.data(), T.data(), trp);
     if (s0.status == ST_NONPHYS_START) {
       info[0] = ST_NONPHYS_START;
       *nhist = 0;
+      if (ntrace) *ntrace = 0;
       return ST_NONPHYS_START;
     }
   }
-  lm_phase(P, true, w, tau, tol, max_iters, s1, hv, &J, S.data(), T.data());
+  lm_phase(P, true, w, tau, tol, max_iters, s1, hv, &J, S.data(), T.data(), trp);
   double ns = 0.0, nt = 0.0;
   for (int c = 0; c < ku; ++c) ns += S[c] * S[c];
   for (int c = 0; c < kx; ++c) nt += T[c] * T[c];
@@ -1592,6 +1607,10 @@ int orc_solve(void* h, int ku, const double* Phi, int kx, const double* Psi, lon
   info[9] = s0.status;
   *nhist = (int)hv.size();
   for (size_t i = 0; i < hv.size(); ++i) hist[i] = hv[i];
+  if (trace) {
+    for (size_t i = 0; i < tr.size(); ++i) trace[i] = tr[i];
+    *ntrace = (int)(tr.size() / (size_t)(ku + kx + 3));
+  }
   return s1.status;
 }
 

@@ -91,3 +91,32 @@ def test_generic_alignment_reaches_first_order_condition():
     assert r["gnorm"] <= 1e-8 * max(1.0, r["g0"])
     F0 = np.concatenate(O.residual(wl.Phi @ wl.w_eval, wl.X.ravel(), mu)[:2])
     assert r["J"] < 0.5 * F0 @ F0
+
+
+def test_mesh_row_damping_by_hand():
+    """Two Burgers elements of degree 0 with the interior vertex free (tests/hand_lm.py
+    with eps = 1): Oracle.align's accepted steps, lambdas, step lengths and point equal
+    the hand-derived LM damped on the mesh row only. Damping the state row instead, or
+    swapping the lambda updates, leaves that path by far more than the tolerance."""
+    import hand_lm as HL
+    phi, mu = np.array([0.8, 1.1]), 1.4
+    X, ev = W.interval_mesh(2)
+    O = orc.Oracle(orc.PROB_BURGERS1D, 0, X, ev)
+    mask = np.array([False, True, False])
+    for z0 in [(0.4, 0.0), (1.5, 0.1), (1.9, -0.2)]:
+        x0 = X.copy()
+        x0[1] = 0.5 + z0[1]
+        r = O.align(phi[:, None], np.array([mu]), np.array([z0[0]]), x0, mask, tol=1e-12, max_iters=100,
+                    trace=True)
+        ref = HL.lm(z0, phi, 1.0, mu, 1e-12)
+        tr = r["trace"]
+        assert r["status"] == 0 and r["iters"] == len(ref) == tr.shape[0]
+        np.testing.assert_array_equal(tr[:, 0], ref[:, 0])
+        np.testing.assert_array_equal(tr[:, 1], ref[:, 1])
+        np.testing.assert_allclose(tr[:, 2], ref[:, 2], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(tr[:, 3], 0.5 + ref[:, 3], rtol=0, atol=1e-12)
+        assert r["x"][0] == 0.0 and r["x"][2] == 1.0
+        for wrong in (dict(damp="w"), dict(schedule="inverted")):
+            alt = HL.lm(z0, phi, 1.0, mu, 1e-12, **wrong)
+            n = min(len(alt), len(ref))
+            assert len(alt) != len(ref) or np.abs(alt[:n, 2:] - ref[:n, 2:]).max() > 1e-6, wrong

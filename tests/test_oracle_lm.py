@@ -4,6 +4,11 @@
   closed form u^2/2 - 1/2 - Q[s], so the Gauss-Newton iteration with the
   line-search reading is written out here by hand and must match the oracle's
   iterates, iteration count and final point;
+* two Burgers elements of degree 0 with one state and one mesh unknown: the
+  damped step (H + diag(0, lambda)) dz = -g of Eqs. lmstep and levmarq-step and
+  the lambda schedule (lambda_0 = 1e-4, lambda/10 after a full step, 10 lambda
+  after a shortened one) are written out by hand (tests/hand_lm.py) and must give
+  the oracle's steps, lambdas, step lengths and point;
 * on the Burgers and Euler workloads: convergence to the optimality tolerance,
   monotone decrease of J, symmetric positive definite H at the solution, and the
   tau = 0 initialisation.
@@ -126,3 +131,36 @@ def test_given_start_skips_init():
     assert warm["init_iters"] == 0
     assert warm["iters"] <= 1
     np.testing.assert_allclose(warm["w"], full["w"], rtol=1e-9)
+
+
+# -- damping placement and lambda schedule (Eqs. levmarq-step and lmstep) -----------
+
+@pytest.mark.parametrize("z0", [(0.4, 0.0), (1.5, 3.0), (0.9, -4.0)])
+def test_damped_two_unknown_step_by_hand(z0):
+    """Two Burgers elements of degree 0, one state and one mesh unknown (tests/hand_lm.py):
+    the oracle's accepted steps, the lambda each used, the step lengths and the final
+    point equal the hand-derived LM. The start (0.4, 0) needs a halved first step, so
+    both lambda updates are taken. The same hand iteration with the damping moved to the
+    w block, or with the two lambda updates swapped, leaves the oracle's path by far more
+    than the tolerance, so either mistake in the oracle would fail here."""
+    import hand_lm as HL
+    phi, eps, mu = np.array([0.8, 1.1]), 0.02, 1.4
+    X, ev = W.interval_mesh(2)
+    O = orc.Oracle(orc.PROB_BURGERS1D, 0, X, ev)
+    Phi = phi[:, None]
+    Psi = np.array([[0.0], [eps], [0.0]])  # one mode moving the interior vertex
+    res = O.solve(Phi, Psi, np.array([mu]), np.array([z0[0]]), tau0=np.array([z0[1]]), do_init=False,
+                  tol=1e-12, trace=True)
+    ref = HL.lm(z0, phi, eps, mu, 1e-12)
+    tr = res["trace"]
+    assert res["status"] == 0 and res["iters"] == len(ref) == tr.shape[0]
+    assert np.all(tr[:, 0] == 1.0)
+    np.testing.assert_array_equal(tr[:, 1], ref[:, 0])  # lambda: exact powers of ten
+    np.testing.assert_array_equal(tr[:, 2], ref[:, 1])  # alpha: exact powers of two
+    np.testing.assert_allclose(tr[:, 3:], ref[:, 2:], rtol=0, atol=1e-12)
+    if z0 == (0.4, 0.0):
+        assert ref[0, 1] < 1.0 and ref[1, 0] == 1e-3 and ref[2, 0] == 1e-4
+    for wrong in (dict(damp="w"), dict(schedule="inverted")):
+        alt = HL.lm(z0, phi, eps, mu, 1e-12, **wrong)
+        n = min(len(alt), len(ref))
+        assert len(alt) != len(ref) or np.abs(alt[:n, 2:] - ref[:n, 2:]).max() > 1e-3, wrong
