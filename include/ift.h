@@ -107,10 +107,17 @@ typedef struct {
                           in [0, 1); 0 selects 1e-12, where every step is the exact Levenberg-Marquardt
                           step (within rounding); larger values take inexact steps (fewer CG iterations,
                           the same stopping test on |J^T F|) */
+  int max_loop_bodies; /* bound on the LM loop bodies a solve (or a batched solve) runs on the device, each
+                          body one evaluation at a trial point and one LM step; 0 selects
+                          (2 max_iters + 4) * 34, which no solve within max_iters per phase reaches. When
+                          the bound is reached the solve ends with IFT_ERR_TIMEOUT, the last accepted
+                          point in y, z, and the context stays usable. The bound is a count kept by the
+                          LM step kernel: nothing on the device waits or spins. */
 } ift_config;
 
 /* Fills cfg with the defaults: gamma 1.4, kappa 0, eps_g 1e-8, tol 1e-8,
-   max_iters 200, FP64, IFT_INIT_PAPER, IFT_CONTRACT_FP, align_cg_tol 1e-12. */
+   max_iters 200, FP64, IFT_INIT_PAPER, IFT_CONTRACT_FP, align_cg_tol 1e-12,
+   max_loop_bodies 0. */
 void ift_config_default(ift_config* cfg);
 
 /* Creates a context on the current CUDA device. stream: a cudaStream_t to run on
@@ -268,11 +275,12 @@ ift_status ift_element_gradients(ift_ctx* ctx, const double* mu, const double* y
                                  const int32_t* elems, double* out);
 
 /* Allocation-free variant of ift_reduced_residual_jacobian_dev, for callers that
-   cannot call cudaMalloc when they need the reduced system: code that is
-   capturing a stream into a CUDA graph, code that owns all device memory
-   through its own pool or arena, and latency-critical loops where an allocation
-   would synchronise the device. It has no counterpart in the paper: it computes
-   the same S~, T~, H, J~ (FP64) as the context-based call, without a context.
+   cannot call cudaMalloc when they need the reduced system: code that owns all
+   device memory through its own pool or arena and forbids other allocators,
+   programs that reserve their whole memory budget at start-up, and
+   latency-critical loops where an allocation would synchronise the device. It
+   has no counterpart in the paper: it computes the same S~, T~, H, J~ (FP64) as
+   the context-based call, without a context.
 
    Every pointer is a caller-owned DEVICE pointer: X (n_verts x dim),
    elem_verts (n_elems x (dim+1)), the face connectivity nbr / nbr_face
@@ -280,20 +288,36 @@ ift_status ift_element_gradients(ift_ctx* ctx, const double* mu, const double* y
    faces) and bc (n_elems x n_face: 0 interior, 1 far field (Euler) or inflow
    u = 1 (Burgers, the face with outward normal -x), 2 outflow (Burgers)),
    Phi (N_u x k_u), Psi (N_x x k_x), the weights (nnz pairs elem/rho, or
-   nnz = -1 for rho = 1 on every element), mu, y, z, and the outputs S, T, H, J
-   as in ift_reduced_residual_jacobian (any output may be NULL). stream: a
-   cudaStream_t or NULL for the default stream; the call is asynchronous.
+   nnz = -1 for rho = 1 on every element; repeated elements are each counted),
+   mu, y, z, and the outputs S, T, H, J as in ift_reduced_residual_jacobian (any
+   output may be NULL). stream: a cudaStream_t or NULL for the default stream.
 
-   The call allocates nothing: its scratch (reference tables, per-CTA partial
-   sums, the reduced result) lives in a 2 MiB array in the library's device
-   memory, held on every GPU that loads the library until the process exits.
-   Limits: k_u + k_x <= 64, p in 1..3. Larger sizes return IFT_ERR_ARG; bad
-   pointers or sizes return IFT_ERR_ARG, CUDA failures IFT_ERR_CUDA (no message
-   is stored: there is no context). The array is shared by all calls and keeps
-   the last call's contents; calls whose GPU work overlaps on one device (other
-   streams or host threads) race on it and must be serialised by the caller.
-   The first call on each device looks up the array's device address; make that
-   first call before any stream capture on that device. */
+   The call is asynchronous: its status covers only the host-side checks, and
+   two outcomes show only in the outputs once the stream has reached them.
+   - A non-physical state at some element (g <= 0, density or pressure <= 0)
+     gives J = +inf with status IFT_OK (the context-based call returns
+     IFT_ERR_NONPHYSICAL there, because it waits for the result).
+   - The device checks, before any assembly, every index the element kernel
+     will use for the listed elements (all elements when nnz = -1): the element
+     ids, their vertex ids (< n_verts) and neighbour ids (< n_elems), and that
+     every rho is finite and >= 0. On a violation no element is evaluated and
+     every output is NaN.
+
+   The call allocates nothing: its scratch (reference tables, an error flag,
+   per-CTA partial sums, the reduced result) lives in an 8 MiB array in the
+   library's device memory, held on every GPU that loads the library until the
+   process exits. Limits: k_u + k_x <= 64, p in 1..3; larger sizes, bad
+   pointers, nnz = 0 or nnz < -1 return IFT_ERR_ARG, CUDA failures IFT_ERR_CUDA
+   (no message is stored: there is no context). The partial sums take
+   k^2 + k + 2 doubles per CTA, so the grid is at most
+   (1,048,576 - 1,504 - (k^2 + k + 2 rounded up to 32)) / (k^2 + k + 2) CTAs:
+   about 250 at k = 64, still more than one per SM on a 152-SM GPU. The array is
+   shared by all calls and keeps the last call's contents (each call clears the
+   flag and overwrites what it reads); calls whose GPU work overlaps on one
+   device (other streams or host threads) race on it and must be serialised by
+   the caller. The first call on each device looks up the array's device
+   address and copies the reference tables into it with a synchronous
+   cudaMemcpy; later calls only launch kernels. */
 ift_status ift_reduced_residual_jacobian_static(
     int problem, int p, int64_t n_verts, const double* X, int64_t n_elems, const int32_t* elem_verts,
     const int32_t* nbr, const int32_t* nbr_face, const int8_t* bc, const double* Phi, int k_u,

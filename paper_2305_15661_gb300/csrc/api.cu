@@ -468,6 +468,10 @@ ift_status ift_create(const ift_config* cfg, void* stream, ift_ctx** out) {
     g_create_error = "align_cg_tol must lie in [0, 1)";
     return IFT_ERR_ARG;
   }
+  if (cfg->max_loop_bodies < 0) {
+    g_create_error = "max_loop_bodies must be >= 0";
+    return IFT_ERR_ARG;
+  }
   if (cfg->contraction != IFT_CONTRACT_FP && cfg->precision == IFT_FP64) {
     g_create_error = "tensor-core contraction needs IFT_FP32 or IFT_MIXED";
     return IFT_ERR_ARG;
@@ -946,7 +950,7 @@ LMConsts lm_consts(ift_ctx* c, double tol) {
   k.max_iters = c->cfg.max_iters;
   k.ku = c->ku;
   k.kx = c->kx;
-  k.body_limit = (2 * c->cfg.max_iters + 4) * 34;
+  k.body_limit = c->cfg.max_loop_bodies > 0 ? c->cfg.max_loop_bodies : (2 * c->cfg.max_iters + 4) * 34;
   k.max_halvings = kMaxHalvings;
   return k;
 }

@@ -1,11 +1,31 @@
 // Builds a KernelSet for one (problem, degree, precision) instantiation.
 #pragma once
+#include <mutex>
 #include <type_traits>
 
 #include "elem.cuh"
 #include "kernels.h"
 
 namespace ift {
+
+// Raises a kernel's dynamic shared-memory limit to at least smem bytes on the
+// current device and never lowers it: several callers (contexts planned for
+// different basis sizes, the allocation-free entry point) share one kernel
+// instantiation, and a launch planned by one of them must stay valid after
+// another has prepared the kernel for a smaller size.
+inline std::mutex& smem_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+template <class F>
+inline cudaError_t raise_smem(F* f, size_t smem) {
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
+  cudaFuncAttributes at;
+  cudaError_t e = cudaFuncGetAttributes(&at, (const void*)f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)at.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
 
 template <class T, int PROB, int P>
 struct KernelSetImpl {
@@ -33,19 +53,15 @@ struct KernelSetImpl {
   }
   static cudaError_t prepare(bool jac, size_t smem) {
     if (jac) {
-      cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = raise_smem(assemble_kernel<T, PROB, P, true>, smem);
       if (e != cudaSuccess) return e;
       if constexpr (kTC) {
-        e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = raise_smem(assemble_kernel<T, PROB, P, true, true>, smem);
         if (e != cudaSuccess) return e;
       }
-      return cudaFuncSetAttribute(inspect_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem);
+      return raise_smem(inspect_kernel<T, PROB, P>, smem);
     }
-    return cudaFuncSetAttribute(assemble_kernel<T, PROB, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return raise_smem(assemble_kernel<T, PROB, P, false>, smem);
   }
   static int blocks_per_sm(bool jac, int block, size_t smem) {
     int n = 0;
@@ -80,14 +96,11 @@ struct KernelSetImpl {
   }
   static cudaError_t prepare_batched(bool jac, size_t smem) {
     if (!jac)
-      return cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaError_t e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return raise_smem(assemble_batched_kernel<T, PROB, P, false>, smem);
+    cudaError_t e = raise_smem(assemble_batched_kernel<T, PROB, P, true>, smem);
     if constexpr (kTC) {
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = raise_smem(assemble_batched_kernel<T, PROB, P, true, true>, smem);
     }
     return e;
   }
@@ -110,15 +123,13 @@ struct KernelSetImpl {
   static cudaError_t element_gradients(const void* args, double* out, int grid, int block, size_t smem,
                                        cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
-    cudaError_t e = cudaFuncSetAttribute(element_gradients_kernel<T, PROB, P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem(element_gradients_kernel<T, PROB, P>, smem);
     if (e != cudaSuccess) return e;
     element_gradients_kernel<T, PROB, P><<<grid, block, smem, s>>>(a, out);
     return cudaGetLastError();
   }
   static cudaError_t prepare_norms(size_t smem) {
-    return cudaFuncSetAttribute(residual_norms_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return raise_smem(residual_norms_kernel<T, PROB, P>, smem);
   }
   static int blocks_per_sm_norms(int block, size_t smem) {
     int n = 0;
@@ -131,10 +142,8 @@ struct KernelSetImpl {
   }
   static int blocks_per_sm_grad(bool batched, int block, size_t smem) {
     int n = 0;
-    cudaError_t e = batched ? cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, false, true>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = batched ? raise_smem(assemble_batched_kernel<T, PROB, P, true, false, true>, smem)
+                            : raise_smem(assemble_kernel<T, PROB, P, true, false, true>, smem);
     if (e != cudaSuccess) return 0;
     e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                       &n, assemble_batched_kernel<T, PROB, P, true, false, true>, block, smem)
@@ -146,8 +155,7 @@ struct KernelSetImpl {
   static cudaError_t align_mode(const AsmArgs<T>& a, const double* Xref, const double* vU, const double* vx,
                                 const double* vN, double* outU, double* outX, int grid, int block, size_t smem,
                                 cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(align_kernel<T, PROB, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem(align_kernel<T, PROB, P, MODE>, smem);
     if (e != cudaSuccess) return e;
     align_kernel<T, PROB, P, MODE><<<grid, block, smem, s>>>(a, Xref, vU, vx, vN, outU, outX);
     return cudaGetLastError();
@@ -171,8 +179,7 @@ struct KernelSetImpl {
     int best_w = 0, best_occ = 0;
     for (int w : {4, 2, 1}) {
       const size_t smem = align_jac_smem(ku, w);
-      if (cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem) != cudaSuccess) {
+      if (raise_smem(align_jac_kernel<T, PROB, P>, smem) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
@@ -188,8 +195,7 @@ struct KernelSetImpl {
       }
     }
     if (best_occ < 1) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(align_jac_kernel<T, PROB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)align_jac_smem(ku, best_w));
+    cudaError_t e = raise_smem(align_jac_kernel<T, PROB, P>, align_jac_smem(ku, best_w));
     if (e != cudaSuccess) return e;
     long g = (n + best_w - 1) / best_w;
     if (g > (long)sm_count * best_occ) g = (long)sm_count * best_occ;
@@ -219,7 +225,7 @@ struct KernelSetImpl {
     using Dd = Disc<PROB, P>;
     auto kern = align_apply_kernel<Dd::NXE, 0>;
     // the shared-memory limit, set here (before any graph capture)
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem(kern, smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * w, smem);
@@ -249,8 +255,7 @@ struct KernelSetImpl {
   }
   static cudaError_t assemble_grad(const void* args, int grid, int block, size_t smem, cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
-    cudaError_t e = cudaFuncSetAttribute(assemble_kernel<T, PROB, P, true, false, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem(assemble_kernel<T, PROB, P, true, false, true>, smem);
     if (e != cudaSuccess) return e;
     assemble_kernel<T, PROB, P, true, false, true><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
@@ -259,8 +264,7 @@ struct KernelSetImpl {
                                            cudaStream_t s) {
     const AsmArgs<T>& a = *(const AsmArgs<T>*)args;
     const BatchArgs& b = *(const BatchArgs*)bargs;
-    cudaError_t e = cudaFuncSetAttribute(assemble_batched_kernel<T, PROB, P, true, false, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem(assemble_batched_kernel<T, PROB, P, true, false, true>, smem);
     if (e != cudaSuccess) return e;
     assemble_batched_kernel<T, PROB, P, true, false, true><<<grid, block, smem, s>>>(a, b);
     return cudaGetLastError();

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
     _fields_ = [("problem", ctypes.c_int), ("p", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("eps_g", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("lm_init", ctypes.c_int),
-                ("contraction", ctypes.c_int), ("q", ctypes.c_int), ("align_cg_tol", ctypes.c_double)]
+                ("contraction", ctypes.c_int), ("q", ctypes.c_int), ("align_cg_tol", ctypes.c_double),
+                ("max_loop_bodies", ctypes.c_int)]
 
 
 class AlignInfo(ctypes.Structure):
@@ -177,7 +178,8 @@ class Context:
 
     def __init__(self, problem: int, p: int, precision: int = FP64, gamma: float = 1.4, kappa: float = 0.0,
                  eps_g: float = 1e-8, tol: float = 1e-8, max_iters: int = 200, lm_init: int = INIT_PAPER,
-                 contraction: int = CONTRACT_FP, stream=None, q: int = 1, align_cg_tol: float = 1e-12):
+                 contraction: int = CONTRACT_FP, stream=None, q: int = 1, align_cg_tol: float = 1e-12,
+                 max_loop_bodies: int = 0):
         lib = load()
         cfg = Config()
         lib.ift_config_default(ctypes.byref(cfg))
@@ -185,6 +187,7 @@ class Context:
         cfg.gamma, cfg.kappa, cfg.eps_g, cfg.tol = gamma, kappa, eps_g, tol
         cfg.max_iters, cfg.lm_init, cfg.contraction = max_iters, lm_init, contraction
         cfg.align_cg_tol = align_cg_tol
+        cfg.max_loop_bodies = max_loop_bodies
         h = ctypes.c_void_p()
         st = lib.ift_create(ctypes.byref(cfg), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
         if st != IFT_OK:

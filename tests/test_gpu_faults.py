@@ -2,6 +2,8 @@
 traps or hangs the GPU): every bad input comes back as a status, and the context
 stays usable for the next good call."""
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -91,3 +93,39 @@ def test_bad_sizes_rejected():
         ctx.set_bases(np.zeros((wl.Phi.shape[0], 65)), wl.Psi)  # k_u + k_x > 64
     with pytest.raises(ift.IFTError):
         ift.MLP(2, 8, 17, 3)
+
+
+def test_loop_body_bound_ends_solve_with_timeout_and_context_recovers():
+    # The device loop of a solve is bounded by a count of loop bodies kept by the LM
+    # step kernel (no wait or spin on the device). A bound of 3 bodies ends the solve
+    # long before it converges; the status is IFT_ERR_TIMEOUT and the same context
+    # then evaluates exactly as a fresh one.
+    wl = W.euler_workload(n=6, p=1, k_u=5, k_x=2, seed=61)
+    ctx = ift.Context.from_workload(wl, max_loop_bodies=3)
+    with pytest.raises(ift.IFTError) as ei:
+        ctx.solve_rom(wl.mus[0])
+    assert ei.value.status == -6
+    fresh = ift.Context.from_workload(wl)
+    a = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    b = fresh.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert a["status"] == 0
+    np.testing.assert_array_equal(a["H"], b["H"])
+    assert a["J"] == b["J"]
+    full = fresh.solve_rom(wl.mus[0])
+    assert full["status"] == 0 and full["init_iters"] + full["iters"] > 3
+    # a batched solve under the same bound: every query ends with the same status
+    sets = W.eq_weight_sets(wl, 3, seed=62, lo=20, hi=40)
+    ctx.set_eq_weights_batched(sets)
+    mus = np.ascontiguousarray(np.stack([wl.mus[0]] * 3))
+    y, z = np.zeros(3 * wl.ku), np.zeros(3 * wl.kx)
+    info = (ift.SolveInfo * 3)()
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = ift.load().ift_solve_rom_batched(ctx._h, P(mus), P(y), P(z), info)
+    assert st == -6 and all(i.status == -6 for i in info)
+    assert ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)["status"] == 0
+
+
+def test_negative_loop_body_bound_is_rejected():
+    with pytest.raises(ift.IFTError) as ei:
+        _ctx(max_loop_bodies=-1)
+    assert ei.value.status == -1
