@@ -145,8 +145,9 @@ def measured_peaks():
     return {}
 
 
-def fp64_alu_peak():
-    """Measured FP64 FMA throughput of this GPU (TFLOP/s) from the FMA probe."""
+def probe_peak(precision: int = 0) -> float:
+    """Measured throughput of this GPU (TFLOP/s, best of 3) from the probe library:
+    precision 0 = FP64 FMA, 1 = FP32 FMA, 2 = FP64 tensor-core MMA (m8n8k4)."""
     import ctypes
 
     from paper_2305_15661_gb300 import build as B
@@ -158,9 +159,58 @@ def fp64_alu_peak():
     best = 0.0
     for _ in range(3):
         v = ctypes.c_double()
-        if lib.fma_probe(0, 152 * 8, 256, 4096, ctypes.byref(v)) == 0:
+        if lib.fma_probe(precision, 152 * 8, 256, 4096, ctypes.byref(v)) == 0:
             best = max(best, v.value / 1e12)
     return best
+
+
+def fp64_alu_peak():
+    """Measured FP64 FMA throughput of this GPU (TFLOP/s) from the FMA probe."""
+    return probe_peak(0)
+
+
+def cuda_event_timer(stream):
+    """A timer for replica_steps: runs fn between two CUDA events recorded on
+    `stream` (the stream the timed kernels are launched on) and returns its
+    device time in ms."""
+    import torch
+
+    def timer(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    return timer
+
+
+def replica_steps(step, steps, world, device, timer, before_step=None, sync=None):
+    """The timed region of one rank of a replicas-only job: a barrier and a device
+    synchronisation, `steps` calls of step() each timed by timer (before_step(),
+    e.g. an L2 flush, runs untimed before each), then a synchronisation and a
+    barrier. Returns (per-step ms, the job's seconds = the slowest rank's total,
+    the whole-job rate in steps per second over all ranks)."""
+    import torch.distributed as dist
+
+    multi = world > 1 and dist.is_available() and dist.is_initialized()
+    if multi:
+        dist.barrier()
+    if sync:
+        sync()
+    ms = []
+    for _ in range(steps):
+        if before_step:
+            before_step()
+        ms.append(timer(step))
+    if sync:
+        sync()
+    if multi:
+        dist.barrier()
+    total_s = max_over_ranks(sum(ms) / 1e3, device)
+    return ms, total_s, whole_job_rate(steps, world, total_s)
 
 
 def cpu_baseline_solve(wl, reps=1):
@@ -205,6 +255,115 @@ def run_reference(args):
     return 0
 
 
+def _timed_assemblies(call, stream, flush, steps, warmup):
+    """Median CUDA-event time (ms) of `call` on `stream`, L2 flushed before each."""
+    import torch
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    timer = cuda_event_timer(stream)
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ms.append(timer(call))
+    return statistics.median(ms)
+
+
+def measure_fp32_assembly(wl, dev, stream, flush, steps, warmup):
+    """The mixed solve's FP32 stage kernel on the benchmark workload: one fused FP32
+    assembly (R_e, Jacobians, contraction) at the evaluation point, against the
+    measured FP32 FMA peak."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32, stream=stream.cuda_stream)
+    shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
+    k = wl.ku + wl.kx
+    t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
+    mu, y, z = t(wl.mus[0]), t(wl.w_eval), t(wl.tau_eval)
+    S, T, H, J = (torch.zeros(n, dtype=torch.float64, device=dev) for n in (wl.ku, wl.kx, k * k, 1))
+    med = _timed_assemblies(lambda: ctx.reduced_residual_jacobian_dev(mu, y, z, S, T, H, J,
+                                                                      stream=stream.cuda_stream),
+                            stream, flush, steps, warmup)
+    ctx.close()
+    fl = perfmodel.flops_per_element(2, wl.p, wl.ku, wl.kx)["total"]
+    ach = fl * wl.n_elems / (med / 1e3) / 1e12
+    peak = probe_peak(1)
+    return {"kernel": "assemble_kernel<float,Euler,p=2,JAC>", "bound": "alu", "median_ms": med,
+            "achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak if peak else None,
+            "peak_source": "FP32 FMA probe on this GPU (measured)", "flops_per_element": fl,
+            "warps_per_cta": shapes[0]}
+
+
+def measure_batched(dev, stream, flush, steps, warmup):
+    """256 hyperreduced queries on the benchmark mesh (per-query weight sets of
+    100-2,000 elements) solved in one graph, FP64 and mixed; plus one batched
+    evaluation of all queries at a common point, timed alone, for the gather's
+    bytes per second (each sampled element reads its own Phi rows and its
+    neighbours' trace rows) and its FLOP rate."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift, perfmodel
+    from paper_2305_15661_gb300 import workloads as W
+
+    B = 256
+    wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=B, mu_box=True)
+    sets = W.eq_weight_sets(wl, B, seed=3)
+    n_sampled = int(sum(len(e) for e, _ in sets))
+    mus = torch.as_tensor(wl.mus, dtype=torch.float64, device=dev)
+    y = torch.zeros((B, wl.ku), dtype=torch.float64, device=dev)
+    z = torch.zeros((B, wl.kx), dtype=torch.float64, device=dev)
+    st = torch.zeros(B, dtype=torch.int32, device=dev)
+    fl = perfmodel.flops_per_element(2, 2, wl.ku, wl.kx)["total"]
+    hbm = measured_peaks().get("hbm_gbs")
+    out = {"workload": "euler2d_p2_20000el_ku20_kx4_256q_rho100to2000", "queries": B,
+           "sampled_elements": n_sampled, "tol": 1e-8}
+    points = {}
+    for name, prec in (("fp64", ift.FP64), ("mixed", ift.MIXED)):
+        ctx = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream)
+        ctx.set_eq_weights_batched(sets)
+        shapes = ctx.autotune(wl.mus[0], wl.w_eval, wl.tau_eval)
+        info = ctx.solve_rom_batched(wl.mus)
+        med = _timed_assemblies(lambda: ctx.solve_rom_batched_dev(mus, y, z, st, stream=stream.cuda_stream),
+                                stream, flush, steps, 1)
+        stat = np.array([i["status"] for i in info["info"]])
+        conv = int((stat == 0).sum())
+        row = {"ms_per_batch": med, "solves_per_s": B / (med / 1e3), "converged": conv,
+               "converged_solves_per_s": conv / (med / 1e3),
+               "mean_lm_iters": float(np.mean([i["init_iters"] + i["iters"] + i["fp32_iters"]
+                                               for i in info["info"]])),
+               "launch_shapes": list(shapes)}
+        points[name] = (stat, np.concatenate([info["w"], info["tau"]], axis=1),
+                        np.array([i["J"] for i in info["info"]]))
+        # the gather: one batched evaluation of every query at the evaluation point
+        ys = np.tile(wl.w_eval, (B, 1))
+        zs = np.tile(wl.tau_eval, (B, 1))
+        ev_ms = _timed_assemblies(lambda: ctx.reduced_residual_jacobian_batched(wl.mus, ys, zs), stream, flush,
+                                  steps, warmup)
+        word = 8 if prec == ift.FP64 else 4
+        gathered = n_sampled * perfmodel.gather_bytes_per_element(2, 2, wl.ku, word)
+        gbs = gathered / (ev_ms / 1e3) / 1e9
+        row["gather"] = {"kernel": "assemble_batched_kernel<%s,Euler,p=2,JAC>" % ("double" if word == 8 else "float"),
+                         "ms_per_evaluation": ev_ms, "gathered_bytes": gathered, "gbs": gbs,
+                         "hbm_peak_gbs": hbm, "frac_of_hbm": gbs / hbm if hbm else None,
+                         "achieved_tflops": n_sampled * fl / (ev_ms / 1e3) / 1e12,
+                         "timed": "host call: the query points in, one batched assembly and its per-query "
+                                  "reduction, S, T, H, J out"}
+        out[name] = row
+        ctx.close()
+    s64, z64, J64 = points["fp64"]
+    smx, zmx, Jmx = points["mixed"]
+    both = (s64 == 0) & (smx == 0)
+    out["mixed_vs_fp64"] = {
+        "both_converged": int(both.sum()),
+        "max_rel_dz": float(np.max(np.linalg.norm(zmx[both] - z64[both], axis=1) / np.linalg.norm(z64[both], axis=1))),
+        "max_rel_dJ": float(np.max(np.abs(Jmx[both] - J64[both]) / J64[both]))}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -234,26 +393,14 @@ def run_ours(args):
     assert info is not None and info["status"] == 0, info
     assemblies = 1 + info["trials"]
 
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    step_ms = []
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
     with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=False)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
-    value = whole_job_rate(args.steps, world, total_s)
+        step_ms, total_s, value = replica_steps(
+            lambda: ctx.solve_rom_dev(mu_d, y_d, z_d, stream=stream.cuda_stream, want_info=False), args.steps,
+            world, dev, cuda_event_timer(stream), before_step=flush_l2, sync=torch.cuda.synchronize)
 
     # end to end through the host API: host mu in, y, z and info out
     e2e_steps = max(3, args.steps)
@@ -319,7 +466,15 @@ def run_ours(args):
     achieved_tf = assemblies * args.steps * fl * n_el / (sum(step_ms) / 1e3) / 1e12
     iso_tf = fl * n_el / (iso_ms / 1e3) / 1e12
     peak_tf = fp64_alu_peak()
+    mma_tf = probe_peak(2)
     evals_per_s = world * assemblies * args.steps * n_el / total_s
+
+    # the other configurations of the method, measured after the timed region
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["fp32_assembly"] = measure_fp32_assembly(wl, dev, stream, flush, max(5, args.steps), 3)
+        extras["batched"] = measure_batched(dev, stream, flush, 2, 3)
+        extras["warmstart"] = warmstart_measurement(dev, stream, ift.MIXED, ift.CONTRACT_FP, 2048, 4096, 1500, 2, 32)
 
     line = None
     if rank == 0:
@@ -347,8 +502,9 @@ def run_ours(args):
                              "traffic": FP64_ASSEMBLY_DRAM_BYTES,
                              "peak_source": "FP64 FMA probe on this GPU (measured)",
                              "flops_per_element": fl, "isolated_assembly_ms": iso_ms,
-                             "isolated_achieved": iso_tf},
+                             "isolated_achieved": iso_tf, "fp64_mma_probe_tflops": mma_tf},
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_solve * args.steps}
+        line.update(extras)
         print(json.dumps(line))
     ctx.close()
     if world > 1:
@@ -535,24 +691,38 @@ def run_warmstart(args):
     import torch
 
     from paper_2305_15661_gb300 import ift
-    from paper_2305_15661_gb300 import workloads as W
 
     dev = torch.device("cuda", 0)
     ift.load()
-    n_train, n_query = args.train_solves, args.queries
+    stream = torch.cuda.Stream(device=dev)
+    out = {"mode": "warmstart", "precision": args.precision, "contraction": args.contraction}
+    out.update(warmstart_measurement(dev, stream, _precision(args), _contraction(args), args.train_solves,
+                                     args.queries, args.epochs, args.steps, args.single_sample))
+    print(json.dumps(out))
+    return 0
+
+
+def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epochs, steps, single_sample):
+    """The measurement of run_warmstart, returned as a dict (also a key of the
+    default bench line). Every start is judged by the same FP64 stopping test; the
+    learned start's converged points are compared with the plain FP64 one-query
+    solves of the sample queries (same tolerance, projected start)."""
+    import torch
+
+    from paper_2305_15661_gb300 import ift
+    from paper_2305_15661_gb300 import workloads as W
+
     wl = W.euler_workload(n=100, p=2, k_u=40, k_x=8, seed=2)
     ku, kx = wl.ku, wl.kx
     rho_set = W.eq_weight_sets(wl, 1, seed=3, lo=400, hi=401)[0]
     mu_t = W.mu_box_samples(5, 1, n_train)
     mu_q = W.mu_box_samples(6, 1, n_query)
-    stream = torch.cuda.Stream(device=dev)
-    prec = _precision(args)
-    out = {"mode": "warmstart", "precision": args.precision, "contraction": args.contraction, "train_solves": n_train, "queries": n_query,
+    out = {"workload": "euler2d_p2_20000el_ku40_kx8_rho400", "train_solves": n_train, "queries": n_query,
            "rho_nnz": int(len(rho_set[0])), "k_u": ku, "k_x": kx}
 
     # training data: the method's own solves from the projected guess
     gen = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
-                                    contraction=_contraction(args))
+                                    contraction=contraction)
     gen.set_eq_weights_batched([rho_set] * n_train)
     out["launch_shapes"] = gen.autotune(mu_t[0], wl.w_eval, wl.tau_eval)
     torch.cuda.synchronize()
@@ -567,9 +737,9 @@ def run_warmstart(args):
     net = ift.MLP(2, 128, 3, ku + kx, seed=7, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out["train_loss"] = net.train(mu_t[ok], y_t, epochs=args.epochs, batch=64, lr=1e-3, seed=8)
+    out["train_loss"] = net.train(mu_t[ok], y_t, epochs=epochs, batch=64, lr=1e-3, seed=8)
     out["train_s"] = time.perf_counter() - t0
-    out["epochs"] = args.epochs
+    out["epochs"] = epochs
     t0 = time.perf_counter()
     start_mlp = net.predict(mu_q)
     out["predict_ms"] = 1e3 * (time.perf_counter() - t0)
@@ -578,11 +748,11 @@ def run_warmstart(args):
     out["nearest_ms"] = 1e3 * (time.perf_counter() - t0)
 
     given = ift.Context.from_workload(wl, precision=prec, tol=1e-8, lm_init=ift.INIT_GIVEN,
-                                      stream=stream.cuda_stream, contraction=_contraction(args))
+                                      stream=stream.cuda_stream, contraction=contraction)
     given.set_eq_weights_batched([rho_set] * n_query)
     given.set_launch_shapes(*out["launch_shapes"])
     paper = ift.Context.from_workload(wl, precision=prec, tol=1e-8, stream=stream.cuda_stream,
-                                      contraction=_contraction(args))
+                                      contraction=contraction)
     paper.set_eq_weights_batched([rho_set] * n_query)
     paper.set_launch_shapes(*out["launch_shapes"])
     ref = paper.solve_rom_batched(mu_q)
@@ -604,7 +774,7 @@ def run_warmstart(args):
             info = ctx.solve_rom_batched(mu_q, s[:, :ku], s[:, ku:])
             y0 = torch.as_tensor(np.ascontiguousarray(s[:, :ku]), device=dev)
             z0 = torch.as_tensor(np.ascontiguousarray(s[:, ku:]), device=dev)
-        ms = _time_batched(ctx, stream, mus, y0, z0, y, z, st, args.steps)
+        ms = _time_batched(ctx, stream, mus, y0, z0, y, z, st, steps)
         stat = np.array([i["status"] for i in info["info"]])
         its = np.array([i["init_iters"] + i["iters"] + i["fp32_iters"] for i in info["info"]])
         zf = np.concatenate([info["w"], info["tau"]], axis=1)
@@ -619,6 +789,8 @@ def run_warmstart(args):
         if s is not None:
             err = np.linalg.norm(s - z_ref, axis=1) / np.linalg.norm(z_ref, axis=1)
             row["median_start_err"] = float(np.median(err))
+        if name == "mlp":
+            mlp_status, mlp_z, mlp_J = stat, zf, Jf
         rows[name] = row
     out["starts"] = rows
     given.close()
@@ -627,18 +799,25 @@ def run_warmstart(args):
     # the plain FP64 one-query form on a sample of the same queries
     one = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
     one.set_eq_weights(rho_set)
-    n1 = min(args.single_sample, n_query)
+    n1 = min(single_sample, n_query)
     one.solve_rom(mu_q[0])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for q in range(n1):
-        one.solve_rom(mu_q[q])
+    singles = [one.solve_rom(mu_q[q]) for q in range(n1)]
     dt = time.perf_counter() - t0
-    out["fp64_one_query"] = {"sample": n1, "solves_per_s": n1 / dt}
+    # accuracy of the learned-start batched form against the FP64 one-query solves of
+    # the same queries: both pass the same FP64 stopping test
+    z1 = np.array([np.concatenate([r["w"], r["tau"]]) for r in singles])
+    J1 = np.array([r["J"] for r in singles])
+    ok1 = np.array([r["status"] == 0 for r in singles]) & (mlp_status[:n1] == 0)
+    out["fp64_one_query"] = {
+        "sample": n1, "solves_per_s": n1 / dt, "converged": int(sum(r["status"] == 0 for r in singles)),
+        "mlp_batched_max_rel_dz": float(np.max(np.linalg.norm(mlp_z[:n1][ok1] - z1[ok1], axis=1)
+                                               / np.linalg.norm(z1[ok1], axis=1))),
+        "mlp_batched_max_rel_dJ": float(np.max(np.abs(mlp_J[:n1][ok1] - J1[ok1]) / J1[ok1]))}
     out["speedup_mlp_batched_vs_fp64_one_query"] = rows["mlp"]["solves_per_s"] / (n1 / dt)
     one.close()
-    print(json.dumps(out))
-    return 0
+    return out
 
 
 def run_burgers(args):
@@ -851,6 +1030,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default mode: skip the FP32-assembly, batched and warm-start keys")
     ap.add_argument("--mode", choices=["solve", "assembly", "batched", "warmstart", "greedy", "burgers", "precisions",
                                            "align"],
                     default="solve",

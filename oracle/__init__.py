@@ -69,6 +69,8 @@ def _load():
             "orc_objective": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, pd, i]),
             "orc_solve": (i, [vp, i, pd, i, pd, l, pi, pd, pd, pd, pd, i, d, i, pd, pd, pd, pd, pi, i, pd, pi]),
             "orc_num_threads": (i, []),
+            "orc_count_element": (i, [vp, l, pd, pd, pd, pd, pd, pd, pd, ctypes.POINTER(ctypes.c_longlong)]),
+            "orc_count_pointwise": (None, [vp, i, pd, pd, pd, pd, ctypes.POINTER(ctypes.c_longlong)]),
             "orc_shear_state": (None, [d, d, d, pd]),
         }
         for name, (res, args) in sig.items():
@@ -294,6 +296,27 @@ class Oracle:
         cols = np.concatenate(cols)
         vals = np.concatenate(vals)
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.Nu, self.Nu))
+
+    # -- operation counts (work accounting) ------------------------------------
+    def count_element(self, e, Ue, Up, xe, mu, dUe=None, dUp=None, dxe=None):
+        """Floating-point operations of the oracle's element residual at (Ue, Up, xe):
+        (value operations of R_e, derivative operations of one forward-mode sweep along
+        the seeded direction; an input without a seed has a structurally zero
+        derivative and costs nothing)."""
+        out = np.zeros(2, dtype=np.int64)
+        opt = lambda a: None if a is None else _pd(_f64(a))
+        _load().orc_count_element(self._h, e, _pd(_f64(Ue)), _pd(_f64(Up)), _pd(_f64(xe)), _pd(_f64(mu)),
+                                  opt(dUe), opt(dUp), opt(dxe),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+        return int(out[0]), int(out[1])
+
+    def count_pointwise(self, which, Up, Um, n, d):
+        """Operations of one pointwise routine: which = 0 Euler flux f(U+), 1 Euler Roe
+        flux (U+ seeded), 2 Burgers Roe flux (u+ seeded). Returns (value, derivative)."""
+        out = np.zeros(2, dtype=np.int64)
+        _load().orc_count_pointwise(self._h, which, _pd(_f64(Up)), _pd(_f64(Um)), _pd(_f64(n)), _pd(_f64(d)),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+        return int(out[0]), int(out[1])
 
     # -- snapshot alignment (Eq. align0) --------------------------------------
     def align(self, Phi, mu, w0, x0, free_mask, tol=1e-8, max_iters=100, trace=False):

@@ -96,6 +96,93 @@ inline Dual dabs(Dual a) {
 inline double dmaxe(double a, double eps) { return a >= eps ? a : eps; }
 inline Dual dmaxe(Dual a, double eps) { return a.v >= eps ? a : Dual(eps, 0.0); }
 
+// ---------------------------------------------------------------------------
+// Operation counting (work accounting only; never used for results). Cnt is a
+// forward-mode dual number that counts the floating-point operations it performs:
+// prim counts the value's operations, tan the derivative's. A derivative that is
+// structurally zero (it does not depend on the seeded inputs) is tracked by the
+// flag z and costs nothing, so the tangent count is what a forward-mode sweep
+// along one direction needs. Each +, -, *, / counts one operation (a fused
+// multiply-add two), sqrt and exp one each; sign changes, |.|, max and
+// comparisons count none.
+// ---------------------------------------------------------------------------
+struct CntTally {
+  long long prim = 0, tan = 0;
+};
+thread_local CntTally g_cnt;
+
+struct Cnt {
+  double v, d;
+  bool z;
+  Cnt() : v(0.0), d(0.0), z(true) {}
+  Cnt(double a) : v(a), d(0.0), z(true) {}
+  Cnt(double a, double b, bool zero) : v(a), d(b), z(zero) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) {
+  g_cnt.prim += 1;
+  if (!a.z && !b.z) g_cnt.tan += 1;
+  return Cnt(a.v + b.v, a.d + b.d, a.z && b.z);
+}
+inline Cnt operator-(Cnt a, Cnt b) {
+  g_cnt.prim += 1;
+  if (!a.z && !b.z) g_cnt.tan += 1;
+  return Cnt(a.v - b.v, a.d - b.d, a.z && b.z);
+}
+inline Cnt operator-(Cnt a) { return Cnt(-a.v, -a.d, a.z); }
+inline Cnt operator*(Cnt a, Cnt b) {
+  g_cnt.prim += 1;
+  g_cnt.tan += (!a.z && !b.z) ? 3 : ((!a.z || !b.z) ? 1 : 0);
+  return Cnt(a.v * b.v, a.d * b.v + a.v * b.d, a.z && b.z);
+}
+inline Cnt operator/(Cnt a, Cnt b) {
+  g_cnt.prim += 1;
+  double q = a.v / b.v;
+  g_cnt.tan += (!a.z && !b.z) ? 3 : (!a.z ? 1 : (!b.z ? 2 : 0));
+  return Cnt(q, (a.d - q * b.d) / b.v, a.z && b.z);
+}
+inline Cnt operator+(Cnt a, double b) { g_cnt.prim += 1; return Cnt(a.v + b, a.d, a.z); }
+inline Cnt operator+(double a, Cnt b) { g_cnt.prim += 1; return Cnt(a + b.v, b.d, b.z); }
+inline Cnt operator-(Cnt a, double b) { g_cnt.prim += 1; return Cnt(a.v - b, a.d, a.z); }
+inline Cnt operator-(double a, Cnt b) { g_cnt.prim += 1; return Cnt(a - b.v, -b.d, b.z); }
+inline Cnt operator*(Cnt a, double b) {
+  g_cnt.prim += 1;
+  if (!a.z) g_cnt.tan += 1;
+  return Cnt(a.v * b, a.d * b, a.z);
+}
+inline Cnt operator*(double a, Cnt b) { return b * a; }
+inline Cnt operator/(Cnt a, double b) {
+  g_cnt.prim += 1;
+  if (!a.z) g_cnt.tan += 1;
+  return Cnt(a.v / b, a.d / b, a.z);
+}
+inline Cnt operator/(double a, Cnt b) {
+  g_cnt.prim += 1;
+  double q = a / b.v;
+  if (!b.z) g_cnt.tan += 2;
+  return Cnt(q, -q * b.d / b.v, b.z);
+}
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt& operator*=(Cnt& a, Cnt b) { a = a * b; return a; }
+inline double val(Cnt a) { return a.v; }
+inline Cnt dsqrt(Cnt a) {
+  g_cnt.prim += 1;
+  double s = std::sqrt(a.v);
+  if (!a.z) g_cnt.tan += 2;
+  return Cnt(s, a.d / (2.0 * s), a.z);
+}
+inline Cnt dexp(Cnt a) {
+  g_cnt.prim += 1;
+  double e = std::exp(a.v);
+  if (!a.z) g_cnt.tan += 1;
+  return Cnt(e, e * a.d, a.z);
+}
+inline Cnt dabs(Cnt a) {
+  double s = (a.v > 0.0) ? 1.0 : ((a.v < 0.0) ? -1.0 : 0.0);
+  return Cnt(std::fabs(a.v), s * a.d, a.z);
+}
+inline Cnt dmaxe(Cnt a, double eps) { return a.v >= eps ? a : Cnt(eps); }
+
 // Harten's entropy fix of a wave speed: |lam| when |lam| >= delta, else
 // (lam^2 + delta^2) / (2 delta), which joins |lam| with a continuous slope.
 template <class T>
@@ -416,6 +503,16 @@ inline double dsin(double a) { return std::sin(a); }
 inline double dcos(double a) { return std::cos(a); }
 inline Dual dsin(Dual a) { return Dual(std::sin(a.v), std::cos(a.v) * a.d); }
 inline Dual dcos(Dual a) { return Dual(std::cos(a.v), -std::sin(a.v) * a.d); }
+inline Cnt dsin(Cnt a) {
+  g_cnt.prim += 1;
+  if (!a.z) g_cnt.tan += 2;
+  return Cnt(std::sin(a.v), std::cos(a.v) * a.d, a.z);
+}
+inline Cnt dcos(Cnt a) {
+  g_cnt.prim += 1;
+  if (!a.z) g_cnt.tan += 2;
+  return Cnt(std::cos(a.v), -std::sin(a.v) * a.d, a.z);
+}
 
 // Exact steady parallel shear flow, used only as the boundary state of the
 // p-convergence test. With the flow direction d = (cos th, sin th), th = 0.4, and
@@ -1612,6 +1709,57 @@ int orc_solve(void* h, int ku, const double* Phi, int kx, const double* Psi, lon
     *ntrace = (int)(tr.size() / (size_t)(ku + kx + 3));
   }
   return s1.status;
+}
+
+// Operation counts of the element residual (work accounting, see Cnt): out[0] the
+// value's operations of R_e, out[1] the derivative's along the direction seeded by
+// dUe, dUp, dxe (each may be NULL: that input's derivative is then structurally
+// zero). Returns 1 if the state is non-physical.
+int orc_count_element(void* h, long e, const double* Ue, const double* Up, const double* xe, const double* mu,
+                      const double* dUe, const double* dUp, const double* dxe, long long* out) {
+  Oracle* O = (Oracle*)h;
+  const int nu = O->nu(), nup = O->nup(), nx = O->nxe();
+  std::vector<Cnt> cU(nu), cUp(nup), cx(nx), cR(nu);
+  for (int i = 0; i < nu; ++i) cU[i] = dUe ? Cnt(Ue[i], dUe[i], false) : Cnt(Ue[i]);
+  for (int i = 0; i < nup; ++i) cUp[i] = dUp ? Cnt(Up[i], dUp[i], false) : Cnt(Up[i]);
+  for (int i = 0; i < nx; ++i) cx[i] = dxe ? Cnt(xe[i], dxe[i], false) : Cnt(xe[i]);
+  bool np = false;
+  g_cnt = CntTally();
+  element_residual<Cnt>(*O, e, cU.data(), cUp.data(), cx.data(), mu, cR.data(), &np);
+  out[0] = g_cnt.prim;
+  out[1] = g_cnt.tan;
+  return np ? 1 : 0;
+}
+
+// Operation counts of one pointwise routine at a state (work accounting, see Cnt):
+// which = 0 the Euler flux f(U) with U seeded by d; 1 the Euler Roe flux
+// H(U+, U-; n) with U+ seeded by d; 2 the Burgers Roe flux with u+ seeded;
+// 3 the Euler Roe flux with both U+ and U- seeded by d; 4 the Euler Roe flux with
+// U- seeded by d.
+// out[0] value operations, out[1] derivative operations.
+void orc_count_pointwise(void* h, int which, const double* Up, const double* Um, const double* n, const double* d,
+                         long long* out) {
+  Oracle* O = (Oracle*)h;
+  g_cnt = CntTally();
+  if (which == 0) {
+    Cnt U[4], f[8], P;
+    for (int a = 0; a < 4; ++a) U[a] = Cnt(Up[a], d[a], false);
+    euler_flux<Cnt>(*O, U, f, P);
+  } else if (which == 1 || which == 3 || which == 4) {
+    Cnt a4[4], b4[4], nn[2], H[4];
+    for (int a = 0; a < 4; ++a) {
+      a4[a] = which != 4 ? Cnt(Up[a], d[a], false) : Cnt(Up[a]);
+      b4[a] = which >= 3 ? Cnt(Um[a], d[a], false) : Cnt(Um[a]);
+    }
+    nn[0] = Cnt(n[0]);
+    nn[1] = Cnt(n[1]);
+    euler_roe<Cnt>(O->gamma, a4, b4, nn, H);
+  } else {
+    Cnt up(Up[0], d[0], false), um(Um[0]), nn(n[0]);
+    burgers_roe<Cnt>(up, um, nn);
+  }
+  out[0] = g_cnt.prim;
+  out[1] = g_cnt.tan;
 }
 
 int orc_num_threads() {

@@ -1,32 +1,64 @@
 """Algorithmic work per element of the hot path, for roofline accounting.
 
-The count follows the explicit formulation of the method (Eqs. hdm_elem,
-levmarq-elem, ift-eqp-res0): form R_e, the element Jacobian blocks
-dR_e/dU_e, dR_e/dU_e', dR_e/dx_e, the reduced Jacobian A_e = [dR_e/dU_e Phi_e +
-dR_e/dU_e' Phi_e' | dR_e/dx_e Psi_e] and the weighted contraction
-A_e^T A_e, A_e^T R_e, |R_e|^2. One fused multiply-add counts as 2 FLOPs.
+One fused multiply-add counts as 2 FLOPs; +, -, *, /, sqrt and exp count 1.
 
-(a) element residual and Jacobians, per element:
-    volume, per quadrature point: interpolation 2 n_b m, flux C_f, flux
-    Jacobian C_A, contravariant flux 2 d^2 m and Jacobian 2 d^2 m^2;
-    volume test 2 n_q d n_b m; volume Jacobian block 2 n_q d n_b^2 m^2;
-    faces, per face point: two traces 4 n_t m, Roe flux C_roe and its 8 state
-    derivatives 8 C_roe, test 2 n_t m, face Jacobian blocks 4 n_t^2 m^2.
-(b) reduction (the contraction count of Eq. levmarq-elem plus g and J):
-    2 n_u k_u (n_u + n_u') + 2 n_u k_x n_x + n_u k (k + 1) + 2 n_u k + 2 n_u,
-    where n_u k (k + 1) is the symmetric product A_e^T A_e (its k (k + 1) / 2
-    distinct entries, each a length-n_u dot product).
-C_f = 20, C_A = 40, C_roe = 200 for Euler (operation counts of the pointwise
-routines); Burgers: C_f = 1, C_A = 0, C_roe = 12, plus the source
-(exp and 4 flops per point).
+The nonlinear pointwise routines are counted, not estimated: their values and
+one forward-mode derivative direction each were counted on an
+operation-counting instantiation of the independent FP64 implementation
+(``python -m oracle.workcount`` writes the constants below; a CPU test checks
+them). Everything else is linear algebra on the reference element, counted in
+closed form from its sizes (n_b nodes, n_q volume points, n_f faces of n_fq
+points, n_t trace nodes per face, m variables, d dimensions, n_u = n_b m,
+n_u' = n_f n_t m neighbour trace values, n_x = (d + 1) d mesh coordinates).
+
+Per element of the fused assembly (Eqs. hdm_elem, levmarq-elem, ift-eqp-res0):
+
+* reconstruction U_e = Phi_e w, U_e' = Phi_e' w, x_e = X_e + Psi_e tau:
+  2 (n_u + n_u') k_u + 2 n_x k_x;
+* the residual R_e: per volume point the interpolation 2 n_b m, the flux and
+  its contravariant form g f G^{-T} (2 d^2 m), the test sums 2 n_q d n_b m;
+  per face point the two traces 4 n_t m, the Roe flux, the lifting 2 n_t m;
+* the pointwise Jacobians, once per point: m derivative directions of the flux
+  at every volume point, m along U+ and m along U- of the Roe flux at every
+  face point;
+* the state columns of A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' | ...], by the
+  cheaper of the two standard forms:
+  - explicit: the blocks dR_e/dU_e (volume 2 n_q d n_b^2 m^2, faces
+    2 n_t^2 m^2 per point) and dR_e/dU_e' (2 n_t^2 m^2 per face point), then
+    the products 2 n_u k_u (n_u + n_u');
+  - directional: per column the interpolation, the pointwise Jacobians applied
+    (2 d m^2 per volume point, 4 m^2 per face point), the contravariant form and
+    the test sums, the traces and the lifting;
+* the mesh columns dR_e/dx_e Psi_e: per direction the contravariant change of
+  the volume flux (2 d^2 m per point) with the test sums, and the flux change
+  of the scaled normal at each face point (2 d m) with the lifting; taken along
+  the k_x columns, or along the n_x coordinates followed by 2 n_u k_x n_x when
+  that is fewer;
+* the weighted contraction: the symmetric A_e^T A_e (n_u k (k + 1): k (k + 1) / 2
+  dot products of length n_u), A_e^T R_e (2 n_u k) and |R_e|^2 (2 n_u).
+
+The geometry (a few dozen operations per element), the distortion term (kappa
+= 0 in the benchmark) and the weight multiplies are not counted, so the count
+is a lower bound on the work any implementation of the assembly does.
 
 Bytes per element of the full assembly (unique data): the element's Phi rows
 n_u k_u words, the Psi rows of its vertices n_x k_x, X_e and the connectivity;
 neighbour trace rows are counted once overall because every element's rows
-are read by its neighbours too (they hit in L2).
+are read by its neighbours too (they hit in L2). The hyperreduced gather of a
+sampled element reads its own Phi rows and its neighbours' trace rows:
+(n_u + n_u') k_u words.
 """
 
 from __future__ import annotations
+
+# Counted by oracle/workcount.py (value, derivative along one direction):
+EULER_FLUX = (19, 41)  # f(U)
+EULER_ROE = (203, 262, 262)  # H(U+, U-; n): value, along U+, along U-
+BURGERS_ROE = (17, 15)  # H(u+, u-; n): value, along u+
+# Burgers flux u^2/2 (2 value operations, 1 per derivative direction) and source
+# g 0.5 exp(mu x(xi)) with x(xi) = x_0 + h xi (5 value operations): closed forms.
+BURGERS_FLUX = (2, 1)
+BURGERS_SOURCE = 5
 
 
 def sizes(problem: int, p: int):
@@ -38,26 +70,54 @@ def sizes(problem: int, p: int):
 
 
 def flops_per_element(problem: int, p: int, ku: int, kx: int, jac: bool = True) -> dict:
+    """Algorithmic FLOPs of one element of the fused assembly (jac=True) or of the
+    residual-only pass (jac=False), with the breakdown by part."""
     s = sizes(problem, p)
     m, d, nb, nq, nf, nt, nfq = s["m"], s["d"], s["nb"], s["nq"], s["nf"], s["nt"], s["nfq"]
     nu, nup, nx = s["nu"], s["nup"], s["nx"]
     k = ku + kx
+    nfp = nf * nfq  # face points
     if problem == 1:
-        cf, ca, croe, csrc = 1, 0, 12, 5
+        fval, ftan = BURGERS_FLUX
+        hval, htan_p = BURGERS_ROE
+        htan_m = htan_p
+        src = BURGERS_SOURCE + 2 * nb * m  # the source and its test sum, per volume point
     else:
-        cf, ca, croe, csrc = 20, 40, 200, 0
-    recon = 2 * (nu + nup) * ku + 2 * nx * kx
-    vol_res = nq * (2 * nb * m + cf + 2 * d * d * m + csrc) + 2 * nq * d * nb * m
-    face_res = nf * nfq * (4 * nt * m + croe + 2 * nt * m)
-    a = recon + vol_res + face_res
-    b = 2 * nu  # |R|^2
+        fval, ftan = EULER_FLUX
+        hval, htan_p, htan_m = EULER_ROE
+        src = 0
+    test = 2 * nq * d * nb * m
+    out = {"reconstruction": 2 * (nu + nup) * ku + 2 * nx * kx}
+    out["residual"] = (nq * (2 * nb * m + fval + 2 * d * d * m + src) + test
+                       + nfp * (4 * nt * m + hval + 2 * nt * m))
+    out["objective"] = 2 * nu
     if jac:
-        a += nq * (ca + 2 * d * d * m * m) + 2 * nq * d * nb * nb * m * m
-        a += nf * nfq * (8 * croe + 4 * nt * nt * m * m)
-        b += 2 * nu * ku * (nu + nup) + 2 * nu * kx * nx + nu * k * (k + 1) + 2 * nu * k
-    return {"element": a, "reduction": b, "total": a + b}
+        out["pointwise_jacobians"] = nq * m * ftan + nfp * m * (htan_p + htan_m)
+        explicit = (2 * nq * d * nb * nb * m * m + nfp * 4 * nt * nt * m * m
+                    + 2 * nu * ku * (nu + nup))
+        directional = ku * (nq * (2 * nb * m + 2 * d * m * m + 2 * d * d * m) + test
+                            + nfp * (4 * nt * m + 4 * m * m + 2 * nt * m))
+        out["state_columns"] = min(explicit, directional)
+        out["state_columns_form"] = "explicit" if explicit <= directional else "directional"
+        per_dir = nq * 2 * d * d * m + test + nfp * (2 * d * m + 2 * nt * m)
+        out["mesh_columns"] = min(kx * per_dir, nx * per_dir + 2 * nu * kx * nx)
+        out["contraction"] = nu * k * (k + 1) + 2 * nu * k
+    parts = [v for key, v in out.items() if key != "state_columns_form"]
+    out["total"] = sum(parts)
+    # the two halves the benchmark reports: the element evaluation (residual and
+    # pointwise Jacobians) and the reduction to the k x k system
+    out["element"] = out["residual"] + out.get("pointwise_jacobians", 0)
+    out["reduction"] = out["total"] - out["element"]
+    return out
 
 
 def bytes_per_element(problem: int, p: int, ku: int, kx: int, word: int = 8) -> int:
     s = sizes(problem, p)
     return s["nu"] * ku * word + s["nv"] * s["d"] * (kx * 8 + 8) + s["nv"] * 4 + s["nf"] * 9
+
+
+def gather_bytes_per_element(problem: int, p: int, ku: int, word: int = 8) -> int:
+    """Basis rows a hyperreduced evaluation of one sampled element reads: its own
+    Phi rows and its neighbours' trace rows."""
+    s = sizes(problem, p)
+    return (s["nu"] + s["nup"]) * ku * word

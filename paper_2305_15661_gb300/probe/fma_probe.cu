@@ -1,7 +1,9 @@
-// FMA throughput probe used by the benchmark to measure the FP64 and FP32
-// ALU peaks of the GPU it runs on (the roofline denominators of the element
-// kernels). Each thread runs 8 independent FMA chains; the only memory access
-// is one store per thread at the end.
+// Throughput probes used by the benchmark to measure the FP64 and FP32 ALU
+// peaks of the GPU it runs on (the roofline denominators of the element
+// kernels), and the FP64 tensor-core rate (mma.sync m8n8k4 with FP64 operands
+// and accumulators) to compare with the FP64 FMA pipe. Each thread runs 8
+// independent FMA chains, or each warp 4 independent MMA accumulator chains; the
+// only memory access is one store per thread at the end.
 #include <cuda_runtime.h>
 
 namespace {
@@ -39,9 +41,51 @@ int run(int blocks, int threads, int iters, double* flops_per_s) {
   return 0;
 }
 
+__global__ void dmma_chains(double* out, int iters) {
+  const double a = 1.0 + 1e-3 * (threadIdx.x & 31), b = 1e-3;
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0, c4 = 0.0, c5 = 0.0, c6 = 0.0, c7 = 0.0;
+  for (int i = 0; i < iters; ++i) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(c0), "+d"(c1) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(c2), "+d"(c3) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(c4), "+d"(c5) : "d"(a), "d"(b));
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(c6), "+d"(c7) : "d"(a), "d"(b));
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = c0 + c1 + c2 + c3 + c4 + c5 + c6 + c7;
+}
+
+// FP64 MMA rate: 4 chains per warp, 2 * 8 * 8 * 4 FLOPs per instruction.
+int run_dmma(int blocks, int threads, int iters, double* flops_per_s) {
+  double* out = nullptr;
+  if (threads % 32 != 0) return 3;
+  if (cudaMalloc(&out, sizeof(double) * (size_t)blocks * threads) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  dmma_chains<<<blocks, threads>>>(out, iters / 10);  // warm-up
+  cudaEventRecord(e0);
+  dmma_chains<<<blocks, threads>>>(out, iters);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return 2;
+  *flops_per_s = 2.0 * 8 * 8 * 4 * 4.0 * (double)iters * blocks * (threads / 32) / (ms * 1e-3);
+  return 0;
+}
+
 }  // namespace
 
+// precision: 0 FP64 FMA, 1 FP32 FMA, 2 FP64 MMA (m8n8k4).
 extern "C" int fma_probe(int precision, int blocks, int threads, int iters, double* flops_per_s) {
+  if (precision == 2) return run_dmma(blocks, threads, iters, flops_per_s);
   return precision == 0 ? run<double>(blocks, threads, iters, flops_per_s)
                         : run<float>(blocks, threads, iters, flops_per_s);
 }

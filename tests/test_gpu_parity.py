@@ -230,7 +230,8 @@ def check_solve_against_oracle(g, r, O, wl, mu, rho_set, tol):
     hence the damping updates are decided by rounding; two FP64 implementations that
     sum in different orders can then stop one or two steps apart. In that case the
     oracle itself must find the GPU's point converged (its own |[S;T]| there within
-    1.5x the threshold) and the two points agree to the stopping tolerance."""
+    1.5x the threshold) and the two points agree to the stopping tolerance.
+    Returns the branch taken: "same" (equal counts, 1e-10) or "certified"."""
     assert g["status"] == 0 and r["status"] == 0, (g, r["status"])
     z = np.concatenate([g["w"], g["tau"]])
     zr = np.concatenate([r["w"], r["tau"]])
@@ -239,30 +240,35 @@ def check_solve_against_oracle(g, r, O, wl, mu, rho_set, tol):
         assert abs(g["trials"] - r["trials"]) <= 2, (g["trials"], r["trials"])
         assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr), np.linalg.norm(z - zr) / np.linalg.norm(zr)
         assert abs(g["J"] - r["J"]) <= 1e-12 * r["J"]
+        return "same"
     else:
         assert abs((g["init_iters"] + g["iters"]) - (r["init_iters"] + r["iters"])) <= 2, (g, r)
         rr = O.reduced(wl.Phi, wl.Psi, g["w"], g["tau"], mu, rho_set=rho_set)
         gn = np.linalg.norm(np.concatenate([rr["S"], rr["T"]]))
         assert gn <= 1.5 * tol * max(1.0, r["g0"]), (gn, r["g0"])
         assert np.linalg.norm(z - zr) <= 1e-6 * np.linalg.norm(zr)
+        return "certified"
 
 
 def _check_solve(*pair):
-    check_solve_against_oracle(*pair)
+    return check_solve_against_oracle(*pair)
 
 
 def test_burgers_config1_solve():
-    _check_solve(*_solve_pair(W.burgers_workload(), tol=1e-10))
+    # the 200-element Burgers configuration: the oracle's trajectory step for step
+    assert _check_solve(*_solve_pair(W.burgers_workload(), tol=1e-10)) == "same"
 
 
 def test_euler_small_solve_dense():
-    _check_solve(*_solve_pair(W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6), tol=1e-8))
+    assert _check_solve(*_solve_pair(W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6), tol=1e-8)) == "same"
 
 
 def test_euler_small_solve_sparse_rho():
+    # the one solve of this file that stops a step or two away from the oracle's count
+    # (its last steps sit at the rounding floor of J), so the oracle certifies the point
     wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=6)
     rs = W.eq_weight_sets(wl, 1, seed=7, lo=96, hi=150)[0]
-    _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs))
+    assert _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs)) in ("same", "certified")
 
 
 def test_given_start_and_repeat_solves():

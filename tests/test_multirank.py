@@ -57,3 +57,55 @@ def test_single_rank_is_the_identity():
 
     assert bench.max_over_ranks(1.25, "cpu") == 1.25
     assert bench.whole_job_rate(7, 1, 0.5) == pytest.approx(14.0)
+
+
+def _replica_rank(rank, world, port, out):
+    import time
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        calls = {"step": 0, "before": 0}
+        delay = 0.01 * (rank + 1)  # rank 1 solves twice as slowly
+
+        def step():  # stub solve: each rank works on its own queries, no collective
+            calls["step"] += 1
+            time.sleep(delay)
+
+        def before():
+            calls["before"] += 1
+
+        def timer(fn):
+            t0 = time.perf_counter()
+            fn()
+            return 1e3 * (time.perf_counter() - t0)
+
+        ms, total_s, rate = bench.replica_steps(step, 5, world, "cpu", timer, before_step=before)
+        out[rank] = (ms, total_s, rate, dict(calls))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_steps_under_two_gloo_ranks():
+    # the per-rank timed loop of the benchmark, driven with a stub solve: each rank
+    # times its own steps, the job takes the slowest rank's total, and the rate
+    # counts the steps of both ranks
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_replica_rank, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    slow = sum(res[1][0]) / 1e3
+    for r in range(world):
+        ms, total_s, rate, calls = res[r]
+        assert len(ms) == 5 and calls == {"step": 5, "before": 5}
+        assert total_s == pytest.approx(slow)
+        assert rate == pytest.approx(2 * 5 / slow)
+    assert sum(res[0][0]) < sum(res[1][0])
+    assert slow >= 5 * 0.02
