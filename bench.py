@@ -41,8 +41,8 @@ import numpy as np  # noqa: E402
 METRIC = "ROM solves/sec at rel. resid 1e-8 vs FP64 oracle; element R+J evals/sec"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused FP64
 # assembly kernel of this workload, from an ncu capture of the current kernel
-# (78.83 MB + 2.66 MB); set to None when the kernel changes until it is re-taken.
-FP64_ASSEMBLY_DRAM_BYTES = 81.49e6
+# (78.89 MB + 2.45 MB); set to None when the kernel changes until it is re-taken.
+FP64_ASSEMBLY_DRAM_BYTES = 81.34e6
 WORKLOAD = "euler2d_p2_20000el_ku20_kx4_rho1_fp64"
 
 
@@ -743,6 +743,10 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
     t0 = time.perf_counter()
     start_mlp = net.predict(mu_q)
     out["predict_ms"] = 1e3 * (time.perf_counter() - t0)
+    net.predict_bf16(mu_q[:128])  # first call: kernel attributes and buffers
+    t0 = time.perf_counter()
+    start_bf16 = net.predict_bf16(mu_q)
+    out["predict_bf16_ms"] = 1e3 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
     start_nn = ift.nearest_start(mu_t[ok], y_t, mu_q, scale=1.0 / W.MU_BOX_WIDTH)
     out["nearest_ms"] = 1e3 * (time.perf_counter() - t0)
@@ -765,7 +769,8 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
     z = torch.zeros((n_query, kx), dtype=torch.float64, device=dev)
     st = torch.zeros(n_query, dtype=torch.int32, device=dev)
     rows = {}
-    for name, ctx, s in (("projected", paper, None), ("nearest", given, start_nn), ("mlp", given, start_mlp)):
+    for name, ctx, s in (("projected", paper, None), ("nearest", given, start_nn), ("mlp", given, start_mlp),
+                         ("mlp_bf16", given, start_bf16)):
         if s is None:
             info = ref
             y0 = torch.zeros_like(y)
@@ -780,9 +785,12 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
         zf = np.concatenate([info["w"], info["tau"]], axis=1)
         both = ok_ref & (stat == 0)
         Jf = np.array([i["J"] for i in info["info"]])
+        gfin = np.array([math.hypot(i["normS"], i["normT"]) for i in info["info"]])
+        thr = np.array([1e-8 * max(1.0, i["g0"]) for i in info["info"]])
         row = {"ms_per_batch": statistics.median(ms), "solves_per_s": n_query / (statistics.median(ms) / 1e3),
                "converged": int((stat == 0).sum()), "mean_lm_iters": float(its.mean()),
                "max_iters": int(its.max()),
+               "median_final_gradient": float(np.median(gfin)), "median_threshold": float(np.median(thr)),
                "max_rel_dz_vs_projected_start": float(np.max(np.linalg.norm(zf[both] - z_ref[both], axis=1)
                                                               / np.linalg.norm(z_ref[both], axis=1))),
                "max_rel_dJ_vs_projected_start": float(np.max(np.abs(Jf[both] - J_ref[both]) / J_ref[both]))}
@@ -817,6 +825,27 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
         "mlp_batched_max_rel_dJ": float(np.max(np.abs(mlp_J[:n1][ok1] - J1[ok1]) / J1[ok1]))}
     out["speedup_mlp_batched_vs_fp64_one_query"] = rows["mlp"]["solves_per_s"] / (n1 / dt)
     one.close()
+    # The stopping test is relative to the gradient at the start of a phase, so a
+    # projected start (large starting gradient) stops at a larger absolute gradient
+    # than a warm start. Both forms' points are judged against the optimum of each
+    # sample query: an FP64 solve continued from the learned start's converged point
+    # (its starting gradient is below 1, so it stops at the absolute 1e-8).
+    tight = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, lm_init=ift.INIT_GIVEN,
+                                      stream=stream.cuda_stream)
+    tight.set_eq_weights(rho_set)
+    opt = [tight.solve_rom(mu_q[q], mlp_z[q, :ku], mlp_z[q, ku:]) for q in range(n1)]
+    tight.close()
+    zs = np.array([np.concatenate([r["w"], r["tau"]]) for r in opt])
+    Js = np.array([r["J"] for r in opt])
+    good = np.array([r["status"] == 0 for r in opt]) & ok1
+    rel = lambda a, b: np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    out["vs_optimum"] = {
+        "sample": int(good.sum()),
+        "fp64_one_query_max_rel_dz": float(np.max(rel(z1[good], zs[good]))),
+        "fp64_one_query_max_rel_dJ": float(np.max(np.abs(J1[good] - Js[good]) / Js[good])),
+        "mlp_batched_max_rel_dz": float(np.max(rel(mlp_z[:n1][good], zs[good]))),
+        "mlp_batched_max_rel_dJ": float(np.max(np.abs(mlp_J[:n1][good] - Js[good]) / Js[good])),
+        "max_extra_iters": int(max(r["iters"] for r in opt))}
     return out
 
 

@@ -21,9 +21,11 @@
 //     with the initialization and stopping test of Remark rem:solver.
 //
 // The paper leaves the DG weak form, the numerical flux, boundary states, nodes,
-// quadrature, the damping rule and the line-search constants open. The readings
-// used here are listed in the design notes of the repository and repeated at the
-// point of use below.
+// quadrature, the damping rule and the line-search constants open. Each reading
+// used here is stated at its point of use below: the weak form above
+// element_residual, the Roe flux with Harten's entropy fix above euler_roe and
+// burgers_roe, the boundary states in element_residual's face loop, nodes and
+// quadrature with the reference element, and the LM constants above lm_phase.
 //
 // Parity status: every function below is pinned by a CPU test (closed forms,
 // conservation, free-stream preservation, equivalence with a physical-space DG
@@ -727,7 +729,9 @@ void phys_point_q2(const Oracle& O, const T* xe, const double* xi, T* x) {
 inline bool bad(double a) { return !std::isfinite(a); }
 
 // Element residual R_e(U_e, U_e', x_e; mu) of the transformed law (Eq. p2r-flux)
-// in the DG weak form (reading of the design notes):
+// in the DG weak form (the paper says only "nodal DG"; this reading is a steady
+// residual without a mass matrix, the flux tested against the gradients of the
+// basis functions and the Roe flux on the faces):
 //   R_e[i] = - int_{Omega_0e} F(U) . grad_0 v_i dX
 //            + int_{dOmega_0e} v_i H(U+, U-; g G^{-T} N) dS_0
 //            - int_{Omega_0e} v_i S dX.

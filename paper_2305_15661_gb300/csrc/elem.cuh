@@ -301,7 +301,7 @@ struct WarpLayout {
       // staging of the reduced-Jacobian passes: volume G (M ku) + F (DIM M ku), faces
       // dU (2 M ku) + dH (M ku), mesh directions E (NB M 4) + dcof (4 kx) + K (NF NT M 2)
       size_t w1 = (size_t)(DIM + 1) * M * ku, w2 = (size_t)3 * M * ku,
-             w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2;
+             w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2 + (size_t)NF * 2 * kx;
       size_t w = w1 > w2 ? w1 : w2;
       if (w3 > w) w = w3;
       // curved mesh columns: dF per (volume point, column) and dH per (face point, column)
@@ -1368,7 +1368,10 @@ struct ElemCore {
     T* E = W;                  // [NB][M][DIM][DIM]
     T* dcof = W + NB * M * 4;  // [kx][4]
     T* K = dcof + 4 * kx;      // [NF][NT][M][2]: sum_f fw[f] Lt[f][j] Hn[kf, f][a][d]
+    T* dnt = K + NF * NT * M * 2;  // [NF][kx][2]: change of face kf's scaled normal along column c
     if (DIM == 2) {
+      // the mesh-direction differences, once per column (FP64 differences of the
+      // vertex rows of Psi, then one conversion each)
       for (int c = lane; c < kx; c += 32) {
         const double* d = &Psie[c];  // column c, stride kx
         const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
@@ -1377,6 +1380,12 @@ struct ElemCore {
         dcof[c * 4 + 1] = -dj10;
         dcof[c * 4 + 2] = -dj01;
         dcof[c * 4 + 3] = dj00;
+#pragma unroll
+        for (int kf = 0; kf < NF; ++kf) {
+          const int k1 = (kf + 1) % 3;
+          dnt[(kf * kx + c) * 2 + 0] = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
+          dnt[(kf * kx + c) * 2 + 1] = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+        }
       }
       for (int e = lane; e < NB * M * 4; e += 32) {
         const int ia = e >> 2, rd = e & 3, r = rd >> 1, d = rd & 1;
@@ -1408,12 +1417,9 @@ struct ElemCore {
         for (int kf = 0; kf < NF; ++kf) {
           const int j = face_pos(kf, i);
           if (j < 0) continue;
-          const int k1 = (kf + 1) % 3;
-          const double* d = &Psie[c];
-          const T dnx = (T)(d[(2 * k1 + 1) * kx] - d[(2 * kf + 1) * kx]);
-          const T dny = (T)(-(d[(2 * k1) * kx] - d[(2 * kf) * kx]));
+          const T* dn = &dnt[(kf * kx + c) * 2];
           const T* kk = &K[((kf * NT + j) * M + a) * 2];
-          s += kk[0] * dnx + kk[1] * dny;
+          s += kk[0] * dn[0] + kk[1] * dn[1];
         }
         A[row * k + ku + c] = s;
       }

@@ -1,7 +1,10 @@
 """Pins of the oracle's physical flux and Roe numerical flux.
 
-The Euler flux is Eq. euler (Sec. 4.2); the Roe flux is the reading of the
-design notes (the paper names no numerical flux). Pins: closed-form values,
+The Euler flux is Eq. euler (Sec. 4.2). The paper names no numerical flux; the
+reading here is the Roe flux with Roe averages weighted by sqrt(rho), waves
+v_n - c, v_n, v_n + c, and Harten's entropy fix |lam| -> (lam^2 + delta^2) /
+(2 delta) below delta = 0.1 c~ (Burgers: upwinding on a = (u+ + u-)/2 with
+delta = 0.05 (|u+| + |u-|) |n|). Pins: closed-form values,
 consistency H(U, U, n) = f(U).n, the Roe property through exact upwinding
 (supersonic normal flow, isolated contact and shear waves), conservation,
 rotational invariance and homogeneity in the scaled normal.

@@ -1,8 +1,9 @@
 """Pins of the oracle's reference element: quadrature, nodes and Lagrange basis.
 
-The paper fixes only "nodal DG" (Sec. 2.3); nodes, basis and quadrature are the
-readings of the design notes (equispaced Lagrange nodes, Gauss-Legendre with
-p+2 points, collapsed Gauss rule on triangles). These tests pin them against
+The paper fixes only "nodal DG" (Sec. 2.3). The readings here: equispaced
+Lagrange nodes (triangles: vertices, then edge-interior nodes edge by edge, then
+interior nodes), Gauss-Legendre with p+2 points on intervals and faces, and the
+collapsed (Duffy) Gauss rule with (p+2)^2 points on triangles. These tests pin them against
 numpy's Gauss-Legendre routine and against exact integrals and interpolation
 identities.
 """
