@@ -376,6 +376,17 @@ ift_status ift_mlp_train(ift_mlp* net, int64_t count, const double* x, const dou
    variables (standardisation applied and undone). */
 ift_status ift_mlp_predict(ift_mlp* net, int64_t count, const double* x, double* out);
 
+/* The same evaluation as ift_mlp_predict with every product of width inputs (the
+   hidden-to-hidden layers and the output layer) on the tensor cores: BF16
+   operands (the FP32 parameters and the GELU outputs rounded to BF16), FP32
+   accumulation and FP32 bias and GELU; the first layer (n_in inputs) stays FP32.
+   One CTA evaluates 128 queries through every layer. Outputs agree with
+   ift_mlp_predict to the BF16 rounding of the operands (about 1e-2 relative).
+   IFT_ERR_NOTIMPL unless depth >= 1, n_in <= 32, width a multiple of 16 in
+   [16, 256] and n_out <= 256; IFT_ERR_TIMEOUT if a bounded device wait for the
+   tensor cores ran out. */
+ift_status ift_mlp_predict_bf16(ift_mlp* net, int64_t count, const double* x, double* out);
+
 /* The start the learned one is compared with: for each query, the outputs of
    the nearest training point, y_out[q] = y_train[argmin_t |scale (x_q - x_t)|]
    (scale: n_in per-column factors, NULL = 1; the lowest index wins ties).

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/ift.h"
+#include "mlp_internal.h"
 
 namespace {
 
@@ -137,22 +138,6 @@ uint64_t mix64(uint64_t z) {
 
 }  // namespace
 
-struct ift_mlp {
-  int n_in = 0, width = 0, depth = 0, n_out = 0;
-  cudaStream_t stream = nullptr;
-  std::vector<int> lin, lout;      // per layer
-  std::vector<size_t> woff, boff;  // parameter offsets
-  size_t np = 0;
-  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
-  int cap = 0;                     // batch capacity of the work buffers
-  std::vector<float*> A, Z, dA;    // per layer: input activations, pre-activations, gradients
-  float *T = nullptr, *Y = nullptr, *dY = nullptr;
-  double* loss_parts = nullptr;
-  int* idx = nullptr;
-  long adam_t = 0;
-  std::vector<double> xm, xs, tm, ts;  // normalisation of inputs and targets (identity until trained)
-  int layers() const { return (int)lin.size(); }
-};
 
 namespace {
 
@@ -310,6 +295,9 @@ ift_status ift_mlp_destroy(ift_mlp* n) {
   mfree(n->Y);
   mfree(n->dY);
   mfree(n->idx);
+  mfree(n->tc_x);
+  mfree(n->tc_y);
+  mfree(n->tc_status);
   delete n;
   return IFT_OK;
 }

@@ -72,7 +72,7 @@ EXPORTS = ["ift_config_default", "ift_create", "ift_destroy", "ift_last_error", 
            "ift_set_eq_weights_batched", "ift_reduced_residual_jacobian_batched", "ift_solve_rom_batched",
            "ift_solve_rom_batched_dev", "ift_autotune", "ift_set_launch_shapes", "ift_hdm_residual_norms", "ift_element_gradients", "ift_mlp_create", "ift_mlp_destroy",
            "ift_mlp_num_params", "ift_mlp_get_params", "ift_mlp_set_params", "ift_mlp_get_scaling", "ift_mlp_set_scaling", "ift_mlp_loss_grad", "ift_mlp_train",
-           "ift_mlp_predict", "ift_nearest_start", "ift_align_residual", "ift_align_jvp", "ift_align_vjp",
+           "ift_mlp_predict", "ift_mlp_predict_bf16", "ift_nearest_start", "ift_align_residual", "ift_align_jvp", "ift_align_vjp",
            "ift_align", "ift_align_dev"]
 
 
@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ift_mlp_loss_grad": (i32, [vp, i64, pd, pd, pd, pd]),
         "ift_mlp_train": (i32, [vp, i64, pd, pd, i32, i32, dbl, ctypes.c_uint64, pd]),
         "ift_mlp_predict": (i32, [vp, i64, pd, pd]),
+        "ift_mlp_predict_bf16": (i32, [vp, i64, pd, pd]),
         "ift_nearest_start": (i32, [i64, i32, pd, i32, pd, i64, pd, pd, pd]),
         "ift_align_residual": (i32, [vp, pd, pd, pd, pd]),
         "ift_align_jvp": (i32, [vp, pd, pd, pd, pd, pd, pd]),
@@ -519,6 +520,14 @@ class MLP:
         x = _f64(x)
         out = np.zeros((x.shape[0], self.n_out))
         self._check(load().ift_mlp_predict(self._h, x.shape[0], _pd(x), _pd(out)), "ift_mlp_predict")
+        return out
+
+    def predict_bf16(self, x):
+        """The same network evaluated on the tensor cores with BF16 operands and FP32
+        accumulation (ift_mlp_predict_bf16)."""
+        x = _f64(x)
+        out = np.zeros((x.shape[0], self.n_out))
+        self._check(load().ift_mlp_predict_bf16(self._h, x.shape[0], _pd(x), _pd(out)), "ift_mlp_predict_bf16")
         return out
 
 

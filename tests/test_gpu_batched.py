@@ -39,7 +39,7 @@ def test_batched_assembly_matches_oracle_per_query():
         assert abs(g["J"][q] - r["J"]) <= 1e-10 * r["J"]
 
 
-def test_batched_solve_matches_oracle_and_single_solves():
+def test_batched_solve_matches_oracle_and_single_solves(record_property):
     wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=6, n_mu=5, mu_box=True)
     sets = W.eq_weight_sets(wl, 5, seed=7, lo=96, hi=200)
     ctx = ift.Context.from_workload(wl, tol=1e-8)
@@ -47,10 +47,12 @@ def test_batched_solve_matches_oracle_and_single_solves():
     res = ctx.solve_rom_batched(wl.mus)
     O = orc.Oracle.from_workload(wl)
     single = ift.Context.from_workload(wl, tol=1e-8)
+    branches = []
     for q in range(5):
         inf = dict(res["info"][q], w=res["w"][q], tau=res["tau"][q])
         r = O.solve(wl.Phi, wl.Psi, wl.mus[q], _guess(wl, wl.mus[q]), rho_set=sets[q], tol=1e-8)
-        check_solve_against_oracle(inf, r, O, wl, wl.mus[q], sets[q], 1e-8)
+        branches.append(check_solve_against_oracle(inf, r, O, wl, wl.mus[q], sets[q], 1e-8))
+        record_property("solve_branches", ",".join(branches))
         # the batched solve of a query follows the single-query solve of the same query
         single.set_eq_weights(sets[q])
         s1 = single.solve_rom(wl.mus[q])
@@ -62,7 +64,7 @@ def test_batched_solve_matches_oracle_and_single_solves():
             assert abs(s1["iters"] + s1["init_iters"] - inf["iters"] - inf["init_iters"]) <= 2 and d <= 1e-6
 
 
-def test_batched_config3_full_size():
+def test_batched_config3_full_size(record_property):
     # 20,000 elements, k_u = 20, k_x = 4, 256 queries with 100..2000 sampled elements each
     wl = W.euler_workload(n=100, p=2, k_u=20, k_x=4, seed=2, n_mu=256, mu_box=True)
     sets = W.eq_weight_sets(wl, 256, seed=3)
@@ -73,10 +75,12 @@ def test_batched_config3_full_size():
     # hyperreduced queries with random (not LP-trained) weights can stall; nearly all converge
     assert (statuses == 0).sum() >= 250, statuses
     O = orc.Oracle.from_workload(wl)
+    branches = []
     for q in [int(i) for i in np.nonzero(statuses == 0)[0][:2]]:
         r = O.solve(wl.Phi, wl.Psi, wl.mus[q], _guess(wl, wl.mus[q]), rho_set=sets[q], tol=1e-8)
         inf = dict(res["info"][q], w=res["w"][q], tau=res["tau"][q])
-        check_solve_against_oracle(inf, r, O, wl, wl.mus[q], sets[q], 1e-8)
+        branches.append(check_solve_against_oracle(inf, r, O, wl, wl.mus[q], sets[q], 1e-8))
+    record_property("solve_branches", ",".join(branches))
 
 
 def test_batched_errors():

@@ -56,6 +56,40 @@ def test_forward_matches_oracle():
     assert np.max(np.abs(y - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("rows", [37, 300, 4096])
+def test_bf16_tensor_core_forward_matches_oracle(rows):
+    # The tensor-core path rounds the operands of every width-input product to BF16
+    # (unit roundoff 2^-9) and accumulates in FP32; through the three products the
+    # outputs carry a relative error of order 1e-2, the stated BF16 tolerance.
+    net = ift.MLP(*ARCH, seed=0)
+    p = _params(7, ARCH)
+    net.set_params(p)
+    x, _ = _data(9, rows, 2, 48)  # 37 and 300 rows leave a partial 128-row tile
+    y16 = net.predict_bf16(x)
+    ref, _ = om.forward(p, x, *ARCH)
+    assert np.linalg.norm(y16 - ref) <= 2e-2 * np.linalg.norm(ref)
+    assert np.max(np.abs(y16 - ref)) <= 5e-2 * np.max(np.abs(ref))
+    # it is the BF16 path: the FP32 network is far closer to the FP64 reference
+    y32 = net.predict(x)
+    assert np.max(np.abs(y32 - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(y16 - y32)) > 1e-4 * np.max(np.abs(ref))
+    # the same inputs give the same outputs on a second call
+    np.testing.assert_array_equal(net.predict_bf16(x), y16)
+
+
+def test_bf16_forward_after_training_and_shape_limits():
+    mus = W.mu_box_samples(80, 1, 256)
+    t = np.stack([mus[:, 0] * (2 + k) + np.cos(30 * mus[:, 1]) for k in range(16)], axis=1)
+    net = ift.MLP(2, 64, 2, 16, seed=81)
+    net.train(mus, t, epochs=100, batch=64, lr=3e-3, seed=82)
+    q = W.mu_box_samples(83, 1, 200)
+    y32, y16 = net.predict(q), net.predict_bf16(q)  # standardisation applied and undone alike
+    assert np.linalg.norm(y16 - y32) <= 2e-2 * np.linalg.norm(y32)
+    with pytest.raises(ift.IFTError) as ei:
+        ift.MLP(2, 20, 2, 4, seed=1).predict_bf16(q)  # width not a multiple of 16
+    assert ei.value.status == -7
+
+
 def test_gradient_matches_oracle():
     net = ift.MLP(*ARCH, seed=0)
     p = _params(9, ARCH)

@@ -263,12 +263,14 @@ def test_euler_small_solve_dense():
     assert _check_solve(*_solve_pair(W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6), tol=1e-8)) == "same"
 
 
-def test_euler_small_solve_sparse_rho():
+def test_euler_small_solve_sparse_rho(record_property):
     # the one solve of this file that stops a step or two away from the oracle's count
     # (its last steps sit at the rounding floor of J), so the oracle certifies the point
     wl = W.euler_workload(n=12, p=2, k_u=8, k_x=2, seed=6)
     rs = W.eq_weight_sets(wl, 1, seed=7, lo=96, hi=150)[0]
-    assert _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs)) in ("same", "certified")
+    branch = _check_solve(*_solve_pair(wl, tol=1e-8, rho_set=rs))
+    record_property("solve_branches", branch)
+    assert branch in ("same", "certified")
 
 
 def test_given_start_and_repeat_solves():
