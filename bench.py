@@ -825,27 +825,31 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
         "mlp_batched_max_rel_dJ": float(np.max(np.abs(mlp_J[:n1][ok1] - J1[ok1]) / J1[ok1]))}
     out["speedup_mlp_batched_vs_fp64_one_query"] = rows["mlp"]["solves_per_s"] / (n1 / dt)
     one.close()
-    # The stopping test is relative to the gradient at the start of a phase, so a
-    # projected start (large starting gradient) stops at a larger absolute gradient
-    # than a warm start. Both forms' points are judged against the optimum of each
-    # sample query: an FP64 solve continued from the learned start's converged point
-    # (its starting gradient is below 1, so it stops at the absolute 1e-8).
-    tight = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, lm_init=ift.INIT_GIVEN,
-                                      stream=stream.cuda_stream)
-    tight.set_eq_weights(rho_set)
-    opt = [tight.solve_rom(mu_q[q], mlp_z[q, :ku], mlp_z[q, ku:]) for q in range(n1)]
-    tight.close()
-    zs = np.array([np.concatenate([r["w"], r["tau"]]) for r in opt])
-    Js = np.array([r["J"] for r in opt])
-    good = np.array([r["status"] == 0 for r in opt]) & ok1
-    rel = lambda a, b: np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
-    out["vs_optimum"] = {
-        "sample": int(good.sum()),
-        "fp64_one_query_max_rel_dz": float(np.max(rel(z1[good], zs[good]))),
-        "fp64_one_query_max_rel_dJ": float(np.max(np.abs(J1[good] - Js[good]) / Js[good])),
-        "mlp_batched_max_rel_dz": float(np.max(rel(mlp_z[:n1][good], zs[good]))),
-        "mlp_batched_max_rel_dJ": float(np.max(np.abs(mlp_J[:n1][good] - Js[good]) / Js[good])),
-        "max_extra_iters": int(max(r["iters"] for r in opt))}
+    # Both forms meet the same stopping test, |[S; T]| <= 1e-8 max(1, |[S0; T0]|), and
+    # here max(1, .) = 1 for every query: an absolute 1e-8. Their points still differ
+    # where H is ill-conditioned: near an optimum z - z* = H^{-1} g, so two points
+    # that pass the test can lie 2 (|g1| + |g2|) / lambda_min(H) apart. Checked on the
+    # sample with H at the learned start's point (FP64 evaluation).
+    one = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
+    one.set_eq_weights(rho_set)
+    ratios, lam_min, conds = [], [], []
+    for q in range(n1):
+        if not ok1[q]:
+            continue
+        ev = one.reduced_residual_jacobian(mu_q[q], mlp_z[q, :ku], mlp_z[q, ku:])
+        lam = np.linalg.eigvalsh(ev["H"])
+        g_mlp = float(np.linalg.norm(np.concatenate([ev["S"], ev["T"]])))
+        g_one = math.hypot(singles[q]["normS"], singles[q]["normT"])
+        dz = float(np.linalg.norm(mlp_z[q] - z1[q]))
+        ratios.append(dz / (2.0 * (g_mlp + g_one) / lam[0]))
+        lam_min.append(float(lam[0]))
+        conds.append(float(lam[-1] / lam[0]))
+    one.close()
+    out["same_test_consistency"] = {
+        "sample": len(ratios), "threshold": 1e-8,
+        "max_dz_over_bound": float(max(ratios)), "median_lambda_min": float(np.median(lam_min)),
+        "median_condition_number": float(np.median(conds)),
+        "reading": "dz_over_bound <= 1: the two forms' points are as close as the common stopping test allows"}
     return out
 
 

@@ -929,7 +929,10 @@ struct ElemCore {
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       const signed char bt = bcs[k];
-#pragma unroll
+      // the face points stay a rolled loop: unrolled, the three faces' copies of
+      // this body made the FP32 kernels stall on instruction fetch (0.290 ->
+      // 0.264 ms at p = 2, 4.40 -> 3.78 ms at p = 3 rolled)
+#pragma unroll 1
       for (int f = 0; f < NFQ; ++f) {
         T dui[M], duo[M];
 #pragma unroll

@@ -298,6 +298,7 @@ ift_status ift_mlp_destroy(ift_mlp* n) {
   mfree(n->tc_x);
   mfree(n->tc_y);
   mfree(n->tc_status);
+  mfree(n->tc_wpk);
   delete n;
   return IFT_OK;
 }

@@ -23,5 +23,7 @@ struct ift_mlp {
   float *tc_x = nullptr, *tc_y = nullptr;
   int* tc_status = nullptr;
   long long tc_cap = 0;
+  unsigned char* tc_wpk = nullptr;  // BF16 operand images of the weights of layers 1..
+  size_t tc_wpk_bytes = 0;
   int layers() const { return (int)lin.size(); }
 };

@@ -12,13 +12,16 @@
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: 8-row x 16-byte core matrices, consecutive along K 128 bytes apart,
 // consecutive 8-row groups SBO = (K / 8) * 128 bytes apart. A (activations) is
-// 128 rows x K, B (weights, one row per output) N rows x K. All weights of the
-// network are converted to BF16 into shared memory once per CTA.
+// 128 rows x K, B (weights, one row per output) N rows x K. A small kernel first
+// writes each layer's weights in BF16 in exactly that image to global memory;
+// each CTA brings them in with one bulk copy per layer (cp.async.bulk completing
+// on an mbarrier), the next layer's copy running under the current epilogue.
 //
-// Waits: the only wait is on the mbarrier that tcgen05.commit arrives on when a
-// layer's products are done; it is bounded (kSpinLimit polls), after which the
-// CTA records a timeout in the status word, waits once more (bounded) for its
-// products, frees its tensor memory and returns.
+// Waits: on the mbarrier of the weight copies and on the one tcgen05.commit
+// arrives on when a layer's products are done; each is bounded (kSpinLimit polls),
+// after which the CTA records a timeout in the status word, waits once more
+// (bounded) for its products and copies in flight, frees its tensor memory and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -96,6 +99,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int li
   return false;
 }
 
+// Arms the mbarrier for `bytes` of asynchronous copies (one arrival) and starts a
+// bulk copy of `bytes` from global memory into shared memory that completes on it.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 // 32 lanes x 16 columns of FP32 from tensor memory: thread t of the warp gets
 // columns [col, col + 16) of lane (lane base + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
@@ -130,6 +143,10 @@ struct NetArgs {
   float* y;        // count x n_out, standardised outputs
   const float* p;  // FP32 parameters, W_l (in x out, row-major) then b_l per layer
   long long woff[kMaxLayers], boff[kMaxLayers];
+  // layers 1.. in BF16, each already in its shared-memory operand image (N rows x K,
+  // K-major, no swizzle), at byte offset wpk_off[l] of wpk
+  const unsigned char* wpk;
+  long long wpk_off[kMaxLayers];
   int count, n_in, width, n_out, layers;
   int n_out_pad;   // n_out rounded up to 16 (the last product's N)
   int tmem_cols;   // tensor-memory columns allocated per CTA (power of two >= 32, >= every N)
@@ -140,6 +157,15 @@ __device__ __forceinline__ void put_bf16(__nv_bfloat16* base, int row, int k, in
   base[kmajor_offset(row, k, K) >> 1] = __float2bfloat16_rn(v);
 }
 
+// The operand image of W_l (in = K rows of the parameter matrix, out = Nreal columns):
+// row n of the image is output n, K-major; rows Nreal..N-1 are zero.
+__global__ void pack_weights_kernel(const float* Wl, int K, int N, int Nreal, __nv_bfloat16* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * K; i += gridDim.x * blockDim.x) {
+    const int k = i / N, n = i - k * N;
+    put_bf16(out, n, k, K, n < Nreal ? Wl[(size_t)k * Nreal + n] : 0.0f);
+  }
+}
+
 __global__ void __launch_bounds__(kRows, 1) mlp_bf16_kernel(NetArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int W = a.width;
@@ -147,10 +173,12 @@ __global__ void __launch_bounds__(kRows, 1) mlp_bf16_kernel(NetArgs a) {
   const int nmax = W > a.n_out_pad ? W : a.n_out_pad;
   __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sm);
   __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(sm + act_bytes);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + act_bytes + (size_t)nmax * W * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + act_bytes + (size_t)nmax * W * 2);  // products done
+  uint64_t* tbar = mbar + 1;                                                               // weights arrived
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long row0 = (long long)blockIdx.x * kRows;
+  auto layer_bytes = [&](int l) { return (uint32_t)((l == a.layers - 1 ? a.n_out_pad : W) * W * 2); };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -158,7 +186,12 @@ __global__ void __launch_bounds__(kRows, 1) mlp_bf16_kernel(NetArgs a) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  if (tid == 0) mbar_init(smem_u32(mbar));
+  if (tid == 0) {
+    mbar_init(smem_u32(mbar));
+    mbar_init(smem_u32(tbar));
+    // the first product's weights, while layer 0 runs on the FMA pipe
+    bulk_copy_g2s(smem_u32(wt), a.wpk + a.wpk_off[1], layer_bytes(1), smem_u32(tbar));
+  }
 
   // layer 0 (n_in -> W, GELU) in FP32, one thread per query
   {
@@ -173,39 +206,43 @@ __global__ void __launch_bounds__(kRows, 1) mlp_bf16_kernel(NetArgs a) {
       put_bf16(act, tid, o, W, gelu(z));
     }
   }
+  fence_async_smem();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = *tslot;
   const uint32_t sbo = (uint32_t)(W / 8) * 128;
-  uint32_t parity = 0;
-  bool timed_out = false;
+  uint32_t mparity = 0, tparity = 0;
+  bool timed_out = false, copy_pending = true;
   for (int l = 1; l < a.layers; ++l) {
     const bool last = l == a.layers - 1;
     const int N = last ? a.n_out_pad : W, Nreal = last ? a.n_out : W;
-    // W_l as N rows (outputs) x K = W (inputs), K-major; rows past the real outputs are zero
-    const float* Wl = a.p + a.woff[l];
-    for (int i = tid; i < N * W; i += kRows) {
-      const int k = i / N, n = i - k * N;
-      put_bf16(wt, n, k, W, n < Nreal ? Wl[(size_t)k * Nreal + n] : 0.0f);
+    // this layer's weights (bulk copy started one layer earlier)
+    const bool wok = mbar_wait(smem_u32(tbar), tparity, kSpinLimit);
+    if (__syncthreads_or(!wok)) {
+      timed_out = true;
+      break;
     }
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
+    copy_pending = false;
+    tparity ^= 1u;
     if (tid == 0) {
+      fence_after_sync();
       const uint32_t ia = smem_u32(act), ib = smem_u32(wt), id = idesc_bf16(kRows, N);
       for (int kk = 0; kk < W / 16; ++kk)
         mma_bf16(tbase, smem_desc(ia + kk * 256, 128, sbo), smem_desc(ib + kk * 256, 128, sbo), id, kk > 0);
       mma_commit(smem_u32(mbar));
     }
-    const bool ok = mbar_wait(smem_u32(mbar), parity, kSpinLimit);
+    const bool ok = mbar_wait(smem_u32(mbar), mparity, kSpinLimit);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
     }
-    parity ^= 1u;
+    mparity ^= 1u;
     fence_after_sync();
+    // the products have read this layer's weights and activations: start the next
+    // layer's weights now, under the epilogue
+    if (!last && tid == 0) bulk_copy_g2s(smem_u32(wt), a.wpk + a.wpk_off[l + 1], layer_bytes(l + 1), smem_u32(tbar));
+    copy_pending = !last;
     // epilogue: this warp's 32 accumulator rows, 16 columns at a time
     const int r = warp * 32 + lane;
     const long long grow = row0 + r;
@@ -222,11 +259,16 @@ __global__ void __launch_bounds__(kRows, 1) mlp_bf16_kernel(NetArgs a) {
           if (c0 + i < Nreal) a.y[grow * Nreal + c0 + i] = v[i] + bl[c0 + i];
       }
     }
+    fence_async_smem();
     fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
   }
   if (timed_out) {
     if (tid == 0) atomicExch(a.status, 1);
-    mbar_wait(smem_u32(mbar), parity, kSpinLimit);  // the products still in flight, bounded
+    // products and a weight copy that may still be in flight, each wait bounded
+    mbar_wait(smem_u32(mbar), mparity, kSpinLimit);
+    if (copy_pending) mbar_wait(smem_u32(tbar), tparity, kSpinLimit);
   }
   fence_before_sync();
   __syncthreads();
@@ -247,7 +289,7 @@ extern "C" ift_status ift_mlp_predict_bf16(ift_mlp* n, int64_t count, const doub
   const int npad = (no + 15) / 16 * 16, nmax = std::max(W, npad);
   int cols = 32;
   while (cols < nmax) cols <<= 1;
-  const size_t smem = (size_t)kRows * W * 2 + (size_t)nmax * W * 2 + 16;
+  const size_t smem = (size_t)kRows * W * 2 + (size_t)nmax * W * 2 + 32;  // + two mbarriers, TMEM slot
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -264,6 +306,21 @@ extern "C" ift_status ift_mlp_predict_bf16(ift_mlp* n, int64_t count, const doub
     n->tc_cap = count;
   }
   if (!n->tc_status && cudaMalloc(&n->tc_status, sizeof(int)) != cudaSuccess) return IFT_ERR_OOM;
+  // the BF16 operand images of layers 1.., rebuilt on every call (training may
+  // have changed the parameters)
+  long long wpk_off[kMaxLayers] = {0};
+  size_t wpk_bytes = 0;
+  for (int l = 1; l < L; ++l) {
+    wpk_off[l] = (long long)wpk_bytes;
+    wpk_bytes += (size_t)(l == L - 1 ? npad : W) * W * 2;
+  }
+  if (wpk_bytes > n->tc_wpk_bytes) {
+    if (n->tc_wpk) cudaFree(n->tc_wpk);
+    n->tc_wpk = nullptr;
+    n->tc_wpk_bytes = 0;
+    if (cudaMalloc(&n->tc_wpk, wpk_bytes) != cudaSuccess) return IFT_ERR_OOM;
+    n->tc_wpk_bytes = wpk_bytes;
+  }
   std::vector<float> hx((size_t)count * ni), hy((size_t)count * no);
   for (int64_t i = 0; i < count; ++i)
     for (int j = 0; j < ni; ++j) hx[(size_t)i * ni + j] = (float)((x[i * ni + j] - n->xm[j]) / n->xs[j]);
@@ -274,7 +331,9 @@ extern "C" ift_status ift_mlp_predict_bf16(ift_mlp* n, int64_t count, const doub
   for (int l = 0; l < kMaxLayers; ++l) {
     a.woff[l] = l < L ? (long long)n->woff[l] : 0;
     a.boff[l] = l < L ? (long long)n->boff[l] : 0;
+    a.wpk_off[l] = wpk_off[l];
   }
+  a.wpk = n->tc_wpk;
   a.count = (int)count;
   a.n_in = ni;
   a.width = W;
@@ -289,6 +348,11 @@ extern "C" ift_status ift_mlp_predict_bf16(ift_mlp* n, int64_t count, const doub
   if (cudaMemcpyAsync(n->tc_x, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(n->tc_status, 0, sizeof(int), s) != cudaSuccess)
     return IFT_ERR_CUDA;
+  for (int l = 1; l < L; ++l) {
+    const int N = l == L - 1 ? npad : W, Nreal = l == L - 1 ? no : W;
+    pack_weights_kernel<<<(N * W + 255) / 256, 256, 0, s>>>(n->p + n->woff[l], W, N, Nreal,
+                                                           reinterpret_cast<__nv_bfloat16*>(n->tc_wpk + wpk_off[l]));
+  }
   const unsigned grid = (unsigned)((count + kRows - 1) / kRows);
   mlp_bf16_kernel<<<grid, kRows, smem, s>>>(a);
   int st = 0;

@@ -183,7 +183,7 @@ def _train_and_solve(n, ku, kx, n_train, n_query, width, epochs, rho_set):
     mu_t = mu_t[ok]
     net = ift.MLP(2, width, 3, ku + kx, seed=43)
     net.train(mu_t, y_t, epochs=epochs, batch=32, lr=2e-3, seed=44)
-    starts = {"mlp": net.predict(mu_q),
+    starts = {"mlp": net.predict(mu_q), "mlp_bf16": net.predict_bf16(mu_q),
               "nearest": ift.nearest_start(mu_t, y_t, mu_q, scale=1.0 / W.MU_BOX_WIDTH)}
     ctx = ift.Context.from_workload(wl, tol=1e-8, lm_init=ift.INIT_GIVEN)
     ctx.set_eq_weights_batched([rho_set] * n_query)
@@ -206,17 +206,21 @@ def test_warm_start_beats_nearest_training_point():
     wl_sets = W.euler_workload(n=16, p=2, k_u=10, k_x=2, seed=40)
     rho_set = W.eq_weight_sets(wl_sets, 1, seed=45, lo=120, hi=121)[0]
     out, exact = _train_and_solve(16, 10, 2, 192, 64, 64, 400, rho_set)
-    m, nn = out["mlp"], out["nearest"]
-    # both starts converge to the same solutions as the projected-guess start
-    assert (m["status"] == 0).mean() >= 0.95 and (nn["status"] == 0).mean() >= 0.95
-    ok = (m["status"] == 0) & (nn["status"] == 0) & np.array([i["status"] == 0 for i in exact["info"]])
+    m, m16, nn = out["mlp"], out["mlp_bf16"], out["nearest"]
+    # every start converges to the same solutions as the projected-guess start
+    for r in (m, m16, nn):
+        assert (r["status"] == 0).mean() >= 0.95
+    ok = ((m["status"] == 0) & (m16["status"] == 0) & (nn["status"] == 0)
+          & np.array([i["status"] == 0 for i in exact["info"]]))
     z_ref = np.concatenate([exact["w"], exact["tau"]], axis=1)
-    for r in (m, nn):
+    for r in (m, m16, nn):
         d = np.linalg.norm(r["final"][ok] - z_ref[ok], axis=1) / np.linalg.norm(z_ref[ok], axis=1)
         assert np.max(d) < 1e-5
-    # the learned start is closer to the solution and needs fewer LM iterations
-    assert np.median(m["start_err"]) < 0.5 * np.median(nn["start_err"])
-    assert m["iters"][ok].mean() < nn["iters"][ok].mean()
+    # the learned start (FP32 or BF16 network) is closer to the solution and needs
+    # fewer LM iterations than the nearest training point
+    for r in (m, m16):
+        assert np.median(r["start_err"]) < 0.5 * np.median(nn["start_err"])
+        assert r["iters"][ok].mean() < nn["iters"][ok].mean()
 
 
 def test_trained_network_checkpoint_roundtrip(tmp_path):
