@@ -827,29 +827,29 @@ def warmstart_measurement(dev, stream, prec, contraction, n_train, n_query, epoc
     one.close()
     # Both forms meet the same stopping test, |[S; T]| <= 1e-8 max(1, |[S0; T0]|), and
     # here max(1, .) = 1 for every query: an absolute 1e-8. Their points still differ
-    # where H is ill-conditioned: near an optimum z - z* = H^{-1} g, so two points
-    # that pass the test can lie 2 (|g1| + |g2|) / lambda_min(H) apart. Checked on the
-    # sample with H at the learned start's point (FP64 evaluation).
+    # where the hyperreduced problem is flat: the sample reports the final gradients,
+    # the signed objective difference and the conditioning of the Gauss-Newton H at
+    # the learned start's point (FP64 evaluation).
     one = ift.Context.from_workload(wl, precision=ift.FP64, tol=1e-8, stream=stream.cuda_stream)
     one.set_eq_weights(rho_set)
-    ratios, lam_min, conds = [], [], []
+    g1s, g2s, dJs, lam_min, conds = [], [], [], [], []
     for q in range(n1):
         if not ok1[q]:
             continue
         ev = one.reduced_residual_jacobian(mu_q[q], mlp_z[q, :ku], mlp_z[q, ku:])
         lam = np.linalg.eigvalsh(ev["H"])
-        g_mlp = float(np.linalg.norm(np.concatenate([ev["S"], ev["T"]])))
-        g_one = math.hypot(singles[q]["normS"], singles[q]["normT"])
-        dz = float(np.linalg.norm(mlp_z[q] - z1[q]))
-        ratios.append(dz / (2.0 * (g_mlp + g_one) / lam[0]))
+        g1s.append(float(np.linalg.norm(np.concatenate([ev["S"], ev["T"]]))))
+        g2s.append(math.hypot(singles[q]["normS"], singles[q]["normT"]))
+        dJs.append(float((mlp_J[q] - J1[q]) / J1[q]))
         lam_min.append(float(lam[0]))
         conds.append(float(lam[-1] / lam[0]))
     one.close()
-    out["same_test_consistency"] = {
-        "sample": len(ratios), "threshold": 1e-8,
-        "max_dz_over_bound": float(max(ratios)), "median_lambda_min": float(np.median(lam_min)),
-        "median_condition_number": float(np.median(conds)),
-        "reading": "dz_over_bound <= 1: the two forms' points are as close as the common stopping test allows"}
+    out["same_test_comparison"] = {
+        "sample": len(dJs), "threshold": 1e-8,
+        "max_final_gradient_mlp_batched": float(max(g1s)), "max_final_gradient_fp64_one_query": float(max(g2s)),
+        "median_rel_dJ_mlp_minus_one_query": float(np.median(dJs)), "min_rel_dJ": float(min(dJs)),
+        "max_rel_dJ": float(max(dJs)), "median_lambda_min_gn": float(np.median(lam_min)),
+        "median_condition_number_gn": float(np.median(conds))}
     return out
 
 
