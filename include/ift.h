@@ -62,7 +62,7 @@ enum { IFT_BURGERS1D = 1, IFT_EULER2D = 2 };
    IFT_FP32: FP32 element kernels and contraction, FP32 sums within a warp's
    elements, FP64 sums across warps and CTAs. IFT_MIXED: evaluation calls as
    IFT_FP32; solves run the LM with FP32 assemblies to a relative optimality of
-   1e-6 (or tol if larger), or until a line search needs more than 8 halvings
+   1e-6 (or tol if larger), or until a line search needs more than one halving
    (FP32 rounding in J~ ends the FP32 stage), then continue from that point to
    tol with the IFT_FP32_JACOBIAN evaluation (H from FP32, S~, T~, J~ in FP64),
    where H is recomputed only at the first point of that stage and after a

@@ -959,6 +959,100 @@ struct ElemCore {
     }
   }
 
+  // The FP32 Euler form of jvp_state (n_b even: p = 2, 3) on packed FP32 pairs: each
+  // __ffma2_rn is two fused multiply-adds in one instruction, the operand pairs read
+  // as 8-byte words. The interpolation and the flux-Jacobian products pair
+  // consecutive table entries (nodes, state components) and add the two halves at
+  // the end; the volume test pairs consecutive nodes i, 2h and 2h + 1, of dR. Same
+  // arithmetic as jvp_state up to the order of the FP32 sums.
+  template <class FE, class FP>
+  __device__ void jvp_state_f2(FE dUe, FP dUp, const signed char* bcs, float dRo[NU]) {
+    static_assert(M == 4 && NB % 2 == 0, "packed pairs need four variables and an even node count");
+    constexpr int NB2 = NB / 2;
+    auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+    float2 dR2[NB2][M];  // (dR[2h][a], dR[2h + 1][a])
+#pragma unroll
+    for (int h = 0; h < NB2; ++h)
+#pragma unroll
+      for (int a = 0; a < M; ++a) dR2[h][a] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+      float du[M];
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        float2 s = __fmul2_rn(ld2(&B[q * NB]), make_float2(dUe(b), dUe(M + b)));
+#pragma unroll
+        for (int h = 1; h < NB2; ++h)
+          s = __ffma2_rn(ld2(&B[q * NB + 2 * h]), make_float2(dUe(2 * h * M + b), dUe((2 * h + 1) * M + b)), s);
+        du[b] = s.x + s.y;
+      }
+      const float2 du01 = make_float2(du[0], du[1]), du23 = make_float2(du[2], du[3]);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        float dFn[M];  // minus the flux change: the volume term enters R_e with a minus sign
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          const float* ah = &Ah[((q * DIM + r) * M + a) * M];
+          const float2 t = __ffma2_rn(ld2(ah + 2), du23, __fmul2_rn(ld2(ah), du01));
+          dFn[a] = -t.x - t.y;
+        }
+#pragma unroll
+        for (int h = 0; h < NB2; ++h) {
+          const float2 d2 = ld2(&D[(r * NQ + q) * NB + 2 * h]);
+#pragma unroll
+          for (int a = 0; a < M; ++a) dR2[h][a] = __ffma2_rn(d2, make_float2(dFn[a], dFn[a]), dR2[h][a]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const signed char bt = bcs[k];
+      // rolled for the same instruction-fetch reason as in jvp_state
+#pragma unroll 1
+      for (int f = 0; f < NFQ; ++f) {
+        float dui[M], duo[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          float s = 0.0f, so = 0.0f;
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            s += Lt[f * NT + j] * dUe(Dd::face_node(k, j) * M + b);
+            so += Lt[f * NT + j] * dUp((k * NT + j) * M + b);
+          }
+          dui[b] = s;
+          duo[b] = (bt == 0) ? so : ((bt == 2) ? s : 0.0f);
+        }
+        const int pt = k * NFQ + f;
+        const float2 ui01 = make_float2(dui[0], dui[1]), ui23 = make_float2(dui[2], dui[3]);
+        const float2 uo01 = make_float2(duo[0], duo[1]), uo23 = make_float2(duo[2], duo[3]);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          const float* hp = &Hp[(pt * M + a) * M];
+          const float* hm = &Hm[(pt * M + a) * M];
+          float2 t = __fmul2_rn(ld2(hp), ui01);
+          t = __ffma2_rn(ld2(hp + 2), ui23, t);
+          t = __ffma2_rn(ld2(hm), uo01, t);
+          t = __ffma2_rn(ld2(hm + 2), uo23, t);
+          const float dH = t.x + t.y;
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const int node = Dd::face_node(k, j);
+            const float v = fw[f] * Lt[f * NT + j] * dH;
+            if (node & 1) dR2[node >> 1][a].y += v;
+            else dR2[node >> 1][a].x += v;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < NB2; ++h)
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        dRo[(2 * h) * M + a] = dR2[h][a].x;
+        dRo[(2 * h + 1) * M + a] = dR2[h][a].y;
+      }
+  }
+
   // Curved geometry derivatives along a direction dx of the six nodes (12 values):
   // dJ at volume point q gives the cofactor change dcof (4), the tangent change at
   // face point pt the scaled-normal change dnt (2); both are linear in dx.
@@ -1093,7 +1187,8 @@ struct ElemCore {
           const long long off = poff[kj];
           return off >= 0 ? PhiG[off + b * ku + c] : T(0);
         };
-        jvp_state(fe, fp, bcs, dR);
+        if constexpr (M == 4 && NB % 2 == 0) jvp_state_f2(fe, fp, bcs, dR);
+        else jvp_state(fe, fp, bcs, dR);
 #pragma unroll
         for (int i = 0; i < NU; ++i) A[i * k + c] = dR[i];
       }

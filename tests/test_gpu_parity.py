@@ -335,3 +335,28 @@ def test_single_element_and_ragged_weight_list():
         g, r, _ = _assembly_pair(wl, rho_set=rs)
         for key in ("S", "T", "H"):
             assert _fro(g[key], r[key]) < 1e-10, key
+
+
+# ---------------------------------------------------------------------------
+# the largest reduced size a context takes (k_u + k_x = 64)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_largest_reduced_size_assembly_and_solve(p, record_property):
+    # 64 unknowns: H is 64 x 64 and the LM step's Cholesky runs on the full warp buffer
+    wl = W.euler_workload(n=8, p=p, k_u=56, k_x=8, seed=17)
+    g, r, _ = _assembly_pair(wl)
+    for key in ("S", "T", "H"):
+        assert _fro(g[key], r[key]) < 1e-10, key
+    assert abs(g["J"] - r["J"]) <= 1e-10 * r["J"]
+    branch = _check_solve(*_solve_pair(wl, tol=1e-8))
+    record_property("solve_branches", branch)
+
+
+def test_reduced_size_above_the_maximum_is_rejected():
+    wl = W.euler_workload(n=4, p=2, k_u=57, k_x=8, seed=17)
+    ctx = ift.Context(wl.problem, wl.p, gamma=wl.gamma)
+    ctx.set_mesh(wl.X, wl.ev)
+    with pytest.raises(ift.IFTError) as ei:
+        ctx.set_bases(wl.Phi, wl.Psi)
+    assert ei.value.status == -1
