@@ -1768,20 +1768,30 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
               ++R;
             }
             const int Bc = R + rem;
-            float h[4][4];
+            // the block on packed pairs: h2[x][p] = (h[x][2p], h[x][2p + 1])
+            float2 h2[4][2];
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-              for (int y = 0; y < 4; ++y) h[x][y] = 0.0f;
+            for (int x = 0; x < 4; ++x) h2[x][0] = h2[x][1] = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int i = 0; i < NU; ++i) {
               const float4 ar = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * R]);
               const float4 bc = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * Bc]);
-              const float av[4] = {ar.x, ar.y, ar.z, ar.w}, bv[4] = {bc.x, bc.y, bc.z, bc.w};
+              const float av[4] = {ar.x, ar.y, ar.z, ar.w};
+              const float2 b01 = make_float2(bc.x, bc.y), b23 = make_float2(bc.z, bc.w);
 #pragma unroll
-              for (int x = 0; x < 4; ++x)
+              for (int x = 0; x < 4; ++x) {
+                const float2 a2 = make_float2(av[x], av[x]);
+                h2[x][0] = __ffma2_rn(a2, b01, h2[x][0]);
+                h2[x][1] = __ffma2_rn(a2, b23, h2[x][1]);
+              }
+            }
+            float h[4][4];
 #pragma unroll
-                for (int y = 0; y < 4; ++y) h[x][y] += av[x] * bv[y];
+            for (int x = 0; x < 4; ++x) {
+              h[x][0] = h2[x][0].x;
+              h[x][1] = h2[x][0].y;
+              h[x][2] = h2[x][1].x;
+              h[x][3] = h2[x][1].y;
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)

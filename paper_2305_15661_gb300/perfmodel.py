@@ -21,19 +21,24 @@ Per element of the fused assembly (Eqs. hdm_elem, levmarq-elem, ift-eqp-res0):
 * the pointwise Jacobians, once per point: m derivative directions of the flux
   at every volume point, m along U+ and m along U- of the Roe flux at every
   face point;
-* the state columns of A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' | ...], by the
-  cheaper of the two standard forms:
-  - explicit: the blocks dR_e/dU_e (volume 2 n_q d n_b^2 m^2, faces
-    2 n_t^2 m^2 per point) and dR_e/dU_e' (2 n_t^2 m^2 per face point), then
-    the products 2 n_u k_u (n_u + n_u');
-  - directional: per column the interpolation, the pointwise Jacobians applied
-    (2 d m^2 per volume point, 4 m^2 per face point), the contravariant form and
-    the test sums, the traces and the lifting;
-* the mesh columns dR_e/dx_e Psi_e: per direction the contravariant change of
-  the volume flux (2 d^2 m per point) with the test sums, and the flux change
-  of the scaled normal at each face point (2 d m) with the lifting; taken along
-  the k_x columns, or along the n_x coordinates followed by 2 n_u k_x n_x when
-  that is fewer;
+* the state columns of A_e = [dR_e/dU_e Phi_e + dR_e/dU_e' Phi_e' | ...], the
+  volume part and the face part each by the cheaper of two standard forms:
+  - volume, explicit: the block dR_e/dU_e formed through the flux Jacobians,
+    per point n_q (2 d n_b m^2 + 2 n_b^2 m^2) (the test against D first, then the
+    basis B), then the product with Phi_e, 2 n_u^2 k_u;
+  - volume, directional: per column the interpolation, the pointwise Jacobians
+    applied (2 d m^2 per point), the contravariant form and the test sums;
+  - faces, explicit: per face point the two trace blocks (4 n_t^2 m^2, the
+    interior one added into dR_e/dU_e before its product), and per face the
+    neighbour block's product with the neighbour's trace rows, 2 (n_t m)^2 k_u;
+  - faces, directional: per column and face point the traces, the two Roe
+    Jacobians applied (4 m^2) and the lifting;
+* the mesh columns dR_e/dx_e Psi_e by the cheaper of: per direction the
+  contravariant change of the volume flux (2 d^2 m per point) with the test
+  sums and the scaled-normal change of the face flux (2 d m per face point) with
+  the lifting, along the k_x columns; or the quadrature sum taken once,
+  E = 2 n_q n_b m d^2, then per column 2 n_u d^2 for the volume and the face
+  terms as before;
 * the weighted contraction: the symmetric A_e^T A_e (n_u k (k + 1): k (k + 1) / 2
   dot products of length n_u), A_e^T R_e (2 n_u k) and |R_e|^2 (2 n_u).
 
@@ -93,14 +98,17 @@ def flops_per_element(problem: int, p: int, ku: int, kx: int, jac: bool = True) 
     out["objective"] = 2 * nu
     if jac:
         out["pointwise_jacobians"] = nq * m * ftan + nfp * m * (htan_p + htan_m)
-        explicit = (2 * nq * d * nb * nb * m * m + nfp * 4 * nt * nt * m * m
-                    + 2 * nu * ku * (nu + nup))
-        directional = ku * (nq * (2 * nb * m + 2 * d * m * m + 2 * d * d * m) + test
-                            + nfp * (4 * nt * m + 4 * m * m + 2 * nt * m))
-        out["state_columns"] = min(explicit, directional)
-        out["state_columns_form"] = "explicit" if explicit <= directional else "directional"
-        per_dir = nq * 2 * d * d * m + test + nfp * (2 * d * m + 2 * nt * m)
-        out["mesh_columns"] = min(kx * per_dir, nx * per_dir + 2 * nu * kx * nx)
+        vol_explicit = nq * (2 * d * nb * m * m + 2 * nb * nb * m * m) + 2 * nu * nu * ku
+        vol_directional = ku * (nq * (2 * nb * m + 2 * d * m * m + 2 * d * d * m) + test)
+        face_explicit = nfp * 4 * nt * nt * m * m + nf * 2 * (nt * m) ** 2 * ku
+        face_directional = ku * nfp * (4 * nt * m + 4 * m * m + 2 * nt * m)
+        out["state_columns"] = min(vol_explicit, vol_directional) + min(face_explicit, face_directional)
+        out["state_columns_form"] = ("volume " + ("explicit" if vol_explicit <= vol_directional else "directional")
+                                     + ", faces " + ("explicit" if face_explicit <= face_directional else "directional"))
+        face_dir = nfp * (2 * d * m + 2 * nt * m)
+        per_dir = nq * 2 * d * d * m + test + face_dir
+        via_e = 2 * nq * nb * m * d * d + kx * (2 * nu * d * d + face_dir)
+        out["mesh_columns"] = min(kx * per_dir, via_e) if kx > 0 else 0
         out["contraction"] = nu * k * (k + 1) + 2 * nu * k
     parts = [v for key, v in out.items() if key != "state_columns_form"]
     out["total"] = sum(parts)
