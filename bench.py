@@ -42,7 +42,7 @@ METRIC = "ROM solves/sec at rel. resid 1e-8 vs FP64 oracle; element R+J evals/se
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused FP64
 # assembly kernel of this workload, from an ncu capture of the current kernel
 # (78.89 MB + 2.45 MB); set to None when the kernel changes until it is re-taken.
-FP64_ASSEMBLY_DRAM_BYTES = 81.34e6
+FP64_ASSEMBLY_DRAM_BYTES = None
 WORKLOAD = "euler2d_p2_20000el_ku20_kx4_rho1_fp64"
 
 

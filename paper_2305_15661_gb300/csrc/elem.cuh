@@ -235,6 +235,10 @@ struct Tabs {
   // points (NQ x 6 x 2), and dN_j/dt along each face at its points (NF x NFQ x 6)
   static constexpr int nGv = Dd::CURVED ? Dd::NQ * 12 : 0, nGt = Dd::CURVED ? Dd::NFACE * Dd::NFQ * 6 : 0;
   static constexpr int total = nD + nB + nL + nfw + nqw + nqx + nGv + nGt;
+  // face coefficients fw[f] Lt[f][i] Lt[f][j] (NFQ x NT x NT), built beside the
+  // staged tables (not part of the packed host tables)
+  static constexpr int nC = Dd::NFQ * Dd::NTRACE * Dd::NTRACE;
+  __host__ __device__ static constexpr size_t cf_offset() { return ((size_t)total * sizeof(T) + 15) / 16 * 16; }
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -332,8 +336,8 @@ struct WarpLayout {
 
 template <class T, int PROB, int P>
 __host__ __device__ inline size_t cta_bytes(int ku, int kx) {
-  return align16(Tabs<T, PROB, P>::total * sizeof(T)) + align16((size_t)(ku > 0 ? ku : 1) * sizeof(T)) +
-         align16((size_t)(kx > 0 ? kx : 1) * 8);
+  return align16(Tabs<T, PROB, P>::total * sizeof(T)) + align16(Tabs<T, PROB, P>::nC * sizeof(T)) +
+         align16((size_t)(ku > 0 ? ku : 1) * sizeof(T)) + align16((size_t)(kx > 0 ? kx : 1) * 8);
 }
 
 template <class T, int PROB, int P, bool JAC, bool GRAD = false>
@@ -366,6 +370,7 @@ struct ElemCore {
                        NXE = Dd::NXE, NF = Dd::NFACE, NFQ = Dd::NFQ, NT = Dd::NTRACE;
   // shared tables (GdV, GtF: curved geometry shape-function derivatives)
   const T *D, *B, *Lt, *fw, *qw, *qxi, *GdV, *GtF;
+  const T* Cf;  // fw[f] Lt[f][i] Lt[f][j]: the face blocks of dR_e/dU_e
   // warp buffers
   double *xe, *Psie, *dN;
   T *Phie, *Ue, *Up, *Fh, *fph, *Ah, *sq, *Hf, *Hp, *Hm, *Hn, *Ui, *Uo, *R, *A, *dNt, *W, *acc;
@@ -1231,6 +1236,32 @@ struct ElemCore {
             }
           }
         }
+        // the faces' blocks of dR_e/dU_e (both nodes on face kf): sum_f fw Lt[f][i] Lt[f][j]
+        // times dH/dU+ (plus dH/dU- on outflow faces, where U- = U+), added before the
+        // product with Phi_e; jac_state_faces then does the neighbour traces only
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+          const int e = lane + 32 * t;
+          if (e < RP * NU) {
+            const int rl = e / NU, col = e - rl * NU;
+            const int row = r0 + rl, i = row / M, a = row - i * M;
+            const int j = col / M, b = col - j * M;
+            T s = T(0);
+#pragma unroll
+            for (int kf = 0; kf < NF; ++kf) {
+              const int ii = face_pos(kf, i), jj = face_pos(kf, j);
+              if (ii < 0 || jj < 0) continue;
+              const bool outflow = bcs[kf] == 2;
+#pragma unroll
+              for (int f = 0; f < NFQ; ++f) {
+                const int o = ((kf * NFQ + f) * M + a) * M + b;
+                const T h = outflow ? Hp[o] + Hm[o] : Hp[o];
+                s += Cf[(f * NT + ii) * NT + jj] * h;
+              }
+            }
+            jv[t] += s;
+          }
+        }
 #pragma unroll
         for (int t = 0; t < NJ; ++t) {
           const int e = lane + 32 * t;
@@ -1250,7 +1281,7 @@ struct ElemCore {
     } else {
       jac_state_volume_jvp(lane, ku, k);
     }
-    jac_state_faces(lane, bcs, ku, k);
+    jac_state_faces(lane, bcs, ku, k, kExplicitVolume(NU, sizeof(T)));
   }
 
   // Volume part of the state columns by Jacobian-vector products: per volume point,
@@ -1295,14 +1326,18 @@ struct ElemCore {
   // Face part of the state columns: per face point, the trace directions dU+ (this
   // element's Phi rows) and dU- (the neighbour's trace rows), dH = Hp dU+ + Hm dU-,
   // lifted onto the face's nodes.
-  __device__ void jac_state_faces(int lane, const signed char* bcs, int ku, int k) {
+  // neighbour_only: the interior trace's blocks are already in the volume block
+  // (explicit form), so only interior faces' neighbour traces remain: dH = Hm dU-.
+  __device__ void jac_state_faces(int lane, const signed char* bcs, int ku, int k, bool neighbour_only = false) {
     T* dU = W;                // [2][M][ku]: interior, exterior
     T* dH = W + 2 * M * ku;   // [M][ku]
+    const int s0 = neighbour_only ? 1 : 0;  // first side staged
     for (int pt = 0; pt < NF * NFQ; ++pt) {
       const int kf = pt / NFQ, f = pt - kf * NFQ;
       const signed char bt = bcs[kf];
+      if (neighbour_only && bt != 0) continue;  // boundary faces: no neighbour trace
       __syncwarp();
-      for (int e = lane; e < 2 * M * ku; e += 32) {
+      for (int e = lane + s0 * M * ku; e < 2 * M * ku; e += 32) {
         const int sb = dku.div(e), c = e - sb * ku;
         const int side = sb / M, b = sb - side * M;
         T s = T(0);
@@ -1325,8 +1360,13 @@ struct ElemCore {
         const T* hp = &Hp[(pt * M + a) * M];
         const T* hm = &Hm[(pt * M + a) * M];
         T s = T(0);
+        if (neighbour_only) {
 #pragma unroll
-        for (int b = 0; b < M; ++b) s += hp[b] * dU[b * ku + c] + hm[b] * dU[(M + b) * ku + c];
+          for (int b = 0; b < M; ++b) s += hm[b] * dU[(M + b) * ku + c];
+        } else {
+#pragma unroll
+          for (int b = 0; b < M; ++b) s += hp[b] * dU[b * ku + c] + hm[b] * dU[(M + b) * ku + c];
+        }
         dH[e] = fw[f] * s;
       }
       __syncwarp();
@@ -1601,10 +1641,21 @@ template <class T, int PROB, int P>
 __device__ inline void stage_cta(const AsmArgs<T>& a, unsigned char* smem, const double* w, const double* tau,
                                  T*& tab, T*& wT, double*& tauD) {
   using TB = Tabs<T, PROB, P>;
+  using Dd = Disc<PROB, P>;
   tab = (T*)smem;
-  wT = (T*)(smem + align16(TB::total * sizeof(T)));
-  tauD = (double*)(smem + align16(TB::total * sizeof(T)) + align16((size_t)(a.ku > 0 ? a.ku : 1) * sizeof(T)));
+  const size_t o_w = align16(TB::total * sizeof(T)) + align16(TB::nC * sizeof(T));
+  wT = (T*)(smem + o_w);
+  tauD = (double*)(smem + o_w + align16((size_t)(a.ku > 0 ? a.ku : 1) * sizeof(T)));
   for (int i = threadIdx.x; i < TB::total; i += blockDim.x) tab[i] = (T)a.tables[i];
+  // fw[f] Lt[f][i] Lt[f][j] from the FP64 host tables (packed D | B | Lt | fw | ...)
+  T* cf = (T*)(smem + TB::cf_offset());
+  for (int i = threadIdx.x; i < TB::nC; i += blockDim.x) {
+    const int f = i / (Dd::NTRACE * Dd::NTRACE), ij = i - f * Dd::NTRACE * Dd::NTRACE;
+    const int ii = ij / Dd::NTRACE, jj = ij - ii * Dd::NTRACE;
+    const double* Lt = a.tables + TB::nD + TB::nB;
+    const double w = a.tables[TB::nD + TB::nB + TB::nL + f];
+    cf[i] = (T)(w * Lt[f * Dd::NTRACE + ii] * Lt[f * Dd::NTRACE + jj]);
+  }
   for (int i = threadIdx.x; i < a.ku; i += blockDim.x) wT[i] = (T)w[i];
   for (int i = threadIdx.x; i < a.kx; i += blockDim.x) tauD[i] = tau[i];
 }
@@ -1620,6 +1671,7 @@ __device__ inline void bind_tables(ElemCore<T, PROB, P, JAC>& C, T* tab) {
   C.qxi = C.qw + TB::nqw;
   C.GdV = C.qxi + TB::nqx;
   C.GtF = C.GdV + TB::nGv;
+  C.Cf = (const T*)((const unsigned char*)tab + TB::cf_offset());
 }
 
 // Steps 1-5 for element e at the state (wT, tauD) and parameters mu: gather,

@@ -33,6 +33,9 @@ Per element of the fused assembly (Eqs. hdm_elem, levmarq-elem, ift-eqp-res0):
     neighbour block's product with the neighbour's trace rows, 2 (n_t m)^2 k_u;
   - faces, directional: per column and face point the traces, the two Roe
     Jacobians applied (4 m^2) and the lifting;
+  - faces, mixed: the interior trace's block (2 n_t^2 m^2 per face point) added
+    into dR_e/dU_e before its product, and per column and face point only the
+    neighbour's trace, dH/dU- applied (2 m^2) and the lifting;
 * the mesh columns dR_e/dx_e Psi_e by the cheaper of: per direction the
   contravariant change of the volume flux (2 d^2 m per point) with the test
   sums and the scaled-normal change of the face flux (2 d m per face point) with
@@ -102,9 +105,12 @@ def flops_per_element(problem: int, p: int, ku: int, kx: int, jac: bool = True) 
         vol_directional = ku * (nq * (2 * nb * m + 2 * d * m * m + 2 * d * d * m) + test)
         face_explicit = nfp * 4 * nt * nt * m * m + nf * 2 * (nt * m) ** 2 * ku
         face_directional = ku * nfp * (4 * nt * m + 4 * m * m + 2 * nt * m)
-        out["state_columns"] = min(vol_explicit, vol_directional) + min(face_explicit, face_directional)
+        face_mixed = nfp * 2 * nt * nt * m * m + ku * nfp * (2 * nt * m + 2 * m * m + 2 * nt * m)
+        faces = {"explicit": face_explicit, "directional": face_directional, "mixed": face_mixed}
+        face_form = min(faces, key=faces.get)
+        out["state_columns"] = min(vol_explicit, vol_directional) + faces[face_form]
         out["state_columns_form"] = ("volume " + ("explicit" if vol_explicit <= vol_directional else "directional")
-                                     + ", faces " + ("explicit" if face_explicit <= face_directional else "directional"))
+                                     + ", faces " + face_form)
         face_dir = nfp * (2 * d * m + 2 * nt * m)
         per_dir = nq * 2 * d * d * m + test + face_dir
         via_e = 2 * nq * nb * m * d * d + kx * (2 * nu * d * d + face_dir)
