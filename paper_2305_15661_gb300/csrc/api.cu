@@ -41,6 +41,7 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
                                        const double* mu, int mustride, const double* colsum, const double* y0,
                                        const double* z0, int phase);
 __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum);
+__global__ void geo32_kernel(const double* X, const int* ev, const double* Psi, int kx, long n_elems, float4* out);
 __global__ void lm_restart_kernel(LMState* states, int B, int ku, int kx);
 __global__ void residual_norms_finish_kernel(const double* part, int B, int nchunk, double* norms);
 __global__ void merge_grad_kernel(const double* g, int k, int nacc, double* res, const LMState* states);
@@ -127,6 +128,7 @@ struct ift_ctx {
   int ku = 0, kx = 0;
   double* d_Phi = nullptr;
   float* d_Phi32 = nullptr;
+  float4* d_geo32 = nullptr;  // FP32 edge table of straight-sided triangles (FP32 contexts)
   double* d_Psi = nullptr;
   // weights
   int64_t nnz = -1;
@@ -275,6 +277,7 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
   a.skip = skip;
   a.contraction = c->cfg.contraction;
   a.need_hn = 0;
+  a.geo32 = c->d_geo32;
   return a;
 }
 
@@ -283,7 +286,7 @@ AsmArgs<TT> make_args(ift_ctx* c, const TT* Phi, const double* w, const double* 
 // need; the shape is fixed per configuration, so sums are reproducible.
 // Dynamic shared memory of the fused element kernel of precision wp for w warps per CTA.
 size_t shapes_smem(const ift_ctx* c, int wp, int w) {
-  return c->ks[wp].valid ? c->ks[wp].smem_bytes(true, c->ku, c->kx, w) : 0;
+  return c->ks[wp].valid ? c->ks[wp].smem_bytes_fused(true, c->ku, c->kx, w) : 0;
 }
 
 // Warps of the fused element kernel of precision wp resident per SM with w warps per CTA
@@ -305,7 +308,7 @@ ift_status plan_launch(ift_ctx* c, int wp) {
   const long items = (c->nnz < 0) ? c->n_elems : c->nnz;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, wpc);
+    const size_t smem = ks.smem_bytes_fused(jac, c->ku, c->kx, wpc);
     if (smem > (size_t)c->smem_optin)
       return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", wpc, smem,
                      c->smem_optin);
@@ -581,6 +584,7 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_bc);
   dfree(c->d_Phi);
   dfree(c->d_Phi32);
+  dfree(c->d_geo32);
   dfree(c->d_Psi);
   dfree(c->d_elems);
   dfree(c->d_rho);
@@ -736,6 +740,15 @@ ift_status ift_set_bases(ift_ctx* c, int64_t N_u, int k_u, const double* Phi, in
   }
   CK(dalloc(c->d_Psi, (size_t)N_x * (k_x > 0 ? k_x : 1)), "alloc Psi");
   if (k_x > 0) CK(cudaMemcpy(c->d_Psi, Psi, (size_t)N_x * k_x * 8, cudaMemcpyHostToDevice), "copy Psi");
+  dfree(c->d_geo32);
+  if (c->cfg.precision != IFT_FP64 && c->dim == 2 && c->nv == 3) {
+    // straight-sided triangles: the FP32 element pass takes its geometry from this table
+    CK(dalloc(c->d_geo32, (size_t)c->n_elems * (1 + k_x)), "alloc edge table");
+    const long g = std::min<long>((c->n_elems + 255) / 256, 4096);
+    geo32_kernel<<<(int)(g > 0 ? g : 1), 256, 0, c->stream>>>(c->d_X, c->d_ev, c->d_Psi, k_x, c->n_elems,
+                                                             c->d_geo32);
+    CK(cudaGetLastError(), "edge table");
+  }
   c->ku = k_u;
   c->kx = k_x;
   const int nacc = c->nacc();
@@ -1184,7 +1197,7 @@ ift_status plan_batched(ift_ctx* c, int wp) {
   const int bwpc = c->bwpc[wp], block = 32 * bwpc;
   for (int j = 0; j < 2; ++j) {
     const bool jac = j == 1;
-    const size_t smem = ks.smem_bytes(jac, c->ku, c->kx, bwpc);
+    const size_t smem = ks.smem_bytes_fused(jac, c->ku, c->kx, bwpc);
     if (smem > (size_t)c->smem_optin)
       return c->fail(IFT_ERR_ARG, "%d warps per CTA need %zu bytes of shared memory (at most %d)", bwpc, smem,
                      c->smem_optin);

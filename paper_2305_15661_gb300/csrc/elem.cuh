@@ -117,6 +117,11 @@ struct AsmArgs {
   // form dH/dn at face points even without mesh columns (the snapshot alignment
   // applies dR/dx to full mesh directions)
   int need_hn;
+  // FP32 straight-sided 2-D elements (may be null): per element 1 + kx groups of
+  // four floats, the reference edges (x_1 - x_0, x_2 - x_0) = (e1x, e1y, e2x, e2y)
+  // and the same differences of each mesh column of Psi (taken in FP64, rounded
+  // once); the FP32 geometry is formed from them with no FP64 arithmetic
+  const float4* geo32 = nullptr;
 };
 
 // H += rho A^T A on the tensor cores (warp-level mma.m16n8k8, TF32 inputs, FP32
@@ -252,22 +257,33 @@ __host__ __device__ constexpr bool kExplicitVolume(int nu, int word) { return wo
 // Entries of Jv per register pass (9 doubles per lane).
 constexpr int kJvPass = 288;
 
+// FP32 Euler state columns by rows of dR_e/dU_e in registers (jac_state_rows_f2):
+// an even node count (packed pairs) and at most one row per lane (p <= 2); p = 3
+// (40 rows) takes the per-column products, which measured faster there.
+__host__ __device__ constexpr bool kStateRowsF32(int m, int nb) { return m == 4 && nb % 2 == 0 && m * nb <= 32; }
+
 // Per-warp shared-memory layout. GRAD: the gradient pass, which for Euler forms no
 // Jacobian columns, no face Jacobians and no volume flux Jacobians (the states U_q
 // only), and accumulates only [g | J | count] (SLIM: those buffers shrink to what it uses).
-template <class T, int PROB, int P, bool JAC, bool GRAD = false>
+// FUSED: the layout of the fused assembly kernels (assemble_kernel and
+// assemble_batched_kernel); other kernels that carve the same buffers (inspection,
+// per-element gradients, alignment) take the general layout.
+template <class T, int PROB, int P, bool JAC, bool GRAD = false, bool FUSED = false>
 struct WarpLayout {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE,
                        NF = Dd::NFACE, NFQ = Dd::NFQ;
   static constexpr bool SLIM = GRAD && JAC && Dd::EULER;
+  // the fused FP32 Euler Jacobian pass of p <= 2 forms the state columns by rows in
+  // registers and stages only the mesh columns' sums in W
+  static constexpr bool ROWS = FUSED && JAC && !GRAD && sizeof(T) == 4 && kStateRowsF32(Dd::M, Dd::NB);
   // elements a warp evaluates at once: two (one per half-warp, each with its own
   // copy of this layout) in the Euler gradient pass, else one
   static constexpr int PER_WARP = SLIM ? 2 : 1;
   // offset of g (the tail [g | J | count]) within the accumulators
   __host__ __device__ static int gacc_offset(int k) { return SLIM ? 0 : acc_tail(k); }
   size_t oxe, oPsie, odN, oPhie, oPoff, oUe, oUp, oFh, ofph, oAh, osq, oHf, oHp, oHm, oHn, oUi, oUo, oR, oA, odNt,
-      oW, owq, otq, oacc, ocofq, ontq, bytes;
+      oW, owq, otq, otqf, oacc, ocofq, ontq, bytes;
   __host__ __device__ WarpLayout(int ku, int kx) {
     const int k = ku + kx;
     size_t b = 0;
@@ -306,7 +322,7 @@ struct WarpLayout {
       // dU (2 M ku) + dH (M ku), mesh directions E (NB M 4) + dcof (4 kx) + K (NF NT M 2)
       size_t w1 = (size_t)(DIM + 1) * M * ku, w2 = (size_t)3 * M * ku,
              w3 = (size_t)Dd::NB * M * 4 + 4 * kx + (size_t)NF * Dd::NTRACE * M * 2 + (size_t)NF * 2 * kx;
-      size_t w = w1 > w2 ? w1 : w2;
+      size_t w = ROWS ? 0 : (w1 > w2 ? w1 : w2);
       if (w3 > w) w = w3;
       // curved mesh columns: dF per (volume point, column) and dH per (face point, column)
       if (Dd::CURVED) {
@@ -314,7 +330,7 @@ struct WarpLayout {
         if (wc > w) w = wc;
       }
       if (SLIM) w = 0;  // the gradient pass stages only the adjoint below
-      {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), nu (2 NF NFQ),
+      if (!ROWS) {  // adjoint pass: t_q (NQ M), mu+ and mu- per face point (2 NF NFQ M), nu (2 NF NFQ),
          // eps per volume point (4 NQ), dU_e, dU_e' (NU + NU'), eps (4)
         const size_t wa = (size_t)NQ * M + (size_t)2 * NF * NFQ * M + (size_t)2 * NF * NFQ + (size_t)4 * NQ + NU +
                           NUP + 4;
@@ -329,6 +345,7 @@ struct WarpLayout {
     }
     owq = put(ku > 0 ? ku : 1, sizeof(T));
     otq = put(kx > 0 ? kx : 1, 8);
+    otqf = put(kx > 0 ? kx : 1, 4);  // the same tau in FP32 (FP32 geometry from the edge table)
     oacc = put(SLIM ? (size_t)k + 2 : (size_t)acc_count(k), sizeof(T));
     bytes = b;
   }
@@ -337,15 +354,23 @@ struct WarpLayout {
 template <class T, int PROB, int P>
 __host__ __device__ inline size_t cta_bytes(int ku, int kx) {
   return align16(Tabs<T, PROB, P>::total * sizeof(T)) + align16(Tabs<T, PROB, P>::nC * sizeof(T)) +
-         align16((size_t)(ku > 0 ? ku : 1) * sizeof(T)) + align16((size_t)(kx > 0 ? kx : 1) * 8);
+         align16((size_t)(ku > 0 ? ku : 1) * sizeof(T)) + align16((size_t)(kx > 0 ? kx : 1) * 8) +
+         align16((size_t)(kx > 0 ? kx : 1) * 4);
 }
 
-template <class T, int PROB, int P, bool JAC, bool GRAD = false>
+// The upper-triangle pair table of the lane-owned contraction; the fused FP32
+// kernels with k a multiple of 4 take 4 x 4 blocks (or tensor-core tiles) instead.
+template <class T>
+__host__ __device__ inline bool needs_pair_table(bool jac, bool grad, bool fused, int k) {
+  return jac && !grad && !(fused && sizeof(T) == 4 && k % 4 == 0);
+}
+
+template <class T, int PROB, int P, bool JAC, bool GRAD = false, bool FUSED = false>
 __host__ __device__ inline size_t assemble_smem_bytes(int ku, int kx, int warps) {
   const int k = ku + kx;
-  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD, FUSED>;
   return cta_bytes<T, PROB, P>(ku, kx) + (size_t)warps * Lay::PER_WARP * Lay(ku, kx).bytes +
-         (GRAD ? 0 : align16((size_t)k * (k + 1)));  // upper-triangle pair table
+         (needs_pair_table<T>(JAC, GRAD, FUSED, k) ? align16((size_t)k * (k + 1)) : 0);
 }
 
 // Pointwise stage and residual for one element whose U_e, U_e', x_e are staged.
@@ -380,14 +405,16 @@ struct ElemCore {
   T cof[4];      // cof[d*2 + r] = (g J^{-T})[d][r]
   T detJ;
   T nt[3][2];    // scaled face normals (2-D)
+  bool g32;      // this element's geometry came from the FP32 edge table (Psie holds its rows)
   double x0d, x1d;  // 1-D end points
   const T* PhiG;     // Phi in global memory (neighbour trace rows)
   long long* poff;   // per face and trace position: row-block offset in PhiG, -1 on boundary faces
   FastDiv dku, dkx;  // division by k_u and k_x in the lane loops
 
-  template <bool GRAD = false>
+  template <bool GRAD = false, bool FUSED = false>
   __device__ void carve(unsigned char* base, int ku, int kx) {
-    WarpLayout<T, PROB, P, JAC, GRAD> L(ku, kx);
+    WarpLayout<T, PROB, P, JAC, GRAD, FUSED> L(ku, kx);
+    g32 = false;
     dku.init(ku > 0 ? ku : 1);
     dkx.init(kx > 0 ? kx : 1);
     xe = (double*)(base + L.oxe);
@@ -494,6 +521,38 @@ struct ElemCore {
       }
       return det > 0.0;
     }
+  }
+
+  // Straight-sided 2-D geometry in FP32 from the element's rows of the edge table
+  // (staged in Psie: the reference edges, then one row per mesh column): the current
+  // edges x_1 - x_0 = (j00, j10) and x_2 - x_0 = (j01, j11) are the reference ones plus
+  // sum_c tau_c times the column's edge differences, and the cofactor, determinant
+  // and scaled normals follow as in geometry(). Returns false if the element is inverted.
+  __device__ bool geometry32(const float* tauF, int kx) {
+    const float4* g = reinterpret_cast<const float4*>(Psie);
+    float4 j = g[0];  // (j00, j10, j01, j11)
+    for (int c = 0; c < kx; ++c) {
+      const float4 d = g[1 + c];
+      const float t = tauF[c];
+      j.x = fmaf(d.x, t, j.x);
+      j.y = fmaf(d.y, t, j.y);
+      j.z = fmaf(d.z, t, j.z);
+      j.w = fmaf(d.w, t, j.w);
+    }
+    const float det = j.x * j.w - j.z * j.y;
+    detJ = (T)det;
+    cof[0] = (T)j.w;
+    cof[1] = (T)(-j.y);
+    cof[2] = (T)(-j.z);
+    cof[3] = (T)j.x;
+    // face k runs from vertex k to vertex k + 1: x_1 - x_0, x_2 - x_1, x_0 - x_2
+    nt[0][0] = (T)j.y;
+    nt[0][1] = (T)(-j.x);
+    nt[1][0] = (T)(j.w - j.y);
+    nt[1][1] = (T)(-(j.z - j.x));
+    nt[2][0] = (T)(-j.w);
+    nt[2][1] = (T)j.z;
+    return det > 0.0f;
   }
 
   // Step 4: pointwise quantities. bcs: per-face boundary type.
@@ -1058,6 +1117,196 @@ struct ElemCore {
       }
   }
 
+  // FP32 Euler state columns (n_b even: p = 2) by rows of the element Jacobian.
+  // Lane r owns row r = (i, a) of J = dR_e/dU_e with its n_u entries in registers,
+  // paired over the nodes 2h, 2h + 1: the volume block
+  //   J[(i,a)][(j,b)] = -sum_q B_q[j] sum_r D_r[q][i] Ahat_qr[a][b]
+  // plus the interior trace's face blocks sum_f fw Lt[f][ii] Lt[f][jj] (dH/dU+,
+  // plus dH/dU- on outflow faces where U- = U+)[a][b], then
+  //   A[r][c] = sum_col J[r][col] Phi_e[col][c]
+  // eight or four columns at a time on packed pairs. The neighbour traces of
+  // interior faces are added by columns afterwards (jac_state_neighbours_f2). The
+  // same sums as the Jacobian-vector products, taken in another order.
+  __device__ void jac_state_rows_f2(int lane, const signed char* bcs, int ku, int k) {
+    static_assert(M == 4 && NB % 2 == 0 && DIM == 2, "packed rows need four variables and an even node count");
+    constexpr int NB2 = NB / 2;
+    auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+    auto ld4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+    const bool vec = (ku % 4 == 0) && (k % 4 == 0);  // 16-byte rows of Phi_e and A
+    for (int row = lane; row < NU; row += 32) {
+      const int i = row >> 2, a = row & 3;
+      float2 J2[NB2][M];  // (J[row][(2h, b)], J[row][(2h + 1, b)])
+#pragma unroll
+      for (int h = 0; h < NB2; ++h)
+#pragma unroll
+        for (int b = 0; b < M; ++b) J2[h][b] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+      for (int q = 0; q < NQ; ++q) {
+        // t[b] = -sum_r D_r[q][i] Ahat_qr[a][b] (the volume term enters R_e with a minus sign)
+        const float d0 = -D[q * NB + i], d1 = -D[(NQ + q) * NB + i];
+        const float4 a0 = ld4(&Ah[((q * DIM + 0) * M + a) * M]);
+        const float4 a1 = ld4(&Ah[((q * DIM + 1) * M + a) * M]);
+        const float2 dd0 = make_float2(d0, d0), dd1 = make_float2(d1, d1);
+        const float2 t01 = __ffma2_rn(dd1, make_float2(a1.x, a1.y), __fmul2_rn(dd0, make_float2(a0.x, a0.y)));
+        const float2 t23 = __ffma2_rn(dd1, make_float2(a1.z, a1.w), __fmul2_rn(dd0, make_float2(a0.z, a0.w)));
+        const float2 tb[4] = {make_float2(t01.x, t01.x), make_float2(t01.y, t01.y), make_float2(t23.x, t23.x),
+                              make_float2(t23.y, t23.y)};
+#pragma unroll
+        for (int h = 0; h < NB2; ++h) {
+          const float2 b2 = ld2(&B[q * NB + 2 * h]);
+#pragma unroll
+          for (int b = 0; b < M; ++b) J2[h][b] = __ffma2_rn(b2, tb[b], J2[h][b]);
+        }
+      }
+      // the interior trace's face blocks (both nodes on face kf)
+#pragma unroll
+      for (int kf = 0; kf < NF; ++kf) {
+        const int ii = face_pos(kf, i);
+        if (ii < 0) continue;
+        const bool outflow = bcs[kf] == 2;
+#pragma unroll 1
+        for (int f = 0; f < NFQ; ++f) {
+          const int o = ((kf * NFQ + f) * M + a) * M;
+          float4 hv = ld4(&Hp[o]);
+          if (outflow) {
+            const float4 hm = ld4(&Hm[o]);
+            hv.x += hm.x;
+            hv.y += hm.y;
+            hv.z += hm.z;
+            hv.w += hm.w;
+          }
+          const float hb[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+          for (int jj = 0; jj < NT; ++jj) {
+            const int node = Dd::face_node(kf, jj);
+            const float cf = Cf[(f * NT + ii) * NT + jj];
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+              if (node & 1) J2[node >> 1][b].y += cf * hb[b];
+              else J2[node >> 1][b].x += cf * hb[b];
+            }
+          }
+        }
+      }
+      // A[row][c] = J[row] . Phi_e[:, c]
+      float* arow = &A[row * k];
+      int c0 = 0;
+      if (vec) {
+        for (; c0 + 8 <= ku; c0 += 8) {
+          float2 s[4] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f),
+                         make_float2(0.0f, 0.0f)};
+#pragma unroll
+          for (int h = 0; h < NB2; ++h)
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+#pragma unroll
+              for (int o = 0; o < 2; ++o) {
+                const float jv = o ? J2[h][b].y : J2[h][b].x;
+                const float2 jj = make_float2(jv, jv);
+                const float* pr = &Phie[((2 * h + o) * M + b) * ku + c0];
+                const float4 p0 = ld4(pr), p1 = ld4(pr + 4);
+                s[0] = __ffma2_rn(jj, make_float2(p0.x, p0.y), s[0]);
+                s[1] = __ffma2_rn(jj, make_float2(p0.z, p0.w), s[1]);
+                s[2] = __ffma2_rn(jj, make_float2(p1.x, p1.y), s[2]);
+                s[3] = __ffma2_rn(jj, make_float2(p1.z, p1.w), s[3]);
+              }
+          *reinterpret_cast<float4*>(&arow[c0]) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+          *reinterpret_cast<float4*>(&arow[c0 + 4]) = make_float4(s[2].x, s[2].y, s[3].x, s[3].y);
+        }
+        if (c0 + 4 <= ku) {
+          float2 s[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+#pragma unroll
+          for (int h = 0; h < NB2; ++h)
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+#pragma unroll
+              for (int o = 0; o < 2; ++o) {
+                const float jv = o ? J2[h][b].y : J2[h][b].x;
+                const float2 jj = make_float2(jv, jv);
+                const float4 p0 = ld4(&Phie[((2 * h + o) * M + b) * ku + c0]);
+                s[0] = __ffma2_rn(jj, make_float2(p0.x, p0.y), s[0]);
+                s[1] = __ffma2_rn(jj, make_float2(p0.z, p0.w), s[1]);
+              }
+          *reinterpret_cast<float4*>(&arow[c0]) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+          c0 += 4;
+        }
+      }
+      for (int c = c0; c < ku; ++c) {
+        float s = 0.0f;
+#pragma unroll
+        for (int h = 0; h < NB2; ++h)
+#pragma unroll
+          for (int b = 0; b < M; ++b) {
+            s += J2[h][b].x * Phie[((2 * h) * M + b) * ku + c];
+            s += J2[h][b].y * Phie[((2 * h + 1) * M + b) * ku + c];
+          }
+        arow[c] = s;
+      }
+    }
+    __syncwarp();
+    jac_state_neighbours_f2(lane, bcs, ku, k);
+  }
+
+  // The neighbour traces of the interior faces, one column of Phi per lane: at each
+  // face point the neighbour's trace along the column, dU- = sum_j Lt[f][j]
+  // Phi'[j][:, c], dH = dH/dU- dU-, lifted onto the face's nodes (fw Lt[f][j] dH) and
+  // added to A. Boundary faces have none: their exterior state is the far field
+  // (no dependence on U) or the interior trace (in the face blocks of J).
+  __device__ void jac_state_neighbours_f2(int lane, const signed char* bcs, int ku, int k) {
+    auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+    for (int c = lane; c < ku; c += 32) {
+#pragma unroll
+      for (int kf = 0; kf < NF; ++kf) {
+        if (bcs[kf] != 0) continue;
+        float up[NT][M];  // the neighbour's trace rows along this column
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const long long off = poff[kf * NT + j];
+#pragma unroll
+          for (int b = 0; b < M; ++b) up[j][b] = PhiG[off + b * ku + c];
+        }
+        float add[NT][M];
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int a = 0; a < M; ++a) add[j][a] = 0.0f;
+#pragma unroll 1
+        for (int f = 0; f < NFQ; ++f) {
+          float duo[M];
+#pragma unroll
+          for (int b = 0; b < M; ++b) {
+            float s = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) s += Lt[f * NT + j] * up[j][b];
+            duo[b] = s;
+          }
+          const float2 u01 = make_float2(duo[0], duo[1]), u23 = make_float2(duo[2], duo[3]);
+          const int pt = kf * NFQ + f;
+          float dH[M];
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            const float* hm = &Hm[(pt * M + a) * M];
+            const float2 t = __ffma2_rn(ld2(hm + 2), u23, __fmul2_rn(ld2(hm), u01));
+            dH[a] = t.x + t.y;
+          }
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const float wl = fw[f] * Lt[f * NT + j];
+#pragma unroll
+            for (int a = 0; a < M; ++a) add[j][a] += wl * dH[a];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const int node = Dd::face_node(kf, j);
+#pragma unroll
+          for (int a = 0; a < M; ++a) A[(node * M + a) * k + c] += add[j][a];
+        }
+      }
+    }
+    __syncwarp();
+  }
+
   // Curved geometry derivatives along a direction dx of the six nodes (12 values):
   // dJ at volume point q gives the cofactor change dcof (4), the tangent change at
   // face point pt the scaled-normal change dnt (2); both are linear in dx.
@@ -1181,6 +1430,12 @@ struct ElemCore {
   // (DIM M x ku) in W, then every lane updates its own flattened (row, c) entries;
   // per face point it stages the trace directions dU+/dU- and dH = Hp dU+ + Hm dU-.
   __device__ void jac_state(int lane, const signed char* bcs, int ku, int k) {
+    if constexpr (sizeof(T) == 4 && kStateRowsF32(M, NB)) {
+      // FP32 Euler with p <= 2 (issue-bound): the rows of dR_e/dU_e in registers,
+      // then their products with Phi_e, and the neighbour traces by columns
+      jac_state_rows_f2(lane, bcs, ku, k);
+      return;
+    }
     if constexpr (sizeof(T) == 4) {
       // FP32 (issue-bound): one lane per column of Phi_e, the whole derivative of R_e
       // along it by Jacobian-vector products with no index arithmetic and no staging
@@ -1511,6 +1766,23 @@ struct ElemCore {
       // the mesh-direction differences, once per column (FP64 differences of the
       // vertex rows of Psi, then one conversion each)
       for (int c = lane; c < kx; c += 32) {
+        if constexpr (sizeof(T) == 4) {
+          if (g32) {
+            // the column's edge differences from the FP32 edge table: (dj00, dj10, dj01, dj11)
+            const float4 d = reinterpret_cast<const float4*>(Psie)[1 + c];
+            dcof[c * 4 + 0] = d.w;
+            dcof[c * 4 + 1] = -d.y;
+            dcof[c * 4 + 2] = -d.z;
+            dcof[c * 4 + 3] = d.x;
+            dnt[(0 * kx + c) * 2 + 0] = d.y;
+            dnt[(0 * kx + c) * 2 + 1] = -d.x;
+            dnt[(1 * kx + c) * 2 + 0] = d.w - d.y;
+            dnt[(1 * kx + c) * 2 + 1] = -(d.z - d.x);
+            dnt[(2 * kx + c) * 2 + 0] = -d.w;
+            dnt[(2 * kx + c) * 2 + 1] = d.z;
+            continue;
+          }
+        }
         const double* d = &Psie[c];  // column c, stride kx
         const T dj00 = (T)(d[2 * kx] - d[0]), dj01 = (T)(d[4 * kx] - d[0]);
         const T dj10 = (T)(d[3 * kx] - d[1 * kx]), dj11 = (T)(d[5 * kx] - d[1 * kx]);
@@ -1639,7 +1911,7 @@ struct ElemCore {
 // Stage the shared reference tables (converted to T) and the evaluation point.
 template <class T, int PROB, int P>
 __device__ inline void stage_cta(const AsmArgs<T>& a, unsigned char* smem, const double* w, const double* tau,
-                                 T*& tab, T*& wT, double*& tauD) {
+                                 T*& tab, T*& wT, double*& tauD, float** tauF = nullptr) {
   using TB = Tabs<T, PROB, P>;
   using Dd = Disc<PROB, P>;
   tab = (T*)smem;
@@ -1658,6 +1930,9 @@ __device__ inline void stage_cta(const AsmArgs<T>& a, unsigned char* smem, const
   }
   for (int i = threadIdx.x; i < a.ku; i += blockDim.x) wT[i] = (T)w[i];
   for (int i = threadIdx.x; i < a.kx; i += blockDim.x) tauD[i] = tau[i];
+  float* tf = (float*)((unsigned char*)tauD + align16((size_t)(a.kx > 0 ? a.kx : 1) * 8));
+  for (int i = threadIdx.x; i < a.kx; i += blockDim.x) tf[i] = (float)tau[i];
+  if (tauF) *tauF = tf;
 }
 
 template <class T, int PROB, int P, bool JAC>
@@ -1682,20 +1957,31 @@ template <class T, int PROB, int P, bool JAC>
 __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e,
                                               const T* wT, const double* tauD, const double* mu, int lane,
                                               signed char* bcs, bool face_jac = true, bool vol_jac = true,
-                                              int step = 32) {
+                                              int step = 32, const float* tauF = nullptr) {
   using Dd = Disc<PROB, P>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
                 NT = Dd::NTRACE, NV = Dd::NV;
   const int ku = a.ku, kx = a.kx;
   const bool need_hn = JAC && (kx > 0 || a.need_hn) && face_jac;
     const int* vv = &a.ev[(long)e * NV];
-    // 1. gather: Phi_e and Psi_e by asynchronous copies (all in flight at once),
-    // overlapped with the neighbour offsets
+    // FP32 straight-sided elements without the distortion term take their geometry
+    // from the FP32 edge table (no FP64 arithmetic in the element pass)
+    bool g32 = false;
+    if constexpr (sizeof(T) == 4 && !Dd::CURVED && DIM == 2)
+      g32 = tauF != nullptr && a.geo32 != nullptr && a.kappa == 0.0;
+    C.g32 = g32;
+    // 1. gather: Phi_e and Psi_e (or the element's edge-table rows) by asynchronous
+    // copies (all in flight at once), overlapped with the neighbour offsets
     warp_copy_async(C.Phie, a.Phi + (size_t)e * NU * ku, NU * ku, lane, step);
-    for (int i = lane; i < NXE * kx; i += step) {
-      const int r = C.dkx.div(i), c = i - r * kx;
-      const int v = r / DIM, d = r - v * DIM;
-      cp_async8(&C.Psie[i], &a.Psi[((size_t)vv[v] * DIM + d) * kx + c]);
+    if (g32) {
+      const float4* src = a.geo32 + (size_t)e * (1 + kx);
+      for (int i = lane; i < 1 + kx; i += step) cp_async16(reinterpret_cast<float4*>(C.Psie) + i, src + i);
+    } else {
+      for (int i = lane; i < NXE * kx; i += step) {
+        const int r = C.dkx.div(i), c = i - r * kx;
+        const int v = r / DIM, d = r - v * DIM;
+        cp_async8(&C.Psie[i], &a.Psi[((size_t)vv[v] * DIM + d) * kx + c]);
+      }
     }
     for (int t = lane; t < NF * NT; t += step) {
       const int kf = t / NT, j = t - kf * NT;
@@ -1730,7 +2016,7 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
         C.Up[r] = s;
       }
     }
-    for (int t = lane; t < NXE; t += step) {
+    for (int t = g32 ? NXE : lane; t < NXE; t += step) {
       const int v = t / DIM, d = t - v * DIM;
       double s = a.X[(size_t)vv[v] * DIM + d];
       for (int c = 0; c < kx; ++c) s += C.Psie[t * kx + c] * tauD[c];
@@ -1742,6 +2028,8 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
     if constexpr (Dd::CURVED) {
       bad = !C.geometry_curved(lane, step);
       __syncwarp();
+    } else if constexpr (sizeof(T) == 4 && DIM == 2) {
+      bad = g32 ? !C.geometry32(tauF, kx) : !C.geometry();
     } else {
       bad = !C.geometry();
     }
@@ -1761,13 +2049,13 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 template <class T, int PROB, int P, bool JAC, bool TC = false>
 __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
                                              const T* wT, const double* tauD, const double* mu,
-                                             const unsigned char* pairs, int lane) {
+                                             const unsigned char* pairs, int lane, const float* tauF = nullptr) {
   using Dd = Disc<PROB, P>;
   constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
   const int ku = a.ku, kx = a.kx, k = ku + kx;
     const int* vv = &a.ev[(long)e * NV];
     signed char bcs[NF];
-    bool bad = element_front<T, PROB, P, JAC>(C, a, e, wT, tauD, mu, lane, bcs);
+    bool bad = element_front<T, PROB, P, JAC>(C, a, e, wT, tauD, mu, lane, bcs, true, true, 32, tauF);
     // distortion
     const bool dist = a.kappa != 0.0;
     if (dist && lane == 0) {
@@ -2028,8 +2316,15 @@ __device__ inline int acc_source(int i, int k) {
 // for one query: a grid-stride loop of warps over the items; one FP64 partial per CTA.
 // The FP32 Jacobian form is capped at 168 registers (3 CTAs of 128 threads, 6 of
 // the 64-thread CTAs it runs with); its small spill costs less than lost warps.
+// Register cap of the FP32 Jacobian assembly (blocks of 128 threads per SM): 128
+// registers where the element's state fits in them without spilling and its
+// shared memory lets 16 warps reside (straight-sided p <= 2); 168 elsewhere
+// (curved elements spill at 128; at p = 3 shared memory holds 6 warps anyway).
+constexpr int kFp32JacMinBlocks(int prob, int p) { return (prob == PROB_EULER_Q2 || p > 2) ? 3 : 4; }
+
 template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? 3 : 0) assemble_kernel(AsmArgs<T> a) {
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? kFp32JacMinBlocks(PROB, P) : 0)
+    assemble_kernel(AsmArgs<T> a) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip != nullptr && *(volatile const int*)a.skip) return;
@@ -2037,20 +2332,21 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? 3 : 0) assemble
   const int ku = a.ku, kx = a.kx, k = ku + kx;
   T *tab, *wT;
   double* tauD;
-  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD);
-  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  float* tauF;
+  stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT, tauD, &tauF);
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD, !GRAD>;
   constexpr int PW = Lay::PER_WARP;  // 2: two elements per warp, one per half-warp
   const int half = PW == 2 ? (lane >> 4) : 0, sub = PW == 2 ? (lane & 15) : lane, step = 32 / PW;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
   const size_t eb = Lay(ku, kx).bytes;  // one element's region; a warp holds PW of them
   Core C;
-  C.template carve<GRAD>(smem + cb + (warp * PW + half) * eb, ku, kx);
+  C.template carve<GRAD, !GRAD>(smem + cb + (warp * PW + half) * eb, ku, kx);
   bind_tables(C, tab);
   const int nacc = k * k + k + 2;  // entries of a partial row (full H)
   const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
   for (int i = sub; i < nzero; i += step) C.acc[i] = T(0);
   unsigned char* pairs = smem + cb + nw * PW * eb;
-  if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
+  if (needs_pair_table<T>(JAC, GRAD, true, k) && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   if constexpr (PW == 2) {
     // both halves take the same number of trips; a half without an element of its
@@ -2068,7 +2364,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? 3 : 0) assemble
       const int e = a.elems ? a.elems[it] : (int)it;
       const double rho = a.rho ? a.rho[it] : 1.0;
       if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, lane);
-      else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane);
+      else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane, tauF);
     }
   }
   __syncthreads();
@@ -2110,7 +2406,7 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
   T *tab, *wT_unused;
   double* tau_unused;
   stage_cta<T, PROB, P>(a, smem, a.w, a.tau, tab, wT_unused, tau_unused);
-  using Lay = WarpLayout<T, PROB, P, JAC, GRAD>;
+  using Lay = WarpLayout<T, PROB, P, JAC, GRAD, !GRAD>;
   constexpr int PW = Lay::PER_WARP;  // 2: two elements per warp, one per half-warp
   const int half = PW == 2 ? (lane >> 4) : 0, sub = PW == 2 ? (lane & 15) : lane, step = 32 / PW;
   const size_t cb = cta_bytes<T, PROB, P>(ku, kx);
@@ -2118,21 +2414,25 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
   Lay L(ku, kx);
   unsigned char* wbase = smem + cb + (warp * PW + half) * eb;
   Core C;
-  C.template carve<GRAD>(wbase, ku, kx);
+  C.template carve<GRAD, !GRAD>(wbase, ku, kx);
   bind_tables(C, tab);
   T* wq = (T*)(wbase + L.owq);
   double* tq = (double*)(wbase + L.otq);
+  float* tqf = (float*)(wbase + L.otqf);
   const int nacc = k * k + k + 2;
   const int nzero = Lay::SLIM ? k + 2 : acc_count(k);
   unsigned char* pairs = smem + cb + nw * PW * eb;
-  if (JAC && !GRAD && threadIdx.x == 0) build_pairs(pairs, k);
+  if (needs_pair_table<T>(JAC, GRAD, true, k) && threadIdx.x == 0) build_pairs(pairs, k);
   __syncthreads();
   for (int ch = blockIdx.x * nw + warp; ch < b.n_chunks; ch += gridDim.x * nw) {
     const int q = b.chunk_query[ch];
     if (b.done != nullptr && *(volatile const int*)(b.done + (long)q * b.donestride)) continue;
     const double* wsrc = b.w + (long)q * b.wstride;
     for (int i = sub; i < ku; i += step) wq[i] = (T)wsrc[i];
-    for (int i = sub; i < kx; i += step) tq[i] = wsrc[ku + i];
+    for (int i = sub; i < kx; i += step) {
+      tq[i] = wsrc[ku + i];
+      tqf[i] = (float)wsrc[ku + i];
+    }
     for (int i = sub; i < nzero; i += step) C.acc[i] = T(0);
     __syncwarp();
     const double* muq = b.mu + (long)q * b.mustride;
@@ -2151,7 +2451,7 @@ __global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, Bat
 #pragma unroll 1
       for (int it = b.chunk_start[ch]; it < b.chunk_start[ch + 1]; ++it) {
         if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, a.elems[it], a.rho[it], wq, tq, muq, lane);
-        else element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane);
+        else element_pass<T, PROB, P, JAC, TC>(C, a, a.elems[it], a.rho[it], wq, tq, muq, pairs, lane, tqf);
       }
     }
     __syncwarp();

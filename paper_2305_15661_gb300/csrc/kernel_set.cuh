@@ -51,6 +51,10 @@ struct KernelSetImpl {
     return jac ? assemble_smem_bytes<T, PROB, P, true>(ku, kx, warps)
                : assemble_smem_bytes<T, PROB, P, false>(ku, kx, warps);
   }
+  static size_t smem_bytes_fused(bool jac, int ku, int kx, int warps) {
+    return jac ? assemble_smem_bytes<T, PROB, P, true, false, true>(ku, kx, warps)
+               : assemble_smem_bytes<T, PROB, P, false, false, true>(ku, kx, warps);
+  }
   static cudaError_t prepare(bool jac, size_t smem) {
     if (jac) {
       cudaError_t e = raise_smem(assemble_kernel<T, PROB, P, true>, smem);
@@ -274,6 +278,7 @@ struct KernelSetImpl {
     k.valid = true;
     k.assemble = &assemble;
     k.smem_bytes = &smem_bytes;
+    k.smem_bytes_fused = &smem_bytes_fused;
     k.prepare = &prepare;
     k.blocks_per_sm = &blocks_per_sm;
     k.inspect = &inspect;

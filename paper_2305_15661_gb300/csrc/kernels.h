@@ -11,7 +11,11 @@ struct KernelSet {
   // launch the fused assembly (jac = true) or the objective-only pass (jac = false);
   // args points to an AsmArgs<T> of the set's precision
   cudaError_t (*assemble)(const void* args, bool jac, int grid, int block, size_t smem, cudaStream_t s) = nullptr;
+  // dynamic shared memory: smem_bytes for the kernels that share the element layout
+  // (inspection, per-element gradients, norms, alignment), smem_bytes_fused for the
+  // fused assembly kernels (assemble and assemble_batched), whose FP32 layout is smaller
   size_t (*smem_bytes)(bool jac, int ku, int kx, int warps) = nullptr;
+  size_t (*smem_bytes_fused)(bool jac, int ku, int kx, int warps) = nullptr;
   cudaError_t (*prepare)(bool jac, size_t smem) = nullptr;
   int (*blocks_per_sm)(bool jac, int block, size_t smem) = nullptr;
   cudaError_t (*inspect)(const void* args, const double* U, const double* x, double* R, double* J, double* N,

@@ -378,6 +378,25 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
   }
 }
 
+// The FP32 edge table of straight-sided triangles: per element e, 1 + kx groups of
+// four floats, first the reference edges (x_1 - x_0, x_2 - x_0) as (e1x, e1y, e2x, e2y),
+// then for each mesh column c the same differences of its vertex rows of Psi. The
+// differences are taken in FP64 and rounded once, so the FP32 element pass forms
+// the current edges (reference + sum_c tau_c column differences) without FP64 work.
+__global__ void geo32_kernel(const double* X, const int* ev, const double* Psi, int kx, long n_elems, float4* out) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n_elems; e += (long)gridDim.x * blockDim.x) {
+    const long v0 = ev[e * 3], v1 = ev[e * 3 + 1], v2 = ev[e * 3 + 2];
+    float4* o = out + e * (1 + kx);
+    o[0] = make_float4((float)(X[v1 * 2] - X[v0 * 2]), (float)(X[v1 * 2 + 1] - X[v0 * 2 + 1]),
+                       (float)(X[v2 * 2] - X[v0 * 2]), (float)(X[v2 * 2 + 1] - X[v0 * 2 + 1]));
+    for (int c = 0; c < kx; ++c)
+      o[1 + c] = make_float4((float)(Psi[(v1 * 2) * kx + c] - Psi[(v0 * 2) * kx + c]),
+                             (float)(Psi[(v1 * 2 + 1) * kx + c] - Psi[(v0 * 2 + 1) * kx + c]),
+                             (float)(Psi[(v2 * 2) * kx + c] - Psi[(v0 * 2) * kx + c]),
+                             (float)(Psi[(v2 * 2 + 1) * kx + c] - Psi[(v0 * 2 + 1) * kx + c]));
+  }
+}
+
 // colsum[a][c] = sum over the rows r of Phi with r mod m = a of Phi[r][c] (one block per column).
 __global__ void phi_colsum_kernel(const double* Phi, long Nu, int ku, int m, double* colsum) {
   __shared__ double red[4][256];

@@ -179,6 +179,19 @@ def test_fp32_small_assembly_tolerances():
     assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
 
 
+@pytest.mark.parametrize("p,ku,kx", [(2, 16, 4), (2, 20, 4), (2, 4, 4), (2, 10, 3), (2, 13, 3), (3, 12, 4),
+                                     (3, 9, 2), (1, 8, 4)])
+def test_fp32_reduced_assembly_shapes(p, ku, kx):
+    # the FP32 state columns of p = 2 take eight- and four-column blocks when k_u and
+    # k are multiples of four and single columns otherwise; p = 3 and p = 1 take the
+    # per-column products
+    wl = W.euler_workload(n=6, p=p, k_u=ku, k_x=kx, seed=40 + ku)
+    g, r, _ = _assembly_pair(wl, precision=ift.FP32)
+    assert _fro(g["H"], r["H"]) < 1e-5
+    assert _fro(np.concatenate([g["S"], g["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-3
+    assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
+
+
 def test_assembly_is_deterministic():
     wl = W.euler_workload(n=20, p=2, k_u=10, k_x=4, seed=8)
     ctx = ift.Context.from_workload(wl)
