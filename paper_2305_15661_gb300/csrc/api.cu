@@ -369,7 +369,7 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "element kernel launch");
   const int nacc = c->nacc();
-  reduce_partials_kernel<<<(nacc + 31) / 32, 256, 0, s>>>(c->d_partial, grid, nacc, out, skip);
+  reduce_partials_kernel<<<(nacc + 31) / 32, 1024, 0, s>>>(c->d_partial, grid, nacc, out, skip);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "reduce launch");
   return IFT_OK;
@@ -389,7 +389,7 @@ ift_status launch_grad(ift_ctx* c, const double* w, const double* tau, const dou
   AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
   cudaError_t e = ks.assemble_grad(&a, grid, 32 * c->wpc[0], c->plan_smem_grad, s);
   if (e != cudaSuccess) return c->cuda_fail(e, "gradient pass launch");
-  reduce_partials_kernel<<<(k + 2 + 31) / 32, 256, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres, skip);
+  reduce_partials_kernel<<<(k + 2 + 31) / 32, 1024, 0, s>>>(c->d_partial, grid, k + 2, c->d_gres, skip);
   merge_grad_kernel<<<1, 64, 0, s>>>(c->d_gres, k, c->nacc(), out, states);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "gradient reduce launch");
@@ -2057,7 +2057,7 @@ ift_status align_form(ift_ctx* c, AlignWork& W, double& J, cudaStream_t s) {
   CK(cudaMemsetAsync(W.nbad, 0, 8, s), "zero count");
   CK(ks.align_jac(&a, c->d_X, W.M, W.ge, W.F, W.nbad, W.hpart, W.jwarps, W.jgrid, s), "alignment Jacobian pass");
   const int nh = W.ku * (W.ku + 1) / 2;
-  reduce_partials_kernel<<<(nh + 31) / 32, 256, 0, s>>>(W.hpart, W.jgrid, nh, W.H, nullptr);
+  reduce_partials_kernel<<<(nh + 31) / 32, 1024, 0, s>>>(W.hpart, W.jgrid, nh, W.H, nullptr);
   CK(cudaGetLastError(), "H_ww");
   J = 0.5 * align_dot(W, W.F, W.F, W.Nu + W.Ne, s);
   double nb = 0.0;

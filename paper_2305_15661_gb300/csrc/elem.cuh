@@ -257,6 +257,31 @@ __host__ __device__ constexpr bool kExplicitVolume(int nu, int word) { return wo
 // Entries of Jv per register pass (9 doubles per lane).
 constexpr int kJvPass = 288;
 
+// Four consecutive entries at a 16-byte aligned shared-memory address: one vector
+// store in FP32 (a warp's scalar stores to per-point rows conflict on the banks;
+// the vector form moves four words per bank pass), four stores in FP64.
+template <class T>
+__device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  } else {
+    p[0] = a;
+    p[1] = b;
+    p[2] = c;
+    p[3] = d;
+  }
+}
+
+// Per-volume-point stride of the contravariant flux Jacobians Ahat_qr (the DIM M x M
+// blocks of point q start at q * stride). FP32 Euler pads it by four floats: the
+// lanes of step 4 each write their own point's 32 entries, and with a stride of 32
+// words all of them hit the same bank (16-way conflicts); 36 words leaves at most
+// two lanes per bank and keeps every row 16-byte aligned. FP64 keeps the dense
+// stride (its shared memory is the tighter limit there).
+__host__ __device__ constexpr int ah_stride(int m, int dim, int word) {
+  return (word == 4 && m == 4) ? dim * m * m + 4 : dim * m * m;
+}
+
 // FP32 Euler state columns by rows of dR_e/dU_e in registers (jac_state_rows_f2):
 // an even node count (packed pairs) and at most one row per lane (p <= 2); p = 3
 // (40 rows) takes the per-column products, which measured faster there.
@@ -303,7 +328,7 @@ struct WarpLayout {
     oUp = put(NUP, sizeof(T));
     oFh = put(NQ * DIM * M, sizeof(T));
     ofph = put(NQ * DIM * M, sizeof(T));
-    oAh = put(JAC ? (SLIM ? NQ * M : NQ * DIM * M * M) : 1, sizeof(T));
+    oAh = put(JAC ? (SLIM ? NQ * M : NQ * ah_stride(M, DIM, sizeof(T))) : 1, sizeof(T));
     osq = put(NQ, sizeof(T));
     oHf = put(NF * NFQ * M, sizeof(T));
     // curved elements: the cofactor at every volume point and the scaled normal at every face point
@@ -393,6 +418,7 @@ struct ElemCore {
   using Dd = Disc<PROB, P>;
   static constexpr int M = Dd::M, DIM = Dd::DIM, NB = Dd::NB, NQ = Dd::NQ, NU = Dd::NU, NUP = Dd::NUP,
                        NXE = Dd::NXE, NF = Dd::NFACE, NFQ = Dd::NFQ, NT = Dd::NTRACE;
+  static constexpr int AQ = ah_stride(M, DIM, sizeof(T));  // point stride of Ah
   // shared tables (GdV, GtF: curved geometry shape-function derivatives)
   const T *D, *B, *Lt, *fw, *qw, *qxi, *GdV, *GtF;
   const T* Cf;  // fw[f] Lt[f][i] Lt[f][j]: the face blocks of dR_e/dU_e
@@ -579,12 +605,14 @@ struct ElemCore {
         T fx[4], fy[4], Pq;
         euler_flux(U, g1, fx, fy, Pq);
         if (!(U[0] > T(0)) || !(Pq > T(0))) bad = true;
+        st4(&fph[(q * 2 + 0) * 4], fx[0], fx[1], fx[2], fx[3]);
+        st4(&fph[(q * 2 + 1) * 4], fy[0], fy[1], fy[2], fy[3]);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          fph[(q * 2 + 0) * 4 + a] = fx[a];
-          fph[(q * 2 + 1) * 4 + a] = fy[a];
+        for (int r = 0; r < 2; ++r) {
+          T fr[4];
 #pragma unroll
-          for (int r = 0; r < 2; ++r) Fh[(q * 2 + r) * 4 + a] = fx[a] * cofv(q, 0 * 2 + r) + fy[a] * cofv(q, 1 * 2 + r);
+          for (int a = 0; a < 4; ++a) fr[a] = fx[a] * cofv(q, 0 * 2 + r) + fy[a] * cofv(q, 1 * 2 + r);
+          st4(&Fh[(q * 2 + r) * 4], fr[0], fr[1], fr[2], fr[3]);
         }
         if (JAC && vol_jac) {
           T Ax[16], Ay[16];
@@ -592,10 +620,14 @@ struct ElemCore {
 #pragma unroll
           for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int ab = 0; ab < 16; ++ab) Ah[(q * 2 + r) * 16 + ab] = Ax[ab] * cofv(q, r) + Ay[ab] * cofv(q, 2 + r);
-        } else if (JAC) {
+            for (int a = 0; a < 4; ++a) {
+              T v[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) Ah[q * 4 + a] = U[a];
+              for (int b = 0; b < 4; ++b) v[b] = Ax[a * 4 + b] * cofv(q, r) + Ay[a * 4 + b] * cofv(q, 2 + r);
+              st4(&Ah[q * AQ + r * 16 + a * 4], v[0], v[1], v[2], v[3]);
+            }
+        } else if (JAC) {
+          st4(&Ah[q * 4], U[0], U[1], U[2], U[3]);
         }
       } else {
         T f = T(0.5) * U[0] * U[0];
@@ -641,18 +673,14 @@ struct ElemCore {
           const T Pi = Uin[3] * Uin[0] - T(0.5) * (Uin[1] * Uin[1] + Uin[2] * Uin[2]);
           const T Po = Uout[3] * Uout[0] - T(0.5) * (Uout[1] * Uout[1] + Uout[2] * Uout[2]);
           if (!(Uin[0] > T(0)) || !(Pi > T(0)) || !(Uout[0] > T(0)) || !(Po > T(0))) bad = true;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            Ui[pt * 4 + a] = Uin[a];
-            Uo[pt * 4 + a] = Uout[a];
-          }
+          st4(&Ui[pt * 4], Uin[0], Uin[1], Uin[2], Uin[3]);
+          st4(&Uo[pt * 4], Uout[0], Uout[1], Uout[2], Uout[3]);
         }
         if (!fj) {
           T n2[2] = {ntv(pt, k, 0), ntv(pt, k, 1)};
           T H[4];
           euler_roe<T, T, T>(Uin, Uout, n2, g1, H);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) hf[a] = H[a];
+          st4(hf, H[0], H[1], H[2], H[3]);
         } else {
           // group 0: dH/dU+ with U+ as the dual side; group 1: dH/dU- from the same
           // code on the swapped states and reversed normal (H(U+, U-; n) = -H(U-, U+; -n)),
@@ -670,12 +698,9 @@ struct ElemCore {
           const T n2[2] = {sg * ntv(pt, k, 0), sg * ntv(pt, k, 1)};
           euler_roe<Dual<T, 4>, T, T>(dA, B, n2, g1, H);
           T* dst = sw ? &Hm[pt * 16] : &Hp[pt * 16];
+          if (!sw) st4(hf, H[0].v, H[1].v, H[2].v, H[3].v);
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (!sw) hf[a] = H[a].v;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) dst[a * 4 + b] = sg * H[a].d[b];
-          }
+          for (int a = 0; a < 4; ++a) st4(&dst[a * 4], sg * H[a].d[0], sg * H[a].d[1], sg * H[a].d[2], sg * H[a].d[3]);
         }
       } else {
         // Burgers: inflow u- = 1 on the face with normal -x, outflow u- = u+
@@ -754,7 +779,7 @@ struct ElemCore {
 #pragma unroll
           for (int r = 0; r < DIM; ++r)
 #pragma unroll
-            for (int a = 0; a < M; ++a) v += Ah[((q * DIM + r) * M + a) * M + b] * sr[r][a];
+            for (int a = 0; a < M; ++a) v += Ah[q * AQ + (r * M + a) * M + b] * sr[r][a];
           tq[q * M + b] = v;
         }
       } else {
@@ -985,7 +1010,7 @@ struct ElemCore {
         for (int a = 0; a < M; ++a) {
           T dF = T(0);
 #pragma unroll
-          for (int b = 0; b < M; ++b) dF += Ah[((q * DIM + r) * M + a) * M + b] * du[b];
+          for (int b = 0; b < M; ++b) dF += Ah[q * AQ + (r * M + a) * M + b] * du[b];
 #pragma unroll
           for (int i = 0; i < NB; ++i) dR[i * M + a] -= D[(r * NQ + q) * NB + i] * dF;
         }
@@ -1056,7 +1081,7 @@ struct ElemCore {
         float dFn[M];  // minus the flux change: the volume term enters R_e with a minus sign
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-          const float* ah = &Ah[((q * DIM + r) * M + a) * M];
+          const float* ah = &Ah[q * AQ + (r * M + a) * M];
           const float2 t = __ffma2_rn(ld2(ah + 2), du23, __fmul2_rn(ld2(ah), du01));
           dFn[a] = -t.x - t.y;
         }
@@ -1144,8 +1169,8 @@ struct ElemCore {
       for (int q = 0; q < NQ; ++q) {
         // t[b] = -sum_r D_r[q][i] Ahat_qr[a][b] (the volume term enters R_e with a minus sign)
         const float d0 = -D[q * NB + i], d1 = -D[(NQ + q) * NB + i];
-        const float4 a0 = ld4(&Ah[((q * DIM + 0) * M + a) * M]);
-        const float4 a1 = ld4(&Ah[((q * DIM + 1) * M + a) * M]);
+        const float4 a0 = ld4(&Ah[q * AQ + (0 * M + a) * M]);
+        const float4 a1 = ld4(&Ah[q * AQ + (1 * M + a) * M]);
         const float2 dd0 = make_float2(d0, d0), dd1 = make_float2(d1, d1);
         const float2 t01 = __ffma2_rn(dd1, make_float2(a1.x, a1.y), __fmul2_rn(dd0, make_float2(a0.x, a0.y)));
         const float2 t23 = __ffma2_rn(dd1, make_float2(a1.z, a1.w), __fmul2_rn(dd0, make_float2(a0.z, a0.w)));
@@ -1477,7 +1502,7 @@ struct ElemCore {
             const int row = r0 + rl, i = row / M, a = row - i * M;
             T s = T(0);
 #pragma unroll
-            for (int r = 0; r < DIM; ++r) s += D[(r * NQ + q) * NB + i] * Ah[((q * DIM + r) * M + a) * M + b];
+            for (int r = 0; r < DIM; ++r) s += D[(r * NQ + q) * NB + i] * Ah[q * AQ + (r * M + a) * M + b];
             Tq[e] = s;
           }
           __syncwarp();
@@ -1560,7 +1585,7 @@ struct ElemCore {
       __syncwarp();
       for (int e = lane; e < DIM * M * ku; e += 32) {
         const int ra = dku.div(e), c = e - ra * ku;
-        const T* ah = &Ah[(q * DIM * M + ra) * M];
+        const T* ah = &Ah[q * AQ + ra * M];
         T s = T(0);
 #pragma unroll
         for (int b = 0; b < M; ++b) s += ah[b] * G[b * ku + c];
@@ -2398,7 +2423,8 @@ struct BatchArgs {
 };
 
 template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
-__global__ void __launch_bounds__(128) assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? kFp32JacMinBlocks(PROB, P) : 0)
+    assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

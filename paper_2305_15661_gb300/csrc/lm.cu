@@ -475,26 +475,36 @@ __global__ void residual_norms_finish_kernel(const double* part, int B, int nchu
   norms[q] = sqrt(s);
 }
 
-// Block b sums columns [32 b, 32 b + 32) of the partials: its 8 warps each sum one
-// contiguous eighth of the rows (coalesced 32-column reads), then the eight
-// segment sums are added in segment order (the order is fixed for a launch shape).
+// Block b sums columns [32 b, 32 b + 32) of the partials: each of its warps (up to
+// 32) sums one contiguous segment of the rows (coalesced 32-column reads, eight rows
+// in flight per lane), then warp 0 adds the segment sums in segment order (the
+// order is fixed for a launch shape).
 // skip (optional): a device flag; when non-zero the block returns at once and out is
 // left as it is (a finished solve, or an evaluation that keeps H).
-__global__ void reduce_partials_kernel(const double* partial, int nparts, int nacc, double* out, const int* skip) {
+__global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* partial, int nparts, int nacc,
+                                                              double* out, const int* skip) {
   if (skip != nullptr && *skip) return;
-  __shared__ double seg[8][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double seg[32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i = blockIdx.x * 32 + lane;
-  const int per = (nparts + 7) / 8, c0 = w * per, c1 = min(nparts, c0 + per);
+  const int per = (nparts + nw - 1) / nw, c0 = w * per, c1 = min(nparts, c0 + per);
   double s = 0.0;
-  if (i < nacc)
-    for (int c = c0; c < c1; ++c) s += partial[(size_t)c * nacc + i];
+  if (i < nacc) {
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = partial[(size_t)(c + u) * nacc + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; c < c1; ++c) s += partial[(size_t)c * nacc + i];
+  }
   seg[w][lane] = s;
   __syncthreads();
   if (w == 0 && i < nacc) {
     double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) t += seg[k][lane];
+    for (int k = 0; k < nw; ++k) t += seg[k][lane];
     out[i] = t;
   }
 }
