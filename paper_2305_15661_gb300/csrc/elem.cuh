@@ -145,11 +145,11 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const 
 }
 
 template <int NU, bool SPLIT>
-__device__ __forceinline__ void syrk_upper_tf32(const float* A, int k, float* acc, float rho, int lane) {
+__device__ __forceinline__ void syrk_upper_tf32(const float* A, int k, int ka, float* acc, float rho, int lane) {
   const int g = lane >> 2, t = lane & 3;
   constexpr int KS = (NU + 7) / 8;
   const int mtiles = (k + 15) / 16, ntiles = (k + 7) / 8;
-  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * k + col] : 0.0f; };
+  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * ka + col] : 0.0f; };
   for (int mt = 0; mt < mtiles; ++mt) {
     const int r0 = mt * 16 + g, r1 = r0 + 8;
     for (int nt = 2 * mt; nt < ntiles; ++nt) {
@@ -204,11 +204,11 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
 }
 
 template <int NU>
-__device__ __forceinline__ void syrk_upper_bf16(const float* A, int k, float* acc, float rho, int lane) {
+__device__ __forceinline__ void syrk_upper_bf16(const float* A, int k, int ka, float* acc, float rho, int lane) {
   const int g = lane >> 2, t = lane & 3;
   constexpr int KS = (NU + 15) / 16;
   const int mtiles = (k + 15) / 16, ntiles = (k + 7) / 8;
-  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * k + col] : 0.0f; };
+  auto ld = [&](int i, int col) { return (i < NU && col < k) ? A[i * ka + col] : 0.0f; };
   for (int mt = 0; mt < mtiles; ++mt) {
     const int r0 = mt * 16 + g, r1 = r0 + 8;
     for (int nt = 2 * mt; nt < ntiles; ++nt) {
@@ -271,6 +271,13 @@ __device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {
     p[3] = d;
   }
 }
+
+// Row stride of the element's Jacobian columns A (n_u x k, row-major). FP32 elements
+// with more rows than lanes (p = 3) pad each row by four floats: the tensor-core
+// fragments read A down its columns, eight rows apart per lane group, and with
+// k = 48 every such read hit one bank four times; k + 4 spreads them over the banks
+// and keeps rows 16-byte aligned. Elsewhere the padding would cost occupancy.
+__host__ __device__ constexpr int a_row_stride(int k, int nu, int word) { return (word == 4 && nu > 32) ? k + 4 : k; }
 
 // Per-volume-point stride of the contravariant flux Jacobians Ahat_qr (the DIM M x M
 // blocks of point q start at q * stride). FP32 Euler pads it by four floats: the
@@ -340,7 +347,7 @@ struct WarpLayout {
     oUi = put(NF * NFQ * M, sizeof(T));
     oUo = put(NF * NFQ * M, sizeof(T));
     oR = put(NU, sizeof(T));
-    oA = put(JAC && !SLIM ? (size_t)NU * k : 1, sizeof(T));
+    oA = put(JAC && !SLIM ? (size_t)NU * a_row_stride(k, NU, sizeof(T)) : 1, sizeof(T));
     odNt = put(kx + 1, sizeof(T));
     {
       // staging of the reduced-Jacobian passes: volume G (M ku) + F (DIM M ku), faces
@@ -436,6 +443,7 @@ struct ElemCore {
   const T* PhiG;     // Phi in global memory (neighbour trace rows)
   long long* poff;   // per face and trace position: row-block offset in PhiG, -1 on boundary faces
   FastDiv dku, dkx;  // division by k_u and k_x in the lane loops
+  int ka;            // row stride of A (a_row_stride)
 
   template <bool GRAD = false, bool FUSED = false>
   __device__ void carve(unsigned char* base, int ku, int kx) {
@@ -463,6 +471,7 @@ struct ElemCore {
     W = (T*)(base + L.oW);
     R = (T*)(base + L.oR);
     A = (T*)(base + L.oA);
+    ka = a_row_stride(ku + kx, NU, sizeof(T));
     dNt = (T*)(base + L.odNt);
     acc = (T*)(base + L.oacc);
     gacc = acc + L.gacc_offset(ku + kx);
@@ -1214,7 +1223,7 @@ struct ElemCore {
         }
       }
       // A[row][c] = J[row] . Phi_e[:, c]
-      float* arow = &A[row * k];
+      float* arow = &A[row * ka];
       int c0 = 0;
       if (vec) {
         for (; c0 + 8 <= ku; c0 += 8) {
@@ -1325,7 +1334,7 @@ struct ElemCore {
         for (int j = 0; j < NT; ++j) {
           const int node = Dd::face_node(kf, j);
 #pragma unroll
-          for (int a = 0; a < M; ++a) A[(node * M + a) * k + c] += add[j][a];
+          for (int a = 0; a < M; ++a) A[(node * M + a) * ka + c] += add[j][a];
         }
       }
     }
@@ -1475,7 +1484,7 @@ struct ElemCore {
         if constexpr (M == 4 && NB % 2 == 0) jvp_state_f2(fe, fp, bcs, dR);
         else jvp_state(fe, fp, bcs, dR);
 #pragma unroll
-        for (int i = 0; i < NU; ++i) A[i * k + c] = dR[i];
+        for (int i = 0; i < NU; ++i) A[i * ka + c] = dR[i];
       }
       __syncwarp();
       return;
@@ -1554,7 +1563,7 @@ struct ElemCore {
           T s = T(0);
 #pragma unroll
           for (int col = 0; col < NU; ++col) s += jr[col] * Phie[col * ku + c];
-          A[(r0 + rl) * k + c] = s;
+          A[(r0 + rl) * ka + c] = s;
         }
         __syncwarp();
       }
@@ -1569,7 +1578,7 @@ struct ElemCore {
   __device__ void jac_state_volume_jvp(int lane, int ku, int k) {
     for (int e = lane; e < NU * ku; e += 32) {
       const int row = dku.div(e), c = e - row * ku;
-      A[row * k + c] = T(0);
+      A[row * ka + c] = T(0);
     }
     T* G = W;
     T* F = W + M * ku;
@@ -1595,10 +1604,10 @@ struct ElemCore {
       for (int e = lane; e < NU * ku; e += 32) {
         const int row = dku.div(e), c = e - row * ku;
         const int i = row / M, a = row - i * M;
-        T s = A[row * k + c];
+        T s = A[row * ka + c];
 #pragma unroll
         for (int r = 0; r < DIM; ++r) s -= D[(r * NQ + q) * NB + i] * F[(r * M + a) * ku + c];
-        A[row * k + c] = s;
+        A[row * ka + c] = s;
       }
     }
   }
@@ -1654,7 +1663,7 @@ struct ElemCore {
         const int ja = dku.div(e), c = e - ja * ku;
         const int j = ja / M, a = ja - j * M;
         const int node = (kf == 0) ? Dd::face_node(0, j) : ((kf == 1) ? Dd::face_node(1, j) : Dd::face_node(2, j));
-        A[(node * M + a) * k + c] += Lt[f * NT + j] * dH[a * ku + c];
+        A[(node * M + a) * ka + c] += Lt[f * NT + j] * dH[a * ku + c];
       }
     }
     __syncwarp();
@@ -1707,7 +1716,7 @@ struct ElemCore {
 #pragma unroll
         for (int f = 0; f < NFQ; ++f) s += fw[f] * Lt[f * NT + j] * dHf[(((kf * NFQ + f) * kx) + c) * M + a];
       }
-      A[row * k + ku + c] = s;
+      A[row * ka + ku + c] = s;
     }
     if (dist) {
       for (int c = lane; c < kx; c += 32) {
@@ -1856,7 +1865,7 @@ struct ElemCore {
           const T* kk = &K[((kf * NT + j) * M + a) * 2];
           s += kk[0] * dn[0] + kk[1] * dn[1];
         }
-        A[row * k + ku + c] = s;
+        A[row * ka + ku + c] = s;
       }
     } else {
       const T mu0 = (T)mu[0];
@@ -1869,7 +1878,7 @@ struct ElemCore {
           const T dxq = dx0 + qxi[q] * ddet;
           s -= B[q * NB + i] * qw[q] * (mu0 * sq[q] * dxq * detJ + sq[q] * ddet);
         }
-        A[i * k + ku + c] = s;
+        A[i * ka + ku + c] = s;
       }
     }
     if (dist) {
@@ -2101,9 +2110,9 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       if constexpr (std::is_same<T, float>::value && TC) {
         {
           __syncwarp();
-          if (a.contraction == 3) syrk_upper_bf16<NU>(C.A, k, C.acc, rT, lane);
-          else if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.acc, rT, lane);
-          else syrk_upper_tf32<NU, false>(C.A, k, C.acc, rT, lane);
+          if (a.contraction == 3) syrk_upper_bf16<NU>(C.A, k, C.ka, C.acc, rT, lane);
+          else if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.ka, C.acc, rT, lane);
+          else syrk_upper_tf32<NU, false>(C.A, k, C.ka, C.acc, rT, lane);
           if (dist) {
             // distortion block of the mesh columns, Eq. levmarq-elem
             const int np = kx * (kx + 1) / 2;
@@ -2139,8 +2148,8 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
             for (int x = 0; x < 4; ++x) h2[x][0] = h2[x][1] = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int i = 0; i < NU; ++i) {
-              const float4 ar = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * R]);
-              const float4 bc = *reinterpret_cast<const float4*>(&C.A[i * k + 4 * Bc]);
+              const float4 ar = *reinterpret_cast<const float4*>(&C.A[i * C.ka + 4 * R]);
+              const float4 bc = *reinterpret_cast<const float4*>(&C.A[i * C.ka + 4 * Bc]);
               const float av[4] = {ar.x, ar.y, ar.z, ar.w};
               const float2 b01 = make_float2(bc.x, bc.y), b23 = make_float2(bc.z, bc.w);
 #pragma unroll
@@ -2177,14 +2186,14 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
         const int r = pairs[2 * pidx], b = pairs[2 * pidx + 1];
         T s = T(0);
 #pragma unroll
-        for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.A[i * k + b];
+        for (int i = 0; i < NU; ++i) s += C.A[i * C.ka + r] * C.A[i * C.ka + b];
         if (dist && r >= ku) s += C.dNt[r - ku] * C.dNt[b - ku];
         C.acc[pidx] += rT * s;  // pairs run over the upper triangle in accumulator order
       }
       for (int r = lane; r < k; r += 32) {
         T s = T(0);
 #pragma unroll
-        for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
+        for (int i = 0; i < NU; ++i) s += C.A[i * C.ka + r] * C.R[i];
         if (dist && r >= ku) s += C.dNt[r - ku] * Ne;
         C.acc[acc_tail(k) + r] += rT * s;
       }
@@ -2296,7 +2305,7 @@ __device__ __forceinline__ void element_grad_pass(ElemCore<T, PROB, P, true>& C,
       for (int c = lane; c < kx; c += 32) {
         T s = T(0);
 #pragma unroll
-        for (int i = 0; i < NU; ++i) s += C.A[i * k + ku + c] * C.R[i];
+        for (int i = 0; i < NU; ++i) s += C.A[i * C.ka + ku + c] * C.R[i];
         if (dist) s += C.dNt[c] * Ne;
         g[ku + c] += rT * s;
       }
@@ -2591,7 +2600,7 @@ __global__ void __launch_bounds__(128) element_gradients_kernel(AsmArgs<T> a, do
     for (int r = lane; r < k; r += 32) {
       T s = T(0);
 #pragma unroll
-      for (int i = 0; i < NU; ++i) s += C.A[i * k + r] * C.R[i];
+      for (int i = 0; i < NU; ++i) s += C.A[i * C.ka + r] * C.R[i];
       if (dist && r >= ku) s += C.dNt[r - ku] * Ne;
       row[r] = bad ? (double)NAN : (double)s;
     }
@@ -2854,13 +2863,13 @@ __global__ void __launch_bounds__(128) align_jac_kernel(AsmArgs<T> a, const doub
     auto dot = [&](int j, int c) {
       double m = 0.0;
 #pragma unroll 8
-      for (int i = 0; i < NU; ++i) m += (double)C.A[i * k + j] * (double)C.A[i * k + c];
+      for (int i = 0; i < NU; ++i) m += (double)C.A[i * C.ka + j] * (double)C.A[i * C.ka + c];
       return m;
     };
     for (int c = lane; c < k; c += 32) {
       const double dnc = c >= ku ? C.dN[c - ku] : 0.0;
       double gc = dnc * Ne;
-      for (int i = 0; i < NU; ++i) gc += (double)C.A[i * k + c] * (double)C.R[i];
+      for (int i = 0; i < NU; ++i) gc += (double)C.A[i * C.ka + c] * (double)C.R[i];
       gout[(size_t)e * k + c] = gc;
       if (c < ku) {
         // column c of H_ww (rows j <= c), the row c of (M_e)_wx
