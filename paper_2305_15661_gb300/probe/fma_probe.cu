@@ -81,7 +81,71 @@ int run_dmma(int blocks, int threads, int iters, double* flops_per_s) {
   return 0;
 }
 
+// Do the FP64 FMA pipe and the FP64 MMA path share hardware? Even warps run FMA
+// chains (iters_f), odd warps MMA chains (iters_m); mode 1 keeps only the FMA
+// warps working, mode 2 only the MMA warps, mode 0 both. If the two paths are
+// separate, the mode-0 time is near the larger of the other two; if they share
+// one unit, near their sum.
+__global__ void fp64_mixed_chains(double* out, int iters_f, int iters_m, int mode) {
+  const bool mma_warp = (threadIdx.x >> 5) & 1;
+  double r = 0.0;
+  if (!mma_warp && mode != 2) {
+    const double a = 0.999, b = 0.001;
+    double x0 = (double)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
+           x7 = x0 + 7;
+    for (int i = 0; i < iters_f; ++i) {
+      x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+      x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+    r = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  } else if (mma_warp && mode != 1) {
+    const double a = 1.0 + 1e-3 * (threadIdx.x & 31), b = 1e-3;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0, c4 = 0.0, c5 = 0.0, c6 = 0.0, c7 = 0.0;
+    for (int i = 0; i < iters_m; ++i) {
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c0), "+d"(c1) : "d"(a), "d"(b));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c2), "+d"(c3) : "d"(a), "d"(b));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c4), "+d"(c5) : "d"(a), "d"(b));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c6), "+d"(c7) : "d"(a), "d"(b));
+    }
+    r = c0 + c1 + c2 + c3 + c4 + c5 + c6 + c7;
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+int run_mixed(int mode, int blocks, int threads, int iters_f, int iters_m, double* ms_out) {
+  double* out = nullptr;
+  if (threads % 64 != 0) return 3;
+  if (cudaMalloc(&out, sizeof(double) * (size_t)blocks * threads) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_mixed_chains<<<blocks, threads>>>(out, iters_f / 10, iters_m / 10, mode);  // warm-up
+  cudaEventRecord(e0);
+  fp64_mixed_chains<<<blocks, threads>>>(out, iters_f, iters_m, mode);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return 2;
+  *ms_out = ms;
+  return 0;
+}
+
 }  // namespace
+
+// Time (ms) of the FP64 FMA / MMA sharing test above (mode 0 both, 1 FMA warps only,
+// 2 MMA warps only).
+extern "C" int fp64_pipe_probe(int mode, int blocks, int threads, int iters_f, int iters_m, double* ms) {
+  return run_mixed(mode, blocks, threads, iters_f, iters_m, ms);
+}
 
 // precision: 0 FP64 FMA, 1 FP32 FMA, 2 FP64 MMA (m8n8k4).
 extern "C" int fma_probe(int precision, int blocks, int threads, int iters, double* flops_per_s) {
