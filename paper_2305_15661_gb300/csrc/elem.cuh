@@ -2432,7 +2432,7 @@ struct BatchArgs {
 };
 
 template <class T, int PROB, int P, bool JAC, bool TC = false, bool GRAD = false>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? kFp32JacMinBlocks(PROB, P) : 0)
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC && PROB != PROB_EULER_Q2) ? kFp32JacMinBlocks(PROB, P) : 0)
     assemble_batched_kernel(AsmArgs<T> a, BatchArgs b) {
   using Core = ElemCore<T, PROB, P, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
