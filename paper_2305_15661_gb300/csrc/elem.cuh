@@ -231,6 +231,76 @@ __device__ __forceinline__ void syrk_upper_bf16(const float* A, int k, int ka, f
   }
 }
 
+// The same BF16 upper-triangle product with its operands staged once per element:
+// A (n_u x k FP32, row stride ka) is rounded to BF16 and transposed into T (k rows of
+// kp = n_u rounded up to 16 entries, zero beyond n_u; rs bytes per row, 16 more than
+// the data so that the eight rows of an ldmatrix phase fall on different banks),
+// and each 16 x 16 (A^T) and 16 x 8 (A) fragment is one ldmatrix. Rows of a tile
+// beyond k read row k - 1; their products land outside the triangle and are dropped.
+// T takes rs * k bytes of shared memory the caller no longer needs (Phi_e).
+__host__ __device__ constexpr int syrk_bf16_rs(int nu) { return ((nu + 15) / 16) * 32 + 16; }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+
+template <int NU>
+__device__ __forceinline__ void syrk_upper_bf16_staged(const float* A, int k, int ka, unsigned char* Tb, float* acc,
+                                                       float rho, int lane) {
+  constexpr int KS = (NU + 15) / 16;  // 16-entry steps of the contraction index
+  constexpr int rs = syrk_bf16_rs(NU);
+  // transpose and round, one row m of T per lane: 16-byte groups of four BF16 pairs
+  // (A[i][m], A[i + 1][m]), zero beyond n_u
+  for (int m = lane; m < k; m += 32) {
+#pragma unroll
+    for (int grp = 0; grp < KS * 2; ++grp) {
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i0 = grp * 8 + 2 * u, i1 = i0 + 1;
+        const float lo = i0 < NU ? A[i0 * ka + m] : 0.0f, hi = i1 < NU ? A[i1 * ka + m] : 0.0f;
+        w[u] = pack_bf16x2(lo, hi);
+      }
+      *reinterpret_cast<uint4*>(Tb + m * rs + grp * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  __syncwarp();
+  const uint32_t tb = (uint32_t)__cvta_generic_to_shared(Tb);
+  const int g = lane >> 2, t = lane & 3;
+  const int mtiles = (k + 15) / 16, ntiles = (k + 7) / 8;
+  // ldmatrix row addresses: x4 (A^T tile) lanes 8j..8j+7 give rows (j & 1) * 8 + r at
+  // column (j >> 1) * 8; x2 (A tile) lanes 0..15 give rows r at column ((lane >> 3) & 1) * 8
+  const int ra = ((lane >> 3) & 1) * 8 + (lane & 7), ca = (lane >> 4) * 8;
+  const int rb = lane & 7, cb8 = ((lane >> 3) & 1) * 8;
+  for (int mt = 0; mt < mtiles; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+    const int rowa = min(mt * 16 + ra, k - 1);
+    for (int nt = 2 * mt; nt < ntiles; ++nt) {
+      const int rowb = min(nt * 8 + rb, k - 1);
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t av[4], bv[2];
+        ldsm_x4(av, tb + rowa * rs + (ks * 16 + ca) * 2);
+        ldsm_x2(bv, tb + rowb * rs + (ks * 16 + cb8) * 2);
+        mma_bf16(c, av, bv);
+      }
+      const int cb = nt * 8 + 2 * t;
+      const int rr[4] = {r0, r0, r1, r1}, cc[4] = {cb, cb + 1, cb, cb + 1};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (rr[j] <= cc[j] && cc[j] < k) acc[acc_h(rr[j], cc[j], k)] += rho * c[j];
+    }
+  }
+  __syncwarp();
+}
+
 template <class T, int PROB, int P>
 struct Tabs {
   using Dd = Disc<PROB, P>;
@@ -2110,7 +2180,13 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       if constexpr (std::is_same<T, float>::value && TC) {
         {
           __syncwarp();
-          if (a.contraction == 3) syrk_upper_bf16<NU>(C.A, k, C.ka, C.acc, rT, lane);
+          if (a.contraction == 3) {
+            // staged operands when T fits in the (no longer needed) Phi_e buffer
+            if ((size_t)syrk_bf16_rs(NU) * k <= (size_t)NU * ku * sizeof(float))
+              syrk_upper_bf16_staged<NU>(C.A, k, C.ka, reinterpret_cast<unsigned char*>(C.Phie), C.acc, rT, lane);
+            else
+              syrk_upper_bf16<NU>(C.A, k, C.ka, C.acc, rT, lane);
+          }
           else if (a.contraction == 2) syrk_upper_tf32<NU, true>(C.A, k, C.ka, C.acc, rT, lane);
           else syrk_upper_tf32<NU, false>(C.A, k, C.ka, C.acc, rT, lane);
           if (dist) {
