@@ -139,6 +139,64 @@ int run_mixed(int mode, int blocks, int threads, int iters_f, int iters_m, doubl
   return 0;
 }
 
+// Float-float arithmetic (a value as an unevaluated sum hi + lo of two floats, about
+// 48 significant bits): the multiply-add by Dekker's product error through fmaf and
+// Knuth's error-free sum, on the FP32 pipe. 8 independent chains per thread.
+struct ff_t {
+  float hi, lo;
+};
+__device__ __forceinline__ ff_t ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff_t ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff_t ff_fma(ff_t a, ff_t b, ff_t c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const ff_t s = ff_two_sum(p, c.hi);
+  return ff_fast_two_sum(s.hi, s.lo + e + c.lo);
+}
+__global__ void ff_chains(float* out, int iters) {
+  ff_t x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = {1.0f + 1e-3f * threadIdx.x + j, 1e-9f};
+  const ff_t a = {0.999f, 1e-9f}, b = {0.001f, 1e-11f};
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = ff_fma(x[j], a, b);
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j].hi + x[j].lo;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int run_ff(int blocks, int threads, int iters, double* fma_per_s) {
+  float* out = nullptr;
+  if (cudaMalloc(&out, sizeof(float) * (size_t)blocks * threads) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ff_chains<<<blocks, threads>>>(out, iters / 10);  // warm-up
+  cudaEventRecord(e0);
+  ff_chains<<<blocks, threads>>>(out, iters);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return 2;
+  *fma_per_s = 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+  return 0;
+}
+
 }  // namespace
 
 // Time (ms) of the FP64 FMA / MMA sharing test above (mode 0 both, 1 FMA warps only,
@@ -147,9 +205,15 @@ extern "C" int fp64_pipe_probe(int mode, int blocks, int threads, int iters_f, i
   return run_mixed(mode, blocks, threads, iters_f, iters_m, ms);
 }
 
-// precision: 0 FP64 FMA, 1 FP32 FMA, 2 FP64 MMA (m8n8k4).
+// precision: 0 FP64 FMA, 1 FP32 FMA, 2 FP64 MMA (m8n8k4), 3 float-float multiply-adds
+// (reported as 2 FLOPs each, like an FMA).
 extern "C" int fma_probe(int precision, int blocks, int threads, int iters, double* flops_per_s) {
   if (precision == 2) return run_dmma(blocks, threads, iters, flops_per_s);
+  if (precision == 3) {
+    const int rc = run_ff(blocks, threads, iters, flops_per_s);
+    *flops_per_s *= 2.0;
+    return rc;
+  }
   return precision == 0 ? run<double>(blocks, threads, iters, flops_per_s)
                         : run<float>(blocks, threads, iters, flops_per_s);
 }

@@ -192,6 +192,20 @@ def test_fp32_reduced_assembly_shapes(p, ku, kx):
     assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_fp32_assembly_on_a_translated_mesh(p):
+    # the same mesh moved to x, y ~ 1000: FP32 vertex coordinates there are only good
+    # to ~6e-5 absolute, 5e-4 of an element's edge, while the FP32 element pass takes
+    # its edges from differences formed in FP64 and rounded once (the edge table), so
+    # the FP32 tolerances still hold
+    wl = W.euler_workload(n=8, p=p, k_u=12, k_x=4, seed=61)
+    wl.X = wl.X + 1000.0
+    g, r, _ = _assembly_pair(wl, precision=ift.FP32)
+    assert _fro(g["H"], r["H"]) < 1e-5
+    assert _fro(np.concatenate([g["S"], g["T"]]), np.concatenate([r["S"], r["T"]])) < 1e-3
+    assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
+
+
 def test_assembly_is_deterministic():
     wl = W.euler_workload(n=20, p=2, k_u=10, k_x=4, seed=8)
     ctx = ift.Context.from_workload(wl)
