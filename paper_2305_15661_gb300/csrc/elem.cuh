@@ -319,10 +319,10 @@ struct Tabs {
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // FP64 elements whose volume Jacobian dR_e/dU_e (n_u x n_u) fits in 18 registers
-// per lane form it explicitly and multiply by Phi_e (fewer FP64 operations, the
-// bound of the FP64 kernels); larger ones (p = 3 Euler) and the FP32 kernels
-// (bound by issue and latency, where the extra registers cost occupancy) take
-// Jacobian-vector products per quadrature point.
+// per lane form it explicitly in staged passes and multiply by Phi_e (fewer FP64
+// operations, the bound of the FP64 kernels); larger ones (p = 3 Euler) take
+// Jacobian-vector products per quadrature point. The FP32 kernels have their own
+// forms (jac_state: rows in registers for p <= 2, per-column products otherwise).
 __host__ __device__ constexpr bool kExplicitVolume(int nu, int word) { return word == 8 && nu * nu <= 576; }
 // Entries of Jv per register pass (9 doubles per lane).
 constexpr int kJvPass = 288;

@@ -197,7 +197,50 @@ int run_ff(int blocks, int threads, int iters, double* fma_per_s) {
   return 0;
 }
 
+// FP64 FMA chains run by only the first `active` lanes of every warp (the others
+// wait at the branch): does the FP64 unit charge a warp instruction by its active
+// lanes or as a whole?
+__global__ void fp64_lanes_chains(double* out, int iters, int active) {
+  double x0 = (double)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
+         x7 = x0 + 7;
+  if ((int)(threadIdx.x & 31) < active) {
+    const double a = 0.999, b = 0.001;
+    for (int i = 0; i < iters; ++i) {
+      x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+      x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+int run_lanes(int active, int blocks, int threads, int iters, double* ms_out) {
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * (size_t)blocks * threads) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_lanes_chains<<<blocks, threads>>>(out, iters / 10, active);  // warm-up
+  cudaEventRecord(e0);
+  fp64_lanes_chains<<<blocks, threads>>>(out, iters, active);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return 2;
+  *ms_out = ms;
+  return 0;
+}
+
 }  // namespace
+
+// Time (ms) of FP64 FMA chains on `active` lanes of every warp (1..32).
+extern "C" int fp64_lanes_probe(int active, int blocks, int threads, int iters, double* ms) {
+  return run_lanes(active, blocks, threads, iters, ms);
+}
 
 // Time (ms) of the FP64 FMA / MMA sharing test above (mode 0 both, 1 FMA warps only,
 // 2 MMA warps only).
