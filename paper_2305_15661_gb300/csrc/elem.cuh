@@ -1062,7 +1062,7 @@ struct ElemCore {
           for (int f = 0; f < NFQ; ++f) s += fw[f] * Lt[f * NT + j] * Hf[(k * NFQ + f) * M + a];
         }
       R[ia] = s;
-      if (!isfinite((double)s)) bad = true;
+      if (!isfinite(s)) bad = true;
     }
     return group_any(bad, step);
   }
