@@ -721,6 +721,11 @@ struct ElemCore {
     // face points: task t -> (group, face point); group 0: H and dH/dU+, group 1: dH/dU-
     const int npts = NF * NFQ;
     const int ngroups = (Dd::EULER && fj) ? 2 : 1;
+    // dH/dn inside the task loop when both groups run in one trip of a whole warp
+    // (every Euler degree here: at most 2 x 15 tasks); otherwise in a pass of its own
+    const bool hn_fused = Dd::EULER && fj && need_hn && step == 32 && 2 * npts <= 32;
+    const unsigned hn_mask = 2 * npts >= 32 ? 0xffffffffu : ((1u << (2 * npts)) - 1u);
+    const bool hn_here = hn_fused && lane < 2 * npts;
     for (int t = lane; t < npts * ngroups; t += step) {
       const int grp = t / npts, pt = t % npts;
       const int k = pt / NFQ, f = pt % NFQ;
@@ -780,6 +785,29 @@ struct ElemCore {
           if (!sw) st4(hf, H[0].v, H[1].v, H[2].v, H[3].v);
 #pragma unroll
           for (int a = 0; a < 4; ++a) st4(&dst[a * 4], sg * H[a].d[0], sg * H[a].d[1], sg * H[a].d[2], sg * H[a].d[3]);
+          if (hn_here) {
+            // dH/dn from the identities below, formed where the Jacobians are in
+            // registers: each group applies its own Jacobian to G(its state) (see the
+            // separate pass), and group 1 hands its part to group 0 by a shuffle
+            const T* us = sw ? Uout : Uin;
+            T part[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) part[a] = (sg * H[a].d[1]) * (-us[2]) + (sg * H[a].d[2]) * us[1];
+            T other[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) other[a] = __shfl_down_sync(hn_mask, part[a], npts);
+            if (!sw) {
+              const T nx = ntv(pt, k, 0), ny = ntv(pt, k, 1);
+              const T inv = T(1) / (nx * nx + ny * ny);
+              const T Gh[4] = {T(0), -H[2].v, H[1].v, T(0)};
+#pragma unroll
+              for (int a = 0; a < 4; ++a) {
+                const T K = Gh[a] - part[a] - other[a];
+                Hn[pt * 8 + a * 2 + 0] = (H[a].v * nx - K * ny) * inv;
+                Hn[pt * 8 + a * 2 + 1] = (H[a].v * ny + K * nx) * inv;
+              }
+            }
+          }
         }
       } else {
         // Burgers: inflow u- = 1 on the face with normal -x, outflow u- = u+
@@ -795,7 +823,7 @@ struct ElemCore {
         }
       }
     }
-    if (Dd::EULER && fj && need_hn) {
+    if (Dd::EULER && fj && need_hn && !hn_fused) {
       __syncwarp();
       // dH/dn from two identities of the Roe flux: homogeneity, dH/dn . n = H, and
       // rotational invariance, dH/dn . (J n) = G(H) - dH/dU+ G(U+) - dH/dU- G(U-),
@@ -2479,13 +2507,21 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? kFp32JacMinBloc
   }
   __syncthreads();
   // CTA partial: sum the accumulators of the CTA's element regions in order, in FP64
-  // (gradient pass: rows of [g | J | count] only)
+  // (gradient pass: rows of [g | J | count] only). FP32 accumulators are added in
+  // FP32 and converted once: the FP64 unit takes a whole warp instruction per
+  // conversion or add, and all CTAs reach this step at once at the end of the launch.
   Lay L(ku, kx);
   const int nrow = GRAD ? k + 2 : nacc;
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
     const int src = GRAD ? Lay::gacc_offset(k) + i : acc_source(i, k);
     double s = 0.0;
-    for (int w = 0; w < nw * PW; ++w) s += (double)((const T*)(smem + cb + w * eb + L.oacc))[src];
+    if constexpr (sizeof(T) == 4) {
+      T f = T(0);
+      for (int w = 0; w < nw * PW; ++w) f += ((const T*)(smem + cb + w * eb + L.oacc))[src];
+      s = (double)f;
+    } else {
+      for (int w = 0; w < nw * PW; ++w) s += (double)((const T*)(smem + cb + w * eb + L.oacc))[src];
+    }
     a.partial[(size_t)blockIdx.x * nrow + i] = s;
   }
 }
