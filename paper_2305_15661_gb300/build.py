@@ -37,7 +37,8 @@ def _nvcc() -> str:
 def _units():
     units = [("api", "api.cu", []), ("lm", "lm.cu", []), ("refelem", "refelem.cpp", []),
              ("dispatch", "dispatch.cpp", []), ("noalloc", "noalloc.cu", []),
-             ("mlp", "mlp.cu", []), ("mlp_tc", "mlp_tc.cu", [])]
+             ("mlp", "mlp.cu", []), ("mlp_tc", "mlp_tc.cu", []),
+             ("syrk_tc", "syrk_tc.cu", [])]
     for prob in (1, 2, 3):
         for p in (1, 2, 3):
             for prec in (0, 1):

@@ -18,6 +18,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "syrk_tc.h"
 #include "../../include/ift.h"
 #include "elem.cuh"
 #include "kernels.h"
@@ -129,6 +130,11 @@ struct ift_ctx {
   double* d_Phi = nullptr;
   float* d_Phi32 = nullptr;
   float4* d_geo32 = nullptr;  // FP32 edge table of straight-sided triangles (FP32 contexts)
+  // FP32 contexts with BF16 contraction: the transposed BF16 stack of sqrt(rho_e) A_e
+  // rows (k rows of at_ld values) the tensor-core product reads, and its status word
+  uint16_t* d_at = nullptr;
+  long at_ld = 0, at_rows = 0;
+  int* d_tc_status = nullptr;
   double* d_Psi = nullptr;
   // weights
   int64_t nnz = -1;
@@ -337,6 +343,26 @@ ift_status plan_launch(ift_ctx* c, int wp) {
     c->plan_grid_grad = (int)grid;
     c->plan_smem_grad = smem;
   }
+  // FP32 with BF16 contraction: the stack of the tensor-core product (zero past the
+  // items' rows), sized for the current items; allocated here, before any capture
+  const int kk = c->ku + c->kx;
+  if (wp == 1 && c->cfg.contraction == IFT_CONTRACT_BF16 && c->nu % 2 == 0 && kk <= 64) {
+    const long rows = (long)items * c->nu;
+    const long ld = syrk_tc_rows(rows);
+    if (!c->d_at || c->at_ld != ld) {
+      CK(dalloc(c->d_at, (size_t)kk * ld), "alloc tensor-core stack");
+      CK(cudaMemset(c->d_at, 0, (size_t)kk * ld * sizeof(uint16_t)), "clear tensor-core stack");
+      c->at_ld = ld;
+    }
+    c->at_rows = rows;
+    if (!c->d_tc_status) {
+      CK(dalloc(c->d_tc_status, 1), "alloc status");
+      CK(cudaMemset(c->d_tc_status, 0, sizeof(int)), "clear status");
+    }
+    CK(syrk_tc_prepare(), "tensor-core product attributes");
+  } else {
+    c->at_rows = 0;
+  }
   // the inspection kernel shares the fused kernel's attribute; make sure it covers its layout
   const size_t ismem = ks.smem_bytes(true, 1, 0, wpc);
   if (ismem > c->plan_smem[wp][1]) {
@@ -360,8 +386,13 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   const int grid = c->plan_grid[wp][jac ? 1 : 0];
   const size_t smem = c->plan_smem[wp][jac ? 1 : 0];
   cudaError_t e;
+  const bool tc_stack = wp == 1 && jac && c->at_rows > 0;
   if (wp == 1) {
     AsmArgs<float> a = make_args<float>(c, c->d_Phi32, w, tau, mu, false, skip);
+    if (tc_stack) {
+      a.at_out = reinterpret_cast<uint32_t*>(c->d_at);
+      a.at_ld = c->at_ld;
+    }
     e = ks.assemble(&a, jac, grid, block, smem, s);
   } else {
     AsmArgs<double> a = make_args<double>(c, c->d_Phi, w, tau, mu, false, skip);
@@ -369,7 +400,16 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   }
   if (e != cudaSuccess) return c->cuda_fail(e, "element kernel launch");
   const int nacc = c->nacc();
-  reduce_partials_kernel<<<(nacc + 31) / 32, 1024, 0, s>>>(c->d_partial, grid, nacc, out, skip);
+  int nparts = grid;
+  if (tc_stack) {
+    // H from the stack on the tensor cores: its partial rows follow the element CTAs'
+    int ctas = 0;
+    e = syrk_tc_launch(c->d_at, c->at_ld, c->at_rows, c->ku + c->kx, std::min(c->sm_count, c->max_parts - grid),
+                       c->d_partial + (size_t)grid * nacc, nacc, skip, c->d_tc_status, &ctas, s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "tensor-core product launch");
+    nparts += ctas;
+  }
+  reduce_partials_kernel<<<(nacc + 31) / 32, 1024, 0, s>>>(c->d_partial, nparts, nacc, out, skip);
   e = cudaGetLastError();
   if (e != cudaSuccess) return c->cuda_fail(e, "reduce launch");
   return IFT_OK;
@@ -585,6 +625,8 @@ ift_status ift_destroy(ift_ctx* c) {
   dfree(c->d_Phi);
   dfree(c->d_Phi32);
   dfree(c->d_geo32);
+  dfree(c->d_at);
+  dfree(c->d_tc_status);
   dfree(c->d_Psi);
   dfree(c->d_elems);
   dfree(c->d_rho);
@@ -836,6 +878,14 @@ ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const dou
   std::vector<double> res(nacc);
   CK(cudaMemcpyAsync(res.data(), c->d_res, nacc * 8, cudaMemcpyDeviceToHost, s), "copy result");
   CK(cudaStreamSynchronize(s), "assembly");
+  if (c->d_tc_status) {
+    int tcs = 0;
+    CK(cudaMemcpy(&tcs, c->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    if (tcs != 0) {
+      cudaMemset(c->d_tc_status, 0, sizeof(int));
+      return c->fail(IFT_ERR_TIMEOUT, "the tensor-core product timed out waiting for its operands");
+    }
+  }
   if (H) std::memcpy(H, res.data(), (size_t)k * k * 8);
   if (S) std::memcpy(S, res.data() + k * k, c->ku * 8);
   if (T && c->kx > 0) std::memcpy(T, res.data() + k * k + c->ku, c->kx * 8);

@@ -122,6 +122,12 @@ struct AsmArgs {
   // and the same differences of each mesh column of Psi (taken in FP64, rounded
   // once); the FP32 geometry is formed from them with no FP64 arithmetic
   const float4* geo32 = nullptr;
+  // FP32 with BF16 contraction (may be null): instead of forming H in the element
+  // pass, write the element's rows of sqrt(rho_e) A_e transposed in BF16 pairs,
+  // At[m][item * n_u + i] (row stride at_ld values), for the tensor-core product
+  // that follows the pass (syrk_tc.cu)
+  uint32_t* at_out = nullptr;
+  long at_ld = 0;
 };
 
 // H += rho A^T A on the tensor cores (warp-level mma.m16n8k8, TF32 inputs, FP32
@@ -2181,7 +2187,8 @@ __device__ __forceinline__ bool element_front(ElemCore<T, PROB, P, JAC>& C, cons
 template <class T, int PROB, int P, bool JAC, bool TC = false>
 __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const AsmArgs<T>& a, int e, double rho,
                                              const T* wT, const double* tauD, const double* mu,
-                                             const unsigned char* pairs, int lane, const float* tauF = nullptr) {
+                                             const unsigned char* pairs, int lane, const float* tauF = nullptr,
+                                             long item = -1) {
   using Dd = Disc<PROB, P>;
   constexpr int DIM = Dd::DIM, NU = Dd::NU, NXE = Dd::NXE, NF = Dd::NFACE, NV = Dd::NV;
   const int ku = a.ku, kx = a.kx, k = ku + kx;
@@ -2208,7 +2215,19 @@ __device__ __forceinline__ void element_pass(ElemCore<T, PROB, P, JAC>& C, const
       if constexpr (std::is_same<T, float>::value && TC) {
         {
           __syncwarp();
-          if (a.contraction == 3) {
+          if (a.contraction == 3 && NU % 2 == 0 && a.at_out != nullptr && item >= 0) {
+            // the rows of sqrt(rho_e) A_e, transposed, to the stack the tensor-core
+            // product reads after the pass (rho >= 0): word (m at_ld + item n_u) / 2 + j
+            // holds (row 2j, row 2j + 1) of column m
+            constexpr int NP = NU / 2;
+            const float sr = sqrtf(rT);
+            uint32_t* col0 = a.at_out + ((size_t)item * NU) / 2;
+            for (int idx = lane; idx < k * NP; idx += 32) {
+              const int m = idx / NP, j = idx - m * NP;
+              col0[((size_t)m * a.at_ld) / 2 + j] =
+                  pack_bf16x2(sr * C.A[(2 * j) * C.ka + m], sr * C.A[(2 * j + 1) * C.ka + m]);
+            }
+          } else if (a.contraction == 3) {
             // staged operands when T fits in the (no longer needed) Phi_e buffer
             if ((size_t)syrk_bf16_rs(NU) * k <= (size_t)NU * ku * sizeof(float))
               syrk_upper_bf16_staged<NU>(C.A, k, C.ka, reinterpret_cast<unsigned char*>(C.Phie), C.acc, rT, lane);
@@ -2502,7 +2521,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 && JAC) ? kFp32JacMinBloc
       const int e = a.elems ? a.elems[it] : (int)it;
       const double rho = a.rho ? a.rho[it] : 1.0;
       if constexpr (GRAD && JAC) element_grad_pass<T, PROB, P>(C, a, e, rho, wT, tauD, a.mu, lane);
-      else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane, tauF);
+      else element_pass<T, PROB, P, JAC, TC>(C, a, e, rho, wT, tauD, a.mu, pairs, lane, tauF, it);
     }
   }
   __syncthreads();
