@@ -404,7 +404,7 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   if (tc_stack) {
     // H from the stack on the tensor cores: its partial rows follow the element CTAs'
     int ctas = 0;
-    e = syrk_tc_launch(c->d_at, c->at_ld, c->at_rows, c->ku + c->kx, std::min(c->sm_count, c->max_parts - grid),
+    e = syrk_tc_launch(c->d_at, c->at_ld, c->at_rows, c->ku + c->kx, std::min(2 * c->sm_count, c->max_parts - grid),
                        c->d_partial + (size_t)grid * nacc, nacc, skip, c->d_tc_status, &ctas, s);
     if (e != cudaSuccess) return c->cuda_fail(e, "tensor-core product launch");
     nparts += ctas;

@@ -121,7 +121,9 @@ __device__ __forceinline__ void load_tile(uint32_t stage, const uint16_t* At, lo
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// Two CTAs per SM (2 x 98 KB of shared memory): the stack is read once, and the
+// copies in flight across both CTAs' rings set the bandwidth.
+__global__ void __launch_bounds__(kThreads, 2)
     syrk_tc_kernel(const uint16_t* At, long ldr, int k, long tiles, long tiles_per_cta, double* partial, int nacc,
                    const int* skip, int* status) {
   if (skip != nullptr && *(volatile const int*)skip) return;
