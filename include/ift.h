@@ -83,7 +83,13 @@ enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2, IFT_FP32_JACOBIAN = 3 };
    accuracy; BF16 = tensor cores with BF16 inputs (7-bit mantissa) and FP32
    accumulation, H to a few 1e-3 relative. S~, T~ and J~ are FP32 fused
    multiply-adds in every mode, so the optimum of a solve does not depend on this
-   choice (H only steers the step). */
+   choice (H only steers the step). With BF16, the single-query FP32 evaluations
+   (ift_reduced_residual_jacobian, ift_solve_rom) form H with tcgen05 products from
+   a stack of the rows of sqrt(rho_e) A_e in BF16, which takes (k_u + k_x) x
+   (items x n_u) x 2 bytes of device memory (items: the elements with nonzero
+   weight; 307 MB for 80,000 p = 3 elements at k = 48), allocated when the weights
+   are set or first used; a bounded wait there that runs out makes the evaluation
+   return IFT_ERR_TIMEOUT. The batched calls keep warp-level tensor-core tiles. */
 enum { IFT_CONTRACT_FP = 0, IFT_CONTRACT_TF32 = 1, IFT_CONTRACT_3XTF32 = 2, IFT_CONTRACT_BF16 = 3 };
 /* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
    LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */
