@@ -89,7 +89,8 @@ enum { IFT_FP64 = 0, IFT_FP32 = 1, IFT_MIXED = 2, IFT_FP32_JACOBIAN = 3 };
    (items x n_u) x 2 bytes of device memory (items: the elements with nonzero
    weight; 307 MB for 80,000 p = 3 elements at k = 48), allocated when the weights
    are set or first used; a bounded wait there that runs out makes the evaluation
-   return IFT_ERR_TIMEOUT. The batched calls keep warp-level tensor-core tiles. */
+   or the solve return IFT_ERR_TIMEOUT (ift_solve_rom_dev: when it is given
+   info_host). The batched calls keep warp-level tensor-core tiles. */
 enum { IFT_CONTRACT_FP = 0, IFT_CONTRACT_TF32 = 1, IFT_CONTRACT_3XTF32 = 2, IFT_CONTRACT_BF16 = 3 };
 /* LM start: PAPER = w from Phi^T U_guess then LM on w with tau = 0, then joint
    LM (Remark rem:solver); GIVEN = start the joint LM at the caller's (y, z). */

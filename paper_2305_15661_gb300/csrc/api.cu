@@ -415,6 +415,17 @@ ift_status launch_assemble(ift_ctx* c, int wp, bool jac, const double* w, const 
   return IFT_OK;
 }
 
+// After a synchronised evaluation or solve: IFT_ERR_TIMEOUT (and the word cleared)
+// if the tensor-core product recorded a bounded wait that ran out.
+ift_status tc_status_check(ift_ctx* c) {
+  if (!c->d_tc_status) return IFT_OK;
+  int tcs = 0;
+  CK(cudaMemcpy(&tcs, c->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+  if (tcs == 0) return IFT_OK;
+  cudaMemset(c->d_tc_status, 0, sizeof(int));
+  return c->fail(IFT_ERR_TIMEOUT, "the tensor-core product timed out waiting for its operands");
+}
+
 // The FP64 gradient pass at (w, tau): S~, T~, J~ and the non-physical count into
 // the [g | J | count] part of out (the H part is left as it is). states (optional):
 // the solve's LM state, whose flags say whether the FP32 pass ran in this body.
@@ -878,14 +889,8 @@ ift_status ift_reduced_residual_jacobian(ift_ctx* c, const double* mu, const dou
   std::vector<double> res(nacc);
   CK(cudaMemcpyAsync(res.data(), c->d_res, nacc * 8, cudaMemcpyDeviceToHost, s), "copy result");
   CK(cudaStreamSynchronize(s), "assembly");
-  if (c->d_tc_status) {
-    int tcs = 0;
-    CK(cudaMemcpy(&tcs, c->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
-    if (tcs != 0) {
-      cudaMemset(c->d_tc_status, 0, sizeof(int));
-      return c->fail(IFT_ERR_TIMEOUT, "the tensor-core product timed out waiting for its operands");
-    }
-  }
+  st = tc_status_check(c);
+  if (st != IFT_OK) return st;
   if (H) std::memcpy(H, res.data(), (size_t)k * k * 8);
   if (S) std::memcpy(S, res.data() + k * k, c->ku * 8);
   if (T && c->kx > 0) std::memcpy(T, res.data() + k * k + c->ku, c->kx * 8);
@@ -1202,6 +1207,8 @@ ift_status ift_solve_rom(ift_ctx* c, const double* mu, double* y, double* z, ift
   for (int i = 0; i < c->ku; ++i) y[i] = hs.z[i];
   for (int i = 0; i < c->kx; ++i) z[i] = hs.z[c->ku + i];
   fill_info(hs, info, c->ku, c->kx);
+  st = tc_status_check(c);
+  if (st != IFT_OK) return st;
   return (ift_status)hs.status;
 }
 
@@ -1229,6 +1236,8 @@ ift_status ift_solve_rom_dev(ift_ctx* c, const double* mu, double* y, double* z,
     CK(cudaMemcpyAsync(&hs, c->d_lm, sizeof(LMState), cudaMemcpyDeviceToHost, s), "copy state");
     CK(cudaStreamSynchronize(s), "solve");
     fill_info(hs, info_host, c->ku, c->kx);
+    st = tc_status_check(c);
+    if (st != IFT_OK) return st;
     return (ift_status)hs.status;
   }
   return IFT_OK;
