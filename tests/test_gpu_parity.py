@@ -355,6 +355,25 @@ def test_no_mesh_motion_basis():
     assert g["T"].shape == (0,)
 
 
+@pytest.mark.parametrize("contraction,htol", [(ift.CONTRACT_FP, 1e-5), (ift.CONTRACT_BF16, 3e-2)])
+def test_no_mesh_motion_basis_fp32(contraction, htol):
+    # k_x = 0 in FP32: the edge table holds only the reference edges, the state
+    # columns take the 8-column blocks (k = 8), and with BF16 the tcgen05 product
+    # forms H from the stack
+    wl = W.euler_workload(n=6, p=2, k_u=8, k_x=2, seed=3)
+    wl.Psi = np.zeros((wl.Psi.shape[0], 0))
+    wl.tau_eval = np.zeros(0)
+    O = orc.Oracle.from_workload(wl)
+    r = O.reduced(wl.Phi, wl.Psi, wl.w_eval, wl.tau_eval, wl.mus[0])
+    ctx = ift.Context.from_workload(wl, precision=ift.FP32, contraction=contraction)
+    g = ctx.reduced_residual_jacobian(wl.mus[0], wl.w_eval, wl.tau_eval)
+    assert _fro(g["H"], r["H"]) < htol
+    assert _fro(g["S"], r["S"]) < 1e-3
+    assert abs(g["J"] - r["J"]) <= 1e-5 * r["J"]
+    assert g["T"].shape == (0,)
+    ctx.close()
+
+
 def test_single_element_and_ragged_weight_list():
     wl = W.euler_workload(n=5, p=2, k_u=6, k_x=2, seed=2)
     for elems in ([7], [0, 1, 2], list(range(0, 50, 3))):
