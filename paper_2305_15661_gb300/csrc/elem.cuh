@@ -2853,7 +2853,7 @@ __global__ void __launch_bounds__(128) align_kernel(AsmArgs<T> a, const double* 
   constexpr bool JK = MODE != 0;
   using Core = ElemCore<T, PROB, P, JK>;
   constexpr int M = Dd::M, DIM = Dd::DIM, NU = Dd::NU, NUP = Dd::NUP, NXE = Dd::NXE, NF = Dd::NFACE,
-                NT = Dd::NTRACE, NV = Dd::NV;
+                NV = Dd::NV;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ku = a.ku;
