@@ -27,45 +27,66 @@ __device__ double active_norm(const LMState& s, int ku, int kx, bool full) {
 }
 
 // Cholesky of the n x n matrix in shared memory A (row-major, lower triangle used),
-// done by one warp, right-looking: for each column j, the pivot, the column below
-// it, then the trailing lower triangle updated row by row (lane-owned rows).
+// done by one warp, right-looking. On return the strict lower triangle holds L and
+// the diagonal holds 1 / L_jj (the solve below multiplies by it). An FP64 warp
+// instruction costs the same with one active lane as with 32, so each column takes
+// one reciprocal square root for its pivot, one scaling of the column below it
+// and then the trailing lower triangle, all m (m + 1) / 2 of its entries spread
+// over the 32 lanes (m = n - 1 - j): entry t of that triangle is (i, l) with
+// l = n - 1 - a, i = l + b, t = a (a + 1) / 2 + b, 0 <= b <= a.
 __device__ bool warp_cholesky(double* A, int n, int lane) {
   for (int j = 0; j < n; ++j) {
     __syncwarp();
     const double d = A[j * n + j];
     if (!(d > 0.0)) return false;
-    const double r = sqrt(d);
+    const double inv = rsqrt(d);
     __syncwarp();
-    for (int i = j + 1 + lane; i < n; i += 32) A[i * n + j] /= r;
-    if (lane == 0) A[j * n + j] = r;
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * n + j] *= inv;
+    if (lane == 0) A[j * n + j] = inv;
     __syncwarp();
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      const double lij = A[i * n + j];
-      for (int l = j + 1; l <= i; ++l) A[i * n + l] -= lij * A[l * n + j];
+    const int m = n - 1 - j;
+    const int tri = m * (m + 1) / 2;
+    for (int t = lane; t < tri; t += 32) {
+      int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((a + 1) * (a + 2) / 2 <= t) ++a;
+      if (a * (a + 1) / 2 > t) --a;
+      const int l = n - 1 - a;
+      const int i = l + (t - a * (a + 1) / 2);
+      A[i * n + l] -= A[i * n + j] * A[l * n + j];
     }
   }
   __syncwarp();
   return true;
 }
 
-// Solves L L^T x = b in place in rhs (n values, shared memory) with the factor in
-// the lower triangle of L, by one warp: column-oriented forward and backward
-// substitution (one pivot per step, lane-parallel updates of the remaining rows).
+// Solves L L^T x = b in place in rhs (n values, shared memory) with the factor of
+// warp_cholesky (strict lower triangle L, diagonal 1 / L_jj), by one warp:
+// column-oriented forward and backward substitution (one pivot per step,
+// lane-parallel updates of the remaining rows).
 __device__ void warp_cholesky_solve(const double* L, int n, double* rhs, int lane) {
   for (int j = 0; j < n; ++j) {  // L y = b
     __syncwarp();
-    const double yj = rhs[j] / L[j * n + j];
+    const double yj = rhs[j] * L[j * n + j];
     __syncwarp();
     if (lane == 0) rhs[j] = yj;
     for (int i = j + 1 + lane; i < n; i += 32) rhs[i] -= L[i * n + j] * yj;
   }
   for (int i = n - 1; i >= 0; --i) {  // L^T x = y
     __syncwarp();
-    const double xi = rhs[i] / L[i * n + i];
+    const double xi = rhs[i] * L[i * n + i];
     __syncwarp();
     if (lane == 0) rhs[i] = xi;
     for (int j = lane; j < i; j += 32) rhs[j] -= L[i * n + j] * xi;
   }
+  __syncwarp();
+}
+
+// The LM state of one query, copied between global and shared memory by one warp.
+__device__ void copy_state(LMState& dst, const LMState& src, int lane) {
+  static_assert(sizeof(LMState) % 8 == 0, "LMState is copied in 8-byte words");
+  auto* d = reinterpret_cast<unsigned long long*>(&dst);
+  const auto* v = reinterpret_cast<const unsigned long long*>(&src);
+  for (int w = lane; w < (int)(sizeof(LMState) / 8); w += 32) d[w] = v[w];
   __syncwarp();
 }
 
@@ -104,13 +125,18 @@ __device__ bool decide(LMState& s, const LMConsts& c) {
 }
 
 // One LM step of one query by one warp. res = [H (k*k) | g (k) | J | nonphysical count]
-// at s.trial; Ms (LM_KMAX^2) and rhs (LM_KMAX) are the warp's shared buffers.
-__device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, double* Ms, double* rhs, int lane) {
+// at s.trial; s is the query's state in shared memory (the scalar logic runs on
+// lane 0 and would wait on global memory at every field); Ms (LM_KMAX^2), rhs
+// (LM_KMAX) and gs (LM_KMAX + 2) are the warp's shared buffers.
+__device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, double* Ms, double* rhs, double* gs,
+                             int lane) {
   const int ku = c.ku, kx = c.kx, k = ku + kx;
   const double* Hr = res;
-  const double* gr = res + k * k;
-  const double Jr = res[k * k + k];
-  const double npr = res[k * k + k + 1];
+  for (int i = lane; i < k + 2; i += 32) gs[i] = res[k * k + i];
+  __syncwarp();
+  const double* gr = gs;
+  const double Jr = gs[k];
+  const double npr = gs[k + 1];
   int need_solve = 0;
   bool refresh_h = false;  // the next evaluation recomputes H (after a shortened step)
   if (lane == 0 && !s.done) {
@@ -181,11 +207,14 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
       Ms[i] = v;
     }
     __syncwarp();
-    double tr = 0.0;
-    for (int i = 0; i < ka; ++i) tr += Ms[i * ka + i];
-    __syncwarp();
     bool ok = warp_cholesky(Ms, ka, lane);
-    double sh = 1e-14 * tr / ka;
+    // the diagonal shift of a failed factorisation: 1e-14 trace / k of the damped matrix
+    double sh = 0.0;
+    if (!ok) {
+      double tr = 0.0;
+      for (int i = 0; i < ka; ++i) tr += Hr[i * k + i] + ((damp && i >= ku) ? lam : 0.0);
+      sh = 1e-14 * tr / ka;
+    }
     int nsh = 0;
     while (!ok && nsh < kMaxShifts) {
       __syncwarp();
@@ -241,15 +270,32 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
   __syncwarp();
 }
 
+// A finished query's step changes nothing but the kept-H flag (set, as the step
+// itself would set it); its state is then not copied at all. Returns true if the
+// query is finished.
+__device__ bool lm_step_finished(LMState& g, const LMConsts& c, int lane) {
+  const bool done = g.done != 0;
+  if (done && lane == 0 && c.keep_h) g.hkeep = 1;
+  return done;
+}
+
 // One LM step, single warp (the single-query solve).
 __global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsigned long long cond_handle,
                                int use_cond) {
   __shared__ double Ms[LM_KMAX * LM_KMAX];
   __shared__ double rhs[LM_KMAX];
+  __shared__ double gs[LM_KMAX + 2];
+  __shared__ LMState st;
   const int lane = threadIdx.x;
-  lm_step_warp(*sp, res, c, Ms, rhs, lane);
+  if (lm_step_finished(*sp, c, lane)) {
+    if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, 0u);
+    return;
+  }
+  copy_state(st, *sp, lane);
+  lm_step_warp(st, res, c, Ms, rhs, gs, lane);
+  copy_state(*sp, st, lane);
   // inside the solve graph: keep looping while the solve is not finished
-  if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, sp->done ? 0u : 1u);
+  if (use_cond && lane == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, st.done ? 0u : 1u);
 }
 
 // One LM step for each of B queries: block q (one warp) steps query q with its
@@ -257,8 +303,13 @@ __global__ void lm_step_kernel(LMState* sp, const double* res, LMConsts c, unsig
 __global__ void lm_step_batched_kernel(LMState* states, const double* res, int nacc, LMConsts c) {
   __shared__ double Ms[LM_KMAX * LM_KMAX];
   __shared__ double rhs[LM_KMAX];
-  const int q = blockIdx.x;
-  lm_step_warp(states[q], res + (size_t)q * nacc, c, Ms, rhs, threadIdx.x);
+  __shared__ double gs[LM_KMAX + 2];
+  __shared__ LMState st;
+  const int q = blockIdx.x, lane = threadIdx.x;
+  if (lm_step_finished(states[q], c, lane)) return;
+  copy_state(st, states[q], lane);
+  lm_step_warp(st, res + (size_t)q * nacc, c, Ms, rhs, gs, lane);
+  copy_state(states[q], st, lane);
 }
 
 // Loop condition of the batched solve: keep looping while any query is unfinished.
