@@ -372,9 +372,10 @@ ift_status ift_mlp_loss_grad(ift_mlp* net, int64_t count, const double* x, const
 
 /* Trains on count pairs (x, t): inputs and targets are first standardised per
    column (mean 0, standard deviation 1, kept in the network for predict), then
-   `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over
-   mini-batches of `batch` rows in a seeded random order (the last partial batch
-   of an epoch is dropped). final_loss (may be NULL): the loss over all pairs in
+   `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8) over mini-batches of
+   `batch` rows in a seeded random order (the last partial batch of an epoch is
+   dropped); the step of update t of T is lr (0.01 + 0.99 (1 + cos(pi t / T)) / 2),
+   from lr down to lr / 100. final_loss (may be NULL): the loss over all pairs in
    the standardised variables after training. */
 ift_status ift_mlp_train(ift_mlp* net, int64_t count, const double* x, const double* t, int epochs, int batch,
                          double lr, uint64_t seed, double* final_loss);

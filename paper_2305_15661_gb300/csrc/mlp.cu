@@ -422,6 +422,11 @@ ift_status ift_mlp_train(ift_mlp* n, int64_t count, const double* x, const doubl
   std::vector<int> perm(count);
   uint64_t ctr = 0;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  // the step decays from lr to lr / 100 along a half cosine over the run's steps:
+  // with a constant step the final weights are one point of Adam's noise band, and
+  // a change in the last bits of the targets picks another one
+  const double steps_total = (double)epochs * (double)(count / b);
+  double step_no = 0.0;
   for (int ep = 0; ep < epochs; ++ep) {
     for (int64_t i = 0; i < count; ++i) perm[i] = (int)i;
     for (int64_t i = count - 1; i > 0; --i) {  // Fisher-Yates with splitmix64 draws
@@ -439,8 +444,11 @@ ift_status ift_mlp_train(ift_mlp* n, int64_t count, const double* x, const doubl
       ++n->adam_t;
       const float c1 = 1.0f / (1.0f - std::pow(b1, (float)n->adam_t));
       const float c2 = 1.0f / (1.0f - std::pow(b2, (float)n->adam_t));
-      adam_kernel<<<grid_for(n->np, 256), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->np, (float)lr, b1, b2, eps,
-                                                               c1, c2);
+      const double lr_t =
+          lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(3.141592653589793 * step_no / std::max(steps_total, 1.0))));
+      step_no += 1.0;
+      adam_kernel<<<grid_for(n->np, 256), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->np, (float)lr_t, b1, b2,
+                                                               eps, c1, c2);
     }
   }
   double total = 0.0;
