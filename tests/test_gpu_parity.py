@@ -7,6 +7,8 @@ count. FP32 element kernels: the tolerances below follow from FP32 rounding
 cancellation in g = sum_e A_e^T R_e.
 """
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -288,6 +290,22 @@ def test_burgers_config1_solve():
 
 def test_euler_small_solve_dense():
     assert _check_solve(*_solve_pair(W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6), tol=1e-8)) == "same"
+
+
+def test_singular_w_block_solve_takes_the_shifted_factorisation():
+    # a zero column of Phi: H has a zero row and column, so each LM step's Cholesky
+    # meets a zero pivot on both sides and is retried with the diagonal shift
+    # 1e-14 tr(M)/k; the same steps, the same number of shifts, and the zero
+    # column's coefficient exactly 0
+    wl = W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6)
+    Phi = wl.Phi.copy()
+    Phi[:, -1] = 0.0
+    pair = _solve_pair(dataclasses.replace(wl, Phi=Phi), tol=1e-8)
+    g, r = pair[0], pair[1]
+    assert _check_solve(*pair) == "same"
+    assert r["shifts"] == r["init_iters"] + r["iters"] > 0
+    assert g["shifts"] == r["shifts"]
+    assert g["w"][-1] == 0.0
 
 
 def test_euler_small_solve_sparse_rho(record_property):

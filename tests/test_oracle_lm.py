@@ -11,7 +11,9 @@
   the oracle's steps, lambdas, step lengths and point;
 * on the Burgers and Euler workloads: convergence to the optimality tolerance,
   monotone decrease of J, symmetric positive definite H at the solution, and the
-  tau = 0 initialisation.
+  tau = 0 initialisation;
+* a zero column of Phi (an exactly singular w block): every factorisation takes
+  one diagonal shift, and the solve matches the one without that column.
 """
 
 import math
@@ -164,3 +166,30 @@ def test_damped_two_unknown_step_by_hand(z0):
         alt = HL.lm(z0, phi, eps, mu, 1e-12, **wrong)
         n = min(len(alt), len(ref))
         assert len(alt) != len(ref) or np.abs(alt[:n, 2:] - ref[:n, 2:]).max() > 1e-3, wrong
+
+
+def test_zero_basis_column_takes_the_shifted_factorisation():
+    # A zero column of Phi gives H a zero row and column, so every factorisation of
+    # the w block meets a zero pivot and is retried with the diagonal shift
+    # 1e-14 tr(M)/k (times 10 per further retry). That shift is far below the other
+    # pivots, so one retry succeeds, the zero column's coefficient stays exactly 0,
+    # and the solve takes the same steps to the same optimum as the problem without
+    # that column.
+    wl = W.euler_workload(n=8, p=2, k_u=8, k_x=4, seed=6)
+    mu = wl.mus[0]
+    U0 = W.replicate_guess(wl, wl.U_guess)
+    O = orc.Oracle.from_workload(wl)
+    Pz = wl.Phi.copy()
+    Pz[:, -1] = 0.0
+    rz = O.solve(Pz, wl.Psi, mu, Pz.T @ U0, tol=1e-8)
+    P7 = np.ascontiguousarray(wl.Phi[:, :-1])
+    r7 = O.solve(P7, wl.Psi, mu, P7.T @ U0, tol=1e-8)
+    assert rz["status"] == 0 and r7["status"] == 0
+    assert r7["shifts"] == 0
+    assert rz["shifts"] == rz["init_iters"] + rz["iters"] > 0  # one retry per factorisation
+    assert (rz["init_iters"], rz["iters"]) == (r7["init_iters"], r7["iters"])
+    assert rz["w"][-1] == 0.0
+    z = np.concatenate([rz["w"][:-1], rz["tau"]])
+    z7 = np.concatenate([r7["w"], r7["tau"]])
+    assert np.linalg.norm(z - z7) <= 1e-10 * np.linalg.norm(z7)
+    assert abs(rz["J"] - r7["J"]) <= 1e-12 * r7["J"]
