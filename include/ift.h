@@ -199,7 +199,9 @@ typedef struct {
   int fp32_iters;      /* mixed precision: joint-phase steps of the FP32 stage (iters counts the FP64 stage) */
   int fp32_trials;     /* mixed precision: objective evaluations of the FP32 stage */
   int h_evals;         /* mixed precision: evaluations of the FP64 stage that recomputed H (FP32
-                          Jacobian pass); the others kept the H of an earlier one */
+                          Jacobian pass); the others kept the H of an earlier one (at the
+                          stage's first point, the FP32 stage's last H when it was evaluated
+                          there) */
 } ift_solve_info;
 
 /* Levenberg-Marquardt solve of the hyperreduced problem (Sec. 3.2.3):

@@ -141,6 +141,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
   bool refresh_h = false;  // the next evaluation recomputes H (after a shortened step)
   if (lane == 0 && !s.done) {
     s.bodies += 1;
+    s.res_at_z = 0;
     if (c.keep_h && !s.hkeep) s.hevals += 1;
     if (s.bodies > c.body_limit) {
       s.status = IFT_ERR_TIMEOUT;
@@ -157,6 +158,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
         }
         s.J = Jr;
         s.state = 1;
+        s.res_at_z = 1;
         begin_phase(s, c);
         need_solve = decide(s, c);
       }
@@ -171,6 +173,7 @@ __device__ void lm_step_warp(LMState& s, const double* res, const LMConsts& c, d
         }
         s.J = Jr;
         s.iters[s.phase] += 1;
+        s.res_at_z = 1;
         need_solve = decide(s, c);
       } else if (s.h + 1 > c.max_halvings) {
         // line search failed: this phase ends at the current iterate
@@ -373,6 +376,7 @@ __global__ void lm_init_kernel(LMState* sp, const double* w0, const double* tau0
     s.trials32 = 0;
     s.hkeep = 0;
     s.hevals = 0;
+    s.res_at_z = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -420,6 +424,7 @@ __global__ void lm_init_batched_kernel(LMState* states, int B, int ku, int kx, i
     s.trials32 = 0;
     s.hkeep = 0;
     s.hevals = 0;
+    s.res_at_z = 0;
     s.lam = kLam0;
     s.alpha = 1.0;
     s.J = 0.0;
@@ -476,7 +481,11 @@ __device__ void restart_fp64(LMState& s, int k, int tid, int nthreads) {
     s.dz[i] = 0.0;
   }
   if (tid == 0) {
-    s.hkeep = 0;
+    // the FP32 stage's last result was evaluated at its final point (it ended on an
+    // accepted step or at its start, not on a rejected trial): the H of the result
+    // row is H there, which the first FP64-stage evaluation would recompute bit for
+    // bit (the same FP32 pass at the same point), so that evaluation keeps it
+    s.hkeep = s.res_at_z ? 1 : 0;
     s.iters32 = s.iters[1];
     s.trials32 = s.trials;
     s.iters[1] = 0;

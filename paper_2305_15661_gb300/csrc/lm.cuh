@@ -35,6 +35,7 @@ struct LMState {
   int iters32, trials32;  // joint-phase steps and trials of the FP32 stage of a mixed solve
   int hkeep;        // 1: the next evaluation leaves H as it is (no FP32 Jacobian pass)
   int hevals;       // evaluations with keep_h that recomputed H
+  int res_at_z;     // 1: the result the last step read was evaluated at the current iterate z
   double lam, alpha, J, slope, g0, thresh;
   double z[LM_KMAX];      // current iterate (w | tau)
   double dz[LM_KMAX];     // step

@@ -40,14 +40,16 @@ def test_mixed_solve_dense_matches_fp64_oracle():
     assert g["status"] == 0 and ref["status"] == 0
     # part of the joint iteration runs in FP32 and the FP64 stage is shorter than an FP64 solve
     assert g["fp32_iters"] > 0 and g["iters"] < ref["iters"]
-    # the FP64 stage recomputes H at its first point and after shortened steps only
-    assert 1 <= g["h_evals"] <= g["trials"] + 1
+    # the FP64 stage recomputes H after shortened steps only, and at its first point
+    # only if the FP32 stage's last result was not evaluated there
+    assert 0 <= g["h_evals"] <= g["trials"] + 1
     _certify(O, wl, mu, None, g["w"], g["tau"], ref, 1e-8)
 
 
 def test_mixed_finishing_stage_keeps_h():
-    # A finishing stage of several full steps: H is recomputed at its first point
-    # (and after any shortened step) only, the point still certified by the oracle.
+    # A finishing stage of several full steps: H is recomputed after a shortened step
+    # only (at its first point it is the FP32 stage's last H when that was evaluated
+    # there), the point still certified by the oracle.
     wl = W.euler_workload(n=12, p=2, k_u=12, k_x=4, seed=31, n_mu=3, mu_box=True)
     sets = W.eq_weight_sets(wl, 3, seed=32, lo=150, hi=250)
     ctx = ift.Context.from_workload(wl, precision=ift.MIXED, tol=1e-9)
@@ -59,7 +61,7 @@ def test_mixed_finishing_stage_keeps_h():
         i = res["info"][q]
         assert i["status"] == 0
         evals = i["trials"] + 1  # the restart point, then every trial point (new steps and halvings)
-        assert 1 <= i["h_evals"] <= evals
+        assert 0 <= i["h_evals"] <= evals
         kept += evals - i["h_evals"]
         mu = wl.mus[q]
         wg = wl.Phi.T @ W.replicate_guess(wl, W.freestream_state(wl.gamma, mu[0], mu[1]))
